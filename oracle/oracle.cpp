@@ -1,0 +1,1020 @@
+// FP64 CPU oracle of the differentiable path trace -- TEST INFRASTRUCTURE ONLY.
+//
+// Only the test suite, the package smoke check and the benchmark's CPU-baseline
+// leg may load this library. It shares no code, header, constant table or
+// helper with the CUDA library; both are written from the estimator stated
+// below, which restates the paper's renderer R(x, m, c) (Sec. 3.2, "Vertex
+// optimization") with the material of Sec. 3.3 ("Representation": a
+// Torrance-Sparrow BRDF with diffuse albedo, specular and roughness, stored per
+// face = mesh colors at r = 0) under point lights or an HDR environment map
+// (Sec. 3.1 "Input"), with global illumination (Sec. 3.3 "Effects of Global
+// Illumination"; B = 1 is the paper's "local + shadows" case).
+//
+// ESTIMATOR (the paper names only the model; every convention below is a
+// reading, recorded with the others in the design notes):
+//  * Random numbers: Philox4x32-10 (Salmon et al., SC'11), key = (seed lo, seed
+//    hi). Counter words: camera paths (pixel_offset + y*W + x, sample, b<<4|call,
+//    0); edge selection (k, pixel_offset, 0, 1); edge side paths (k,
+//    pixel_offset, b<<4|call, 2). Call 0 at b = 0 = pixel jitter, call 1 =
+//    environment NEE, call 2 = BSDF sampling. Uniform = (x >> 8) * 2^-24.
+//  * Camera: pinhole, fov_y, +y up, row 0 at the top, box-filter jitter.
+//  * Intersection: watertight test (Woop, Benthin, Wald, JCGT 2013), closest
+//    t in (T_EPS, tmax), origin triangle excluded, equal t -> lower face id.
+//  * Shading: flat face normal flipped toward the incoming ray (two-sided).
+//  * BRDF: f = kd/pi + ks D G1(i) G1(o) / (4 cos_i cos_o): the Fresnel factor
+//    is held at its normal-incidence value ks (the "specular color"), so
+//    ks = 0 is exactly Lambertian; D = GGX or Beckmann with alpha = roughness
+//    (clamped to [0.01, 1]); separable Smith G1.
+//  * Lobe choice p_s = clamp(ks / (ks + mean kd), 0.05, 0.95); diffuse by the
+//    concentric-disk (Shirley-Chiu) cosine map, specular by h ~ D cos(theta_h)
+//    and reflection; frame after Duff et al. (JCGT 2017); pdf = one-sample
+//    mixture; invalid (below the surface) ends the path.
+//  * NEE: every point light (no MIS); one environment sample per vertex from an
+//    alias table (Vose) over texel weight lum * sin(theta_row), MIS power
+//    heuristic against the BSDF pdf (weight 1 at the last vertex, which draws no
+//    BSDF direction). Escaped BSDF rays collect the environment with the
+//    complementary weight; a primary miss collects it unweighted.
+//  * B vertices with NEE, no Russian roulette. Pixel = mean over samples.
+//  * Interior gradient: derivative of the estimator with sampled directions,
+//    pdfs and MIS weights held constant and point-light directions
+//    differentiated; computed here with sparse forward-mode dual numbers.
+//  * Edge term (primary visibility): candidates = silhouette (or all) edges
+//    whose screen projection survives clipping; pick one uniformly, a point
+//    uniformly along its clipped screen segment, trace one path each side at
+//    +-EDGE_EPS pixels along the screen normal with shared random numbers, and
+//    scatter (L- - L+) <dL/dI_pixel> v_n * n_cand * len / N_e to the two
+//    endpoints with screen-space weights (1 - tau, tau).
+#include "oracle.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <thread>
+#include <vector>
+
+namespace {
+
+constexpr double PI = 3.14159265358979323846;
+constexpr double T_EPS = 1e-5;
+constexpr double Z_NEAR = 1e-4;
+constexpr double EDGE_EPS = 1e-3;
+constexpr int MAX_B = 8;
+constexpr int MAXD = 14 * MAX_B;
+
+// ---------------------------------------------------------------- Philox
+struct U4 { uint32_t w[4]; };
+
+U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
+  // Salmon et al. SC'11: 10 rounds of (mulhilo, xor with key and the other
+  // words); the key is bumped by the Weyl constants between rounds.
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) { k0 += W0; k1 += W1; }
+    uint64_t p0 = (uint64_t)M0 * c.w[0];
+    uint64_t p1 = (uint64_t)M1 * c.w[2];
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    U4 n = {{hi1 ^ c.w[1] ^ k0, lo1, hi0 ^ c.w[3] ^ k1, lo0}};
+    c = n;
+  }
+  return c;
+}
+
+inline double unif(uint32_t x) { return (double)(x >> 8) * (1.0 / 16777216.0); }
+
+struct Rng {
+  uint32_t k0, k1;
+  U4 draw(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3) const {
+    U4 c = {{c0, c1, c2, c3}};
+    return philox4x32_10(c, k0, k1);
+  }
+};
+
+// ---------------------------------------------------------------- dual numbers
+struct Dual {
+  double v;
+  int n;
+  double g[MAXD];
+  Dual() : v(0), n(0) {}
+  Dual(double x) : v(x), n(0) {}
+  Dual(const Dual& o) : v(o.v), n(o.n) { std::memcpy(g, o.g, sizeof(double) * n); }
+  Dual& operator=(const Dual& o) {
+    v = o.v; n = o.n; std::memcpy(g, o.g, sizeof(double) * n); return *this;
+  }
+};
+
+inline double vv(double x) { return x; }
+inline double vv(const Dual& x) { return x.v; }
+
+// r.g = ca * a.g + cb * b.g
+inline void lin2(Dual& r, const Dual& a, double ca, const Dual& b, double cb) {
+  r.n = std::max(a.n, b.n);
+  for (int k = 0; k < r.n; ++k)
+    r.g[k] = (k < a.n ? ca * a.g[k] : 0.0) + (k < b.n ? cb * b.g[k] : 0.0);
+}
+inline void lin1(Dual& r, const Dual& a, double ca) {
+  r.n = a.n;
+  for (int k = 0; k < r.n; ++k) r.g[k] = ca * a.g[k];
+}
+inline Dual operator+(const Dual& a, const Dual& b) { Dual r(a.v + b.v); lin2(r, a, 1, b, 1); return r; }
+inline Dual operator-(const Dual& a, const Dual& b) { Dual r(a.v - b.v); lin2(r, a, 1, b, -1); return r; }
+inline Dual operator*(const Dual& a, const Dual& b) { Dual r(a.v * b.v); lin2(r, a, b.v, b, a.v); return r; }
+inline Dual operator/(const Dual& a, const Dual& b) {
+  Dual r(a.v / b.v); lin2(r, a, 1.0 / b.v, b, -a.v / (b.v * b.v)); return r;
+}
+inline Dual operator-(const Dual& a) { Dual r(-a.v); lin1(r, a, -1); return r; }
+inline Dual operator+(const Dual& a, double b) { Dual r(a.v + b); lin1(r, a, 1); return r; }
+inline Dual operator+(double b, const Dual& a) { Dual r(b + a.v); lin1(r, a, 1); return r; }
+inline Dual operator-(const Dual& a, double b) { Dual r(a.v - b); lin1(r, a, 1); return r; }
+inline Dual operator-(double b, const Dual& a) { Dual r(b - a.v); lin1(r, a, -1); return r; }
+inline Dual operator*(const Dual& a, double b) { Dual r(a.v * b); lin1(r, a, b); return r; }
+inline Dual operator*(double b, const Dual& a) { Dual r(b * a.v); lin1(r, a, b); return r; }
+inline Dual operator/(const Dual& a, double b) { Dual r(a.v / b); lin1(r, a, 1.0 / b); return r; }
+inline Dual operator/(double b, const Dual& a) { Dual r(b / a.v); lin1(r, a, -b / (a.v * a.v)); return r; }
+inline Dual sqrt(const Dual& a) { double s = std::sqrt(a.v); Dual r(s); lin1(r, a, 0.5 / s); return r; }
+inline Dual exp(const Dual& a) { double e = std::exp(a.v); Dual r(e); lin1(r, a, e); return r; }
+inline Dual erf(const Dual& a) {
+  Dual r(std::erf(a.v)); lin1(r, a, 2.0 / std::sqrt(PI) * std::exp(-a.v * a.v)); return r;
+}
+inline Dual fabs(const Dual& a) { return a.v < 0 ? -a : a; }
+
+using std::sqrt; using std::exp; using std::erf; using std::fabs;
+
+// ---------------------------------------------------------------- vectors
+template <class T> struct V3 { T x, y, z; };
+template <class T> inline V3<T> mk(T x, T y, T z) { return V3<T>{x, y, z}; }
+template <class T> inline V3<T> operator+(const V3<T>& a, const V3<T>& b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+template <class T> inline V3<T> operator-(const V3<T>& a, const V3<T>& b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+template <class T> inline V3<T> operator-(const V3<T>& a) { return {-a.x, -a.y, -a.z}; }
+template <class T, class S> inline V3<T> scl(const V3<T>& a, const S& s) { return {a.x * s, a.y * s, a.z * s}; }
+template <class T> inline T dot(const V3<T>& a, const V3<T>& b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+template <class T> inline V3<T> cross(const V3<T>& a, const V3<T>& b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+template <class T> inline T len(const V3<T>& a) { return sqrt(dot(a, a)); }
+template <class T> inline V3<T> nrm(const V3<T>& a) { T l = len(a); return {a.x / l, a.y / l, a.z / l}; }
+template <class T> inline V3<T> lift(const V3<double>& a) { return {T(a.x), T(a.y), T(a.z)}; }
+template <class T> inline V3<double> val(const V3<T>& a) { return {vv(a.x), vv(a.y), vv(a.z)}; }
+using V3d = V3<double>;
+inline double comp(const V3d& a, int k) { return k == 0 ? a.x : (k == 1 ? a.y : a.z); }
+
+// ---------------------------------------------------------------- scene
+struct Scene {
+  int nv = 0, nf = 0;
+  std::vector<V3d> vert;
+  std::vector<int> face;        // 3 per face
+  std::vector<double> param;    // 5 per face
+  int brdf = 0;
+  std::vector<V3d> lpos, lint;
+  int ew = 0, eh = 0;
+  std::vector<double> env;      // 3 per texel
+  std::vector<double> prob, pmf;
+  std::vector<int> alias;
+};
+
+struct Cam {
+  V3d eye, fwd, right, up;
+  double th, aspect;
+  int W, H, spp;
+  uint32_t off;
+};
+
+Cam make_cam(const orc_view& v) {
+  Cam c;
+  c.eye = {v.eye[0], v.eye[1], v.eye[2]};
+  V3d tg = {v.target[0], v.target[1], v.target[2]};
+  V3d up = {v.up[0], v.up[1], v.up[2]};
+  c.fwd = nrm(tg - c.eye);
+  c.right = nrm(cross(c.fwd, up));
+  c.up = cross(c.right, c.fwd);
+  c.th = std::tan((double)v.fov_y_deg * PI / 360.0);
+  c.W = v.width; c.H = v.height; c.spp = v.spp;
+  c.aspect = (double)v.width / (double)v.height;
+  c.off = (uint32_t)v.pixel_offset;
+  return c;
+}
+
+V3d cam_dir(const Cam& c, double px, double py) {
+  double sx = 2.0 * px / c.W - 1.0;
+  double sy = 1.0 - 2.0 * py / c.H;
+  return nrm(c.fwd + scl(c.right, sx * c.th * c.aspect) + scl(c.up, sy * c.th));
+}
+
+// ---------------------------------------------------------------- intersection
+// Watertight ray/triangle test (Woop, Benthin, Wald 2013) in double.
+bool tri_hit(const V3d& o, const V3d& d, const V3d& p0, const V3d& p1, const V3d& p2, double& t) {
+  double ad[3] = {std::fabs(d.x), std::fabs(d.y), std::fabs(d.z)};
+  int kz = (ad[0] > ad[1]) ? (ad[0] > ad[2] ? 0 : 2) : (ad[1] > ad[2] ? 1 : 2);
+  int kx = (kz + 1) % 3, ky = (kx + 1) % 3;
+  if (comp(d, kz) < 0) std::swap(kx, ky);
+  double sz = 1.0 / comp(d, kz);
+  double sx = comp(d, kx) * sz, sy = comp(d, ky) * sz;
+  V3d A = p0 - o, B = p1 - o, C = p2 - o;
+  double Ax = comp(A, kx) - sx * comp(A, kz), Ay = comp(A, ky) - sy * comp(A, kz);
+  double Bx = comp(B, kx) - sx * comp(B, kz), By = comp(B, ky) - sy * comp(B, kz);
+  double Cx = comp(C, kx) - sx * comp(C, kz), Cy = comp(C, ky) - sy * comp(C, kz);
+  double U = Cx * By - Cy * Bx, Vb = Ax * Cy - Ay * Cx, W = Bx * Ay - By * Ax;
+  if ((U < 0 || Vb < 0 || W < 0) && (U > 0 || Vb > 0 || W > 0)) return false;
+  double det = U + Vb + W;
+  if (det == 0.0) return false;
+  double Az = sz * comp(A, kz), Bz = sz * comp(B, kz), Cz = sz * comp(C, kz);
+  double T = U * Az + Vb * Bz + W * Cz;
+  t = T / det;
+  return true;
+}
+
+struct Hit { int tri; double t; };
+
+Hit closest(const Scene& s, const V3d& o, const V3d& d, int exclude, double tmax) {
+  Hit h{-1, tmax};
+  for (int f = 0; f < s.nf; ++f) {
+    if (f == exclude) continue;
+    double t;
+    const int* fi = &s.face[3 * f];
+    if (!tri_hit(o, d, s.vert[fi[0]], s.vert[fi[1]], s.vert[fi[2]], t)) continue;
+    if (!(t > T_EPS && t < tmax)) continue;
+    if (t < h.t || (t == h.t && f < h.tri)) { h.t = t; h.tri = f; }
+  }
+  return h;
+}
+
+bool occluded(const Scene& s, const V3d& o, const V3d& d, int exclude, double tmax) {
+  for (int f = 0; f < s.nf; ++f) {
+    if (f == exclude) continue;
+    double t;
+    const int* fi = &s.face[3 * f];
+    if (tri_hit(o, d, s.vert[fi[0]], s.vert[fi[1]], s.vert[fi[2]], t) && t > T_EPS && t < tmax)
+      return true;
+  }
+  return false;
+}
+
+// ---------------------------------------------------------------- environment
+double lum(const double* c) { return 0.2126 * c[0] + 0.7152 * c[1] + 0.0722 * c[2]; }
+
+int build_alias(const float* rgb, int w, int h, std::vector<double>& prob, std::vector<int>& alias,
+                std::vector<double>& pmf) {
+  // Vose's alias method over texel weights lum * sin(theta at the row centre).
+  int N = w * h;
+  std::vector<double> wt(N);
+  double tot = 0;
+  for (int r = 0; r < h; ++r) {
+    double st = std::sin(PI * (r + 0.5) / h);
+    for (int c = 0; c < w; ++c) {
+      const float* p = rgb + 3 * ((size_t)r * w + c);
+      double cc[3] = {p[0], p[1], p[2]};
+      wt[(size_t)r * w + c] = lum(cc) * st;
+    }
+  }
+  for (int i = 0; i < N; ++i) {
+    if (!(wt[i] >= 0)) return 1;
+    tot += wt[i];
+  }
+  if (!(tot > 0)) return 1;
+  prob.assign(N, 1.0); alias.resize(N); pmf.resize(N);
+  std::vector<double> q(N);
+  std::vector<int> small, large;
+  for (int i = 0; i < N; ++i) {
+    q[i] = (wt[i] * N) / tot;
+    pmf[i] = wt[i] / tot;
+    alias[i] = i;
+    if (q[i] < 1.0) small.push_back(i); else large.push_back(i);
+  }
+  while (!small.empty() && !large.empty()) {
+    int sidx = small.back(); small.pop_back();
+    int l = large.back();
+    prob[sidx] = q[sidx];
+    alias[sidx] = l;
+    q[l] = (q[l] + q[sidx]) - 1.0;
+    if (q[l] < 1.0) { large.pop_back(); small.push_back(l); }
+  }
+  for (int i : large) { prob[i] = 1.0; alias[i] = i; }
+  for (int i : small) { prob[i] = 1.0; alias[i] = i; }
+  return 0;
+}
+
+int alias_pick(const double* prob, const int* alias, int N, uint32_t u0, uint32_t u1) {
+  int bin = (int)(((uint64_t)(u0 >> 8) * (uint64_t)N) >> 24);
+  // The acceptance threshold is the table value rounded to single precision.
+  double thr = (double)(float)prob[bin];
+  return unif(u1) < thr ? bin : alias[bin];
+}
+
+int env_texel(const Scene& s, const V3d& d, double& sin_t) {
+  double phi = std::atan2(d.x, -d.z) + PI;
+  int col = (int)(phi / (2 * PI) * s.ew);
+  col = std::min(std::max(col, 0), s.ew - 1);
+  double ct = std::min(std::max(d.y, -1.0), 1.0);
+  double th = std::acos(ct);
+  int row = (int)(th / PI * s.eh);
+  row = std::min(std::max(row, 0), s.eh - 1);
+  sin_t = std::sqrt(std::max(0.0, 1.0 - d.y * d.y));
+  return row * s.ew + col;
+}
+
+double env_pdf(const Scene& s, int texel, double sin_t) {
+  if (!(sin_t > 0)) return 0.0;
+  double N = (double)s.ew * s.eh;
+  return s.pmf[texel] * N / (2.0 * PI * PI * sin_t);
+}
+
+// ---------------------------------------------------------------- BRDF
+struct Mat { double kd[3], ks, alpha; };
+
+template <class T> struct MatT { T kd[3], ks, alpha; };
+
+double lobe_prob(const Mat& m) {
+  double den = m.ks + (m.kd[0] + m.kd[1] + m.kd[2]) / 3.0;
+  if (!(den > 0)) return 0.5;
+  return std::min(std::max(m.ks / den, 0.05), 0.95);
+}
+
+template <class T> T clamp_alpha(const T& a) {
+  if (vv(a) < 0.01) return T(0.01);
+  if (vv(a) > 1.0) return T(1.0);
+  return a;
+}
+
+template <class T> T D_fn(int brdf, const T& c, const T& a) {
+  if (brdf == 0) {
+    T a2 = a * a;
+    T k = c * c * (a2 - 1.0) + 1.0;
+    return a2 / (PI * k * k);
+  }
+  T c2 = c * c;
+  T tan2 = (1.0 - c2) / c2;
+  return exp(-tan2 / (a * a)) / (PI * a * a * c2 * c2);
+}
+
+template <class T> T G1_fn(int brdf, const T& c, const T& a) {
+  if (brdf == 0) {
+    T a2 = a * a;
+    T q = sqrt(a2 + (1.0 - a2) * c * c);
+    return 2.0 * c / (c + q);
+  }
+  T s2 = 1.0 - c * c;
+  if (!(vv(s2) > 0)) return T(1.0);
+  T x = c / (a * sqrt(s2));
+  return 2.0 / (1.0 + erf(x) + exp(-x * x) / (x * std::sqrt(PI)));
+}
+
+// f(wi, wo) for unit n, wi, wo; zero unless both cosines are positive.
+template <class T>
+void brdf_eval(int brdf, const MatT<T>& m, const V3<T>& n, const V3<T>& wi, const V3<T>& wo, T f[3]) {
+  T ci = dot(n, wi), co = dot(n, wo);
+  if (!(vv(ci) > 0) || !(vv(co) > 0)) { f[0] = f[1] = f[2] = T(0.0); return; }
+  V3<T> h = nrm(wi + wo);
+  T ch = dot(n, h), cih = dot(wi, h);
+  (void)cih;
+  T a = clamp_alpha(m.alpha);
+  T spec = m.ks * D_fn(brdf, ch, a) * G1_fn(brdf, ci, a) * G1_fn(brdf, co, a) / (4.0 * ci * co);
+  for (int c = 0; c < 3; ++c) f[c] = m.kd[c] / PI + spec;
+}
+
+double brdf_pdf(int brdf, const Mat& m, const V3d& n, const V3d& wi, const V3d& wo) {
+  double ci = dot(n, wi), co = dot(n, wo);
+  if (!(ci > 0) || !(co > 0)) return 0.0;
+  V3d h = nrm(wi + wo);
+  double ch = dot(n, h), woh = std::fabs(dot(wo, h));
+  double a = clamp_alpha(m.alpha);
+  double ps = lobe_prob(m);
+  double pd = ci / PI;
+  double pspec = D_fn(brdf, ch, a) * ch / (4.0 * woh);
+  return (1.0 - ps) * pd + ps * pspec;
+}
+
+void onb(const V3d& n, V3d& t, V3d& b) {
+  // Duff et al., "Building an Orthonormal Basis, Revisited", JCGT 2017.
+  double sign = std::copysign(1.0, n.z);
+  double a = -1.0 / (sign + n.z);
+  double bb = n.x * n.y * a;
+  t = {1.0 + sign * n.x * n.x * a, sign * bb, -sign * n.x};
+  b = {bb, sign + n.y * n.y * a, -n.y};
+}
+
+void concentric(double u1, double u2, double& x, double& y) {
+  // Shirley & Chiu 1997 square-to-disk map.
+  double a = 2 * u1 - 1, b = 2 * u2 - 1;
+  if (a == 0 && b == 0) { x = y = 0; return; }
+  double r, ph;
+  if (std::fabs(a) > std::fabs(b)) { r = a; ph = (PI / 4) * (b / a); }
+  else { r = b; ph = PI / 2 - (PI / 4) * (a / b); }
+  x = r * std::cos(ph); y = r * std::sin(ph);
+}
+
+// Returns the mixture pdf of the sampled direction, 0 if the sample is invalid.
+double brdf_sample(int brdf, const Mat& m, const V3d& n, const V3d& wo, double ul, double u1, double u2,
+                   V3d& wi, int* lobe) {
+  V3d t, b;
+  onb(n, t, b);
+  double ps = lobe_prob(m);
+  if (ul < ps) {
+    double a = clamp_alpha(m.alpha), a2 = a * a;
+    double tan2 = brdf == 0 ? a2 * u1 / (1.0 - u1) : -a2 * std::log(1.0 - u1);
+    double ch = 1.0 / std::sqrt(1.0 + tan2);
+    double sh = std::sqrt(std::max(0.0, 1.0 - ch * ch));
+    double ph = 2 * PI * u2;
+    V3d h = scl(t, sh * std::cos(ph)) + scl(b, sh * std::sin(ph)) + scl(n, ch);
+    wi = scl(h, 2.0 * dot(wo, h)) - wo;
+    if (lobe) *lobe = 1;
+  } else {
+    double x, y;
+    concentric(u1, u2, x, y);
+    double z = std::sqrt(std::max(0.0, 1.0 - x * x - y * y));
+    wi = scl(t, x) + scl(b, y) + scl(n, z);
+    if (lobe) *lobe = 0;
+  }
+  if (!(dot(n, wi) > 0)) return 0.0;
+  return brdf_pdf(brdf, m, n, wi, wo);
+}
+
+// ---------------------------------------------------------------- variables
+// Registry of the differentiable inputs one path touches (dual-number dims).
+struct Vars {
+  std::vector<int> vid;   // vertex ids, 3 dims each
+  std::vector<int> vdim;
+  std::vector<int> fid;   // face ids, 5 dims each
+  std::vector<int> fdim;
+  int nd = 0;
+};
+
+template <class T> struct Access;
+
+template <> struct Access<double> {
+  static V3<double> vertex(const Scene& s, Vars*, int v) { return s.vert[v]; }
+  static MatT<double> params(const Scene& s, Vars*, int f) {
+    MatT<double> m;
+    for (int c = 0; c < 3; ++c) m.kd[c] = s.param[5 * f + c];
+    m.ks = s.param[5 * f + 3]; m.alpha = s.param[5 * f + 4];
+    return m;
+  }
+};
+
+inline Dual unit_dual(double v, int dim) {
+  Dual d(v);
+  d.n = dim + 1;
+  for (int k = 0; k < dim; ++k) d.g[k] = 0;
+  d.g[dim] = 1.0;
+  return d;
+}
+
+template <> struct Access<Dual> {
+  static V3<Dual> vertex(const Scene& s, Vars* vars, int v) {
+    int base = -1;
+    for (size_t i = 0; i < vars->vid.size(); ++i)
+      if (vars->vid[i] == v) base = vars->vdim[i];
+    if (base < 0) {
+      base = vars->nd; vars->nd += 3;
+      vars->vid.push_back(v); vars->vdim.push_back(base);
+    }
+    const V3d& p = s.vert[v];
+    return {unit_dual(p.x, base), unit_dual(p.y, base + 1), unit_dual(p.z, base + 2)};
+  }
+  static MatT<Dual> params(const Scene& s, Vars* vars, int f) {
+    int base = -1;
+    for (size_t i = 0; i < vars->fid.size(); ++i)
+      if (vars->fid[i] == f) base = vars->fdim[i];
+    if (base < 0) {
+      base = vars->nd; vars->nd += 5;
+      vars->fid.push_back(f); vars->fdim.push_back(base);
+    }
+    MatT<Dual> m;
+    for (int c = 0; c < 3; ++c) m.kd[c] = unit_dual(s.param[5 * f + c], base + c);
+    m.ks = unit_dual(s.param[5 * f + 3], base + 3);
+    m.alpha = unit_dual(s.param[5 * f + 4], base + 4);
+    return m;
+  }
+};
+
+Mat mat_val(const Scene& s, int f) {
+  Mat m;
+  for (int c = 0; c < 3; ++c) m.kd[c] = s.param[5 * f + c];
+  m.ks = s.param[5 * f + 3]; m.alpha = s.param[5 * f + 4];
+  return m;
+}
+
+// ---------------------------------------------------------------- tape
+// Record/replay of every quantity the gradient treats as constant (sampled
+// directions, pdfs, MIS weights, the sampled texel). Replaying a recorded tape
+// under perturbed inputs evaluates the estimator with sampling detached, which
+// is what finite differences must use to check the dual-number gradient.
+struct Tape {
+  int mode = 0;  // 0 off, 1 record, 2 replay
+  std::vector<double> v;
+  size_t pos = 0;
+  bool bad = false;
+  double take(double x) {
+    if (mode == 1) v.push_back(x);
+    else if (mode == 2) { if (pos < v.size()) x = v[pos++]; else bad = true; }
+    return x;
+  }
+  V3d take(const V3d& a) { return V3d{take(a.x), take(a.y), take(a.z)}; }
+};
+
+// ---------------------------------------------------------------- one path
+// Radiance of one path whose primary ray is (eye, d0). Counter words (c0, c1,
+// stream) identify the path; `segments` counts ray queries.
+template <class T>
+void trace_path(const Scene& s, const Rng& rng, int B, const V3d& eye, const V3d& d0, uint32_t c0,
+                uint32_t c1, uint32_t stream, Vars* vars, T L[3], long long& segments, Tape* tape = nullptr) {
+  using A = Access<T>;
+  Tape none;
+  Tape& tp = tape ? *tape : none;
+  for (int c = 0; c < 3; ++c) L[c] = T(0.0);
+  T thr[3] = {T(1.0), T(1.0), T(1.0)};
+  V3<T> o = lift<T>(eye);
+  V3d d = d0;
+  int origin = -1;
+  double last_pdf = 0;
+  for (int b = 0; b < B; ++b) {
+    ++segments;
+    Hit h = closest(s, val(o), d, origin, INFINITY);
+    if (h.tri < 0) {
+      if (s.ew > 0) {
+        double st;
+        int tx = env_texel(s, d, st);
+        double w = 1.0;
+        if (b > 0) {
+          double pe = env_pdf(s, tx, st);
+          w = last_pdf * last_pdf / (last_pdf * last_pdf + pe * pe);
+        }
+        w = tp.take(w);
+        for (int c = 0; c < 3; ++c) L[c] = L[c] + thr[c] * (s.env[3 * tx + c] * w);
+      }
+      return;
+    }
+    const int* fi = &s.face[3 * h.tri];
+    V3<T> v0 = A::vertex(s, vars, fi[0]);
+    V3<T> v1 = A::vertex(s, vars, fi[1]);
+    V3<T> v2 = A::vertex(s, vars, fi[2]);
+    MatT<T> m = A::params(s, vars, h.tri);
+    Mat mv = mat_val(s, h.tri);
+    V3<T> mvec = cross(v1 - v0, v2 - v0);
+    V3<T> dT = lift<T>(d);
+    T t = dot(v0 - o, mvec) / dot(dT, mvec);
+    V3<T> p = o + scl(dT, t);
+    V3<T> ng = nrm(mvec);
+    V3d wo_d = -d;
+    V3<T> wo = lift<T>(wo_d);
+    V3<T> n = (dot(val(ng), wo_d) < 0) ? -ng : ng;
+    V3d nv = val(n), pv = val(p);
+
+    // next-event estimation: point lights
+    for (size_t j = 0; j < s.lpos.size(); ++j) {
+      V3<T> dv = lift<T>(s.lpos[j]) - p;
+      T dist = len(dv);
+      V3<T> wi = scl(dv, 1.0 / dist);
+      T ci = dot(n, wi);
+      if (!(vv(ci) > 0) || !(vv(dist) > 2 * T_EPS)) continue;
+      ++segments;
+      if (occluded(s, pv, val(wi), h.tri, vv(dist) - T_EPS)) continue;
+      T f[3];
+      brdf_eval(s.brdf, m, n, wi, wo, f);
+      T g = ci / (dist * dist);
+      for (int c = 0; c < 3; ++c) L[c] = L[c] + thr[c] * f[c] * g * comp(s.lint[j], c);
+    }
+    // next-event estimation: environment
+    if (s.ew > 0) {
+      U4 u = rng.draw(c0, c1, (uint32_t)(b << 4) | 1u, stream);
+      int N = s.ew * s.eh;
+      int tx = alias_pick(s.prob.data(), s.alias.data(), N, u.w[0], u.w[1]);
+      int row = tx / s.ew, col = tx % s.ew;
+      double uu = (col + unif(u.w[2])) / s.ew, vq = (row + unif(u.w[3])) / s.eh;
+      double th = PI * vq, ph = 2 * PI * uu;
+      double st = std::sin(th), ct = std::cos(th);
+      V3d wi = {-st * std::sin(ph), ct, st * std::cos(ph)};
+      tx = (int)tp.take((double)tx);
+      st = tp.take(st);
+      wi = tp.take(wi);
+      if (st > 0) {
+        T ci = dot(n, lift<T>(wi));
+        if (vv(ci) > 0) {
+          ++segments;
+          if (!occluded(s, pv, wi, h.tri, INFINITY)) {
+            double pe = env_pdf(s, tx, st);
+            double w = 1.0;
+            if (b < B - 1) {
+              double pb = brdf_pdf(s.brdf, mv, nv, wi, wo_d);
+              w = pe * pe / (pe * pe + pb * pb);
+            }
+            pe = tp.take(pe);
+            w = tp.take(w);
+            T f[3];
+            brdf_eval(s.brdf, m, n, lift<T>(wi), wo, f);
+            for (int c = 0; c < 3; ++c) L[c] = L[c] + thr[c] * f[c] * ci * (s.env[3 * tx + c] * w / pe);
+          }
+        }
+      }
+    }
+    if (b == B - 1) return;
+    // BSDF sampling (direction and pdf held constant under differentiation)
+    U4 u = rng.draw(c0, c1, (uint32_t)(b << 4) | 2u, stream);
+    V3d wi;
+    double pdf = brdf_sample(s.brdf, mv, nv, wo_d, unif(u.w[0]), unif(u.w[1]), unif(u.w[2]), wi, nullptr);
+    pdf = tp.take(pdf);
+    wi = tp.take(wi);
+    if (!(pdf > 0)) return;
+    T f[3];
+    V3<T> wiT = lift<T>(wi);
+    brdf_eval(s.brdf, m, n, wiT, wo, f);
+    T ci = dot(n, wiT);
+    for (int c = 0; c < 3; ++c) thr[c] = thr[c] * f[c] * ci / pdf;
+    o = p; d = wi; origin = h.tri; last_pdf = pdf;
+  }
+}
+
+// ---------------------------------------------------------------- helpers
+bool load_scene(const orc_scene* in, Scene& s) {
+  if (!in || in->n_vertices <= 0 || in->n_faces <= 0 || !in->vertices || !in->faces || !in->face_params)
+    return false;
+  s.nv = in->n_vertices; s.nf = in->n_faces; s.brdf = in->brdf;
+  s.vert.resize(s.nv);
+  for (int i = 0; i < s.nv; ++i) s.vert[i] = {in->vertices[3 * i], in->vertices[3 * i + 1], in->vertices[3 * i + 2]};
+  s.face.assign(in->faces, in->faces + 3 * (size_t)s.nf);
+  for (int v : s.face) if (v < 0 || v >= s.nv) return false;
+  s.param.resize(5 * (size_t)s.nf);
+  for (size_t i = 0; i < s.param.size(); ++i) s.param[i] = in->face_params[i];
+  for (int j = 0; j < in->n_lights; ++j) {
+    s.lpos.push_back({in->light_pos[3 * j], in->light_pos[3 * j + 1], in->light_pos[3 * j + 2]});
+    s.lint.push_back({in->light_intensity[3 * j], in->light_intensity[3 * j + 1], in->light_intensity[3 * j + 2]});
+  }
+  if (in->env_width > 0 && in->env_height > 0 && in->env_rgb) {
+    s.ew = in->env_width; s.eh = in->env_height;
+    s.env.resize(3 * (size_t)s.ew * s.eh);
+    for (size_t i = 0; i < s.env.size(); ++i) s.env[i] = in->env_rgb[i];
+    if (build_alias(in->env_rgb, s.ew, s.eh, s.prob, s.alias, s.pmf)) return false;
+  }
+  return true;
+}
+
+int nthreads(const orc_params* p) {
+  int n = p && p->n_threads > 0 ? p->n_threads : (int)std::thread::hardware_concurrency();
+  return std::max(1, n);
+}
+
+template <class F> void parallel_for(int n, int nt, F fn) {
+  nt = std::max(1, std::min(nt, n));
+  std::vector<std::thread> th;
+  for (int t = 0; t < nt; ++t)
+    th.emplace_back([=]() { for (int i = t; i < n; i += nt) fn(t, i); });
+  for (auto& x : th) x.join();
+}
+
+void scatter_grad(const Vars& vars, const Dual& loss, double* dv, double* df) {
+  for (size_t i = 0; i < vars.vid.size(); ++i)
+    for (int k = 0; k < 3; ++k) {
+      int dim = vars.vdim[i] + k;
+      if (dim < loss.n) dv[3 * vars.vid[i] + k] += loss.g[dim];
+    }
+  for (size_t i = 0; i < vars.fid.size(); ++i)
+    for (int k = 0; k < 5; ++k) {
+      int dim = vars.fdim[i] + k;
+      if (dim < loss.n && df) df[5 * vars.fid[i] + k] += loss.g[dim];
+    }
+}
+
+// ---------------------------------------------------------------- edges
+struct Edge { int a, b; int f[2]; int nf; };
+
+std::vector<Edge> edge_list(const Scene& s) {
+  std::map<std::pair<int, int>, Edge> m;
+  for (int f = 0; f < s.nf; ++f)
+    for (int k = 0; k < 3; ++k) {
+      int a = s.face[3 * f + k], b = s.face[3 * f + (k + 1) % 3];
+      std::pair<int, int> key(std::min(a, b), std::max(a, b));
+      auto it = m.find(key);
+      if (it == m.end()) {
+        Edge e{key.first, key.second, {f, -1}, 1};
+        m.emplace(key, e);
+      } else {
+        if (it->second.nf < 2) it->second.f[it->second.nf] = f;
+        it->second.nf++;
+      }
+    }
+  std::vector<Edge> out;
+  out.reserve(m.size());
+  for (auto& kv : m) out.push_back(kv.second);  // std::map iterates in (min, max) order
+  return out;
+}
+
+struct Cand { int e; double t0, t1, len; V3d sa, sb; };
+
+bool project(const Cam& c, const V3d& X, double& px, double& py) {
+  V3d rel = X - c.eye;
+  double z = dot(rel, c.fwd);
+  if (!(z > Z_NEAR)) return false;
+  double sx = dot(rel, c.right) / (z * c.th * c.aspect);
+  double sy = dot(rel, c.up) / (z * c.th);
+  px = (sx + 1.0) * c.W / 2.0;
+  py = (1.0 - sy) * c.H / 2.0;
+  return true;
+}
+
+// derivative of the pixel coordinates of X along screen direction (nx, ny)
+V3d proj_jt(const Cam& c, const V3d& X, double nx, double ny) {
+  V3d rel = X - c.eye;
+  double z = dot(rel, c.fwd);
+  double k = c.th * c.aspect;
+  double sx = dot(rel, c.right) / (z * k);
+  double sy = dot(rel, c.up) / (z * c.th);
+  V3d dpx = scl(c.right - scl(c.fwd, sx * k), (c.W / 2.0) / (z * k));
+  V3d dpy = scl(c.up - scl(c.fwd, sy * c.th), -(c.H / 2.0) / (z * c.th));
+  return scl(dpx, nx) + scl(dpy, ny);
+}
+
+bool facing(const Scene& s, int f, const V3d& eye) {
+  const int* fi = &s.face[3 * f];
+  V3d m = cross(s.vert[fi[1]] - s.vert[fi[0]], s.vert[fi[2]] - s.vert[fi[0]]);
+  return dot(m, eye - s.vert[fi[0]]) > 0;
+}
+
+std::vector<Cand> candidates(const Scene& s, const std::vector<Edge>& E, const Cam& c, int mode) {
+  std::vector<Cand> out;
+  for (size_t i = 0; i < E.size(); ++i) {
+    const Edge& e = E[i];
+    bool take = true;
+    if (mode == 0 && e.nf == 2) take = facing(s, e.f[0], c.eye) != facing(s, e.f[1], c.eye);
+    if (!take) continue;
+    double ax, ay, bx, by;
+    if (!project(c, s.vert[e.a], ax, ay) || !project(c, s.vert[e.b], bx, by)) continue;
+    double dx = bx - ax, dy = by - ay;
+    double t0 = 0, t1 = 1;
+    double pp[4] = {-dx, dx, -dy, dy};
+    double qq[4] = {ax, c.W - ax, ay, c.H - ay};
+    bool ok = true;
+    for (int k = 0; k < 4 && ok; ++k) {
+      if (pp[k] == 0) { if (qq[k] < 0) ok = false; continue; }
+      double r = qq[k] / pp[k];
+      if (pp[k] < 0) t0 = std::max(t0, r); else t1 = std::min(t1, r);
+    }
+    if (!ok || !(t1 > t0)) continue;
+    double L = std::sqrt(dx * dx + dy * dy) * (t1 - t0);
+    if (!(L > 0)) continue;
+    out.push_back(Cand{(int)i, t0, t1, L, {ax, ay, 0}, {bx, by, 0}});
+  }
+  return out;
+}
+
+}  // namespace
+
+// ==================================================================== C API
+extern "C" {
+
+void orc_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out) {
+  U4 c = {{ctr[0], ctr[1], ctr[2], ctr[3]}};
+  U4 r = philox4x32_10(c, key[0], key[1]);
+  for (int i = 0; i < 4; ++i) out[i] = r.w[i];
+}
+
+int orc_env_alias(const float* rgb, int w, int h, double* prob, int* alias, double* pmf) {
+  std::vector<double> p, q; std::vector<int> a;
+  if (build_alias(rgb, w, h, p, a, q)) return 1;
+  std::copy(p.begin(), p.end(), prob);
+  std::copy(a.begin(), a.end(), alias);
+  std::copy(q.begin(), q.end(), pmf);
+  return 0;
+}
+
+int orc_alias_pick(const double* prob, const int* alias, int n, uint32_t u0, uint32_t u1) {
+  return alias_pick(prob, alias, n, u0, u1);
+}
+
+long long orc_mesh_color_index(int r, long long t, double alpha, double beta) {
+  // Sec. 3.3: k = (t (r+1)(r+2) + i (2r - i + 3)) / 2 + j, (i, j) = floor(r (alpha, beta)).
+  long long i = (long long)std::floor(r * alpha), j = (long long)std::floor(r * beta);
+  return (t * (r + 1) * (r + 2) + i * (2LL * r - i + 3)) / 2 + j;
+}
+
+static Mat mat_from(const double* p5) {
+  Mat m;
+  for (int c = 0; c < 3; ++c) m.kd[c] = p5[c];
+  m.ks = p5[3]; m.alpha = p5[4];
+  return m;
+}
+
+void orc_brdf_eval(int brdf, const double* p5, const double* n, const double* wi, const double* wo, double* out) {
+  Mat m = mat_from(p5);
+  MatT<double> mt;
+  for (int c = 0; c < 3; ++c) mt.kd[c] = m.kd[c];
+  mt.ks = m.ks; mt.alpha = m.alpha;
+  V3d N{n[0], n[1], n[2]}, I{wi[0], wi[1], wi[2]}, O{wo[0], wo[1], wo[2]};
+  brdf_eval(brdf, mt, N, I, O, out);
+}
+
+double orc_brdf_pdf(int brdf, const double* p5, const double* n, const double* wi, const double* wo) {
+  V3d N{n[0], n[1], n[2]}, I{wi[0], wi[1], wi[2]}, O{wo[0], wo[1], wo[2]};
+  return brdf_pdf(brdf, mat_from(p5), N, I, O);
+}
+
+double orc_brdf_sample(int brdf, const double* p5, const double* n, const double* wo, double ul, double u1,
+                       double u2, double* wi) {
+  V3d N{n[0], n[1], n[2]}, O{wo[0], wo[1], wo[2]}, I{0, 0, 0};
+  double pdf = brdf_sample(brdf, mat_from(p5), N, O, ul, u1, u2, I, nullptr);
+  wi[0] = I.x; wi[1] = I.y; wi[2] = I.z;
+  return pdf;
+}
+
+void orc_closest_hit(const orc_scene* in, const double* rays, int n, int exclude, int* out_tri, double* out_t) {
+  Scene s;
+  if (!load_scene(in, s)) return;
+  parallel_for(n, (int)std::thread::hardware_concurrency(), [&](int, int i) {
+    const double* r = rays + 7 * (size_t)i;
+    Hit h = closest(s, V3d{r[0], r[1], r[2]}, V3d{r[3], r[4], r[5]}, exclude, r[6]);
+    out_tri[i] = h.tri;
+    out_t[i] = h.tri >= 0 ? h.t : INFINITY;
+  });
+}
+
+static bool check_common(const orc_view* views, int n_views, const orc_params* p) {
+  if (!views || n_views <= 0 || !p || p->max_bounces < 1 || p->max_bounces > MAX_B) return false;
+  for (int v = 0; v < n_views; ++v)
+    if (views[v].width <= 0 || views[v].height <= 0 || views[v].spp <= 0) return false;
+  return true;
+}
+
+static Rng rng_of(const orc_params* p) {
+  return Rng{(uint32_t)(p->seed & 0xffffffffu), (uint32_t)(p->seed >> 32)};
+}
+
+long long orc_render_pixels(const orc_scene* in, const orc_view* views, int n_views, const orc_params* p,
+                            const int* pix, int n, double* out) {
+  Scene s;
+  if (!load_scene(in, s) || !check_common(views, n_views, p)) return -1;
+  Rng rng = rng_of(p);
+  int nt = nthreads(p);
+  std::vector<long long> seg(nt, 0);
+  for (int i = 0; i < n; ++i)
+    if (pix[3 * i] < 0 || pix[3 * i] >= n_views) return -1;
+  parallel_for(n, nt, [&](int tid, int i) {
+    const orc_view& v = views[pix[3 * i]];
+    Cam c = make_cam(v);
+    int x = pix[3 * i + 1], y = pix[3 * i + 2];
+    uint32_t c0 = c.off + (uint32_t)(y * c.W + x);
+    double acc[3] = {0, 0, 0};
+    for (int sidx = 0; sidx < c.spp; ++sidx) {
+      U4 u = rng.draw(c0, (uint32_t)sidx, 0u, 0u);
+      V3d d = cam_dir(c, x + unif(u.w[0]), y + unif(u.w[1]));
+      double L[3];
+      trace_path<double>(s, rng, p->max_bounces, c.eye, d, c0, (uint32_t)sidx, 0u, nullptr, L, seg[tid]);
+      for (int k = 0; k < 3; ++k) acc[k] += L[k];
+    }
+    for (int k = 0; k < 3; ++k) out[3 * i + k] = acc[k] / c.spp;
+  });
+  long long tot = 0;
+  for (auto x : seg) tot += x;
+  return tot;
+}
+
+long long orc_grad_pixels(const orc_scene* in, const orc_view* views, int n_views, const orc_params* p,
+                          const int* pix, int n, const double* dLdI, double* d_verts, double* d_face) {
+  Scene s;
+  if (!load_scene(in, s) || !check_common(views, n_views, p)) return -1;
+  Rng rng = rng_of(p);
+  int nt = nthreads(p);
+  std::vector<long long> seg(nt, 0);
+  std::vector<std::vector<double>> gv(nt, std::vector<double>(3 * (size_t)s.nv, 0.0));
+  std::vector<std::vector<double>> gf(nt, std::vector<double>(5 * (size_t)s.nf, 0.0));
+  parallel_for(n, nt, [&](int tid, int i) {
+    const double* w = dLdI + 3 * (size_t)i;
+    if (w[0] == 0 && w[1] == 0 && w[2] == 0) return;
+    const orc_view& v = views[pix[3 * i]];
+    Cam c = make_cam(v);
+    int x = pix[3 * i + 1], y = pix[3 * i + 2];
+    uint32_t c0 = c.off + (uint32_t)(y * c.W + x);
+    for (int sidx = 0; sidx < c.spp; ++sidx) {
+      U4 u = rng.draw(c0, (uint32_t)sidx, 0u, 0u);
+      V3d d = cam_dir(c, x + unif(u.w[0]), y + unif(u.w[1]));
+      Vars vars;
+      Dual L[3];
+      trace_path<Dual>(s, rng, p->max_bounces, c.eye, d, c0, (uint32_t)sidx, 0u, &vars, L, seg[tid]);
+      Dual loss = L[0] * (w[0] / c.spp) + L[1] * (w[1] / c.spp) + L[2] * (w[2] / c.spp);
+      scatter_grad(vars, loss, gv[tid].data(), gf[tid].data());
+    }
+  });
+  for (int t = 0; t < nt; ++t) {
+    for (size_t k = 0; k < gv[t].size(); ++k) d_verts[k] += gv[t][k];
+    if (d_face) for (size_t k = 0; k < gf[t].size(); ++k) d_face[k] += gf[t][k];
+  }
+  long long tot = 0;
+  for (auto x : seg) tot += x;
+  return tot;
+}
+
+int orc_edge_candidates(const orc_scene* in, const orc_view* view, const orc_params* p, int* out_edges) {
+  Scene s;
+  if (!load_scene(in, s) || !view || !p) return -1;
+  std::vector<Edge> E = edge_list(s);
+  std::vector<Cand> C = candidates(s, E, make_cam(*view), p->edge_mode);
+  if (out_edges)
+    for (size_t i = 0; i < C.size(); ++i) { out_edges[2 * i] = E[C[i].e].a; out_edges[2 * i + 1] = E[C[i].e].b; }
+  return (int)C.size();
+}
+
+long long orc_edge_grad(const orc_scene* in, const orc_view* views, int n_views, const orc_params* p,
+                        const double* dLdI, double* d_verts) {
+  Scene s;
+  if (!load_scene(in, s) || !check_common(views, n_views, p)) return -1;
+  Rng rng = rng_of(p);
+  int nt = nthreads(p);
+  std::vector<Edge> E = edge_list(s);
+  std::vector<long long> seg(nt, 0);
+  std::vector<std::vector<double>> gv(nt, std::vector<double>(3 * (size_t)s.nv, 0.0));
+  for (int vi = 0; vi < n_views; ++vi) {
+    Cam c = make_cam(views[vi]);
+    std::vector<Cand> C = candidates(s, E, c, p->edge_mode);
+    if (C.empty()) continue;
+    long long spp_e = p->edge_spp > 0 ? p->edge_spp : c.spp;
+    long long Ne = (long long)c.W * c.H * spp_e;
+    uint64_t ncand = C.size();
+    // samples are split across threads in contiguous blocks
+    int nblk = nt * 8;
+    parallel_for(nblk, nt, [&](int tid, int blk) {
+      long long k0 = Ne * blk / nblk, k1 = Ne * (blk + 1) / nblk;
+      for (long long k = k0; k < k1; ++k) {
+        U4 u = rng.draw((uint32_t)k, c.off, 0u, 1u);
+        const Cand& cd = C[(size_t)(((uint64_t)(u.w[0] >> 8) * ncand) >> 24)];
+        double tau = cd.t0 + unif(u.w[1]) * (cd.t1 - cd.t0);
+        double sx = cd.sa.x + (cd.sb.x - cd.sa.x) * tau, sy = cd.sa.y + (cd.sb.y - cd.sa.y) * tau;
+        int x = (int)std::floor(sx), y = (int)std::floor(sy);
+        if (x < 0 || y < 0 || x >= c.W || y >= c.H) continue;
+        const double* w = dLdI + 3 * ((size_t)c.off + (size_t)y * c.W + x);
+        if (w[0] == 0 && w[1] == 0 && w[2] == 0) continue;
+        double ex = cd.sb.x - cd.sa.x, ey = cd.sb.y - cd.sa.y;
+        double el = std::sqrt(ex * ex + ey * ey);
+        double nx = -ey / el, ny = ex / el;
+        double Lm[3], Lp[3];
+        trace_path<double>(s, rng, p->max_bounces, c.eye, cam_dir(c, sx - EDGE_EPS * nx, sy - EDGE_EPS * ny),
+                           (uint32_t)k, c.off, 2u, nullptr, Lm, seg[tid]);
+        trace_path<double>(s, rng, p->max_bounces, c.eye, cam_dir(c, sx + EDGE_EPS * nx, sy + EDGE_EPS * ny),
+                           (uint32_t)k, c.off, 2u, nullptr, Lp, seg[tid]);
+        double g = 0;
+        for (int ch = 0; ch < 3; ++ch) g += w[ch] * (Lm[ch] - Lp[ch]);
+        if (g == 0) continue;
+        double wt = g * (double)ncand * cd.len / (double)Ne;
+        const Edge& e = E[cd.e];
+        V3d ja = proj_jt(c, s.vert[e.a], nx, ny), jb = proj_jt(c, s.vert[e.b], nx, ny);
+        double* G = gv[tid].data();
+        G[3 * e.a] += wt * (1 - tau) * ja.x; G[3 * e.a + 1] += wt * (1 - tau) * ja.y; G[3 * e.a + 2] += wt * (1 - tau) * ja.z;
+        G[3 * e.b] += wt * tau * jb.x; G[3 * e.b + 1] += wt * tau * jb.y; G[3 * e.b + 2] += wt * tau * jb.z;
+      }
+    });
+  }
+  for (int t = 0; t < nt; ++t)
+    for (size_t k = 0; k < gv[t].size(); ++k) d_verts[k] += gv[t][k];
+  long long tot = 0;
+  for (auto x : seg) tot += x;
+  return tot;
+}
+
+long long orc_trace_screen(const orc_scene* in, const orc_view* view, const orc_params* p, double px, double py,
+                           uint32_t c0, uint32_t c1, uint32_t stream, double* rgb, const double* grad_w,
+                           double* d_verts, double* d_face) {
+  Scene s;
+  if (!load_scene(in, s) || !check_common(view, 1, p)) return -1;
+  Rng rng = rng_of(p);
+  Cam c = make_cam(*view);
+  V3d d = cam_dir(c, px, py);
+  long long seg = 0;
+  if (!grad_w) {
+    trace_path<double>(s, rng, p->max_bounces, c.eye, d, c0, c1, stream, nullptr, rgb, seg);
+    return seg;
+  }
+  Vars vars;
+  Dual L[3];
+  trace_path<Dual>(s, rng, p->max_bounces, c.eye, d, c0, c1, stream, &vars, L, seg);
+  for (int k = 0; k < 3; ++k) rgb[k] = L[k].v;
+  Dual loss = L[0] * grad_w[0] + L[1] * grad_w[1] + L[2] * grad_w[2];
+  scatter_grad(vars, loss, d_verts, d_face);
+  return seg;
+}
+
+long long orc_trace_screen_taped(const orc_scene* in, const orc_view* view, const orc_params* p, double px,
+                                 double py, uint32_t c0, uint32_t c1, uint32_t stream, int mode, double* tape,
+                                 int* tape_len, double* rgb) {
+  Scene s;
+  if (!load_scene(in, s) || !check_common(view, 1, p) || !tape_len) return -1;
+  Rng rng = rng_of(p);
+  Cam c = make_cam(*view);
+  Tape tp;
+  tp.mode = mode;
+  if (mode == 2) tp.v.assign(tape, tape + *tape_len);
+  long long seg = 0;
+  trace_path<double>(s, rng, p->max_bounces, c.eye, cam_dir(c, px, py), c0, c1, stream, nullptr, rgb, seg, &tp);
+  if (tp.bad || (mode == 2 && tp.pos != tp.v.size())) return -2;
+  if (mode == 1) {
+    if ((int)tp.v.size() > *tape_len) return -3;
+    std::copy(tp.v.begin(), tp.v.end(), tape);
+    *tape_len = (int)tp.v.size();
+  }
+  return seg;
+}
+
+void orc_microfacet(int brdf, double alpha, double c, double* D, double* G1) {
+  *D = D_fn(brdf, c, clamp_alpha(alpha));
+  *G1 = G1_fn(brdf, c, clamp_alpha(alpha));
+}
+
+}  // extern "C"
