@@ -1,0 +1,185 @@
+/*
+ * st.h -- C ABI of the GB300 differentiable path tracer (libst.so).
+ *
+ * The library renders a triangle mesh with per-face Torrance-Sparrow
+ * reflectance under point lights and/or an HDR environment map by Monte Carlo
+ * path tracing, and computes the gradient of an image loss with respect to the
+ * vertex positions and the per-face material parameters. This is the
+ * differentiable renderer R(x, m, c) the paper optimises through (Sec. 3.2,
+ * "Vertex optimization": the MSE loss over views c_i and its gradient with
+ * respect to vertex positions x; Sec. 3.3, "Material Optimization": the same
+ * loss with respect to the material m; material "Representation": a
+ * Torrance-Sparrow BRDF with diffuse albedo, specular and roughness per mesh
+ * facet, i.e. mesh colors at resolution r = 0; Sec. 3.1 "Input": point lights
+ * or an HDR environment map; Sec. 3.3 "Effects of Global Illumination":
+ * multi-bounce transport, max_bounces = 1 being "local + shadows").
+ *
+ * Conventions shared by every call:
+ *  - Every call returns an st_status; nothing aborts. On a non-OK status,
+ *    st_last_error() gives a message (thread-local, valid until the next call
+ *    on the same thread).
+ *  - Device pointers are CUDA device memory of the device that is current when
+ *    the scene was created; they are owned by the caller unless stated.
+ *    Host pointers are read before the call returns.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream). Calls enqueue
+ *    work and return without synchronising unless stated; outputs are valid
+ *    when the stream reaches that point.
+ *  - A scene is not thread-safe; distinct scenes are independent. Calls on one
+ *    scene must be issued on one stream, or ordered by the caller.
+ *  - Images are packed: view v occupies rows [pixel_offset, pixel_offset+W*H)
+ *    of a float [N][3] array, row-major within the view, row 0 at the top.
+ *  - Randomness is a pure function of (seed, view pixel_offset, pixel,
+ *    sample): identical arguments give a bitwise identical image whatever
+ *    the batching mode; st_render_backward with the same seed replays the
+ *    forward paths (no path storage between the two calls).
+ */
+#ifndef ST_H
+#define ST_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ST_OK = 0,
+  ST_ERR_INVALID_ARG = 1,  /* a size, pointer or index is out of range */
+  ST_ERR_OOM = 2,          /* device or host allocation failed */
+  ST_ERR_CUDA = 3,         /* a CUDA runtime call failed (message has the CUDA error) */
+  ST_ERR_TIMEOUT = 4,      /* reserved: no call in this library waits on a device flag */
+  ST_ERR_STATE = 5,        /* call not valid for the scene's current state */
+  ST_ERR_UNSUPPORTED = 6,  /* feature outside the library's limits (see ST_MAX_*) */
+  ST_ERR_DEVICE = 7        /* a kernel latched an error (e.g. BVH stack overflow) */
+} st_status;
+
+#define ST_MAX_LIGHTS 8
+#define ST_MAX_BOUNCES 8
+#define ST_BRDF_GGX 0
+#define ST_BRDF_BECKMANN 1
+#define ST_EDGE_SILHOUETTE 0  /* edges whose two faces face opposite ways, and boundary edges */
+#define ST_EDGE_ALL 1         /* every mesh edge (also the shading discontinuities of flat faces) */
+#define ST_MODE_BATCHED 0     /* all views in one job space, persistent kernels, optional CUDA graph */
+#define ST_MODE_PER_VIEW 1    /* one view at a time, grids sized from host-read queue counts */
+
+typedef struct st_scene st_scene; /* opaque, library-owned */
+
+/* Point light (Sec. 3.1): position and radiant intensity (W/sr), RGB. */
+typedef struct {
+  float pos[3];
+  float intensity[3];
+} st_point_light;
+
+/* Equirectangular HDR environment (Sec. 3.1): HOST pointer to float [H][W][3]
+ * radiance. Row 0 is theta = 0 (the +y pole); direction for (theta, phi) is
+ * (-sin theta sin phi, cos theta, sin theta cos phi), phi = 2 pi (col + 0.5)/W
+ * at texel centres. Copied, and its FP64 alias table built, at scene create. */
+typedef struct {
+  int width, height;
+  const float* rgb;
+} st_envmap;
+
+/* Pinhole view c_i (Sec. 3.2): fov_y in degrees, +y up on screen. spp == 0
+ * takes the call's default_spp. pixel_offset = first packed-image row of the
+ * view; it also keys the view's random numbers. */
+typedef struct {
+  float eye[3], target[3], up[3];
+  float fov_y_deg;
+  int width, height, spp;
+  long long pixel_offset;
+} st_view;
+
+typedef struct {
+  int n_vertices, n_faces;
+  const float* vertices;     /* device, float [V][3] */
+  const int* faces;          /* device, int [F][3] vertex indices */
+  const float* face_params;  /* device, float [F][5]: kd_r, kd_g, kd_b, ks, roughness */
+  int brdf;                  /* ST_BRDF_GGX or ST_BRDF_BECKMANN */
+  int n_point_lights;        /* 0..ST_MAX_LIGHTS */
+  const st_point_light* point_lights; /* host array */
+  const st_envmap* env;      /* NULL if no environment */
+} st_scene_desc;
+
+typedef struct {
+  int edge_term;    /* backward: add the primary-visibility edge term (1) or not (0) */
+  int edge_mode;    /* ST_EDGE_SILHOUETTE or ST_EDGE_ALL */
+  int edge_spp;     /* edge samples per pixel; 0 = the view's spp */
+  int mode;         /* ST_MODE_BATCHED or ST_MODE_PER_VIEW */
+  int use_graph;    /* batched mode: capture and replay the call as a CUDA graph */
+  int chunk_paths;  /* paths in flight per wavefront chunk; 0 = library default */
+  int time_kernels; /* per-view or ungraphed batched: time the closest-hit kernel (see st_stats) */
+  int count_visits; /* run the instrumented traversal that counts node visits and triangle tests */
+} st_render_opts;
+
+typedef struct {
+  long long paths;            /* camera + edge-side paths started by the last call */
+  long long extension_rays;   /* closest-hit queries of the last call */
+  long long shadow_rays;      /* any-hit queries of the last call */
+  long long edge_samples;     /* edge samples of the last call (each traces two paths) */
+  long long node_visits;      /* instrumented calls only: internal nodes fetched by closest-hit */
+  long long tri_tests;        /* instrumented calls only: triangle tests by closest-hit */
+  int extend_launches;        /* closest-hit launches timed (time_kernels) */
+  double extend_ms;           /* their summed CUDA-event time */
+  int device_error;           /* latched device error bits (0 = none) */
+  int bvh_nodes;              /* internal nodes of the current BVH */
+  long long scratch_bytes;    /* device bytes held by the scene's wavefront buffers */
+} st_stats;
+
+/* Create a scene: copies the mesh into scene-owned device memory, builds the
+ * LBVH (Morton codes, radix sort, Karras hierarchy, bottom-up boxes), the edge
+ * list and the environment alias table. Synchronises `stream` once. */
+st_status st_scene_create(const st_scene_desc* desc, void* stream, st_scene** out);
+
+/* Free everything the scene owns. NULL is accepted. */
+st_status st_scene_destroy(st_scene* scene);
+
+/* New vertex positions (device float [V][3], same topology): recompute
+ * triangle records and boxes bottom-up on the existing hierarchy. The vertex
+ * update of every optimisation step (Sec. 3.2). */
+st_status st_refit(st_scene* scene, const float* new_vertices, void* stream);
+
+/* New vertex positions with a full rebuild (Morton order recomputed). */
+st_status st_rebuild(st_scene* scene, const float* new_vertices, void* stream);
+
+/* New per-face parameters (device float [F][5]); the material update (Sec. 3.3). */
+st_status st_set_face_params(st_scene* scene, const float* face_params, void* stream);
+
+/* Forward render of n_views views (host array) with max_bounces surface
+ * vertices per path (1..ST_MAX_BOUNCES). out_image: device float [N][3], N =
+ * max over views of pixel_offset + W*H; it is overwritten on every pixel of
+ * the views (other rows untouched). opts may be NULL (batched, graph on). */
+st_status st_render(st_scene* scene, const st_view* views, int n_views, int default_spp,
+                    int max_bounces, unsigned long long seed, const st_render_opts* opts,
+                    float* out_image, void* stream);
+
+/* Adjoint: given dL/dI (device float [N][3], same layout as out_image),
+ * ACCUMULATE (+=) dL/dvertices into d_vertices (device float [V][3]) and
+ * dL/dface_params into d_face_params (device float [F][5]). The interior term
+ * replays the forward paths of the same seed and sweeps each in reverse; the
+ * edge term (opts->edge_term) samples visibility edges. Either gradient
+ * pointer may be NULL to skip it (d_vertices may not be NULL with edge_term). */
+st_status st_render_backward(st_scene* scene, const st_view* views, int n_views, int default_spp,
+                             int max_bounces, unsigned long long seed, const st_render_opts* opts,
+                             const float* dL_dimage, float* d_vertices, float* d_face_params,
+                             void* stream);
+
+/* Closest-hit query through the BVH for n rays: rays device float [n][8] =
+ * (ox, oy, oz, unused, dx, dy, dz, tmax), d of unit length; out_tri device
+ * int [n] (face id, -1 = miss), out_t device float [n] (+inf on a miss). Hits
+ * at t <= 1e-5 are not reported (the path tracer's self-intersection bound);
+ * exclude_face is skipped (-1 = none); equal t resolves to the lower face id. */
+st_status st_trace_closest(st_scene* scene, const float* rays, int n, int exclude_face, int* out_tri,
+                           float* out_t, void* stream);
+
+/* Statistics of the last render/backward call; synchronises the scene's work. */
+st_status st_get_stats(st_scene* scene, st_stats* out);
+
+/* Copy the BVH for inspection (host arrays, sizes from st_get_stats):
+ * nodes float [F-1][16] as stored on the device, leaf_faces int [F]. */
+st_status st_debug_bvh(st_scene* scene, float* nodes, int* leaf_faces);
+
+/* Message for the last non-OK status on this thread. */
+const char* st_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,726 @@
+// C ABI of libst: scene lifetime, host-side preprocessing (edge list, FP64
+// alias table), per-call planning of the job space, the wavefront chunk loop in
+// its two launch modes (batched persistent + CUDA graph, or plain per-view),
+// and statistics.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "st_kernels.cuh"
+
+namespace st {
+
+static thread_local std::string g_err;
+void set_error(const std::string& msg) { g_err = msg; }
+
+namespace {
+
+constexpr int DEFAULT_CHUNK = 1 << 22;
+constexpr long long SEG_ALIGN = 32;
+
+st_status fail(st_status s, const std::string& msg) {
+  set_error(msg);
+  return s;
+}
+
+st_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(ST_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define ST_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+template <class T>
+cudaError_t dalloc(T** p, size_t n, long long* acc = nullptr) {
+  *p = nullptr;
+  if (n == 0) return cudaSuccess;
+  if (acc) *acc += (long long)(n * sizeof(T));
+  return cudaMalloc((void**)p, n * sizeof(T));
+}
+
+template <class T>
+void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+// Vose's alias method over texel weights lum * sin(theta at the row centre),
+// built in double precision: small and large worklists are stacks seeded in
+// index order; a small bin takes the top large bin as alias, which keeps
+// (q_l + q_s) - 1 and moves to the small list once below one.
+bool build_alias(const float* rgb, int w, int h, std::vector<float4>& tex, std::vector<float2>& tab) {
+  const int N = w * h;
+  std::vector<double> wt(N), q(N), prob(N, 1.0);
+  std::vector<int> alias(N);
+  double total = 0;
+  const double PI = 3.14159265358979323846;
+  for (int r = 0; r < h; ++r) {
+    double s = std::sin(PI * (r + 0.5) / h);
+    for (int c = 0; c < w; ++c) {
+      const float* t = rgb + 3 * ((size_t)r * w + c);
+      double l = 0.2126 * (double)t[0] + 0.7152 * (double)t[1] + 0.0722 * (double)t[2];
+      wt[(size_t)r * w + c] = l * s;
+    }
+  }
+  for (int i = 0; i < N; ++i) {
+    if (!(wt[i] >= 0.0) || !std::isfinite(wt[i])) return false;
+    total += wt[i];
+  }
+  if (!(total > 0.0)) return false;
+  std::vector<int> small, large;
+  for (int i = 0; i < N; ++i) {
+    q[i] = (wt[i] * N) / total;
+    alias[i] = i;
+    (q[i] < 1.0 ? small : large).push_back(i);
+  }
+  while (!small.empty() && !large.empty()) {
+    int a = small.back();
+    small.pop_back();
+    int b = large.back();
+    prob[a] = q[a];
+    alias[a] = b;
+    q[b] = (q[b] + q[a]) - 1.0;
+    if (q[b] < 1.0) {
+      large.pop_back();
+      small.push_back(b);
+    }
+  }
+  for (int i : large) { prob[i] = 1.0; alias[i] = i; }
+  for (int i : small) { prob[i] = 1.0; alias[i] = i; }
+  tex.resize(N);
+  tab.resize(N);
+  for (int i = 0; i < N; ++i) {
+    const float* t = rgb + 3 * (size_t)i;
+    tex[i] = make_float4(t[0], t[1], t[2], (float)(wt[i] / total));
+    float abits;
+    std::memcpy(&abits, &alias[i], sizeof(float));
+    tab[i] = make_float2((float)prob[i], abits);
+  }
+  return true;
+}
+
+// Undirected edges sorted by (min vertex, max vertex) with up to two faces.
+void build_edges(const std::vector<int>& F, int nf, std::vector<int2>& ev, std::vector<int2>& ef) {
+  std::vector<std::pair<unsigned long long, int>> e;
+  e.reserve(3 * (size_t)nf);
+  for (int f = 0; f < nf; ++f)
+    for (int k = 0; k < 3; ++k) {
+      unsigned a = (unsigned)F[3 * f + k], b = (unsigned)F[3 * f + (k + 1) % 3];
+      unsigned lo = std::min(a, b), hi = std::max(a, b);
+      e.push_back({((unsigned long long)lo << 32) | hi, f});
+    }
+  std::sort(e.begin(), e.end());
+  ev.clear();
+  ef.clear();
+  for (size_t i = 0; i < e.size();) {
+    size_t j = i;
+    while (j < e.size() && e[j].first == e[i].first) ++j;
+    ev.push_back(make_int2((int)(e[i].first >> 32), (int)(e[i].first & 0xffffffffu)));
+    int second = j - i == 1 ? -1 : (j - i == 2 ? e[i + 1].second : -2);
+    ef.push_back(make_int2(e[i].second, second));
+    i = j;
+  }
+}
+
+DevView make_view(const st_view& v, int spp) {
+  double eye[3] = {v.eye[0], v.eye[1], v.eye[2]};
+  double f[3] = {v.target[0] - eye[0], v.target[1] - eye[1], v.target[2] - eye[2]};
+  double fl = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+  for (double& x : f) x /= fl;
+  double up[3] = {v.up[0], v.up[1], v.up[2]};
+  double r[3] = {f[1] * up[2] - f[2] * up[1], f[2] * up[0] - f[0] * up[2], f[0] * up[1] - f[1] * up[0]};
+  double rl = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+  for (double& x : r) x /= rl;
+  double u[3] = {r[1] * f[2] - r[2] * f[1], r[2] * f[0] - r[0] * f[2], r[0] * f[1] - r[1] * f[0]};
+  double th = std::tan((double)v.fov_y_deg * 3.14159265358979323846 / 360.0);
+  DevView d;
+  d.eye = mk3(v.eye[0], v.eye[1], v.eye[2]);
+  d.fwd = mk3((float)f[0], (float)f[1], (float)f[2]);
+  d.right = mk3((float)r[0], (float)r[1], (float)r[2]);
+  d.up = mk3((float)u[0], (float)u[1], (float)u[2]);
+  d.kx = (float)(th * v.width / v.height);
+  d.ky = (float)th;
+  d.W = v.width;
+  d.H = v.height;
+  d.spp = spp;
+  d.off = (uint32_t)v.pixel_offset;
+  d.pix_off = v.pixel_offset;
+  return d;
+}
+
+bool view_ok(const st_view& v) {
+  auto fin = [](const float* a, int n) {
+    for (int i = 0; i < n; ++i)
+      if (!std::isfinite(a[i])) return false;
+    return true;
+  };
+  if (v.width <= 0 || v.height <= 0 || v.pixel_offset < 0 || v.spp < 0) return false;
+  if (!fin(v.eye, 3) || !fin(v.target, 3) || !fin(v.up, 3) || !(v.fov_y_deg > 0 && v.fov_y_deg < 180)) return false;
+  double f[3] = {v.target[0] - v.eye[0], v.target[1] - v.eye[1], v.target[2] - v.eye[2]};
+  double c[3] = {f[1] * v.up[2] - f[2] * v.up[1], f[2] * v.up[0] - f[0] * v.up[2], f[0] * v.up[1] - f[1] * v.up[0]};
+  return c[0] * c[0] + c[1] * c[1] + c[2] * c[2] > 0;
+}
+
+// ------------------------------------------------------------------ per-call plan
+struct Plan {
+  int kind = 0;  // 0 forward, 1 backward
+  int B = 1;
+  std::vector<DevView> views;
+  std::vector<Seg> segs;
+  std::vector<std::pair<long long, long long>> view_range;  // job range per view (per-view mode)
+  long long total = 0;
+  bool interior = false, edges = false;
+  st_render_opts o{};
+};
+
+st_render_opts default_opts() {
+  st_render_opts o;
+  std::memset(&o, 0, sizeof(o));
+  o.use_graph = 1;
+  o.edge_mode = ST_EDGE_SILHOUETTE;
+  return o;
+}
+
+void free_engine(Engine& e) {
+  dfree(e.o); dfree(e.d); dfree(e.thr); dfree(e.rad); dfree(e.ctr); dfree(e.hit); dfree(e.origin);
+  dfree(e.q0); dfree(e.q1); dfree(e.qs); dfree(e.sh_dir); dfree(e.sh_c);
+  dfree(e.r0); dfree(e.r1); dfree(e.r2); dfree(e.r3); dfree(e.esc); dfree(e.nb); dfree(e.cnt); dfree(e.stat);
+  e = Engine();
+}
+
+void drop_graphs(st_scene* s) {
+  for (auto& g : s->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  s->graphs.clear();
+}
+
+st_status ensure_engine(st_scene* s, int Q, int B, int NS, bool records) {
+  Engine& e = s->eng;
+  if (e.Q >= Q && e.NS >= NS && (!records || (e.records && e.B >= B))) return ST_OK;
+  // grow: keep the larger of old and new sizes so alternating calls do not thrash
+  int nQ = std::max(Q, e.Q), nNS = std::max(NS, e.NS), nB = std::max(B, e.B);
+  bool nrec = records || e.records;
+  cudaDeviceSynchronize();
+  drop_graphs(s);
+  free_engine(e);
+  long long acc = 0;
+  size_t q = (size_t)nQ;
+  cudaError_t r = cudaSuccess;
+  auto chk = [&](cudaError_t x) { if (x != cudaSuccess && r == cudaSuccess) r = x; };
+  chk(dalloc(&e.o, q, &acc)); chk(dalloc(&e.d, q, &acc)); chk(dalloc(&e.thr, q, &acc)); chk(dalloc(&e.rad, q, &acc));
+  chk(dalloc(&e.ctr, q, &acc)); chk(dalloc(&e.hit, q, &acc)); chk(dalloc(&e.origin, q, &acc));
+  chk(dalloc(&e.q0, q, &acc)); chk(dalloc(&e.q1, q, &acc)); chk(dalloc(&e.qs, q, &acc));
+  chk(dalloc(&e.sh_dir, q * std::max(nNS, 1), &acc)); chk(dalloc(&e.sh_c, q * std::max(nNS, 1), &acc));
+  if (nrec) {
+    chk(dalloc(&e.r0, q * nB, &acc)); chk(dalloc(&e.r1, q * (nB + 1), &acc)); chk(dalloc(&e.r2, q * nB, &acc));
+    chk(dalloc(&e.r3, q * nB, &acc)); chk(dalloc(&e.esc, q, &acc)); chk(dalloc(&e.nb, q, &acc));
+  }
+  chk(dalloc(&e.cnt, CNT_SIZE, &acc));
+  chk(dalloc(&e.stat, STAT_SIZE, &acc));
+  if (r != cudaSuccess) {
+    free_engine(e);
+    cudaGetLastError();
+    return fail(ST_ERR_OOM, std::string("wavefront buffers: ") + cudaGetErrorString(r));
+  }
+  e.Q = nQ; e.B = nB; e.NS = nNS; e.records = nrec; e.bytes = acc;
+  return ST_OK;
+}
+
+st_status ensure_tables(st_scene* s, int n_views, int n_segs, bool edges) {
+  int need = std::max(n_views, n_segs);
+  if (need > s->view_cap) {
+    cudaDeviceSynchronize();
+    drop_graphs(s);
+    dfree(s->d_views);
+    dfree(s->d_segs);
+    if (dalloc(&s->d_views, need) != cudaSuccess || dalloc(&s->d_segs, need) != cudaSuccess)
+      return fail(ST_ERR_OOM, "view tables");
+    s->view_cap = need;
+  }
+  if (edges && n_views > s->edge_cap_views) {
+    cudaDeviceSynchronize();
+    drop_graphs(s);
+    dfree(s->edge_flag);
+    dfree(s->edge_cand);
+    dfree(s->edge_ncand);
+    size_t n = (size_t)n_views * std::max(s->n_edges, 1);
+    if (dalloc(&s->edge_flag, n) != cudaSuccess || dalloc(&s->edge_cand, n) != cudaSuccess ||
+        dalloc(&s->edge_ncand, (size_t)n_views) != cudaSuccess)
+      return fail(ST_ERR_OOM, "edge tables");
+    s->edge_cap_views = n_views;
+  }
+  return ST_OK;
+}
+
+KCtx make_ctx(st_scene* s, const Plan& p) {
+  KCtx c;
+  c.V = s->verts; c.F = s->faces; c.P = s->params; c.nodes = s->nodes; c.tri = s->tri; c.nf = s->nf;
+  c.lights = s->lights; c.nl = s->nl; c.NS = s->nl + (s->env.w > 0 ? 1 : 0);
+  c.env = s->env; c.brdf = s->brdf;
+  c.edge_v = s->edge_v; c.edge_f = s->edge_f; c.n_edges = s->n_edges; c.edge_mode = p.o.edge_mode;
+  c.edge_flag = s->edge_flag; c.edge_cand = s->edge_cand; c.edge_ncand = s->edge_ncand;
+  c.views = s->d_views; c.segs = s->d_segs; c.n_segs = (int)p.segs.size();
+  c.args = s->d_args; c.B = p.B; c.e = s->eng; c.e.records = p.kind == 1; c.err = s->d_err;
+  return c;
+}
+
+int grid_of(const void* fn, int block, int sm) {
+  int per = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, block, 0);
+  return std::max(1, per) * std::max(1, sm);
+}
+
+cudaEvent_t next_event(st_scene* s, bool start) {
+  if (s->ev_used >= (int)s->ev.size()) {
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    s->ev.push_back({a, b});
+  }
+  auto& pr = s->ev[s->ev_used];
+  if (!start) s->ev_used++;
+  return start ? pr.first : pr.second;
+}
+
+// Enqueue one chunk [j0, j0 + n) of the job space. host_sized: read the queue
+// counts after each stage and size each grid to them (plain per-view path).
+st_status run_chunk(st_scene* s, const Plan& p, const KCtx& c, long long j0, int n, cudaStream_t st, bool host_sized,
+                    bool timing, bool has_cam, bool has_edge) {
+  int sm = s->sm_count;
+  static int g_ext = 0, g_ext_s = 0, g_shade = 0, g_shadow = 0;
+  if (!g_ext) {
+    g_ext = grid_of((const void*)k_extend<false>, EXT_BLOCK, sm);
+    g_ext_s = grid_of((const void*)k_extend<true>, EXT_BLOCK, sm);
+    g_shade = grid_of((const void*)k_shade, 256, sm);
+    g_shadow = grid_of((const void*)k_shadow, EXT_BLOCK, sm);
+  }
+  int* cnt = s->eng.cnt;
+  int hc[CNT_SIZE];
+  k_reset<<<1, 128, 0, st>>>(cnt);
+  k_raygen<<<(n + 255) / 256, 256, 0, st>>>(c, j0, n);
+  for (int b = 0; b < p.B; ++b) {
+    int ge = p.o.count_visits ? g_ext_s : g_ext, gs = g_shade, gw = g_shadow;
+    if (host_sized) {
+      ST_CUDA(cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, st));
+      ST_CUDA(cudaStreamSynchronize(st));
+      int q = hc[CNT_EXT + b];
+      if (q == 0) break;
+      ge = (q + EXT_BLOCK - 1) / EXT_BLOCK;
+      gs = (q + 255) / 256;
+    }
+    if (timing) ST_CUDA(cudaEventRecord(next_event(s, true), st));
+    if (p.o.count_visits) k_extend<true><<<ge, EXT_BLOCK, 0, st>>>(c, b);
+    else k_extend<false><<<ge, EXT_BLOCK, 0, st>>>(c, b);
+    if (timing) ST_CUDA(cudaEventRecord(next_event(s, false), st));
+    k_shade<<<gs, 256, 0, st>>>(c, b);
+    if (host_sized) {
+      ST_CUDA(cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, st));
+      ST_CUDA(cudaStreamSynchronize(st));
+      int q = hc[CNT_SH + b];
+      gw = (q + EXT_BLOCK - 1) / EXT_BLOCK;
+      if (q > 0) k_shadow<<<gw, EXT_BLOCK, 0, st>>>(c, b);
+    } else if (c.NS > 0) {
+      k_shadow<<<gw, EXT_BLOCK, 0, st>>>(c, b);
+    }
+  }
+  if (p.kind == 0) {
+    k_resolve<<<(n + 255) / 256, 256, 0, st>>>(c, j0, n);
+  } else {
+    if (has_cam && p.interior) k_adjoint<<<(n + ADJ_BLOCK - 1) / ADJ_BLOCK, ADJ_BLOCK, 0, st>>>(c, j0, n);
+    if (has_edge) k_edge_resolve<<<(n + ADJ_BLOCK - 1) / ADJ_BLOCK, ADJ_BLOCK, 0, st>>>(c, j0, n);
+  }
+  ST_CUDA(cudaGetLastError());
+  return ST_OK;
+}
+
+// Does any segment of kind k overlap [a, b)?
+bool overlaps(const Plan& p, int kind, long long a, long long b) {
+  for (auto& sg : p.segs)
+    if (sg.kind == kind && sg.base < b && sg.base + sg.count > a) return true;
+  return false;
+}
+
+st_status enqueue_call(st_scene* s, const Plan& p, int Q, cudaStream_t st, bool host_sized, bool timing) {
+  KCtx c = make_ctx(s, p);
+  ST_CUDA(cudaMemsetAsync(s->eng.stat, 0, sizeof(unsigned long long) * STAT_SIZE, st));
+  if (p.kind == 0) {
+    // zero each view's rows, merging adjacent ranges
+    std::vector<std::pair<long long, long long>> rg;
+    for (auto& v : p.views) rg.push_back({v.pix_off, v.pix_off + (long long)v.W * v.H});
+    std::sort(rg.begin(), rg.end());
+    std::vector<std::pair<long long, long long>> m;
+    for (auto& r : rg) {
+      if (!m.empty() && r.first <= m.back().second) m.back().second = std::max(m.back().second, r.second);
+      else m.push_back(r);
+    }
+    for (auto& r : m)
+      ST_CUDA(cudaMemsetAsync(s->image_ptr + 3 * r.first, 0, sizeof(float) * 3 * (r.second - r.first), st));
+  }
+  if (p.edges) {
+    dim3 g((s->n_edges + 255) / 256, (unsigned)p.views.size());
+    k_edge_flags<<<g, 256, 0, st>>>(c, (int)p.views.size());
+    k_edge_compact<<<(unsigned)p.views.size(), 1024, 0, st>>>(c);
+  }
+  auto chunks = [&](long long a, long long b) -> st_status {
+    for (long long j0 = a; j0 < b; j0 += Q) {
+      int n = (int)std::min<long long>(Q, b - j0);
+      st_status r = run_chunk(s, p, c, j0, n, st, host_sized, timing, overlaps(p, 0, j0, j0 + n),
+                              overlaps(p, 1, j0, j0 + n));
+      if (r != ST_OK) return r;
+    }
+    return ST_OK;
+  };
+  if (p.o.mode == ST_MODE_PER_VIEW) {
+    for (auto& r : p.view_range) {
+      st_status x = chunks(r.first, r.second);
+      if (x != ST_OK) return x;
+    }
+  } else {
+    st_status x = chunks(0, p.total);
+    if (x != ST_OK) return x;
+  }
+  return ST_OK;
+}
+
+std::vector<long long> graph_key(const Plan& p, int Q, const st_scene* s) {
+  std::vector<long long> k = {p.kind, p.B, (long long)p.views.size(), Q, p.o.edge_term, p.o.edge_mode, p.o.edge_spp,
+                              p.interior, p.edges, (long long)(size_t)s->image_ptr, p.o.count_visits};
+  for (auto& v : p.views) { k.push_back(v.W); k.push_back(v.H); k.push_back(v.spp); k.push_back(v.pix_off); }
+  return k;
+}
+
+st_status plan_call(st_scene* s, const st_view* views, int n_views, int default_spp, int B, const st_render_opts* opts,
+                    int kind, bool want_interior, Plan& p) {
+  if (!views || n_views <= 0) return fail(ST_ERR_INVALID_ARG, "no views");
+  if (B < 1 || B > ST_MAX_BOUNCES) return fail(ST_ERR_UNSUPPORTED, "max_bounces must be in [1, 8]");
+  p.kind = kind;
+  p.B = B;
+  p.o = opts ? *opts : default_opts();
+  if (p.o.mode != ST_MODE_BATCHED && p.o.mode != ST_MODE_PER_VIEW) return fail(ST_ERR_INVALID_ARG, "bad mode");
+  if (p.o.edge_mode != ST_EDGE_SILHOUETTE && p.o.edge_mode != ST_EDGE_ALL) return fail(ST_ERR_INVALID_ARG, "bad edge_mode");
+  if (p.o.edge_spp < 0 || p.o.chunk_paths < 0) return fail(ST_ERR_INVALID_ARG, "negative option");
+  p.interior = kind == 1 && want_interior;
+  p.edges = kind == 1 && p.o.edge_term != 0;
+  long long base = 0;
+  for (int i = 0; i < n_views; ++i) {
+    const st_view& v = views[i];
+    if (!view_ok(v)) return fail(ST_ERR_INVALID_ARG, "view " + std::to_string(i) + " is invalid");
+    int spp = v.spp > 0 ? v.spp : default_spp;
+    if (spp <= 0) return fail(ST_ERR_INVALID_ARG, "view " + std::to_string(i) + " has no samples");
+    if ((long long)v.width * v.height > (1LL << 31) || v.pixel_offset + (long long)v.width * v.height > (1LL << 32))
+      return fail(ST_ERR_UNSUPPORTED, "view too large for 32-bit pixel counters");
+    p.views.push_back(make_view(v, spp));
+    long long start = base;
+    long long cam = (long long)v.width * v.height * spp;
+    if (kind == 0 || p.interior) {
+      Seg sg{base, cam, i, 0, cam};
+      p.segs.push_back(sg);
+      base += (cam + SEG_ALIGN - 1) / SEG_ALIGN * SEG_ALIGN;
+    }
+    if (p.edges) {
+      long long ne = (long long)v.width * v.height * (p.o.edge_spp > 0 ? p.o.edge_spp : spp);
+      Seg sg{base, 2 * ne, i, 1, ne};
+      p.segs.push_back(sg);
+      base += (2 * ne + SEG_ALIGN - 1) / SEG_ALIGN * SEG_ALIGN;
+    }
+    p.view_range.push_back({start, base});
+  }
+  p.total = base;
+  s->last_edge_samples = 0;
+  for (auto& sg : p.segs)
+    if (sg.kind == 1) s->last_edge_samples += sg.n_samples;
+  return ST_OK;
+}
+
+st_status run_call(st_scene* s, Plan& p, const CallArgs& args, cudaStream_t st) {
+  st_status r = ensure_tables(s, (int)p.views.size(), (int)p.segs.size(), p.edges);
+  if (r != ST_OK) return r;
+  long long Q64 = p.o.chunk_paths > 0 ? p.o.chunk_paths : DEFAULT_CHUNK;
+  Q64 = std::min<long long>(Q64, std::max<long long>(p.total, SEG_ALIGN));
+  Q64 = (Q64 + SEG_ALIGN - 1) / SEG_ALIGN * SEG_ALIGN;
+  int Q = (int)Q64;
+  if (p.o.mode == ST_MODE_PER_VIEW) {
+    long long mx = SEG_ALIGN;
+    for (auto& vr : p.view_range) mx = std::max(mx, vr.second - vr.first);
+    Q = (int)std::min<long long>(Q, (mx + SEG_ALIGN - 1) / SEG_ALIGN * SEG_ALIGN);
+  }
+  int NS = s->nl + (s->env.w > 0 ? 1 : 0);
+  r = ensure_engine(s, Q, p.B, NS, p.kind == 1);
+  if (r != ST_OK) return r;
+  ST_CUDA(cudaMemcpyAsync(s->d_views, p.views.data(), sizeof(DevView) * p.views.size(), cudaMemcpyHostToDevice, st));
+  ST_CUDA(cudaMemcpyAsync(s->d_segs, p.segs.data(), sizeof(Seg) * p.segs.size(), cudaMemcpyHostToDevice, st));
+  ST_CUDA(cudaMemcpyAsync(s->d_args, &args, sizeof(CallArgs), cudaMemcpyHostToDevice, st));
+  bool timing = p.o.time_kernels != 0;
+  s->ev_used = 0;
+  bool graph = p.o.mode == ST_MODE_BATCHED && p.o.use_graph && !timing;
+  if (!graph) return enqueue_call(s, p, Q, st, p.o.mode == ST_MODE_PER_VIEW, timing);
+  std::vector<long long> key = graph_key(p, Q, s);
+  for (auto& g : s->graphs)
+    if (g.key == key) {
+      ST_CUDA(cudaGraphLaunch(g.exec, st));
+      return ST_OK;
+    }
+  // capture on the scene's own stream, ordered after the uploads above
+  cudaEvent_t ready;
+  ST_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+  ST_CUDA(cudaEventRecord(ready, st));
+  ST_CUDA(cudaStreamWaitEvent(s->cap_stream, ready, 0));
+  ST_CUDA(cudaStreamSynchronize(s->cap_stream));
+  cudaEventDestroy(ready);
+  ST_CUDA(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+  st_status er = enqueue_call(s, p, Q, s->cap_stream, false, false);
+  cudaGraph_t graph_obj = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(s->cap_stream, &graph_obj);
+  if (er != ST_OK) {
+    if (graph_obj) cudaGraphDestroy(graph_obj);
+    return er;
+  }
+  if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+  GraphEntry ge;
+  ge.key = key;
+  ce = cudaGraphInstantiate(&ge.exec, graph_obj, 0);
+  cudaGraphDestroy(graph_obj);
+  if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate");
+  if (s->graphs.size() >= 16) {
+    cudaGraphExecDestroy(s->graphs.front().exec);
+    s->graphs.erase(s->graphs.begin());
+  }
+  s->graphs.push_back(ge);
+  ST_CUDA(cudaGraphLaunch(ge.exec, st));
+  return ST_OK;
+}
+
+void destroy(st_scene* s) {
+  if (!s) return;
+  cudaSetDevice(s->device);
+  cudaDeviceSynchronize();
+  drop_graphs(s);
+  free_engine(s->eng);
+  dfree(s->verts); dfree(s->faces); dfree(s->params); dfree(s->tri); dfree(s->nodes); dfree(s->parent);
+  dfree(s->flags); dfree(s->keys); dfree(s->keys2); dfree(s->ids); dfree(s->ids2); dfree(s->hist); dfree(s->bounds);
+  dfree(s->lights); dfree(s->env_tex); dfree(s->env_alias); dfree(s->edge_v); dfree(s->edge_f);
+  dfree(s->edge_flag); dfree(s->edge_cand); dfree(s->edge_ncand); dfree(s->d_views); dfree(s->d_segs);
+  dfree(s->d_args); dfree(s->d_err);
+  for (auto& e : s->ev) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+  if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+  delete s;
+}
+
+__global__ void k_params_in(const float* in, float4* out, int nf) {
+  int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= nf) return;
+  const float* p = in + 5 * f;
+  out[2 * f] = make_float4(p[0], p[1], p[2], p[3]);
+  out[2 * f + 1] = make_float4(p[4], 0.0f, 0.0f, 0.0f);
+}
+
+}  // namespace
+}  // namespace st
+
+using namespace st;
+
+extern "C" {
+
+const char* st_last_error(void) { return g_err.c_str(); }
+
+st_status st_scene_create(const st_scene_desc* d, void* stream, st_scene** out) {
+  if (!out) return fail(ST_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!d || d->n_vertices <= 0 || d->n_faces <= 0 || !d->vertices || !d->faces || !d->face_params)
+    return fail(ST_ERR_INVALID_ARG, "mesh description incomplete");
+  if (d->n_faces > (1 << 28)) return fail(ST_ERR_UNSUPPORTED, "too many faces");
+  if (d->brdf != ST_BRDF_GGX && d->brdf != ST_BRDF_BECKMANN) return fail(ST_ERR_INVALID_ARG, "unknown brdf");
+  if (d->n_point_lights < 0 || d->n_point_lights > ST_MAX_LIGHTS || (d->n_point_lights > 0 && !d->point_lights))
+    return fail(ST_ERR_INVALID_ARG, "bad point lights");
+  if (d->n_point_lights == 0 && !d->env) return fail(ST_ERR_INVALID_ARG, "scene has no light");
+  for (int j = 0; j < d->n_point_lights; ++j)
+    for (int k = 0; k < 3; ++k)
+      if (!std::isfinite(d->point_lights[j].pos[k]) || !std::isfinite(d->point_lights[j].intensity[k]) ||
+          d->point_lights[j].intensity[k] < 0)
+        return fail(ST_ERR_INVALID_ARG, "point light " + std::to_string(j) + " is invalid");
+  if (d->env && (d->env->width <= 0 || d->env->height <= 0 || !d->env->rgb ||
+                 (long long)d->env->width * d->env->height > (1LL << 24)))
+    return fail(ST_ERR_INVALID_ARG, "bad environment map");
+  cudaStream_t st = (cudaStream_t)stream;
+  st_scene* s = new st_scene();
+  cudaGetDevice(&s->device);
+  cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, s->device);
+  s->nv = d->n_vertices;
+  s->nf = d->n_faces;
+  s->brdf = d->brdf;
+  s->nl = d->n_point_lights;
+  // host copy of the faces: validation and edge list
+  std::vector<int> hf(3 * (size_t)s->nf);
+  std::vector<float> hv(3 * (size_t)s->nv);
+  cudaError_t e = cudaMemcpyAsync(hf.data(), d->faces, hf.size() * sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hv.data(), d->vertices, hv.size() * sizeof(float), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) { destroy(s); return cuda_fail(e, "reading the mesh"); }
+  for (int v : hf)
+    if (v < 0 || v >= s->nv) { destroy(s); return fail(ST_ERR_INVALID_ARG, "face index out of range"); }
+  for (float x : hv)
+    if (!std::isfinite(x)) { destroy(s); return fail(ST_ERR_INVALID_ARG, "non-finite vertex"); }
+  for (int f = 0; f < s->nf; ++f) {
+    int a = hf[3 * f], b = hf[3 * f + 1], c = hf[3 * f + 2];
+    if (a == b || b == c || a == c) { destroy(s); return fail(ST_ERR_INVALID_ARG, "degenerate face " + std::to_string(f)); }
+  }
+  std::vector<int2> ev, ef;
+  build_edges(hf, s->nf, ev, ef);
+  s->n_edges = (int)ev.size();
+  std::vector<float4> etex;
+  std::vector<float2> etab;
+  if (d->env) {
+    if (!build_alias(d->env->rgb, d->env->width, d->env->height, etex, etab)) {
+      destroy(s);
+      return fail(ST_ERR_INVALID_ARG, "environment map has no positive finite weight");
+    }
+  }
+  int n = s->nf;
+  s->sort_blocks = sort_blocks_for(n);
+  e = cudaSuccess;
+  auto chk = [&](cudaError_t x) { if (x != cudaSuccess && e == cudaSuccess) e = x; };
+  chk(dalloc(&s->verts, 3 * (size_t)s->nv)); chk(dalloc(&s->faces, 3 * (size_t)n)); chk(dalloc(&s->params, 2 * (size_t)n));
+  chk(dalloc(&s->tri, 3 * (size_t)n)); chk(dalloc(&s->nodes, 4 * (size_t)std::max(n - 1, 1)));
+  chk(dalloc(&s->parent, 2 * (size_t)n)); chk(dalloc(&s->flags, (size_t)std::max(n - 1, 1)));
+  chk(dalloc(&s->keys, (size_t)n)); chk(dalloc(&s->keys2, (size_t)n)); chk(dalloc(&s->ids, (size_t)n));
+  chk(dalloc(&s->ids2, (size_t)n)); chk(dalloc(&s->hist, 256 * (size_t)s->sort_blocks)); chk(dalloc(&s->bounds, 6));
+  chk(dalloc(&s->lights, 2 * (size_t)std::max(s->nl, 1))); chk(dalloc(&s->edge_v, ev.size()));
+  chk(dalloc(&s->edge_f, ef.size())); chk(dalloc(&s->d_args, 1)); chk(dalloc(&s->d_err, 1));
+  if (d->env) { chk(dalloc(&s->env_tex, etex.size())); chk(dalloc(&s->env_alias, etab.size())); }
+  if (e != cudaSuccess) { destroy(s); cudaGetLastError(); return fail(ST_ERR_OOM, "scene buffers"); }
+  std::vector<float4> hl(2 * (size_t)std::max(s->nl, 1), make_float4(0, 0, 0, 0));
+  for (int j = 0; j < s->nl; ++j) {
+    const st_point_light& L = d->point_lights[j];
+    s->host_lights.push_back(L);
+    hl[2 * j] = make_float4(L.pos[0], L.pos[1], L.pos[2], 0.0f);
+    hl[2 * j + 1] = make_float4(L.intensity[0], L.intensity[1], L.intensity[2], 0.0f);
+  }
+  chk(cudaMemcpyAsync(s->verts, d->vertices, 3 * sizeof(float) * s->nv, cudaMemcpyDeviceToDevice, st));
+  chk(cudaMemcpyAsync(s->faces, d->faces, 3 * sizeof(int) * n, cudaMemcpyDeviceToDevice, st));
+  if (n > 0) k_params_in<<<(n + 255) / 256, 256, 0, st>>>(d->face_params, s->params, n);
+  chk(cudaMemcpyAsync(s->lights, hl.data(), hl.size() * sizeof(float4), cudaMemcpyHostToDevice, st));
+  chk(cudaMemcpyAsync(s->edge_v, ev.data(), ev.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
+  chk(cudaMemcpyAsync(s->edge_f, ef.data(), ef.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
+  chk(cudaMemsetAsync(s->d_err, 0, sizeof(int), st));
+  if (d->env) {
+    chk(cudaMemcpyAsync(s->env_tex, etex.data(), etex.size() * sizeof(float4), cudaMemcpyHostToDevice, st));
+    chk(cudaMemcpyAsync(s->env_alias, etab.data(), etab.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
+    s->env.w = d->env->width;
+    s->env.h = d->env->height;
+    s->env.tex = s->env_tex;
+    s->env.alias = s->env_alias;
+    s->env.pdf_scale = (float)((double)d->env->width * d->env->height / (2.0 * 3.14159265358979323846 * 3.14159265358979323846));
+  }
+  chk(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
+  if (e == cudaSuccess) e = bvh_build(s, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) { destroy(s); return cuda_fail(e, "scene create"); }
+  *out = s;
+  return ST_OK;
+}
+
+st_status st_scene_destroy(st_scene* s) {
+  destroy(s);
+  return ST_OK;
+}
+
+static st_status update_vertices(st_scene* s, const float* v, void* stream, bool rebuild) {
+  if (!s || !v) return fail(ST_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  ST_CUDA(cudaMemcpyAsync(s->verts, v, 3 * sizeof(float) * s->nv, cudaMemcpyDeviceToDevice, st));
+  cudaError_t e = rebuild ? bvh_build(s, st) : bvh_refit(s, st);
+  if (e != cudaSuccess) return cuda_fail(e, rebuild ? "rebuild" : "refit");
+  return ST_OK;
+}
+
+st_status st_refit(st_scene* s, const float* v, void* stream) { return update_vertices(s, v, stream, false); }
+st_status st_rebuild(st_scene* s, const float* v, void* stream) { return update_vertices(s, v, stream, true); }
+
+st_status st_set_face_params(st_scene* s, const float* p, void* stream) {
+  if (!s || !p) return fail(ST_ERR_INVALID_ARG, "NULL argument");
+  k_params_in<<<(s->nf + 255) / 256, 256, 0, (cudaStream_t)stream>>>(p, s->params, s->nf);
+  ST_CUDA(cudaGetLastError());
+  return ST_OK;
+}
+
+st_status st_render(st_scene* s, const st_view* views, int n_views, int default_spp, int max_bounces,
+                    unsigned long long seed, const st_render_opts* opts, float* out_image, void* stream) {
+  if (!s || !out_image) return fail(ST_ERR_INVALID_ARG, "NULL argument");
+  Plan p;
+  st_status r = plan_call(s, views, n_views, default_spp, max_bounces, opts, 0, false, p);
+  if (r != ST_OK) return r;
+  CallArgs a{(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32), out_image, nullptr, nullptr, nullptr};
+  s->image_ptr = out_image;
+  return run_call(s, p, a, (cudaStream_t)stream);
+}
+
+st_status st_render_backward(st_scene* s, const st_view* views, int n_views, int default_spp, int max_bounces,
+                             unsigned long long seed, const st_render_opts* opts, const float* dLdI, float* dV,
+                             float* dF, void* stream) {
+  if (!s || !dLdI) return fail(ST_ERR_INVALID_ARG, "NULL argument");
+  st_render_opts o = opts ? *opts : default_opts();
+  if (o.edge_term && !dV) return fail(ST_ERR_INVALID_ARG, "edge term needs d_vertices");
+  if (!dV && !dF) return fail(ST_ERR_INVALID_ARG, "no gradient requested");
+  Plan p;
+  st_status r = plan_call(s, views, n_views, default_spp, max_bounces, &o, 1, true, p);
+  if (r != ST_OK) return r;
+  CallArgs a{(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32), nullptr, dLdI, dV, dF};
+  s->image_ptr = nullptr;
+  return run_call(s, p, a, (cudaStream_t)stream);
+}
+
+st_status st_trace_closest(st_scene* s, const float* rays, int n, int exclude, int* out_tri, float* out_t,
+                           void* stream) {
+  if (!s || (n > 0 && (!rays || !out_tri || !out_t)) || n < 0) return fail(ST_ERR_INVALID_ARG, "bad arguments");
+  if (n == 0) return ST_OK;
+  k_trace_rays<<<(n + EXT_BLOCK - 1) / EXT_BLOCK, EXT_BLOCK, 0, (cudaStream_t)stream>>>(
+      s->nodes, s->tri, s->nf, (const float4*)rays, n, exclude, out_tri, out_t, s->d_err);
+  ST_CUDA(cudaGetLastError());
+  return ST_OK;
+}
+
+st_status st_get_stats(st_scene* s, st_stats* out) {
+  if (!s || !out) return fail(ST_ERR_INVALID_ARG, "NULL argument");
+  ST_CUDA(cudaDeviceSynchronize());
+  st_stats r;
+  std::memset(&r, 0, sizeof(r));
+  unsigned long long h[STAT_SIZE] = {0};
+  if (s->eng.stat) ST_CUDA(cudaMemcpy(h, s->eng.stat, sizeof(h), cudaMemcpyDeviceToHost));
+  int err = 0;
+  ST_CUDA(cudaMemcpy(&err, s->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  r.paths = (long long)h[STAT_PATHS];
+  r.extension_rays = (long long)h[STAT_EXT];
+  r.shadow_rays = (long long)h[STAT_SHADOW];
+  r.node_visits = (long long)h[STAT_VISITS];
+  r.tri_tests = (long long)h[STAT_TESTS];
+  r.edge_samples = s->last_edge_samples;
+  double ms = 0;
+  for (int i = 0; i < s->ev_used; ++i) {
+    float x = 0;
+    cudaEventElapsedTime(&x, s->ev[i].first, s->ev[i].second);
+    ms += x;
+  }
+  r.extend_launches = s->ev_used;
+  r.extend_ms = ms;
+  r.device_error = err;
+  r.bvh_nodes = std::max(s->nf - 1, 0);
+  r.scratch_bytes = s->eng.bytes;
+  *out = r;
+  return ST_OK;
+}
+
+st_status st_debug_bvh(st_scene* s, float* nodes, int* leaf_faces) {
+  if (!s || !nodes || !leaf_faces) return fail(ST_ERR_INVALID_ARG, "NULL argument");
+  ST_CUDA(cudaDeviceSynchronize());
+  if (s->nf > 1) ST_CUDA(cudaMemcpy(nodes, s->nodes, sizeof(float4) * 4 * (s->nf - 1), cudaMemcpyDeviceToHost));
+  ST_CUDA(cudaMemcpy(leaf_faces, s->ids, sizeof(int) * s->nf, cudaMemcpyDeviceToHost));
+  return ST_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,259 @@
+// LBVH construction and refit.
+//
+// Build: centroid bounds -> 30-bit Morton code per triangle centroid -> stable
+// LSD radix sort of (code, face id) -> Karras' parallel hierarchy ("Maximizing
+// Parallelism in the Construction of BVHs, Octrees, and k-d Trees", HPG 2012),
+// ties between equal codes broken by the leaf index -> leaf triangle records in
+// Morton order -> boxes bottom-up, the second thread to reach a node merging
+// its two children. Refit reuses the order and the hierarchy: new vertex
+// positions only rewrite the leaf records and the boxes.
+#include <cstdio>
+
+#include "st_internal.h"
+
+namespace st {
+namespace {
+
+constexpr int RS_THREADS = 256;
+constexpr int RS_ROUNDS = 16;
+constexpr int RS_TILE = RS_THREADS * RS_ROUNDS;
+
+__device__ __forceinline__ int ordered(float f) {
+  int i = __float_as_int(f);
+  return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float unordered(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
+
+__device__ __forceinline__ float3 centroid(const float* V, const int* F, int f) {
+  int a = F[3 * f], b = F[3 * f + 1], c = F[3 * f + 2];
+  return mk3((V[3 * a] + V[3 * b] + V[3 * c]) * (1.0f / 3.0f), (V[3 * a + 1] + V[3 * b + 1] + V[3 * c + 1]) * (1.0f / 3.0f),
+             (V[3 * a + 2] + V[3 * b + 2] + V[3 * c + 2]) * (1.0f / 3.0f));
+}
+
+__global__ void k_init_bounds(int* b) {
+  if (threadIdx.x < 3) b[threadIdx.x] = 0x7fffffff;
+  else if (threadIdx.x < 6) b[threadIdx.x] = (int)0x80000000;
+}
+
+__global__ void k_centroid_bounds(const float* V, const int* F, int nf, int* bounds) {
+  float3 lo = mk3(3.4e38f, 3.4e38f, 3.4e38f), hi = mk3(-3.4e38f, -3.4e38f, -3.4e38f);
+  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += gridDim.x * blockDim.x) {
+    float3 c = centroid(V, F, f);
+    lo = mk3(fminf(lo.x, c.x), fminf(lo.y, c.y), fminf(lo.z, c.z));
+    hi = mk3(fmaxf(hi.x, c.x), fmaxf(hi.y, c.y), fmaxf(hi.z, c.z));
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    lo.x = fminf(lo.x, __shfl_xor_sync(0xffffffffu, lo.x, off));
+    lo.y = fminf(lo.y, __shfl_xor_sync(0xffffffffu, lo.y, off));
+    lo.z = fminf(lo.z, __shfl_xor_sync(0xffffffffu, lo.z, off));
+    hi.x = fmaxf(hi.x, __shfl_xor_sync(0xffffffffu, hi.x, off));
+    hi.y = fmaxf(hi.y, __shfl_xor_sync(0xffffffffu, hi.y, off));
+    hi.z = fmaxf(hi.z, __shfl_xor_sync(0xffffffffu, hi.z, off));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(&bounds[0], ordered(lo.x)); atomicMin(&bounds[1], ordered(lo.y)); atomicMin(&bounds[2], ordered(lo.z));
+    atomicMax(&bounds[3], ordered(hi.x)); atomicMax(&bounds[4], ordered(hi.y)); atomicMax(&bounds[5], ordered(hi.z));
+  }
+}
+
+__device__ __forceinline__ uint32_t spread10(uint32_t v) {
+  v = (v * 0x00010001u) & 0xFF0000FFu;
+  v = (v * 0x00000101u) & 0x0F00F00Fu;
+  v = (v * 0x00000011u) & 0xC30C30C3u;
+  v = (v * 0x00000005u) & 0x49249249u;
+  return v;
+}
+
+__global__ void k_morton(const float* V, const int* F, int nf, const int* bounds, uint32_t* keys, int* ids) {
+  int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= nf) return;
+  float3 lo = mk3(unordered(bounds[0]), unordered(bounds[1]), unordered(bounds[2]));
+  float3 hi = mk3(unordered(bounds[3]), unordered(bounds[4]), unordered(bounds[5]));
+  float3 c = centroid(V, F, f);
+  float3 ext = hi - lo;
+  auto q = [](float x, float l, float e) -> uint32_t {
+    float u = e > 0.0f ? (x - l) / e : 0.5f;
+    return (uint32_t)fminf(fmaxf(u * 1024.0f, 0.0f), 1023.0f);
+  };
+  keys[f] = (spread10(q(c.x, lo.x, ext.x)) << 2) | (spread10(q(c.y, lo.y, ext.y)) << 1) | spread10(q(c.z, lo.z, ext.z));
+  ids[f] = f;
+}
+
+// ---- stable LSD radix sort, 8-bit digits
+__global__ void k_rs_hist(const uint32_t* keys, int n, int shift, uint32_t* hist, int nblk) {
+  __shared__ uint32_t h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  int base = blockIdx.x * RS_TILE;
+  for (int i = threadIdx.x; i < RS_TILE; i += RS_THREADS) {
+    int idx = base + i;
+    if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  hist[threadIdx.x * nblk + blockIdx.x] = h[threadIdx.x];
+}
+
+// exclusive scan of m counters in place, one block of 1024 threads
+__global__ void k_rs_scan(uint32_t* hist, int m) {
+  __shared__ uint32_t part[1024];
+  int per = (m + 1023) / 1024;
+  int b = threadIdx.x * per, e = min(b + per, m);
+  uint32_t s = 0;
+  for (int i = b; i < e; ++i) s += hist[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    uint32_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  uint32_t run = part[threadIdx.x] - s;
+  for (int i = b; i < e; ++i) { uint32_t c = hist[i]; hist[i] = run; run += c; }
+}
+
+__global__ void k_rs_scatter(const uint32_t* kin, const int* iin, uint32_t* kout, int* iout, int n, int shift,
+                             const uint32_t* hist, int nblk) {
+  __shared__ uint32_t offs[256];
+  __shared__ uint32_t wc[RS_THREADS / 32][256];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  offs[t] = hist[t * nblk + blockIdx.x];
+  const unsigned lt = (1u << lane) - 1u;
+  int base = blockIdx.x * RS_TILE;
+  for (int r = 0; r < RS_ROUNDS; ++r) {
+#pragma unroll
+    for (int w = 0; w < RS_THREADS / 32; ++w) wc[w][t] = 0;
+    __syncthreads();
+    int idx = base + r * RS_THREADS + t;
+    bool valid = idx < n;
+    uint32_t key = valid ? kin[idx] : 0u;
+    int id = valid ? iin[idx] : 0;
+    int digit = valid ? (int)((key >> shift) & 255u) : 256;
+    unsigned peers = __match_any_sync(0xffffffffu, digit);
+    int rank = __popc(peers & lt);
+    if (valid && rank == 0) wc[warp][digit] = __popc(peers);
+    __syncthreads();
+    uint32_t run = 0;
+#pragma unroll
+    for (int w = 0; w < RS_THREADS / 32; ++w) { uint32_t c = wc[w][t]; wc[w][t] = run; run += c; }
+    __syncthreads();
+    if (valid) {
+      uint32_t dst = offs[digit] + wc[warp][digit] + rank;
+      kout[dst] = key;
+      iout[dst] = id;
+    }
+    __syncthreads();
+    offs[t] += run;
+    __syncthreads();
+  }
+}
+
+// ---- Karras hierarchy
+__device__ __forceinline__ int delta(const uint32_t* k, int n, int i, int j) {
+  if (j < 0 || j >= n) return -1;
+  uint32_t a = k[i], b = k[j];
+  return a != b ? __clz(a ^ b) : 32 + __clz((uint32_t)i ^ (uint32_t)j);
+}
+
+__global__ void k_hierarchy(const uint32_t* keys, int n, float4* nodes, int* parent) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n - 1) return;
+  int dir = (delta(keys, n, i, i + 1) - delta(keys, n, i, i - 1)) >= 0 ? 1 : -1;
+  int dmin = delta(keys, n, i, i - dir);
+  int lmax = 2;
+  while (delta(keys, n, i, i + lmax * dir) > dmin) lmax <<= 1;
+  int l = 0;
+  for (int t = lmax >> 1; t >= 1; t >>= 1)
+    if (delta(keys, n, i, i + (l + t) * dir) > dmin) l += t;
+  int j = i + l * dir;
+  int dnode = delta(keys, n, i, j);
+  int s = 0, t = l;
+  do {
+    t = (t + 1) >> 1;
+    if (delta(keys, n, i, i + (s + t) * dir) > dnode) s += t;
+  } while (t > 1);
+  int g = i + s * dir + min(dir, 0);
+  int left = (min(i, j) == g) ? ~g : g;
+  int right = (max(i, j) == g + 1) ? ~(g + 1) : g + 1;
+  nodes[4 * i + 3] = make_float4(__int_as_float(left), __int_as_float(right), 0.0f, 0.0f);
+  if (left < 0) parent[(n - 1) + ~left] = i; else parent[left] = i;
+  if (right < 0) parent[(n - 1) + ~right] = i; else parent[right] = i;
+  if (i == 0) parent[0] = -1;
+}
+
+// ---- leaf records and bottom-up boxes
+__global__ void k_boxes(const float* V, const int* F, const int* ids, int n, float4* tri, float4* nodes,
+                        const int* parent, int* flags) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int f = ids[i];
+  int a = F[3 * f], b = F[3 * f + 1], c = F[3 * f + 2];
+  float3 p0 = mk3(V[3 * a], V[3 * a + 1], V[3 * a + 2]);
+  float3 p1 = mk3(V[3 * b], V[3 * b + 1], V[3 * b + 2]);
+  float3 p2 = mk3(V[3 * c], V[3 * c + 1], V[3 * c + 2]);
+  tri[3 * i] = make_float4(p0.x, p0.y, p0.z, __int_as_float(f));
+  tri[3 * i + 1] = make_float4(p1.x, p1.y, p1.z, 0.0f);
+  tri[3 * i + 2] = make_float4(p2.x, p2.y, p2.z, 0.0f);
+  if (n == 1) return;
+  float3 lo = mk3(fminf(fminf(p0.x, p1.x), p2.x), fminf(fminf(p0.y, p1.y), p2.y), fminf(fminf(p0.z, p1.z), p2.z));
+  float3 hi = mk3(fmaxf(fmaxf(p0.x, p1.x), p2.x), fmaxf(fmaxf(p0.y, p1.y), p2.y), fmaxf(fmaxf(p0.z, p1.z), p2.z));
+  int child = ~i;
+  int node = parent[(n - 1) + i];
+  while (node >= 0) {
+    float4* np = nodes + 4 * node;
+    int cl = __float_as_int(np[3].x);
+    if (cl == child) {
+      np[0] = make_float4(lo.x, hi.x, lo.y, hi.y);
+      np[1].x = lo.z; np[1].y = hi.z;
+    } else {
+      np[1].z = lo.x; np[1].w = hi.x;
+      np[2] = make_float4(lo.y, hi.y, lo.z, hi.z);
+    }
+    __threadfence();
+    if (atomicAdd(&flags[node], 1) == 0) return;  // the sibling's thread finishes this node
+    __threadfence();
+    float4 n0 = __ldcg(np), n1 = __ldcg(np + 1), n2 = __ldcg(np + 2);
+    lo = mk3(fminf(n0.x, n1.z), fminf(n0.z, n2.x), fminf(n1.x, n2.z));
+    hi = mk3(fmaxf(n0.y, n1.w), fmaxf(n0.w, n2.y), fmaxf(n1.y, n2.w));
+    child = node;
+    node = parent[node];
+  }
+}
+
+cudaError_t boxes(st_scene* s, cudaStream_t stream) {
+  int n = s->nf;
+  if (n > 1) cudaMemsetAsync(s->flags, 0, sizeof(int) * (n - 1), stream);
+  k_boxes<<<(n + 255) / 256, 256, 0, stream>>>(s->verts, s->faces, s->ids, n, s->tri, s->nodes, s->parent, s->flags);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t bvh_build(st_scene* s, cudaStream_t stream) {
+  int n = s->nf;
+  k_init_bounds<<<1, 32, 0, stream>>>(s->bounds);
+  int g = min((n + 255) / 256, 4 * max(s->sm_count, 1));
+  k_centroid_bounds<<<g, 256, 0, stream>>>(s->verts, s->faces, n, s->bounds);
+  k_morton<<<(n + 255) / 256, 256, 0, stream>>>(s->verts, s->faces, n, s->bounds, s->keys, s->ids);
+  uint32_t *ka = s->keys, *kb = s->keys2;
+  int *ia = s->ids, *ib = s->ids2;
+  int nblk = s->sort_blocks;
+  for (int shift = 0; shift < 32; shift += 8) {
+    k_rs_hist<<<nblk, RS_THREADS, 0, stream>>>(ka, n, shift, s->hist, nblk);
+    k_rs_scan<<<1, 1024, 0, stream>>>(s->hist, 256 * nblk);
+    k_rs_scatter<<<nblk, RS_THREADS, 0, stream>>>(ka, ia, kb, ib, n, shift, s->hist, nblk);
+    std::swap(ka, kb);
+    std::swap(ia, ib);
+  }
+  // four passes: the sorted data is back in the primary buffers
+  if (n > 1) k_hierarchy<<<(n - 1 + 255) / 256, 256, 0, stream>>>(s->keys, n, s->nodes, s->parent);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return boxes(s, stream);
+}
+
+cudaError_t bvh_refit(st_scene* s, cudaStream_t stream) { return boxes(s, stream); }
+
+int sort_blocks_for(int n) { return (n + RS_TILE - 1) / RS_TILE; }
+
+}  // namespace st

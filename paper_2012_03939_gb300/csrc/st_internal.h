@@ -1,0 +1,120 @@
+// Library-internal scene state shared by the translation units of libst.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "st.h"
+#include "st_device.cuh"
+
+namespace st {
+
+// Per-call arguments the kernels read from device memory, so a captured CUDA
+// graph can be replayed with a new seed, new output pointers and new camera
+// poses without recapture.
+struct CallArgs {
+  uint32_t k0, k1;          // Philox key = seed
+  float* image;             // forward output
+  const float* dLdI;        // backward input
+  float* dV;                // backward outputs (accumulated)
+  float* dF;
+};
+
+// A contiguous range of the call's job space: camera samples of one view, or
+// edge-sample sides of one view.
+struct Seg {
+  long long base, count;
+  int view, kind;           // kind 0 = camera paths, 1 = edge sides (two jobs per sample)
+  long long n_samples;      // kind 1: N_e; kind 0: W*H*spp
+};
+
+// Device pointers of the wavefront engine (one chunk of Q path slots).
+struct Engine {
+  int Q = 0, B = 0, NS = 0;   // capacity, bounces the records were sized for, shadow rays per path
+  bool records = false;
+  float4 *o = nullptr, *d = nullptr, *thr = nullptr, *rad = nullptr;
+  int4* ctr = nullptr;        // (c0, c1, stream, job kind)
+  int2* hit = nullptr;        // (face, t bits)
+  int* origin = nullptr;
+  int *q0 = nullptr, *q1 = nullptr, *qs = nullptr;
+  float4 *sh_dir = nullptr, *sh_c = nullptr;  // [NS][Q]
+  float4 *r0 = nullptr, *r1 = nullptr, *r2 = nullptr, *r3 = nullptr;  // [B+1][Q] records
+  float4* esc = nullptr;      // escape radiance (rgb, flag)
+  int* nb = nullptr;          // hits per path
+  int* cnt = nullptr;         // counters, see CNT_*
+  unsigned long long* stat = nullptr;  // per-call 64-bit statistics, see STAT_*
+  long long bytes = 0;
+};
+
+enum { CNT_EXT = 0, CNT_EXT_FETCH = 16, CNT_SHADE_FETCH = 32, CNT_SH = 48, CNT_SH_FETCH = 64, CNT_MISC = 80,
+       CNT_SIZE = 96 };
+enum { STAT_PATHS = 0, STAT_EXT = 1, STAT_SHADOW = 2, STAT_EDGE = 3, STAT_VISITS = 4, STAT_TESTS = 5,
+       STAT_SIZE = 8 };
+
+struct GraphEntry {
+  std::vector<long long> key;
+  cudaGraphExec_t exec = nullptr;
+};
+
+}  // namespace st
+
+struct st_scene {
+  int device = 0;
+  int nv = 0, nf = 0, brdf = 0, nl = 0;
+  float* verts = nullptr;        // [V*3]
+  int* faces = nullptr;          // [F*3]
+  float4* params = nullptr;      // [F*2]: (kd_r, kd_g, kd_b, ks), (roughness, 0, 0, 0)
+  // LBVH
+  float4* tri = nullptr;         // [F*3] triangles in leaf order; tri[3i].w = face id bits
+  float4* nodes = nullptr;       // [(F-1)*4]
+  int* parent = nullptr;         // [F-1] internal parents, then [F] leaf parents
+  int* flags = nullptr;          // [F-1] bottom-up visit counters
+  uint32_t *keys = nullptr, *keys2 = nullptr;
+  int *ids = nullptr, *ids2 = nullptr;
+  uint32_t* hist = nullptr;
+  int* bounds = nullptr;         // [6] ordered-int centroid bounds
+  int sort_blocks = 0;
+  // lights
+  float4* lights = nullptr;      // [nl*2]: (pos, 0), (intensity, 0)
+  std::vector<st_point_light> host_lights;
+  // environment
+  st::DevEnv env{};
+  float4* env_tex = nullptr;
+  float2* env_alias = nullptr;
+  // edges (sorted by (min vertex, max vertex))
+  int n_edges = 0;
+  int2* edge_v = nullptr;
+  int2* edge_f = nullptr;        // second face -1 on a boundary; -2 if more than two faces
+  int* edge_flag = nullptr;      // [views * E]
+  int* edge_cand = nullptr;      // [views * E]
+  int* edge_ncand = nullptr;     // [views]
+  int edge_cap_views = 0;
+  // per-call tables
+  st::DevView* d_views = nullptr;
+  st::Seg* d_segs = nullptr;
+  st::CallArgs* d_args = nullptr;
+  int view_cap = 0;
+  st::Engine eng;
+  int* d_err = nullptr;
+  // graph cache
+  cudaStream_t cap_stream = nullptr;
+  std::vector<st::GraphEntry> graphs;
+  // timing
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+  int ev_used = 0;
+  int sm_count = 0;
+  float* image_ptr = nullptr;    // forward output of the call being planned (graph key)
+  long long last_edge_samples = 0;
+  st_stats last{};
+};
+
+namespace st {
+cudaError_t bvh_build(st_scene* s, cudaStream_t stream);    // Morton order + hierarchy + boxes
+cudaError_t bvh_refit(st_scene* s, cudaStream_t stream);    // leaf records + boxes, same order
+cudaError_t trace_closest(st_scene* s, const float* rays, int n, int exclude, int* out_tri, float* out_t,
+                          cudaStream_t stream);
+void set_error(const std::string& msg);
+int sort_blocks_for(int n);
+}  // namespace st

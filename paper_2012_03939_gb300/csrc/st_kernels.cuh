@@ -1,0 +1,684 @@
+// Wavefront kernels of the forward path trace, its adjoint and the edge term.
+//
+// One chunk of Q path slots is processed stage by stage: raygen fills the
+// extension queue, then for each bounce b: extend (closest hit), shade
+// (flat-normal Torrance-Sparrow vertex: next-event rays to every point light
+// and one alias-sampled environment direction, then a BSDF-sampled
+// continuation appended to the next queue), shadow (any hit for the NEE rays).
+// Queues are compacted with warp-aggregated atomics. Stage kernels are
+// persistent: each warp fetches 32 queue entries at a time from a device
+// counter, so the same launch works for any queue length (needed for CUDA
+// graph replay, where the host never reads the counts).
+#pragma once
+#include "st_internal.h"
+#include "st_trace.cuh"
+
+namespace st {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int EXT_BLOCK = 128;
+constexpr int ENV_VALID = 1 << 30;
+constexpr int ENV_VIS = 1 << 8;
+
+struct KCtx {
+  const float* V;
+  const int* F;
+  const float4* P;
+  const float4* nodes;
+  const float4* tri;
+  int nf;
+  const float4* lights;
+  int nl, NS;
+  DevEnv env;
+  int brdf;
+  const int2* edge_v;
+  const int2* edge_f;
+  int n_edges;
+  int edge_mode;
+  int* edge_flag;
+  int* edge_cand;
+  int* edge_ncand;
+  const DevView* views;
+  const Seg* segs;
+  int n_segs;
+  const CallArgs* args;
+  int B;
+  Engine e;
+  int* err;
+};
+
+__device__ __forceinline__ int find_seg(const Seg* segs, int n, long long job) {
+  int lo = 0, hi = n - 1, r = -1;
+  while (lo <= hi) {
+    int mid = (lo + hi) >> 1;
+    if (segs[mid].base <= job) { r = mid; lo = mid + 1; } else hi = mid - 1;
+  }
+  return r;
+}
+
+// all 32 lanes must call; returns this lane's slot in the queue (or -1)
+__device__ __forceinline__ int warp_append(int* counter, bool pred) {
+  unsigned m = __ballot_sync(FULL, pred);
+  int lane = threadIdx.x & 31;
+  int base = 0;
+  if (m) {
+    int leader = __ffs(m) - 1;
+    if (lane == leader) base = atomicAdd(counter, __popc(m));
+    base = __shfl_sync(FULL, base, leader);
+  }
+  return pred ? base + __popc(m & ((1u << lane) - 1u)) : -1;
+}
+
+__device__ __forceinline__ float3 fetch_vertex(const float* V, int v) { return mk3(V[3 * v], V[3 * v + 1], V[3 * v + 2]); }
+
+__device__ __forceinline__ Mat fetch_mat(const float4* P, int f) {
+  float4 a = __ldg(&P[2 * f]), b = __ldg(&P[2 * f + 1]);
+  Mat m;
+  m.kd[0] = a.x; m.kd[1] = a.y; m.kd[2] = a.z; m.ks = a.w; m.alpha = b.x;
+  return m;
+}
+
+// ------------------------------------------------------------------ edges
+__device__ __forceinline__ bool facing(const KCtx& c, int f, float3 eye) {
+  int a = c.F[3 * f], b = c.F[3 * f + 1], d = c.F[3 * f + 2];
+  float3 p0 = fetch_vertex(c.V, a);
+  float3 m = cross3(fetch_vertex(c.V, b) - p0, fetch_vertex(c.V, d) - p0);
+  return dot3(m, eye - p0) > 0.0f;
+}
+
+// screen segment of edge e clipped to the image; false if not drawable
+__device__ __forceinline__ bool edge_screen(const KCtx& c, const DevView& v, int e, float2& sa, float2& sb, float& t0,
+                                            float& t1) {
+  int2 ev = c.edge_v[e];
+  if (!cam_project(v, fetch_vertex(c.V, ev.x), sa.x, sa.y)) return false;
+  if (!cam_project(v, fetch_vertex(c.V, ev.y), sb.x, sb.y)) return false;
+  float dx = sb.x - sa.x, dy = sb.y - sa.y;
+  float pp[4] = {-dx, dx, -dy, dy};
+  float qq[4] = {sa.x, (float)v.W - sa.x, sa.y, (float)v.H - sa.y};
+  t0 = 0.0f; t1 = 1.0f;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (pp[k] == 0.0f) { if (qq[k] < 0.0f) return false; continue; }
+    float r = qq[k] / pp[k];
+    if (pp[k] < 0.0f) t0 = fmaxf(t0, r); else t1 = fminf(t1, r);
+  }
+  if (!(t1 > t0)) return false;
+  return sqrtf(dx * dx + dy * dy) * (t1 - t0) > 0.0f;
+}
+
+__device__ __forceinline__ bool edge_candidate(const KCtx& c, const DevView& v, int e) {
+  if (c.edge_mode == 0) {
+    int2 ef = c.edge_f[e];
+    if (ef.y >= 0 && facing(c, ef.x, v.eye) == facing(c, ef.y, v.eye)) return false;
+  }
+  float2 sa, sb;
+  float t0, t1;
+  return edge_screen(c, v, e, sa, sb, t0, t1);
+}
+
+struct EdgeSample {
+  bool valid;
+  int e, px, py;
+  float tau, len;
+  float2 S, ns;
+};
+
+// Sample k of view vi: candidate chosen uniformly by an integer map of a 24-bit
+// word, point uniform along its clipped screen segment.
+__device__ __forceinline__ EdgeSample edge_sample(const KCtx& c, int vi, const DevView& v, long long k, Key key) {
+  EdgeSample s;
+  s.valid = false;
+  int nc = c.edge_ncand[vi];
+  if (nc <= 0) return s;
+  U4 u = philox((uint32_t)k, v.off, 0u, 1u, key.k0, key.k1);
+  int i = (int)(((uint64_t)(u.x >> 8) * (uint64_t)nc) >> 24);
+  s.e = c.edge_cand[(size_t)vi * c.n_edges + i];
+  float2 sa, sb;
+  float t0, t1;
+  if (!edge_screen(c, v, s.e, sa, sb, t0, t1)) return s;
+  s.tau = t0 + unif(u.y) * (t1 - t0);
+  float ex = sb.x - sa.x, ey = sb.y - sa.y;
+  s.S = make_float2(sa.x + ex * s.tau, sa.y + ey * s.tau);
+  s.px = (int)floorf(s.S.x);
+  s.py = (int)floorf(s.S.y);
+  if (s.px < 0 || s.py < 0 || s.px >= v.W || s.py >= v.H) return s;
+  float el = sqrtf(ex * ex + ey * ey);
+  s.ns = make_float2(-ey / el, ex / el);
+  s.len = el * (t1 - t0);
+  s.valid = true;
+  return s;
+}
+
+__global__ void k_edge_flags(KCtx c, int n_views) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  int vi = blockIdx.y;
+  if (e >= c.n_edges || vi >= n_views) return;
+  DevView v = c.views[vi];
+  c.edge_flag[(size_t)vi * c.n_edges + e] = edge_candidate(c, v, e) ? 1 : 0;
+}
+
+// one block per view: ordered compaction of the candidate flags
+__global__ void k_edge_compact(KCtx c) {
+  __shared__ int part[1024];
+  int vi = blockIdx.x;
+  const int* fl = c.edge_flag + (size_t)vi * c.n_edges;
+  int* out = c.edge_cand + (size_t)vi * c.n_edges;
+  int E = c.n_edges;
+  int per = (E + 1023) / 1024;
+  int b = threadIdx.x * per, en = min(b + per, E);
+  int s = 0;
+  for (int i = b; i < en; ++i) s += fl[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    int v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int run = part[threadIdx.x] - s;
+  for (int i = b; i < en; ++i)
+    if (fl[i]) out[run++] = i;
+  if (threadIdx.x == 1023) c.edge_ncand[vi] = part[1023];
+}
+
+// ------------------------------------------------------------------ chunk stages
+__global__ void k_reset(int* cnt) {
+  for (int i = threadIdx.x; i < CNT_SIZE; i += blockDim.x) cnt[i] = 0;
+}
+
+__global__ void k_raygen(KCtx c, long long j0, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const Engine& E = c.e;
+  bool ok = false;
+  float3 o = mk3(0, 0, 0), d = mk3(0, 0, 1);
+  int4 ct = make_int4(0, 0, 0, 0);
+  if (i < n) {
+    long long job = j0 + i;
+    int si = find_seg(c.segs, c.n_segs, job);
+    if (si >= 0) {
+      Seg sg = c.segs[si];
+      long long local = job - sg.base;
+      if (local < sg.count) {
+        DevView v = c.views[sg.view];
+        Key key{c.args->k0, c.args->k1};
+        if (sg.kind == 0) {
+          long long pixel = local / v.spp;
+          int s = (int)(local - pixel * v.spp);
+          int x = (int)(pixel % v.W), y = (int)(pixel / v.W);
+          uint32_t c0 = v.off + (uint32_t)pixel;
+          U4 u = philox(c0, (uint32_t)s, 0u, 0u, key.k0, key.k1);
+          d = cam_dir(v, (float)x + unif(u.x), (float)y + unif(u.y));
+          o = v.eye;
+          ct = make_int4((int)c0, s, 0, 0);
+          ok = true;
+        } else {
+          long long k = local >> 1;
+          EdgeSample es = edge_sample(c, sg.view, v, k, key);
+          if (es.valid) {
+            float sg2 = (local & 1) ? EDGE_EPS : -EDGE_EPS;
+            d = cam_dir(v, es.S.x + sg2 * es.ns.x, es.S.y + sg2 * es.ns.y);
+            o = v.eye;
+            ct = make_int4((int)(uint32_t)k, (int)v.off, 2, 1);
+            ok = true;
+          }
+        }
+      }
+    }
+    E.rad[i] = make_float4(0, 0, 0, 0);
+    if (E.records) {
+      E.nb[i] = 0;
+      E.esc[i] = make_float4(0, 0, 0, 0);
+      E.r1[i] = make_float4(d.x, d.y, d.z, 0.0f);
+    }
+    if (ok) {
+      E.o[i] = make_float4(o.x, o.y, o.z, 0.0f);
+      E.d[i] = make_float4(d.x, d.y, d.z, 0.0f);
+      E.thr[i] = make_float4(1, 1, 1, 0);
+      E.origin[i] = -1;
+      E.ctr[i] = ct;
+    }
+  }
+  int q = warp_append(&E.cnt[CNT_EXT + 0], ok);
+  if (ok) E.q0[q] = i;
+  unsigned m = __ballot_sync(FULL, ok);
+  if ((threadIdx.x & 31) == 0 && m) atomicAdd(&E.stat[STAT_PATHS], (unsigned long long)__popc(m));
+}
+
+// persistent fetch: a warp takes 32 consecutive queue entries per step
+#define ST_WARP_LOOP(total_expr, fetch_ptr)                                      \
+  const int lane_ = threadIdx.x & 31;                                          \
+  const int total_ = (total_expr);                                             \
+  for (;;) {                                                                   \
+    int base_ = 0;                                                             \
+    if (lane_ == 0) base_ = atomicAdd((fetch_ptr), 32);                        \
+    base_ = __shfl_sync(FULL, base_, 0);                                       \
+    if (base_ >= total_) break;                                                \
+    const int qi_ = base_ + lane_;                                             \
+    const bool live_ = qi_ < total_;
+
+#define ST_WARP_LOOP_END }
+
+template <bool STATS>
+__global__ void __launch_bounds__(EXT_BLOCK) k_extend(KCtx c, int b) {
+  __shared__ int sstack[TRACE_SH * EXT_BLOCK];
+  const Engine& E = c.e;
+  const int* q = (b & 1) ? E.q1 : E.q0;
+  TraceStats ts{0, 0};
+  ST_WARP_LOOP(E.cnt[CNT_EXT + b], &E.cnt[CNT_EXT_FETCH + b])
+  if (live_) {
+    int slot = q[qi_];
+    float4 o = E.o[slot], d = E.d[slot];
+    float t;
+    int f = trace_bvh<false, STATS>(c.nodes, c.tri, c.nf, xyz(o), xyz(d), __int_as_float(0x7f800000), E.origin[slot],
+                                    t, sstack + threadIdx.x, c.err, &ts);
+    E.hit[slot] = make_int2(f, __float_as_int(t));
+  }
+  ST_WARP_LOOP_END
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&E.stat[STAT_EXT], (unsigned long long)E.cnt[CNT_EXT + b]);
+  if (STATS) {
+    for (int off = 16; off > 0; off >>= 1) {
+      ts.visits += __shfl_xor_sync(FULL, ts.visits, off);
+      ts.tests += __shfl_xor_sync(FULL, ts.tests, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(&E.stat[STAT_VISITS], (unsigned long long)ts.visits);
+      atomicAdd(&E.stat[STAT_TESTS], (unsigned long long)ts.tests);
+    }
+  }
+}
+
+__global__ void k_shade(KCtx c, int b) {
+  const Engine& E = c.e;
+  const int* qin = (b & 1) ? E.q1 : E.q0;
+  int* qout = (b & 1) ? E.q0 : E.q1;
+  const size_t Q = (size_t)E.Q;
+  Key key{c.args->k0, c.args->k1};
+  ST_WARP_LOOP(E.cnt[CNT_EXT + b], &E.cnt[CNT_SHADE_FETCH + b])
+  bool sh_any = false, cont = false;
+  int slot = live_ ? qin[qi_] : 0;
+  if (live_) {
+    int2 h = E.hit[slot];
+    float4 o4 = E.o[slot], d4 = E.d[slot];
+    float3 dir = xyz(d4);
+    float3 T = xyz(E.thr[slot]);
+    if (h.x < 0) {
+      if (c.env.w > 0) {
+        float st_;
+        int tx = env_texel(c.env, dir, st_);
+        float4 te = __ldg(&c.env.tex[tx]);
+        float w = 1.0f;
+        if (b > 0) {
+          float pe = env_pdf(c.env, te.w, st_);
+          float lp = d4.w;
+          w = lp * lp / (lp * lp + pe * pe);
+        }
+        float3 Lw = mk3(te.x, te.y, te.z) * w;
+        float4 r = E.rad[slot];
+        E.rad[slot] = make_float4(r.x + T.x * Lw.x, r.y + T.y * Lw.y, r.z + T.z * Lw.z, 0.0f);
+        if (E.records && b > 0) E.esc[slot] = make_float4(Lw.x, Lw.y, Lw.z, 1.0f);
+      }
+    } else {
+      int f = h.x;
+      float t = __int_as_float(h.y);
+      float3 p = xyz(o4) + dir * t;
+      int ia = c.F[3 * f], ib = c.F[3 * f + 1], ic = c.F[3 * f + 2];
+      float3 v0 = fetch_vertex(c.V, ia), v1 = fetch_vertex(c.V, ib), v2 = fetch_vertex(c.V, ic);
+      float3 ng = norm3(cross3(v1 - v0, v2 - v0));
+      float3 wo = -dir;
+      float3 n = dot3(ng, wo) < 0.0f ? -ng : ng;
+      Mat m = fetch_mat(c.P, f);
+      if (E.records) {
+        E.r0[b * Q + slot] = make_float4(p.x, p.y, p.z, __int_as_float(f));
+        E.nb[slot] = b + 1;
+      }
+      for (int j = 0; j < c.nl; ++j) {
+        float4 lp = __ldg(&c.lights[2 * j]), li = __ldg(&c.lights[2 * j + 1]);
+        float3 dv = xyz(lp) - p;
+        float dist = len3(dv);
+        float3 wi = dv * (1.0f / dist);
+        float ci = dot3(n, wi);
+        bool valid = ci > 0.0f && dist > 2.0f * T_EPS;
+        float3 cc = mk3(0, 0, 0);
+        if (valid) cc = mul(mul(T, brdf_cos(c.brdf, m, n, wi, wo)), xyz(li)) * (1.0f / (dist * dist));
+        E.sh_dir[j * Q + slot] = make_float4(wi.x, wi.y, wi.z, dist - T_EPS);
+        E.sh_c[j * Q + slot] = make_float4(cc.x, cc.y, cc.z, valid ? 1.0f : 0.0f);
+        sh_any |= valid;
+      }
+      int flags = 0;
+      float3 ewi = mk3(0, 0, 0), escale = mk3(0, 0, 0);
+      if (c.env.w > 0) {
+        U4 u = philox((uint32_t)E.ctr[slot].x, (uint32_t)E.ctr[slot].y, (uint32_t)(b << 4) | 1u,
+                      (uint32_t)E.ctr[slot].z, key.k0, key.k1);
+        int tx = env_pick(c.env, u.x, u.y);
+        int row = tx / c.env.w, col = tx - row * c.env.w;
+        float uu = ((float)col + unif(u.z)) / (float)c.env.w, vq = ((float)row + unif(u.w)) / (float)c.env.h;
+        float sth, cth, sph, cph;
+        sincosf(PI_F * vq, &sth, &cth);
+        sincosf(2.0f * PI_F * uu, &sph, &cph);
+        ewi = mk3(-sth * sph, cth, sth * cph);
+        bool valid = sth > 0.0f && dot3(n, ewi) > 0.0f;
+        float3 cc = mk3(0, 0, 0);
+        if (valid) {
+          float4 te = __ldg(&c.env.tex[tx]);
+          float pe = env_pdf(c.env, te.w, sth);
+          float w = 1.0f;
+          if (b < c.B - 1) {
+            float pb = brdf_pdf(c.brdf, m, n, ewi, wo);
+            w = pe * pe / (pe * pe + pb * pb);
+          }
+          escale = mk3(te.x, te.y, te.z) * (w / pe);
+          cc = mul(mul(T, brdf_cos(c.brdf, m, n, ewi, wo)), escale);
+          flags |= ENV_VALID;
+        }
+        E.sh_dir[c.nl * Q + slot] = make_float4(ewi.x, ewi.y, ewi.z, __int_as_float(0x7f800000));
+        E.sh_c[c.nl * Q + slot] = make_float4(cc.x, cc.y, cc.z, valid ? 1.0f : 0.0f);
+        sh_any |= valid;
+      }
+      if (E.records) {
+        E.r2[b * Q + slot] = make_float4(ewi.x, ewi.y, ewi.z, __int_as_float(flags));
+        E.r3[b * Q + slot] = make_float4(escale.x, escale.y, escale.z, 0.0f);
+      }
+      E.o[slot] = make_float4(p.x, p.y, p.z, 0.0f);
+      if (b < c.B - 1) {
+        U4 u = philox((uint32_t)E.ctr[slot].x, (uint32_t)E.ctr[slot].y, (uint32_t)(b << 4) | 2u,
+                      (uint32_t)E.ctr[slot].z, key.k0, key.k1);
+        float3 wi;
+        float pdf = brdf_sample(c.brdf, m, n, wo, unif(u.x), unif(u.y), unif(u.z), wi);
+        if (pdf > 0.0f) {
+          float3 Qv = brdf_cos(c.brdf, m, n, wi, wo);
+          T = mul(T, Qv) * (1.0f / pdf);
+          E.thr[slot] = make_float4(T.x, T.y, T.z, 0.0f);
+          E.d[slot] = make_float4(wi.x, wi.y, wi.z, pdf);
+          E.origin[slot] = f;
+          if (E.records) E.r1[(b + 1) * Q + slot] = make_float4(wi.x, wi.y, wi.z, pdf);
+          cont = true;
+        }
+      }
+    }
+  }
+  int qs = warp_append(&E.cnt[CNT_SH + b], sh_any);
+  if (sh_any) E.qs[qs] = slot;
+  int qn = warp_append(&E.cnt[CNT_EXT + b + 1], cont);
+  if (cont) qout[qn] = slot;
+  ST_WARP_LOOP_END
+}
+
+__global__ void __launch_bounds__(EXT_BLOCK) k_shadow(KCtx c, int b) {
+  __shared__ int sstack[TRACE_SH * EXT_BLOCK];
+  const Engine& E = c.e;
+  const size_t Q = (size_t)E.Q;
+  int traced = 0;
+  ST_WARP_LOOP(E.cnt[CNT_SH + b], &E.cnt[CNT_SH_FETCH + b])
+  if (live_) {
+    int slot = E.qs[qi_];
+    float3 p = xyz(E.o[slot]);
+    int exclude = E.hit[slot].x;
+    float3 L = mk3(0, 0, 0);
+    int vis = 0;
+    for (int k = 0; k < c.NS; ++k) {
+      float4 sc = E.sh_c[k * Q + slot];
+      if (sc.w == 0.0f) continue;
+      float4 sd = E.sh_dir[k * Q + slot];
+      float t;
+      ++traced;
+      int hf = trace_bvh<true, false>(c.nodes, c.tri, c.nf, p, xyz(sd), sd.w, exclude, t, sstack + threadIdx.x, c.err,
+                                      nullptr);
+      if (hf < 0) {
+        L += xyz(sc);
+        vis |= (k < c.nl) ? (1 << k) : ENV_VIS;
+      }
+    }
+    float4 r = E.rad[slot];
+    E.rad[slot] = make_float4(r.x + L.x, r.y + L.y, r.z + L.z, 0.0f);
+    if (E.records && vis) {
+      float4 r2 = E.r2[b * Q + slot];
+      E.r2[b * Q + slot] = make_float4(r2.x, r2.y, r2.z, __int_as_float(__float_as_int(r2.w) | vis));
+    }
+  }
+  ST_WARP_LOOP_END
+  for (int off = 16; off > 0; off >>= 1) traced += __shfl_xor_sync(FULL, traced, off);
+  if ((threadIdx.x & 31) == 0 && traced) atomicAdd(&E.stat[STAT_SHADOW], (unsigned long long)traced);
+}
+
+// image[pixel] accumulates its samples in sample order, so the result does not
+// depend on where chunk boundaries fall
+__global__ void k_resolve(KCtx c, long long j0, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  long long job = j0 + i;
+  int si = find_seg(c.segs, c.n_segs, job);
+  if (si < 0) return;
+  Seg sg = c.segs[si];
+  long long local = job - sg.base;
+  if (sg.kind != 0 || local >= sg.count) return;
+  DevView v = c.views[sg.view];
+  long long pixel = local / v.spp;
+  int s = (int)(local - pixel * v.spp);
+  if (s != 0 && i != 0) return;
+  float* img = c.args->image + 3 * (v.pix_off + pixel);
+  float3 acc = mk3(img[0], img[1], img[2]);
+  float inv = 1.0f / (float)v.spp;
+  for (int k = i; s < v.spp && k < n; ++k, ++s) acc += xyz(c.e.rad[k]) * inv;
+  img[0] = acc.x; img[1] = acc.y; img[2] = acc.z;
+}
+
+// ------------------------------------------------------------------ gradient scatter
+// Lanes holding values for the same key are summed by the lowest such lane
+// (peers found with match.any), which then issues the atomics.
+template <int NV>
+__device__ __forceinline__ void warp_reduce_peers(int key, float (&vals)[NV], float* scratch, bool& leader) {
+  int lane = threadIdx.x & 31;
+  unsigned peers = __match_any_sync(FULL, key);
+#pragma unroll
+  for (int k = 0; k < NV; ++k) scratch[lane * (NV + 1) + k] = vals[k];
+  __syncwarp();
+  leader = key >= 0 && lane == __ffs(peers) - 1;
+  if (leader) {
+    unsigned rest = peers & ~(1u << lane);
+    while (rest) {
+      int l = __ffs(rest) - 1;
+      rest &= rest - 1;
+#pragma unroll
+      for (int k = 0; k < NV; ++k) vals[k] += scratch[l * (NV + 1) + k];
+    }
+  }
+  __syncwarp();
+}
+
+constexpr int ADJ_BLOCK = 128;
+
+__global__ void __launch_bounds__(ADJ_BLOCK) k_adjoint(KCtx c, long long j0, int n) {
+  __shared__ float scratch[ADJ_BLOCK / 32][32 * 15];
+  float* scr = scratch[threadIdx.x >> 5];
+  const Engine& E = c.e;
+  const size_t Q = (size_t)E.Q;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  float* dV = c.args->dV;
+  float* dF = c.args->dF;
+  int nbv = 0;
+  float3 g = mk3(0, 0, 0);
+  if (i < n) {
+    long long job = j0 + i;
+    int si = find_seg(c.segs, c.n_segs, job);
+    if (si >= 0) {
+      Seg sg = c.segs[si];
+      long long local = job - sg.base;
+      if (sg.kind == 0 && local < sg.count) {
+        DevView v = c.views[sg.view];
+        long long pixel = local / v.spp;
+        const float* gp = c.args->dLdI + 3 * (v.pix_off + pixel);
+        float inv = 1.0f / (float)v.spp;
+        g = mk3(gp[0] * inv, gp[1] * inv, gp[2] * inv);
+        if (g.x != 0.0f || g.y != 0.0f || g.z != 0.0f) nbv = E.nb[i];
+      }
+    }
+  }
+  // forward sweep: throughput before each vertex
+  float3 T[MAX_B];
+  T[0] = mk3(1, 1, 1);
+  for (int b = 0; b + 1 < nbv; ++b) {
+    float4 r0 = E.r0[b * Q + i], r1 = E.r1[b * Q + i], r1n = E.r1[(b + 1) * Q + i];
+    int f = __float_as_int(r0.w);
+    float3 v0 = fetch_vertex(c.V, c.F[3 * f]), v1 = fetch_vertex(c.V, c.F[3 * f + 1]),
+           v2 = fetch_vertex(c.V, c.F[3 * f + 2]);
+    float3 wo = -xyz(r1);
+    float3 ng = norm3(cross3(v1 - v0, v2 - v0));
+    float3 nn = dot3(ng, wo) < 0.0f ? -ng : ng;
+    float3 Qv = brdf_cos(c.brdf, fetch_mat(c.P, f), nn, xyz(r1n), wo);
+    T[b + 1] = mul(T[b], Qv) * (1.0f / r1n.w);
+  }
+  bool esc = nbv > 0 && E.esc[i].w != 0.0f;
+  float3 A = mk3(0, 0, 0);
+  if (esc) A = mul(g, xyz(E.esc[i]));
+  float3 Pnext = mk3(0, 0, 0);
+  for (int b = c.B - 1; b >= 0; --b) {
+    float vals[14];
+#pragma unroll
+    for (int k = 0; k < 14; ++k) vals[k] = 0.0f;
+    int face = -1;
+    if (b < nbv) {
+      float4 r0 = E.r0[b * Q + i], r1 = E.r1[b * Q + i], r2 = E.r2[b * Q + i], r3 = E.r3[b * Q + i];
+      int f = __float_as_int(r0.w);
+      face = f;
+      float3 p = xyz(r0), d = xyz(r1), wo = -d;
+      float3 v0 = fetch_vertex(c.V, c.F[3 * f]), v1 = fetch_vertex(c.V, c.F[3 * f + 1]),
+             v2 = fetch_vertex(c.V, c.F[3 * f + 2]);
+      float3 e1 = v1 - v0, e2 = v2 - v0;
+      float3 mv = cross3(e1, e2);
+      float ml = len3(mv);
+      float3 mh = mv * (1.0f / ml);
+      float sgn = dot3(mh, wo) < 0.0f ? -1.0f : 1.0f;
+      float3 nn = mh * sgn;
+      Mat m = fetch_mat(c.P, f);
+      float3 Nb = mk3(0, 0, 0), Pb = Pnext;
+      float dm[5] = {0, 0, 0, 0, 0};
+      float3 gC = mul(g, T[b]);
+      float3 C = mk3(0, 0, 0);
+      int flags = __float_as_int(r2.w);
+      for (int j = 0; j < c.nl; ++j) {
+        if (!(flags & (1 << j))) continue;
+        float4 lp = __ldg(&c.lights[2 * j]), li = __ldg(&c.lights[2 * j + 1]);
+        float3 l = xyz(lp) - p;
+        float r = len3(l);
+        float3 wi = l * (1.0f / r);
+        float ir2 = 1.0f / (r * r);
+        float3 Qv = brdf_cos(c.brdf, m, nn, wi, wo);
+        C += mul(Qv, xyz(li)) * ir2;
+        float3 gw = mul(gC, xyz(li)) * ir2;
+        float3 dwi = mk3(0, 0, 0);
+        brdf_cos_adj(c.brdf, m, nn, wi, wo, gw, Nb, &dwi, dm);
+        float sr = gC.x * Qv.x * li.x + gC.y * Qv.y * li.y + gC.z * Qv.z * li.z;
+        float rbar = sr * (-2.0f * ir2 / r);
+        float3 lbar = (dwi - wi * dot3(dwi, wi)) * (1.0f / r) + wi * rbar;
+        Pb -= lbar;
+      }
+      if (flags & ENV_VIS) {
+        float3 wi = xyz(r2), sc = xyz(r3);
+        C += mul(brdf_cos(c.brdf, m, nn, wi, wo), sc);
+        brdf_cos_adj(c.brdf, m, nn, wi, wo, mul(gC, sc), Nb, nullptr, dm);
+      }
+      float3 w = mk3(0, 0, 0);
+      if (b + 1 < nbv || esc) {
+        float4 r1n = E.r1[(b + 1) * Q + i];
+        float ip = 1.0f / r1n.w;
+        float3 wi = xyz(r1n);
+        w = brdf_cos(c.brdf, m, nn, wi, wo) * ip;
+        brdf_cos_adj(c.brdf, m, nn, wi, wo, mul(A, T[b]) * ip, Nb, nullptr, dm);
+      }
+      A = mul(g, C) + mul(A, w);
+      // n = sgn * m / |m|, p = o + t d with t = ((v0 - o) . m) / (d . m)
+      float3 mbar = (Nb - mh * dot3(Nb, mh)) * (sgn / ml);
+      float dmv = dot3(d, mv);
+      float tb = dot3(Pb, d) / dmv;
+      float3 obar = Pb - mv * tb;
+      float3 v0bar = mv * tb;
+      mbar += (v0 - p) * tb;
+      float3 e1bar = cross3(e2, mbar), e2bar = cross3(mbar, e1);
+      v0bar -= e1bar + e2bar;
+      Pnext = obar;
+      vals[0] = v0bar.x; vals[1] = v0bar.y; vals[2] = v0bar.z;
+      vals[3] = e1bar.x; vals[4] = e1bar.y; vals[5] = e1bar.z;
+      vals[6] = e2bar.x; vals[7] = e2bar.y; vals[8] = e2bar.z;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) vals[9 + k] = dm[k];
+    }
+    bool leader;
+    warp_reduce_peers<14>(face, vals, scr, leader);
+    if (leader) {
+      if (dV) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          int vid = c.F[3 * face + k];
+          atomicAdd(&dV[3 * vid], vals[3 * k]);
+          atomicAdd(&dV[3 * vid + 1], vals[3 * k + 1]);
+          atomicAdd(&dV[3 * vid + 2], vals[3 * k + 2]);
+        }
+      }
+      if (dF) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) atomicAdd(&dF[5 * face + k], vals[9 + k]);
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(ADJ_BLOCK) k_edge_resolve(KCtx c, long long j0, int n) {
+  __shared__ float scratch[ADJ_BLOCK / 32][32 * 7];
+  float* scr = scratch[threadIdx.x >> 5];
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  float vals[6] = {0, 0, 0, 0, 0, 0};
+  int key = -1, va = 0, vb = 0;
+  if (i < n && (i & 1) == 0) {
+    long long job = j0 + i;
+    int si = find_seg(c.segs, c.n_segs, job);
+    if (si >= 0) {
+      Seg sg = c.segs[si];
+      long long local = job - sg.base;
+      if (sg.kind == 1 && local < sg.count) {
+        DevView v = c.views[sg.view];
+        Key kk{c.args->k0, c.args->k1};
+        EdgeSample es = edge_sample(c, sg.view, v, local >> 1, kk);
+        if (es.valid) {
+          const float* gp = c.args->dLdI + 3 * (v.pix_off + (long long)es.py * v.W + es.px);
+          float3 Lm = xyz(c.e.rad[i]), Lp = xyz(c.e.rad[i + 1]);
+          float gsum = gp[0] * (Lm.x - Lp.x) + gp[1] * (Lm.y - Lp.y) + gp[2] * (Lm.z - Lp.z);
+          if (gsum != 0.0f) {
+            float wt = gsum * (float)c.edge_ncand[sg.view] * es.len / (float)sg.n_samples;
+            int2 ev = c.edge_v[es.e];
+            float3 ja = cam_project_jt(v, fetch_vertex(c.V, ev.x), es.ns.x, es.ns.y) * (wt * (1.0f - es.tau));
+            float3 jb = cam_project_jt(v, fetch_vertex(c.V, ev.y), es.ns.x, es.ns.y) * (wt * es.tau);
+            vals[0] = ja.x; vals[1] = ja.y; vals[2] = ja.z;
+            vals[3] = jb.x; vals[4] = jb.y; vals[5] = jb.z;
+            key = es.e;
+            va = ev.x;
+            vb = ev.y;
+          }
+        }
+      }
+    }
+  }
+  bool leader;
+  warp_reduce_peers<6>(key, vals, scr, leader);
+  if (leader) {
+    float* dV = c.args->dV;
+    atomicAdd(&dV[3 * va], vals[0]); atomicAdd(&dV[3 * va + 1], vals[1]); atomicAdd(&dV[3 * va + 2], vals[2]);
+    atomicAdd(&dV[3 * vb], vals[3]); atomicAdd(&dV[3 * vb + 1], vals[4]); atomicAdd(&dV[3 * vb + 2], vals[5]);
+  }
+}
+
+// closest-hit queries for st_trace_closest
+__global__ void __launch_bounds__(EXT_BLOCK) k_trace_rays(const float4* nodes, const float4* tri, int nf,
+                                                          const float4* rays, int n, int exclude, int* out_tri,
+                                                          float* out_t, int* err) {
+  __shared__ int sstack[TRACE_SH * EXT_BLOCK];
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float4 a = rays[2 * i], b = rays[2 * i + 1];
+  float t;
+  int f = trace_bvh<false, false>(nodes, tri, nf, xyz(a), xyz(b), b.w, exclude, t, sstack + threadIdx.x, err, nullptr);
+  out_tri[i] = f;
+  out_t[i] = f >= 0 ? t : __int_as_float(0x7f800000);
+}
+
+}  // namespace st

@@ -1,0 +1,263 @@
+"""Thin Python binding of libst (argument marshalling only).
+
+Every step of the forward and adjoint path trace runs in the CUDA library
+declared by ``include/st.h``; this module only converts torch tensors and
+Python objects into the C structures and raw pointers that library takes. There
+is no CPU fallback: if ``libst.so`` is missing or cannot be loaded the import of
+the library fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libst.so")
+
+ST_OK = 0
+STATUS = {0: "ST_OK", 1: "ST_ERR_INVALID_ARG", 2: "ST_ERR_OOM", 3: "ST_ERR_CUDA", 4: "ST_ERR_TIMEOUT",
+          5: "ST_ERR_STATE", 6: "ST_ERR_UNSUPPORTED", 7: "ST_ERR_DEVICE"}
+MODE_BATCHED, MODE_PER_VIEW = 0, 1
+EDGE_SILHOUETTE, EDGE_ALL = 0, 1
+
+EXPORTED = ["st_scene_create", "st_scene_destroy", "st_refit", "st_rebuild", "st_set_face_params", "st_render",
+            "st_render_backward", "st_trace_closest", "st_get_stats", "st_debug_bvh", "st_last_error"]
+
+
+class StError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class PointLight(C.Structure):
+    _fields_ = [("pos", C.c_float * 3), ("intensity", C.c_float * 3)]
+
+
+class EnvMap(C.Structure):
+    _fields_ = [("width", C.c_int), ("height", C.c_int), ("rgb", C.c_void_p)]
+
+
+class View(C.Structure):
+    _fields_ = [("eye", C.c_float * 3), ("target", C.c_float * 3), ("up", C.c_float * 3), ("fov_y_deg", C.c_float),
+                ("width", C.c_int), ("height", C.c_int), ("spp", C.c_int), ("pixel_offset", C.c_longlong)]
+
+
+class SceneDesc(C.Structure):
+    _fields_ = [("n_vertices", C.c_int), ("n_faces", C.c_int), ("vertices", C.c_void_p), ("faces", C.c_void_p),
+                ("face_params", C.c_void_p), ("brdf", C.c_int), ("n_point_lights", C.c_int),
+                ("point_lights", C.c_void_p), ("env", C.c_void_p)]
+
+
+class RenderOpts(C.Structure):
+    _fields_ = [("edge_term", C.c_int), ("edge_mode", C.c_int), ("edge_spp", C.c_int), ("mode", C.c_int),
+                ("use_graph", C.c_int), ("chunk_paths", C.c_int), ("time_kernels", C.c_int),
+                ("count_visits", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("paths", C.c_longlong), ("extension_rays", C.c_longlong), ("shadow_rays", C.c_longlong),
+                ("edge_samples", C.c_longlong), ("node_visits", C.c_longlong), ("tri_tests", C.c_longlong),
+                ("extend_launches", C.c_int), ("extend_ms", C.c_double), ("device_error", C.c_int),
+                ("bvh_nodes", C.c_int), ("scratch_bytes", C.c_longlong)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libst.so (built by ``paper_2012_03939_gb300.build``); raise if it is absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libst.so is not built (run paper_2012_03939_gb300.build.build()); "
+                              "there is no fallback path")
+        L = C.CDLL(LIB_PATH)
+        P, I, U = C.c_void_p, C.c_int, C.c_ulonglong
+        L.st_scene_create.argtypes = [P, P, P]
+        L.st_scene_destroy.argtypes = [P]
+        L.st_refit.argtypes = [P, P, P]
+        L.st_rebuild.argtypes = [P, P, P]
+        L.st_set_face_params.argtypes = [P, P, P]
+        L.st_render.argtypes = [P, P, I, I, I, U, P, P, P]
+        L.st_render_backward.argtypes = [P, P, I, I, I, U, P, P, P, P, P]
+        L.st_trace_closest.argtypes = [P, P, I, I, P, P, P]
+        L.st_get_stats.argtypes = [P, P]
+        L.st_debug_bvh.argtypes = [P, P, P]
+        L.st_last_error.restype = C.c_char_p
+        L.st_last_error.argtypes = []
+        for name in EXPORTED[:-1]:
+            getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != ST_OK:
+        raise StError(status, lib().st_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def make_views(views, default_spp=0):
+    """ctypes array of View from ``scenes.View`` objects (or View structures)."""
+    arr = (View * len(views))()
+    for i, v in enumerate(views):
+        if isinstance(v, View):
+            arr[i] = v
+        else:
+            arr[i] = View((C.c_float * 3)(*v.eye), (C.c_float * 3)(*v.target), (C.c_float * 3)(*v.up),
+                          v.fov_y_deg, v.width, v.height, v.spp, v.pixel_offset)
+    return arr
+
+
+def n_pixels(views) -> int:
+    return int(max(v.pixel_offset + v.width * v.height for v in views))
+
+
+def make_opts(**kw) -> RenderOpts:
+    o = RenderOpts(0, EDGE_SILHOUETTE, 0, MODE_BATCHED, 1, 0, 0, 0)
+    for k, v in kw.items():
+        if k == "mode" and isinstance(v, str):
+            v = {"batched": MODE_BATCHED, "per_view": MODE_PER_VIEW}[v]
+        if k == "edge_mode" and isinstance(v, str):
+            v = {"silhouette": EDGE_SILHOUETTE, "all": EDGE_ALL}[v]
+        setattr(o, k, int(v))
+    return o
+
+
+class Scene:
+    """A mesh scene on the current CUDA device (owns a library scene handle)."""
+
+    def __init__(self, vertices: torch.Tensor, faces: torch.Tensor, face_params: torch.Tensor, brdf: str = "ggx",
+                 light_pos=None, light_intensity=None, env: Optional[np.ndarray] = None, stream=None):
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.vertices = vertices.detach().to(dev, torch.float32).contiguous()
+        self.faces = faces.detach().to(dev, torch.int32).contiguous()
+        self.face_params = face_params.detach().to(dev, torch.float32).contiguous()
+        self.nv, self.nf = self.vertices.shape[0], self.faces.shape[0]
+        lp = np.zeros((0, 3), np.float32) if light_pos is None else np.asarray(light_pos, np.float32).reshape(-1, 3)
+        li = np.zeros((0, 3), np.float32) if light_intensity is None else np.asarray(light_intensity,
+                                                                                    np.float32).reshape(-1, 3)
+        self._lights = (PointLight * max(len(lp), 1))()
+        for j in range(len(lp)):
+            self._lights[j] = PointLight((C.c_float * 3)(*lp[j]), (C.c_float * 3)(*li[j]))
+        self._env_arr = None if env is None else np.ascontiguousarray(env, np.float32)
+        self._env = None
+        if self._env_arr is not None:
+            self._env = EnvMap(self._env_arr.shape[1], self._env_arr.shape[0], self._env_arr.ctypes.data)
+        desc = SceneDesc(self.nv, self.nf, self.vertices.data_ptr(), self.faces.data_ptr(),
+                         self.face_params.data_ptr(), {"ggx": 0, "beckmann": 1}[brdf], len(lp),
+                         C.addressof(self._lights), None if self._env is None else C.addressof(self._env))
+        h = C.c_void_p()
+        _check(lib().st_scene_create(C.byref(desc), _stream(stream), C.byref(h)))
+        self.handle = h
+
+    @classmethod
+    def from_scene(cls, sc, vertices=None, device="cuda"):
+        V = torch.as_tensor(sc.vertices if vertices is None else vertices, dtype=torch.float32, device=device)
+        return cls(V, torch.as_tensor(sc.faces, device=device), torch.as_tensor(sc.face_params, device=device),
+                   sc.brdf, sc.light_pos, sc.light_intensity, sc.env)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().st_scene_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def refit(self, vertices: torch.Tensor, stream=None):
+        v = vertices.detach().to(torch.float32).contiguous()
+        _check(lib().st_refit(self.handle, v.data_ptr(), _stream(stream)))
+        self.vertices.copy_(v)
+
+    def rebuild(self, vertices: torch.Tensor, stream=None):
+        v = vertices.detach().to(torch.float32).contiguous()
+        _check(lib().st_rebuild(self.handle, v.data_ptr(), _stream(stream)))
+        self.vertices.copy_(v)
+
+    def set_face_params(self, p: torch.Tensor, stream=None):
+        p = p.detach().to(torch.float32).contiguous()
+        _check(lib().st_set_face_params(self.handle, p.data_ptr(), _stream(stream)))
+        self.face_params.copy_(p)
+
+    def render(self, views, max_bounces: int, seed: int, opts: Optional[RenderOpts] = None, out=None,
+               default_spp: int = 0, stream=None) -> torch.Tensor:
+        vs = make_views(views)
+        if out is None:
+            out = torch.zeros((n_pixels(views), 3), dtype=torch.float32, device=self.vertices.device)
+        _check(lib().st_render(self.handle, vs, len(vs), default_spp, max_bounces, seed,
+                               None if opts is None else C.byref(opts), out.data_ptr(), _stream(stream)))
+        return out
+
+    def backward(self, views, max_bounces: int, seed: int, dLdI: torch.Tensor, opts: Optional[RenderOpts] = None,
+                 d_vertices=None, d_face_params=None, want_vertices=True, want_params=True, default_spp: int = 0,
+                 stream=None):
+        vs = make_views(views)
+        dLdI = dLdI.detach().to(torch.float32).contiguous()
+        if want_vertices and d_vertices is None:
+            d_vertices = torch.zeros((self.nv, 3), dtype=torch.float32, device=dLdI.device)
+        if want_params and d_face_params is None:
+            d_face_params = torch.zeros((self.nf, 5), dtype=torch.float32, device=dLdI.device)
+        _check(lib().st_render_backward(self.handle, vs, len(vs), default_spp, max_bounces, seed,
+                                        None if opts is None else C.byref(opts), dLdI.data_ptr(),
+                                        None if d_vertices is None else d_vertices.data_ptr(),
+                                        None if d_face_params is None else d_face_params.data_ptr(),
+                                        _stream(stream)))
+        return d_vertices, d_face_params
+
+    def trace_closest(self, rays: torch.Tensor, exclude: int = -1, stream=None):
+        rays = rays.detach().to(torch.float32).contiguous()
+        n = rays.shape[0]
+        tri = torch.empty(n, dtype=torch.int32, device=rays.device)
+        t = torch.empty(n, dtype=torch.float32, device=rays.device)
+        _check(lib().st_trace_closest(self.handle, rays.data_ptr(), n, exclude, tri.data_ptr(), t.data_ptr(),
+                                      _stream(stream)))
+        return tri, t
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(lib().st_get_stats(self.handle, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+    def debug_bvh(self):
+        nodes = np.zeros((max(self.nf - 1, 1), 16), np.float32)
+        leaf = np.zeros(self.nf, np.int32)
+        _check(lib().st_debug_bvh(self.handle, nodes.ctypes.data, leaf.ctypes.data))
+        return nodes[: self.nf - 1], leaf
+
+
+class STRender(torch.autograd.Function):
+    """images = R(vertices, face_params; views). Backward replays the forward's seed (path replay)."""
+
+    @staticmethod
+    def forward(ctx, vertices, face_params, scene: Scene, views, max_bounces: int, seed: int,
+                opts: Optional[RenderOpts] = None, bwd_opts: Optional[RenderOpts] = None):
+        scene.refit(vertices)
+        scene.set_face_params(face_params)
+        img = scene.render(views, max_bounces, seed, opts)
+        ctx.scene, ctx.views, ctx.B, ctx.seed, ctx.bwd_opts = scene, views, max_bounces, seed, bwd_opts
+        ctx.needs = (ctx.needs_input_grad[0], ctx.needs_input_grad[1])
+        return img
+
+    @staticmethod
+    def backward(ctx, gI):
+        dV, dF = ctx.scene.backward(ctx.views, ctx.B, ctx.seed, gI, ctx.bwd_opts, want_vertices=ctx.needs[0],
+                                    want_params=ctx.needs[1])
+        return dV, dF, None, None, None, None, None, None
+
+
+def render(vertices, face_params, scene: Scene, views, max_bounces: int, seed: int, opts=None, bwd_opts=None):
+    return STRender.apply(vertices, face_params, scene, views, max_bounces, seed, opts, bwd_opts)
