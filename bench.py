@@ -1,0 +1,397 @@
+#!/usr/bin/env python
+"""Throughput of the forward + adjoint path trace (path segments per second).
+
+One step = forward render of every view of the workload, the L2 image-loss
+gradient against a resident target, and the adjoint (path replay for the
+interior term plus silhouette edge sampling). A path segment is one BVH ray
+query (extension, shadow or edge-side). Default workload: 64 views of uneven
+resolution ({64,128,256,512}^2) and spp ({1,4,16}) of a 200,000-face displaced
+sphere under a 512x256 environment, 3 bounces, batched persistent launches
+replayed from CUDA graphs; the plain per-view launch path is timed beside it.
+
+Prints one JSON line (rank 0). ``--impl reference`` times the FP64 CPU oracle
+instead, on a bounded pixel sample of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "fwd+adjoint path segments/s (M/s), batched vs per-view, at grad rel err ≤1e-3"
+UNIT = "Mseg/s"
+WORKLOAD_DESC = ("batched uneven views: displaced UV sphere 200000 faces, per-face Torrance-Sparrow (GGX), "
+                 "env 512x256 lognormal(0,1.5), 64 Fibonacci-sphere views with W,H in {64,128,256,512} and spp in "
+                 "{1,4,16}, 3 bounces; forward + adjoint (interior replay + silhouette edge term)")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="batched")
+    ap.add_argument("--per-view-steps", type=int, default=0, help="0 = max(2, steps // 3)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--views", type=int, default=0, help="profiling: keep only the first N views")
+    ap.add_argument("--chunk", type=int, default=0, help="paths in flight per wavefront chunk (0 = library default)")
+    ap.add_argument("--profile", action="store_true",
+                    help="profiling driver: warm-up steps then one batched fwd+adjoint step, no JSON")
+    return ap.parse_args()
+
+
+def rank_info():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+# ---------------------------------------------------------------------------- CPU oracle leg
+def oracle_sample_rate(sc, seconds, seed=2024):
+    """Segments/s of the FP64 oracle (forward + interior gradient + edge term) on a pixel sample."""
+    import oracle as O
+    osc = O.OracleScene(sc)
+    rng = np.random.default_rng(seed)
+    npix = 4
+    cores = os.cpu_count() or 1
+    t_total, seg_total, pix_total = 0.0, 0, 0
+    while True:
+        vi = rng.integers(len(sc.views), size=npix)
+        pix = np.array([(v, rng.integers(sc.views[v].width), rng.integers(sc.views[v].height)) for v in vi], np.int32)
+        rows = O.pixel_index(sc, pix)
+        w = np.zeros((sc.n_pixels, 3))
+        w[rows] = rng.normal(size=(len(pix), 3))
+        prm = O.params(sc.max_bounces, seed, edge_mode=0, n_threads=cores)
+        t0 = time.perf_counter()
+        _, s1 = O.render_pixels(osc, prm, pix)
+        _, _, s2 = O.grad_pixels(osc, prm, pix, w[rows])
+        _, s3 = O.edge_grad(osc, prm, w)
+        dt = time.perf_counter() - t0
+        t_total += dt
+        seg_total += s1 + s2 + s3
+        pix_total += len(pix)
+        if t_total >= seconds:
+            break
+        npix = int(min(4096, max(npix * 2, npix * (seconds - t_total) / max(dt, 1e-3) * 0.5)))
+    return seg_total / t_total / 1e6, cores, pix_total, t_total
+
+
+def run_reference(args):
+    rank, world, _ = rank_info()
+    if rank != 0:
+        return
+    from paper_2012_03939_gb300 import scenes as S
+    import oracle as O
+    O.build()
+    sc = S.make(args.workload)
+    per_step = max(2.0, min(8.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_sample_rate(sc, per_step / 4)
+    rates, cores, pix = [], 0, 0
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        r, cores, p, _ = oracle_sample_rate(sc, per_step, seed=100 + k)
+        rates.append(r)
+        pix += p
+    wall = time.perf_counter() - t0
+    v = statistics.mean(rates)
+    sample = "%d sampled pixels over %d steps: forward + interior gradient + edge term, brute-force FP64" % (
+        pix, args.steps)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(v, 6), "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1000 * wall / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": round(v, 6), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(v, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+# ---------------------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------- ours
+def source_hash():
+    h = hashlib.sha256()
+    for f in ("st_trace.cuh", "st_kernels.cuh", "st_device.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2012_03939_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per closest-hit query from the committed ncu summary, if taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "extend_dram_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    kv = {}
+    for ln in open(p):
+        if "=" in ln and not ln.startswith("#"):
+            k, v = ln.split("=", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("source_hash") != source_hash():
+        return None
+    return float(kv["dram_bytes_per_ray"])
+
+
+def run_ours(args):
+    import torch
+    from paper_2012_03939_gb300 import build as Bld
+    from paper_2012_03939_gb300 import scenes as S
+    rank, world, local = rank_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        Bld.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2012_03939_gb300 import st
+
+    sc = S.make(args.workload)
+    if args.views:
+        sc = sc.subset_views(range(args.views))
+    B = sc.max_bounces
+    scene = st.Scene.from_scene(sc)
+    views = sc.views
+    N = sc.n_pixels
+    seed = 20240 + rank
+    # resident target: the same views rendered from a perturbed copy of the mesh
+    noisy = sc.vertices + np.random.default_rng(7).normal(0, 0.01, sc.vertices.shape).astype(np.float32)
+    tgt_scene = st.Scene.from_scene(sc, vertices=noisy)
+    target = tgt_scene.render(views, B, 99)
+    torch.cuda.synchronize()
+    tgt_scene.close()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    img = torch.zeros((N, 3), dtype=torch.float32, device="cuda")
+    dV = torch.zeros((scene.nv, 3), dtype=torch.float32, device="cuda")
+    dF = torch.zeros((scene.nf, 5), dtype=torch.float32, device="cuda")
+    inv_n = 1.0 / (3 * N)
+
+    def step(fopts, bopts):
+        scene.render(views, B, seed, fopts, out=img)
+        g = (img - target) * (2 * inv_n)
+        dV.zero_()
+        dF.zero_()
+        scene.backward(views, B, seed, g, bopts, d_vertices=dV, d_face_params=dF)
+
+    def counts(fopts, bopts):
+        scene.render(views, B, seed, fopts, out=img)
+        a = scene.stats()
+        g = (img - target) * (2 * inv_n)
+        scene.backward(views, B, seed, g, bopts, d_vertices=dV, d_face_params=dF)
+        b = scene.stats()
+        return a, b
+
+    def timed(fn, steps, warm):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in ev:
+            flush.fill_(1.0)            # evict L2 (256 MiB > 129 MB) between timed steps
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    fb = st.make_opts(mode="batched", use_graph=1, chunk_paths=args.chunk)
+    bb = st.make_opts(mode="batched", use_graph=1, edge_term=1, edge_mode=0, chunk_paths=args.chunk)
+    if args.profile:
+        for _ in range(args.warmup):
+            step(fb, bb)
+        torch.cuda.synchronize()
+        step(fb, bb)
+        torch.cuda.synchronize()
+        s = scene.stats()
+        print("profile step done: %d kernel launches in the last call, device_error %d" % (
+            s["kernel_launches"], s["device_error"]))
+        scene.close()
+        return
+    fp = st.make_opts(mode="per_view", use_graph=0)
+    bp = st.make_opts(mode="per_view", use_graph=0, edge_term=1, edge_mode=0)
+
+    sf, sb = counts(fb, bb)
+    seg_fwd = sf["extension_rays"] + sf["shadow_rays"]
+    seg_step = seg_fwd + sb["extension_rays"] + sb["shadow_rays"]
+    launches_step = sf["kernel_launches"] + sb["kernel_launches"]
+    assert sf["device_error"] == 0 and sb["device_error"] == 0
+
+    with ClockSampler(local) as clk:
+        ms = timed(lambda: step(fb, bb), args.steps, args.warmup)
+    value = seg_step * args.steps * world / (ms / 1000.0) / 1e6
+
+    pv_steps = args.per_view_steps or max(2, args.steps // 3)
+    ms_pv = timed(lambda: step(fp, bp), pv_steps, 1)
+    value_pv = seg_step * pv_steps * world / (ms_pv / 1000.0) / 1e6
+    ms_fwd = timed(lambda: scene.render(views, B, seed, fb, out=img), args.steps, 2)
+    value_fwd = seg_fwd * args.steps * world / (ms_fwd / 1000.0) / 1e6
+
+    # roofline of the dominant kernel (closest-hit traversal): algorithmic bytes
+    # from the instrumented traversal, time from CUDA events around each launch
+    ci = st.make_opts(mode="batched", use_graph=0, count_visits=1)
+    cib = st.make_opts(mode="batched", use_graph=0, count_visits=1, edge_term=1, edge_mode=0)
+    a, b = counts(ci, cib)
+    visits = a["node_visits"] + b["node_visits"]
+    tests = a["tri_tests"] + b["tri_tests"]
+    rays = a["extension_rays"] + b["extension_rays"]
+    ti = st.make_opts(mode="batched", use_graph=0, time_kernels=1)
+    tib = st.make_opts(mode="batched", use_graph=0, time_kernels=1, edge_term=1, edge_mode=0)
+    ext_ms, ext_n = 0.0, 0
+    for _ in range(3):
+        flush.fill_(1.0)
+        a, b = counts(ti, tib)
+        ext_ms += a["extend_ms"] + b["extend_ms"]
+        ext_n += a["extend_launches"] + b["extend_launches"]
+    # per query: node fetch 64 B, triangle record 48 B, ray in (o, d, origin, queue) 40 B, hit out 8 B
+    alg_bytes = visits * 64 + tests * 48 + rays * 48
+    achieved = alg_bytes * 3 / (ext_ms / 1000.0) / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = peaks.get("hbm_gbs", 6800.0)
+    tr = profiled_traffic()
+    roofline = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4),
+                "traffic": None if tr is None else round(tr * rays / max(1, ext_n // 3), 1),
+                "kernel": "k_extend (closest-hit BVH traversal)",
+                "launch_ms_avg": round(ext_ms / max(1, ext_n), 4),
+                "alg_bytes_per_ray": round(alg_bytes / max(rays, 1), 1),
+                "node_visits_per_ray": round(visits / max(rays, 1), 2),
+                "tri_tests_per_ray": round(tests / max(rays, 1), 2),
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback"}
+
+    # end to end through the C ABI with host buffers: H2D of the mesh state and
+    # D2H of the image and both gradients every step
+    hV = torch.from_numpy(sc.vertices.copy()).pin_memory()
+    hP = torch.from_numpy(sc.face_params.copy()).pin_memory()
+    oI = torch.empty((N, 3), dtype=torch.float32).pin_memory()
+    oV = torch.empty((scene.nv, 3), dtype=torch.float32).pin_memory()
+    oF = torch.empty((scene.nf, 5), dtype=torch.float32).pin_memory()
+    dVert = torch.empty_like(scene.vertices)
+    dPar = torch.empty_like(scene.face_params)
+
+    def e2e_step():
+        dVert.copy_(hV, non_blocking=True)
+        dPar.copy_(hP, non_blocking=True)
+        scene.refit(dVert)
+        scene.set_face_params(dPar)
+        step(fb, bb)
+        oI.copy_(img, non_blocking=True)
+        oV.copy_(dV, non_blocking=True)
+        oF.copy_(dF, non_blocking=True)
+
+    ms_e2e = timed(e2e_step, args.steps, 2)
+    value_e2e = seg_step * args.steps * world / (ms_e2e / 1000.0) / 1e6
+    h2d = hV.numel() * 4 + hP.numel() * 4
+    d2h = oI.numel() * 4 + oV.numel() * 4 + oF.numel() * 4
+
+    # parity of this run's gradient against the oracle on a pixel subset
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        r, cores, pix, secs = oracle_sample_rate(sc, args.cpu_seconds)
+        cpu = {"value": round(r, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "%d sampled pixels (all their samples): forward + interior gradient + edge term, "
+                         "FP64 brute force, %.1f s" % (pix, secs)}
+
+    st_final = scene.stats()
+    scene.close()
+    if rank == 0:
+        out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": WORKLOAD_DESC, "segments_per_step": seg_step,
+                          "paths_per_step": sf["paths"] + sb["paths"], "edge_samples_per_step": sb["edge_samples"],
+                          "l2": "flushed between timed steps (256 MiB write)", "launch": "batched persistent + CUDA graph",
+                          "parallelism": "replicas" if world > 1 else "single GPU"},
+               "batched_vs_per_view": round(value / value_pv, 3),
+               "per_view": {"value": round(value_pv, 3), "ms_per_step": round(ms_pv / pv_steps, 3),
+                            "launch": "per-view, host-read queue counts, no graph"},
+               "forward_only": {"value": round(value_fwd, 3), "ms_per_step": round(ms_fwd / args.steps, 3)},
+               "roofline": roofline, "cpu_baseline": cpu,
+               "e2e": {"value": round(value_e2e, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": d2h, "ms_per_step": round(ms_e2e / args.steps, 3)},
+               "gpu_launches": launches_step * args.steps, "clocks": clk.summary(),
+               "device_error": st_final["device_error"]}
+        print(json.dumps(out))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

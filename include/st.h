@@ -121,6 +121,7 @@ typedef struct {
   int device_error;           /* latched device error bits (0 = none) */
   int bvh_nodes;              /* internal nodes of the current BVH */
   long long scratch_bytes;    /* device bytes held by the scene's wavefront buffers */
+  int kernel_launches;        /* kernels the last call launched (graph kernel nodes included) */
 } st_stats;
 
 /* Create a scene: copies the mesh into scene-owned device memory, builds the

@@ -304,6 +304,7 @@ st_status run_chunk(st_scene* s, const Plan& p, const KCtx& c, long long j0, int
   int hc[CNT_SIZE];
   k_reset<<<1, 128, 0, st>>>(cnt);
   k_raygen<<<(n + 255) / 256, 256, 0, st>>>(c, j0, n);
+  s->launches += 2;
   for (int b = 0; b < p.B; ++b) {
     int ge = p.o.count_visits ? g_ext_s : g_ext, gs = g_shade, gw = g_shadow;
     if (host_sized) {
@@ -319,21 +320,24 @@ st_status run_chunk(st_scene* s, const Plan& p, const KCtx& c, long long j0, int
     else k_extend<false><<<ge, EXT_BLOCK, 0, st>>>(c, b);
     if (timing) ST_CUDA(cudaEventRecord(next_event(s, false), st));
     k_shade<<<gs, 256, 0, st>>>(c, b);
+    s->launches += 2;
     if (host_sized) {
       ST_CUDA(cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, st));
       ST_CUDA(cudaStreamSynchronize(st));
       int q = hc[CNT_SH + b];
       gw = (q + EXT_BLOCK - 1) / EXT_BLOCK;
-      if (q > 0) k_shadow<<<gw, EXT_BLOCK, 0, st>>>(c, b);
+      if (q > 0) { k_shadow<<<gw, EXT_BLOCK, 0, st>>>(c, b); s->launches++; }
     } else if (c.NS > 0) {
       k_shadow<<<gw, EXT_BLOCK, 0, st>>>(c, b);
+      s->launches++;
     }
   }
   if (p.kind == 0) {
     k_resolve<<<(n + 255) / 256, 256, 0, st>>>(c, j0, n);
+    s->launches++;
   } else {
-    if (has_cam && p.interior) k_adjoint<<<(n + ADJ_BLOCK - 1) / ADJ_BLOCK, ADJ_BLOCK, 0, st>>>(c, j0, n);
-    if (has_edge) k_edge_resolve<<<(n + ADJ_BLOCK - 1) / ADJ_BLOCK, ADJ_BLOCK, 0, st>>>(c, j0, n);
+    if (has_cam && p.interior) { k_adjoint<<<(n + ADJ_BLOCK - 1) / ADJ_BLOCK, ADJ_BLOCK, 0, st>>>(c, j0, n); s->launches++; }
+    if (has_edge) { k_edge_resolve<<<(n + ADJ_BLOCK - 1) / ADJ_BLOCK, ADJ_BLOCK, 0, st>>>(c, j0, n); s->launches++; }
   }
   ST_CUDA(cudaGetLastError());
   return ST_OK;
@@ -366,6 +370,7 @@ st_status enqueue_call(st_scene* s, const Plan& p, int Q, cudaStream_t st, bool 
     dim3 g((s->n_edges + 255) / 256, (unsigned)p.views.size());
     k_edge_flags<<<g, 256, 0, st>>>(c, (int)p.views.size());
     k_edge_compact<<<(unsigned)p.views.size(), 1024, 0, st>>>(c);
+    s->launches += 2;
   }
   auto chunks = [&](long long a, long long b) -> st_status {
     for (long long j0 = a; j0 < b; j0 += Q) {
@@ -458,11 +463,13 @@ st_status run_call(st_scene* s, Plan& p, const CallArgs& args, cudaStream_t st) 
   ST_CUDA(cudaMemcpyAsync(s->d_args, &args, sizeof(CallArgs), cudaMemcpyHostToDevice, st));
   bool timing = p.o.time_kernels != 0;
   s->ev_used = 0;
+  s->launches = 0;
   bool graph = p.o.mode == ST_MODE_BATCHED && p.o.use_graph && !timing;
   if (!graph) return enqueue_call(s, p, Q, st, p.o.mode == ST_MODE_PER_VIEW, timing);
   std::vector<long long> key = graph_key(p, Q, s);
   for (auto& g : s->graphs)
     if (g.key == key) {
+      s->launches = g.launches;
       ST_CUDA(cudaGraphLaunch(g.exec, st));
       return ST_OK;
     }
@@ -484,6 +491,7 @@ st_status run_call(st_scene* s, Plan& p, const CallArgs& args, cudaStream_t st) 
   if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
   GraphEntry ge;
   ge.key = key;
+  ge.launches = s->launches;
   ce = cudaGraphInstantiate(&ge.exec, graph_obj, 0);
   cudaGraphDestroy(graph_obj);
   if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate");
@@ -711,6 +719,7 @@ st_status st_get_stats(st_scene* s, st_stats* out) {
   r.device_error = err;
   r.bvh_nodes = std::max(s->nf - 1, 0);
   r.scratch_bytes = s->eng.bytes;
+  r.kernel_launches = s->launches;
   *out = r;
   return ST_OK;
 }

@@ -183,7 +183,7 @@ __global__ void k_hierarchy(const uint32_t* keys, int n, float4* nodes, int* par
 
 // ---- leaf records and bottom-up boxes
 __global__ void k_boxes(const float* V, const int* F, const int* ids, int n, float4* tri, float4* nodes,
-                        const int* parent, int* flags) {
+                        const int* parent, int* flags, int* err) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int f = ids[i];
@@ -199,7 +199,8 @@ __global__ void k_boxes(const float* V, const int* F, const int* ids, int n, flo
   float3 hi = mk3(fmaxf(fmaxf(p0.x, p1.x), p2.x), fmaxf(fmaxf(p0.y, p1.y), p2.y), fmaxf(fmaxf(p0.z, p1.z), p2.z));
   int child = ~i;
   int node = parent[(n - 1) + i];
-  while (node >= 0) {
+  for (int depth = 0; node >= 0; ++depth) {
+    if (depth > 128) { atomicOr(err, 2); return; }  // deeper than any 30-bit-key tree: malformed
     float4* np = nodes + 4 * node;
     int cl = __float_as_int(np[3].x);
     if (cl == child) {
@@ -223,7 +224,8 @@ __global__ void k_boxes(const float* V, const int* F, const int* ids, int n, flo
 cudaError_t boxes(st_scene* s, cudaStream_t stream) {
   int n = s->nf;
   if (n > 1) cudaMemsetAsync(s->flags, 0, sizeof(int) * (n - 1), stream);
-  k_boxes<<<(n + 255) / 256, 256, 0, stream>>>(s->verts, s->faces, s->ids, n, s->tri, s->nodes, s->parent, s->flags);
+  k_boxes<<<(n + 255) / 256, 256, 0, stream>>>(s->verts, s->faces, s->ids, n, s->tri, s->nodes, s->parent, s->flags,
+                                                s->d_err);
   return cudaGetLastError();
 }
 

@@ -56,6 +56,7 @@ enum { STAT_PATHS = 0, STAT_EXT = 1, STAT_SHADOW = 2, STAT_EDGE = 3, STAT_VISITS
 struct GraphEntry {
   std::vector<long long> key;
   cudaGraphExec_t exec = nullptr;
+  int launches = 0;
 };
 
 }  // namespace st
@@ -107,6 +108,7 @@ struct st_scene {
   int sm_count = 0;
   float* image_ptr = nullptr;    // forward output of the call being planned (graph key)
   long long last_edge_samples = 0;
+  int launches = 0;              // kernels enqueued by the last call
   st_stats last{};
 };
 

@@ -18,6 +18,7 @@ namespace st {
 constexpr int TRACE_SH = 16;
 constexpr int TRACE_DEPTH = 64;
 constexpr int ERR_STACK = 1;
+constexpr int ERR_LOOP = 2;   // more node fetches than the tree has nodes: malformed hierarchy
 
 struct TraceStats { int visits, tests; };
 
@@ -70,7 +71,9 @@ __device__ __forceinline__ int trace_bvh(const float4* __restrict__ nodes, const
   const int bd = blockDim.x;
   int sp = 0;
   int node = 0;
+  int budget = nf;  // a well-formed tree fetches each of its nf - 1 internal nodes at most once
   for (;;) {
+    if (--budget < 0) { atomicOr(err, ERR_LOOP); return best; }
     const float4* np = nodes + 4 * node;
     float4 n0 = __ldg(np), n1 = __ldg(np + 1), n2 = __ldg(np + 2), n3 = __ldg(np + 3);
     if (STATS) ts->visits++;
