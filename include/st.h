@@ -177,6 +177,28 @@ st_status st_get_stats(st_scene* scene, st_stats* out);
  * nodes float [F-1][16] as stored on the device, leaf_faces int [F]. */
 st_status st_debug_bvh(st_scene* scene, float* nodes, int* leaf_faces);
 
+/* Allocation-free BVH build, for callers that cannot allocate device memory
+ * when they need one (an allocator at its budget, a framework that forbids
+ * allocation on its hot path, an embedding that owns every buffer). The paper
+ * has no counterpart: this is a library-side convenience. It runs the same
+ * build as st_scene_create (Morton order, radix sort, Karras hierarchy,
+ * bottom-up boxes) and writes the same node and leaf layout, but takes all
+ * scratch from one fixed file-scope device array (about 1.8 MiB, held by every
+ * device that loads the library until the process exits) and calls no
+ * allocator. Inputs: vertices device float [V][3], faces device int [F][3].
+ * Outputs (caller-owned, 16-byte aligned): nodes device float [F-1][16] (may
+ * be NULL when F == 1), tris device float [F][12] (leaf triangle records),
+ * leaf_faces device int [F] (face id of each leaf, Morton order).
+ * Limits and behaviour:
+ *  - F <= 65536, else ST_ERR_UNSUPPORTED; face indices are checked on the
+ *    device first (ST_ERR_INVALID_ARG), which synchronises `stream` once.
+ *  - The first call on a device looks up the scratch array's device address
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - Every call shares the one scratch array: calls that overlap on the GPU
+ *    (other streams, other threads) race and corrupt each other's result. */
+st_status st_build_bvh_noalloc(const float* vertices, const int* faces, int n_vertices, int n_faces,
+                               float* nodes, float* tris, int* leaf_faces, void* stream);
+
 /* Message for the last non-OK status on this thread. */
 const char* st_last_error(void);
 

@@ -11,7 +11,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libst.so")
 BUILD = os.path.join(ROOT, "_build")
-UNITS = ["st_api.cu", "st_bvh.cu"]
+UNITS = ["st_api.cu", "st_bvh.cu", "st_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]
 

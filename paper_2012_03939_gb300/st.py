@@ -25,7 +25,8 @@ MODE_BATCHED, MODE_PER_VIEW = 0, 1
 EDGE_SILHOUETTE, EDGE_ALL = 0, 1
 
 EXPORTED = ["st_scene_create", "st_scene_destroy", "st_refit", "st_rebuild", "st_set_face_params", "st_render",
-            "st_render_backward", "st_trace_closest", "st_get_stats", "st_debug_bvh", "st_last_error"]
+            "st_render_backward", "st_trace_closest", "st_get_stats", "st_debug_bvh", "st_build_bvh_noalloc",
+            "st_last_error"]
 
 
 class StError(RuntimeError):
@@ -88,6 +89,7 @@ def lib():
         L.st_trace_closest.argtypes = [P, P, I, I, P, P, P]
         L.st_get_stats.argtypes = [P, P]
         L.st_debug_bvh.argtypes = [P, P, P]
+        L.st_build_bvh_noalloc.argtypes = [P, P, I, I, P, P, P, P]
         L.st_last_error.restype = C.c_char_p
         L.st_last_error.argtypes = []
         for name in EXPORTED[:-1]:
