@@ -39,8 +39,10 @@
 //    pdfs and MIS weights held constant and point-light directions
 //    differentiated; computed here with sparse forward-mode dual numbers.
 //  * Edge term (primary visibility): candidates = silhouette (or all) edges
-//    whose screen projection survives clipping; pick one uniformly, a point
-//    uniformly along its clipped screen segment, trace one path each side at
+//    whose screen projection survives clipping; sample k of N_e picks one with
+//    probability 1/n_cand by a stratified integer map (consecutive samples walk
+//    the candidate list in order), a point uniformly along its clipped screen
+//    segment, trace one path each side at
 //    +-EDGE_EPS pixels along the screen normal with shared random numbers, and
 //    scatter (L- - L+) <dL/dI_pixel> v_n * n_cand * len / N_e to the two
 //    endpoints with screen-space weights (1 - tau, tau).
@@ -935,7 +937,10 @@ long long orc_edge_grad(const orc_scene* in, const orc_view* views, int n_views,
       long long k0 = Ne * blk / nblk, k1 = Ne * (blk + 1) / nblk;
       for (long long k = k0; k < k1; ++k) {
         U4 u = rng.draw((uint32_t)k, c.off, 0u, 1u);
-        const Cand& cd = C[(size_t)(((uint64_t)(u.w[0] >> 8) * ncand) >> 24)];
+        // stratified: sample k draws uniformly from the integers [k*n, (k+1)*n) and
+        // integer t selects candidate t / N_e, so each candidate has probability 1/n
+        uint64_t t = (uint64_t)k * ncand + (((uint64_t)(u.w[0] >> 8) * ncand) >> 24);
+        const Cand& cd = C[(size_t)(t / (uint64_t)Ne)];
         double tau = cd.t0 + unif(u.w[1]) * (cd.t1 - cd.t0);
         double sx = cd.sa.x + (cd.sb.x - cd.sa.x) * tau, sy = cd.sa.y + (cd.sb.y - cd.sa.y) * tau;
         int x = (int)std::floor(sx), y = (int)std::floor(sy);

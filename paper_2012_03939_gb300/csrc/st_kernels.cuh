@@ -123,15 +123,19 @@ struct EdgeSample {
   float2 S, ns;
 };
 
-// Sample k of view vi: candidate chosen uniformly by an integer map of a 24-bit
-// word, point uniform along its clipped screen segment.
-__device__ __forceinline__ EdgeSample edge_sample(const KCtx& c, int vi, const DevView& v, long long k, Key key) {
+// Sample k of the view's n_samples: candidate t / n_samples for an integer t
+// drawn uniformly from [k * nc, (k + 1) * nc) (stratified, probability 1/nc
+// per candidate, consecutive samples on the same edge), then a point uniform
+// along the candidate's clipped screen segment.
+__device__ __forceinline__ EdgeSample edge_sample(const KCtx& c, int vi, const DevView& v, long long k,
+                                                  long long n_samples, Key key) {
   EdgeSample s;
   s.valid = false;
   int nc = c.edge_ncand[vi];
   if (nc <= 0) return s;
   U4 u = philox((uint32_t)k, v.off, 0u, 1u, key.k0, key.k1);
-  int i = (int)(((uint64_t)(u.x >> 8) * (uint64_t)nc) >> 24);
+  uint64_t t = (uint64_t)k * (uint64_t)nc + (((uint64_t)(u.x >> 8) * (uint64_t)nc) >> 24);
+  int i = (int)(t / (uint64_t)n_samples);
   s.e = c.edge_cand[(size_t)vi * c.n_edges + i];
   float2 sa, sb;
   float t0, t1;
@@ -214,7 +218,7 @@ __global__ void k_raygen(KCtx c, long long j0, int n) {
           ok = true;
         } else {
           long long k = local >> 1;
-          EdgeSample es = edge_sample(c, sg.view, v, k, key);
+          EdgeSample es = edge_sample(c, sg.view, v, k, sg.n_samples, key);
           if (es.valid) {
             float sg2 = (local & 1) ? EDGE_EPS : -EDGE_EPS;
             d = cam_dir(v, es.S.x + sg2 * es.ns.x, es.S.y + sg2 * es.ns.y);
@@ -638,7 +642,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_edge_resolve(KCtx c, long long j0
       if (sg.kind == 1 && local < sg.count) {
         DevView v = c.views[sg.view];
         Key kk{c.args->k0, c.args->k1};
-        EdgeSample es = edge_sample(c, sg.view, v, local >> 1, kk);
+        EdgeSample es = edge_sample(c, sg.view, v, local >> 1, sg.n_samples, kk);
         if (es.valid) {
           const float* gp = c.args->dLdI + 3 * (v.pix_off + (long long)es.py * v.W + es.px);
           float3 Lm = xyz(c.e.rad[i]), Lp = xyz(c.e.rad[i + 1]);
