@@ -311,8 +311,8 @@ def run_ours(args):
         a, b = counts(ti, tib)
         ext_ms += a["extend_ms"] + b["extend_ms"]
         ext_n += a["extend_launches"] + b["extend_launches"]
-    # per query: node fetch 64 B, triangle record 48 B, ray in (o, d, origin, queue) 40 B, hit out 8 B
-    alg_bytes = visits * 64 + tests * 48 + rays * 48
+    # per query: 4-wide node fetch 112 B, triangle record 48 B, ray in (o, d, origin, queue) 40 B, hit out 8 B
+    alg_bytes = visits * 112 + tests * 48 + rays * 48
     achieved = alg_bytes * 3 / (ext_ms / 1000.0) / 1e9
     peaks = {}
     try:

@@ -119,9 +119,10 @@ typedef struct {
   int extend_launches;        /* closest-hit launches timed (time_kernels) */
   double extend_ms;           /* their summed CUDA-event time */
   int device_error;           /* latched device error bits (0 = none) */
-  int bvh_nodes;              /* internal nodes of the current BVH */
+  int bvh_nodes;              /* internal nodes of the binary BVH (refit / st_debug_bvh layout) */
   long long scratch_bytes;    /* device bytes held by the scene's wavefront buffers */
   int kernel_launches;        /* kernels the last call launched (graph kernel nodes included) */
+  int bvh4_nodes;             /* nodes of the 4-wide BVH the traversal walks */
 } st_stats;
 
 /* Create a scene: copies the mesh into scene-owned device memory, builds the

@@ -19,7 +19,10 @@ void set_error(const std::string& msg) { g_err = msg; }
 namespace {
 
 constexpr int DEFAULT_CHUNK = 1 << 22;
-constexpr long long SEG_ALIGN = 32;
+// Segment bases and chunk sizes are multiples of 64: an edge segment is laid out
+// in blocks of 64 jobs, the minus sides of 32 consecutive samples then their plus
+// sides, so every warp traces one side along one edge (same behaviour per lane).
+constexpr long long SEG_ALIGN = 64;
 
 st_status fail(st_status s, const std::string& msg) {
   set_error(msg);
@@ -260,7 +263,7 @@ st_status ensure_tables(st_scene* s, int n_views, int n_segs, bool edges) {
 
 KCtx make_ctx(st_scene* s, const Plan& p) {
   KCtx c;
-  c.V = s->verts; c.F = s->faces; c.P = s->params; c.nodes = s->nodes; c.tri = s->tri; c.nf = s->nf;
+  c.V = s->verts; c.F = s->faces; c.P = s->params; c.nodes = s->nodes4; c.tri = s->tri; c.nf = s->nf;
   c.lights = s->lights; c.nl = s->nl; c.NS = s->nl + (s->env.w > 0 ? 1 : 0);
   c.env = s->env; c.brdf = s->brdf;
   c.edge_v = s->edge_v; c.edge_f = s->edge_f; c.n_edges = s->n_edges; c.edge_mode = p.o.edge_mode;
@@ -430,9 +433,9 @@ st_status plan_call(st_scene* s, const st_view* views, int n_views, int default_
     }
     if (p.edges) {
       long long ne = (long long)v.width * v.height * (p.o.edge_spp > 0 ? p.o.edge_spp : spp);
-      Seg sg{base, 2 * ne, i, 1, ne};
+      Seg sg{base, (ne + 31) / 32 * 64, i, 1, ne};
       p.segs.push_back(sg);
-      base += (2 * ne + SEG_ALIGN - 1) / SEG_ALIGN * SEG_ALIGN;
+      base += sg.count;
     }
     p.view_range.push_back({start, base});
   }
@@ -512,6 +515,7 @@ void destroy(st_scene* s) {
   free_engine(s->eng);
   dfree(s->verts); dfree(s->faces); dfree(s->params); dfree(s->tri); dfree(s->nodes); dfree(s->parent);
   dfree(s->flags); dfree(s->keys); dfree(s->keys2); dfree(s->ids); dfree(s->ids2); dfree(s->hist); dfree(s->bounds);
+  dfree(s->nodes4); dfree(s->src4); dfree(s->q4); dfree(s->c4);
   dfree(s->lights); dfree(s->env_tex); dfree(s->env_alias); dfree(s->edge_v); dfree(s->edge_f);
   dfree(s->edge_flag); dfree(s->edge_cand); dfree(s->edge_ncand); dfree(s->d_views); dfree(s->d_segs);
   dfree(s->d_args); dfree(s->d_err);
@@ -598,6 +602,8 @@ st_status st_scene_create(const st_scene_desc* d, void* stream, st_scene** out) 
   chk(dalloc(&s->parent, 2 * (size_t)n)); chk(dalloc(&s->flags, (size_t)std::max(n - 1, 1)));
   chk(dalloc(&s->keys, (size_t)n)); chk(dalloc(&s->keys2, (size_t)n)); chk(dalloc(&s->ids, (size_t)n));
   chk(dalloc(&s->ids2, (size_t)n)); chk(dalloc(&s->hist, 256 * (size_t)s->sort_blocks)); chk(dalloc(&s->bounds, 6));
+  chk(dalloc(&s->nodes4, 7 * (size_t)std::max(n - 1, 1))); chk(dalloc(&s->src4, 4 * (size_t)std::max(n - 1, 1)));
+  chk(dalloc(&s->q4, 4 * (size_t)n)); chk(dalloc(&s->c4, 2));
   chk(dalloc(&s->lights, 2 * (size_t)std::max(s->nl, 1))); chk(dalloc(&s->edge_v, ev.size()));
   chk(dalloc(&s->edge_f, ef.size())); chk(dalloc(&s->d_args, 1)); chk(dalloc(&s->d_err, 1));
   if (d->env) { chk(dalloc(&s->env_tex, etex.size())); chk(dalloc(&s->env_alias, etab.size())); }
@@ -627,6 +633,7 @@ st_status st_scene_create(const st_scene_desc* d, void* stream, st_scene** out) 
   }
   chk(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
   if (e == cudaSuccess) e = bvh_build(s, st);
+  if (e == cudaSuccess) e = bvh_collapse(s, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) { destroy(s); return cuda_fail(e, "scene create"); }
   *out = s;
@@ -643,6 +650,7 @@ static st_status update_vertices(st_scene* s, const float* v, void* stream, bool
   cudaStream_t st = (cudaStream_t)stream;
   ST_CUDA(cudaMemcpyAsync(s->verts, v, 3 * sizeof(float) * s->nv, cudaMemcpyDeviceToDevice, st));
   cudaError_t e = rebuild ? bvh_build(s, st) : bvh_refit(s, st);
+  if (e == cudaSuccess && rebuild) e = bvh_collapse(s, st);
   if (e != cudaSuccess) return cuda_fail(e, rebuild ? "rebuild" : "refit");
   return ST_OK;
 }
@@ -688,7 +696,7 @@ st_status st_trace_closest(st_scene* s, const float* rays, int n, int exclude, i
   if (!s || (n > 0 && (!rays || !out_tri || !out_t)) || n < 0) return fail(ST_ERR_INVALID_ARG, "bad arguments");
   if (n == 0) return ST_OK;
   k_trace_rays<<<(n + EXT_BLOCK - 1) / EXT_BLOCK, EXT_BLOCK, 0, (cudaStream_t)stream>>>(
-      s->nodes, s->tri, s->nf, (const float4*)rays, n, exclude, out_tri, out_t, s->d_err);
+      s->nodes4, s->tri, s->nf, (const float4*)rays, n, exclude, out_tri, out_t, s->d_err);
   ST_CUDA(cudaGetLastError());
   return ST_OK;
 }
@@ -718,6 +726,7 @@ st_status st_get_stats(st_scene* s, st_stats* out) {
   r.extend_ms = ms;
   r.device_error = err;
   r.bvh_nodes = std::max(s->nf - 1, 0);
+  r.bvh4_nodes = s->n4;
   r.scratch_bytes = s->eng.bytes;
   r.kernel_launches = s->launches;
   *out = r;

@@ -254,7 +254,124 @@ cudaError_t bvh_build(st_scene* s, cudaStream_t stream) {
   return boxes(s, stream);
 }
 
-cudaError_t bvh_refit(st_scene* s, cudaStream_t stream) { return boxes(s, stream); }
+// ---- 4-wide collapse: each 4-wide node takes a binary node's children and
+// repeatedly opens the internal child of largest surface area until it holds
+// four children (or only leaves); the opened-up children become 4-wide nodes.
+__device__ __forceinline__ float binary_area(const float4* nodes, int c) {
+  const float4* np = nodes + 4 * c;
+  float4 n0 = np[0], n1 = np[1], n2 = np[2];
+  float dx = fmaxf(n0.y, n1.w) - fminf(n0.x, n1.z);
+  float dy = fmaxf(n0.w, n2.y) - fminf(n0.z, n2.x);
+  float dz = fmaxf(n1.y, n2.w) - fminf(n1.x, n2.z);
+  return dx * dy + dy * dz + dz * dx;
+}
+
+constexpr int EMPTY4 = (int)0x80000000;
+
+__global__ void k_collapse(const float4* nodes, const int* qin, int nin, int* qout, int* counters, int* src4,
+                           float4* nodes4) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nin) return;
+  int b = qin[2 * k], id = qin[2 * k + 1];
+  float4 n3 = nodes[4 * b + 3];
+  int slot[4] = {__float_as_int(n3.x), __float_as_int(n3.y), EMPTY4, EMPTY4};
+  int n = 2;
+  while (n < 4) {
+    int best = -1;
+    float ba = -1.0f;
+    for (int j = 0; j < n; ++j)
+      if (slot[j] >= 0) {
+        float a = binary_area(nodes, slot[j]);
+        if (a > ba) { ba = a; best = j; }
+      }
+    if (best < 0) break;
+    float4 c3 = nodes[4 * slot[best] + 3];
+    slot[best] = __float_as_int(c3.x);
+    slot[n++] = __float_as_int(c3.y);
+  }
+  int child[4];
+  for (int j = 0; j < 4; ++j) {
+    int sj = slot[j];
+    child[j] = sj;
+    if (sj >= 0) {
+      int nid = atomicAdd(&counters[0], 1);
+      int qi = atomicAdd(&counters[1], 1);
+      qout[2 * qi] = sj;
+      qout[2 * qi + 1] = nid;
+      child[j] = nid;
+    }
+    src4[4 * id + j] = sj;
+  }
+  nodes4[7 * id + 6] = make_float4(__int_as_float(child[0]), __int_as_float(child[1]), __int_as_float(child[2]),
+                                   __int_as_float(child[3]));
+}
+
+// child boxes of every 4-wide node from the binary boxes / leaf triangles
+__global__ void k_refit4(const float4* nodes, const float4* tri, const int* src4, int n4, float4* nodes4) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n4) return;
+  float lo[3][4], hi[3][4];
+  for (int j = 0; j < 4; ++j) {
+    int sj = src4[4 * k + j];
+    float3 a = mk3(1e30f, 1e30f, 1e30f), b = mk3(-1e30f, -1e30f, -1e30f);
+    if (sj != EMPTY4 && sj < 0) {
+      int li = ~sj;
+      float3 p0 = xyz(tri[3 * li]), p1 = xyz(tri[3 * li + 1]), p2 = xyz(tri[3 * li + 2]);
+      a = mk3(fminf(fminf(p0.x, p1.x), p2.x), fminf(fminf(p0.y, p1.y), p2.y), fminf(fminf(p0.z, p1.z), p2.z));
+      b = mk3(fmaxf(fmaxf(p0.x, p1.x), p2.x), fmaxf(fmaxf(p0.y, p1.y), p2.y), fmaxf(fmaxf(p0.z, p1.z), p2.z));
+    } else if (sj >= 0) {
+      const float4* np = nodes + 4 * sj;
+      float4 n0 = np[0], n1 = np[1], n2 = np[2];
+      a = mk3(fminf(n0.x, n1.z), fminf(n0.z, n2.x), fminf(n1.x, n2.z));
+      b = mk3(fmaxf(n0.y, n1.w), fmaxf(n0.w, n2.y), fmaxf(n1.y, n2.w));
+    }
+    lo[0][j] = a.x; lo[1][j] = a.y; lo[2][j] = a.z;
+    hi[0][j] = b.x; hi[1][j] = b.y; hi[2][j] = b.z;
+  }
+  float4* o = nodes4 + 7 * k;
+  for (int ax = 0; ax < 3; ++ax) {
+    o[2 * ax] = make_float4(lo[ax][0], lo[ax][1], lo[ax][2], lo[ax][3]);
+    o[2 * ax + 1] = make_float4(hi[ax][0], hi[ax][1], hi[ax][2], hi[ax][3]);
+  }
+}
+
+cudaError_t refit4(st_scene* s, cudaStream_t stream) {
+  if (!s->nodes4 || s->n4 <= 0) return cudaSuccess;
+  k_refit4<<<(s->n4 + 127) / 128, 128, 0, stream>>>(s->nodes, s->tri, s->src4, s->n4, s->nodes4);
+  return cudaGetLastError();
+}
+
+cudaError_t bvh_refit(st_scene* s, cudaStream_t stream) {
+  cudaError_t e = boxes(s, stream);
+  return e != cudaSuccess ? e : refit4(s, stream);
+}
+
+cudaError_t bvh_collapse(st_scene* s, cudaStream_t stream) {
+  int n = s->nf;
+  s->n4 = 0;
+  if (n < 2) return cudaSuccess;
+  int init[2] = {0, 0};   // binary root -> 4-wide node 0
+  int cnt[2] = {1, 0};
+  int* qa = s->q4;
+  int* qb = s->q4 + 2 * (size_t)n;
+  cudaError_t e = cudaMemcpyAsync(qa, init, sizeof(init), cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(s->c4, cnt, sizeof(cnt), cudaMemcpyHostToDevice, stream);
+  int nin = 1;
+  for (int level = 0; nin > 0 && e == cudaSuccess; ++level) {
+    if (level > 64) return cudaErrorIllegalState;  // deeper than any tree built here: malformed
+    e = cudaMemsetAsync(s->c4 + 1, 0, sizeof(int), stream);
+    if (e != cudaSuccess) break;
+    k_collapse<<<(nin + 127) / 128, 128, 0, stream>>>(s->nodes, qa, nin, qb, s->c4, s->src4, s->nodes4);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cnt, s->c4, sizeof(cnt), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    nin = cnt[1];
+    std::swap(qa, qb);
+  }
+  if (e != cudaSuccess) return e;
+  s->n4 = cnt[0];
+  return refit4(s, stream);
+}
 
 int sort_blocks_for(int n) { return (n + RS_TILE - 1) / RS_TILE; }
 

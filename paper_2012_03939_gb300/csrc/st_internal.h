@@ -77,6 +77,12 @@ struct st_scene {
   uint32_t* hist = nullptr;
   int* bounds = nullptr;         // [6] ordered-int centroid bounds
   int sort_blocks = 0;
+  // 4-wide BVH collapsed from the binary tree (what the traversal walks)
+  float4* nodes4 = nullptr;      // [n4*7]: lo.x[4], hi.x[4], lo.y[4], hi.y[4], lo.z[4], hi.z[4], children[4]
+  int* src4 = nullptr;           // [n4*4]: binary node (>= 0) or ~leaf (< 0) behind each child slot
+  int* q4 = nullptr;             // [4*F] collapse work queues
+  int* c4 = nullptr;             // [2] collapse counters
+  int n4 = 0;
   // lights
   float4* lights = nullptr;      // [nl*2]: (pos, 0), (intensity, 0)
   std::vector<st_point_light> host_lights;
@@ -114,7 +120,8 @@ struct st_scene {
 
 namespace st {
 cudaError_t bvh_build(st_scene* s, cudaStream_t stream);    // Morton order + hierarchy + boxes
-cudaError_t bvh_refit(st_scene* s, cudaStream_t stream);    // leaf records + boxes, same order
+cudaError_t bvh_refit(st_scene* s, cudaStream_t stream);    // leaf records + boxes, same order (+ 4-wide boxes)
+cudaError_t bvh_collapse(st_scene* s, cudaStream_t stream); // 4-wide tree from the binary one (synchronises)
 cudaError_t trace_closest(st_scene* s, const float* rays, int n, int exclude, int* out_tri, float* out_t,
                           cudaStream_t stream);
 void set_error(const std::string& msg);

@@ -217,10 +217,13 @@ __global__ void k_raygen(KCtx c, long long j0, int n) {
           ct = make_int4((int)c0, s, 0, 0);
           ok = true;
         } else {
-          long long k = local >> 1;
-          EdgeSample es = edge_sample(c, sg.view, v, k, sg.n_samples, key);
+          // block of 64 jobs: minus sides of samples 32b..32b+31, then their plus sides
+          long long k = (local >> 6) * 32 + (local & 31);
+          EdgeSample es;
+          es.valid = false;
+          if (k < sg.n_samples) es = edge_sample(c, sg.view, v, k, sg.n_samples, key);
           if (es.valid) {
-            float sg2 = (local & 1) ? EDGE_EPS : -EDGE_EPS;
+            float sg2 = (local & 32) ? EDGE_EPS : -EDGE_EPS;
             d = cam_dir(v, es.S.x + sg2 * es.ns.x, es.S.y + sg2 * es.ns.y);
             o = v.eye;
             ct = make_int4((int)(uint32_t)k, (int)v.off, 2, 1);
@@ -633,19 +636,20 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_edge_resolve(KCtx c, long long j0
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   float vals[6] = {0, 0, 0, 0, 0, 0};
   int key = -1, va = 0, vb = 0;
-  if (i < n && (i & 1) == 0) {
+  if (i < n) {
     long long job = j0 + i;
     int si = find_seg(c.segs, c.n_segs, job);
     if (si >= 0) {
       Seg sg = c.segs[si];
       long long local = job - sg.base;
-      if (sg.kind == 1 && local < sg.count) {
+      long long k = (local >> 6) * 32 + (local & 31);
+      if (sg.kind == 1 && local < sg.count && (local & 32) == 0 && k < sg.n_samples) {
         DevView v = c.views[sg.view];
         Key kk{c.args->k0, c.args->k1};
-        EdgeSample es = edge_sample(c, sg.view, v, local >> 1, sg.n_samples, kk);
+        EdgeSample es = edge_sample(c, sg.view, v, k, sg.n_samples, kk);
         if (es.valid) {
           const float* gp = c.args->dLdI + 3 * (v.pix_off + (long long)es.py * v.W + es.px);
-          float3 Lm = xyz(c.e.rad[i]), Lp = xyz(c.e.rad[i + 1]);
+          float3 Lm = xyz(c.e.rad[i]), Lp = xyz(c.e.rad[i + 32]);
           float gsum = gp[0] * (Lm.x - Lp.x) + gp[1] * (Lm.y - Lp.y) + gp[2] * (Lm.z - Lp.z);
           if (gsum != 0.0f) {
             float wt = gsum * (float)c.edge_ncand[sg.view] * es.len / (float)sg.n_samples;

@@ -1,22 +1,19 @@
-// Stack-based traversal of the LBVH (closest hit and any hit).
+// Stack-based traversal of the 4-wide BVH (closest hit and any hit).
 //
-// Internal node layout (64 bytes, four float4, read as 16-byte vector loads):
-//   n0 = (lo_l.x, hi_l.x, lo_l.y, hi_l.y)
-//   n1 = (lo_l.z, hi_l.z, lo_r.x, hi_r.x)
-//   n2 = (lo_r.y, hi_r.y, lo_r.z, hi_r.z)
-//   n3 = (child_l, child_r, -, -) as int bits; a child c < 0 is leaf ~c.
-// Leaf i is the triangle record tri[3i..3i+2] = v0 (w = face id bits), v1, v2,
-// stored in Morton order. Children that are leaves are intersected as soon as
-// their box is hit; the far internal child is pushed. The first TRACE_SH
-// entries of the stack live in shared memory (strided by block size), the
-// rest in local memory.
+// The binary LBVH (internal node = 64 bytes: both child boxes, then the two
+// child links) is collapsed into 4-wide nodes of 112 bytes, seven float4 read
+// as 16-byte vector loads: lo.x, hi.x, lo.y, hi.y, lo.z, hi.z of the four
+// children, then the four child links. Leaf i is the triangle record
+// tri[3i..3i+2] = v0 (w = face id bits), v1, v2, stored in Morton order.
+// The first TRACE_SH entries of the stack live in shared memory (strided by
+// block size), the rest in local memory.
 #pragma once
 #include "st_device.cuh"
 
 namespace st {
 
 constexpr int TRACE_SH = 16;
-constexpr int TRACE_DEPTH = 64;
+constexpr int TRACE_DEPTH = 96;   // 4-wide nodes push up to three children per level
 constexpr int ERR_STACK = 1;
 constexpr int ERR_LOOP = 2;   // more node fetches than the tree has nodes: malformed hierarchy
 
@@ -41,6 +38,10 @@ __device__ __forceinline__ float box_hit(float lx, float hx, float ly, float hy,
 }
 
 // ANY = stop at the first hit (shadow rays). Returns the face id or -1; t in tbest.
+// nodes = the 4-wide tree: per node lo.x, hi.x, lo.y, hi.y, lo.z, hi.z (one
+// float4 of four children each) and the four child links (>= 0 node, < 0 leaf
+// ~i, INT_MIN empty). Hit leaves are tested at once; hit internal children are
+// sorted by entry distance, the nearest is visited next, the others pushed.
 template <bool ANY, bool STATS>
 __device__ __forceinline__ int trace_bvh(const float4* __restrict__ nodes, const float4* __restrict__ tri, int nf,
                                          float3 o, float3 d, float tmax, int exclude, float& tbest, int* sstack,
@@ -67,36 +68,57 @@ __device__ __forceinline__ int trace_bvh(const float4* __restrict__ nodes, const
     leaf(0);
     return best;
   }
+  const float INF = __int_as_float(0x7f800000);
+  const int EMPTY = (int)0x80000000;
   int local[TRACE_DEPTH - TRACE_SH];
   const int bd = blockDim.x;
   int sp = 0;
   int node = 0;
-  int budget = nf;  // a well-formed tree fetches each of its nf - 1 internal nodes at most once
+  int budget = nf;  // a well-formed tree fetches each of its < nf nodes at most once
   for (;;) {
     if (--budget < 0) { atomicOr(err, ERR_LOOP); return best; }
-    const float4* np = nodes + 4 * node;
-    float4 n0 = __ldg(np), n1 = __ldg(np + 1), n2 = __ldg(np + 2), n3 = __ldg(np + 3);
+    const float4* np = nodes + 7 * node;
+    float4 lx = __ldg(np), hx = __ldg(np + 1), ly = __ldg(np + 2), hy = __ldg(np + 3), lz = __ldg(np + 4),
+           hz = __ldg(np + 5), ch = __ldg(np + 6);
     if (STATS) ts->visits++;
-    float tl = box_hit(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, o, inv, tbest);
-    float tr = box_hit(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, o, inv, tbest);
-    int cl = __float_as_int(n3.x), cr = __float_as_int(n3.y);
-    bool hl = tl != __int_as_float(0x7f800000), hr = tr != __int_as_float(0x7f800000);
-    if (hl && cl < 0) { if (leaf(~cl) && ANY) return best; hl = false; }
-    if (hr && cr < 0) { if (leaf(~cr) && ANY) return best; hr = false; }
-    if (hl && hr) {
-      int nearc = tl <= tr ? cl : cr, farc = tl <= tr ? cr : cl;
-      if (sp >= TRACE_DEPTH) { atomicOr(err, ERR_STACK); return best; }
-      if (sp < TRACE_SH) sstack[sp * bd] = farc; else local[sp - TRACE_SH] = farc;
-      ++sp;
-      node = nearc;
-    } else if (hl) {
-      node = cl;
-    } else if (hr) {
-      node = cr;
-    } else {
+    int c[4] = {__float_as_int(ch.x), __float_as_int(ch.y), __float_as_int(ch.z), __float_as_int(ch.w)};
+    float t[4];
+    t[0] = box_hit(lx.x, hx.x, ly.x, hy.x, lz.x, hz.x, o, inv, tbest);
+    t[1] = box_hit(lx.y, hx.y, ly.y, hy.y, lz.y, hz.y, o, inv, tbest);
+    t[2] = box_hit(lx.z, hx.z, ly.z, hy.z, lz.z, hz.z, o, inv, tbest);
+    t[3] = box_hit(lx.w, hx.w, ly.w, hy.w, lz.w, hz.w, o, inv, tbest);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (c[j] == EMPTY) t[j] = INF;
+      if (c[j] < 0 && t[j] != INF) {
+        if (leaf(~c[j]) && ANY) return best;
+        t[j] = INF;
+      }
+    }
+    // internal children still in front of the current hit, nearest first
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (t[j] > tbest * 1.00000036f) t[j] = INF;
+    auto cswap = [&](int a, int b) {
+      if (t[b] < t[a]) {
+        float tt = t[a]; t[a] = t[b]; t[b] = tt;
+        int cc = c[a]; c[a] = c[b]; c[b] = cc;
+      }
+    };
+    cswap(0, 1); cswap(2, 3); cswap(0, 2); cswap(1, 3); cswap(1, 2);
+    if (t[0] == INF) {
       if (sp == 0) break;
       --sp;
       node = sp < TRACE_SH ? sstack[sp * bd] : local[sp - TRACE_SH];
+      continue;
+    }
+    node = c[0];
+#pragma unroll
+    for (int j = 3; j >= 1; --j) {
+      if (t[j] == INF) continue;
+      if (sp >= TRACE_DEPTH) { atomicOr(err, ERR_STACK); return best; }
+      if (sp < TRACE_SH) sstack[sp * bd] = c[j]; else local[sp - TRACE_SH] = c[j];
+      ++sp;
     }
   }
   return best;

@@ -64,7 +64,8 @@ class Stats(C.Structure):
     _fields_ = [("paths", C.c_longlong), ("extension_rays", C.c_longlong), ("shadow_rays", C.c_longlong),
                 ("edge_samples", C.c_longlong), ("node_visits", C.c_longlong), ("tri_tests", C.c_longlong),
                 ("extend_launches", C.c_int), ("extend_ms", C.c_double), ("device_error", C.c_int),
-                ("bvh_nodes", C.c_int), ("scratch_bytes", C.c_longlong), ("kernel_launches", C.c_int)]
+                ("bvh_nodes", C.c_int), ("scratch_bytes", C.c_longlong), ("kernel_launches", C.c_int),
+                ("bvh4_nodes", C.c_int)]
 
 
 _lib = None
