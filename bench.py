@@ -30,9 +30,20 @@ import numpy as np  # noqa: E402
 
 METRIC = "fwd+adjoint path segments/s (M/s), batched vs per-view, at grad rel err ≤1e-3"
 UNIT = "Mseg/s"
-WORKLOAD_DESC = ("batched uneven views: displaced UV sphere 200000 faces, per-face Torrance-Sparrow (GGX), "
-                 "env 512x256 lognormal(0,1.5), 64 Fibonacci-sphere views with W,H in {64,128,256,512} and spp in "
-                 "{1,4,16}, 3 bounces; forward + adjoint (interior replay + silhouette edge term)")
+DESCRIPTIONS = {
+    "batched": ("batched uneven views: displaced UV sphere 200000 faces, per-face Torrance-Sparrow (GGX), env 512x256 "
+                "lognormal(0,1.5), 64 Fibonacci-sphere views with W,H in {64,128,256,512} and spp in {1,4,16}, "
+                "3 bounces; forward + adjoint (interior replay + silhouette edge term)"),
+    "tiny": ("tiny: icosphere 320 faces, 1 point light, one 64x64 view, 4 spp, 2 bounces; forward + adjoint "
+             "(interior + silhouette edges)"),
+    "edges": ("edges: displaced icosphere 5120 faces, 3 point lights, 16 ring views 128x128, 16 spp, 3 bounces; "
+              "forward + adjoint (interior + silhouette edges)"),
+    "env": ("env: torus knot 50000 faces, env 256x128 lognormal(0,1.5), 32 views 256x256, 4 spp, 4 bounces; "
+            "forward + interior adjoint with path replay"),
+    "scale": ("scale: fractal-displaced UV sphere 1000000 faces, env 1024x512 + 2 point lights, 100 views 512x512, "
+              "16 spp, 5 bounces; one step = one Adam iteration over an 8-view minibatch (BVH refit, forward, "
+              "MSE, adjoint with interior + silhouette edges, Adam update at zero learning rate)"),
+}
 
 
 def parse():
@@ -57,11 +68,13 @@ def rank_info():
 
 
 # ---------------------------------------------------------------------------- CPU oracle leg
-def oracle_sample_rate(sc, seconds, seed=2024):
+def oracle_sample_rate(sc, seconds, seed=2024, max_views=4):
     """Segments/s of the FP64 oracle (forward + interior gradient + edge term) on a pixel sample."""
     import oracle as O
-    osc = O.OracleScene(sc)
     rng = np.random.default_rng(seed)
+    if len(sc.views) > max_views:
+        sc = sc.subset_views(sorted(rng.choice(len(sc.views), size=max_views, replace=False)))
+    osc = O.OracleScene(sc)
     npix = 4
     cores = os.cpu_count() or 1
     t_total, seg_total, pix_total = 0.0, 0, 0
@@ -111,7 +124,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": round(v, 6), "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1000 * wall / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "l2": "n/a (CPU)"},
+        "config": {"workload": DESCRIPTIONS[args.workload], "l2": "n/a (CPU)"},
         "cpu_baseline": {"value": round(v, 6), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": round(v, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
@@ -191,6 +204,11 @@ def profiled_traffic():
     return float(kv["dram_bytes_per_ray"])
 
 
+def l2_peak_gbs(st):
+    """Best of a few sizes of the library's L2-resident read probe (GB/s)."""
+    return max(st.measure_l2_read(mb << 20, 64) for mb in (16, 32, 48))
+
+
 def run_ours(args):
     import torch
     from paper_2012_03939_gb300 import build as Bld
@@ -227,7 +245,34 @@ def run_ours(args):
     dF = torch.zeros((scene.nf, 5), dtype=torch.float32, device="cuda")
     inv_n = 1.0 / (3 * N)
 
+    adam = args.workload == "scale"
+    if adam:
+        # one step = one Adam iteration over an 8-view minibatch (refit, render, MSE, adjoint, update)
+        import dataclasses
+        from paper_2012_03939_gb300 import optimize as Opt
+        rec = Opt.Reconstruction(scene, views, target, torch.from_numpy(sc.vertices).cuda(),
+                                 torch.from_numpy(sc.face_params).cuda(),
+                                 # zero learning rates: every step still refits, renders, differentiates
+                                 # and runs the Adam arithmetic, but the mesh stays the one whose ray
+                                 # queries were counted, so the segment count is exact for every step
+                                 Opt.AdamConfig(max_bounces=B, minibatch=8, edge_term=1, seed=seed,
+                                                lr_vertices=0.0, lr_params=0.0))
+        step_views, off = [], 0
+        for v in views[:8]:
+            step_views.append(dataclasses.replace(v, pixel_offset=off))
+            off += v.width * v.height
+        Ns = off
+        img = torch.zeros((Ns, 3), dtype=torch.float32, device="cuda")
+        step_target = target[:Ns]
+    else:
+        step_views, Ns, step_target = views, N, target
+    inv_s = 1.0 / (3 * Ns)
+
     def step(fopts, bopts):
+        if adam:
+            rec.fopts, rec.bopts = fopts, bopts
+            rec.step()
+            return
         scene.render(views, B, seed, fopts, out=img)
         g = (img - target) * (2 * inv_n)
         dV.zero_()
@@ -235,10 +280,10 @@ def run_ours(args):
         scene.backward(views, B, seed, g, bopts, d_vertices=dV, d_face_params=dF)
 
     def counts(fopts, bopts):
-        scene.render(views, B, seed, fopts, out=img)
+        scene.render(step_views, B, seed, fopts, out=img)
         a = scene.stats()
-        g = (img - target) * (2 * inv_n)
-        scene.backward(views, B, seed, g, bopts, d_vertices=dV, d_face_params=dF)
+        g = (img - step_target) * (2 * inv_s)
+        scene.backward(step_views, B, seed, g, bopts, d_vertices=dV, d_face_params=dF)
         b = scene.stats()
         return a, b
 
@@ -263,8 +308,17 @@ def run_ours(args):
             ms = float(t.item())
         return ms
 
-    fb = st.make_opts(mode="batched", use_graph=1, chunk_paths=args.chunk)
-    bb = st.make_opts(mode="batched", use_graph=1, edge_term=1, edge_mode=0, chunk_paths=args.chunk)
+    edge_on = 0 if args.workload == "env" else 1     # the environment workload is forward + interior adjoint
+    tuned = None
+    chunk, persist = args.chunk, 0
+    if not args.chunk and not args.profile:
+        from paper_2012_03939_gb300 import autotune
+        tuned = autotune.tune(scene, step_views, B, seed, edge_term=edge_on, edge_mode=0,
+                              cache_path=os.path.join(ROOT, "_work", "autotune_cache.json"))
+        chunk, persist = tuned["chunk_paths"], tuned["persist_blocks"]
+    fb = st.make_opts(mode="batched", use_graph=1, chunk_paths=chunk, persist_blocks=persist)
+    bb = st.make_opts(mode="batched", use_graph=1, edge_term=edge_on, edge_mode=0, chunk_paths=chunk,
+                      persist_blocks=persist)
     if args.profile:
         for _ in range(args.warmup):
             step(fb, bb)
@@ -277,7 +331,7 @@ def run_ours(args):
         scene.close()
         return
     fp = st.make_opts(mode="per_view", use_graph=0)
-    bp = st.make_opts(mode="per_view", use_graph=0, edge_term=1, edge_mode=0)
+    bp = st.make_opts(mode="per_view", use_graph=0, edge_term=edge_on, edge_mode=0)
 
     sf, sb = counts(fb, bb)
     seg_fwd = sf["extension_rays"] + sf["shadow_rays"]
@@ -292,19 +346,19 @@ def run_ours(args):
     pv_steps = args.per_view_steps or max(2, args.steps // 3)
     ms_pv = timed(lambda: step(fp, bp), pv_steps, 1)
     value_pv = seg_step * pv_steps * world / (ms_pv / 1000.0) / 1e6
-    ms_fwd = timed(lambda: scene.render(views, B, seed, fb, out=img), args.steps, 2)
+    ms_fwd = timed(lambda: scene.render(step_views, B, seed, fb, out=img), args.steps, 2)
     value_fwd = seg_fwd * args.steps * world / (ms_fwd / 1000.0) / 1e6
 
     # roofline of the dominant kernel (closest-hit traversal): algorithmic bytes
     # from the instrumented traversal, time from CUDA events around each launch
-    ci = st.make_opts(mode="batched", use_graph=0, count_visits=1)
-    cib = st.make_opts(mode="batched", use_graph=0, count_visits=1, edge_term=1, edge_mode=0)
+    ci = st.make_opts(mode="batched", use_graph=0, count_visits=1, chunk_paths=chunk)
+    cib = st.make_opts(mode="batched", use_graph=0, count_visits=1, edge_term=edge_on, edge_mode=0, chunk_paths=chunk)
     a, b = counts(ci, cib)
     visits = a["node_visits"] + b["node_visits"]
     tests = a["tri_tests"] + b["tri_tests"]
     rays = a["extension_rays"] + b["extension_rays"]
-    ti = st.make_opts(mode="batched", use_graph=0, time_kernels=1)
-    tib = st.make_opts(mode="batched", use_graph=0, time_kernels=1, edge_term=1, edge_mode=0)
+    ti = st.make_opts(mode="batched", use_graph=0, time_kernels=1, chunk_paths=chunk)
+    tib = st.make_opts(mode="batched", use_graph=0, time_kernels=1, edge_term=edge_on, edge_mode=0, chunk_paths=chunk)
     ext_ms, ext_n = 0.0, 0
     for _ in range(3):
         flush.fill_(1.0)
@@ -321,6 +375,7 @@ def run_ours(args):
         pass
     peak = peaks.get("hbm_gbs", 6800.0)
     tr = profiled_traffic()
+    l2 = l2_peak_gbs(st)
     roofline = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4),
                 "traffic": None if tr is None else round(tr * rays / max(1, ext_n // 3), 1),
@@ -329,7 +384,9 @@ def run_ours(args):
                 "alg_bytes_per_ray": round(alg_bytes / max(rays, 1), 1),
                 "node_visits_per_ray": round(visits / max(rays, 1), 2),
                 "tri_tests_per_ray": round(tests / max(rays, 1), 2),
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback"}
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback",
+                "l2": {"peak": round(l2, 1), "frac": round(achieved / l2, 4), "unit": "GB/s",
+                       "peak_source": "st_measure_l2_read: L2-resident read, best of 16/32/48 MiB, measured live"}}
 
     # end to end through the C ABI with host buffers: H2D of the mesh state and
     # D2H of the image and both gradients every step
@@ -342,6 +399,15 @@ def run_ours(args):
     dPar = torch.empty_like(scene.face_params)
 
     def e2e_step():
+        if adam:
+            # the model lives on the host: upload it, iterate, read the updated model back
+            with torch.no_grad():
+                rec.V.copy_(hV, non_blocking=True)
+                rec.P.copy_(hP, non_blocking=True)
+            step(fb, bb)
+            oV.copy_(rec.V.detach(), non_blocking=True)
+            oF.copy_(rec.P.detach(), non_blocking=True)
+            return
         dVert.copy_(hV, non_blocking=True)
         dPar.copy_(hP, non_blocking=True)
         scene.refit(dVert)
@@ -354,7 +420,7 @@ def run_ours(args):
     ms_e2e = timed(e2e_step, args.steps, 2)
     value_e2e = seg_step * args.steps * world / (ms_e2e / 1000.0) / 1e6
     h2d = hV.numel() * 4 + hP.numel() * 4
-    d2h = oI.numel() * 4 + oV.numel() * 4 + oF.numel() * 4
+    d2h = (0 if adam else oI.numel() * 4) + oV.numel() * 4 + oF.numel() * 4
 
     # parity of this run's gradient against the oracle on a pixel subset
     cpu = None
@@ -370,9 +436,11 @@ def run_ours(args):
         out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-               "config": {"workload": WORKLOAD_DESC, "segments_per_step": seg_step,
+               "config": {"workload": DESCRIPTIONS[args.workload], "segments_per_step": seg_step,
                           "paths_per_step": sf["paths"] + sb["paths"], "edge_samples_per_step": sb["edge_samples"],
                           "l2": "flushed between timed steps (256 MiB write)", "launch": "batched persistent + CUDA graph",
+                          "autotuned": None if tuned is None else {k: tuned[k] for k in ("chunk_paths", "persist_blocks")},
+                          "edge_term": bool(edge_on),
                           "parallelism": "replicas" if world > 1 else "single GPU"},
                "batched_vs_per_view": round(value / value_pv, 3),
                "per_view": {"value": round(value_pv, 3), "ms_per_step": round(ms_pv / pv_steps, 3),

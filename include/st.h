@@ -107,6 +107,7 @@ typedef struct {
   int chunk_paths;  /* paths in flight per wavefront chunk; 0 = library default */
   int time_kernels; /* per-view or ungraphed batched: time the closest-hit kernel (see st_stats) */
   int count_visits; /* run the instrumented traversal that counts node visits and triangle tests */
+  int persist_blocks; /* batched mode: resident blocks per SM of the persistent stage kernels (0 = occupancy limit) */
 } st_render_opts;
 
 typedef struct {
@@ -199,6 +200,12 @@ st_status st_debug_bvh(st_scene* scene, float* nodes, int* leaf_faces);
  *    (other streams, other threads) race and corrupt each other's result. */
 st_status st_build_bvh_noalloc(const float* vertices, const int* faces, int n_vertices, int n_faces,
                                float* nodes, float* tris, int* leaf_faces, void* stream);
+
+/* Measurement utility, not part of the method: read bandwidth (GB/s) of a
+ * device buffer of `bytes` (>= 1 MiB) that is resident in L2, read `passes`
+ * times by one kernel with cache-global 16-byte loads. Allocates and frees the
+ * buffer; synchronises `stream`. Used as the L2 roofline denominator. */
+st_status st_measure_l2_read(long long bytes, int passes, void* stream, double* gbs);
 
 /* Message for the last non-OK status on this thread. */
 const char* st_last_error(void);

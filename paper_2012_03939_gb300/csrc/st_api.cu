@@ -303,13 +303,15 @@ st_status run_chunk(st_scene* s, const Plan& p, const KCtx& c, long long j0, int
     g_shade = grid_of((const void*)k_shade, 256, sm);
     g_shadow = grid_of((const void*)k_shadow, EXT_BLOCK, sm);
   }
+  // persistent grids: occupancy limit, or fewer resident blocks per SM if asked
+  auto cap = [&](int g) { return p.o.persist_blocks > 0 ? std::min(g, p.o.persist_blocks * sm) : g; };
   int* cnt = s->eng.cnt;
   int hc[CNT_SIZE];
   k_reset<<<1, 128, 0, st>>>(cnt);
   k_raygen<<<(n + 255) / 256, 256, 0, st>>>(c, j0, n);
   s->launches += 2;
   for (int b = 0; b < p.B; ++b) {
-    int ge = p.o.count_visits ? g_ext_s : g_ext, gs = g_shade, gw = g_shadow;
+    int ge = cap(p.o.count_visits ? g_ext_s : g_ext), gs = cap(g_shade), gw = cap(g_shadow);
     if (host_sized) {
       ST_CUDA(cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, st));
       ST_CUDA(cudaStreamSynchronize(st));
@@ -398,7 +400,8 @@ st_status enqueue_call(st_scene* s, const Plan& p, int Q, cudaStream_t st, bool 
 
 std::vector<long long> graph_key(const Plan& p, int Q, const st_scene* s) {
   std::vector<long long> k = {p.kind, p.B, (long long)p.views.size(), Q, p.o.edge_term, p.o.edge_mode, p.o.edge_spp,
-                              p.interior, p.edges, (long long)(size_t)s->image_ptr, p.o.count_visits};
+                              p.interior, p.edges, (long long)(size_t)s->image_ptr, p.o.count_visits,
+                              p.o.persist_blocks};
   for (auto& v : p.views) { k.push_back(v.W); k.push_back(v.H); k.push_back(v.spp); k.push_back(v.pix_off); }
   return k;
 }
@@ -412,7 +415,8 @@ st_status plan_call(st_scene* s, const st_view* views, int n_views, int default_
   p.o = opts ? *opts : default_opts();
   if (p.o.mode != ST_MODE_BATCHED && p.o.mode != ST_MODE_PER_VIEW) return fail(ST_ERR_INVALID_ARG, "bad mode");
   if (p.o.edge_mode != ST_EDGE_SILHOUETTE && p.o.edge_mode != ST_EDGE_ALL) return fail(ST_ERR_INVALID_ARG, "bad edge_mode");
-  if (p.o.edge_spp < 0 || p.o.chunk_paths < 0) return fail(ST_ERR_INVALID_ARG, "negative option");
+  if (p.o.edge_spp < 0 || p.o.chunk_paths < 0 || p.o.persist_blocks < 0)
+    return fail(ST_ERR_INVALID_ARG, "negative option");
   p.interior = kind == 1 && want_interior;
   p.edges = kind == 1 && p.o.edge_term != 0;
   long long base = 0;
@@ -738,6 +742,54 @@ st_status st_debug_bvh(st_scene* s, float* nodes, int* leaf_faces) {
   ST_CUDA(cudaDeviceSynchronize());
   if (s->nf > 1) ST_CUDA(cudaMemcpy(nodes, s->nodes, sizeof(float4) * 4 * (s->nf - 1), cudaMemcpyDeviceToHost));
   ST_CUDA(cudaMemcpy(leaf_faces, s->ids, sizeof(int) * s->nf, cudaMemcpyDeviceToHost));
+  return ST_OK;
+}
+
+// Measurement utility (not part of the path trace): read bandwidth of a buffer
+// that stays resident in L2, so rooflines of L2-resident kernels (the BVH
+// traversal) have a measured denominator beside the HBM copy bandwidth.
+__global__ void k_l2_read(const float4* __restrict__ p, long long n4, int passes, float* out) {
+  float4 acc = make_float4(0, 0, 0, 0);
+  for (int r = 0; r < passes; ++r)
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x) {
+      float4 v = __ldcg(p + i);
+      acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+    }
+  float sum = acc.x + acc.y + acc.z + acc.w;
+  if (sum == -1.0f) out[blockIdx.x] = sum;   // keeps the loads; the buffer holds zeros, so this never stores
+}
+
+st_status st_measure_l2_read(long long bytes, int passes, void* stream, double* gbs) {
+  if (bytes < (1 << 20) || passes < 1 || !gbs) return fail(ST_ERR_INVALID_ARG, "bad arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  long long n4 = bytes / 16;
+  float4* buf = nullptr;
+  float* out = nullptr;
+  cudaEvent_t a = nullptr, b = nullptr;
+  int dev = 0, sm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev);
+  int grid = sm * 4;
+  cudaError_t e = cudaMalloc((void**)&buf, n4 * 16);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&out, sizeof(float) * grid);
+  if (e == cudaSuccess) e = cudaMemsetAsync(buf, 0, n4 * 16, st);
+  if (e == cudaSuccess) e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  if (e == cudaSuccess) {
+    k_l2_read<<<grid, 512, 0, st>>>(buf, n4, 2, out);   // warm: the buffer becomes L2 resident
+    cudaEventRecord(a, st);
+    k_l2_read<<<grid, 512, 0, st>>>(buf, n4, passes, out);
+    cudaEventRecord(b, st);
+    e = cudaEventSynchronize(b);
+  }
+  float ms = 0;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  if (buf) cudaFree(buf);
+  if (out) cudaFree(out);
+  if (e != cudaSuccess) return cuda_fail(e, "st_measure_l2_read");
+  *gbs = (double)n4 * 16.0 * passes / (ms / 1000.0) / 1e9;
   return ST_OK;
 }
 

@@ -26,7 +26,7 @@ EDGE_SILHOUETTE, EDGE_ALL = 0, 1
 
 EXPORTED = ["st_scene_create", "st_scene_destroy", "st_refit", "st_rebuild", "st_set_face_params", "st_render",
             "st_render_backward", "st_trace_closest", "st_get_stats", "st_debug_bvh", "st_build_bvh_noalloc",
-            "st_last_error"]
+            "st_measure_l2_read", "st_last_error"]
 
 
 class StError(RuntimeError):
@@ -57,7 +57,7 @@ class SceneDesc(C.Structure):
 class RenderOpts(C.Structure):
     _fields_ = [("edge_term", C.c_int), ("edge_mode", C.c_int), ("edge_spp", C.c_int), ("mode", C.c_int),
                 ("use_graph", C.c_int), ("chunk_paths", C.c_int), ("time_kernels", C.c_int),
-                ("count_visits", C.c_int)]
+                ("count_visits", C.c_int), ("persist_blocks", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -91,6 +91,7 @@ def lib():
         L.st_get_stats.argtypes = [P, P]
         L.st_debug_bvh.argtypes = [P, P, P]
         L.st_build_bvh_noalloc.argtypes = [P, P, I, I, P, P, P, P]
+        L.st_measure_l2_read.argtypes = [C.c_longlong, I, P, P]
         L.st_last_error.restype = C.c_char_p
         L.st_last_error.argtypes = []
         for name in EXPORTED[:-1]:
@@ -127,7 +128,7 @@ def n_pixels(views) -> int:
 
 
 def make_opts(**kw) -> RenderOpts:
-    o = RenderOpts(0, EDGE_SILHOUETTE, 0, MODE_BATCHED, 1, 0, 0, 0)
+    o = RenderOpts(0, EDGE_SILHOUETTE, 0, MODE_BATCHED, 1, 0, 0, 0, 0)
     for k, v in kw.items():
         if k == "mode" and isinstance(v, str):
             v = {"batched": MODE_BATCHED, "per_view": MODE_PER_VIEW}[v]
@@ -240,6 +241,13 @@ class Scene:
         leaf = np.zeros(self.nf, np.int32)
         _check(lib().st_debug_bvh(self.handle, nodes.ctypes.data, leaf.ctypes.data))
         return nodes[: self.nf - 1], leaf
+
+
+def measure_l2_read(bytes_=32 << 20, passes=64, stream=None) -> float:
+    """L2-resident read bandwidth in GB/s (library measurement utility)."""
+    g = C.c_double()
+    _check(lib().st_measure_l2_read(bytes_, passes, _stream(stream), C.byref(g)))
+    return g.value
 
 
 class STRender(torch.autograd.Function):

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     src = open(os.path.join(ROOT, "include", "st.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(st_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(st_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_header_declares_the_boundary():
@@ -29,7 +29,7 @@ def test_library_builds_loads_and_exports_all_symbols():
     for n in _declared():
         assert hasattr(lib, n), n
     out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
-    exported = set(re.findall(r" T (st_[a-z_]+)", out))
+    exported = set(re.findall(r" T (st_[a-z0-9_]+)", out))
     assert set(_declared()) <= exported
 
 
@@ -53,5 +53,5 @@ def test_structure_sizes_match_c_layout():
     from paper_2012_03939_gb300 import st
     # st_view: 10 floats, 3 ints, 4 bytes padding, one long long
     assert ctypes.sizeof(st.View) == 10 * 4 + 3 * 4 + 4 + 8
-    assert ctypes.sizeof(st.RenderOpts) == 8 * 4
+    assert ctypes.sizeof(st.RenderOpts) == 9 * 4
     assert ctypes.sizeof(st.PointLight) == 24
