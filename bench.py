@@ -223,6 +223,7 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     from paper_2012_03939_gb300 import st
+    from paper_2012_03939_gb300.dist import max_over_ranks
 
     sc = S.make(args.workload)
     if args.views:
@@ -302,11 +303,7 @@ def run_ours(args):
             b.record(stream)
         torch.cuda.synchronize()
         ms = sum(a.elapsed_time(b) for a, b in ev)
-        if world > 1:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return max_over_ranks(ms, device="cuda")
 
     edge_on = 0 if args.workload == "env" else 1     # the environment workload is forward + interior adjoint
     tuned = None
