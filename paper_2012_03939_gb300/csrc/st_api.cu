@@ -178,6 +178,7 @@ struct Plan {
   std::vector<Seg> segs;
   std::vector<std::pair<long long, long long>> view_range;  // job range per view (per-view mode)
   long long total = 0;
+  long long pixels = 0;       // sum of W*H: the primary-visibility bin space
   bool interior = false, edges = false;
   st_render_opts o{};
 };
@@ -191,7 +192,7 @@ st_render_opts default_opts() {
 }
 
 void free_engine(Engine& e) {
-  dfree(e.o); dfree(e.d); dfree(e.thr); dfree(e.rad); dfree(e.ctr); dfree(e.hit); dfree(e.origin);
+  dfree(e.o); dfree(e.d); dfree(e.thr); dfree(e.rad); dfree(e.ctr); dfree(e.hit); dfree(e.origin); dfree(e.brange);
   dfree(e.q0); dfree(e.q1); dfree(e.qs); dfree(e.sh_dir); dfree(e.sh_c);
   dfree(e.r0); dfree(e.r1); dfree(e.r2); dfree(e.r3); dfree(e.esc); dfree(e.nb); dfree(e.cnt); dfree(e.stat);
   e = Engine();
@@ -218,6 +219,7 @@ st_status ensure_engine(st_scene* s, int Q, int B, int NS, bool records) {
   auto chk = [&](cudaError_t x) { if (x != cudaSuccess && r == cudaSuccess) r = x; };
   chk(dalloc(&e.o, q, &acc)); chk(dalloc(&e.d, q, &acc)); chk(dalloc(&e.thr, q, &acc)); chk(dalloc(&e.rad, q, &acc));
   chk(dalloc(&e.ctr, q, &acc)); chk(dalloc(&e.hit, q, &acc)); chk(dalloc(&e.origin, q, &acc));
+  chk(dalloc(&e.brange, q, &acc));
   chk(dalloc(&e.q0, q, &acc)); chk(dalloc(&e.q1, q, &acc)); chk(dalloc(&e.qs, q, &acc));
   chk(dalloc(&e.sh_dir, q * std::max(nNS, 1), &acc)); chk(dalloc(&e.sh_c, q * std::max(nNS, 1), &acc));
   if (nrec) {
@@ -261,6 +263,31 @@ st_status ensure_tables(st_scene* s, int n_views, int n_segs, bool edges) {
   return ST_OK;
 }
 
+st_status ensure_bins(st_scene* s, const Plan& p) {
+  long long P = p.pixels;
+  long long want = std::max<long long>(8 * P, 1 << 20);
+  if (s->bin_total_host && *s->bin_total_host > s->bin_cap) want = std::max(want, 2LL * *s->bin_total_host);
+  want = std::min<long long>(want, 0x7ffffff0LL);   // a clamped total (INT_MAX) always exceeds it
+  bool grow = P > s->bin_pix_cap || (int)p.views.size() > s->bin_views_cap || want > s->bin_cap;
+  if (!grow) return ST_OK;
+  cudaDeviceSynchronize();
+  drop_graphs(s);
+  long long nP = std::max(P, s->bin_pix_cap), nC = std::max(want, s->bin_cap);
+  int nV = std::max((int)p.views.size(), s->bin_views_cap);
+  dfree(s->bin_start); dfree(s->bin_cur); dfree(s->bin_list); dfree(s->bin_ok); dfree(s->bin_part);
+  long long nb = (nP + 4095) / 4096;
+  if (dalloc(&s->bin_start, (size_t)nP + 1) != cudaSuccess || dalloc(&s->bin_cur, (size_t)nP) != cudaSuccess ||
+      dalloc(&s->bin_list, (size_t)nC) != cudaSuccess || dalloc(&s->bin_ok, (size_t)nV) != cudaSuccess ||
+      dalloc(&s->bin_part, (size_t)nb) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ST_ERR_OOM, "primary-visibility bins");
+  }
+  if (!s->bin_total_host) cudaMallocHost((void**)&s->bin_total_host, sizeof(int));
+  if (s->bin_total_host) *s->bin_total_host = 0;
+  s->bin_pix_cap = nP; s->bin_cap = nC; s->bin_views_cap = nV;
+  return ST_OK;
+}
+
 KCtx make_ctx(st_scene* s, const Plan& p) {
   KCtx c;
   c.V = s->verts; c.F = s->faces; c.P = s->params; c.nodes = s->nodes4; c.tri = s->tri; c.nf = s->nf;
@@ -268,6 +295,8 @@ KCtx make_ctx(st_scene* s, const Plan& p) {
   c.env = s->env; c.brdf = s->brdf;
   c.edge_v = s->edge_v; c.edge_f = s->edge_f; c.n_edges = s->n_edges; c.edge_mode = p.o.edge_mode;
   c.edge_flag = s->edge_flag; c.edge_cand = s->edge_cand; c.edge_ncand = s->edge_ncand;
+  c.bin_start = s->bin_start; c.bin_list = s->bin_list; c.bin_cur = s->bin_cur; c.bin_ok = s->bin_ok;
+  c.bin_cap = s->bin_cap; c.bin_pixels = p.pixels;
   c.views = s->d_views; c.segs = s->d_segs; c.n_segs = (int)p.segs.size();
   c.args = s->d_args; c.B = p.B; c.e = s->eng; c.e.records = p.kind == 1; c.err = s->d_err;
   return c;
@@ -371,6 +400,23 @@ st_status enqueue_call(st_scene* s, const Plan& p, int Q, cudaStream_t st, bool 
     for (auto& r : m)
       ST_CUDA(cudaMemsetAsync(s->image_ptr + 3 * r.first, 0, sizeof(float) * 3 * (r.second - r.first), st));
   }
+  {
+    // primary-visibility bins of every view: count, scan, fill
+    long long P = p.pixels;
+    int nv = (int)p.views.size();
+    long long nb = (P + 4095) / 4096;
+    dim3 g((s->nf + 127) / 128, (unsigned)nv);
+    ST_CUDA(cudaMemsetAsync(s->bin_cur, 0, sizeof(int) * P, st));
+    k_fill_int<<<(nv + 127) / 128, 128, 0, st>>>(s->bin_ok, nv, 1);
+    k_bin<0><<<g, 128, 0, st>>>(c, nv, s->bin_ok);
+    k_scan_blocks<<<(unsigned)nb, SCAN_BLOCK, 0, st>>>(s->bin_cur, s->bin_start, P, s->bin_part);
+    k_scan_parts<<<1, SCAN_BLOCK, 0, st>>>(s->bin_part, (int)nb, s->bin_start, P);
+    k_scan_add<<<(unsigned)nb, SCAN_BLOCK, 0, st>>>(s->bin_start, P, s->bin_part);
+    ST_CUDA(cudaMemsetAsync(s->bin_cur, 0, sizeof(int) * P, st));
+    k_bin<1><<<g, 128, 0, st>>>(c, nv, s->bin_ok);
+    ST_CUDA(cudaMemcpyAsync(s->bin_total_host, s->bin_start + P, sizeof(int), cudaMemcpyDeviceToHost, st));
+    s->launches += 6;
+  }
   if (p.edges) {
     dim3 g((s->n_edges + 255) / 256, (unsigned)p.views.size());
     k_edge_flags<<<g, 256, 0, st>>>(c, (int)p.views.size());
@@ -401,7 +447,7 @@ st_status enqueue_call(st_scene* s, const Plan& p, int Q, cudaStream_t st, bool 
 std::vector<long long> graph_key(const Plan& p, int Q, const st_scene* s) {
   std::vector<long long> k = {p.kind, p.B, (long long)p.views.size(), Q, p.o.edge_term, p.o.edge_mode, p.o.edge_spp,
                               p.interior, p.edges, (long long)(size_t)s->image_ptr, p.o.count_visits,
-                              p.o.persist_blocks};
+                              p.o.persist_blocks, s->bin_cap};
   for (auto& v : p.views) { k.push_back(v.W); k.push_back(v.H); k.push_back(v.spp); k.push_back(v.pix_off); }
   return k;
 }
@@ -428,6 +474,8 @@ st_status plan_call(st_scene* s, const st_view* views, int n_views, int default_
     if ((long long)v.width * v.height > (1LL << 31) || v.pixel_offset + (long long)v.width * v.height > (1LL << 32))
       return fail(ST_ERR_UNSUPPORTED, "view too large for 32-bit pixel counters");
     p.views.push_back(make_view(v, spp));
+    p.views.back().bin_base = p.pixels;
+    p.pixels += (long long)v.width * v.height;
     long long start = base;
     long long cam = (long long)v.width * v.height * spp;
     if (kind == 0 || p.interior) {
@@ -452,6 +500,8 @@ st_status plan_call(st_scene* s, const st_view* views, int n_views, int default_
 
 st_status run_call(st_scene* s, Plan& p, const CallArgs& args, cudaStream_t st) {
   st_status r = ensure_tables(s, (int)p.views.size(), (int)p.segs.size(), p.edges);
+  if (r != ST_OK) return r;
+  r = ensure_bins(s, p);
   if (r != ST_OK) return r;
   long long Q64 = p.o.chunk_paths > 0 ? p.o.chunk_paths : DEFAULT_CHUNK;
   Q64 = std::min<long long>(Q64, std::max<long long>(p.total, SEG_ALIGN));
@@ -522,6 +572,8 @@ void destroy(st_scene* s) {
   dfree(s->nodes4); dfree(s->src4); dfree(s->q4); dfree(s->c4);
   dfree(s->lights); dfree(s->env_tex); dfree(s->env_alias); dfree(s->edge_v); dfree(s->edge_f);
   dfree(s->edge_flag); dfree(s->edge_cand); dfree(s->edge_ncand); dfree(s->d_views); dfree(s->d_segs);
+  dfree(s->bin_start); dfree(s->bin_cur); dfree(s->bin_list); dfree(s->bin_ok); dfree(s->bin_part);
+  if (s->bin_total_host) cudaFreeHost(s->bin_total_host);
   dfree(s->d_args); dfree(s->d_err);
   for (auto& e : s->ev) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
   if (s->cap_stream) cudaStreamDestroy(s->cap_stream);

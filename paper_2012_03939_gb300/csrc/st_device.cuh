@@ -69,6 +69,7 @@ struct DevView {
   int W, H, spp;
   uint32_t off;            // low 32 bits of pixel_offset (counter word)
   long long pix_off;       // packed-image row of pixel (0, 0)
+  long long bin_base;      // first pixel of the view in the primary-visibility bins
 };
 
 __device__ __forceinline__ float3 cam_dir(const DevView& v, float px, float py) {

@@ -37,6 +37,7 @@ struct Engine {
   float4 *o = nullptr, *d = nullptr, *thr = nullptr, *rad = nullptr;
   int4* ctr = nullptr;        // (c0, c1, stream, job kind)
   int2* hit = nullptr;        // (face, t bits)
+  int2* brange = nullptr;     // primary rays: range of the pixel's bin list, (-1, -1) = use the BVH
   int* origin = nullptr;
   int *q0 = nullptr, *q1 = nullptr, *qs = nullptr;
   float4 *sh_dir = nullptr, *sh_c = nullptr;  // [NS][Q]
@@ -98,6 +99,16 @@ struct st_scene {
   int* edge_cand = nullptr;      // [views * E]
   int* edge_ncand = nullptr;     // [views]
   int edge_cap_views = 0;
+  // primary-visibility bins: per view pixel, the leaves whose screen box covers it
+  int* bin_start = nullptr;      // [P + 1] exclusive prefix of the counts
+  int* bin_cur = nullptr;        // [P] counts, then fill cursors
+  int* bin_list = nullptr;       // [bin_cap] leaf indices
+  int* bin_ok = nullptr;         // [views] 1 = the view's primary rays may use the bins
+  int* bin_part = nullptr;       // scan block sums
+  long long bin_pix_cap = 0;     // P capacity
+  long long bin_cap = 0;         // list capacity
+  int bin_views_cap = 0;
+  int* bin_total_host = nullptr; // pinned: list length the last call needed
   // per-call tables
   st::DevView* d_views = nullptr;
   st::Seg* d_segs = nullptr;

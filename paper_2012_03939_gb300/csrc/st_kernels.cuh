@@ -38,6 +38,12 @@ struct KCtx {
   int* edge_flag;
   int* edge_cand;
   int* edge_ncand;
+  const int* bin_start;   // primary-visibility bins (see k_bin)
+  const int* bin_list;    // leaf indices per pixel
+  int* bin_cur;
+  const int* bin_ok;
+  long long bin_cap;
+  long long bin_pixels;
   const DevView* views;
   const Seg* segs;
   int n_segs;
@@ -186,6 +192,133 @@ __global__ void k_edge_compact(KCtx c) {
   if (threadIdx.x == 1023) c.edge_ncand[vi] = part[1023];
 }
 
+// ------------------------------------------------------------------ primary-visibility bins
+// Every primary ray leaves the eye, so the triangles it can hit are those whose
+// projection covers its screen point. Per view and pixel the bins list the
+// leaves whose conservative screen box (padded by BIN_PAD pixels) covers the
+// pixel; a primary ray tests its pixel's list with the same watertight test
+// and tie rule as the traversal, which therefore finds the same closest hit.
+// A view with a triangle straddling the eye plane (projection undefined) keeps
+// the BVH for its primary rays.
+constexpr float BIN_PAD = 0.02f;
+constexpr int BIN_MAX_BOX = 1 << 16;   // a larger screen box sends its view back to the BVH
+
+
+// 0: cannot be hit from the eye or off screen; 1: box in (x0..x1, y0..y1);
+// -1: view must use the BVH
+__device__ __forceinline__ int leaf_screen_box(const DevView& v, float4 a, float4 b, float4 c, int& x0, int& y0,
+                                               int& x1, int& y1) {
+  float3 P[3] = {xyz(a), xyz(b), xyz(c)};
+  int front = 0, behind = 0;
+  float px[3], py[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    float3 rel = P[k] - v.eye;
+    float z = dot3(rel, v.fwd);
+    front += z > Z_NEAR;
+    behind += z <= 0.0f;
+    float zz = fmaxf(z, Z_NEAR);
+    px[k] = (dot3(rel, v.right) / (zz * v.kx) + 1.0f) * (float)v.W * 0.5f;
+    py[k] = (1.0f - dot3(rel, v.up) / (zz * v.ky)) * (float)v.H * 0.5f;
+  }
+  if (behind == 3) return 0;
+  if (front < 3) return -1;
+  float lx = fminf(fminf(px[0], px[1]), px[2]) - BIN_PAD, hx = fmaxf(fmaxf(px[0], px[1]), px[2]) + BIN_PAD;
+  float ly = fminf(fminf(py[0], py[1]), py[2]) - BIN_PAD, hy = fmaxf(fmaxf(py[0], py[1]), py[2]) + BIN_PAD;
+  if (hx < 0.0f || hy < 0.0f || lx >= (float)v.W || ly >= (float)v.H) return 0;
+  x0 = max(0, (int)floorf(lx)); y0 = max(0, (int)floorf(ly));
+  x1 = min(v.W - 1, (int)floorf(hx)); y1 = min(v.H - 1, (int)floorf(hy));
+  if ((long long)(x1 - x0 + 1) * (y1 - y0 + 1) > BIN_MAX_BOX) return -1;
+  return 1;
+}
+
+// fill = 0: count leaves per pixel; fill = 1: write them at start + cursor
+template <int FILL>
+__global__ void k_bin(KCtx c, int n_views, int* ok) {
+  int li = blockIdx.x * blockDim.x + threadIdx.x;
+  int vi = blockIdx.y;
+  if (li >= c.nf || vi >= n_views) return;
+  DevView v = c.views[vi];
+  int x0, y0, x1, y1;
+  int r = leaf_screen_box(v, __ldg(&c.tri[3 * li]), __ldg(&c.tri[3 * li + 1]), __ldg(&c.tri[3 * li + 2]), x0, y0, x1,
+                          y1);
+  if (r < 0) { if (!FILL) atomicAnd(&ok[vi], 0); return; }
+  if (r == 0) return;
+  if (FILL && c.bin_start[c.bin_pixels] > c.bin_cap) return;   // overflow: every view uses the BVH
+  for (int y = y0; y <= y1; ++y)
+    for (int x = x0; x <= x1; ++x) {
+      long long p = v.bin_base + (long long)y * v.W + x;
+      int k = atomicAdd(&c.bin_cur[p], 1);
+      if (FILL) const_cast<int*>(c.bin_list)[c.bin_start[p] + k] = li;
+    }
+}
+
+__global__ void k_fill_int(int* a, int n, int value) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = value;
+}
+
+// exclusive scan of n counts into out[0..n] (out[n] = total): per-block scans,
+// one block for the block sums, then the add-back
+constexpr int SCAN_BLOCK = 1024, SCAN_ITEMS = 4;
+__global__ void k_scan_blocks(const int* in, int* out, long long n, int* part) {
+  __shared__ int sh[SCAN_BLOCK];
+  long long base = (long long)blockIdx.x * SCAN_BLOCK * SCAN_ITEMS + (long long)threadIdx.x * SCAN_ITEMS;
+  int v[SCAN_ITEMS];
+  int s = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) { v[k] = base + k < n ? in[base + k] : 0; s += v[k]; }
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 1; off < SCAN_BLOCK; off <<= 1) {
+    int t = threadIdx.x >= off ? sh[threadIdx.x - off] : 0;
+    __syncthreads();
+    sh[threadIdx.x] += t;
+    __syncthreads();
+  }
+  int run = sh[threadIdx.x] - s;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    if (base + k < n) out[base + k] = run;
+    run += v[k];
+  }
+  if (threadIdx.x == SCAN_BLOCK - 1) part[blockIdx.x] = sh[SCAN_BLOCK - 1];
+}
+
+__global__ void k_scan_parts(int* part, int nb, int* out, long long n) {
+  __shared__ int sh[SCAN_BLOCK];
+  int per = (nb + SCAN_BLOCK - 1) / SCAN_BLOCK;
+  int b = threadIdx.x * per, e = min(b + per, nb);
+  long long s = 0;
+  for (int i = b; i < e; ++i) s += part[i];
+  sh[threadIdx.x] = (int)min(s, (long long)0x7fffffff);
+  __syncthreads();
+  for (int off = 1; off < SCAN_BLOCK; off <<= 1) {
+    int t = threadIdx.x >= off ? sh[threadIdx.x - off] : 0;
+    __syncthreads();
+    sh[threadIdx.x] = (int)min((long long)sh[threadIdx.x] + t, (long long)0x7fffffff);
+    __syncthreads();
+  }
+  long long run = sh[threadIdx.x] - s;
+  for (int i = b; i < e; ++i) { int c2 = part[i]; part[i] = (int)run; run += c2; }
+  if (threadIdx.x == SCAN_BLOCK - 1) out[n] = sh[SCAN_BLOCK - 1];
+}
+
+__global__ void k_scan_add(int* out, long long n, const int* part) {
+  long long i = (long long)blockIdx.x * SCAN_BLOCK * SCAN_ITEMS + threadIdx.x;
+  int add = part[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k, i += SCAN_BLOCK)
+    if (i < n) out[i] += add;
+}
+
+__device__ __forceinline__ int2 bin_range(const KCtx& c, int vi, const DevView& v, int x, int y) {
+  if (c.bin_start == nullptr || !c.bin_ok[vi] || c.bin_start[c.bin_pixels] > c.bin_cap) return make_int2(-1, -1);
+  if (x < 0 || y < 0 || x >= v.W || y >= v.H) return make_int2(-1, -1);
+  long long p = v.bin_base + (long long)y * v.W + x;
+  return make_int2(c.bin_start[p], c.bin_start[p + 1]);
+}
+
 // ------------------------------------------------------------------ chunk stages
 __global__ void k_reset(int* cnt) {
   for (int i = threadIdx.x; i < CNT_SIZE; i += blockDim.x) cnt[i] = 0;
@@ -197,6 +330,7 @@ __global__ void k_raygen(KCtx c, long long j0, int n) {
   bool ok = false;
   float3 o = mk3(0, 0, 0), d = mk3(0, 0, 1);
   int4 ct = make_int4(0, 0, 0, 0);
+  int2 br = make_int2(-1, -1);
   if (i < n) {
     long long job = j0 + i;
     int si = find_seg(c.segs, c.n_segs, job);
@@ -215,6 +349,7 @@ __global__ void k_raygen(KCtx c, long long j0, int n) {
           d = cam_dir(v, (float)x + unif(u.x), (float)y + unif(u.y));
           o = v.eye;
           ct = make_int4((int)c0, s, 0, 0);
+          br = bin_range(c, sg.view, v, x, y);
           ok = true;
         } else {
           // block of 64 jobs: minus sides of samples 32b..32b+31, then their plus sides
@@ -224,8 +359,10 @@ __global__ void k_raygen(KCtx c, long long j0, int n) {
           if (k < sg.n_samples) es = edge_sample(c, sg.view, v, k, sg.n_samples, key);
           if (es.valid) {
             float sg2 = (local & 32) ? EDGE_EPS : -EDGE_EPS;
-            d = cam_dir(v, es.S.x + sg2 * es.ns.x, es.S.y + sg2 * es.ns.y);
+            float sx = es.S.x + sg2 * es.ns.x, sy = es.S.y + sg2 * es.ns.y;
+            d = cam_dir(v, sx, sy);
             o = v.eye;
+            br = bin_range(c, sg.view, v, (int)floorf(sx), (int)floorf(sy));
             ct = make_int4((int)(uint32_t)k, (int)v.off, 2, 1);
             ok = true;
           }
@@ -244,6 +381,7 @@ __global__ void k_raygen(KCtx c, long long j0, int n) {
       E.thr[i] = make_float4(1, 1, 1, 0);
       E.origin[i] = -1;
       E.ctr[i] = ct;
+      E.brange[i] = br;
     }
   }
   int q = warp_append(&E.cnt[CNT_EXT + 0], ok);
@@ -276,9 +414,23 @@ __global__ void __launch_bounds__(EXT_BLOCK) k_extend(KCtx c, int b) {
   if (live_) {
     int slot = q[qi_];
     float4 o = E.o[slot], d = E.d[slot];
-    float t;
-    int f = trace_bvh<false, STATS>(c.nodes, c.tri, c.nf, xyz(o), xyz(d), __int_as_float(0x7f800000), E.origin[slot],
-                                    t, sstack + threadIdx.x, c.err, &ts);
+    float t = __int_as_float(0x7f800000);
+    int f = -1;
+    int2 br = b == 0 ? E.brange[slot] : make_int2(-1, -1);
+    if (br.x >= 0) {
+      RayPre rp = ray_pre(xyz(o), xyz(d));
+      for (int k = br.x; k < br.y; ++k) {
+        int li = __ldg(&c.bin_list[k]);
+        float4 ta = __ldg(&c.tri[3 * li]), tb = __ldg(&c.tri[3 * li + 1]), tc = __ldg(&c.tri[3 * li + 2]);
+        int fid = __float_as_int(ta.w);
+        float th = tri_test(rp, xyz(ta), xyz(tb), xyz(tc), t * 1.0000001f + 1e-30f);
+        if (th > 0.0f && (th < t || (th == t && fid < f))) { t = th; f = fid; }
+        if (STATS) ts.tests++;
+      }
+    } else {
+      f = trace_bvh<false, STATS>(c.nodes, c.tri, c.nf, xyz(o), xyz(d), __int_as_float(0x7f800000), E.origin[slot], t,
+                                  sstack + threadIdx.x, c.err, &ts);
+    }
     E.hit[slot] = make_int2(f, __float_as_int(t));
   }
   ST_WARP_LOOP_END

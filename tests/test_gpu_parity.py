@@ -312,3 +312,19 @@ def test_empty_and_degenerate_views(st):
                         np.array([[1, 0, 0]], np.int32))
     assert_image_parity(img[35:36], ref, what="1x1")
     scene.close()
+
+
+def test_primary_bins_and_bvh_fallback_views(st):
+    # one view outside the mesh (primary rays use the screen-space bins) and one
+    # inside it, where triangles straddle the eye plane and the view's primary
+    # rays fall back to the BVH; both match the oracle
+    sc = S.tiny()
+    out = S.View((0.0, 0.0, 3.0), (0.0, 0.0, 0.0), (0.0, 1.0, 0.0), 45.0, 30, 22, 3, 0)
+    inside = S.View((0.1, 0.2, 0.3), (0.0, 0.0, -2.0), (0.0, 1.0, 0.0), 90.0, 27, 31, 3, 30 * 22)
+    sc.views = [out, inside]
+    sc.light_pos = np.array([[0.0, 0.0, 0.0], [0.0, 2.1, 2.1]], np.float32)
+    sc.light_intensity = np.array([[0.5, 0.5, 0.5], [9.0, 9.0, 9.0]], np.float32)
+    img, stats = gpu_image(st, sc, 2, 41)
+    ref, seg = O.render_pixels(O.OracleScene(sc), O.params(2, 41), O.all_pixels(sc))
+    assert_image_parity(img, ref, what="bins + fallback")
+    assert stats["extension_rays"] + stats["shadow_rays"] == seg
