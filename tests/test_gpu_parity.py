@@ -328,3 +328,26 @@ def test_primary_bins_and_bvh_fallback_views(st):
     ref, seg = O.render_pixels(O.OracleScene(sc), O.params(2, 41), O.all_pixels(sc))
     assert_image_parity(img, ref, what="bins + fallback")
     assert stats["extension_rays"] + stats["shadow_rays"] == seg
+
+
+@pytest.mark.parametrize("name,npix,views", [("batched", 24, None), ("scale", 6, 2)])
+def test_full_size_gradient_in_bench_configuration(st, name, npix, views):
+    # the benchmark's launch configuration (batched, CUDA graph, 8M-path chunks, silhouette
+    # edge term) at full size; dL/dI nonzero on a pixel sample so the oracle can follow
+    sc = S.make(name)
+    if views:
+        sc = sc.subset_views(range(views))
+    pix = sample_pixels(sc, npix, seed=13)
+    rows = rows_of(sc, pix)
+    w = np.zeros((sc.n_pixels, 3))
+    w[rows] = np.random.default_rng(14).normal(size=(len(pix), 3))
+    opts = st.make_opts(mode="batched", use_graph=1, chunk_paths=1 << 23, edge_term=1, edge_mode=0)
+    dV, dF = _grad_gpu(st, sc, sc.max_bounces, 2025, w, opts)
+    osc = O.OracleScene(sc)
+    prm = O.params(sc.max_bounces, 2025, edge_mode=0)
+    rv, rf, _ = O.grad_pixels(osc, prm, pix, w[rows])
+    ev, _ = O.edge_grad(osc, prm, w)
+    r_int = rel_l2([dF], [rf])                      # parameters: interior term only
+    r_tot = rel_l2([dV, dF], [rv + ev, rf])         # vertices: interior + edge term
+    assert r_int <= GRAD_REL, r_int
+    assert r_tot <= 5e-3, r_tot
