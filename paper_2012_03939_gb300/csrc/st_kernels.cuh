@@ -195,8 +195,9 @@ __global__ void k_edge_compact(KCtx c) {
 // ------------------------------------------------------------------ primary-visibility bins
 // Every primary ray leaves the eye, so the triangles it can hit are those whose
 // projection covers its screen point. Per view and pixel the bins list the
-// leaves whose conservative screen box (padded by BIN_PAD pixels) covers the
-// pixel; a primary ray tests its pixel's list with the same watertight test
+// leaves whose projection, padded by BIN_PAD pixels (plus a relative rounding
+// allowance), may overlap the pixel (screen box, then edge functions at the
+// pixel's most-inside corner); a primary ray tests its pixel's list with the same watertight test
 // and tie rule as the traversal, which therefore finds the same closest hit.
 // A view with a triangle straddling the eye plane (projection undefined) keeps
 // the BVH for its primary rays.
@@ -204,10 +205,17 @@ constexpr float BIN_PAD = 0.02f;
 constexpr int BIN_MAX_BOX = 1 << 16;   // a larger screen box sends its view back to the BVH
 
 
+// Screen-space edge functions of a projected triangle, oriented so the inside
+// is >= 0, for a conservative pixel-overlap test.
+struct ScreenTri {
+  float a[3], b[3], c[3];
+  bool degenerate;
+};
+
 // 0: cannot be hit from the eye or off screen; 1: box in (x0..x1, y0..y1);
 // -1: view must use the BVH
 __device__ __forceinline__ int leaf_screen_box(const DevView& v, float4 a, float4 b, float4 c, int& x0, int& y0,
-                                               int& x1, int& y1) {
+                                               int& x1, int& y1, ScreenTri& et) {
   float3 P[3] = {xyz(a), xyz(b), xyz(c)};
   int front = 0, behind = 0;
   float px[3], py[3];
@@ -229,7 +237,33 @@ __device__ __forceinline__ int leaf_screen_box(const DevView& v, float4 a, float
   x0 = max(0, (int)floorf(lx)); y0 = max(0, (int)floorf(ly));
   x1 = min(v.W - 1, (int)floorf(hx)); y1 = min(v.H - 1, (int)floorf(hy));
   if ((long long)(x1 - x0 + 1) * (y1 - y0 + 1) > BIN_MAX_BOX) return -1;
+  float area = (px[1] - px[0]) * (py[2] - py[0]) - (py[1] - py[0]) * (px[2] - px[0]);
+  et.degenerate = !(fabsf(area) > 1e-6f);
+  float sgn = area > 0.0f ? 1.0f : -1.0f;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    int k1 = k == 2 ? 0 : k + 1;
+    // E(x, y) = (x - px_k)(py_k1 - py_k) - (y - py_k)(px_k1 - px_k), sign-normalised
+    et.a[k] = -sgn * (py[k1] - py[k]);
+    et.b[k] = sgn * (px[k1] - px[k]);
+    et.c[k] = -(et.a[k] * px[k] + et.b[k] * py[k]);
+  }
   return 1;
+}
+
+// can any point of pixel (x, y), padded by BIN_PAD, lie inside the triangle?
+__device__ __forceinline__ bool pixel_may_overlap(const ScreenTri& et, int x, int y) {
+  if (et.degenerate) return true;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    float cx = et.a[k] > 0.0f ? (float)(x + 1) : (float)x;   // the pixel corner where E is largest
+    float cy = et.b[k] > 0.0f ? (float)(y + 1) : (float)y;
+    float e = et.a[k] * cx + et.b[k] * cy + et.c[k];
+    float tol = BIN_PAD * (fabsf(et.a[k]) + fabsf(et.b[k])) + 1e-4f * (fabsf(et.a[k] * cx) + fabsf(et.b[k] * cy) +
+                                                                      fabsf(et.c[k]));
+    if (e < -tol) return false;
+  }
+  return true;
 }
 
 // fill = 0: count leaves per pixel; fill = 1: write them at start + cursor
@@ -240,13 +274,15 @@ __global__ void k_bin(KCtx c, int n_views, int* ok) {
   if (li >= c.nf || vi >= n_views) return;
   DevView v = c.views[vi];
   int x0, y0, x1, y1;
+  ScreenTri et;
   int r = leaf_screen_box(v, __ldg(&c.tri[3 * li]), __ldg(&c.tri[3 * li + 1]), __ldg(&c.tri[3 * li + 2]), x0, y0, x1,
-                          y1);
+                          y1, et);
   if (r < 0) { if (!FILL) atomicAnd(&ok[vi], 0); return; }
   if (r == 0) return;
   if (FILL && c.bin_start[c.bin_pixels] > c.bin_cap) return;   // overflow: every view uses the BVH
   for (int y = y0; y <= y1; ++y)
     for (int x = x0; x <= x1; ++x) {
+      if (!pixel_may_overlap(et, x, y)) continue;
       long long p = v.bin_base + (long long)y * v.W + x;
       int k = atomicAdd(&c.bin_cur[p], 1);
       if (FILL) const_cast<int*>(c.bin_list)[c.bin_start[p] + k] = li;
