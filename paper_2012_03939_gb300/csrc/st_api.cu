@@ -388,17 +388,8 @@ st_status enqueue_call(st_scene* s, const Plan& p, int Q, cudaStream_t st, bool 
   KCtx c = make_ctx(s, p);
   ST_CUDA(cudaMemsetAsync(s->eng.stat, 0, sizeof(unsigned long long) * STAT_SIZE, st));
   if (p.kind == 0) {
-    // zero each view's rows, merging adjacent ranges
-    std::vector<std::pair<long long, long long>> rg;
-    for (auto& v : p.views) rg.push_back({v.pix_off, v.pix_off + (long long)v.W * v.H});
-    std::sort(rg.begin(), rg.end());
-    std::vector<std::pair<long long, long long>> m;
-    for (auto& r : rg) {
-      if (!m.empty() && r.first <= m.back().second) m.back().second = std::max(m.back().second, r.second);
-      else m.push_back(r);
-    }
-    for (auto& r : m)
-      ST_CUDA(cudaMemsetAsync(s->image_ptr + 3 * r.first, 0, sizeof(float) * 3 * (r.second - r.first), st));
+    k_zero_views<<<(unsigned)((p.pixels + 255) / 256), 256, 0, st>>>(c, (int)p.views.size());
+    s->launches++;
   }
   {
     // primary-visibility bins of every view: count, scan, fill
@@ -446,7 +437,7 @@ st_status enqueue_call(st_scene* s, const Plan& p, int Q, cudaStream_t st, bool 
 
 std::vector<long long> graph_key(const Plan& p, int Q, const st_scene* s) {
   std::vector<long long> k = {p.kind, p.B, (long long)p.views.size(), Q, p.o.edge_term, p.o.edge_mode, p.o.edge_spp,
-                              p.interior, p.edges, (long long)(size_t)s->image_ptr, p.o.count_visits,
+                              p.interior, p.edges, p.o.count_visits,
                               p.o.persist_blocks, s->bin_cap};
   for (auto& v : p.views) { k.push_back(v.W); k.push_back(v.H); k.push_back(v.spp); k.push_back(v.pix_off); }
   return k;
@@ -492,6 +483,14 @@ st_status plan_call(st_scene* s, const st_view* views, int n_views, int default_
     p.view_range.push_back({start, base});
   }
   p.total = base;
+  {
+    std::vector<std::pair<long long, long long>> rg;
+    for (int i = 0; i < n_views; ++i)
+      rg.push_back({views[i].pixel_offset, views[i].pixel_offset + (long long)views[i].width * views[i].height});
+    std::sort(rg.begin(), rg.end());
+    for (size_t i = 1; i < rg.size(); ++i)
+      if (rg[i].first < rg[i - 1].second) return fail(ST_ERR_INVALID_ARG, "views' pixel ranges overlap");
+  }
   s->last_edge_samples = 0;
   for (auto& sg : p.segs)
     if (sg.kind == 1) s->last_edge_samples += sg.n_samples;
@@ -728,7 +727,6 @@ st_status st_render(st_scene* s, const st_view* views, int n_views, int default_
   st_status r = plan_call(s, views, n_views, default_spp, max_bounces, opts, 0, false, p);
   if (r != ST_OK) return r;
   CallArgs a{(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32), out_image, nullptr, nullptr, nullptr};
-  s->image_ptr = out_image;
   return run_call(s, p, a, (cudaStream_t)stream);
 }
 
@@ -743,7 +741,6 @@ st_status st_render_backward(st_scene* s, const st_view* views, int n_views, int
   st_status r = plan_call(s, views, n_views, default_spp, max_bounces, &o, 1, true, p);
   if (r != ST_OK) return r;
   CallArgs a{(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32), nullptr, dLdI, dV, dF};
-  s->image_ptr = nullptr;
   return run_call(s, p, a, (cudaStream_t)stream);
 }
 

@@ -123,7 +123,6 @@ struct st_scene {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
   int ev_used = 0;
   int sm_count = 0;
-  float* image_ptr = nullptr;    // forward output of the call being planned (graph key)
   long long last_edge_samples = 0;
   int launches = 0;              // kernels enqueued by the last call
   st_stats last{};

@@ -289,6 +289,20 @@ __global__ void k_bin(KCtx c, int n_views, int* ok) {
     }
 }
 
+// zero the image rows of every view (the output pointer comes from the per-call
+// arguments, so a captured graph writes wherever the current call asks)
+__global__ void k_zero_views(KCtx c, int n_views) {
+  long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= c.bin_pixels) return;
+  int lo = 0, hi = n_views - 1, vi = 0;
+  while (lo <= hi) {
+    int mid = (lo + hi) >> 1;
+    if (c.views[mid].bin_base <= p) { vi = mid; lo = mid + 1; } else hi = mid - 1;
+  }
+  float* img = c.args->image + 3 * (c.views[vi].pix_off + (p - c.views[vi].bin_base));
+  img[0] = 0.0f; img[1] = 0.0f; img[2] = 0.0f;
+}
+
 __global__ void k_fill_int(int* a, int n, int value) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) a[i] = value;

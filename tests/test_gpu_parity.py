@@ -166,6 +166,26 @@ def test_batched_per_view_and_graph_agree_bitwise(st):
     assert not np.array_equal(g2, imgs[0])
 
 
+def test_graph_replay_writes_each_calls_output_and_rejects_overlaps(st):
+    # one captured graph serves calls with different output tensors (the image
+    # pointer is a per-call argument, not part of the graph)
+    sc = S.small_variant(S.batched(), n_views=3, max_res=32, spp=2)
+    scene = st.Scene.from_scene(sc)
+    a = torch.full((sc.n_pixels, 3), 7.0, device="cuda")
+    b = torch.full((sc.n_pixels, 3), -3.0, device="cuda")
+    scene.render(sc.views, 3, 5, st.make_opts(use_graph=1), out=a)
+    scene.render(sc.views, 3, 5, st.make_opts(use_graph=1), out=b)
+    ref = scene.render(sc.views, 3, 5, st.make_opts(use_graph=0)).cpu().numpy()
+    np.testing.assert_array_equal(a.cpu().numpy(), ref)
+    np.testing.assert_array_equal(b.cpu().numpy(), ref)
+    import dataclasses
+    bad = [sc.views[0], dataclasses.replace(sc.views[1], pixel_offset=sc.views[0].width * sc.views[0].height - 5)]
+    with pytest.raises(st.StError) as e:
+        scene.render(bad, 3, 5)
+    assert e.value.status == 1
+    scene.close()
+
+
 # ---------------------------------------------------------------------------- adjoint
 def _grad_gpu(st, sc, B, seed, dLdI, opts):
     scene = st.Scene.from_scene(sc)
