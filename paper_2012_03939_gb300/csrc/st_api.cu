@@ -180,6 +180,7 @@ struct Plan {
   long long total = 0;
   long long pixels = 0;       // sum of W*H: the primary-visibility bin space
   bool interior = false, edges = false;
+  bool bins = false;          // build primary-visibility bins (worth it only for many primary rays)
   st_render_opts o{};
 };
 
@@ -295,8 +296,10 @@ KCtx make_ctx(st_scene* s, const Plan& p) {
   c.env = s->env; c.brdf = s->brdf;
   c.edge_v = s->edge_v; c.edge_f = s->edge_f; c.n_edges = s->n_edges; c.edge_mode = p.o.edge_mode;
   c.edge_flag = s->edge_flag; c.edge_cand = s->edge_cand; c.edge_ncand = s->edge_ncand;
-  c.bin_start = s->bin_start; c.bin_list = s->bin_list; c.bin_cur = s->bin_cur; c.bin_ok = s->bin_ok;
+  c.bin_start = p.bins ? s->bin_start : nullptr;   // nullptr: every primary ray traverses the BVH
+  c.bin_list = s->bin_list; c.bin_cur = s->bin_cur; c.bin_ok = s->bin_ok;
   c.bin_cap = s->bin_cap; c.bin_pixels = p.pixels;
+  c.acc = s->acc;
   c.views = s->d_views; c.segs = s->d_segs; c.n_segs = (int)p.segs.size();
   c.args = s->d_args; c.B = p.B; c.e = s->eng; c.e.records = p.kind == 1; c.err = s->d_err;
   return c;
@@ -388,10 +391,10 @@ st_status enqueue_call(st_scene* s, const Plan& p, int Q, cudaStream_t st, bool 
   KCtx c = make_ctx(s, p);
   ST_CUDA(cudaMemsetAsync(s->eng.stat, 0, sizeof(unsigned long long) * STAT_SIZE, st));
   if (p.kind == 0) {
-    k_zero_views<<<(unsigned)((p.pixels + 255) / 256), 256, 0, st>>>(c, (int)p.views.size());
+    k_zero_acc<<<(unsigned)((p.pixels + 255) / 256), 256, 0, st>>>(c);
     s->launches++;
   }
-  {
+  if (p.bins) {
     // primary-visibility bins of every view: count, scan, fill
     long long P = p.pixels;
     int nv = (int)p.views.size();
@@ -432,12 +435,17 @@ st_status enqueue_call(st_scene* s, const Plan& p, int Q, cudaStream_t st, bool 
     st_status x = chunks(0, p.total);
     if (x != ST_OK) return x;
   }
+  if (p.kind == 0) {
+    k_finish_views<<<(unsigned)((p.pixels + 255) / 256), 256, 0, st>>>(c, (int)p.views.size());
+    s->launches++;
+    ST_CUDA(cudaGetLastError());
+  }
   return ST_OK;
 }
 
 std::vector<long long> graph_key(const Plan& p, int Q, const st_scene* s) {
   std::vector<long long> k = {p.kind, p.B, (long long)p.views.size(), Q, p.o.edge_term, p.o.edge_mode, p.o.edge_spp,
-                              p.interior, p.edges, p.o.count_visits,
+                              p.interior, p.edges, p.o.count_visits, p.bins,
                               p.o.persist_blocks, s->bin_cap};
   for (auto& v : p.views) { k.push_back(v.W); k.push_back(v.H); k.push_back(v.spp); k.push_back(v.pix_off); }
   return k;
@@ -483,6 +491,9 @@ st_status plan_call(st_scene* s, const st_view* views, int n_views, int default_
     p.view_range.push_back({start, base});
   }
   p.total = base;
+  // below about a million primary rays the fixed cost of building the bins
+  // (seven launches) exceeds what they save; those calls traverse the BVH
+  p.bins = p.total >= (1LL << 20);
   {
     std::vector<std::pair<long long, long long>> rg;
     for (int i = 0; i < n_views; ++i)
@@ -500,8 +511,21 @@ st_status plan_call(st_scene* s, const st_view* views, int n_views, int default_
 st_status run_call(st_scene* s, Plan& p, const CallArgs& args, cudaStream_t st) {
   st_status r = ensure_tables(s, (int)p.views.size(), (int)p.segs.size(), p.edges);
   if (r != ST_OK) return r;
-  r = ensure_bins(s, p);
-  if (r != ST_OK) return r;
+  if (p.bins) {
+    r = ensure_bins(s, p);
+    if (r != ST_OK) return r;
+  }
+  if (p.kind == 0 && p.pixels > s->acc_cap) {
+    cudaDeviceSynchronize();
+    drop_graphs(s);
+    dfree(s->acc);
+    if (dalloc(&s->acc, 3 * (size_t)p.pixels) != cudaSuccess) {
+      cudaGetLastError();
+      s->acc_cap = 0;
+      return fail(ST_ERR_OOM, "forward accumulation buffer");
+    }
+    s->acc_cap = p.pixels;
+  }
   long long Q64 = p.o.chunk_paths > 0 ? p.o.chunk_paths : DEFAULT_CHUNK;
   Q64 = std::min<long long>(Q64, std::max<long long>(p.total, SEG_ALIGN));
   Q64 = (Q64 + SEG_ALIGN - 1) / SEG_ALIGN * SEG_ALIGN;
@@ -572,6 +596,7 @@ void destroy(st_scene* s) {
   dfree(s->lights); dfree(s->env_tex); dfree(s->env_alias); dfree(s->edge_v); dfree(s->edge_f);
   dfree(s->edge_flag); dfree(s->edge_cand); dfree(s->edge_ncand); dfree(s->d_views); dfree(s->d_segs);
   dfree(s->bin_start); dfree(s->bin_cur); dfree(s->bin_list); dfree(s->bin_ok); dfree(s->bin_part);
+  dfree(s->acc);
   if (s->bin_total_host) cudaFreeHost(s->bin_total_host);
   dfree(s->d_args); dfree(s->d_err);
   for (auto& e : s->ev) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }

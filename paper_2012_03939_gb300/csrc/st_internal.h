@@ -109,6 +109,8 @@ struct st_scene {
   long long bin_cap = 0;         // list capacity
   int bin_views_cap = 0;
   int* bin_total_host = nullptr; // pinned: list length the last call needed
+  double* acc = nullptr;         // [3 * pixels] forward accumulation in double, in sample order
+  long long acc_cap = 0;
   // per-call tables
   st::DevView* d_views = nullptr;
   st::Seg* d_segs = nullptr;

@@ -44,6 +44,7 @@ struct KCtx {
   const int* bin_ok;
   long long bin_cap;
   long long bin_pixels;
+  double* acc;            // per-pixel sample sums (bin-space pixel index), forward calls
   const DevView* views;
   const Seg* segs;
   int n_segs;
@@ -289,18 +290,34 @@ __global__ void k_bin(KCtx c, int n_views, int* ok) {
     }
 }
 
-// zero the image rows of every view (the output pointer comes from the per-call
-// arguments, so a captured graph writes wherever the current call asks)
-__global__ void k_zero_views(KCtx c, int n_views) {
-  long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= c.bin_pixels) return;
+__device__ __forceinline__ int view_of_pixel(const KCtx& c, int n_views, long long p) {
   int lo = 0, hi = n_views - 1, vi = 0;
   while (lo <= hi) {
     int mid = (lo + hi) >> 1;
     if (c.views[mid].bin_base <= p) { vi = mid; lo = mid + 1; } else hi = mid - 1;
   }
-  float* img = c.args->image + 3 * (c.views[vi].pix_off + (p - c.views[vi].bin_base));
-  img[0] = 0.0f; img[1] = 0.0f; img[2] = 0.0f;
+  return vi;
+}
+
+// forward calls accumulate every pixel's samples in double, in sample order, so
+// neither the sample count nor the chunking changes the result
+__global__ void k_zero_acc(KCtx c) {
+  long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= c.bin_pixels) return;
+  c.acc[3 * p] = 0.0; c.acc[3 * p + 1] = 0.0; c.acc[3 * p + 2] = 0.0;
+}
+
+// image rows of every view = mean of the samples (the output pointer comes from
+// the per-call arguments, so a captured graph writes wherever the call asks)
+__global__ void k_finish_views(KCtx c, int n_views) {
+  long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= c.bin_pixels) return;
+  const DevView& v = c.views[view_of_pixel(c, n_views, p)];
+  float* img = c.args->image + 3 * (v.pix_off + (p - v.bin_base));
+  double inv = 1.0 / (double)v.spp;
+  img[0] = (float)(c.acc[3 * p] * inv);
+  img[1] = (float)(c.acc[3 * p + 1] * inv);
+  img[2] = (float)(c.acc[3 * p + 2] * inv);
 }
 
 __global__ void k_fill_int(int* a, int n, int value) {
@@ -650,8 +667,8 @@ __global__ void __launch_bounds__(EXT_BLOCK) k_shadow(KCtx c, int b) {
   if ((threadIdx.x & 31) == 0 && traced) atomicAdd(&E.stat[STAT_SHADOW], (unsigned long long)traced);
 }
 
-// image[pixel] accumulates its samples in sample order, so the result does not
-// depend on where chunk boundaries fall
+// the pixel's double accumulator takes its samples in sample order, so the
+// result does not depend on where chunk boundaries fall
 __global__ void k_resolve(KCtx c, long long j0, int n) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -665,11 +682,13 @@ __global__ void k_resolve(KCtx c, long long j0, int n) {
   long long pixel = local / v.spp;
   int s = (int)(local - pixel * v.spp);
   if (s != 0 && i != 0) return;
-  float* img = c.args->image + 3 * (v.pix_off + pixel);
-  float3 acc = mk3(img[0], img[1], img[2]);
-  float inv = 1.0f / (float)v.spp;
-  for (int k = i; s < v.spp && k < n; ++k, ++s) acc += xyz(c.e.rad[k]) * inv;
-  img[0] = acc.x; img[1] = acc.y; img[2] = acc.z;
+  double* a = c.acc + 3 * (v.bin_base + pixel);
+  double ax = a[0], ay = a[1], az = a[2];
+  for (int k = i; s < v.spp && k < n; ++k, ++s) {
+    float4 r = c.e.rad[k];
+    ax += (double)r.x; ay += (double)r.y; az += (double)r.z;
+  }
+  a[0] = ax; a[1] = ay; a[2] = az;
 }
 
 // ------------------------------------------------------------------ gradient scatter

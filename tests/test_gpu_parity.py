@@ -338,9 +338,11 @@ def test_primary_bins_and_bvh_fallback_views(st):
     # one view outside the mesh (primary rays use the screen-space bins) and one
     # inside it, where triangles straddle the eye plane and the view's primary
     # rays fall back to the BVH; both match the oracle
+    # over 2^20 primary rays, so the library builds the bins (at ordinary spp: the
+    # per-pixel check assumes few samples per pixel, as in the workloads)
     sc = S.tiny()
-    out = S.View((0.0, 0.0, 3.0), (0.0, 0.0, 0.0), (0.0, 1.0, 0.0), 45.0, 30, 22, 3, 0)
-    inside = S.View((0.1, 0.2, 0.3), (0.0, 0.0, -2.0), (0.0, 1.0, 0.0), 90.0, 27, 31, 3, 30 * 22)
+    out = S.View((0.0, 0.0, 3.0), (0.0, 0.0, 0.0), (0.0, 1.0, 0.0), 45.0, 384, 360, 4, 0)
+    inside = S.View((0.1, 0.2, 0.3), (0.0, 0.0, -2.0), (0.0, 1.0, 0.0), 90.0, 370, 352, 4, 384 * 360)
     sc.views = [out, inside]
     sc.light_pos = np.array([[0.0, 0.0, 0.0], [0.0, 2.1, 2.1]], np.float32)
     sc.light_intensity = np.array([[0.5, 0.5, 0.5], [9.0, 9.0, 9.0]], np.float32)
