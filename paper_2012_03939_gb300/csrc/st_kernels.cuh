@@ -408,9 +408,10 @@ __global__ void k_raygen(KCtx c, long long j0, int n) {
         DevView v = c.views[sg.view];
         Key key{c.args->k0, c.args->k1};
         if (sg.kind == 0) {
-          long long pixel = local / v.spp;
-          int s = (int)(local - pixel * v.spp);
-          int x = (int)(pixel % v.W), y = (int)(pixel / v.W);
+          // a segment holds at most 2^31 jobs, so 32-bit division suffices
+          unsigned lj = (unsigned)local, pixel = lj / (unsigned)v.spp;
+          int s = (int)(lj - pixel * (unsigned)v.spp);
+          int x = (int)(pixel % (unsigned)v.W), y = (int)(pixel / (unsigned)v.W);
           uint32_t c0 = v.off + (uint32_t)pixel;
           U4 u = philox(c0, (uint32_t)s, 0u, 0u, key.k0, key.k1);
           d = cam_dir(v, (float)x + unif(u.x), (float)y + unif(u.y));
@@ -482,7 +483,7 @@ __global__ void __launch_bounds__(EXT_BLOCK) k_extend(KCtx c, int b) {
     int slot = q[qi_];
     float4 o = E.o[slot], d = E.d[slot];
     float t = __int_as_float(0x7f800000);
-    int f = -1;
+    int f = -1, fl = -1;
     int2 br = b == 0 ? E.brange[slot] : make_int2(-1, -1);
     if (br.x >= 0) {
       RayPre rp = ray_pre(xyz(o), xyz(d));
@@ -491,14 +492,14 @@ __global__ void __launch_bounds__(EXT_BLOCK) k_extend(KCtx c, int b) {
         float4 ta = __ldg(&c.tri[3 * li]), tb = __ldg(&c.tri[3 * li + 1]), tc = __ldg(&c.tri[3 * li + 2]);
         int fid = __float_as_int(ta.w);
         float th = tri_test(rp, xyz(ta), xyz(tb), xyz(tc), t * 1.0000001f + 1e-30f);
-        if (th > 0.0f && (th < t || (th == t && fid < f))) { t = th; f = fid; }
+        if (th > 0.0f && (th < t || (th == t && fid < f))) { t = th; f = fid; fl = li; }
         if (STATS) ts.tests++;
       }
     } else {
       f = trace_bvh<false, STATS>(c.nodes, c.tri, c.nf, xyz(o), xyz(d), __int_as_float(0x7f800000), E.origin[slot], t,
-                                  sstack + threadIdx.x, c.err, &ts);
+                                  sstack + threadIdx.x, c.err, &ts, &fl);
     }
-    E.hit[slot] = make_int2(f, __float_as_int(t));
+    E.hit[slot] = make_int2(fl, __float_as_int(t));   // leaf index: shading reads the contiguous leaf record
   }
   ST_WARP_LOOP_END
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&E.stat[STAT_EXT], (unsigned long long)E.cnt[CNT_EXT + b]);
@@ -545,11 +546,11 @@ __global__ void k_shade(KCtx c, int b) {
         if (E.records && b > 0) E.esc[slot] = make_float4(Lw.x, Lw.y, Lw.z, 1.0f);
       }
     } else {
-      int f = h.x;
+      float4 ta = __ldg(&c.tri[3 * h.x]), tb = __ldg(&c.tri[3 * h.x + 1]), tc = __ldg(&c.tri[3 * h.x + 2]);
+      int f = __float_as_int(ta.w);
       float t = __int_as_float(h.y);
       float3 p = xyz(o4) + dir * t;
-      int ia = c.F[3 * f], ib = c.F[3 * f + 1], ic = c.F[3 * f + 2];
-      float3 v0 = fetch_vertex(c.V, ia), v1 = fetch_vertex(c.V, ib), v2 = fetch_vertex(c.V, ic);
+      float3 v0 = xyz(ta), v1 = xyz(tb), v2 = xyz(tc);
       float3 ng = norm3(cross3(v1 - v0, v2 - v0));
       float3 wo = -dir;
       float3 n = dot3(ng, wo) < 0.0f ? -ng : ng;
@@ -606,6 +607,7 @@ __global__ void k_shade(KCtx c, int b) {
         E.r3[b * Q + slot] = make_float4(escale.x, escale.y, escale.z, 0.0f);
       }
       E.o[slot] = make_float4(p.x, p.y, p.z, 0.0f);
+      E.origin[slot] = f;          // excluded by this vertex's shadow rays and by its continuation
       if (b < c.B - 1) {
         U4 u = philox((uint32_t)E.ctr[slot].x, (uint32_t)E.ctr[slot].y, (uint32_t)(b << 4) | 2u,
                       (uint32_t)E.ctr[slot].z, key.k0, key.k1);
@@ -616,7 +618,6 @@ __global__ void k_shade(KCtx c, int b) {
           T = mul(T, Qv) * (1.0f / pdf);
           E.thr[slot] = make_float4(T.x, T.y, T.z, 0.0f);
           E.d[slot] = make_float4(wi.x, wi.y, wi.z, pdf);
-          E.origin[slot] = f;
           if (E.records) E.r1[(b + 1) * Q + slot] = make_float4(wi.x, wi.y, wi.z, pdf);
           cont = true;
         }
@@ -639,7 +640,7 @@ __global__ void __launch_bounds__(EXT_BLOCK) k_shadow(KCtx c, int b) {
   if (live_) {
     int slot = E.qs[qi_];
     float3 p = xyz(E.o[slot]);
-    int exclude = E.hit[slot].x;
+    int exclude = E.origin[slot];
     float3 L = mk3(0, 0, 0);
     int vis = 0;
     for (int k = 0; k < c.NS; ++k) {

@@ -37,7 +37,8 @@ __device__ __forceinline__ float box_hit(float lx, float hx, float ly, float hy,
   return tn <= tf * 1.00000036f ? tn : __int_as_float(0x7f800000);
 }
 
-// ANY = stop at the first hit (shadow rays). Returns the face id or -1; t in tbest.
+// ANY = stop at the first hit (shadow rays). Returns the face id or -1; t in
+// tbest; the hit's leaf index in *leaf_out if given.
 // nodes = the 4-wide tree: per node lo.x, hi.x, lo.y, hi.y, lo.z, hi.z (one
 // float4 of four children each) and the four child links (>= 0 node, < 0 leaf
 // ~i, INT_MIN empty). Hit leaves are tested at once; hit internal children are
@@ -45,10 +46,10 @@ __device__ __forceinline__ float box_hit(float lx, float hx, float ly, float hy,
 template <bool ANY, bool STATS>
 __device__ __forceinline__ int trace_bvh(const float4* __restrict__ nodes, const float4* __restrict__ tri, int nf,
                                          float3 o, float3 d, float tmax, int exclude, float& tbest, int* sstack,
-                                         int* err, TraceStats* ts) {
+                                         int* err, TraceStats* ts, int* leaf_out = nullptr) {
   RayPre rp = ray_pre(o, d);
   float3 inv = safe_inv(d);
-  int best = -1;
+  int best = -1, best_leaf = -1;
   tbest = tmax;
   auto leaf = [&](int li) -> bool {
     float4 a = __ldg(&tri[3 * li]);
@@ -59,13 +60,14 @@ __device__ __forceinline__ int trace_bvh(const float4* __restrict__ nodes, const
     float4 c = __ldg(&tri[3 * li + 2]);
     float t = tri_test(rp, xyz(a), xyz(b), xyz(c), ANY ? tmax : tbest * 1.0000001f + 1e-30f);
     if (t > 0.0f) {
-      if (ANY) { best = fid; tbest = t; return true; }
-      if (t < tbest || (t == tbest && fid < best)) { tbest = t; best = fid; }
+      if (ANY) { best = fid; best_leaf = li; tbest = t; return true; }
+      if (t < tbest || (t == tbest && fid < best)) { tbest = t; best = fid; best_leaf = li; }
     }
     return false;
   };
   if (nf == 1) {
     leaf(0);
+    if (leaf_out) *leaf_out = best_leaf;
     return best;
   }
   const float INF = __int_as_float(0x7f800000);
@@ -121,6 +123,7 @@ __device__ __forceinline__ int trace_bvh(const float4* __restrict__ nodes, const
       ++sp;
     }
   }
+  if (leaf_out) *leaf_out = best_leaf;
   return best;
 }
 
