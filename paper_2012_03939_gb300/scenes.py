@@ -350,7 +350,50 @@ def scale(seed=BASE_SEED + 4, n_views=100, res=512, spp=16, n_lon=1000, n_bands=
                  max_bounces=5, edge_term=True, seed=seed)
 
 
-WORKLOADS = {"tiny": tiny, "edges": edges, "env": env, "batched": batched, "scale": scale}
+def _grid_quad(origin, u, v, n):
+    """n x n quads spanning origin + [0,1] u + [0,1] v, two triangles each, normal along u x v."""
+    origin, u, v = (np.asarray(a, np.float64) for a in (origin, u, v))
+    g = np.arange(n + 1) / n
+    P = origin + g[:, None, None] * u + g[None, :, None] * v
+    idx = np.arange((n + 1) * (n + 1)).reshape(n + 1, n + 1)
+    a, b, c, d = idx[:-1, :-1], idx[1:, :-1], idx[1:, 1:], idx[:-1, 1:]
+    F = np.concatenate([np.stack([a, b, c], -1).reshape(-1, 3), np.stack([a, c, d], -1).reshape(-1, 3)])
+    return P.reshape(-1, 3), F
+
+
+def color_bleed(seed=BASE_SEED + 5, res=64, spp=16, n=8, plane_kd=((0.8, 0.1, 0.1), (0.1, 0.1, 0.8), (0.8, 0.8, 0.8))):
+    """Three intersecting planes -- red wall, blue wall, white floor -- seen from the open side, as in the
+    paper's study of global illumination on material estimation (Sec. 3.3, colour bleeding).
+    face_plane gives each face's plane (0 red, 1 blue, 2 floor)."""
+    walls = [((0, 0, 0), (0, 2, 0), (0, 0, 2)),     # x = 0, red, normal +x
+             ((0, 0, 0), (2, 0, 0), (0, 2, 0)),     # z = 0, blue, normal +z
+             ((0, 0, 0), (0, 0, 2), (2, 0, 0))]     # y = 0, white floor, normal +y
+    Vs, Fs, plane = [], [], []
+    off = 0
+    for k, (o, u, v) in enumerate(walls):
+        P, F = _grid_quad(o, u, v, n)
+        Vs.append(P)
+        Fs.append(F + off)
+        plane.append(np.full(len(F), k))
+        off += len(P)
+    V = np.concatenate(Vs)
+    F = np.concatenate(Fs).astype(np.int32)
+    plane = np.concatenate(plane)
+    P = np.zeros((len(F), 5), np.float32)
+    P[:, :3] = np.asarray(plane_kd, np.float32)[plane]
+    P[:, 3] = 0.0
+    P[:, 4] = 0.5
+    vs = []
+    for i, (ex, ez) in enumerate([(3.6, 3.0), (3.0, 3.6), (3.4, 3.4), (4.0, 2.6)]):
+        vs.append(View((ex, 2.2, ez), (0.6, 0.5, 0.6), (0.0, 1.0, 0.0), 45.0, res, res, spp))
+    _pack_offsets(vs)
+    sc = Scene("color_bleed", _f32(V), F, P, "ggx", light_pos=_f32([[1.3, 1.6, 1.3]]),
+               light_intensity=_f32([[4.0, 4.0, 4.0]]), views=vs, max_bounces=3, seed=seed)
+    sc.face_plane = plane
+    return sc
+
+
+WORKLOADS = {"tiny": tiny, "edges": edges, "env": env, "batched": batched, "scale": scale, "color_bleed": color_bleed}
 
 
 def make(name: str, **kw) -> Scene:
