@@ -166,6 +166,7 @@ inline double comp(const V3d& a, int k) { return k == 0 ? a.x : (k == 1 ? a.y : 
 // ---------------------------------------------------------------- scene
 struct Scene {
   int nv = 0, nf = 0;
+  int res = 0, ntex = 1;        // mesh-colors resolution r and texels per face (r+1)(r+2)/2
   std::vector<V3d> vert;
   std::vector<int> face;        // 3 per face
   std::vector<double> param;    // 5 per face
@@ -206,8 +207,10 @@ V3d cam_dir(const Cam& c, double px, double py) {
 }
 
 // ---------------------------------------------------------------- intersection
-// Watertight ray/triangle test (Woop, Benthin, Wald 2013) in double.
-bool tri_hit(const V3d& o, const V3d& d, const V3d& p0, const V3d& p1, const V3d& p2, double& t) {
+// Watertight ray/triangle test (Woop, Benthin, Wald 2013) in double; b1, b2 =
+// barycentric weights of p1 and p2 at the hit.
+bool tri_hit(const V3d& o, const V3d& d, const V3d& p0, const V3d& p1, const V3d& p2, double& t,
+             double* b1 = nullptr, double* b2 = nullptr) {
   double ad[3] = {std::fabs(d.x), std::fabs(d.y), std::fabs(d.z)};
   int kz = (ad[0] > ad[1]) ? (ad[0] > ad[2] ? 0 : 2) : (ad[1] > ad[2] ? 1 : 2);
   int kx = (kz + 1) % 3, ky = (kx + 1) % 3;
@@ -225,20 +228,22 @@ bool tri_hit(const V3d& o, const V3d& d, const V3d& p0, const V3d& p1, const V3d
   double Az = sz * comp(A, kz), Bz = sz * comp(B, kz), Cz = sz * comp(C, kz);
   double T = U * Az + Vb * Bz + W * Cz;
   t = T / det;
+  if (b1) *b1 = Vb / det;
+  if (b2) *b2 = W / det;
   return true;
 }
 
-struct Hit { int tri; double t; };
+struct Hit { int tri; double t, b1, b2; };
 
 Hit closest(const Scene& s, const V3d& o, const V3d& d, int exclude, double tmax) {
-  Hit h{-1, tmax};
+  Hit h{-1, tmax, 0, 0};
   for (int f = 0; f < s.nf; ++f) {
     if (f == exclude) continue;
-    double t;
+    double t, b1, b2;
     const int* fi = &s.face[3 * f];
-    if (!tri_hit(o, d, s.vert[fi[0]], s.vert[fi[1]], s.vert[fi[2]], t)) continue;
+    if (!tri_hit(o, d, s.vert[fi[0]], s.vert[fi[1]], s.vert[fi[2]], t, &b1, &b2)) continue;
     if (!(t > T_EPS && t < tmax)) continue;
-    if (t < h.t || (t == h.t && f < h.tri)) { h.t = t; h.tri = f; }
+    if (t < h.t || (t == h.t && f < h.tri)) { h.t = t; h.tri = f; h.b1 = b1; h.b2 = b2; }
   }
   return h;
 }
@@ -491,6 +496,17 @@ template <> struct Access<Dual> {
   }
 };
 
+// Mesh-colors texel of the hit (Sec. 3.3): k = (t (r+1)(r+2) + i (2r - i + 3)) / 2 + j,
+// (i, j) = floor(r (alpha, beta)), alpha and beta the barycentric weights of the
+// face's second and third vertices; clamped so rounding cannot leave the face's block.
+long long texel(const Scene& s, int t, double alpha, double beta) {
+  if (s.res == 0) return t;
+  long long r = s.res;
+  long long i = std::min<long long>(std::max<long long>((long long)std::floor(r * alpha), 0), r);
+  long long j = std::min<long long>(std::max<long long>((long long)std::floor(r * beta), 0), r - i);
+  return (t * (r + 1) * (r + 2) + i * (2 * r - i + 3)) / 2 + j;
+}
+
 Mat mat_val(const Scene& s, int f) {
   Mat m;
   for (int c = 0; c < 3; ++c) m.kd[c] = s.param[5 * f + c];
@@ -552,8 +568,9 @@ void trace_path(const Scene& s, const Rng& rng, int B, const V3d& eye, const V3d
     V3<T> v0 = A::vertex(s, vars, fi[0]);
     V3<T> v1 = A::vertex(s, vars, fi[1]);
     V3<T> v2 = A::vertex(s, vars, fi[2]);
-    MatT<T> m = A::params(s, vars, h.tri);
-    Mat mv = mat_val(s, h.tri);
+    long long tex = texel(s, h.tri, h.b1, h.b2);
+    MatT<T> m = A::params(s, vars, (int)tex);
+    Mat mv = mat_val(s, (int)tex);
     V3<T> mvec = cross(v1 - v0, v2 - v0);
     V3<T> dT = lift<T>(d);
     T t = dot(v0 - o, mvec) / dot(dT, mvec);
@@ -637,7 +654,10 @@ bool load_scene(const orc_scene* in, Scene& s) {
   for (int i = 0; i < s.nv; ++i) s.vert[i] = {in->vertices[3 * i], in->vertices[3 * i + 1], in->vertices[3 * i + 2]};
   s.face.assign(in->faces, in->faces + 3 * (size_t)s.nf);
   for (int v : s.face) if (v < 0 || v >= s.nv) return false;
-  s.param.resize(5 * (size_t)s.nf);
+  if (in->color_res < 0 || in->color_res > 64) return false;
+  s.res = in->color_res;
+  s.ntex = (s.res + 1) * (s.res + 2) / 2;
+  s.param.resize(5 * (size_t)s.nf * s.ntex);
   for (size_t i = 0; i < s.param.size(); ++i) s.param[i] = in->face_params[i];
   for (int j = 0; j < in->n_lights; ++j) {
     s.lpos.push_back({in->light_pos[3 * j], in->light_pos[3 * j + 1], in->light_pos[3 * j + 2]});
@@ -878,7 +898,7 @@ long long orc_grad_pixels(const orc_scene* in, const orc_view* views, int n_view
   int nt = nthreads(p);
   std::vector<long long> seg(nt, 0);
   std::vector<std::vector<double>> gv(nt, std::vector<double>(3 * (size_t)s.nv, 0.0));
-  std::vector<std::vector<double>> gf(nt, std::vector<double>(5 * (size_t)s.nf, 0.0));
+  std::vector<std::vector<double>> gf(nt, std::vector<double>(5 * (size_t)s.nf * s.ntex, 0.0));
   parallel_for(n, nt, [&](int tid, int i) {
     const double* w = dLdI + 3 * (size_t)i;
     if (w[0] == 0 && w[1] == 0 && w[2] == 0) return;

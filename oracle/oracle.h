@@ -38,6 +38,8 @@ typedef struct {
   const double* light_intensity; /* [L][3] radiant intensity, RGB */
   int env_width, env_height; /* 0 if no environment */
   const float* env_rgb;      /* [H][W][3] */
+  int color_res;             /* mesh-colors resolution r >= 0; face_params then holds
+                                F*(r+1)(r+2)/2 texels of 5 params, texel k(r, t, alpha, beta) */
 } orc_scene;
 
 typedef struct {
@@ -62,7 +64,7 @@ long long orc_render_pixels(const orc_scene* s, const orc_view* views, int n_vie
                             double* out /*[n][3]*/);
 
 /* Interior gradient for the listed pixels with weights dLdI [n][3]:
- * d_verts [V][3] and d_face [F][5] are ACCUMULATED (+=). Returns segments or -1. */
+ * d_verts [V][3] and d_face [texels][5] are ACCUMULATED (+=). Returns segments or -1. */
 long long orc_grad_pixels(const orc_scene* s, const orc_view* views, int n_views,
                           const orc_params* p, const int* pix, int n, const double* dLdI,
                           double* d_verts, double* d_face);

@@ -52,6 +52,7 @@ class Scene:
     edge_term: bool = False
     seed: int = BASE_SEED
     target_vertices: Optional[np.ndarray] = None  # perturbed copy used to render a target
+    color_res: int = 0              # mesh-colors resolution r: face_params has F*(r+1)(r+2)/2 texel rows
 
     @property
     def n_pixels(self) -> int:

@@ -539,3 +539,98 @@ def test_edge_plus_interior_matches_crn_finite_difference():
     g, f = np.array(grads), np.array(fds)
     se = math.sqrt(g.var(ddof=1) / len(g) + f.var(ddof=1) / len(f))
     assert abs(g.mean() - f.mean()) < 3 * se + 1e-3 * abs(f.mean()), (g.mean(), f.mean(), se)
+
+
+# ---------------------------------------------------------------------------- mesh colors r > 0
+def _texel_index(r, t, alpha, beta):
+    i = min(max(int(math.floor(r * alpha)), 0), r)
+    j = min(max(int(math.floor(r * beta)), 0), r - i)
+    return (t * (r + 1) * (r + 2) + i * (2 * r - i + 3)) // 2 + j
+
+
+def test_mesh_colors_uniform_texels_equal_per_face():
+    sc = S.tiny(res=24, spp=2)
+    r = 2
+    n = (r + 1) * (r + 2) // 2
+    P = np.repeat(sc.face_params, n, axis=0)
+    ref, _ = O.render_pixels(O.OracleScene(sc), O.params(2, 3), O.all_pixels(sc))
+    sc2 = S.tiny(res=24, spp=2)
+    sc2.color_res = r
+    got, _ = O.render_pixels(O.OracleScene(sc2, face_params=P), O.params(2, 3), O.all_pixels(sc2))
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_mesh_colors_texel_lookup_on_a_triangle():
+    # one Lambertian triangle, r = 3 (10 texels, each its own kd); at screen points
+    # of known barycentrics the radiance difference of two kd sets isolates the
+    # texel the estimator used: (kd_a - kd_b)[k] / pi * I cos / d^2
+    r = 3
+    sc = S.single_triangle(16, 16, light_dist=2.5)
+    sc.color_res = r
+    sc.light_pos = np.array([[0.3, -0.2, 2.4]], np.float32)
+    sc.light_intensity = np.array([[5.0, 5.0, 5.0]], np.float32)
+    n = (r + 1) * (r + 2) // 2
+    rng = np.random.default_rng(21)
+    Pa = np.c_[rng.uniform(0.1, 0.9, (n, 3)), np.zeros(n), np.full(n, 0.5)]
+    Pb = np.c_[rng.uniform(0.1, 0.9, (n, 3)), np.zeros(n), np.full(n, 0.5)]
+    oa, ob = O.OracleScene(sc, face_params=Pa), O.OracleScene(sc, face_params=Pb)
+    prm = O.params(1, 5)
+    V = sc.vertices.astype(np.float64)
+    nrm = np.cross(V[1] - V[0], V[2] - V[0])
+    nrm /= np.linalg.norm(nrm)
+    seen = set()
+    for px in np.linspace(0.25, 15.75, 48):
+        for py in np.linspace(0.25, 15.75, 48):
+            o, d = G.pixel_ray(sc.views[0], px, py)
+            t = ((V[0] - o) @ nrm) / (d @ nrm)
+            p = o + t * d
+            # weights (w0, alpha, beta) of v0, v1, v2
+            alpha, beta = np.linalg.lstsq(np.c_[V[1] - V[0], V[2] - V[0]], p - V[0], rcond=None)[0]
+            w0 = 1 - alpha - beta
+            if min(w0, alpha, beta) < 1e-3:
+                continue
+            ra, rb = r * alpha, r * beta
+            if min(abs(ra - round(ra)), abs(rb - round(rb))) < 1e-6:
+                continue
+            k = _texel_index(r, 0, alpha, beta)
+            seen.add(k)
+            Lp = sc.light_pos[0].astype(np.float64)
+            wl = Lp - p
+            dist = np.linalg.norm(wl)
+            n_ = nrm if nrm @ -d > 0 else -nrm
+            exp = (Pa[k, :3] - Pb[k, :3]) / math.pi * 5.0 * max(0.0, n_ @ wl / dist) / dist ** 2
+            got = O.trace_screen(oa, prm, 0, px, py) - O.trace_screen(ob, prm, 0, px, py)
+            np.testing.assert_allclose(got, exp, rtol=1e-9, atol=1e-13)
+    # every texel reachable from the triangle's interior (i + j < r) was used; the
+    # others (i + j = r) are met only on the edge alpha + beta = 1
+    interior = {_texel_index(r, 0, (i + 0.5) / r, (j + 0.5) / r) for i in range(r) for j in range(r - i)}
+    assert seen == interior, (seen, interior)
+
+
+def test_mesh_colors_texel_gradient_matches_tape_replay_fd():
+    sc = _book_scene()
+    r = 2
+    n = (r + 1) * (r + 2) // 2
+    sc.color_res = r
+    rng = np.random.default_rng(22)
+    P0 = np.repeat(sc.face_params.astype(np.float64), n, axis=0)
+    P0[:, :3] = np.clip(P0[:, :3] + rng.normal(0, 0.1, (len(P0), 3)), 0.05, 0.95)
+    V0 = sc.vertices.astype(np.float64)
+    prm = O.params(3, 99)
+    w = np.array([0.4, -0.2, 0.9])
+    checked = 0
+    for (px, py, c1) in [(5.3, 9.1, 0), (8.7, 11.2, 1), (10.1, 6.4, 2)]:
+        osc = O.OracleScene(sc, vertices=V0, face_params=P0)
+        _, dv, df = O.trace_screen(osc, prm, 0, px, py, c0=3, c1=c1, grad_w=w)
+        _, tape = O.trace_screen_taped(osc, prm, 0, px, py, c0=3, c1=c1)
+        h = 1e-6
+        for (ti, k) in [(i, k) for i in range(len(P0)) for k in range(5) if df[i, k] != 0]:
+            Pp, Pm = P0.copy(), P0.copy()
+            Pp[ti, k] += h
+            Pm[ti, k] -= h
+            fp = O.trace_screen_taped(O.OracleScene(sc, vertices=V0, face_params=Pp), prm, 0, px, py, 3, c1, tape=tape)
+            fm = O.trace_screen_taped(O.OracleScene(sc, vertices=V0, face_params=Pm), prm, 0, px, py, 3, c1, tape=tape)
+            fd = (w @ fp - w @ fm) / (2 * h)
+            assert abs(fd - df[ti, k]) < 1e-5 * max(1.0, abs(fd)), (ti, k, fd, df[ti, k])
+            checked += 1
+    assert checked > 10
