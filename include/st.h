@@ -87,15 +87,22 @@ typedef struct {
   long long pixel_offset;
 } st_view;
 
+/* Material: mesh colors (Sec. 3.3) at resolution r = color_res. Face t owns
+ * the texels t*n .. t*n + n - 1, n = (r+1)(r+2)/2; a point of barycentric
+ * weights (alpha, beta) for the face's second and third vertices uses texel
+ * k = (t (r+1)(r+2) + i (2r - i + 3)) / 2 + j, (i, j) = floor(r (alpha, beta)).
+ * r = 0 is one parameter set per face. Each texel holds kd_r, kd_g, kd_b, ks,
+ * roughness. */
 typedef struct {
   int n_vertices, n_faces;
   const float* vertices;     /* device, float [V][3] */
   const int* faces;          /* device, int [F][3] vertex indices */
-  const float* face_params;  /* device, float [F][5]: kd_r, kd_g, kd_b, ks, roughness */
+  const float* face_params;  /* device, float [F*n][5] texel parameters (n = 1 when color_res = 0) */
   int brdf;                  /* ST_BRDF_GGX or ST_BRDF_BECKMANN */
   int n_point_lights;        /* 0..ST_MAX_LIGHTS */
   const st_point_light* point_lights; /* host array */
   const st_envmap* env;      /* NULL if no environment */
+  int color_res;             /* mesh-colors resolution r, 0..64 */
 } st_scene_desc;
 
 typedef struct {
@@ -142,7 +149,7 @@ st_status st_refit(st_scene* scene, const float* new_vertices, void* stream);
 /* New vertex positions with a full rebuild (Morton order recomputed). */
 st_status st_rebuild(st_scene* scene, const float* new_vertices, void* stream);
 
-/* New per-face parameters (device float [F][5]); the material update (Sec. 3.3). */
+/* New texel parameters (device float [F*n][5], see st_scene_desc); the material update (Sec. 3.3). */
 st_status st_set_face_params(st_scene* scene, const float* face_params, void* stream);
 
 /* Forward render of n_views views (host array) with max_bounces surface
@@ -155,7 +162,7 @@ st_status st_render(st_scene* scene, const st_view* views, int n_views, int defa
 
 /* Adjoint: given dL/dI (device float [N][3], same layout as out_image),
  * ACCUMULATE (+=) dL/dvertices into d_vertices (device float [V][3]) and
- * dL/dface_params into d_face_params (device float [F][5]). The interior term
+ * dL/dtexel-parameters into d_face_params (device float [F*n][5]). The interior term
  * replays the forward paths of the same seed and sweeps each in reverse; the
  * edge term (opts->edge_term) samples visibility edges. Either gradient
  * pointer may be NULL to skip it (d_vertices may not be NULL with edge_term). */

@@ -293,7 +293,7 @@ KCtx make_ctx(st_scene* s, const Plan& p) {
   KCtx c;
   c.V = s->verts; c.F = s->faces; c.P = s->params; c.nodes = s->nodes4; c.tri = s->tri; c.nf = s->nf;
   c.lights = s->lights; c.nl = s->nl; c.NS = s->nl + (s->env.w > 0 ? 1 : 0);
-  c.env = s->env; c.brdf = s->brdf;
+  c.env = s->env; c.brdf = s->brdf; c.res = s->res; c.ntex = s->ntex;
   c.edge_v = s->edge_v; c.edge_f = s->edge_f; c.n_edges = s->n_edges; c.edge_mode = p.o.edge_mode;
   c.edge_flag = s->edge_flag; c.edge_cand = s->edge_cand; c.edge_ncand = s->edge_ncand;
   c.bin_start = p.bins ? s->bin_start : nullptr;   // nullptr: every primary ray traverses the BVH
@@ -628,6 +628,9 @@ st_status st_scene_create(const st_scene_desc* d, void* stream, st_scene** out) 
     return fail(ST_ERR_INVALID_ARG, "mesh description incomplete");
   if (d->n_faces > (1 << 28)) return fail(ST_ERR_UNSUPPORTED, "too many faces");
   if (d->brdf != ST_BRDF_GGX && d->brdf != ST_BRDF_BECKMANN) return fail(ST_ERR_INVALID_ARG, "unknown brdf");
+  if (d->color_res < 0 || d->color_res > 64) return fail(ST_ERR_UNSUPPORTED, "mesh-colors resolution must be in [0, 64]");
+  if ((long long)d->n_faces * (d->color_res + 1) * (d->color_res + 2) / 2 > (1LL << 30))
+    return fail(ST_ERR_UNSUPPORTED, "too many mesh-colors texels");
   if (d->n_point_lights < 0 || d->n_point_lights > ST_MAX_LIGHTS || (d->n_point_lights > 0 && !d->point_lights))
     return fail(ST_ERR_INVALID_ARG, "bad point lights");
   if (d->n_point_lights == 0 && !d->env) return fail(ST_ERR_INVALID_ARG, "scene has no light");
@@ -647,6 +650,8 @@ st_status st_scene_create(const st_scene_desc* d, void* stream, st_scene** out) 
   s->nf = d->n_faces;
   s->brdf = d->brdf;
   s->nl = d->n_point_lights;
+  s->res = d->color_res;
+  s->ntex = (s->res + 1) * (s->res + 2) / 2;
   // host copy of the faces: validation and edge list
   std::vector<int> hf(3 * (size_t)s->nf);
   std::vector<float> hv(3 * (size_t)s->nv);
@@ -677,7 +682,8 @@ st_status st_scene_create(const st_scene_desc* d, void* stream, st_scene** out) 
   s->sort_blocks = sort_blocks_for(n);
   e = cudaSuccess;
   auto chk = [&](cudaError_t x) { if (x != cudaSuccess && e == cudaSuccess) e = x; };
-  chk(dalloc(&s->verts, 3 * (size_t)s->nv)); chk(dalloc(&s->faces, 3 * (size_t)n)); chk(dalloc(&s->params, 2 * (size_t)n));
+  chk(dalloc(&s->verts, 3 * (size_t)s->nv)); chk(dalloc(&s->faces, 3 * (size_t)n));
+  chk(dalloc(&s->params, 2 * (size_t)n * s->ntex));
   chk(dalloc(&s->tri, 3 * (size_t)n)); chk(dalloc(&s->nodes, 4 * (size_t)std::max(n - 1, 1)));
   chk(dalloc(&s->parent, 2 * (size_t)n)); chk(dalloc(&s->flags, (size_t)std::max(n - 1, 1)));
   chk(dalloc(&s->keys, (size_t)n)); chk(dalloc(&s->keys2, (size_t)n)); chk(dalloc(&s->ids, (size_t)n));
@@ -697,7 +703,10 @@ st_status st_scene_create(const st_scene_desc* d, void* stream, st_scene** out) 
   }
   chk(cudaMemcpyAsync(s->verts, d->vertices, 3 * sizeof(float) * s->nv, cudaMemcpyDeviceToDevice, st));
   chk(cudaMemcpyAsync(s->faces, d->faces, 3 * sizeof(int) * n, cudaMemcpyDeviceToDevice, st));
-  if (n > 0) k_params_in<<<(n + 255) / 256, 256, 0, st>>>(d->face_params, s->params, n);
+  {
+    int nt = n * s->ntex;
+    k_params_in<<<(nt + 255) / 256, 256, 0, st>>>(d->face_params, s->params, nt);
+  }
   chk(cudaMemcpyAsync(s->lights, hl.data(), hl.size() * sizeof(float4), cudaMemcpyHostToDevice, st));
   chk(cudaMemcpyAsync(s->edge_v, ev.data(), ev.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
   chk(cudaMemcpyAsync(s->edge_f, ef.data(), ef.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
@@ -740,7 +749,8 @@ st_status st_rebuild(st_scene* s, const float* v, void* stream) { return update_
 
 st_status st_set_face_params(st_scene* s, const float* p, void* stream) {
   if (!s || !p) return fail(ST_ERR_INVALID_ARG, "NULL argument");
-  k_params_in<<<(s->nf + 255) / 256, 256, 0, (cudaStream_t)stream>>>(p, s->params, s->nf);
+  int nt = s->nf * s->ntex;
+  k_params_in<<<(nt + 255) / 256, 256, 0, (cudaStream_t)stream>>>(p, s->params, nt);
   ST_CUDA(cudaGetLastError());
   return ST_OK;
 }

@@ -65,9 +65,10 @@ struct GraphEntry {
 struct st_scene {
   int device = 0;
   int nv = 0, nf = 0, brdf = 0, nl = 0;
+  int res = 0, ntex = 1;         // mesh-colors resolution and texels per face
   float* verts = nullptr;        // [V*3]
   int* faces = nullptr;          // [F*3]
-  float4* params = nullptr;      // [F*2]: (kd_r, kd_g, kd_b, ks), (roughness, 0, 0, 0)
+  float4* params = nullptr;      // [F*ntex*2] per texel: (kd_r, kd_g, kd_b, ks), (roughness, 0, 0, 0)
   // LBVH
   float4* tri = nullptr;         // [F*3] triangles in leaf order; tri[3i].w = face id bits
   float4* nodes = nullptr;       // [(F-1)*4]

@@ -31,6 +31,7 @@ struct KCtx {
   int nl, NS;
   DevEnv env;
   int brdf;
+  int res, ntex;          // mesh-colors resolution r and texels per face
   const int2* edge_v;
   const int2* edge_f;
   int n_edges;
@@ -83,6 +84,21 @@ __device__ __forceinline__ Mat fetch_mat(const float4* P, int f) {
   Mat m;
   m.kd[0] = a.x; m.kd[1] = a.y; m.kd[2] = a.z; m.ks = a.w; m.alpha = b.x;
   return m;
+}
+
+// Mesh-colors texel of a hit at p on face f (Sec. 3.3): k = (f (r+1)(r+2) +
+// i (2r - i + 3)) / 2 + j with (i, j) = floor(r (alpha, beta)), alpha and beta
+// the barycentric weights of the face's second and third vertices.
+__device__ __forceinline__ int texel_of(const KCtx& c, int f, float3 p, float3 v0, float3 v1, float3 v2) {
+  if (c.res == 0) return f;
+  float3 e1 = v1 - v0, e2 = v2 - v0, q = p - v0;
+  float3 m = cross3(e1, e2);
+  float im = 1.0f / dot3(m, m);
+  float alpha = dot3(cross3(q, e2), m) * im, beta = dot3(cross3(e1, q), m) * im;
+  int r = c.res;
+  int i = min(max((int)floorf((float)r * alpha), 0), r);
+  int j = min(max((int)floorf((float)r * beta), 0), r - i);
+  return f * c.ntex + (i * (2 * r - i + 3)) / 2 + j;
 }
 
 // ------------------------------------------------------------------ edges
@@ -554,7 +570,8 @@ __global__ void k_shade(KCtx c, int b) {
       float3 ng = norm3(cross3(v1 - v0, v2 - v0));
       float3 wo = -dir;
       float3 n = dot3(ng, wo) < 0.0f ? -ng : ng;
-      Mat m = fetch_mat(c.P, f);
+      int tex = texel_of(c, f, p, v0, v1, v2);
+      Mat m = fetch_mat(c.P, tex);
       if (E.records) {
         E.r0[b * Q + slot] = make_float4(p.x, p.y, p.z, __int_as_float(f));
         E.nb[slot] = b + 1;
@@ -604,7 +621,7 @@ __global__ void k_shade(KCtx c, int b) {
       }
       if (E.records) {
         E.r2[b * Q + slot] = make_float4(ewi.x, ewi.y, ewi.z, __int_as_float(flags));
-        E.r3[b * Q + slot] = make_float4(escale.x, escale.y, escale.z, 0.0f);
+        E.r3[b * Q + slot] = make_float4(escale.x, escale.y, escale.z, __int_as_float(tex));
       }
       E.o[slot] = make_float4(p.x, p.y, p.z, 0.0f);
       E.origin[slot] = f;          // excluded by this vertex's shadow rays and by its continuation
@@ -754,7 +771,8 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_adjoint(KCtx c, long long j0, int
     float3 wo = -xyz(r1);
     float3 ng = norm3(cross3(v1 - v0, v2 - v0));
     float3 nn = dot3(ng, wo) < 0.0f ? -ng : ng;
-    float3 Qv = brdf_cos(c.brdf, fetch_mat(c.P, f), nn, xyz(r1n), wo);
+    int tex = __float_as_int(E.r3[b * Q + i].w);
+    float3 Qv = brdf_cos(c.brdf, fetch_mat(c.P, tex), nn, xyz(r1n), wo);
     T[b + 1] = mul(T[b], Qv) * (1.0f / r1n.w);
   }
   bool esc = nbv > 0 && E.esc[i].w != 0.0f;
@@ -765,11 +783,12 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_adjoint(KCtx c, long long j0, int
     float vals[14];
 #pragma unroll
     for (int k = 0; k < 14; ++k) vals[k] = 0.0f;
-    int face = -1;
+    int face = -1, key = -1;      // key = texel: equal keys share face and parameters
     if (b < nbv) {
       float4 r0 = E.r0[b * Q + i], r1 = E.r1[b * Q + i], r2 = E.r2[b * Q + i], r3 = E.r3[b * Q + i];
       int f = __float_as_int(r0.w);
       face = f;
+      key = __float_as_int(r3.w);
       float3 p = xyz(r0), d = xyz(r1), wo = -d;
       float3 v0 = fetch_vertex(c.V, c.F[3 * f]), v1 = fetch_vertex(c.V, c.F[3 * f + 1]),
              v2 = fetch_vertex(c.V, c.F[3 * f + 2]);
@@ -779,7 +798,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_adjoint(KCtx c, long long j0, int
       float3 mh = mv * (1.0f / ml);
       float sgn = dot3(mh, wo) < 0.0f ? -1.0f : 1.0f;
       float3 nn = mh * sgn;
-      Mat m = fetch_mat(c.P, f);
+      Mat m = fetch_mat(c.P, key);
       float3 Nb = mk3(0, 0, 0), Pb = Pnext;
       float dm[5] = {0, 0, 0, 0, 0};
       float3 gC = mul(g, T[b]);
@@ -833,7 +852,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_adjoint(KCtx c, long long j0, int
       for (int k = 0; k < 5; ++k) vals[9 + k] = dm[k];
     }
     bool leader;
-    warp_reduce_peers<14>(face, vals, scr, leader);
+    warp_reduce_peers<14>(key, vals, scr, leader);
     if (leader) {
       if (dV) {
 #pragma unroll
@@ -846,7 +865,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_adjoint(KCtx c, long long j0, int
       }
       if (dF) {
 #pragma unroll
-        for (int k = 0; k < 5; ++k) atomicAdd(&dF[5 * face + k], vals[9 + k]);
+        for (int k = 0; k < 5; ++k) atomicAdd(&dF[5 * key + k], vals[9 + k]);
       }
     }
   }

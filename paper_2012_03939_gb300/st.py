@@ -51,7 +51,7 @@ class View(C.Structure):
 class SceneDesc(C.Structure):
     _fields_ = [("n_vertices", C.c_int), ("n_faces", C.c_int), ("vertices", C.c_void_p), ("faces", C.c_void_p),
                 ("face_params", C.c_void_p), ("brdf", C.c_int), ("n_point_lights", C.c_int),
-                ("point_lights", C.c_void_p), ("env", C.c_void_p)]
+                ("point_lights", C.c_void_p), ("env", C.c_void_p), ("color_res", C.c_int)]
 
 
 class RenderOpts(C.Structure):
@@ -142,12 +142,14 @@ class Scene:
     """A mesh scene on the current CUDA device (owns a library scene handle)."""
 
     def __init__(self, vertices: torch.Tensor, faces: torch.Tensor, face_params: torch.Tensor, brdf: str = "ggx",
-                 light_pos=None, light_intensity=None, env: Optional[np.ndarray] = None, stream=None):
+                 light_pos=None, light_intensity=None, env: Optional[np.ndarray] = None, stream=None,
+                 color_res: int = 0):
         dev = torch.device("cuda", torch.cuda.current_device())
         self.vertices = vertices.detach().to(dev, torch.float32).contiguous()
         self.faces = faces.detach().to(dev, torch.int32).contiguous()
         self.face_params = face_params.detach().to(dev, torch.float32).contiguous()
         self.nv, self.nf = self.vertices.shape[0], self.faces.shape[0]
+        self.ntex = self.face_params.shape[0]      # texels: faces * (r+1)(r+2)/2
         lp = np.zeros((0, 3), np.float32) if light_pos is None else np.asarray(light_pos, np.float32).reshape(-1, 3)
         li = np.zeros((0, 3), np.float32) if light_intensity is None else np.asarray(light_intensity,
                                                                                     np.float32).reshape(-1, 3)
@@ -160,7 +162,8 @@ class Scene:
             self._env = EnvMap(self._env_arr.shape[1], self._env_arr.shape[0], self._env_arr.ctypes.data)
         desc = SceneDesc(self.nv, self.nf, self.vertices.data_ptr(), self.faces.data_ptr(),
                          self.face_params.data_ptr(), {"ggx": 0, "beckmann": 1}[brdf], len(lp),
-                         C.addressof(self._lights), None if self._env is None else C.addressof(self._env))
+                         C.addressof(self._lights), None if self._env is None else C.addressof(self._env),
+                         int(color_res))
         h = C.c_void_p()
         _check(lib().st_scene_create(C.byref(desc), _stream(stream), C.byref(h)))
         self.handle = h
@@ -169,7 +172,7 @@ class Scene:
     def from_scene(cls, sc, vertices=None, device="cuda"):
         V = torch.as_tensor(sc.vertices if vertices is None else vertices, dtype=torch.float32, device=device)
         return cls(V, torch.as_tensor(sc.faces, device=device), torch.as_tensor(sc.face_params, device=device),
-                   sc.brdf, sc.light_pos, sc.light_intensity, sc.env)
+                   sc.brdf, sc.light_pos, sc.light_intensity, sc.env, color_res=getattr(sc, "color_res", 0))
 
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:
@@ -214,7 +217,7 @@ class Scene:
         if want_vertices and d_vertices is None:
             d_vertices = torch.zeros((self.nv, 3), dtype=torch.float32, device=dLdI.device)
         if want_params and d_face_params is None:
-            d_face_params = torch.zeros((self.nf, 5), dtype=torch.float32, device=dLdI.device)
+            d_face_params = torch.zeros((self.ntex, 5), dtype=torch.float32, device=dLdI.device)
         _check(lib().st_render_backward(self.handle, vs, len(vs), default_spp, max_bounces, seed,
                                         None if opts is None else C.byref(opts), dLdI.data_ptr(),
                                         None if d_vertices is None else d_vertices.data_ptr(),
