@@ -44,7 +44,7 @@ class _View(C.Structure):
 
 class _Params(C.Structure):
     _fields_ = [("max_bounces", C.c_int), ("seed", C.c_ulonglong), ("edge_mode", C.c_int),
-                ("edge_spp", C.c_int), ("n_threads", C.c_int)]
+                ("edge_spp", C.c_int), ("n_threads", C.c_int), ("secondary", C.c_int)]
 
 
 _lib = None
@@ -120,8 +120,8 @@ class OracleScene:
         self.ntex = len(self.P)          # texels (= faces at mesh-colors resolution 0)
 
 
-def params(max_bounces, seed, edge_mode=0, edge_spp=0, n_threads=0):
-    return _Params(max_bounces, seed, edge_mode, edge_spp, n_threads)
+def params(max_bounces, seed, edge_mode=0, edge_spp=0, n_threads=0, secondary=0):
+    return _Params(max_bounces, seed, edge_mode, edge_spp, n_threads, secondary)
 
 
 def render_pixels(osc: OracleScene, prm, pix):

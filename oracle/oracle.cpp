@@ -46,6 +46,14 @@
 //    +-EDGE_EPS pixels along the screen normal with shared random numbers, and
 //    scatter (L- - L+) <dL/dI_pixel> v_n * n_cand * len / N_e to the two
 //    endpoints with screen-space weights (1 - tau, tau).
+//  * Edge term (secondary visibility, gradients only, orc_params.secondary):
+//    at every vertex b of a camera path, one edge of the mesh picked uniformly
+//    (u from counter (c0, c1, b<<4|3, stream): integer pick (u0>>8)*E>>24, u1
+//    along the edge), kept if it is a silhouette seen from the vertex (or every
+//    edge, edge_mode 1), is not an edge of the vertex's face, and has a part
+//    above the tangent plane; a point uniform on that part; two side paths at
+//    +-SEC_EPS radians across the edge's arc continue the path from vertex
+//    b + 1 (counters (c0, c1, vertex<<4|call, 16 + b)); see secondary_edge().
 #include "oracle.h"
 
 #include <algorithm>
@@ -54,6 +62,7 @@
 #include <cstring>
 #include <map>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 namespace {
@@ -62,8 +71,12 @@ constexpr double PI = 3.14159265358979323846;
 constexpr double T_EPS = 1e-5;
 constexpr double Z_NEAR = 1e-4;
 constexpr double EDGE_EPS = 1e-3;
+constexpr double SEC_EPS = 1e-4;     // secondary edge: angular offset of the two side rays (radians)
+constexpr double SEC_BAND = 1e-5;    // secondary edge: plane-distance band, times (1 + |p|_inf)
+constexpr double SEC_RMIN = 1e-6;    // secondary edge: nearest edge point accepted
+constexpr double SEC_SMIN = 1e-6;    // secondary edge: sine of the edge/view angle accepted
 constexpr int MAX_B = 8;
-constexpr int MAXD = 14 * MAX_B;
+constexpr int MAXD = 20 * MAX_B;
 
 // ---------------------------------------------------------------- Philox
 struct U4 { uint32_t w[4]; };
@@ -532,12 +545,139 @@ struct Tape {
   V3d take(const V3d& a) { return V3d{take(a.x), take(a.y), take(a.z)}; }
 };
 
+// ---------------------------------------------------------------- edges
+struct Edge { int a, b; int f[2]; int nf; };
+
+std::vector<Edge> edge_list(const Scene& s) {
+  std::map<std::pair<int, int>, Edge> m;
+  for (int f = 0; f < s.nf; ++f)
+    for (int k = 0; k < 3; ++k) {
+      int a = s.face[3 * f + k], b = s.face[3 * f + (k + 1) % 3];
+      std::pair<int, int> key(std::min(a, b), std::max(a, b));
+      auto it = m.find(key);
+      if (it == m.end()) {
+        Edge e{key.first, key.second, {f, -1}, 1};
+        m.emplace(key, e);
+      } else {
+        if (it->second.nf < 2) it->second.f[it->second.nf] = f;
+        it->second.nf++;
+      }
+    }
+  std::vector<Edge> out;
+  out.reserve(m.size());
+  for (auto& kv : m) out.push_back(kv.second);  // std::map iterates in (min, max) order
+  return out;
+}
+
+// Secondary-visibility edge sampling context: the mesh's edge list and the
+// candidate rule (0 = silhouettes as seen from the vertex, 1 = every edge).
+struct SecCtx { const std::vector<Edge>* E; int mode; };
+
+// Signed distance of p from the plane of face f (unit normal of the face's winding).
+double face_side(const Scene& s, int f, const V3d& p) {
+  const int* fi = &s.face[3 * f];
+  V3d a = s.vert[fi[0]];
+  V3d m = nrm(cross(s.vert[fi[1]] - a, s.vert[fi[2]] - a));
+  return dot(m, p - a);
+}
+
+template <class T>
+void trace_path(const Scene& s, const Rng& rng, int B, const V3d& eye, const V3d& d0, uint32_t c0,
+                uint32_t c1, uint32_t stream, Vars* vars, T L[3], long long& segments, Tape* tape = nullptr,
+                const SecCtx* sec = nullptr, int b0 = 0, int origin0 = -1);
+
+// One secondary-visibility edge sample at path vertex b (the boundary term of
+// the vertex's integral over incoming directions; Li et al.'s edge sampling,
+// which the paper's gradient relies on, Sec. 3.2). The integrand g(w) = f cos
+// L_in(w) jumps where the direction crosses the image of a mesh edge on the
+// vertex's sphere of directions; moving the edge's endpoints (x) or the vertex
+// (p) moves that arc by m.(dx - dp)/r along its normal m. The boundary term
+// integral over the arc of (g(w - eps m) - g(w + eps m)) m.(dx - dp)/r is
+// estimated with one edge picked uniformly from all E mesh edges, one point x
+// uniform along the part of it above the vertex's tangent plane, and two side
+// paths (shared random numbers, stream 16 + b) that continue the path from
+// vertex b + 1. Arc length per unit edge length is |w x t|/r, t the unit edge
+// direction, so the sample's weight is |w x t| E len (tau1 - tau0) / r^2 times
+// T_b (g- - g+). It is added to L as a dual with zero value whose derivative is
+// that weight times m.(dx - dp), dx = (1 - tau) dA + tau dB.
+void secondary_edge(const Scene& s, const Rng& rng, int B, int b, const V3<Dual>& p, const V3d& nv, const V3d& wo,
+                    int f0, long long tex, const Dual thr[3], uint32_t c0, uint32_t c1, uint32_t stream,
+                    const SecCtx& sc, Vars* vars, Dual L[3], long long& segments) {
+  const std::vector<Edge>& E = *sc.E;
+  if (E.empty()) return;
+  U4 u = rng.draw(c0, c1, (uint32_t)(b << 4) | 3u, stream);
+  uint64_t nE = E.size();
+  const Edge& e = E[(size_t)(((uint64_t)(u.w[0] >> 8) * nE) >> 24)];
+  if (e.f[0] == f0 || (e.nf >= 2 && e.f[1] == f0)) return;   // its arc lies on the vertex's horizon
+  V3d pv = val(p);
+  V3d A = s.vert[e.a], Bv = s.vert[e.b];
+  double bnd = SEC_BAND * (1.0 + std::max(std::fabs(pv.x), std::max(std::fabs(pv.y), std::fabs(pv.z))));
+  if (sc.mode == 0) {
+    double s1 = face_side(s, e.f[0], pv);
+    bool sil;
+    if (e.nf == 2) {
+      double s2 = face_side(s, e.f[1], pv);
+      sil = (s1 > bnd && s2 < -bnd) || (s1 < -bnd && s2 > bnd);
+    } else {
+      sil = std::fabs(s1) > bnd;
+    }
+    if (!sil) return;
+  }
+  // the part of the edge above the tangent plane (below it the BRDF is zero)
+  double hA = dot(nv, A - pv), hB = dot(nv, Bv - pv);
+  if (!(hA > bnd) && !(hB > bnd)) return;
+  double t0 = 0.0, t1 = 1.0;
+  if (!(hA > bnd)) t0 = (bnd - hA) / (hB - hA);
+  if (!(hB > bnd)) t1 = (hA - bnd) / (hA - hB);
+  if (!(t1 > t0)) return;
+  double tau = t0 + unif(u.w[1]) * (t1 - t0);
+  V3d tv = Bv - A;
+  V3d x = A + scl(tv, tau);
+  V3d dv = x - pv;
+  double r = len(dv);
+  if (!(r > SEC_RMIN)) return;
+  V3d w = scl(dv, 1.0 / r);
+  double l = len(tv);
+  V3d cr = cross(w, scl(tv, 1.0 / l));
+  double sn = len(cr);
+  if (!(sn > SEC_SMIN)) return;
+  V3d mh = scl(cr, 1.0 / sn);
+  double coef = sn * (double)nE * l * (t1 - t0) / (r * r);
+  MatT<double> m = Access<double>::params(s, nullptr, (int)tex);
+  double g[2][3];
+  for (int side = 0; side < 2; ++side) {
+    V3d ws = nrm(w + scl(mh, side == 0 ? -SEC_EPS : SEC_EPS));
+    double f[3], Li[3];
+    brdf_eval(s.brdf, m, nv, ws, wo, f);
+    double ci = dot(nv, ws);
+    trace_path<double>(s, rng, B, pv, ws, c0, c1, 16u + (uint32_t)b, nullptr, Li, segments, nullptr, nullptr, b + 1,
+                       f0);
+    for (int c = 0; c < 3; ++c) g[side][c] = ci > 0 ? f[c] * ci * Li[c] : 0.0;
+  }
+  double k[3];
+  bool any = false;
+  for (int c = 0; c < 3; ++c) {
+    k[c] = thr[c].v * (g[0][c] - g[1][c]) * coef;
+    any |= k[c] != 0.0;
+  }
+  if (!any) return;
+  V3<Dual> Ad = Access<Dual>::vertex(s, vars, e.a), Bd = Access<Dual>::vertex(s, vars, e.b);
+  V3<Dual> xd = scl(Ad, 1.0 - tau) + scl(Bd, tau);
+  Dual ed = dot(lift<Dual>(mh), xd - p);
+  Dual z = ed - ed.v;
+  for (int c = 0; c < 3; ++c) L[c] = L[c] + z * k[c];
+}
+
 // ---------------------------------------------------------------- one path
 // Radiance of one path whose primary ray is (eye, d0). Counter words (c0, c1,
 // stream) identify the path; `segments` counts ray queries.
+// b0 > 0 starts a path at vertex b0 from a point on face origin0 (a side path of
+// a secondary edge sample): its first ray collects the environment unweighted,
+// and a first ray that would find vertex B adds nothing.
 template <class T>
 void trace_path(const Scene& s, const Rng& rng, int B, const V3d& eye, const V3d& d0, uint32_t c0,
-                uint32_t c1, uint32_t stream, Vars* vars, T L[3], long long& segments, Tape* tape = nullptr) {
+                uint32_t c1, uint32_t stream, Vars* vars, T L[3], long long& segments, Tape* tape,
+                const SecCtx* sec, int b0, int origin0) {
   using A = Access<T>;
   Tape none;
   Tape& tp = tape ? *tape : none;
@@ -545,9 +685,9 @@ void trace_path(const Scene& s, const Rng& rng, int B, const V3d& eye, const V3d
   T thr[3] = {T(1.0), T(1.0), T(1.0)};
   V3<T> o = lift<T>(eye);
   V3d d = d0;
-  int origin = -1;
+  int origin = origin0;
   double last_pdf = 0;
-  for (int b = 0; b < B; ++b) {
+  for (int b = b0;; ++b) {
     ++segments;
     Hit h = closest(s, val(o), d, origin, INFINITY);
     if (h.tri < 0) {
@@ -555,7 +695,7 @@ void trace_path(const Scene& s, const Rng& rng, int B, const V3d& eye, const V3d
         double st;
         int tx = env_texel(s, d, st);
         double w = 1.0;
-        if (b > 0) {
+        if (b > b0) {
           double pe = env_pdf(s, tx, st);
           w = last_pdf * last_pdf / (last_pdf * last_pdf + pe * pe);
         }
@@ -564,6 +704,7 @@ void trace_path(const Scene& s, const Rng& rng, int B, const V3d& eye, const V3d
       }
       return;
     }
+    if (b >= B) return;
     const int* fi = &s.face[3 * h.tri];
     V3<T> v0 = A::vertex(s, vars, fi[0]);
     V3<T> v1 = A::vertex(s, vars, fi[1]);
@@ -627,6 +768,9 @@ void trace_path(const Scene& s, const Rng& rng, int B, const V3d& eye, const V3d
           }
         }
       }
+    }
+    if constexpr (std::is_same<T, Dual>::value) {
+      if (sec) secondary_edge(s, rng, B, b, p, nv, wo_d, h.tri, tex, thr, c0, c1, stream, *sec, vars, L, segments);
     }
     if (b == B - 1) return;
     // BSDF sampling (direction and pdf held constant under differentiation)
@@ -696,30 +840,6 @@ void scatter_grad(const Vars& vars, const Dual& loss, double* dv, double* df) {
       int dim = vars.fdim[i] + k;
       if (dim < loss.n && df) df[5 * vars.fid[i] + k] += loss.g[dim];
     }
-}
-
-// ---------------------------------------------------------------- edges
-struct Edge { int a, b; int f[2]; int nf; };
-
-std::vector<Edge> edge_list(const Scene& s) {
-  std::map<std::pair<int, int>, Edge> m;
-  for (int f = 0; f < s.nf; ++f)
-    for (int k = 0; k < 3; ++k) {
-      int a = s.face[3 * f + k], b = s.face[3 * f + (k + 1) % 3];
-      std::pair<int, int> key(std::min(a, b), std::max(a, b));
-      auto it = m.find(key);
-      if (it == m.end()) {
-        Edge e{key.first, key.second, {f, -1}, 1};
-        m.emplace(key, e);
-      } else {
-        if (it->second.nf < 2) it->second.f[it->second.nf] = f;
-        it->second.nf++;
-      }
-    }
-  std::vector<Edge> out;
-  out.reserve(m.size());
-  for (auto& kv : m) out.push_back(kv.second);  // std::map iterates in (min, max) order
-  return out;
 }
 
 struct Cand { int e; double t0, t1, len; V3d sa, sb; };
@@ -899,6 +1019,10 @@ long long orc_grad_pixels(const orc_scene* in, const orc_view* views, int n_view
   std::vector<long long> seg(nt, 0);
   std::vector<std::vector<double>> gv(nt, std::vector<double>(3 * (size_t)s.nv, 0.0));
   std::vector<std::vector<double>> gf(nt, std::vector<double>(5 * (size_t)s.nf * s.ntex, 0.0));
+  std::vector<Edge> E;
+  if (p->secondary) E = edge_list(s);
+  SecCtx sc{&E, p->edge_mode};
+  const SecCtx* sec = p->secondary ? &sc : nullptr;
   parallel_for(n, nt, [&](int tid, int i) {
     const double* w = dLdI + 3 * (size_t)i;
     if (w[0] == 0 && w[1] == 0 && w[2] == 0) return;
@@ -911,7 +1035,7 @@ long long orc_grad_pixels(const orc_scene* in, const orc_view* views, int n_view
       V3d d = cam_dir(c, x + unif(u.w[0]), y + unif(u.w[1]));
       Vars vars;
       Dual L[3];
-      trace_path<Dual>(s, rng, p->max_bounces, c.eye, d, c0, (uint32_t)sidx, 0u, &vars, L, seg[tid]);
+      trace_path<Dual>(s, rng, p->max_bounces, c.eye, d, c0, (uint32_t)sidx, 0u, &vars, L, seg[tid], nullptr, sec);
       Dual loss = L[0] * (w[0] / c.spp) + L[1] * (w[1] / c.spp) + L[2] * (w[2] / c.spp);
       scatter_grad(vars, loss, gv[tid].data(), gf[tid].data());
     }
@@ -1009,7 +1133,11 @@ long long orc_trace_screen(const orc_scene* in, const orc_view* view, const orc_
   }
   Vars vars;
   Dual L[3];
-  trace_path<Dual>(s, rng, p->max_bounces, c.eye, d, c0, c1, stream, &vars, L, seg);
+  std::vector<Edge> E;
+  if (p->secondary) E = edge_list(s);
+  SecCtx sc{&E, p->edge_mode};
+  trace_path<Dual>(s, rng, p->max_bounces, c.eye, d, c0, c1, stream, &vars, L, seg, nullptr,
+                   p->secondary ? &sc : nullptr);
   for (int k = 0; k < 3; ++k) rgb[k] = L[k].v;
   Dual loss = L[0] * grad_w[0] + L[1] * grad_w[1] + L[2] * grad_w[2];
   scatter_grad(vars, loss, d_verts, d_face);

@@ -16,7 +16,8 @@
  *   - the gradient of sum_p <dL/dI_p, I_p> with respect to vertex positions and
  *     per-face parameters (the quantity an MSE loss as in Sec. 3.2 needs),
  *     interior part by sparse forward-mode dual numbers, primary-visibility
- *     edge part by edge sampling.
+ *     edge part by edge sampling in screen space, secondary-visibility edge
+ *     part by edge sampling on each path vertex's sphere of directions.
  * The exact estimator (random-number layout, conventions) is stated in
  * oracle.cpp's header comment.
  */
@@ -55,6 +56,7 @@ typedef struct {
   int edge_mode;    /* 0 = silhouette edges, 1 = every mesh edge */
   int edge_spp;     /* edge samples per pixel; 0 = the view's spp */
   int n_threads;    /* 0 = all hardware threads */
+  int secondary;    /* gradients: add the secondary-visibility edge term at every path vertex */
 } orc_params;
 
 /* Pixel values for a list of pixels (view index, x, y): out [n][3]. Returns the
@@ -63,7 +65,8 @@ long long orc_render_pixels(const orc_scene* s, const orc_view* views, int n_vie
                             const orc_params* p, const int* pix /*[n][3]*/, int n,
                             double* out /*[n][3]*/);
 
-/* Interior gradient for the listed pixels with weights dLdI [n][3]:
+/* Interior gradient for the listed pixels with weights dLdI [n][3] (plus the
+ * secondary-visibility edge term at every path vertex when p->secondary):
  * d_verts [V][3] and d_face [texels][5] are ACCUMULATED (+=). Returns segments or -1. */
 long long orc_grad_pixels(const orc_scene* s, const orc_view* views, int n_views,
                           const orc_params* p, const int* pix, int n, const double* dLdI,

@@ -1,0 +1,266 @@
+"""Pins of the oracle's secondary-visibility edge term (boundary term at every path vertex).
+
+At a path vertex the estimator integrates f cos L_in over incoming directions;
+L_in jumps where a direction crosses a mesh edge that occludes what lies
+behind it. Moving the mesh moves those jumps, and the boundary (edge) term
+accounts for it. The pins below check the oracle's estimate of it against
+values that neither the oracle nor the CUDA library computes:
+
+* a closed form: a Lambertian floor under a uniform environment, shadowed by a
+  floating triangle, has L_o = kd L0 (1 - P/pi) with P the triangle's projected
+  solid angle (Lambert's polygon formula), so every pixel's derivative with
+  respect to every vertex follows from Gauss quadrature over the pixel and
+  central differences;
+* a two-bounce quadrature: the same floor lit only from below the horizon, so
+  all its light arrives after one reflection off the floating triangle's
+  underside (itself lit by the environment around the floor). The pixel value is
+  then a smooth integral over the triangle of the underside's closed-form
+  radiance, which Gauss quadrature evaluates to high accuracy.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2012_03939_gb300 import scenes as S
+from tests import _geom as G
+
+
+def _ray_tri(o, d, a, b, c):
+    """Möller-Trumbore for many rays (o [3], d [N,3]) against one triangle: t [N] (inf on a miss)."""
+    e1, e2 = b - a, c - a
+    pv = np.cross(d, e2)
+    det = pv @ e1
+    inv = 1.0 / det
+    tv = o - a
+    u = (pv @ tv) * inv
+    qv = np.cross(tv, e1)
+    v = (d @ qv) * inv
+    t = (qv @ e2) * inv
+    ok = (u >= 0) & (v >= 0) & (u + v <= 1) & (t > 0)
+    return np.where(ok, t, np.inf)
+
+
+def _projected_solid_angle(p, n, poly):
+    """Lambert's formula: projected solid angle of a polygon above the horizon, seen from points p [N,3]."""
+    tot = np.zeros(len(p))
+    k = len(poly)
+    for i in range(k):
+        a, b = poly[i] - p, poly[(i + 1) % k] - p
+        c = np.cross(a, b)
+        cn = np.linalg.norm(c, axis=1)
+        theta = np.arctan2(cn, np.einsum("ij,ij->i", a, b))
+        tot += theta * np.einsum("ij,ij->i", n, c) / cn
+    return np.abs(tot) / 2
+
+
+def _occluder_scene(spp=1):
+    V = np.array([[-3, 0, -3], [3, 0, -3], [3, 0, 3], [-3, 0, 3],
+                  [-0.45, 0.30, -0.30], [0.50, 0.38, -0.15], [0.05, 0.33, 0.55]], np.float64)
+    F = np.array([[0, 2, 1], [0, 3, 2], [4, 5, 6]], np.int32)
+    P = np.array([[0.7, 0.5, 0.3, 0.0, 0.5], [0.7, 0.5, 0.3, 0.0, 0.5], [0.5, 0.5, 0.5, 0.0, 0.5]], np.float32)
+    env = np.ones((4, 8, 3), np.float32)
+    vs = [S.View((0.9, 2.2, 1.6), (0.0, 0.0, 0.1), (0.0, 1.0, 0.0), 40.0, 12, 12, spp)]
+    return S.Scene("occluder", V.astype(np.float32), F, P, "ggx", env=env, views=vs, max_bounces=1)
+
+
+def _pixel_rays(v, pix, n_gauss):
+    """Eye and unit directions of an n x n Gauss-Legendre rule over every listed pixel: d [pixels * n^2, 3]."""
+    gx, gw = np.polynomial.legendre.leggauss(n_gauss)
+    gx, gw = (gx + 1) / 2, gw / 2
+    ux, uy = np.meshgrid(gx, gx)
+    eye, fwd, right, up, th = G.camera_frame(v)
+    px = (pix[:, 1:2] + ux.ravel()[None, :]).ravel()
+    py = (pix[:, 2:3] + uy.ravel()[None, :]).ravel()
+    sx = 2 * px / v.width - 1
+    sy = 1 - 2 * py / v.height
+    d = fwd[None, :] + right[None, :] * (sx * th * v.width / v.height)[:, None] + up[None, :] * (sy * th)[:, None]
+    return eye, d / np.linalg.norm(d, axis=1, keepdims=True), np.outer(gw, gw).ravel()
+
+
+def _floor_hits(V, o, d):
+    """Hit points and normals (facing the ray's origin) of rays on the two floor triangles of V."""
+    floor = [V[[0, 2, 1]], V[[0, 3, 2]]]
+    ts = np.stack([_ray_tri(o, d, *tri) for tri in floor])
+    k = np.argmin(ts, 0)
+    t = ts[k, np.arange(len(d))]
+    assert np.all(np.isfinite(t))
+    p = o + d * t[:, None]
+    n = np.stack([np.cross(tri[1] - tri[0], tri[2] - tri[0]) for tri in floor])[k]
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    n *= np.where(np.einsum("ij,ij->i", n, d) < 0, 1.0, -1.0)[:, None]
+    return p, n
+
+
+def _free_pixels(sc):
+    v = sc.views[0]
+    occ = G.project(v, sc.vertices[4:7].astype(np.float64))
+    out = []
+    for y in range(v.height):
+        for x in range(v.width):
+            if len(G.clip_polygon(occ, x - 0.05, y - 0.05, x + 1.05, y + 1.05)) < 3:
+                out.append((0, x, y))
+    return np.array(out, np.int32)
+
+
+def _closed_form_pixels(sc, V, pix, n_gauss=8):
+    """Pixel means of kd L0 (1 - P/pi) over each pixel (Gauss-Legendre), camera rays on the floor of V."""
+    eye, d, wpx = _pixel_rays(sc.views[0], pix, n_gauss)
+    p, n = _floor_hits(V, eye, d)
+    occ = V[4:7]
+    assert np.all(occ[None, :, 1] - p[:, None, 1] > 0.2)
+    L = (1.0 - _projected_solid_angle(p, n, occ) / math.pi).reshape(len(pix), -1) @ wpx
+    return L[:, None] * sc.face_params[0, :3].astype(np.float64)[None, :]
+
+
+def test_closed_form_occluded_floor_value():
+    # the forward estimator itself reproduces the closed form (B = 1: one vertex,
+    # environment NEE). A uniform environment is sampled uniformly over the sphere,
+    # so one sample is 4 kd cos(theta) on the upper hemisphere and 0 below: its
+    # standard deviation is at most sqrt(5/3) kd.
+    spp = 1 << 15
+    sc = _occluder_scene(spp=spp)
+    pix = _free_pixels(sc)[::5]
+    exp = _closed_form_pixels(sc, sc.vertices.astype(np.float64), pix)
+    got, _ = O.render_pixels(O.OracleScene(sc), O.params(1, 3), pix)
+    se = math.sqrt(5.0 / 3.0) * sc.face_params[0, :3] / math.sqrt(spp)
+    assert np.all(np.abs(got - exp) < 4 * se), (got, exp, se)
+    assert exp.min() < 0.8 * exp.max()     # the pixels include the penumbra
+
+
+def test_secondary_edge_gradient_matches_closed_form():
+    sc = _occluder_scene(spp=512)
+    pix = _free_pixels(sc)
+    V0 = sc.vertices.astype(np.float64)
+    rng = np.random.default_rng(31)
+    w = rng.normal(size=(len(pix), 3))
+    h = 1e-5
+    exp = np.zeros_like(V0)
+    for vi in range(len(V0)):
+        for k in range(3):
+            Vp, Vm = V0.copy(), V0.copy()
+            Vp[vi, k] += h
+            Vm[vi, k] -= h
+            exp[vi, k] = ((_closed_form_pixels(sc, Vp, pix) - _closed_form_pixels(sc, Vm, pix)) * w).sum() / (2 * h)
+    ests, plain = [], []
+    osc = O.OracleScene(sc)
+    for seed in range(8):
+        dv, _, _ = O.grad_pixels(osc, O.params(1, 700 + seed, secondary=1), pix, w)
+        ests.append(dv)
+        if seed < 2:
+            plain.append(O.grad_pixels(osc, O.params(1, 700 + seed), pix, w)[0])
+    ests = np.array(ests)
+    mean, se = ests.mean(0), ests.std(0, ddof=1) / math.sqrt(len(ests))
+    scale = np.abs(exp).max()
+    assert np.all(np.abs(mean - exp) < 4 * se + 2e-3 * scale), (mean, exp, se)
+    # the occluder's vertices receive their whole gradient from the boundary term:
+    # without it the estimate is exactly zero there
+    assert np.abs(exp[4:]).max() > 0.2 * scale
+    assert np.all(np.array(plain)[:, 4:] == 0)
+
+
+
+def _duffy_rule(n):
+    """Barycentric points (alpha, beta) and weights (summing to 1/2) of an n x n Gauss rule on the unit triangle."""
+    g, w = np.polynomial.legendre.leggauss(n)
+    g, w = (g + 1) / 2, w / 2
+    u, v = np.meshgrid(g, g, indexing="ij")
+    wu, wv = np.meshgrid(w, w, indexing="ij")
+    return u.ravel(), (v * (1 - u)).ravel(), (wu * wv * (1 - u)).ravel()
+
+
+def _underside_scene(spp=1, L0=100.0):
+    V = np.array([[-1.5, 0, -1.5], [1.5, 0, -1.5], [1.5, 0, 1.5], [-1.5, 0, 1.5],
+                  [-0.45, 0.6, -0.30], [0.50, 0.6, -0.15], [0.05, 0.6, 0.55]], np.float64)
+    F = np.array([[0, 2, 1], [0, 3, 2], [4, 5, 6]], np.int32)
+    P = np.array([[0.7, 0.5, 0.3, 0.0, 0.5], [0.7, 0.5, 0.3, 0.0, 0.5], [0.4, 0.6, 0.8, 0.0, 0.5]], np.float32)
+    env = np.zeros((4, 8, 3), np.float32)
+    env[2:] = L0                     # rows below the horizon (theta > pi/2) only
+    vs = [S.View((0.9, 2.2, 1.6), (0.0, 0.0, 0.1), (0.0, 1.0, 0.0), 40.0, 12, 12, spp)]
+    return S.Scene("underside", V.astype(np.float32), F, P, "ggx", env=env, views=vs, max_bounces=2)
+
+
+def _floor_pixels(sc):
+    v = sc.views[0]
+    V = sc.vertices.astype(np.float64)
+    occ = G.project(v, V[4:7])
+    floor = G.project(v, V[0:4])
+    out = []
+    for y in range(v.height):
+        for x in range(v.width):
+            inside = abs(G.polygon_area(G.clip_polygon(floor, x - 0.05, y - 0.05, x + 1.05, y + 1.05)) - 1.21) < 1e-9
+            if inside and len(G.clip_polygon(occ, x - 0.05, y - 0.05, x + 1.05, y + 1.05)) < 3:
+                out.append((0, x, y))
+    return np.array(out, np.int32)
+
+
+def _two_bounce_pixels(sc, V, pix, L0=100.0, n_gauss=4, n_tri=12):
+    """Pixel means of the B = 2 estimator's expectation: floor point p receives, from every point q
+    of the triangle's underside, L1(q) = kd_o L0 (1 - P_floor(q)/pi) (the environment below the
+    horizon that the floor does not hide), times the geometry term cos_p cos_q / r^2."""
+    kd_f = sc.face_params[0, :3].astype(np.float64)
+    kd_o = sc.face_params[2, :3].astype(np.float64)
+    floor = [V[[0, 2, 1]], V[[0, 3, 2]]]
+    a, b, c = V[4], V[5], V[6]
+    al, be, wq = _duffy_rule(n_tri)
+    q = a + al[:, None] * (b - a) + be[:, None] * (c - a)
+    m = np.cross(b - a, c - a)
+    area2 = np.linalg.norm(m)
+    nq = m / area2
+    if nq[1] > 0:
+        nq = -nq                          # the underside faces the floor
+    nqs = np.broadcast_to(nq, q.shape)
+    for tri in floor:
+        assert np.all((tri[None, :, :] - q[:, None, :]) @ nq > 0.1)
+    L1 = 1.0 - sum(_projected_solid_angle(q, nqs, tri) for tri in floor) / math.pi   # times kd_o L0
+    wq = wq * area2                       # dA = |m| d(alpha) d(beta)
+    eye, d, wpx = _pixel_rays(sc.views[0], pix, n_gauss)
+    p, npf = _floor_hits(V, eye, d)
+    dv = q[None, :, :] - p[:, None, :]                      # [pixel points, q points, 3]
+    r2 = np.einsum("ijk,ijk->ij", dv, dv)
+    r = np.sqrt(r2)
+    cp = np.einsum("ijk,ik->ij", dv, npf) / r
+    cq = -(dv @ nq) / r
+    assert np.all(cp > 0) and np.all(cq > 0)
+    E = ((cp * cq / r2 * L1[None, :]) @ wq).reshape(len(pix), -1) @ wpx
+    return E[:, None] * (kd_f * kd_o * L0 / math.pi)[None, :]
+
+
+def test_two_bounce_quadrature_value():
+    spp = 1 << 14
+    sc = _underside_scene(spp=spp)
+    pix = _floor_pixels(sc)[::4]
+    exp = _two_bounce_pixels(sc, sc.vertices.astype(np.float64), pix)
+    vals = np.array([O.render_pixels(O.OracleScene(sc), O.params(2, 40 + s), pix)[0] for s in range(4)])
+    mean, se = vals.mean(0), vals.std(0, ddof=1) / 2
+    assert np.all(np.abs(mean - exp) < 4 * se + 1e-3 * exp.max()), (mean, exp, se)
+    assert exp.min() > 0.02
+
+
+def test_secondary_edge_gradient_two_bounces_matches_quadrature():
+    # every bit of the floor's light takes two bounces, so the gradient exercises
+    # side paths that continue to a shaded vertex (edges seen from the floor) and
+    # edges seen from the triangle's underside (the floor's boundary), with the
+    # vertex-motion part chained back through the earlier vertex
+    sc = _underside_scene(spp=4096)
+    pix = _floor_pixels(sc)
+    V0 = sc.vertices.astype(np.float64)
+    rng = np.random.default_rng(32)
+    w = rng.normal(size=(len(pix), 3))
+    h = 1e-5
+    exp = np.zeros_like(V0)
+    for vi in range(len(V0)):
+        for k in range(3):
+            Vp, Vm = V0.copy(), V0.copy()
+            Vp[vi, k] += h
+            Vm[vi, k] -= h
+            exp[vi, k] = ((_two_bounce_pixels(sc, Vp, pix) - _two_bounce_pixels(sc, Vm, pix)) * w).sum() / (2 * h)
+    osc = O.OracleScene(sc)
+    ests = np.array([O.grad_pixels(osc, O.params(2, 800 + s, secondary=1), pix, w)[0] for s in range(8)])
+    mean, se = ests.mean(0), ests.std(0, ddof=1) / math.sqrt(len(ests))
+    scale = np.abs(exp).max()
+    assert np.all(np.abs(mean - exp) < 4 * se + 2e-3 * scale), (mean, exp, se)
+    # the pin tells the full estimator from one without the boundary term
+    plain = np.array([O.grad_pixels(osc, O.params(2, 800 + s), pix, w)[0] for s in range(4)]).mean(0)
+    assert (np.abs(plain - exp) / (se + 1e-3 * scale)).max() > 10, (plain, exp, se)
