@@ -57,6 +57,8 @@ typedef enum {
 #define ST_BRDF_BECKMANN 1
 #define ST_EDGE_SILHOUETTE 0  /* edges whose two faces face opposite ways, and boundary edges */
 #define ST_EDGE_ALL 1         /* every mesh edge (also the shading discontinuities of flat faces) */
+#define ST_EDGE_TERM_PRIMARY 1    /* edge_term bit: primary visibility (image-space edges) */
+#define ST_EDGE_TERM_SECONDARY 2  /* edge_term bit: secondary visibility (edges seen from path vertices) */
 #define ST_MODE_BATCHED 0     /* all views in one job space, persistent kernels, optional CUDA graph */
 #define ST_MODE_PER_VIEW 1    /* one view at a time, grids sized from host-read queue counts */
 
@@ -106,8 +108,9 @@ typedef struct {
 } st_scene_desc;
 
 typedef struct {
-  int edge_term;    /* backward: add the primary-visibility edge term (1) or not (0) */
-  int edge_mode;    /* ST_EDGE_SILHOUETTE or ST_EDGE_ALL */
+  int edge_term;    /* backward: OR of ST_EDGE_TERM_PRIMARY and ST_EDGE_TERM_SECONDARY (0 = interior only) */
+  int edge_mode;    /* ST_EDGE_SILHOUETTE or ST_EDGE_ALL (silhouettes as seen from the camera, or from each
+                       path vertex for the secondary term) */
   int edge_spp;     /* edge samples per pixel; 0 = the view's spp */
   int mode;         /* ST_MODE_BATCHED or ST_MODE_PER_VIEW */
   int use_graph;    /* batched mode: capture and replay the call as a CUDA graph */
@@ -131,6 +134,7 @@ typedef struct {
   long long scratch_bytes;    /* device bytes held by the scene's wavefront buffers */
   int kernel_launches;        /* kernels the last call launched (graph kernel nodes included) */
   int bvh4_nodes;             /* nodes of the 4-wide BVH the traversal walks */
+  long long secondary_samples; /* accepted secondary edge samples of the last call (each traces two paths) */
 } st_stats;
 
 /* Create a scene: copies the mesh into scene-owned device memory, builds the
@@ -164,8 +168,11 @@ st_status st_render(st_scene* scene, const st_view* views, int n_views, int defa
  * ACCUMULATE (+=) dL/dvertices into d_vertices (device float [V][3]) and
  * dL/dtexel-parameters into d_face_params (device float [F*n][5]). The interior term
  * replays the forward paths of the same seed and sweeps each in reverse; the
- * edge term (opts->edge_term) samples visibility edges. Either gradient
- * pointer may be NULL to skip it (d_vertices may not be NULL with edge_term). */
+ * edge term (opts->edge_term) samples visibility edges: in screen space
+ * (primary) and, at every vertex of every camera path, on the vertex's sphere
+ * of directions (secondary: one uniformly picked mesh edge per vertex, two
+ * side paths continuing from the next vertex). Either gradient pointer may be
+ * NULL to skip it (d_vertices may not be NULL with edge_term). */
 st_status st_render_backward(st_scene* scene, const st_view* views, int n_views, int default_spp,
                              int max_bounces, unsigned long long seed, const st_render_opts* opts,
                              const float* dL_dimage, float* d_vertices, float* d_face_params,

@@ -608,7 +608,7 @@ void secondary_edge(const Scene& s, const Rng& rng, int B, int b, const V3<Dual>
   U4 u = rng.draw(c0, c1, (uint32_t)(b << 4) | 3u, stream);
   uint64_t nE = E.size();
   const Edge& e = E[(size_t)(((uint64_t)(u.w[0] >> 8) * nE) >> 24)];
-  if (e.f[0] == f0 || (e.nf >= 2 && e.f[1] == f0)) return;   // its arc lies on the vertex's horizon
+  if (e.f[0] == f0 || (e.nf == 2 && e.f[1] == f0)) return;   // its arc lies on the vertex's horizon
   V3d pv = val(p);
   V3d A = s.vert[e.a], Bv = s.vert[e.b];
   double bnd = SEC_BAND * (1.0 + std::max(std::fabs(pv.x), std::max(std::fabs(pv.y), std::fabs(pv.z))));

@@ -180,6 +180,7 @@ struct Plan {
   long long total = 0;
   long long pixels = 0;       // sum of W*H: the primary-visibility bin space
   bool interior = false, edges = false;
+  bool sec = false;           // secondary-visibility edge samples at every camera-path vertex
   bool bins = false;          // build primary-visibility bins (worth it only for many primary rays)
   st_render_opts o{};
 };
@@ -196,6 +197,7 @@ void free_engine(Engine& e) {
   dfree(e.o); dfree(e.d); dfree(e.thr); dfree(e.rad); dfree(e.ctr); dfree(e.hit); dfree(e.origin); dfree(e.brange);
   dfree(e.q0); dfree(e.q1); dfree(e.qs); dfree(e.sh_dir); dfree(e.sh_c);
   dfree(e.r0); dfree(e.r1); dfree(e.r2); dfree(e.r3); dfree(e.esc); dfree(e.nb); dfree(e.cnt); dfree(e.stat);
+  dfree(e.sj); dfree(e.sje); dfree(e.pinj);
   e = Engine();
 }
 
@@ -205,12 +207,15 @@ void drop_graphs(st_scene* s) {
   s->graphs.clear();
 }
 
-st_status ensure_engine(st_scene* s, int Q, int B, int NS, bool records) {
+st_status ensure_engine(st_scene* s, int Q, int B, int NS, bool records, bool sec) {
   Engine& e = s->eng;
-  if (e.Q >= Q && e.NS >= NS && (!records || (e.records && e.B >= B))) return ST_OK;
+  if (e.Q >= Q && e.NS >= NS && (!records || (e.records && e.B >= B)) &&
+      (!sec || e.sec_cap >= (long long)e.B * e.Q))
+    return ST_OK;
   // grow: keep the larger of old and new sizes so alternating calls do not thrash
   int nQ = std::max(Q, e.Q), nNS = std::max(NS, e.NS), nB = std::max(B, e.B);
   bool nrec = records || e.records;
+  bool nsec = sec || e.sec_cap > 0;
   cudaDeviceSynchronize();
   drop_graphs(s);
   free_engine(e);
@@ -227,6 +232,9 @@ st_status ensure_engine(st_scene* s, int Q, int B, int NS, bool records) {
     chk(dalloc(&e.r0, q * nB, &acc)); chk(dalloc(&e.r1, q * (nB + 1), &acc)); chk(dalloc(&e.r2, q * nB, &acc));
     chk(dalloc(&e.r3, q * nB, &acc)); chk(dalloc(&e.esc, q, &acc)); chk(dalloc(&e.nb, q, &acc));
   }
+  if (nsec) {
+    chk(dalloc(&e.sj, 4 * q * nB, &acc)); chk(dalloc(&e.sje, q * nB, &acc)); chk(dalloc(&e.pinj, q * nB, &acc));
+  }
   chk(dalloc(&e.cnt, CNT_SIZE, &acc));
   chk(dalloc(&e.stat, STAT_SIZE, &acc));
   if (r != cudaSuccess) {
@@ -235,6 +243,7 @@ st_status ensure_engine(st_scene* s, int Q, int B, int NS, bool records) {
     return fail(ST_ERR_OOM, std::string("wavefront buffers: ") + cudaGetErrorString(r));
   }
   e.Q = nQ; e.B = nB; e.NS = nNS; e.records = nrec; e.bytes = acc;
+  e.sec_cap = nsec ? (long long)nB * nQ : 0;
   return ST_OK;
 }
 
@@ -302,6 +311,7 @@ KCtx make_ctx(st_scene* s, const Plan& p) {
   c.acc = s->acc;
   c.views = s->d_views; c.segs = s->d_segs; c.n_segs = (int)p.segs.size();
   c.args = s->d_args; c.B = p.B; c.e = s->eng; c.e.records = p.kind == 1; c.err = s->d_err;
+  c.sec = p.sec ? 1 : 0;
   return c;
 }
 
@@ -339,42 +349,76 @@ st_status run_chunk(st_scene* s, const Plan& p, const KCtx& c, long long j0, int
   auto cap = [&](int g) { return p.o.persist_blocks > 0 ? std::min(g, p.o.persist_blocks * sm) : g; };
   int* cnt = s->eng.cnt;
   int hc[CNT_SIZE];
+  // extension / shading / shadow stages for `nb` bounces of the paths queued in q0
+  auto bounces = [&](const KCtx& k, int nb) -> st_status {
+    for (int b = 0; b < nb; ++b) {
+      int ge = cap(p.o.count_visits ? g_ext_s : g_ext), gs = cap(g_shade), gw = cap(g_shadow);
+      if (host_sized) {
+        ST_CUDA(cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, st));
+        ST_CUDA(cudaStreamSynchronize(st));
+        int q = hc[CNT_EXT + b];
+        if (q == 0) break;
+        ge = (q + EXT_BLOCK - 1) / EXT_BLOCK;
+        gs = (q + 255) / 256;
+      }
+      if (timing) ST_CUDA(cudaEventRecord(next_event(s, true), st));
+      if (p.o.count_visits) k_extend<true><<<ge, EXT_BLOCK, 0, st>>>(k, b);
+      else k_extend<false><<<ge, EXT_BLOCK, 0, st>>>(k, b);
+      if (timing) ST_CUDA(cudaEventRecord(next_event(s, false), st));
+      k_shade<<<gs, 256, 0, st>>>(k, b);
+      s->launches += 2;
+      if (host_sized) {
+        ST_CUDA(cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, st));
+        ST_CUDA(cudaStreamSynchronize(st));
+        int q = hc[CNT_SH + b];
+        gw = (q + EXT_BLOCK - 1) / EXT_BLOCK;
+        if (q > 0) { k_shadow<<<gw, EXT_BLOCK, 0, st>>>(k, b); s->launches++; }
+      } else if (k.NS > 0) {
+        k_shadow<<<gw, EXT_BLOCK, 0, st>>>(k, b);
+        s->launches++;
+      }
+    }
+    return ST_OK;
+  };
   k_reset<<<1, 128, 0, st>>>(cnt);
   k_raygen<<<(n + 255) / 256, 256, 0, st>>>(c, j0, n);
   s->launches += 2;
-  for (int b = 0; b < p.B; ++b) {
-    int ge = cap(p.o.count_visits ? g_ext_s : g_ext), gs = cap(g_shade), gw = cap(g_shadow);
-    if (host_sized) {
-      ST_CUDA(cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, st));
-      ST_CUDA(cudaStreamSynchronize(st));
-      int q = hc[CNT_EXT + b];
-      if (q == 0) break;
-      ge = (q + EXT_BLOCK - 1) / EXT_BLOCK;
-      gs = (q + 255) / 256;
-    }
-    if (timing) ST_CUDA(cudaEventRecord(next_event(s, true), st));
-    if (p.o.count_visits) k_extend<true><<<ge, EXT_BLOCK, 0, st>>>(c, b);
-    else k_extend<false><<<ge, EXT_BLOCK, 0, st>>>(c, b);
-    if (timing) ST_CUDA(cudaEventRecord(next_event(s, false), st));
-    k_shade<<<gs, 256, 0, st>>>(c, b);
-    s->launches += 2;
-    if (host_sized) {
-      ST_CUDA(cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, st));
-      ST_CUDA(cudaStreamSynchronize(st));
-      int q = hc[CNT_SH + b];
-      gw = (q + EXT_BLOCK - 1) / EXT_BLOCK;
-      if (q > 0) { k_shadow<<<gw, EXT_BLOCK, 0, st>>>(c, b); s->launches++; }
-    } else if (c.NS > 0) {
-      k_shadow<<<gw, EXT_BLOCK, 0, st>>>(c, b);
-      s->launches++;
-    }
-  }
+  st_status r = bounces(c, p.B);
+  if (r != ST_OK) return r;
   if (p.kind == 0) {
     k_resolve<<<(n + 255) / 256, 256, 0, st>>>(c, j0, n);
     s->launches++;
   } else {
-    if (has_cam && p.interior) { k_adjoint<<<(n + ADJ_BLOCK - 1) / ADJ_BLOCK, ADJ_BLOCK, 0, st>>>(c, j0, n); s->launches++; }
-    if (has_edge) { k_edge_resolve<<<(n + ADJ_BLOCK - 1) / ADJ_BLOCK, ADJ_BLOCK, 0, st>>>(c, j0, n); s->launches++; }
+    int ga = (n + ADJ_BLOCK - 1) / ADJ_BLOCK;
+    if (has_edge) { k_edge_resolve<<<ga, ADJ_BLOCK, 0, st>>>(c, j0, n); s->launches++; }
+    if (has_cam && p.sec) {
+      // secondary edge samples: jobs from the recorded vertices, then their side
+      // paths in passes of Q slots (records off: they stay the camera paths'),
+      // each pass resolved before the next reuses the slots
+      k_sec_gen<<<ga, ADJ_BLOCK, 0, st>>>(c, j0, n);
+      s->launches++;
+      long long jobs = (long long)p.B * n;
+      if (host_sized) {
+        ST_CUDA(cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, st));
+        ST_CUDA(cudaStreamSynchronize(st));
+        jobs = hc[CNT_SEC];
+      }
+      int Q = s->eng.Q;
+      long long sides = (jobs + 31) / 32 * 64;
+      int passes = (int)((sides + Q - 1) / Q);
+      KCtx cs = c;
+      cs.e.records = false;
+      for (int ps = 0; ps < passes; ++ps) {
+        k_reset_pass<<<1, 128, 0, st>>>(cnt);
+        k_sec_raygen<<<(Q + 255) / 256, 256, 0, st>>>(cs, ps);
+        s->launches += 2;
+        r = bounces(cs, std::max(1, p.B - 1));
+        if (r != ST_OK) return r;
+        k_sec_resolve<<<(Q + ADJ_BLOCK - 1) / ADJ_BLOCK, ADJ_BLOCK, 0, st>>>(cs, ps);
+        s->launches++;
+      }
+    }
+    if (has_cam && p.interior) { k_adjoint<<<ga, ADJ_BLOCK, 0, st>>>(c, j0, n); s->launches++; }
   }
   ST_CUDA(cudaGetLastError());
   return ST_OK;
@@ -462,8 +506,11 @@ st_status plan_call(st_scene* s, const st_view* views, int n_views, int default_
   if (p.o.edge_mode != ST_EDGE_SILHOUETTE && p.o.edge_mode != ST_EDGE_ALL) return fail(ST_ERR_INVALID_ARG, "bad edge_mode");
   if (p.o.edge_spp < 0 || p.o.chunk_paths < 0 || p.o.persist_blocks < 0)
     return fail(ST_ERR_INVALID_ARG, "negative option");
+  if (p.o.edge_term < 0 || p.o.edge_term > (ST_EDGE_TERM_PRIMARY | ST_EDGE_TERM_SECONDARY))
+    return fail(ST_ERR_INVALID_ARG, "bad edge_term");
   p.interior = kind == 1 && want_interior;
-  p.edges = kind == 1 && p.o.edge_term != 0;
+  p.edges = kind == 1 && (p.o.edge_term & ST_EDGE_TERM_PRIMARY);
+  p.sec = p.interior && (p.o.edge_term & ST_EDGE_TERM_SECONDARY) && s->n_edges > 0;
   long long base = 0;
   for (int i = 0; i < n_views; ++i) {
     const st_view& v = views[i];
@@ -536,7 +583,7 @@ st_status run_call(st_scene* s, Plan& p, const CallArgs& args, cudaStream_t st) 
     Q = (int)std::min<long long>(Q, (mx + SEG_ALIGN - 1) / SEG_ALIGN * SEG_ALIGN);
   }
   int NS = s->nl + (s->env.w > 0 ? 1 : 0);
-  r = ensure_engine(s, Q, p.B, NS, p.kind == 1);
+  r = ensure_engine(s, Q, p.B, NS, p.kind == 1, p.sec);
   if (r != ST_OK) return r;
   ST_CUDA(cudaMemcpyAsync(s->d_views, p.views.data(), sizeof(DevView) * p.views.size(), cudaMemcpyHostToDevice, st));
   ST_CUDA(cudaMemcpyAsync(s->d_segs, p.segs.data(), sizeof(Seg) * p.segs.size(), cudaMemcpyHostToDevice, st));
@@ -803,6 +850,7 @@ st_status st_get_stats(st_scene* s, st_stats* out) {
   r.shadow_rays = (long long)h[STAT_SHADOW];
   r.node_visits = (long long)h[STAT_VISITS];
   r.tri_tests = (long long)h[STAT_TESTS];
+  r.secondary_samples = (long long)h[STAT_SEC];
   r.edge_samples = s->last_edge_samples;
   double ms = 0;
   for (int i = 0; i < s->ev_used; ++i) {

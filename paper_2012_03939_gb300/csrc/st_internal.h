@@ -35,7 +35,7 @@ struct Engine {
   int Q = 0, B = 0, NS = 0;   // capacity, bounces the records were sized for, shadow rays per path
   bool records = false;
   float4 *o = nullptr, *d = nullptr, *thr = nullptr, *rad = nullptr;
-  int4* ctr = nullptr;        // (c0, c1, stream, job kind)
+  int4* ctr = nullptr;        // Philox counter words (c0, c1, stream) and the vertex index of the first ray
   int2* hit = nullptr;        // (face, t bits)
   int2* brange = nullptr;     // primary rays: range of the pixel's bin list, (-1, -1) = use the BVH
   int* origin = nullptr;
@@ -44,15 +44,20 @@ struct Engine {
   float4 *r0 = nullptr, *r1 = nullptr, *r2 = nullptr, *r3 = nullptr;  // [B+1][Q] records
   float4* esc = nullptr;      // escape radiance (rgb, flag)
   int* nb = nullptr;          // hits per path
+  // secondary-visibility edge samples (backward calls that ask for them)
+  long long sec_cap = 0;      // job capacity = B * Q (one sample per path vertex)
+  float4* sj = nullptr;       // [4][sec_cap]: (p, face), (w, weight), (m, tau), (dL/dI * T, edge)
+  int4* sje = nullptr;        // [sec_cap]: (camera counter c0, sample, camera slot, vertex)
+  float4* pinj = nullptr;     // [B][Q]: adjoint of each vertex position from its edge sample
   int* cnt = nullptr;         // counters, see CNT_*
   unsigned long long* stat = nullptr;  // per-call 64-bit statistics, see STAT_*
   long long bytes = 0;
 };
 
 enum { CNT_EXT = 0, CNT_EXT_FETCH = 16, CNT_SHADE_FETCH = 32, CNT_SH = 48, CNT_SH_FETCH = 64, CNT_MISC = 80,
-       CNT_SIZE = 96 };
+       CNT_SEC = CNT_MISC, CNT_SIZE = 96 };
 enum { STAT_PATHS = 0, STAT_EXT = 1, STAT_SHADOW = 2, STAT_EDGE = 3, STAT_VISITS = 4, STAT_TESTS = 5,
-       STAT_SIZE = 8 };
+       STAT_SEC = 6, STAT_SIZE = 8 };
 
 struct GraphEntry {
   std::vector<long long> key;

@@ -51,6 +51,7 @@ struct KCtx {
   int n_segs;
   const CallArgs* args;
   int B;
+  int sec;                // backward: secondary-visibility edge samples on
   Engine e;
   int* err;
 };
@@ -447,7 +448,7 @@ __global__ void k_raygen(KCtx c, long long j0, int n) {
             d = cam_dir(v, sx, sy);
             o = v.eye;
             br = bin_range(c, sg.view, v, (int)floorf(sx), (int)floorf(sy));
-            ct = make_int4((int)(uint32_t)k, (int)v.off, 2, 1);
+            ct = make_int4((int)(uint32_t)k, (int)v.off, 2, 0);
             ok = true;
           }
         }
@@ -542,6 +543,8 @@ __global__ void k_shade(KCtx c, int b) {
   int slot = live_ ? qin[qi_] : 0;
   if (live_) {
     int2 h = E.hit[slot];
+    int4 ct = E.ctr[slot];
+    const int vb = b + ct.w;      // path vertex this ray finds (side paths of edge samples start past 0)
     float4 o4 = E.o[slot], d4 = E.d[slot];
     float3 dir = xyz(d4);
     float3 T = xyz(E.thr[slot]);
@@ -561,7 +564,7 @@ __global__ void k_shade(KCtx c, int b) {
         E.rad[slot] = make_float4(r.x + T.x * Lw.x, r.y + T.y * Lw.y, r.z + T.z * Lw.z, 0.0f);
         if (E.records && b > 0) E.esc[slot] = make_float4(Lw.x, Lw.y, Lw.z, 1.0f);
       }
-    } else {
+    } else if (vb < c.B) {        // a ray past the last vertex adds nothing where it hits
       float4 ta = __ldg(&c.tri[3 * h.x]), tb = __ldg(&c.tri[3 * h.x + 1]), tc = __ldg(&c.tri[3 * h.x + 2]);
       int f = __float_as_int(ta.w);
       float t = __int_as_float(h.y);
@@ -592,8 +595,7 @@ __global__ void k_shade(KCtx c, int b) {
       int flags = 0;
       float3 ewi = mk3(0, 0, 0), escale = mk3(0, 0, 0);
       if (c.env.w > 0) {
-        U4 u = philox((uint32_t)E.ctr[slot].x, (uint32_t)E.ctr[slot].y, (uint32_t)(b << 4) | 1u,
-                      (uint32_t)E.ctr[slot].z, key.k0, key.k1);
+        U4 u = philox((uint32_t)ct.x, (uint32_t)ct.y, (uint32_t)(vb << 4) | 1u, (uint32_t)ct.z, key.k0, key.k1);
         int tx = env_pick(c.env, u.x, u.y);
         int row = tx / c.env.w, col = tx - row * c.env.w;
         float uu = ((float)col + unif(u.z)) / (float)c.env.w, vq = ((float)row + unif(u.w)) / (float)c.env.h;
@@ -607,7 +609,7 @@ __global__ void k_shade(KCtx c, int b) {
           float4 te = __ldg(&c.env.tex[tx]);
           float pe = env_pdf(c.env, te.w, sth);
           float w = 1.0f;
-          if (b < c.B - 1) {
+          if (vb < c.B - 1) {
             float pb = brdf_pdf(c.brdf, m, n, ewi, wo);
             w = pe * pe / (pe * pe + pb * pb);
           }
@@ -625,9 +627,8 @@ __global__ void k_shade(KCtx c, int b) {
       }
       E.o[slot] = make_float4(p.x, p.y, p.z, 0.0f);
       E.origin[slot] = f;          // excluded by this vertex's shadow rays and by its continuation
-      if (b < c.B - 1) {
-        U4 u = philox((uint32_t)E.ctr[slot].x, (uint32_t)E.ctr[slot].y, (uint32_t)(b << 4) | 2u,
-                      (uint32_t)E.ctr[slot].z, key.k0, key.k1);
+      if (vb < c.B - 1) {
+        U4 u = philox((uint32_t)ct.x, (uint32_t)ct.y, (uint32_t)(vb << 4) | 2u, (uint32_t)ct.z, key.k0, key.k1);
         float3 wi;
         float pdf = brdf_sample(c.brdf, m, n, wo, unif(u.x), unif(u.y), unif(u.z), wi);
         if (pdf > 0.0f) {
@@ -800,6 +801,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_adjoint(KCtx c, long long j0, int
       float3 nn = mh * sgn;
       Mat m = fetch_mat(c.P, key);
       float3 Nb = mk3(0, 0, 0), Pb = Pnext;
+      if (c.sec) Pb += xyz(E.pinj[b * Q + i]);   // the vertex's secondary edge sample moves with p
       float dm[5] = {0, 0, 0, 0, 0};
       float3 gC = mul(g, T[b]);
       float3 C = mk3(0, 0, 0);
@@ -914,6 +916,234 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_edge_resolve(KCtx c, long long j0
     atomicAdd(&dV[3 * va], vals[0]); atomicAdd(&dV[3 * va + 1], vals[1]); atomicAdd(&dV[3 * va + 2], vals[2]);
     atomicAdd(&dV[3 * vb], vals[3]); atomicAdd(&dV[3 * vb + 1], vals[4]); atomicAdd(&dV[3 * vb + 2], vals[5]);
   }
+}
+
+// ------------------------------------------------------------------ secondary-visibility edges
+// At a path vertex p the estimator integrates g(w) = f cos L_in(w) over
+// incoming directions; g jumps where w crosses the image of a mesh edge on p's
+// sphere of directions, and moving the edge's endpoints (x) or p moves that arc
+// by m.(dx - dp)/r along its unit normal m (the boundary term of Li et al.'s
+// edge sampling, which the paper's gradient relies on, Sec. 3.2). One sample
+// per vertex: an edge picked uniformly from all E edges by an integer map, a
+// point x uniform on the part of it above the tangent plane, two side paths at
+// w -+ SEC_EPS m that continue the path from the next vertex. Arc length per
+// unit edge length is |w x t|/r (t the unit edge direction), so the sample's
+// weight is |w x t| E len (tau1 - tau0) / r^2 and its derivative
+// <dL/dI, T (g- - g+)> weight m.(dx - dp), dx = (1 - tau) dA + tau dB.
+constexpr float SEC_EPS = 1e-4f;    // side rays' angular offset (radians)
+constexpr float SEC_BAND = 1e-5f;   // plane-distance band, times (1 + |p|_inf): coplanar faces and edges
+constexpr float SEC_RMIN = 1e-6f;   // nearest edge point accepted
+constexpr float SEC_SMIN = 1e-6f;   // sine of the edge/view angle accepted
+
+__device__ __forceinline__ float face_side(const KCtx& c, int f, float3 p) {
+  float3 a = fetch_vertex(c.V, c.F[3 * f]);
+  float3 m = norm3(cross3(fetch_vertex(c.V, c.F[3 * f + 1]) - a, fetch_vertex(c.V, c.F[3 * f + 2]) - a));
+  return dot3(m, p - a);
+}
+
+struct SecSample {
+  int e;
+  float tau, weight;
+  float3 w, mh;
+};
+
+// Edge sample at vertex p (shading normal n, face f0): false if the picked edge
+// is not a candidate (an edge of f0, not a silhouette seen from p in
+// silhouette mode, or wholly at or below the tangent plane).
+__device__ __forceinline__ bool sec_sample(const KCtx& c, float3 p, float3 n, int f0, uint32_t u0, uint32_t u1,
+                                           SecSample& s) {
+  int nE = c.n_edges;
+  if (nE <= 0) return false;
+  s.e = (int)(((unsigned long long)(u0 >> 8) * (unsigned long long)nE) >> 24);
+  int2 ef = c.edge_f[s.e];
+  if (ef.x == f0 || ef.y == f0) return false;
+  float bnd = SEC_BAND * (1.0f + fmaxf(fabsf(p.x), fmaxf(fabsf(p.y), fabsf(p.z))));
+  if (c.edge_mode == 0) {
+    float s1 = face_side(c, ef.x, p);
+    bool sil;
+    if (ef.y >= 0) {
+      float s2 = face_side(c, ef.y, p);
+      sil = (s1 > bnd && s2 < -bnd) || (s1 < -bnd && s2 > bnd);
+    } else {
+      sil = fabsf(s1) > bnd;
+    }
+    if (!sil) return false;
+  }
+  int2 ev = c.edge_v[s.e];
+  float3 A = fetch_vertex(c.V, ev.x), Bv = fetch_vertex(c.V, ev.y);
+  float hA = dot3(n, A - p), hB = dot3(n, Bv - p);
+  if (!(hA > bnd) && !(hB > bnd)) return false;
+  float t0 = 0.0f, t1 = 1.0f;
+  if (!(hA > bnd)) t0 = (bnd - hA) / (hB - hA);
+  if (!(hB > bnd)) t1 = (hA - bnd) / (hA - hB);
+  if (!(t1 > t0)) return false;
+  s.tau = t0 + unif(u1) * (t1 - t0);
+  float3 tv = Bv - A;
+  float3 dv = A + tv * s.tau - p;
+  float r = len3(dv);
+  if (!(r > SEC_RMIN)) return false;
+  s.w = dv * (1.0f / r);
+  float l = len3(tv);
+  float3 cr = cross3(s.w, tv * (1.0f / l));
+  float sn = len3(cr);
+  if (!(sn > SEC_SMIN)) return false;
+  s.mh = cr * (1.0f / sn);
+  s.weight = sn * (float)nE * l * (t1 - t0) / (r * r);
+  return true;
+}
+
+// shading normal of a recorded vertex (face normal turned toward wo)
+__device__ __forceinline__ float3 vertex_normal(const KCtx& c, int f, float3 wo) {
+  float3 v0 = fetch_vertex(c.V, c.F[3 * f]), v1 = fetch_vertex(c.V, c.F[3 * f + 1]),
+         v2 = fetch_vertex(c.V, c.F[3 * f + 2]);
+  float3 ng = norm3(cross3(v1 - v0, v2 - v0));
+  return dot3(ng, wo) < 0.0f ? -ng : ng;
+}
+
+// One edge sample per recorded vertex of every camera path of the chunk whose
+// pixel has a nonzero dL/dI; accepted samples become jobs.
+__global__ void __launch_bounds__(ADJ_BLOCK) k_sec_gen(KCtx c, long long j0, int n) {
+  const Engine& E = c.e;
+  const size_t Q = (size_t)E.Q;
+  const long long cap = E.sec_cap;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int nbv = 0;
+  float3 g = mk3(0, 0, 0);
+  if (i < n) {
+    long long job = j0 + i;
+    int si = find_seg(c.segs, c.n_segs, job);
+    if (si >= 0) {
+      Seg sg = c.segs[si];
+      long long local = job - sg.base;
+      if (sg.kind == 0 && local < sg.count) {
+        DevView v = c.views[sg.view];
+        long long pixel = local / v.spp;
+        const float* gp = c.args->dLdI + 3 * (v.pix_off + pixel);
+        float inv = 1.0f / (float)v.spp;
+        g = mk3(gp[0] * inv, gp[1] * inv, gp[2] * inv);
+        if (g.x != 0.0f || g.y != 0.0f || g.z != 0.0f) nbv = E.nb[i];
+      }
+    }
+  }
+  Key key{c.args->k0, c.args->k1};
+  int4 ct = nbv > 0 ? E.ctr[i] : make_int4(0, 0, 0, 0);
+  float3 T = mk3(1, 1, 1);
+  int made = 0;
+  for (int b = 0; b < c.B; ++b) {
+    bool ok = false;
+    SecSample ss;
+    float4 r0 = make_float4(0, 0, 0, 0);
+    float3 Tn = T;
+    if (b < nbv) {
+      r0 = E.r0[b * Q + i];
+      float4 r1 = E.r1[b * Q + i];
+      int f = __float_as_int(r0.w);
+      float3 wo = -xyz(r1);
+      float3 nn = vertex_normal(c, f, wo);
+      E.pinj[b * Q + i] = make_float4(0, 0, 0, 0);
+      U4 u = philox((uint32_t)ct.x, (uint32_t)ct.y, (uint32_t)(b << 4) | 3u, (uint32_t)ct.z, key.k0, key.k1);
+      ok = sec_sample(c, xyz(r0), nn, f, u.x, u.y, ss);
+      if (b + 1 < nbv) {
+        float4 r1n = E.r1[(b + 1) * Q + i];
+        int tex = __float_as_int(E.r3[b * Q + i].w);
+        Tn = mul(T, brdf_cos(c.brdf, fetch_mat(c.P, tex), nn, xyz(r1n), wo)) * (1.0f / r1n.w);
+      }
+    }
+    int q = warp_append(&E.cnt[CNT_SEC], ok);
+    if (ok && q < cap) {
+      float3 gC = mul(g, T);
+      E.sj[q] = r0;
+      E.sj[cap + q] = make_float4(ss.w.x, ss.w.y, ss.w.z, ss.weight);
+      E.sj[2 * cap + q] = make_float4(ss.mh.x, ss.mh.y, ss.mh.z, ss.tau);
+      E.sj[3 * cap + q] = make_float4(gC.x, gC.y, gC.z, __int_as_float(ss.e));
+      E.sje[q] = make_int4(ct.x, ct.y, i, b);
+      ++made;
+    }
+    T = Tn;
+  }
+  for (int off = 16; off > 0; off >>= 1) made += __shfl_xor_sync(FULL, made, off);
+  if ((threadIdx.x & 31) == 0 && made) atomicAdd(&E.stat[STAT_SEC], (unsigned long long)made);
+}
+
+// Side paths of pass `pass`: side index s = pass * Q + slot; blocks of 64 side
+// indices hold the minus sides of 32 consecutive jobs, then their plus sides.
+__global__ void k_sec_raygen(KCtx c, int pass) {
+  const Engine& E = c.e;
+  const size_t Q = (size_t)E.Q;
+  const long long cap = E.sec_cap;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  long long J = min((long long)E.cnt[CNT_SEC], cap);
+  long long sidx = (long long)pass * E.Q + i;
+  long long job = (sidx >> 6) * 32 + (sidx & 31);
+  bool ok = false;
+  if (i < E.Q && job < J) {
+    float4 a = E.sj[job], w = E.sj[cap + job], m = E.sj[2 * cap + job];
+    int4 je = E.sje[job];
+    int slot = je.z, b = je.w, f = __float_as_int(a.w);
+    float3 wo = -xyz(E.r1[b * Q + slot]);
+    float3 nn = vertex_normal(c, f, wo);
+    float3 ws = norm3(xyz(w) + xyz(m) * ((sidx & 32) ? SEC_EPS : -SEC_EPS));
+    float3 thr = brdf_cos(c.brdf, fetch_mat(c.P, __float_as_int(E.r3[b * Q + slot].w)), nn, ws, wo);
+    E.rad[i] = make_float4(0, 0, 0, 0);
+    if (thr.x > 0.0f || thr.y > 0.0f || thr.z > 0.0f) {
+      E.o[i] = make_float4(a.x, a.y, a.z, 0.0f);
+      E.d[i] = make_float4(ws.x, ws.y, ws.z, 0.0f);
+      E.thr[i] = make_float4(thr.x, thr.y, thr.z, 0.0f);
+      E.origin[i] = f;
+      E.ctr[i] = make_int4(je.x, je.y, 16 + b, b + 1);
+      E.brange[i] = make_int2(-1, -1);
+      ok = true;
+    }
+  }
+  int q = warp_append(&E.cnt[CNT_EXT + 0], ok);
+  if (ok) E.q0[q] = i;
+  unsigned mk = __ballot_sync(FULL, ok);
+  if ((threadIdx.x & 31) == 0 && mk) atomicAdd(&E.stat[STAT_PATHS], (unsigned long long)__popc(mk));
+}
+
+// (g- - g+) of each job of the pass: edge endpoints get weight (1 - tau, tau)
+// times m, the vertex position's adjoint gets -m (read by k_adjoint).
+__global__ void __launch_bounds__(ADJ_BLOCK) k_sec_resolve(KCtx c, int pass) {
+  __shared__ float scratch[ADJ_BLOCK / 32][32 * 7];
+  float* scr = scratch[threadIdx.x >> 5];
+  const Engine& E = c.e;
+  const size_t Q = (size_t)E.Q;
+  const long long cap = E.sec_cap;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  long long J = min((long long)E.cnt[CNT_SEC], cap);
+  long long sidx = (long long)pass * E.Q + i;
+  long long job = (sidx >> 6) * 32 + (sidx & 31);
+  float vals[6] = {0, 0, 0, 0, 0, 0};
+  int key = -1, va = 0, vb = 0;
+  if (i < E.Q && (sidx & 32) == 0 && job < J) {
+    float3 Lm = xyz(E.rad[i]), Lp = xyz(E.rad[i + 32]);
+    float4 w = E.sj[cap + job], m = E.sj[2 * cap + job], gq = E.sj[3 * cap + job];
+    float cv = (gq.x * (Lm.x - Lp.x) + gq.y * (Lm.y - Lp.y) + gq.z * (Lm.z - Lp.z)) * w.w;
+    if (cv != 0.0f) {
+      int4 je = E.sje[job];
+      float3 mh = xyz(m);
+      int e = __float_as_int(gq.w);
+      int2 ev = c.edge_v[e];
+      float3 da = mh * (cv * (1.0f - m.w)), db = mh * (cv * m.w);
+      vals[0] = da.x; vals[1] = da.y; vals[2] = da.z;
+      vals[3] = db.x; vals[4] = db.y; vals[5] = db.z;
+      key = e;
+      va = ev.x;
+      vb = ev.y;
+      E.pinj[je.w * Q + je.z] = make_float4(-cv * mh.x, -cv * mh.y, -cv * mh.z, 0.0f);
+    }
+  }
+  bool leader;
+  warp_reduce_peers<6>(key, vals, scr, leader);
+  if (leader) {
+    float* dV = c.args->dV;
+    atomicAdd(&dV[3 * va], vals[0]); atomicAdd(&dV[3 * va + 1], vals[1]); atomicAdd(&dV[3 * va + 2], vals[2]);
+    atomicAdd(&dV[3 * vb], vals[3]); atomicAdd(&dV[3 * vb + 1], vals[4]); atomicAdd(&dV[3 * vb + 2], vals[5]);
+  }
+}
+
+__global__ void k_reset_pass(int* cnt) {
+  for (int i = threadIdx.x; i < CNT_MISC; i += blockDim.x) cnt[i] = 0;
 }
 
 // closest-hit queries for st_trace_closest

@@ -23,6 +23,7 @@ STATUS = {0: "ST_OK", 1: "ST_ERR_INVALID_ARG", 2: "ST_ERR_OOM", 3: "ST_ERR_CUDA"
           5: "ST_ERR_STATE", 6: "ST_ERR_UNSUPPORTED", 7: "ST_ERR_DEVICE"}
 MODE_BATCHED, MODE_PER_VIEW = 0, 1
 EDGE_SILHOUETTE, EDGE_ALL = 0, 1
+EDGE_TERM_PRIMARY, EDGE_TERM_SECONDARY = 1, 2
 
 EXPORTED = ["st_scene_create", "st_scene_destroy", "st_refit", "st_rebuild", "st_set_face_params", "st_render",
             "st_render_backward", "st_trace_closest", "st_get_stats", "st_debug_bvh", "st_build_bvh_noalloc",
@@ -65,7 +66,7 @@ class Stats(C.Structure):
                 ("edge_samples", C.c_longlong), ("node_visits", C.c_longlong), ("tri_tests", C.c_longlong),
                 ("extend_launches", C.c_int), ("extend_ms", C.c_double), ("device_error", C.c_int),
                 ("bvh_nodes", C.c_int), ("scratch_bytes", C.c_longlong), ("kernel_launches", C.c_int),
-                ("bvh4_nodes", C.c_int)]
+                ("bvh4_nodes", C.c_int), ("secondary_samples", C.c_longlong)]
 
 
 _lib = None
