@@ -346,6 +346,18 @@ def run_ours(args):
     ms_fwd = timed(lambda: scene.render(step_views, B, seed, fb, out=img), args.steps, 2)
     value_fwd = seg_fwd * args.steps * world / (ms_fwd / 1000.0) / 1e6
 
+    # the same step with the secondary-visibility edge term added (one edge
+    # sample per camera-path vertex, two side paths per accepted sample)
+    bs = st.make_opts(mode="batched", use_graph=1, edge_term=edge_on | st.EDGE_TERM_SECONDARY, edge_mode=0,
+                      chunk_paths=chunk, persist_blocks=persist)
+    _, ss = counts(fb, bs)
+    seg_sec = seg_fwd + ss["extension_rays"] + ss["shadow_rays"]
+    sec_steps = max(2, args.steps // 2)
+    ms_sec = timed(lambda: step(fb, bs), sec_steps, 1)
+    with_sec = {"value": round(seg_sec * sec_steps * world / (ms_sec / 1000.0) / 1e6, 3),
+                "ms_per_step": round(ms_sec / sec_steps, 3), "segments_per_step": seg_sec,
+                "secondary_samples_per_step": ss["secondary_samples"]}
+
     # roofline of the dominant kernel (closest-hit traversal): algorithmic bytes
     # from the instrumented traversal, time from CUDA events around each launch
     ci = st.make_opts(mode="batched", use_graph=0, count_visits=1, chunk_paths=chunk)
@@ -443,6 +455,7 @@ def run_ours(args):
                "per_view": {"value": round(value_pv, 3), "ms_per_step": round(ms_pv / pv_steps, 3),
                             "launch": "per-view, host-read queue counts, no graph"},
                "forward_only": {"value": round(value_fwd, 3), "ms_per_step": round(ms_fwd / args.steps, 3)},
+               "with_secondary_edges": with_sec,
                "roofline": roofline, "cpu_baseline": cpu,
                "e2e": {"value": round(value_e2e, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": d2h, "ms_per_step": round(ms_e2e / args.steps, 3)},

@@ -410,11 +410,11 @@ st_status run_chunk(st_scene* s, const Plan& p, const KCtx& c, long long j0, int
       cs.e.records = false;
       for (int ps = 0; ps < passes; ++ps) {
         k_reset_pass<<<1, 128, 0, st>>>(cnt);
-        k_sec_raygen<<<(Q + 255) / 256, 256, 0, st>>>(cs, ps);
+        k_sec_raygen<<<std::min((Q + 255) / 256, 4 * sm), 256, 0, st>>>(cs, ps);
         s->launches += 2;
         r = bounces(cs, std::max(1, p.B - 1));
         if (r != ST_OK) return r;
-        k_sec_resolve<<<(Q + ADJ_BLOCK - 1) / ADJ_BLOCK, ADJ_BLOCK, 0, st>>>(cs, ps);
+        k_sec_resolve<<<std::min((Q + ADJ_BLOCK - 1) / ADJ_BLOCK, 8 * sm), ADJ_BLOCK, 0, st>>>(cs, ps);
         s->launches++;
       }
     }

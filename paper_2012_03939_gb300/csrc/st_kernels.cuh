@@ -481,7 +481,7 @@ __global__ void k_raygen(KCtx c, long long j0, int n) {
   const int total_ = (total_expr);                                             \
   for (;;) {                                                                   \
     int base_ = 0;                                                             \
-    if (lane_ == 0) base_ = atomicAdd((fetch_ptr), 32);                        \
+    if (lane_ == 0) base_ = total_ > 0 ? atomicAdd((fetch_ptr), 32) : 0;       \
     base_ = __shfl_sync(FULL, base_, 0);                                       \
     if (base_ >= total_) break;                                                \
     const int qi_ = base_ + lane_;                                             \
@@ -1065,40 +1065,52 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_sec_gen(KCtx c, long long j0, int
   if ((threadIdx.x & 31) == 0 && made) atomicAdd(&E.stat[STAT_SEC], (unsigned long long)made);
 }
 
-// Side paths of pass `pass`: side index s = pass * Q + slot; blocks of 64 side
-// indices hold the minus sides of 32 consecutive jobs, then their plus sides.
+// Side-index space of J jobs (blocks of 64: 32 minus sides, then their plus
+// sides) that falls into pass `pass` (slots [0, n) of the engine); 0 when the
+// pass has no work, so empty passes of a captured graph cost one launch each.
+__device__ __forceinline__ int sec_pass_slots(const Engine& E, int pass, long long& J) {
+  J = min((long long)E.cnt[CNT_SEC], E.sec_cap);
+  long long rest = (J + 31) / 32 * 64 - (long long)pass * E.Q;
+  return (int)max(0LL, min(rest, (long long)E.Q));
+}
+
+// Side paths of pass `pass`: side index s = pass * Q + slot. Grid-stride over
+// the pass's slots.
 __global__ void k_sec_raygen(KCtx c, int pass) {
   const Engine& E = c.e;
   const size_t Q = (size_t)E.Q;
   const long long cap = E.sec_cap;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  long long J = min((long long)E.cnt[CNT_SEC], cap);
-  long long sidx = (long long)pass * E.Q + i;
-  long long job = (sidx >> 6) * 32 + (sidx & 31);
-  bool ok = false;
-  if (i < E.Q && job < J) {
-    float4 a = E.sj[job], w = E.sj[cap + job], m = E.sj[2 * cap + job];
-    int4 je = E.sje[job];
-    int slot = je.z, b = je.w, f = __float_as_int(a.w);
-    float3 wo = -xyz(E.r1[b * Q + slot]);
-    float3 nn = vertex_normal(c, f, wo);
-    float3 ws = norm3(xyz(w) + xyz(m) * ((sidx & 32) ? SEC_EPS : -SEC_EPS));
-    float3 thr = brdf_cos(c.brdf, fetch_mat(c.P, __float_as_int(E.r3[b * Q + slot].w)), nn, ws, wo);
-    E.rad[i] = make_float4(0, 0, 0, 0);
-    if (thr.x > 0.0f || thr.y > 0.0f || thr.z > 0.0f) {
-      E.o[i] = make_float4(a.x, a.y, a.z, 0.0f);
-      E.d[i] = make_float4(ws.x, ws.y, ws.z, 0.0f);
-      E.thr[i] = make_float4(thr.x, thr.y, thr.z, 0.0f);
-      E.origin[i] = f;
-      E.ctr[i] = make_int4(je.x, je.y, 16 + b, b + 1);
-      E.brange[i] = make_int2(-1, -1);
-      ok = true;
+  long long J;
+  const int total = sec_pass_slots(E, pass, J);
+  for (int base = blockIdx.x * blockDim.x; base < total; base += gridDim.x * blockDim.x) {
+    int i = base + threadIdx.x;
+    long long sidx = (long long)pass * E.Q + i;
+    long long job = (sidx >> 6) * 32 + (sidx & 31);
+    bool ok = false;
+    if (i < total && job < J) {
+      float4 a = E.sj[job], w = E.sj[cap + job], m = E.sj[2 * cap + job];
+      int4 je = E.sje[job];
+      int slot = je.z, b = je.w, f = __float_as_int(a.w);
+      float3 wo = -xyz(E.r1[b * Q + slot]);
+      float3 nn = vertex_normal(c, f, wo);
+      float3 ws = norm3(xyz(w) + xyz(m) * ((sidx & 32) ? SEC_EPS : -SEC_EPS));
+      float3 thr = brdf_cos(c.brdf, fetch_mat(c.P, __float_as_int(E.r3[b * Q + slot].w)), nn, ws, wo);
+      E.rad[i] = make_float4(0, 0, 0, 0);
+      if (thr.x > 0.0f || thr.y > 0.0f || thr.z > 0.0f) {
+        E.o[i] = make_float4(a.x, a.y, a.z, 0.0f);
+        E.d[i] = make_float4(ws.x, ws.y, ws.z, 0.0f);
+        E.thr[i] = make_float4(thr.x, thr.y, thr.z, 0.0f);
+        E.origin[i] = f;
+        E.ctr[i] = make_int4(je.x, je.y, 16 + b, b + 1);
+        E.brange[i] = make_int2(-1, -1);
+        ok = true;
+      }
     }
+    int q = warp_append(&E.cnt[CNT_EXT + 0], ok);
+    if (ok) E.q0[q] = i;
+    unsigned mk = __ballot_sync(FULL, ok);
+    if ((threadIdx.x & 31) == 0 && mk) atomicAdd(&E.stat[STAT_PATHS], (unsigned long long)__popc(mk));
   }
-  int q = warp_append(&E.cnt[CNT_EXT + 0], ok);
-  if (ok) E.q0[q] = i;
-  unsigned mk = __ballot_sync(FULL, ok);
-  if ((threadIdx.x & 31) == 0 && mk) atomicAdd(&E.stat[STAT_PATHS], (unsigned long long)__popc(mk));
 }
 
 // (g- - g+) of each job of the pass: edge endpoints get weight (1 - tau, tau)
@@ -1109,36 +1121,39 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_sec_resolve(KCtx c, int pass) {
   const Engine& E = c.e;
   const size_t Q = (size_t)E.Q;
   const long long cap = E.sec_cap;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  long long J = min((long long)E.cnt[CNT_SEC], cap);
-  long long sidx = (long long)pass * E.Q + i;
-  long long job = (sidx >> 6) * 32 + (sidx & 31);
-  float vals[6] = {0, 0, 0, 0, 0, 0};
-  int key = -1, va = 0, vb = 0;
-  if (i < E.Q && (sidx & 32) == 0 && job < J) {
-    float3 Lm = xyz(E.rad[i]), Lp = xyz(E.rad[i + 32]);
-    float4 w = E.sj[cap + job], m = E.sj[2 * cap + job], gq = E.sj[3 * cap + job];
-    float cv = (gq.x * (Lm.x - Lp.x) + gq.y * (Lm.y - Lp.y) + gq.z * (Lm.z - Lp.z)) * w.w;
-    if (cv != 0.0f) {
-      int4 je = E.sje[job];
-      float3 mh = xyz(m);
-      int e = __float_as_int(gq.w);
-      int2 ev = c.edge_v[e];
-      float3 da = mh * (cv * (1.0f - m.w)), db = mh * (cv * m.w);
-      vals[0] = da.x; vals[1] = da.y; vals[2] = da.z;
-      vals[3] = db.x; vals[4] = db.y; vals[5] = db.z;
-      key = e;
-      va = ev.x;
-      vb = ev.y;
-      E.pinj[je.w * Q + je.z] = make_float4(-cv * mh.x, -cv * mh.y, -cv * mh.z, 0.0f);
+  long long J;
+  const int total = sec_pass_slots(E, pass, J);
+  for (int base = blockIdx.x * blockDim.x; base < total; base += gridDim.x * blockDim.x) {
+    int i = base + threadIdx.x;
+    long long sidx = (long long)pass * E.Q + i;
+    long long job = (sidx >> 6) * 32 + (sidx & 31);
+    float vals[6] = {0, 0, 0, 0, 0, 0};
+    int key = -1, va = 0, vb = 0;
+    if (i < total && (sidx & 32) == 0 && job < J) {
+      float3 Lm = xyz(E.rad[i]), Lp = xyz(E.rad[i + 32]);
+      float4 w = E.sj[cap + job], m = E.sj[2 * cap + job], gq = E.sj[3 * cap + job];
+      float cv = (gq.x * (Lm.x - Lp.x) + gq.y * (Lm.y - Lp.y) + gq.z * (Lm.z - Lp.z)) * w.w;
+      if (cv != 0.0f) {
+        int4 je = E.sje[job];
+        float3 mh = xyz(m);
+        int e = __float_as_int(gq.w);
+        int2 ev = c.edge_v[e];
+        float3 da = mh * (cv * (1.0f - m.w)), db = mh * (cv * m.w);
+        vals[0] = da.x; vals[1] = da.y; vals[2] = da.z;
+        vals[3] = db.x; vals[4] = db.y; vals[5] = db.z;
+        key = e;
+        va = ev.x;
+        vb = ev.y;
+        E.pinj[je.w * Q + je.z] = make_float4(-cv * mh.x, -cv * mh.y, -cv * mh.z, 0.0f);
+      }
     }
-  }
-  bool leader;
-  warp_reduce_peers<6>(key, vals, scr, leader);
-  if (leader) {
-    float* dV = c.args->dV;
-    atomicAdd(&dV[3 * va], vals[0]); atomicAdd(&dV[3 * va + 1], vals[1]); atomicAdd(&dV[3 * va + 2], vals[2]);
-    atomicAdd(&dV[3 * vb], vals[3]); atomicAdd(&dV[3 * vb + 1], vals[4]); atomicAdd(&dV[3 * vb + 2], vals[5]);
+    bool leader;
+    warp_reduce_peers<6>(key, vals, scr, leader);
+    if (leader) {
+      float* dV = c.args->dV;
+      atomicAdd(&dV[3 * va], vals[0]); atomicAdd(&dV[3 * va + 1], vals[1]); atomicAdd(&dV[3 * va + 2], vals[2]);
+      atomicAdd(&dV[3 * vb], vals[3]); atomicAdd(&dV[3 * vb + 1], vals[4]); atomicAdd(&dV[3 * vb + 2], vals[5]);
+    }
   }
 }
 

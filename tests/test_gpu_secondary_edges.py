@@ -65,11 +65,15 @@ def test_secondary_matches_oracle_on_the_pinned_scenes(st, name, B):
     assert rel_l2([dV0, dF0], [rv, rf]) > 0.05
 
 
-@pytest.mark.parametrize("workload,edge_mode,B", [("edges", 0, 3), ("color_bleed", 1, 3), ("env", 0, 2)])
+@pytest.mark.parametrize("workload,edge_mode,B", [("color_bleed", 0, 3), ("color_bleed", 1, 3), ("env", 0, 2),
+                                                   ("env", 1, 3)])
 def test_secondary_matches_oracle_on_workloads(st, workload, edge_mode, B):
+    # the three planes (a concave corner of coplanar grids) and the torus knot
+    # (self-occluding): samples are accepted at many vertices
     sc = S.small_variant(S.make(workload), n_views=2, max_res=24, spp=2)
     w = np.random.default_rng(6).normal(size=(sc.n_pixels, 3))
     dV, dF, stats = _gpu_grad(st, sc, B, 91, w, st.EDGE_TERM_SECONDARY, edge_mode)
+    assert stats["secondary_samples"] > 0
     rv, rf = _oracle_grad(sc, B, 91, w, edge_mode)
     assert rel_l2([dV, dF], [rv, rf]) <= SEC_REL, stats
 
@@ -94,10 +98,10 @@ def test_secondary_is_exactly_zero_on_a_convex_mesh(st):
 
 
 def test_secondary_graph_small_chunks_and_per_view_agree(st):
-    sc = S.small_variant(S.make("edges"), n_views=3, max_res=24, spp=2)
+    sc = S.small_variant(S.make("color_bleed"), n_views=3, max_res=24, spp=2)
     w = np.random.default_rng(9).normal(size=(sc.n_pixels, 3))
     ref = _gpu_grad(st, sc, 3, 21, w, st.EDGE_TERM_SECONDARY)
     for kw in [dict(use_graph=0), dict(chunk_paths=1024), dict(mode="per_view")]:
         got = _gpu_grad(st, sc, 3, 21, w, st.EDGE_TERM_SECONDARY, **kw)
-        assert got[2]["secondary_samples"] == ref[2]["secondary_samples"]
+        assert got[2]["secondary_samples"] == ref[2]["secondary_samples"] > 0
         assert rel_l2(got[:2], ref[:2]) <= 1e-5, kw
