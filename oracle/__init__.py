@@ -39,7 +39,8 @@ class _Scene(C.Structure):
 class _View(C.Structure):
     _fields_ = [("eye", C.c_float * 3), ("target", C.c_float * 3), ("up", C.c_float * 3),
                 ("fov_y_deg", C.c_float), ("width", C.c_int), ("height", C.c_int), ("spp", C.c_int),
-                ("pixel_offset", C.c_longlong)]
+                ("pixel_offset", C.c_longlong), ("n_lights", C.c_int), ("light_pos", (C.c_float * 3) * 2),
+                ("light_intensity", (C.c_float * 3) * 2)]
 
 
 class _Params(C.Structure):
@@ -113,8 +114,11 @@ class OracleScene:
                         None if self.E is None else _ptr(self.E).value, int(getattr(sc, "color_res", 0)))
         self.views = (_View * len(sc.views))()
         for i, v in enumerate(sc.views):
+            lights = list(getattr(v, "lights", ()) or ())
+            lp = ((C.c_float * 3) * 2)(*[(C.c_float * 3)(*l[0]) for l in lights])
+            li = ((C.c_float * 3) * 2)(*[(C.c_float * 3)(*l[1]) for l in lights])
             self.views[i] = _View((C.c_float * 3)(*v.eye), (C.c_float * 3)(*v.target), (C.c_float * 3)(*v.up),
-                                  v.fov_y_deg, v.width, v.height, v.spp, v.pixel_offset)
+                                  v.fov_y_deg, v.width, v.height, v.spp, v.pixel_offset, len(lights), lp, li)
         self.n_views = len(sc.views)
         self.nv, self.nf = len(self.V), len(self.F)
         self.ntex = len(self.P)          # texels (= faces at mesh-colors resolution 0)

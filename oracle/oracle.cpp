@@ -191,15 +191,26 @@ struct Scene {
   std::vector<int> alias;
 };
 
+// Point lights a path of one view sees: the scene's, then the view's own
+// (e.g. a light at the camera, Sec. 4), in that order.
+struct Lights { std::vector<V3d> pos, I; };
+
 struct Cam {
   V3d eye, fwd, right, up;
   double th, aspect;
   int W, H, spp;
   uint32_t off;
+  Lights lt;
 };
 
-Cam make_cam(const orc_view& v) {
+Cam make_cam(const orc_view& v, const Scene& s) {
   Cam c;
+  c.lt.pos = s.lpos;
+  c.lt.I = s.lint;
+  for (int j = 0; j < v.n_lights && j < 2; ++j) {
+    c.lt.pos.push_back({v.light_pos[j][0], v.light_pos[j][1], v.light_pos[j][2]});
+    c.lt.I.push_back({v.light_intensity[j][0], v.light_intensity[j][1], v.light_intensity[j][2]});
+  }
   c.eye = {v.eye[0], v.eye[1], v.eye[2]};
   V3d tg = {v.target[0], v.target[1], v.target[2]};
   V3d up = {v.up[0], v.up[1], v.up[2]};
@@ -582,7 +593,7 @@ double face_side(const Scene& s, int f, const V3d& p) {
 }
 
 template <class T>
-void trace_path(const Scene& s, const Rng& rng, int B, const V3d& eye, const V3d& d0, uint32_t c0,
+void trace_path(const Scene& s, const Rng& rng, int B, const Lights& lt, const V3d& eye, const V3d& d0, uint32_t c0,
                 uint32_t c1, uint32_t stream, Vars* vars, T L[3], long long& segments, Tape* tape = nullptr,
                 const SecCtx* sec = nullptr, int b0 = 0, int origin0 = -1);
 
@@ -600,7 +611,8 @@ void trace_path(const Scene& s, const Rng& rng, int B, const V3d& eye, const V3d
 // direction, so the sample's weight is |w x t| E len (tau1 - tau0) / r^2 times
 // T_b (g- - g+). It is added to L as a dual with zero value whose derivative is
 // that weight times m.(dx - dp), dx = (1 - tau) dA + tau dB.
-void secondary_edge(const Scene& s, const Rng& rng, int B, int b, const V3<Dual>& p, const V3d& nv, const V3d& wo,
+void secondary_edge(const Scene& s, const Rng& rng, int B, const Lights& lt, int b, const V3<Dual>& p, const V3d& nv,
+                    const V3d& wo,
                     int f0, long long tex, const Dual thr[3], uint32_t c0, uint32_t c1, uint32_t stream,
                     const SecCtx& sc, Vars* vars, Dual L[3], long long& segments) {
   const std::vector<Edge>& E = *sc.E;
@@ -650,7 +662,7 @@ void secondary_edge(const Scene& s, const Rng& rng, int B, int b, const V3<Dual>
     double f[3], Li[3];
     brdf_eval(s.brdf, m, nv, ws, wo, f);
     double ci = dot(nv, ws);
-    trace_path<double>(s, rng, B, pv, ws, c0, c1, 16u + (uint32_t)b, nullptr, Li, segments, nullptr, nullptr, b + 1,
+    trace_path<double>(s, rng, B, lt, pv, ws, c0, c1, 16u + (uint32_t)b, nullptr, Li, segments, nullptr, nullptr, b + 1,
                        f0);
     for (int c = 0; c < 3; ++c) g[side][c] = ci > 0 ? f[c] * ci * Li[c] : 0.0;
   }
@@ -675,7 +687,7 @@ void secondary_edge(const Scene& s, const Rng& rng, int B, int b, const V3<Dual>
 // a secondary edge sample): its first ray collects the environment unweighted,
 // and a first ray that would find vertex B adds nothing.
 template <class T>
-void trace_path(const Scene& s, const Rng& rng, int B, const V3d& eye, const V3d& d0, uint32_t c0,
+void trace_path(const Scene& s, const Rng& rng, int B, const Lights& lt, const V3d& eye, const V3d& d0, uint32_t c0,
                 uint32_t c1, uint32_t stream, Vars* vars, T L[3], long long& segments, Tape* tape,
                 const SecCtx* sec, int b0, int origin0) {
   using A = Access<T>;
@@ -723,8 +735,8 @@ void trace_path(const Scene& s, const Rng& rng, int B, const V3d& eye, const V3d
     V3d nv = val(n), pv = val(p);
 
     // next-event estimation: point lights
-    for (size_t j = 0; j < s.lpos.size(); ++j) {
-      V3<T> dv = lift<T>(s.lpos[j]) - p;
+    for (size_t j = 0; j < lt.pos.size(); ++j) {
+      V3<T> dv = lift<T>(lt.pos[j]) - p;
       T dist = len(dv);
       V3<T> wi = scl(dv, 1.0 / dist);
       T ci = dot(n, wi);
@@ -734,7 +746,7 @@ void trace_path(const Scene& s, const Rng& rng, int B, const V3d& eye, const V3d
       T f[3];
       brdf_eval(s.brdf, m, n, wi, wo, f);
       T g = ci / (dist * dist);
-      for (int c = 0; c < 3; ++c) L[c] = L[c] + thr[c] * f[c] * g * comp(s.lint[j], c);
+      for (int c = 0; c < 3; ++c) L[c] = L[c] + thr[c] * f[c] * g * comp(lt.I[j], c);
     }
     // next-event estimation: environment
     if (s.ew > 0) {
@@ -770,7 +782,7 @@ void trace_path(const Scene& s, const Rng& rng, int B, const V3d& eye, const V3d
       }
     }
     if constexpr (std::is_same<T, Dual>::value) {
-      if (sec) secondary_edge(s, rng, B, b, p, nv, wo_d, h.tri, tex, thr, c0, c1, stream, *sec, vars, L, segments);
+      if (sec) secondary_edge(s, rng, B, lt, b, p, nv, wo_d, h.tri, tex, thr, c0, c1, stream, *sec, vars, L, segments);
     }
     if (b == B - 1) return;
     // BSDF sampling (direction and pdf held constant under differentiation)
@@ -973,7 +985,9 @@ void orc_closest_hit(const orc_scene* in, const double* rays, int n, int exclude
 static bool check_common(const orc_view* views, int n_views, const orc_params* p) {
   if (!views || n_views <= 0 || !p || p->max_bounces < 1 || p->max_bounces > MAX_B) return false;
   for (int v = 0; v < n_views; ++v)
-    if (views[v].width <= 0 || views[v].height <= 0 || views[v].spp <= 0) return false;
+    if (views[v].width <= 0 || views[v].height <= 0 || views[v].spp <= 0 || views[v].n_lights < 0 ||
+        views[v].n_lights > 2)
+      return false;
   return true;
 }
 
@@ -992,7 +1006,7 @@ long long orc_render_pixels(const orc_scene* in, const orc_view* views, int n_vi
     if (pix[3 * i] < 0 || pix[3 * i] >= n_views) return -1;
   parallel_for(n, nt, [&](int tid, int i) {
     const orc_view& v = views[pix[3 * i]];
-    Cam c = make_cam(v);
+    Cam c = make_cam(v, s);
     int x = pix[3 * i + 1], y = pix[3 * i + 2];
     uint32_t c0 = c.off + (uint32_t)(y * c.W + x);
     double acc[3] = {0, 0, 0};
@@ -1000,7 +1014,7 @@ long long orc_render_pixels(const orc_scene* in, const orc_view* views, int n_vi
       U4 u = rng.draw(c0, (uint32_t)sidx, 0u, 0u);
       V3d d = cam_dir(c, x + unif(u.w[0]), y + unif(u.w[1]));
       double L[3];
-      trace_path<double>(s, rng, p->max_bounces, c.eye, d, c0, (uint32_t)sidx, 0u, nullptr, L, seg[tid]);
+      trace_path<double>(s, rng, p->max_bounces, c.lt, c.eye, d, c0, (uint32_t)sidx, 0u, nullptr, L, seg[tid]);
       for (int k = 0; k < 3; ++k) acc[k] += L[k];
     }
     for (int k = 0; k < 3; ++k) out[3 * i + k] = acc[k] / c.spp;
@@ -1027,7 +1041,7 @@ long long orc_grad_pixels(const orc_scene* in, const orc_view* views, int n_view
     const double* w = dLdI + 3 * (size_t)i;
     if (w[0] == 0 && w[1] == 0 && w[2] == 0) return;
     const orc_view& v = views[pix[3 * i]];
-    Cam c = make_cam(v);
+    Cam c = make_cam(v, s);
     int x = pix[3 * i + 1], y = pix[3 * i + 2];
     uint32_t c0 = c.off + (uint32_t)(y * c.W + x);
     for (int sidx = 0; sidx < c.spp; ++sidx) {
@@ -1035,7 +1049,7 @@ long long orc_grad_pixels(const orc_scene* in, const orc_view* views, int n_view
       V3d d = cam_dir(c, x + unif(u.w[0]), y + unif(u.w[1]));
       Vars vars;
       Dual L[3];
-      trace_path<Dual>(s, rng, p->max_bounces, c.eye, d, c0, (uint32_t)sidx, 0u, &vars, L, seg[tid], nullptr, sec);
+      trace_path<Dual>(s, rng, p->max_bounces, c.lt, c.eye, d, c0, (uint32_t)sidx, 0u, &vars, L, seg[tid], nullptr, sec);
       Dual loss = L[0] * (w[0] / c.spp) + L[1] * (w[1] / c.spp) + L[2] * (w[2] / c.spp);
       scatter_grad(vars, loss, gv[tid].data(), gf[tid].data());
     }
@@ -1053,7 +1067,7 @@ int orc_edge_candidates(const orc_scene* in, const orc_view* view, const orc_par
   Scene s;
   if (!load_scene(in, s) || !view || !p) return -1;
   std::vector<Edge> E = edge_list(s);
-  std::vector<Cand> C = candidates(s, E, make_cam(*view), p->edge_mode);
+  std::vector<Cand> C = candidates(s, E, make_cam(*view, s), p->edge_mode);
   if (out_edges)
     for (size_t i = 0; i < C.size(); ++i) { out_edges[2 * i] = E[C[i].e].a; out_edges[2 * i + 1] = E[C[i].e].b; }
   return (int)C.size();
@@ -1069,7 +1083,7 @@ long long orc_edge_grad(const orc_scene* in, const orc_view* views, int n_views,
   std::vector<long long> seg(nt, 0);
   std::vector<std::vector<double>> gv(nt, std::vector<double>(3 * (size_t)s.nv, 0.0));
   for (int vi = 0; vi < n_views; ++vi) {
-    Cam c = make_cam(views[vi]);
+    Cam c = make_cam(views[vi], s);
     std::vector<Cand> C = candidates(s, E, c, p->edge_mode);
     if (C.empty()) continue;
     long long spp_e = p->edge_spp > 0 ? p->edge_spp : c.spp;
@@ -1095,9 +1109,9 @@ long long orc_edge_grad(const orc_scene* in, const orc_view* views, int n_views,
         double el = std::sqrt(ex * ex + ey * ey);
         double nx = -ey / el, ny = ex / el;
         double Lm[3], Lp[3];
-        trace_path<double>(s, rng, p->max_bounces, c.eye, cam_dir(c, sx - EDGE_EPS * nx, sy - EDGE_EPS * ny),
+        trace_path<double>(s, rng, p->max_bounces, c.lt, c.eye, cam_dir(c, sx - EDGE_EPS * nx, sy - EDGE_EPS * ny),
                            (uint32_t)k, c.off, 2u, nullptr, Lm, seg[tid]);
-        trace_path<double>(s, rng, p->max_bounces, c.eye, cam_dir(c, sx + EDGE_EPS * nx, sy + EDGE_EPS * ny),
+        trace_path<double>(s, rng, p->max_bounces, c.lt, c.eye, cam_dir(c, sx + EDGE_EPS * nx, sy + EDGE_EPS * ny),
                            (uint32_t)k, c.off, 2u, nullptr, Lp, seg[tid]);
         double g = 0;
         for (int ch = 0; ch < 3; ++ch) g += w[ch] * (Lm[ch] - Lp[ch]);
@@ -1124,11 +1138,11 @@ long long orc_trace_screen(const orc_scene* in, const orc_view* view, const orc_
   Scene s;
   if (!load_scene(in, s) || !check_common(view, 1, p)) return -1;
   Rng rng = rng_of(p);
-  Cam c = make_cam(*view);
+  Cam c = make_cam(*view, s);
   V3d d = cam_dir(c, px, py);
   long long seg = 0;
   if (!grad_w) {
-    trace_path<double>(s, rng, p->max_bounces, c.eye, d, c0, c1, stream, nullptr, rgb, seg);
+    trace_path<double>(s, rng, p->max_bounces, c.lt, c.eye, d, c0, c1, stream, nullptr, rgb, seg);
     return seg;
   }
   Vars vars;
@@ -1136,7 +1150,7 @@ long long orc_trace_screen(const orc_scene* in, const orc_view* view, const orc_
   std::vector<Edge> E;
   if (p->secondary) E = edge_list(s);
   SecCtx sc{&E, p->edge_mode};
-  trace_path<Dual>(s, rng, p->max_bounces, c.eye, d, c0, c1, stream, &vars, L, seg, nullptr,
+  trace_path<Dual>(s, rng, p->max_bounces, c.lt, c.eye, d, c0, c1, stream, &vars, L, seg, nullptr,
                    p->secondary ? &sc : nullptr);
   for (int k = 0; k < 3; ++k) rgb[k] = L[k].v;
   Dual loss = L[0] * grad_w[0] + L[1] * grad_w[1] + L[2] * grad_w[2];
@@ -1150,12 +1164,12 @@ long long orc_trace_screen_taped(const orc_scene* in, const orc_view* view, cons
   Scene s;
   if (!load_scene(in, s) || !check_common(view, 1, p) || !tape_len) return -1;
   Rng rng = rng_of(p);
-  Cam c = make_cam(*view);
+  Cam c = make_cam(*view, s);
   Tape tp;
   tp.mode = mode;
   if (mode == 2) tp.v.assign(tape, tape + *tape_len);
   long long seg = 0;
-  trace_path<double>(s, rng, p->max_bounces, c.eye, cam_dir(c, px, py), c0, c1, stream, nullptr, rgb, seg, &tp);
+  trace_path<double>(s, rng, p->max_bounces, c.lt, c.eye, cam_dir(c, px, py), c0, c1, stream, nullptr, rgb, seg, &tp);
   if (tp.bad || (mode == 2 && tp.pos != tp.v.size())) return -2;
   if (mode == 1) {
     if ((int)tp.v.size() > *tape_len) return -3;

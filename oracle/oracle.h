@@ -48,6 +48,9 @@ typedef struct {
   float fov_y_deg;
   int width, height, spp;
   long long pixel_offset;
+  int n_lights;                  /* point lights of this view only (0..2), after the scene's */
+  float light_pos[2][3];
+  float light_intensity[2][3];
 } orc_view;
 
 typedef struct {

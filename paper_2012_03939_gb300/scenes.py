@@ -35,6 +35,7 @@ class View:
     height: int
     spp: int
     pixel_offset: int = 0
+    lights: tuple = ()              # the view's own point lights: ((x, y, z), (I_r, I_g, I_b)) pairs, at most 2
 
 
 @dataclasses.dataclass

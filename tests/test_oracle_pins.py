@@ -356,6 +356,50 @@ def test_point_light_lambertian_closed_form():
     assert hits > 40
 
 
+@pytest.mark.parametrize("where", ["view", "scene+view", "two view lights"])
+def test_view_lights_lambertian_closed_form(where):
+    # the same closed form with lights that belong to the view (a light at the
+    # camera and one offset from it, as in the paper's captures, Sec. 4): the
+    # radiance is the sum over the scene's and the view's lights
+    import dataclasses
+    sc = S.single_triangle(16, 16, light_dist=2.5)
+    eye = np.array(sc.views[0].eye, np.float64)
+    A = ((0.7, 0.4, 2.2), (3.0, 4.0, 5.0))
+    Bl = (tuple(eye + np.array([0.3, 0.0, 0.0])), (2.0, 1.0, 0.5))
+    Cl = (tuple(eye), (1.5, 1.5, 1.5))
+    scene_l, view_l = {"view": ([], [A]), "scene+view": ([A], [Bl]), "two view lights": ([], [Cl, Bl])}[where]
+    sc.light_pos = np.array([l[0] for l in scene_l], np.float32).reshape(-1, 3)
+    sc.light_intensity = np.array([l[1] for l in scene_l], np.float32).reshape(-1, 3)
+    sc.views = [dataclasses.replace(sc.views[0], lights=tuple(view_l))]
+    pa = np.array([[0.8, 0.5, 0.3, 0.3, 0.4]], np.float32)
+    pb = np.array([[0.2, 0.1, 0.6, 0.3, 0.4]], np.float32)
+    oa, ob = O.OracleScene(sc, face_params=pa), O.OracleScene(sc, face_params=pb)
+    prm = O.params(1, 5)
+    V = sc.vertices.astype(np.float64)
+    nrm = np.cross(V[1] - V[0], V[2] - V[0])
+    nrm /= np.linalg.norm(nrm)
+    dkd = pa[0, :3].astype(np.float64) - pb[0, :3].astype(np.float64)
+    hits = 0
+    for px in np.linspace(0.5, 15.5, 9):
+        for py in np.linspace(0.5, 15.5, 9):
+            o, d = G.pixel_ray(sc.views[0], px, py)
+            t = ((V[0] - o) @ nrm) / (d @ nrm)
+            p = o + t * d
+            lam = np.linalg.solve(np.c_[V[1] - V[0], V[2] - V[0], nrm], p - V[0])
+            if min(lam[0], lam[1], 1 - lam[0] - lam[1]) < 1e-3:
+                continue
+            n = nrm if nrm @ -d > 0 else -nrm
+            exp = np.zeros(3)
+            for pos, inten in scene_l + view_l:
+                wl = np.array(pos, np.float32).astype(np.float64) - p
+                dist = np.linalg.norm(wl)
+                exp += dkd / math.pi * np.array(inten, np.float32).astype(np.float64) * max(0.0, n @ wl / dist) / dist ** 2
+            got = O.trace_screen(oa, prm, 0, px, py) - O.trace_screen(ob, prm, 0, px, py)
+            np.testing.assert_allclose(got, exp, rtol=1e-10, atol=1e-14)
+            hits += 1
+    assert hits > 20
+
+
 # ---------------------------------------------------------------------------- white furnace
 @pytest.mark.parametrize("B", [1, 2, 3])
 def test_white_furnace(B):
