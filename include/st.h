@@ -81,12 +81,18 @@ typedef struct {
 
 /* Pinhole view c_i (Sec. 3.2): fov_y in degrees, +y up on screen. spp == 0
  * takes the call's default_spp. pixel_offset = first packed-image row of the
- * view; it also keys the view's random numbers. */
+ * view; it also keys the view's random numbers. lights: point lights that
+ * only this view's paths see, after the scene's (the paper lights each capture
+ * from the camera and from a point offset from it, Sec. 4); the scene's and
+ * the view's lights together are at most ST_MAX_LIGHTS. */
+#define ST_MAX_VIEW_LIGHTS 2
 typedef struct {
   float eye[3], target[3], up[3];
   float fov_y_deg;
   int width, height, spp;
   long long pixel_offset;
+  int n_lights;                                     /* 0..ST_MAX_VIEW_LIGHTS */
+  struct { float pos[3]; float intensity[3]; } lights[ST_MAX_VIEW_LIGHTS];
 } st_view;
 
 /* Material: mesh colors (Sec. 3.3) at resolution r = color_res. Face t owns
@@ -101,7 +107,7 @@ typedef struct {
   const int* faces;          /* device, int [F][3] vertex indices */
   const float* face_params;  /* device, float [F*n][5] texel parameters (n = 1 when color_res = 0) */
   int brdf;                  /* ST_BRDF_GGX or ST_BRDF_BECKMANN */
-  int n_point_lights;        /* 0..ST_MAX_LIGHTS */
+  int n_point_lights;        /* 0..ST_MAX_LIGHTS (a call needs some light: these, the environment or its views') */
   const st_point_light* point_lights; /* host array */
   const st_envmap* env;      /* NULL if no environment */
   int color_res;             /* mesh-colors resolution r, 0..64 */

@@ -154,6 +154,12 @@ DevView make_view(const st_view& v, int spp) {
   d.spp = spp;
   d.off = (uint32_t)v.pixel_offset;
   d.pix_off = v.pixel_offset;
+  d.nvl = v.n_lights;
+  for (int j = 0; j < 4; ++j) d.vl[j] = make_float4(0, 0, 0, 0);
+  for (int j = 0; j < v.n_lights && j < ST_MAX_VIEW_LIGHTS; ++j) {
+    d.vl[2 * j] = make_float4(v.lights[j].pos[0], v.lights[j].pos[1], v.lights[j].pos[2], 0.0f);
+    d.vl[2 * j + 1] = make_float4(v.lights[j].intensity[0], v.lights[j].intensity[1], v.lights[j].intensity[2], 0.0f);
+  }
   return d;
 }
 
@@ -181,6 +187,7 @@ struct Plan {
   long long pixels = 0;       // sum of W*H: the primary-visibility bin space
   bool interior = false, edges = false;
   bool sec = false;           // secondary-visibility edge samples at every camera-path vertex
+  int max_vl = 0;             // most point lights a view of the call adds to the scene's
   bool bins = false;          // build primary-visibility bins (worth it only for many primary rays)
   st_render_opts o{};
 };
@@ -301,7 +308,7 @@ st_status ensure_bins(st_scene* s, const Plan& p) {
 KCtx make_ctx(st_scene* s, const Plan& p) {
   KCtx c;
   c.V = s->verts; c.F = s->faces; c.P = s->params; c.nodes = s->nodes4; c.tri = s->tri; c.nf = s->nf;
-  c.lights = s->lights; c.nl = s->nl; c.NS = s->nl + (s->env.w > 0 ? 1 : 0);
+  c.lights = s->lights; c.nl = s->nl; c.nlt = s->nl + p.max_vl; c.NS = c.nlt + (s->env.w > 0 ? 1 : 0);
   c.env = s->env; c.brdf = s->brdf; c.res = s->res; c.ntex = s->ntex;
   c.edge_v = s->edge_v; c.edge_f = s->edge_f; c.n_edges = s->n_edges; c.edge_mode = p.o.edge_mode;
   c.edge_flag = s->edge_flag; c.edge_cand = s->edge_cand; c.edge_ncand = s->edge_ncand;
@@ -490,7 +497,7 @@ st_status enqueue_call(st_scene* s, const Plan& p, int Q, cudaStream_t st, bool 
 std::vector<long long> graph_key(const Plan& p, int Q, const st_scene* s) {
   std::vector<long long> k = {p.kind, p.B, (long long)p.views.size(), Q, p.o.edge_term, p.o.edge_mode, p.o.edge_spp,
                               p.interior, p.edges, p.o.count_visits, p.bins,
-                              p.o.persist_blocks, s->bin_cap};
+                              p.o.persist_blocks, s->bin_cap, p.max_vl};
   for (auto& v : p.views) { k.push_back(v.W); k.push_back(v.H); k.push_back(v.spp); k.push_back(v.pix_off); }
   return k;
 }
@@ -515,6 +522,14 @@ st_status plan_call(st_scene* s, const st_view* views, int n_views, int default_
   for (int i = 0; i < n_views; ++i) {
     const st_view& v = views[i];
     if (!view_ok(v)) return fail(ST_ERR_INVALID_ARG, "view " + std::to_string(i) + " is invalid");
+    if (v.n_lights < 0 || v.n_lights > ST_MAX_VIEW_LIGHTS || s->nl + v.n_lights > ST_MAX_LIGHTS)
+      return fail(ST_ERR_INVALID_ARG, "view " + std::to_string(i) + ": bad number of view lights");
+    for (int j = 0; j < v.n_lights; ++j)
+      for (int k = 0; k < 3; ++k)
+        if (!std::isfinite(v.lights[j].pos[k]) || !std::isfinite(v.lights[j].intensity[k]) ||
+            v.lights[j].intensity[k] < 0.0f)
+          return fail(ST_ERR_INVALID_ARG, "view " + std::to_string(i) + ": bad view light");
+    p.max_vl = std::max(p.max_vl, v.n_lights);
     int spp = v.spp > 0 ? v.spp : default_spp;
     if (spp <= 0) return fail(ST_ERR_INVALID_ARG, "view " + std::to_string(i) + " has no samples");
     if ((long long)v.width * v.height > (1LL << 31) || v.pixel_offset + (long long)v.width * v.height > (1LL << 32))
@@ -538,6 +553,8 @@ st_status plan_call(st_scene* s, const st_view* views, int n_views, int default_
     p.view_range.push_back({start, base});
   }
   p.total = base;
+  if (s->nl == 0 && s->env.w == 0 && p.max_vl == 0)
+    return fail(ST_ERR_INVALID_ARG, "no light: the scene has none and no view brings one");
   // below about a million primary rays the fixed cost of building the bins
   // (seven launches) exceeds what they save; those calls traverse the BVH
   p.bins = p.total >= (1LL << 20);
@@ -582,7 +599,7 @@ st_status run_call(st_scene* s, Plan& p, const CallArgs& args, cudaStream_t st) 
     for (auto& vr : p.view_range) mx = std::max(mx, vr.second - vr.first);
     Q = (int)std::min<long long>(Q, (mx + SEG_ALIGN - 1) / SEG_ALIGN * SEG_ALIGN);
   }
-  int NS = s->nl + (s->env.w > 0 ? 1 : 0);
+  int NS = s->nl + p.max_vl + (s->env.w > 0 ? 1 : 0);
   r = ensure_engine(s, Q, p.B, NS, p.kind == 1, p.sec);
   if (r != ST_OK) return r;
   ST_CUDA(cudaMemcpyAsync(s->d_views, p.views.data(), sizeof(DevView) * p.views.size(), cudaMemcpyHostToDevice, st));
@@ -680,7 +697,6 @@ st_status st_scene_create(const st_scene_desc* d, void* stream, st_scene** out) 
     return fail(ST_ERR_UNSUPPORTED, "too many mesh-colors texels");
   if (d->n_point_lights < 0 || d->n_point_lights > ST_MAX_LIGHTS || (d->n_point_lights > 0 && !d->point_lights))
     return fail(ST_ERR_INVALID_ARG, "bad point lights");
-  if (d->n_point_lights == 0 && !d->env) return fail(ST_ERR_INVALID_ARG, "scene has no light");
   for (int j = 0; j < d->n_point_lights; ++j)
     for (int k = 0; k < 3; ++k)
       if (!std::isfinite(d->point_lights[j].pos[k]) || !std::isfinite(d->point_lights[j].intensity[k]) ||

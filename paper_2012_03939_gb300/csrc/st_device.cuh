@@ -70,6 +70,8 @@ struct DevView {
   uint32_t off;            // low 32 bits of pixel_offset (counter word)
   long long pix_off;       // packed-image row of pixel (0, 0)
   long long bin_base;      // first pixel of the view in the primary-visibility bins
+  int nvl;                 // the view's own point lights (after the scene's)
+  float4 vl[4];            // (position, 0), (intensity, 0) per view light
 };
 
 __device__ __forceinline__ float3 cam_dir(const DevView& v, float px, float py) {

@@ -28,7 +28,7 @@ struct KCtx {
   const float4* tri;
   int nf;
   const float4* lights;
-  int nl, NS;
+  int nl, nlt, NS;        // scene lights, + the most any view of the call adds, + environment
   DevEnv env;
   int brdf;
   int res, ntex;          // mesh-colors resolution r and texels per face
@@ -85,6 +85,21 @@ __device__ __forceinline__ Mat fetch_mat(const float4* P, int f) {
   Mat m;
   m.kd[0] = a.x; m.kd[1] = a.y; m.kd[2] = a.z; m.ks = a.w; m.alpha = b.x;
   return m;
+}
+
+// Point light j of a path of view vi: the scene's lights, then the view's own.
+__device__ __forceinline__ void point_light(const KCtx& c, int vi, int j, float4& lp, float4& li) {
+  if (j < c.nl) {
+    lp = __ldg(&c.lights[2 * j]);
+    li = __ldg(&c.lights[2 * j + 1]);
+  } else {
+    lp = c.views[vi].vl[2 * (j - c.nl)];
+    li = c.views[vi].vl[2 * (j - c.nl) + 1];
+  }
+}
+
+__device__ __forceinline__ int lights_of(const KCtx& c, int vi) {
+  return c.nlt > c.nl ? c.nl + c.views[vi].nvl : c.nl;
 }
 
 // Mesh-colors texel of a hit at p on face f (Sec. 3.3): k = (f (r+1)(r+2) +
@@ -433,7 +448,7 @@ __global__ void k_raygen(KCtx c, long long j0, int n) {
           U4 u = philox(c0, (uint32_t)s, 0u, 0u, key.k0, key.k1);
           d = cam_dir(v, (float)x + unif(u.x), (float)y + unif(u.y));
           o = v.eye;
-          ct = make_int4((int)c0, s, 0, 0);
+          ct = make_int4((int)c0, s, 0, sg.view << 4);
           br = bin_range(c, sg.view, v, x, y);
           ok = true;
         } else {
@@ -448,7 +463,7 @@ __global__ void k_raygen(KCtx c, long long j0, int n) {
             d = cam_dir(v, sx, sy);
             o = v.eye;
             br = bin_range(c, sg.view, v, (int)floorf(sx), (int)floorf(sy));
-            ct = make_int4((int)(uint32_t)k, (int)v.off, 2, 0);
+            ct = make_int4((int)(uint32_t)k, (int)v.off, 2, sg.view << 4);
             ok = true;
           }
         }
@@ -544,7 +559,8 @@ __global__ void k_shade(KCtx c, int b) {
   if (live_) {
     int2 h = E.hit[slot];
     int4 ct = E.ctr[slot];
-    const int vb = b + ct.w;      // path vertex this ray finds (side paths of edge samples start past 0)
+    const int vb = b + (ct.w & 15);   // path vertex this ray finds (side paths of edge samples start past 0)
+    const int vi = ct.w >> 4;         // the path's view (its own lights)
     float4 o4 = E.o[slot], d4 = E.d[slot];
     float3 dir = xyz(d4);
     float3 T = xyz(E.thr[slot]);
@@ -579,13 +595,15 @@ __global__ void k_shade(KCtx c, int b) {
         E.r0[b * Q + slot] = make_float4(p.x, p.y, p.z, __int_as_float(f));
         E.nb[slot] = b + 1;
       }
-      for (int j = 0; j < c.nl; ++j) {
-        float4 lp = __ldg(&c.lights[2 * j]), li = __ldg(&c.lights[2 * j + 1]);
+      const int nlp = lights_of(c, vi);
+      for (int j = 0; j < c.nlt; ++j) {
+        float4 lp = make_float4(0, 0, 1, 0), li = make_float4(0, 0, 0, 0);
+        if (j < nlp) point_light(c, vi, j, lp, li);
         float3 dv = xyz(lp) - p;
         float dist = len3(dv);
         float3 wi = dv * (1.0f / dist);
         float ci = dot3(n, wi);
-        bool valid = ci > 0.0f && dist > 2.0f * T_EPS;
+        bool valid = j < nlp && ci > 0.0f && dist > 2.0f * T_EPS;
         float3 cc = mk3(0, 0, 0);
         if (valid) cc = mul(mul(T, brdf_cos(c.brdf, m, n, wi, wo)), xyz(li)) * (1.0f / (dist * dist));
         E.sh_dir[j * Q + slot] = make_float4(wi.x, wi.y, wi.z, dist - T_EPS);
@@ -617,8 +635,8 @@ __global__ void k_shade(KCtx c, int b) {
           cc = mul(mul(T, brdf_cos(c.brdf, m, n, ewi, wo)), escale);
           flags |= ENV_VALID;
         }
-        E.sh_dir[c.nl * Q + slot] = make_float4(ewi.x, ewi.y, ewi.z, __int_as_float(0x7f800000));
-        E.sh_c[c.nl * Q + slot] = make_float4(cc.x, cc.y, cc.z, valid ? 1.0f : 0.0f);
+        E.sh_dir[c.nlt * Q + slot] = make_float4(ewi.x, ewi.y, ewi.z, __int_as_float(0x7f800000));
+        E.sh_c[c.nlt * Q + slot] = make_float4(cc.x, cc.y, cc.z, valid ? 1.0f : 0.0f);
         sh_any |= valid;
       }
       if (E.records) {
@@ -671,7 +689,7 @@ __global__ void __launch_bounds__(EXT_BLOCK) k_shadow(KCtx c, int b) {
                                       nullptr);
       if (hf < 0) {
         L += xyz(sc);
-        vis |= (k < c.nl) ? (1 << k) : ENV_VIS;
+        vis |= (k < c.nlt) ? (1 << k) : ENV_VIS;
       }
     }
     float4 r = E.rad[slot];
@@ -743,7 +761,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_adjoint(KCtx c, long long j0, int
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   float* dV = c.args->dV;
   float* dF = c.args->dF;
-  int nbv = 0;
+  int nbv = 0, vi = 0;
   float3 g = mk3(0, 0, 0);
   if (i < n) {
     long long job = j0 + i;
@@ -753,6 +771,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_adjoint(KCtx c, long long j0, int
       long long local = job - sg.base;
       if (sg.kind == 0 && local < sg.count) {
         DevView v = c.views[sg.view];
+        vi = sg.view;
         long long pixel = local / v.spp;
         const float* gp = c.args->dLdI + 3 * (v.pix_off + pixel);
         float inv = 1.0f / (float)v.spp;
@@ -806,9 +825,10 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_adjoint(KCtx c, long long j0, int
       float3 gC = mul(g, T[b]);
       float3 C = mk3(0, 0, 0);
       int flags = __float_as_int(r2.w);
-      for (int j = 0; j < c.nl; ++j) {
+      for (int j = 0; j < c.nlt; ++j) {
         if (!(flags & (1 << j))) continue;
-        float4 lp = __ldg(&c.lights[2 * j]), li = __ldg(&c.lights[2 * j + 1]);
+        float4 lp, li;
+        point_light(c, vi, j, lp, li);
         float3 l = xyz(lp) - p;
         float r = len3(l);
         float3 wi = l * (1.0f / r);
@@ -1056,7 +1076,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_sec_gen(KCtx c, long long j0, int
       E.sj[cap + q] = make_float4(ss.w.x, ss.w.y, ss.w.z, ss.weight);
       E.sj[2 * cap + q] = make_float4(ss.mh.x, ss.mh.y, ss.mh.z, ss.tau);
       E.sj[3 * cap + q] = make_float4(gC.x, gC.y, gC.z, __int_as_float(ss.e));
-      E.sje[q] = make_int4(ct.x, ct.y, i, b);
+      E.sje[q] = make_int4(ct.x, ct.y, i, b | (ct.w & ~15));
       ++made;
     }
     T = Tn;
@@ -1090,7 +1110,7 @@ __global__ void k_sec_raygen(KCtx c, int pass) {
     if (i < total && job < J) {
       float4 a = E.sj[job], w = E.sj[cap + job], m = E.sj[2 * cap + job];
       int4 je = E.sje[job];
-      int slot = je.z, b = je.w, f = __float_as_int(a.w);
+      int slot = je.z, b = je.w & 15, f = __float_as_int(a.w);
       float3 wo = -xyz(E.r1[b * Q + slot]);
       float3 nn = vertex_normal(c, f, wo);
       float3 ws = norm3(xyz(w) + xyz(m) * ((sidx & 32) ? SEC_EPS : -SEC_EPS));
@@ -1101,7 +1121,7 @@ __global__ void k_sec_raygen(KCtx c, int pass) {
         E.d[i] = make_float4(ws.x, ws.y, ws.z, 0.0f);
         E.thr[i] = make_float4(thr.x, thr.y, thr.z, 0.0f);
         E.origin[i] = f;
-        E.ctr[i] = make_int4(je.x, je.y, 16 + b, b + 1);
+        E.ctr[i] = make_int4(je.x, je.y, 16 + b, (b + 1) | (je.w & ~15));
         E.brange[i] = make_int2(-1, -1);
         ok = true;
       }
@@ -1144,7 +1164,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_sec_resolve(KCtx c, int pass) {
         key = e;
         va = ev.x;
         vb = ev.y;
-        E.pinj[je.w * Q + je.z] = make_float4(-cv * mh.x, -cv * mh.y, -cv * mh.z, 0.0f);
+        E.pinj[(je.w & 15) * Q + je.z] = make_float4(-cv * mh.x, -cv * mh.y, -cv * mh.z, 0.0f);
       }
     }
     bool leader;

@@ -274,6 +274,21 @@ def fibonacci_views(n, widths, heights, spps, radius=3.0, fov=45.0):
     return vs
 
 
+def with_view_lights(views, intensity=(4.0, 4.0, 4.0), offset=0.35):
+    """Copies of ``views`` lit as the paper's captures (Sec. 4): one point light at the camera and one
+    displaced from it along the camera's right (tangent) direction by ``offset``."""
+    out = []
+    for v in views:
+        eye = np.asarray(v.eye, np.float64)
+        fwd = np.asarray(v.target, np.float64) - eye
+        right = np.cross(fwd, np.asarray(v.up, np.float64))
+        right /= np.linalg.norm(right)
+        I = tuple(float(x) for x in intensity)
+        lights = ((tuple(float(x) for x in eye), I), (tuple(float(x) for x in eye + offset * right), I))
+        out.append(dataclasses.replace(v, lights=lights))
+    return out
+
+
 def _f32(a):
     return np.ascontiguousarray(a, dtype=np.float32)
 

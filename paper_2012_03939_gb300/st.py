@@ -44,9 +44,13 @@ class EnvMap(C.Structure):
     _fields_ = [("width", C.c_int), ("height", C.c_int), ("rgb", C.c_void_p)]
 
 
+MAX_VIEW_LIGHTS = 2
+
+
 class View(C.Structure):
     _fields_ = [("eye", C.c_float * 3), ("target", C.c_float * 3), ("up", C.c_float * 3), ("fov_y_deg", C.c_float),
-                ("width", C.c_int), ("height", C.c_int), ("spp", C.c_int), ("pixel_offset", C.c_longlong)]
+                ("width", C.c_int), ("height", C.c_int), ("spp", C.c_int), ("pixel_offset", C.c_longlong),
+                ("n_lights", C.c_int), ("lights", PointLight * MAX_VIEW_LIGHTS)]
 
 
 class SceneDesc(C.Structure):
@@ -119,8 +123,13 @@ def make_views(views, default_spp=0):
         if isinstance(v, View):
             arr[i] = v
         else:
+            lights = list(getattr(v, "lights", ()) or ())
+            if len(lights) > MAX_VIEW_LIGHTS:
+                raise ValueError("at most %d lights per view" % MAX_VIEW_LIGHTS)
+            pl = (PointLight * MAX_VIEW_LIGHTS)(*[PointLight((C.c_float * 3)(*l[0]), (C.c_float * 3)(*l[1]))
+                                                  for l in lights])
             arr[i] = View((C.c_float * 3)(*v.eye), (C.c_float * 3)(*v.target), (C.c_float * 3)(*v.up),
-                          v.fov_y_deg, v.width, v.height, v.spp, v.pixel_offset)
+                          v.fov_y_deg, v.width, v.height, v.spp, v.pixel_offset, len(lights), pl)
     return arr
 
 

@@ -49,9 +49,24 @@ def test_last_error_is_callable_without_gpu():
     assert b"mesh" in L.st_last_error()
 
 
-def test_structure_sizes_match_c_layout():
+def test_structure_sizes_match_c_layout(tmp_path):
+    # every ctypes structure of the binding against the C compiler's layout of include/st.h
+    import subprocess
     from paper_2012_03939_gb300 import st
-    # st_view: 10 floats, 3 ints, 4 bytes padding, one long long
-    assert ctypes.sizeof(st.View) == 10 * 4 + 3 * 4 + 4 + 8
-    assert ctypes.sizeof(st.RenderOpts) == 9 * 4
-    assert ctypes.sizeof(st.PointLight) == 24
+    pairs = {"st_view": st.View, "st_scene_desc": st.SceneDesc, "st_render_opts": st.RenderOpts,
+             "st_stats": st.Stats, "st_point_light": st.PointLight, "st_envmap": st.EnvMap}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "st.h"', "int main(void) {"]
+    for cname, py in pairs.items():
+        lines.append('  printf("%s %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f, _ in py._fields_:
+            lines.append('  printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (cname, f, cname, f))
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = dict(l.split() for l in subprocess.check_output([str(exe)]).decode().splitlines())
+    for cname, py in pairs.items():
+        assert int(got[cname]) == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert int(got["%s.%s" % (cname, f)]) == getattr(py, f).offset, (cname, f)
