@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--views", type=int, default=0, help="profiling: keep only the first N views")
     ap.add_argument("--chunk", type=int, default=0, help="paths in flight per wavefront chunk (0 = library default)")
+    ap.add_argument("--bvh", default="ploc", choices=["ploc", "lbvh"], help="tree builder")
     ap.add_argument("--profile", action="store_true",
                     help="profiling driver: warm-up steps then one batched fwd+adjoint step, no JSON")
     return ap.parse_args()
@@ -229,7 +230,10 @@ def run_ours(args):
     if args.views:
         sc = sc.subset_views(range(args.views))
     B = sc.max_bounces
-    scene = st.Scene.from_scene(sc)
+    t_build = time.perf_counter()
+    scene = st.Scene.from_scene(sc, bvh_builder=args.bvh)
+    torch.cuda.synchronize()
+    t_build = time.perf_counter() - t_build
     views = sc.views
     N = sc.n_pixels
     seed = 20240 + rank
@@ -449,7 +453,8 @@ def run_ours(args):
                           "paths_per_step": sf["paths"] + sb["paths"], "edge_samples_per_step": sb["edge_samples"],
                           "l2": "flushed between timed steps (256 MiB write)", "launch": "batched persistent + CUDA graph",
                           "autotuned": None if tuned is None else {k: tuned[k] for k in ("chunk_paths", "persist_blocks")},
-                          "edge_term": bool(edge_on),
+                          "edge_term": bool(edge_on), "bvh": args.bvh,
+                          "scene_create_ms": round(1000 * t_build, 1),
                           "parallelism": "replicas" if world > 1 else "single GPU"},
                "batched_vs_per_view": round(value / value_pv, 3),
                "per_view": {"value": round(value_pv, 3), "ms_per_step": round(ms_pv / pv_steps, 3),

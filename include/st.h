@@ -57,6 +57,8 @@ typedef enum {
 #define ST_BRDF_BECKMANN 1
 #define ST_EDGE_SILHOUETTE 0  /* edges whose two faces face opposite ways, and boundary edges */
 #define ST_EDGE_ALL 1         /* every mesh edge (also the shading discontinuities of flat faces) */
+#define ST_BVH_PLOC 0   /* tree by locally-ordered clustering (Meister and Bittner 2018): lower traversal cost */
+#define ST_BVH_LBVH 1   /* Karras radix tree over the Morton order: faster build */
 #define ST_EDGE_TERM_PRIMARY 1    /* edge_term bit: primary visibility (image-space edges) */
 #define ST_EDGE_TERM_SECONDARY 2  /* edge_term bit: secondary visibility (edges seen from path vertices) */
 #define ST_MODE_BATCHED 0     /* all views in one job space, persistent kernels, optional CUDA graph */
@@ -111,6 +113,7 @@ typedef struct {
   const st_point_light* point_lights; /* host array */
   const st_envmap* env;      /* NULL if no environment */
   int color_res;             /* mesh-colors resolution r, 0..64 */
+  int bvh_builder;           /* ST_BVH_PLOC (0, default) or ST_BVH_LBVH; st_scene_create and st_rebuild use it */
 } st_scene_desc;
 
 typedef struct {
@@ -203,8 +206,9 @@ st_status st_debug_bvh(st_scene* scene, float* nodes, int* leaf_faces);
  * when they need one (an allocator at its budget, a framework that forbids
  * allocation on its hot path, an embedding that owns every buffer). The paper
  * has no counterpart: this is a library-side convenience. It runs the same
- * build as st_scene_create (Morton order, radix sort, Karras hierarchy,
- * bottom-up boxes) and writes the same node and leaf layout, but takes all
+ * build as st_scene_create with bvh_builder = ST_BVH_LBVH (Morton order, radix
+ * sort, Karras hierarchy, bottom-up boxes) and writes the same node and leaf
+ * layout, but takes all
  * scratch from one fixed file-scope device array (about 1.8 MiB, held by every
  * device that loads the library until the process exits) and calls no
  * allocator. Inputs: vertices device float [V][3], faces device int [F][3].

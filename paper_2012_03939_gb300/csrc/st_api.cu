@@ -393,7 +393,7 @@ st_status run_chunk(st_scene* s, const Plan& p, const KCtx& c, long long j0, int
   st_status r = bounces(c, p.B);
   if (r != ST_OK) return r;
   if (p.kind == 0) {
-    k_resolve<<<(n + 255) / 256, 256, 0, st>>>(c, j0, n);
+    k_resolve<<<(n + RESOLVE_BLOCK - 1) / RESOLVE_BLOCK, RESOLVE_BLOCK, 0, st>>>(c, j0, n);
     s->launches++;
   } else {
     int ga = (n + ADJ_BLOCK - 1) / ADJ_BLOCK;
@@ -692,6 +692,7 @@ st_status st_scene_create(const st_scene_desc* d, void* stream, st_scene** out) 
     return fail(ST_ERR_INVALID_ARG, "mesh description incomplete");
   if (d->n_faces > (1 << 28)) return fail(ST_ERR_UNSUPPORTED, "too many faces");
   if (d->brdf != ST_BRDF_GGX && d->brdf != ST_BRDF_BECKMANN) return fail(ST_ERR_INVALID_ARG, "unknown brdf");
+  if (d->bvh_builder != ST_BVH_PLOC && d->bvh_builder != ST_BVH_LBVH) return fail(ST_ERR_INVALID_ARG, "unknown bvh_builder");
   if (d->color_res < 0 || d->color_res > 64) return fail(ST_ERR_UNSUPPORTED, "mesh-colors resolution must be in [0, 64]");
   if ((long long)d->n_faces * (d->color_res + 1) * (d->color_res + 2) / 2 > (1LL << 30))
     return fail(ST_ERR_UNSUPPORTED, "too many mesh-colors texels");
@@ -714,6 +715,7 @@ st_status st_scene_create(const st_scene_desc* d, void* stream, st_scene** out) 
   s->brdf = d->brdf;
   s->nl = d->n_point_lights;
   s->res = d->color_res;
+  s->builder = d->bvh_builder;
   s->ntex = (s->res + 1) * (s->res + 2) / 2;
   // host copy of the faces: validation and edge list
   std::vector<int> hf(3 * (size_t)s->nf);
@@ -784,7 +786,7 @@ st_status st_scene_create(const st_scene_desc* d, void* stream, st_scene** out) 
     s->env.pdf_scale = (float)((double)d->env->width * d->env->height / (2.0 * 3.14159265358979323846 * 3.14159265358979323846));
   }
   chk(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
-  if (e == cudaSuccess) e = bvh_build(s, st);
+  if (e == cudaSuccess) e = s->builder == ST_BVH_LBVH ? bvh_build(s, st) : bvh_build_ploc(s, st);
   if (e == cudaSuccess) e = bvh_collapse(s, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) { destroy(s); return cuda_fail(e, "scene create"); }
@@ -801,7 +803,7 @@ static st_status update_vertices(st_scene* s, const float* v, void* stream, bool
   if (!s || !v) return fail(ST_ERR_INVALID_ARG, "NULL argument");
   cudaStream_t st = (cudaStream_t)stream;
   ST_CUDA(cudaMemcpyAsync(s->verts, v, 3 * sizeof(float) * s->nv, cudaMemcpyDeviceToDevice, st));
-  cudaError_t e = rebuild ? bvh_build(s, st) : bvh_refit(s, st);
+  cudaError_t e = !rebuild ? bvh_refit(s, st) : s->builder == ST_BVH_LBVH ? bvh_build(s, st) : bvh_build_ploc(s, st);
   if (e == cudaSuccess && rebuild) e = bvh_collapse(s, st);
   if (e != cudaSuccess) return cuda_fail(e, rebuild ? "rebuild" : "refit");
   return ST_OK;

@@ -1,9 +1,11 @@
 // LBVH construction and refit.
 //
 // Build: centroid bounds -> 30-bit Morton code per triangle centroid -> stable
-// LSD radix sort of (code, face id) -> Karras' parallel hierarchy ("Maximizing
-// Parallelism in the Construction of BVHs, Octrees, and k-d Trees", HPG 2012),
-// ties between equal codes broken by the leaf index -> leaf triangle records in
+// LSD radix sort of (code, face id) -> a hierarchy over the leaves in that
+// order: Karras' parallel radix tree ("Maximizing Parallelism in the
+// Construction of BVHs, Octrees, and k-d Trees", HPG 2012; ties between equal
+// codes broken by the leaf index), or PLOC clustering (below: trees of lower
+// surface-area cost for a few more milliseconds) -> leaf triangle records in
 // Morton order -> boxes bottom-up, the second thread to reach a node merging
 // its two children. Refit reuses the order and the hierarchy: new vertex
 // positions only rewrite the leaf records and the boxes.
@@ -200,7 +202,7 @@ __global__ void k_boxes(const float* V, const int* F, const int* ids, int n, flo
   int child = ~i;
   int node = parent[(n - 1) + i];
   for (int depth = 0; node >= 0; ++depth) {
-    if (depth > 128) { atomicOr(err, 2); return; }  // deeper than any 30-bit-key tree: malformed
+    if (depth > 256) { atomicOr(err, 2); return; }  // deeper than any tree built here: malformed
     float4* np = nodes + 4 * node;
     int cl = __float_as_int(np[3].x);
     if (cl == child) {
@@ -231,7 +233,158 @@ cudaError_t boxes(st_scene* s, cudaStream_t stream) {
 
 }  // namespace
 
-cudaError_t bvh_build(st_scene* s, cudaStream_t stream) {
+// ---- PLOC: Meister and Bittner, "Parallel Locally-Ordered Clustering for
+// Bounding Volume Hierarchy Construction" (IEEE TVCG 2018). The leaves in
+// Morton order are the initial clusters; every round each cluster finds, among
+// the PLOC_R clusters on either side of it in the current order, the one whose
+// merged box has the least surface area; mutual nearest neighbours merge into a
+// new internal node that takes the lower position, and the array is compacted
+// in order. Ties compare (area, lower index, higher index), a total order on
+// pairs, so the closest pair of a round is always mutual and every round
+// merges. Nodes are numbered downward from n - 2, so the last merge is the
+// root, node 0; the result has the Karras layout (child links, parent array)
+// that the bottom-up boxes, the refit and the 4-wide collapse read.
+constexpr int PLOC_R = 16;
+constexpr int PLOC_BLOCK = 256;
+constexpr int SCAN2_BLOCK = 1024;
+
+__global__ void k_ploc_init(const float* V, const int* F, const int* ids, int n, int* cid, float4* lo, float4* hi) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int f = ids[i];
+  float3 p0 = mk3(V[3 * F[3 * f]], V[3 * F[3 * f] + 1], V[3 * F[3 * f] + 2]);
+  float3 p1 = mk3(V[3 * F[3 * f + 1]], V[3 * F[3 * f + 1] + 1], V[3 * F[3 * f + 1] + 2]);
+  float3 p2 = mk3(V[3 * F[3 * f + 2]], V[3 * F[3 * f + 2] + 1], V[3 * F[3 * f + 2] + 2]);
+  lo[i] = make_float4(fminf(fminf(p0.x, p1.x), p2.x), fminf(fminf(p0.y, p1.y), p2.y), fminf(fminf(p0.z, p1.z), p2.z), 0.0f);
+  hi[i] = make_float4(fmaxf(fmaxf(p0.x, p1.x), p2.x), fmaxf(fmaxf(p0.y, p1.y), p2.y), fmaxf(fmaxf(p0.z, p1.z), p2.z), 0.0f);
+  cid[i] = ~i;
+}
+
+__device__ __forceinline__ float merged_area(float4 al, float4 ah, float4 bl, float4 bh) {
+  float dx = fmaxf(ah.x, bh.x) - fminf(al.x, bl.x);
+  float dy = fmaxf(ah.y, bh.y) - fminf(al.y, bl.y);
+  float dz = fmaxf(ah.z, bh.z) - fminf(al.z, bl.z);
+  return dx * dy + dy * dz + dz * dx;
+}
+
+__global__ void __launch_bounds__(PLOC_BLOCK) k_ploc_nn(const float4* lo, const float4* hi, int c, int* nn) {
+  __shared__ float4 slo[PLOC_BLOCK + 2 * PLOC_R], shi[PLOC_BLOCK + 2 * PLOC_R];
+  const int b0 = blockIdx.x * PLOC_BLOCK;
+  for (int k = threadIdx.x; k < PLOC_BLOCK + 2 * PLOC_R; k += PLOC_BLOCK) {
+    int g = b0 - PLOC_R + k;
+    if (g >= 0 && g < c) {
+      slo[k] = lo[g];
+      shi[k] = hi[g];
+    }
+  }
+  __syncthreads();
+  int i = b0 + threadIdx.x;
+  if (i >= c) return;
+  float4 al = slo[threadIdx.x + PLOC_R], ah = shi[threadIdx.x + PLOC_R];
+  float best = __int_as_float(0x7f800000);
+  int bj = -1;
+  // ascending j with a strict test keeps the least (area, lower index, higher index)
+  for (int d = -PLOC_R; d <= PLOC_R; ++d) {
+    int j = i + d;
+    if (d == 0 || j < 0 || j >= c) continue;
+    float a = merged_area(al, ah, slo[threadIdx.x + PLOC_R + d], shi[threadIdx.x + PLOC_R + d]);
+    if (a < best) {
+      best = a;
+      bj = j;
+    }
+  }
+  nn[i] = bj;
+}
+
+// (merges, survivors) flags of cluster i: i merges (as the lower of a mutual
+// pair) or survives alone; the higher of a mutual pair disappears.
+__device__ __forceinline__ int2 ploc_flags(const int* nn, int i) {
+  int j = nn[i];
+  bool mutual = j >= 0 && nn[j] == i;
+  return make_int2(mutual && i < j ? 1 : 0, mutual && j < i ? 0 : 1);
+}
+
+__device__ __forceinline__ int2 add2(int2 a, int2 b) { return make_int2(a.x + b.x, a.y + b.y); }
+
+__device__ __forceinline__ int2 block_scan2(int2 v, int2* sh, int2& total) {
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int2 x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    int2 y = make_int2(__shfl_up_sync(0xffffffffu, x.x, o), __shfl_up_sync(0xffffffffu, x.y, o));
+    if (lane >= o) x = add2(x, y);
+  }
+  if (lane == 31) sh[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int nw = blockDim.x >> 5;
+    int2 t = lane < nw ? sh[lane] : make_int2(0, 0);
+    for (int o = 1; o < 32; o <<= 1) {
+      int2 y = make_int2(__shfl_up_sync(0xffffffffu, t.x, o), __shfl_up_sync(0xffffffffu, t.y, o));
+      if (lane >= o) t = add2(t, y);
+    }
+    if (lane < nw) sh[lane] = t;
+  }
+  __syncthreads();
+  int2 before = w > 0 ? sh[w - 1] : make_int2(0, 0);
+  total = sh[(blockDim.x >> 5) - 1];
+  return make_int2(before.x + x.x - v.x, before.y + x.y - v.y);   // exclusive
+}
+
+__global__ void __launch_bounds__(SCAN2_BLOCK) k_ploc_scan(const int* nn, int c, int2* scan, int2* part) {
+  __shared__ int2 sh[32];
+  int i = blockIdx.x * SCAN2_BLOCK + threadIdx.x;
+  int2 v = i < c ? ploc_flags(nn, i) : make_int2(0, 0);
+  int2 tot;
+  int2 ex = block_scan2(v, sh, tot);
+  if (i < c) scan[i] = ex;
+  if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+// exclusive scan of the block totals, in place; part[nb] = the grand total
+__global__ void __launch_bounds__(SCAN2_BLOCK) k_ploc_parts(int2* part, int nb) {
+  __shared__ int2 sh[32];
+  int2 carry = make_int2(0, 0);
+  for (int b = 0; b < nb; b += SCAN2_BLOCK) {
+    int i = b + threadIdx.x;
+    int2 v = i < nb ? part[i] : make_int2(0, 0);
+    int2 tot;
+    int2 ex = block_scan2(v, sh, tot);
+    __syncthreads();
+    if (i < nb) part[i] = add2(ex, carry);
+    carry = add2(carry, tot);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[nb] = carry;
+}
+
+__global__ void __launch_bounds__(SCAN2_BLOCK) k_ploc_merge(const int* nn, int c, const int2* scan, const int2* part,
+                                                           int next, int n, const int* cid, const float4* lo,
+                                                           const float4* hi, int* cid2, float4* lo2, float4* hi2,
+                                                           float4* nodes, int* parent) {
+  int i = blockIdx.x * SCAN2_BLOCK + threadIdx.x;
+  if (i >= c) return;
+  int2 f = ploc_flags(nn, i);
+  int2 pos = add2(scan[i], part[blockIdx.x]);
+  if (f.x) {
+    int j = nn[i];
+    int k = next - 1 - pos.x;
+    int a = cid[i], b = cid[j];
+    nodes[4 * k + 3] = make_float4(__int_as_float(a), __int_as_float(b), 0.0f, 0.0f);
+    if (a >= 0) parent[a] = k; else parent[(n - 1) + ~a] = k;
+    if (b >= 0) parent[b] = k; else parent[(n - 1) + ~b] = k;
+    float4 al = lo[i], ah = hi[i], bl = lo[j], bh = hi[j];
+    cid2[pos.y] = k;
+    lo2[pos.y] = make_float4(fminf(al.x, bl.x), fminf(al.y, bl.y), fminf(al.z, bl.z), 0.0f);
+    hi2[pos.y] = make_float4(fmaxf(ah.x, bh.x), fmaxf(ah.y, bh.y), fmaxf(ah.z, bh.z), 0.0f);
+  } else if (f.y) {
+    cid2[pos.y] = cid[i];
+    lo2[pos.y] = lo[i];
+    hi2[pos.y] = hi[i];
+  }
+}
+
+namespace {
+cudaError_t morton_order(st_scene* s, cudaStream_t stream) {
   int n = s->nf;
   k_init_bounds<<<1, 32, 0, stream>>>(s->bounds);
   int g = min((n + 255) / 256, 4 * max(s->sm_count, 1));
@@ -248,8 +401,62 @@ cudaError_t bvh_build(st_scene* s, cudaStream_t stream) {
     std::swap(ia, ib);
   }
   // four passes: the sorted data is back in the primary buffers
+  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t bvh_build(st_scene* s, cudaStream_t stream) {
+  int n = s->nf;
+  cudaError_t e = morton_order(s, stream);
+  if (e != cudaSuccess) return e;
   if (n > 1) k_hierarchy<<<(n - 1 + 255) / 256, 256, 0, stream>>>(s->keys, n, s->nodes, s->parent);
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return boxes(s, stream);
+}
+
+cudaError_t bvh_build_ploc(st_scene* s, cudaStream_t stream) {
+  int n = s->nf;
+  cudaError_t e = morton_order(s, stream);
+  if (e != cudaSuccess || n < 2) return e != cudaSuccess ? e : boxes(s, stream);
+  // scratch for the rounds: two cluster arrays (box, id), scans, neighbours
+  int nb = (n + SCAN2_BLOCK - 1) / SCAN2_BLOCK;
+  size_t bytes = 4 * (size_t)n * sizeof(float4) + (size_t)n * sizeof(int2) + (size_t)(nb + 1) * sizeof(int2) +
+                 3 * (size_t)n * sizeof(int);
+  char* buf = nullptr;
+  e = cudaMalloc((void**)&buf, bytes);
+  if (e != cudaSuccess) return e;
+  float4* lo[2] = {(float4*)buf, (float4*)buf + n};
+  float4* hi[2] = {(float4*)buf + 2 * (size_t)n, (float4*)buf + 3 * (size_t)n};
+  int2* scan = (int2*)((float4*)buf + 4 * (size_t)n);
+  int2* part = scan + n;
+  int* cid[2] = {(int*)(part + nb + 1), (int*)(part + nb + 1) + n};
+  int* nn = cid[1] + n;
+  k_ploc_init<<<(n + 255) / 256, 256, 0, stream>>>(s->verts, s->faces, s->ids, n, cid[0], lo[0], hi[0]);
+  int c = n, next = n - 1, cur = 0;
+  int2 tot = make_int2(0, 0);
+  for (int round = 0; c > 1 && e == cudaSuccess; ++round) {
+    if (round > 4 * n) { e = cudaErrorIllegalState; break; }
+    int g = (c + PLOC_BLOCK - 1) / PLOC_BLOCK, gs = (c + SCAN2_BLOCK - 1) / SCAN2_BLOCK;
+    k_ploc_nn<<<g, PLOC_BLOCK, 0, stream>>>(lo[cur], hi[cur], c, nn);
+    k_ploc_scan<<<gs, SCAN2_BLOCK, 0, stream>>>(nn, c, scan, part);
+    k_ploc_parts<<<1, SCAN2_BLOCK, 0, stream>>>(part, gs);
+    k_ploc_merge<<<gs, SCAN2_BLOCK, 0, stream>>>(nn, c, scan, part, next, n, cid[cur], lo[cur], hi[cur], cid[cur ^ 1],
+                                                 lo[cur ^ 1], hi[cur ^ 1], s->nodes, s->parent);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&tot, part + gs, sizeof(int2), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) break;
+    // a round without a merge means non-finite boxes
+    if (tot.x <= 0 || tot.y != c - tot.x) { e = cudaErrorIllegalState; break; }
+    next -= tot.x;
+    c = tot.y;
+    cur ^= 1;
+  }
+  if (e == cudaSuccess && next != 0) e = cudaErrorIllegalState;
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->parent, 0xff, sizeof(int), stream);   // the root has no parent
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  cudaFree(buf);
   if (e != cudaSuccess) return e;
   return boxes(s, stream);
 }

@@ -71,6 +71,7 @@ struct st_scene {
   int device = 0;
   int nv = 0, nf = 0, brdf = 0, nl = 0;
   int res = 0, ntex = 1;         // mesh-colors resolution and texels per face
+  int builder = 0;               // ST_BVH_PLOC or ST_BVH_LBVH
   float* verts = nullptr;        // [V*3]
   int* faces = nullptr;          // [F*3]
   float4* params = nullptr;      // [F*ntex*2] per texel: (kd_r, kd_g, kd_b, ks), (roughness, 0, 0, 0)
@@ -137,7 +138,8 @@ struct st_scene {
 };
 
 namespace st {
-cudaError_t bvh_build(st_scene* s, cudaStream_t stream);    // Morton order + hierarchy + boxes
+cudaError_t bvh_build(st_scene* s, cudaStream_t stream);    // Morton order + radix-tree hierarchy + boxes
+cudaError_t bvh_build_ploc(st_scene* s, cudaStream_t stream);  // Morton order + PLOC clustering + boxes (synchronises)
 cudaError_t bvh_refit(st_scene* s, cudaStream_t stream);    // leaf records + boxes, same order (+ 4-wide boxes)
 cudaError_t bvh_collapse(st_scene* s, cudaStream_t stream); // 4-wide tree from the binary one (synchronises)
 cudaError_t trace_closest(st_scene* s, const float* rays, int n, int exclude, int* out_tri, float* out_t,

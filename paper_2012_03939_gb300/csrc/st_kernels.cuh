@@ -705,9 +705,16 @@ __global__ void __launch_bounds__(EXT_BLOCK) k_shadow(KCtx c, int b) {
 }
 
 // the pixel's double accumulator takes its samples in sample order, so the
-// result does not depend on where chunk boundaries fall
-__global__ void k_resolve(KCtx c, long long j0, int n) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+// result does not depend on where chunk boundaries fall. The block stages its
+// slots' radiance in shared memory with coalesced loads; the thread holding a
+// pixel's first sample then sums that pixel's run in order.
+constexpr int RESOLVE_BLOCK = 256;
+__global__ void __launch_bounds__(RESOLVE_BLOCK) k_resolve(KCtx c, long long j0, int n) {
+  __shared__ float4 srad[RESOLVE_BLOCK];
+  const int i0 = blockIdx.x * RESOLVE_BLOCK;
+  const int i = i0 + threadIdx.x;
+  if (i < n) srad[threadIdx.x] = c.e.rad[i];
+  __syncthreads();
   if (i >= n) return;
   long long job = j0 + i;
   int si = find_seg(c.segs, c.n_segs, job);
@@ -722,7 +729,7 @@ __global__ void k_resolve(KCtx c, long long j0, int n) {
   double* a = c.acc + 3 * (v.bin_base + pixel);
   double ax = a[0], ay = a[1], az = a[2];
   for (int k = i; s < v.spp && k < n; ++k, ++s) {
-    float4 r = c.e.rad[k];
+    float4 r = k < i0 + RESOLVE_BLOCK ? srad[k - i0] : c.e.rad[k];
     ax += (double)r.x; ay += (double)r.y; az += (double)r.z;
   }
   a[0] = ax; a[1] = ay; a[2] = az;

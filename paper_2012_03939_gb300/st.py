@@ -24,6 +24,7 @@ STATUS = {0: "ST_OK", 1: "ST_ERR_INVALID_ARG", 2: "ST_ERR_OOM", 3: "ST_ERR_CUDA"
 MODE_BATCHED, MODE_PER_VIEW = 0, 1
 EDGE_SILHOUETTE, EDGE_ALL = 0, 1
 EDGE_TERM_PRIMARY, EDGE_TERM_SECONDARY = 1, 2
+BVH_PLOC, BVH_LBVH = 0, 1
 
 EXPORTED = ["st_scene_create", "st_scene_destroy", "st_refit", "st_rebuild", "st_set_face_params", "st_render",
             "st_render_backward", "st_trace_closest", "st_get_stats", "st_debug_bvh", "st_build_bvh_noalloc",
@@ -56,7 +57,7 @@ class View(C.Structure):
 class SceneDesc(C.Structure):
     _fields_ = [("n_vertices", C.c_int), ("n_faces", C.c_int), ("vertices", C.c_void_p), ("faces", C.c_void_p),
                 ("face_params", C.c_void_p), ("brdf", C.c_int), ("n_point_lights", C.c_int),
-                ("point_lights", C.c_void_p), ("env", C.c_void_p), ("color_res", C.c_int)]
+                ("point_lights", C.c_void_p), ("env", C.c_void_p), ("color_res", C.c_int), ("bvh_builder", C.c_int)]
 
 
 class RenderOpts(C.Structure):
@@ -153,7 +154,7 @@ class Scene:
 
     def __init__(self, vertices: torch.Tensor, faces: torch.Tensor, face_params: torch.Tensor, brdf: str = "ggx",
                  light_pos=None, light_intensity=None, env: Optional[np.ndarray] = None, stream=None,
-                 color_res: int = 0):
+                 color_res: int = 0, bvh_builder: str = "ploc"):
         dev = torch.device("cuda", torch.cuda.current_device())
         self.vertices = vertices.detach().to(dev, torch.float32).contiguous()
         self.faces = faces.detach().to(dev, torch.int32).contiguous()
@@ -173,16 +174,16 @@ class Scene:
         desc = SceneDesc(self.nv, self.nf, self.vertices.data_ptr(), self.faces.data_ptr(),
                          self.face_params.data_ptr(), {"ggx": 0, "beckmann": 1}[brdf], len(lp),
                          C.addressof(self._lights), None if self._env is None else C.addressof(self._env),
-                         int(color_res))
+                         int(color_res), {"ploc": BVH_PLOC, "lbvh": BVH_LBVH}[bvh_builder])
         h = C.c_void_p()
         _check(lib().st_scene_create(C.byref(desc), _stream(stream), C.byref(h)))
         self.handle = h
 
     @classmethod
-    def from_scene(cls, sc, vertices=None, device="cuda"):
+    def from_scene(cls, sc, vertices=None, device="cuda", **kw):
         V = torch.as_tensor(sc.vertices if vertices is None else vertices, dtype=torch.float32, device=device)
         return cls(V, torch.as_tensor(sc.faces, device=device), torch.as_tensor(sc.face_params, device=device),
-                   sc.brdf, sc.light_pos, sc.light_intensity, sc.env, color_res=getattr(sc, "color_res", 0))
+                   sc.brdf, sc.light_pos, sc.light_intensity, sc.env, color_res=getattr(sc, "color_res", 0), **kw)
 
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:

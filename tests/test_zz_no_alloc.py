@@ -5,8 +5,8 @@ memory when they need a BVH; its scratch lives in one fixed device array that
 every call shares. This checks, through the C ABI, that two calls in a row
 (different meshes, so the second starts from the first one's leftovers) each
 reproduce exactly the nodes, leaf order and leaf triangles of the allocating
-path, and that oversized or invalid meshes are refused. This file is named to
-be collected last.
+path with the same builder (the radix tree), and that oversized or invalid
+meshes are refused. This file is named to be collected last.
 """
 import ctypes
 
@@ -46,7 +46,7 @@ def _noalloc(st, V, F):
 
 
 def _reference(st, sc):
-    scene = st.Scene.from_scene(sc)
+    scene = st.Scene.from_scene(sc, bvh_builder="lbvh")
     nodes, leaf = scene.debug_bvh()
     scene.close()
     return nodes, leaf
