@@ -131,6 +131,36 @@ void build_edges(const std::vector<int>& F, int nf, std::vector<int2>& ev, std::
   }
 }
 
+// True when the faces form one connected surface (across shared edges) in
+// which every edge has exactly two faces that traverse it in opposite
+// directions: a closed, consistently wound mesh. Seen from outside its bounds,
+// such a surface is first hit on a face wound toward the eye (the outward side
+// when the signed volume is positive), so the other faces can be left out of
+// the primary-visibility bins.
+bool closed_single_surface(const std::vector<int>& F, int nf, const std::vector<int2>& ef) {
+  std::vector<unsigned long long> dir;
+  dir.reserve(3 * (size_t)nf);
+  for (int f = 0; f < nf; ++f)
+    for (int k = 0; k < 3; ++k)
+      dir.push_back(((unsigned long long)(unsigned)F[3 * f + k] << 32) | (unsigned)F[3 * f + (k + 1) % 3]);
+  std::sort(dir.begin(), dir.end());
+  for (size_t i = 0; i < dir.size(); ++i) {
+    if (i > 0 && dir[i] == dir[i - 1]) return false;                      // an edge traversed twice the same way
+    unsigned long long rev = (dir[i] << 32) | (dir[i] >> 32);
+    if (!std::binary_search(dir.begin(), dir.end(), rev)) return false;   // a boundary edge
+  }
+  std::vector<int> up(nf);
+  for (int f = 0; f < nf; ++f) up[f] = f;
+  auto root = [&](int x) { while (up[x] != x) { up[x] = up[up[x]]; x = up[x]; } return x; };
+  int comps = nf;
+  for (const int2& e : ef) {
+    if (e.y < 0) return false;
+    int a = root(e.x), b = root(e.y);
+    if (a != b) { up[a] = b; --comps; }
+  }
+  return comps == 1;
+}
+
 DevView make_view(const st_view& v, int spp) {
   double eye[3] = {v.eye[0], v.eye[1], v.eye[2]};
   double f[3] = {v.target[0] - eye[0], v.target[1] - eye[1], v.target[2] - eye[2]};
@@ -315,6 +345,7 @@ KCtx make_ctx(st_scene* s, const Plan& p) {
   c.bin_start = p.bins ? s->bin_start : nullptr;   // nullptr: every primary ray traverses the BVH
   c.bin_list = s->bin_list; c.bin_cur = s->bin_cur; c.bin_ok = s->bin_ok;
   c.bin_cap = s->bin_cap; c.bin_pixels = p.pixels;
+  c.cull = s->closed ? 1 : 0; c.mstat = s->mstat;
   c.acc = s->acc;
   c.views = s->d_views; c.segs = s->d_segs; c.n_segs = (int)p.segs.size();
   c.args = s->d_args; c.B = p.B; c.e = s->eng; c.e.records = p.kind == 1; c.err = s->d_err;
@@ -660,7 +691,7 @@ void destroy(st_scene* s) {
   dfree(s->lights); dfree(s->env_tex); dfree(s->env_alias); dfree(s->edge_v); dfree(s->edge_f);
   dfree(s->edge_flag); dfree(s->edge_cand); dfree(s->edge_ncand); dfree(s->d_views); dfree(s->d_segs);
   dfree(s->bin_start); dfree(s->bin_cur); dfree(s->bin_list); dfree(s->bin_ok); dfree(s->bin_part);
-  dfree(s->acc);
+  dfree(s->acc); dfree(s->mstat);
   if (s->bin_total_host) cudaFreeHost(s->bin_total_host);
   dfree(s->d_args); dfree(s->d_err);
   for (auto& e : s->ev) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
@@ -734,6 +765,7 @@ st_status st_scene_create(const st_scene_desc* d, void* stream, st_scene** out) 
   }
   std::vector<int2> ev, ef;
   build_edges(hf, s->nf, ev, ef);
+  s->closed = closed_single_surface(hf, s->nf, ef);
   s->n_edges = (int)ev.size();
   std::vector<float4> etex;
   std::vector<float2> etab;
@@ -757,6 +789,7 @@ st_status st_scene_create(const st_scene_desc* d, void* stream, st_scene** out) 
   chk(dalloc(&s->q4, 4 * (size_t)n)); chk(dalloc(&s->c4, 2));
   chk(dalloc(&s->lights, 2 * (size_t)std::max(s->nl, 1))); chk(dalloc(&s->edge_v, ev.size()));
   chk(dalloc(&s->edge_f, ef.size())); chk(dalloc(&s->d_args, 1)); chk(dalloc(&s->d_err, 1));
+  chk(dalloc(&s->mstat, 1));
   if (d->env) { chk(dalloc(&s->env_tex, etex.size())); chk(dalloc(&s->env_alias, etab.size())); }
   if (e != cudaSuccess) { destroy(s); cudaGetLastError(); return fail(ST_ERR_OOM, "scene buffers"); }
   std::vector<float4> hl(2 * (size_t)std::max(s->nl, 1), make_float4(0, 0, 0, 0));
@@ -788,6 +821,7 @@ st_status st_scene_create(const st_scene_desc* d, void* stream, st_scene** out) 
   chk(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
   if (e == cudaSuccess) e = s->builder == ST_BVH_LBVH ? bvh_build(s, st) : bvh_build_ploc(s, st);
   if (e == cudaSuccess) e = bvh_collapse(s, st);
+  if (e == cudaSuccess) e = mesh_stat(s, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) { destroy(s); return cuda_fail(e, "scene create"); }
   *out = s;
@@ -805,6 +839,7 @@ static st_status update_vertices(st_scene* s, const float* v, void* stream, bool
   ST_CUDA(cudaMemcpyAsync(s->verts, v, 3 * sizeof(float) * s->nv, cudaMemcpyDeviceToDevice, st));
   cudaError_t e = !rebuild ? bvh_refit(s, st) : s->builder == ST_BVH_LBVH ? bvh_build(s, st) : bvh_build_ploc(s, st);
   if (e == cudaSuccess && rebuild) e = bvh_collapse(s, st);
+  if (e == cudaSuccess) e = mesh_stat(s, st);
   if (e != cudaSuccess) return cuda_fail(e, rebuild ? "rebuild" : "refit");
   return ST_OK;
 }

@@ -9,6 +9,7 @@
 // Morton order -> boxes bottom-up, the second thread to reach a node merging
 // its two children. Refit reuses the order and the hierarchy: new vertex
 // positions only rewrite the leaf records and the boxes.
+#include <algorithm>
 #include <cstdio>
 
 #include "st_internal.h"
@@ -581,5 +582,60 @@ cudaError_t bvh_collapse(st_scene* s, cudaStream_t stream) {
 }
 
 int sort_blocks_for(int n) { return (n + RS_TILE - 1) / RS_TILE; }
+
+// ---- mesh statistics for back-face culling of the primary-visibility bins
+__global__ void k_mesh_stat_init(MeshStat* m) {
+  m->vol6 = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    m->lo[k] = 0x7fffffff;
+    m->hi[k] = (int)0x80000000;
+  }
+}
+
+__global__ void k_mesh_stat(const float* V, int nv, const int* F, int nf, MeshStat* m) {
+  __shared__ double sv[8];
+  double v = 0.0;
+  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += gridDim.x * blockDim.x) {
+    const int* fi = F + 3 * f;
+    double a[3], b[3], c[3];
+    for (int k = 0; k < 3; ++k) {
+      a[k] = V[3 * fi[0] + k]; b[k] = V[3 * fi[1] + k]; c[k] = V[3 * fi[2] + k];
+    }
+    v += a[0] * (b[1] * c[2] - b[2] * c[1]) - a[1] * (b[0] * c[2] - b[2] * c[0]) + a[2] * (b[0] * c[1] - b[1] * c[0]);
+  }
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sv[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sv[w];
+    atomicAdd(&m->vol6, t);
+  }
+  int lo[3] = {0x7fffffff, 0x7fffffff, 0x7fffffff}, hi[3] = {(int)0x80000000, (int)0x80000000, (int)0x80000000};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += gridDim.x * blockDim.x)
+    for (int k = 0; k < 3; ++k) {
+      int q = ordered(V[3 * i + k]);
+      lo[k] = min(lo[k], q);
+      hi[k] = max(hi[k], q);
+    }
+  for (int k = 0; k < 3; ++k) {
+    for (int o = 16; o > 0; o >>= 1) {
+      lo[k] = min(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+      hi[k] = max(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicMin(&m->lo[k], lo[k]);
+      atomicMax(&m->hi[k], hi[k]);
+    }
+  }
+}
+
+cudaError_t mesh_stat(st_scene* s, cudaStream_t stream) {
+  if (!s->mstat) return cudaSuccess;
+  k_mesh_stat_init<<<1, 1, 0, stream>>>(s->mstat);
+  int g = std::min((std::max(s->nf, s->nv) + 255) / 256, 4 * std::max(s->sm_count, 1));
+  k_mesh_stat<<<g, 256, 0, stream>>>(s->verts, s->nv, s->faces, s->nf, s->mstat);
+  return cudaGetLastError();
+}
 
 }  // namespace st

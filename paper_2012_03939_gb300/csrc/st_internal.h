@@ -11,6 +11,14 @@
 
 namespace st {
 
+// Mesh facts the primary-visibility bins use to drop back faces: six times the
+// signed volume (its sign tells outward from inward winding) and the vertex
+// bounds as order-preserving ints.
+struct MeshStat {
+  double vol6;
+  int lo[3], hi[3];
+};
+
 // Per-call arguments the kernels read from device memory, so a captured CUDA
 // graph can be replayed with a new seed, new output pointers and new camera
 // poses without recapture.
@@ -72,6 +80,8 @@ struct st_scene {
   int nv = 0, nf = 0, brdf = 0, nl = 0;
   int res = 0, ntex = 1;         // mesh-colors resolution and texels per face
   int builder = 0;               // ST_BVH_PLOC or ST_BVH_LBVH
+  bool closed = false;           // one surface; every edge has two faces that traverse it in opposite directions
+  st::MeshStat* mstat = nullptr; // signed volume and vertex bounds, recomputed on the device after each update
   float* verts = nullptr;        // [V*3]
   int* faces = nullptr;          // [F*3]
   float4* params = nullptr;      // [F*ntex*2] per texel: (kd_r, kd_g, kd_b, ks), (roughness, 0, 0, 0)
@@ -139,6 +149,7 @@ struct st_scene {
 
 namespace st {
 cudaError_t bvh_build(st_scene* s, cudaStream_t stream);    // Morton order + radix-tree hierarchy + boxes
+cudaError_t mesh_stat(st_scene* s, cudaStream_t stream);   // MeshStat of the current vertices (no sync)
 cudaError_t bvh_build_ploc(st_scene* s, cudaStream_t stream);  // Morton order + PLOC clustering + boxes (synchronises)
 cudaError_t bvh_refit(st_scene* s, cudaStream_t stream);    // leaf records + boxes, same order (+ 4-wide boxes)
 cudaError_t bvh_collapse(st_scene* s, cudaStream_t stream); // 4-wide tree from the binary one (synchronises)

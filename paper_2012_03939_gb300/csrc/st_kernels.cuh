@@ -46,6 +46,8 @@ struct KCtx {
   long long bin_cap;
   long long bin_pixels;
   double* acc;            // per-pixel sample sums (bin-space pixel index), forward calls
+  int cull;               // the mesh is one closed, consistently wound surface (see MeshStat)
+  const MeshStat* mstat;
   const DevView* views;
   const Seg* segs;
   int n_segs;
@@ -299,6 +301,28 @@ __device__ __forceinline__ bool pixel_may_overlap(const ScreenTri& et, int x, in
   return true;
 }
 
+__device__ __forceinline__ float from_ordered(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
+
+// A closed, consistently wound surface seen from an eye outside its bounds is
+// first hit on a face wound toward the eye (outward when the signed volume is
+// positive); faces clearly wound the other way (beyond a 1e-5 relative band, so
+// edge-on faces stay) can never be a primary ray's closest hit.
+__device__ __forceinline__ bool hidden_back_face(const KCtx& c, const DevView& v, float4 a, float4 b, float4 cc) {
+  if (!c.cull || !c.mstat) return false;
+  double vol = c.mstat->vol6;
+  if (vol == 0.0) return false;
+  float3 lo = mk3(from_ordered(c.mstat->lo[0]), from_ordered(c.mstat->lo[1]), from_ordered(c.mstat->lo[2]));
+  float3 hi = mk3(from_ordered(c.mstat->hi[0]), from_ordered(c.mstat->hi[1]), from_ordered(c.mstat->hi[2]));
+  float m = 1e-4f * fmaxf(hi.x - lo.x, fmaxf(hi.y - lo.y, hi.z - lo.z)) + 1e-6f;
+  bool outside = v.eye.x < lo.x - m || v.eye.x > hi.x + m || v.eye.y < lo.y - m || v.eye.y > hi.y + m ||
+                 v.eye.z < lo.z - m || v.eye.z > hi.z + m;
+  if (!outside) return false;
+  float3 n = cross3(xyz(b) - xyz(a), xyz(cc) - xyz(a));
+  float3 e = v.eye - xyz(a);
+  float f = dot3(n, e), tol = 1e-5f * len3(n) * len3(e);
+  return vol > 0.0 ? f < -tol : f > tol;
+}
+
 // fill = 0: count leaves per pixel; fill = 1: write them at start + cursor
 template <int FILL>
 __global__ void k_bin(KCtx c, int n_views, int* ok) {
@@ -308,8 +332,9 @@ __global__ void k_bin(KCtx c, int n_views, int* ok) {
   DevView v = c.views[vi];
   int x0, y0, x1, y1;
   ScreenTri et;
-  int r = leaf_screen_box(v, __ldg(&c.tri[3 * li]), __ldg(&c.tri[3 * li + 1]), __ldg(&c.tri[3 * li + 2]), x0, y0, x1,
-                          y1, et);
+  float4 ta = __ldg(&c.tri[3 * li]), tb = __ldg(&c.tri[3 * li + 1]), tc = __ldg(&c.tri[3 * li + 2]);
+  if (hidden_back_face(c, v, ta, tb, tc)) return;
+  int r = leaf_screen_box(v, ta, tb, tc, x0, y0, x1, y1, et);
   if (r < 0) { if (!FILL) atomicAnd(&ok[vi], 0); return; }
   if (r == 0) return;
   if (FILL && c.bin_start[c.bin_pixels] > c.bin_cap) return;   // overflow: every view uses the BVH
@@ -318,7 +343,11 @@ __global__ void k_bin(KCtx c, int n_views, int* ok) {
       if (!pixel_may_overlap(et, x, y)) continue;
       long long p = v.bin_base + (long long)y * v.W + x;
       int k = atomicAdd(&c.bin_cur[p], 1);
-      if (FILL) const_cast<int*>(c.bin_list)[c.bin_start[p] + k] = li;
+      if (FILL) {
+        long long at = (long long)c.bin_start[p] + k;
+        if (at < c.bin_start[p + 1] && at < c.bin_cap) const_cast<int*>(c.bin_list)[at] = li;
+        else atomicOr(c.err, ERR_INDEX);
+      }
     }
 }
 
@@ -519,8 +548,10 @@ __global__ void __launch_bounds__(EXT_BLOCK) k_extend(KCtx c, int b) {
     int2 br = b == 0 ? E.brange[slot] : make_int2(-1, -1);
     if (br.x >= 0) {
       RayPre rp = ray_pre(xyz(o), xyz(d));
+      if (br.y > c.bin_cap || br.x > br.y) { atomicOr(c.err, ERR_INDEX); br.y = br.x; }
       for (int k = br.x; k < br.y; ++k) {
         int li = __ldg(&c.bin_list[k]);
+        if ((unsigned)li >= (unsigned)c.nf) { atomicOr(c.err, ERR_INDEX); continue; }
         float4 ta = __ldg(&c.tri[3 * li]), tb = __ldg(&c.tri[3 * li + 1]), tc = __ldg(&c.tri[3 * li + 2]);
         int fid = __float_as_int(ta.w);
         float th = tri_test(rp, xyz(ta), xyz(tb), xyz(tc), t * 1.0000001f + 1e-30f);
@@ -726,6 +757,7 @@ __global__ void __launch_bounds__(RESOLVE_BLOCK) k_resolve(KCtx c, long long j0,
   long long pixel = local / v.spp;
   int s = (int)(local - pixel * v.spp);
   if (s != 0 && i != 0) return;
+  if (v.bin_base + pixel >= c.bin_pixels) { atomicOr(c.err, ERR_INDEX); return; }
   double* a = c.acc + 3 * (v.bin_base + pixel);
   double ax = a[0], ay = a[1], az = a[2];
   for (int k = i; s < v.spp && k < n; ++k, ++s) {

@@ -15,7 +15,8 @@ namespace st {
 constexpr int TRACE_SH = 16;
 constexpr int TRACE_DEPTH = 96;   // 4-wide nodes push up to three children per level
 constexpr int ERR_STACK = 1;
-constexpr int ERR_LOOP = 2;   // more node fetches than the tree has nodes: malformed hierarchy
+constexpr int ERR_LOOP = 2;   // more node fetches than the tree has nodes, or a node index past them
+constexpr int ERR_INDEX = 8;  // a leaf or bin-list index outside its array (the access is skipped)
 
 struct TraceStats { int visits, tests; };
 
@@ -52,6 +53,7 @@ __device__ __forceinline__ int trace_bvh(const float4* __restrict__ nodes, const
   int best = -1, best_leaf = -1;
   tbest = tmax;
   auto leaf = [&](int li) -> bool {
+    if ((unsigned)li >= (unsigned)nf) { atomicOr(err, ERR_INDEX); return false; }
     float4 a = __ldg(&tri[3 * li]);
     int fid = __float_as_int(a.w);
     if (STATS) ts->tests++;
@@ -78,7 +80,7 @@ __device__ __forceinline__ int trace_bvh(const float4* __restrict__ nodes, const
   int node = 0;
   int budget = nf;  // a well-formed tree fetches each of its < nf nodes at most once
   for (;;) {
-    if (--budget < 0) { atomicOr(err, ERR_LOOP); return best; }
+    if (--budget < 0 || (unsigned)node >= (unsigned)nf) { atomicOr(err, ERR_LOOP); return best; }
     const float4* np = nodes + 7 * node;
     float4 lx = __ldg(np), hx = __ldg(np + 1), ly = __ldg(np + 2), hy = __ldg(np + 3), lz = __ldg(np + 4),
            hz = __ldg(np + 5), ch = __ldg(np + 6);
