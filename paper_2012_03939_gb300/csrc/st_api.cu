@@ -614,7 +614,7 @@ st_status run_call(st_scene* s, Plan& p, const CallArgs& args, cudaStream_t st) 
     cudaDeviceSynchronize();
     drop_graphs(s);
     dfree(s->acc);
-    if (dalloc(&s->acc, 3 * (size_t)p.pixels) != cudaSuccess) {
+    if (dalloc(&s->acc, 6 * (size_t)p.pixels) != cudaSuccess) {
       cudaGetLastError();
       s->acc_cap = 0;
       return fail(ST_ERR_OOM, "forward accumulation buffer");

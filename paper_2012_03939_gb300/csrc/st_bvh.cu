@@ -586,6 +586,7 @@ int sort_blocks_for(int n) { return (n + RS_TILE - 1) / RS_TILE; }
 // ---- mesh statistics for back-face culling of the primary-visibility bins
 __global__ void k_mesh_stat_init(MeshStat* m) {
   m->vol6 = 0.0;
+  m->winding = 0;
   for (int k = 0; k < 3; ++k) {
     m->lo[k] = 0x7fffffff;
     m->hi[k] = (int)0x80000000;
@@ -630,11 +631,20 @@ __global__ void k_mesh_stat(const float* V, int nv, const int* F, int nf, MeshSt
   }
 }
 
+// the winding's sign only where the volume is clearly nonzero (a thousandth of the bounding box's)
+__global__ void k_mesh_stat_final(MeshStat* m) {
+  double d[3];
+  for (int k = 0; k < 3; ++k) d[k] = (double)unordered(m->hi[k]) - (double)unordered(m->lo[k]);
+  double box6 = 6.0 * d[0] * d[1] * d[2];
+  m->winding = fabs(m->vol6) > 1e-3 * box6 ? (m->vol6 > 0.0 ? 1 : -1) : 0;
+}
+
 cudaError_t mesh_stat(st_scene* s, cudaStream_t stream) {
   if (!s->mstat) return cudaSuccess;
   k_mesh_stat_init<<<1, 1, 0, stream>>>(s->mstat);
   int g = std::min((std::max(s->nf, s->nv) + 255) / 256, 4 * std::max(s->sm_count, 1));
   k_mesh_stat<<<g, 256, 0, stream>>>(s->verts, s->nv, s->faces, s->nf, s->mstat);
+  k_mesh_stat_final<<<1, 1, 0, stream>>>(s->mstat);
   return cudaGetLastError();
 }
 

@@ -17,6 +17,7 @@ namespace st {
 struct MeshStat {
   double vol6;
   int lo[3], hi[3];
+  int winding;   // +1 outward, -1 inward, 0 when the volume is too small against the bounds to tell
 };
 
 // Per-call arguments the kernels read from device memory, so a captured CUDA
@@ -126,7 +127,7 @@ struct st_scene {
   long long bin_cap = 0;         // list capacity
   int bin_views_cap = 0;
   int* bin_total_host = nullptr; // pinned: list length the last call needed
-  double* acc = nullptr;         // [3 * pixels] forward accumulation in double, in sample order
+  float* acc = nullptr;          // [6 * pixels] forward accumulation, compensated FP32 (sum, error) per channel
   long long acc_cap = 0;
   // per-call tables
   st::DevView* d_views = nullptr;

@@ -45,7 +45,7 @@ struct KCtx {
   const int* bin_ok;
   long long bin_cap;
   long long bin_pixels;
-  double* acc;            // per-pixel sample sums (bin-space pixel index), forward calls
+  float* acc;             // per-pixel compensated sample sums, (sum, error) x 3 (bin-space pixel index)
   int cull;               // the mesh is one closed, consistently wound surface (see MeshStat)
   const MeshStat* mstat;
   const DevView* views;
@@ -305,12 +305,12 @@ __device__ __forceinline__ float from_ordered(int i) { return __int_as_float(i >
 
 // A closed, consistently wound surface seen from an eye outside its bounds is
 // first hit on a face wound toward the eye (outward when the signed volume is
-// positive); faces clearly wound the other way (beyond a 1e-5 relative band, so
-// edge-on faces stay) can never be a primary ray's closest hit.
+// positive, MeshStat::winding); faces clearly wound the other way (beyond a 1e-5
+// relative band, so edge-on faces stay) can never be a primary ray's closest hit.
 __device__ __forceinline__ bool hidden_back_face(const KCtx& c, const DevView& v, float4 a, float4 b, float4 cc) {
   if (!c.cull || !c.mstat) return false;
-  double vol = c.mstat->vol6;
-  if (vol == 0.0) return false;
+  int w = c.mstat->winding;
+  if (w == 0) return false;
   float3 lo = mk3(from_ordered(c.mstat->lo[0]), from_ordered(c.mstat->lo[1]), from_ordered(c.mstat->lo[2]));
   float3 hi = mk3(from_ordered(c.mstat->hi[0]), from_ordered(c.mstat->hi[1]), from_ordered(c.mstat->hi[2]));
   float m = 1e-4f * fmaxf(hi.x - lo.x, fmaxf(hi.y - lo.y, hi.z - lo.z)) + 1e-6f;
@@ -320,7 +320,7 @@ __device__ __forceinline__ bool hidden_back_face(const KCtx& c, const DevView& v
   float3 n = cross3(xyz(b) - xyz(a), xyz(cc) - xyz(a));
   float3 e = v.eye - xyz(a);
   float f = dot3(n, e), tol = 1e-5f * len3(n) * len3(e);
-  return vol > 0.0 ? f < -tol : f > tol;
+  return w > 0 ? f < -tol : f > tol;
 }
 
 // fill = 0: count leaves per pixel; fill = 1: write them at start + cursor
@@ -365,7 +365,8 @@ __device__ __forceinline__ int view_of_pixel(const KCtx& c, int n_views, long lo
 __global__ void k_zero_acc(KCtx c) {
   long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= c.bin_pixels) return;
-  c.acc[3 * p] = 0.0; c.acc[3 * p + 1] = 0.0; c.acc[3 * p + 2] = 0.0;
+  float2* a = reinterpret_cast<float2*>(c.acc) + 3 * p;
+  a[0] = make_float2(0.0f, 0.0f); a[1] = make_float2(0.0f, 0.0f); a[2] = make_float2(0.0f, 0.0f);
 }
 
 // image rows of every view = mean of the samples (the output pointer comes from
@@ -375,10 +376,11 @@ __global__ void k_finish_views(KCtx c, int n_views) {
   if (p >= c.bin_pixels) return;
   const DevView& v = c.views[view_of_pixel(c, n_views, p)];
   float* img = c.args->image + 3 * (v.pix_off + (p - v.bin_base));
-  double inv = 1.0 / (double)v.spp;
-  img[0] = (float)(c.acc[3 * p] * inv);
-  img[1] = (float)(c.acc[3 * p + 1] * inv);
-  img[2] = (float)(c.acc[3 * p + 2] * inv);
+  const float2* a = reinterpret_cast<const float2*>(c.acc) + 3 * p;
+  float inv = 1.0f / (float)v.spp;
+  img[0] = (a[0].x - a[0].y) * inv;   // compensated sum: running sum minus the carried error
+  img[1] = (a[1].x - a[1].y) * inv;
+  img[2] = (a[2].x - a[2].y) * inv;
 }
 
 __global__ void k_fill_int(int* a, int n, int value) {
@@ -735,7 +737,16 @@ __global__ void __launch_bounds__(EXT_BLOCK) k_shadow(KCtx c, int b) {
   if ((threadIdx.x & 31) == 0 && traced) atomicAdd(&E.stat[STAT_SHADOW], (unsigned long long)traced);
 }
 
-// the pixel's double accumulator takes its samples in sample order, so the
+// Compensated (Kahan) summation in FP32: (sum, carried error); FP64 adds would
+// run on this part's slow FP64 pipe. Same order of operations, same result.
+__device__ __forceinline__ void kahan_add(float2& a, float x) {
+  float y = __fsub_rn(x, a.y);
+  float t = __fadd_rn(a.x, y);
+  a.y = __fsub_rn(__fsub_rn(t, a.x), y);
+  a.x = t;
+}
+
+// the pixel's compensated accumulator takes its samples in sample order, so the
 // result does not depend on where chunk boundaries fall. The block stages its
 // slots' radiance in shared memory with coalesced loads; the thread holding a
 // pixel's first sample then sums that pixel's run in order.
@@ -758,11 +769,11 @@ __global__ void __launch_bounds__(RESOLVE_BLOCK) k_resolve(KCtx c, long long j0,
   int s = (int)(local - pixel * v.spp);
   if (s != 0 && i != 0) return;
   if (v.bin_base + pixel >= c.bin_pixels) { atomicOr(c.err, ERR_INDEX); return; }
-  double* a = c.acc + 3 * (v.bin_base + pixel);
-  double ax = a[0], ay = a[1], az = a[2];
+  float2* a = reinterpret_cast<float2*>(c.acc) + 3 * (v.bin_base + pixel);
+  float2 ax = a[0], ay = a[1], az = a[2];
   for (int k = i; s < v.spp && k < n; ++k, ++s) {
     float4 r = k < i0 + RESOLVE_BLOCK ? srad[k - i0] : c.e.rad[k];
-    ax += (double)r.x; ay += (double)r.y; az += (double)r.z;
+    kahan_add(ax, r.x); kahan_add(ay, r.y); kahan_add(az, r.z);
   }
   a[0] = ax; a[1] = ay; a[2] = az;
 }
