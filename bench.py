@@ -43,6 +43,8 @@ DESCRIPTIONS = {
     "scale": ("scale: fractal-displaced UV sphere 1000000 faces, env 1024x512 + 2 point lights, 100 views 512x512, "
               "16 spp, 5 bounces; one step = one Adam iteration over an 8-view minibatch (BVH refit, forward, "
               "MSE, adjoint with interior + silhouette edges, Adam update at zero learning rate)"),
+    "color_bleed": ("color_bleed: three intersecting planes (red, blue, white floor) of 384 faces, 1 point light, "
+                    "4 views 64x64, 16 spp, 3 bounces; forward + adjoint (interior + silhouette edges)"),
 }
 
 
