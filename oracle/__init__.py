@@ -59,6 +59,8 @@ def lib():
         P = C.c_void_p
         L.orc_render_pixels.restype = C.c_longlong
         L.orc_render_pixels.argtypes = [P, P, C.c_int, P, P, C.c_int, P]
+        L.orc_render_signatures.restype = C.c_longlong
+        L.orc_render_signatures.argtypes = [P, P, C.c_int, P, P, C.c_int, P]
         L.orc_grad_pixels.restype = C.c_longlong
         L.orc_grad_pixels.argtypes = [P, P, C.c_int, P, P, C.c_int, P, P, P]
         L.orc_edge_grad.restype = C.c_longlong
@@ -136,6 +138,17 @@ def render_pixels(osc: OracleScene, prm, pix):
     if seg < 0:
         raise ValueError("oracle rejected the input")
     return out, seg
+
+
+def render_signatures(osc: OracleScene, prm, pix):
+    """Per listed pixel: the sum (mod 2^64) of its samples' path-decision hashes."""
+    pix = np.ascontiguousarray(pix, np.int32).reshape(-1, 3)
+    out = np.zeros(len(pix), np.uint64)
+    seg = lib().orc_render_signatures(C.byref(osc.s), osc.views, osc.n_views, C.byref(prm), _ptr(pix), len(pix),
+                                      _ptr(out))
+    if seg < 0:
+        raise ValueError("oracle rejected the input")
+    return out
 
 
 def all_pixels(sc):

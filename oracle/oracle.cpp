@@ -100,6 +100,18 @@ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
 
 inline double unif(uint32_t x) { return (double)(x >> 8) * (1.0 / 16777216.0); }
 
+// Path signature: FNV-1a style 64-bit hash of a path's discrete decisions, in
+// this order at every vertex: the face hit (0xffffffff for a miss), the
+// environment texel drawn for NEE, the BSDF lobe code (1 = specular, + 2 when
+// the sampled direction is valid) where a direction is drawn, and the
+// visibility bits of the vertex's shadow rays (bit j = point light j seen, bit
+// 8 = the environment sample seen) when at least one was traced. A pixel's
+// signature is the sum of its samples' hashes modulo 2^64. Equal signatures mean
+// the two implementations took the same decisions, so their values may differ
+// only by rounding.
+constexpr uint64_t SIG_BASIS = 0xcbf29ce484222325ull;
+inline uint64_t sig_mix(uint64_t h, uint32_t x) { return (h ^ (uint64_t)x) * 0x100000001b3ull; }
+
 struct Rng {
   uint32_t k0, k1;
   U4 draw(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3) const {
@@ -595,7 +607,7 @@ double face_side(const Scene& s, int f, const V3d& p) {
 template <class T>
 void trace_path(const Scene& s, const Rng& rng, int B, const Lights& lt, const V3d& eye, const V3d& d0, uint32_t c0,
                 uint32_t c1, uint32_t stream, Vars* vars, T L[3], long long& segments, Tape* tape = nullptr,
-                const SecCtx* sec = nullptr, int b0 = 0, int origin0 = -1);
+                const SecCtx* sec = nullptr, int b0 = 0, int origin0 = -1, uint64_t* sig = nullptr);
 
 // One secondary-visibility edge sample at path vertex b (the boundary term of
 // the vertex's integral over incoming directions; Li et al.'s edge sampling,
@@ -689,8 +701,14 @@ void secondary_edge(const Scene& s, const Rng& rng, int B, const Lights& lt, int
 template <class T>
 void trace_path(const Scene& s, const Rng& rng, int B, const Lights& lt, const V3d& eye, const V3d& d0, uint32_t c0,
                 uint32_t c1, uint32_t stream, Vars* vars, T L[3], long long& segments, Tape* tape,
-                const SecCtx* sec, int b0, int origin0) {
+                const SecCtx* sec, int b0, int origin0, uint64_t* sig) {
   using A = Access<T>;
+  uint64_t hsig = SIG_BASIS;
+  auto mix = [&](uint32_t x) { hsig = sig_mix(hsig, x); };
+  struct SigOut {
+    uint64_t* out; const uint64_t* h;
+    ~SigOut() { if (out) *out = *h; }
+  } sig_out{sig, &hsig};
   Tape none;
   Tape& tp = tape ? *tape : none;
   for (int c = 0; c < 3; ++c) L[c] = T(0.0);
@@ -702,6 +720,8 @@ void trace_path(const Scene& s, const Rng& rng, int B, const Lights& lt, const V
   for (int b = b0;; ++b) {
     ++segments;
     Hit h = closest(s, val(o), d, origin, INFINITY);
+    if (h.tri < 0) mix(0xffffffffu);
+    else if (b < B) mix((uint32_t)h.tri);
     if (h.tri < 0) {
       if (s.ew > 0) {
         double st;
@@ -735,6 +755,8 @@ void trace_path(const Scene& s, const Rng& rng, int B, const Lights& lt, const V
     V3d nv = val(n), pv = val(p);
 
     // next-event estimation: point lights
+    bool traced = false;      // any shadow ray at this vertex
+    uint32_t vis = 0;         // bit j: light j seen; bit 8: the environment sample seen
     for (size_t j = 0; j < lt.pos.size(); ++j) {
       V3<T> dv = lift<T>(lt.pos[j]) - p;
       T dist = len(dv);
@@ -742,7 +764,9 @@ void trace_path(const Scene& s, const Rng& rng, int B, const Lights& lt, const V
       T ci = dot(n, wi);
       if (!(vv(ci) > 0) || !(vv(dist) > 2 * T_EPS)) continue;
       ++segments;
+      traced = true;
       if (occluded(s, pv, val(wi), h.tri, vv(dist) - T_EPS)) continue;
+      vis |= 1u << j;
       T f[3];
       brdf_eval(s.brdf, m, n, wi, wo, f);
       T g = ci / (dist * dist);
@@ -753,6 +777,7 @@ void trace_path(const Scene& s, const Rng& rng, int B, const Lights& lt, const V
       U4 u = rng.draw(c0, c1, (uint32_t)(b << 4) | 1u, stream);
       int N = s.ew * s.eh;
       int tx = alias_pick(s.prob.data(), s.alias.data(), N, u.w[0], u.w[1]);
+      mix((uint32_t)tx);
       int row = tx / s.ew, col = tx % s.ew;
       double uu = (col + unif(u.w[2])) / s.ew, vq = (row + unif(u.w[3])) / s.eh;
       double th = PI * vq, ph = 2 * PI * uu;
@@ -765,7 +790,9 @@ void trace_path(const Scene& s, const Rng& rng, int B, const Lights& lt, const V
         T ci = dot(n, lift<T>(wi));
         if (vv(ci) > 0) {
           ++segments;
+          traced = true;
           if (!occluded(s, pv, wi, h.tri, INFINITY)) {
+            vis |= 1u << 8;
             double pe = env_pdf(s, tx, st);
             double w = 1.0;
             if (b < B - 1) {
@@ -784,11 +811,17 @@ void trace_path(const Scene& s, const Rng& rng, int B, const Lights& lt, const V
     if constexpr (std::is_same<T, Dual>::value) {
       if (sec) secondary_edge(s, rng, B, lt, b, p, nv, wo_d, h.tri, tex, thr, c0, c1, stream, *sec, vars, L, segments);
     }
-    if (b == B - 1) return;
+    if (b == B - 1) {
+      if (traced) mix(vis);
+      return;
+    }
     // BSDF sampling (direction and pdf held constant under differentiation)
     U4 u = rng.draw(c0, c1, (uint32_t)(b << 4) | 2u, stream);
     V3d wi;
-    double pdf = brdf_sample(s.brdf, mv, nv, wo_d, unif(u.w[0]), unif(u.w[1]), unif(u.w[2]), wi, nullptr);
+    int lobe = 0;
+    double pdf = brdf_sample(s.brdf, mv, nv, wo_d, unif(u.w[0]), unif(u.w[1]), unif(u.w[2]), wi, &lobe);
+    mix((uint32_t)lobe | (pdf > 0 ? 2u : 0u));
+    if (traced) mix(vis);
     pdf = tp.take(pdf);
     wi = tp.take(wi);
     if (!(pdf > 0)) return;
@@ -1018,6 +1051,37 @@ long long orc_render_pixels(const orc_scene* in, const orc_view* views, int n_vi
       for (int k = 0; k < 3; ++k) acc[k] += L[k];
     }
     for (int k = 0; k < 3; ++k) out[3 * i + k] = acc[k] / c.spp;
+  });
+  long long tot = 0;
+  for (auto x : seg) tot += x;
+  return tot;
+}
+
+long long orc_render_signatures(const orc_scene* in, const orc_view* views, int n_views, const orc_params* p,
+                                const int* pix, int n, uint64_t* out) {
+  Scene s;
+  if (!load_scene(in, s) || !check_common(views, n_views, p)) return -1;
+  for (int i = 0; i < n; ++i)
+    if (pix[3 * i] < 0 || pix[3 * i] >= n_views) return -1;
+  Rng rng = rng_of(p);
+  int nt = nthreads(p);
+  std::vector<long long> seg(nt, 0);
+  parallel_for(n, nt, [&](int tid, int i) {
+    const orc_view& v = views[pix[3 * i]];
+    Cam c = make_cam(v, s);
+    int x = pix[3 * i + 1], y = pix[3 * i + 2];
+    uint32_t c0 = c.off + (uint32_t)(y * c.W + x);
+    uint64_t acc = 0;
+    for (int sidx = 0; sidx < c.spp; ++sidx) {
+      U4 u = rng.draw(c0, (uint32_t)sidx, 0u, 0u);
+      V3d d = cam_dir(c, x + unif(u.w[0]), y + unif(u.w[1]));
+      double L[3];
+      uint64_t h = 0;
+      trace_path<double>(s, rng, p->max_bounces, c.lt, c.eye, d, c0, (uint32_t)sidx, 0u, nullptr, L, seg[tid],
+                         nullptr, nullptr, 0, -1, &h);
+      acc += h;
+    }
+    out[i] = acc;
   });
   long long tot = 0;
   for (auto x : seg) tot += x;

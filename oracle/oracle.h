@@ -68,6 +68,13 @@ long long orc_render_pixels(const orc_scene* s, const orc_view* views, int n_vie
                             const orc_params* p, const int* pix /*[n][3]*/, int n,
                             double* out /*[n][3]*/);
 
+/* Path signatures of the listed pixels: out [n] = the sum over the pixel's
+ * samples (mod 2^64) of a 64-bit FNV-1a hash of each path's discrete decisions
+ * (faces hit, environment texels drawn, BSDF lobes, shadow-ray visibility; the
+ * order is stated in oracle.cpp). Returns segments or -1. */
+long long orc_render_signatures(const orc_scene* s, const orc_view* views, int n_views,
+                                const orc_params* p, const int* pix, int n, uint64_t* out);
+
 /* Interior gradient for the listed pixels with weights dLdI [n][3] (plus the
  * secondary-visibility edge term at every path vertex when p->secondary):
  * d_verts [V][3] and d_face [texels][5] are ACCUMULATED (+=). Returns segments or -1. */

@@ -678,3 +678,46 @@ def test_mesh_colors_texel_gradient_matches_tape_replay_fd():
             assert abs(fd - df[ti, k]) < 1e-5 * max(1.0, abs(fd)), (ti, k, fd, df[ti, k])
             checked += 1
     assert checked > 10
+
+
+# ---------------------------------------------------------------------------- path signatures
+def _fnv(h, x):
+    return ((h ^ x) * 0x100000001b3) & 0xffffffffffffffff
+
+
+def test_path_signature_closed_cases():
+    # one Lambertian triangle facing the camera, one point light, one vertex per path:
+    # a covered pixel's paths hit face 0 and then either see the light (visibility
+    # bit 0) or trace no shadow ray (light behind the face); an uncovered pixel's
+    # paths miss. The pixel signature is spp times the path hash, modulo 2^64.
+    basis = 0xcbf29ce484222325
+    spp = 4
+    for light_z, expect_hit in [(2.5, _fnv(_fnv(basis, 0), 1)), (-2.5, _fnv(basis, 0))]:
+        sc = S.single_triangle(16, 16, light_dist=2.5)
+        sc.light_pos = np.array([[0.0, 0.0, light_z]], np.float32)
+        sc.views[0].spp = spp
+        sig = O.render_signatures(O.OracleScene(sc), O.params(1, 3), np.array([[0, 8, 8], [0, 0, 0]], np.int32))
+        assert int(sig[0]) == (spp * expect_hit) & 0xffffffffffffffff
+        assert int(sig[1]) == (spp * _fnv(basis, 0xffffffff)) & 0xffffffffffffffff
+
+
+def test_path_signature_depends_on_decisions_only():
+    # with ks = 0 the lobe probability is the same for any albedo, so changing kd
+    # changes the pixel values but no decision: equal signatures; moving the
+    # mesh changes the faces hit: different signatures
+    sc = S.tiny(res=16, spp=2)
+    P = sc.face_params.copy()
+    P[:, 3] = 0.0
+    P2 = P.copy()
+    P2[:, :3] = np.clip(P2[:, :3] * 0.5 + 0.2, 0, 1)
+    pix = O.all_pixels(sc)
+    prm = O.params(3, 17)
+    a = O.render_signatures(O.OracleScene(sc, face_params=P), prm, pix)
+    b = O.render_signatures(O.OracleScene(sc, face_params=P2), prm, pix)
+    va, _ = O.render_pixels(O.OracleScene(sc, face_params=P), prm, pix)
+    vb, _ = O.render_pixels(O.OracleScene(sc, face_params=P2), prm, pix)
+    np.testing.assert_array_equal(a, b)
+    assert np.abs(va - vb).max() > 1e-3
+    V2 = sc.vertices.astype(np.float64) * 1.05
+    c = O.render_signatures(O.OracleScene(sc, vertices=V2, face_params=P), prm, pix)
+    assert (c != a).mean() > 0.2
