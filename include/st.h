@@ -127,6 +127,13 @@ typedef struct {
   int time_kernels; /* per-view or ungraphed batched: time the closest-hit kernel (see st_stats) */
   int count_visits; /* run the instrumented traversal that counts node visits and triangle tests */
   int persist_blocks; /* batched mode: resident blocks per SM of the persistent stage kernels (0 = occupancy limit) */
+  unsigned long long* path_signatures; /* forward, optional: device uint64 [N], same rows as out_image: per pixel,
+                       the sum over its samples (mod 2^64) of a 64-bit FNV-1a hash of each path's discrete decisions:
+                       at every vertex the face hit (0xffffffff for a miss), the environment texel drawn for NEE,
+                       the BSDF lobe code (1 = specular, + 2 when the direction is valid) where one is drawn, then
+                       the shadow rays' visibility bits (bit j = point light j seen, bit 8 = the environment sample
+                       seen) when any was traced; basis 0xcbf29ce484222325, prime 0x100000001b3. Equal signatures
+                       with another implementation of the estimator mean the same decisions were taken. */
 } st_render_opts;
 
 typedef struct {

@@ -217,6 +217,7 @@ struct Plan {
   long long pixels = 0;       // sum of W*H: the primary-visibility bin space
   bool interior = false, edges = false;
   bool sec = false;           // secondary-visibility edge samples at every camera-path vertex
+  bool sig = false;           // forward: path signatures
   int max_vl = 0;             // most point lights a view of the call adds to the scene's
   bool bins = false;          // build primary-visibility bins (worth it only for many primary rays)
   st_render_opts o{};
@@ -234,7 +235,7 @@ void free_engine(Engine& e) {
   dfree(e.o); dfree(e.d); dfree(e.thr); dfree(e.rad); dfree(e.ctr); dfree(e.hit); dfree(e.origin); dfree(e.brange);
   dfree(e.q0); dfree(e.q1); dfree(e.qs); dfree(e.sh_dir); dfree(e.sh_c);
   dfree(e.r0); dfree(e.r1); dfree(e.r2); dfree(e.r3); dfree(e.esc); dfree(e.nb); dfree(e.cnt); dfree(e.stat);
-  dfree(e.sj); dfree(e.sje); dfree(e.pinj);
+  dfree(e.sj); dfree(e.sje); dfree(e.pinj); dfree(e.sig);
   e = Engine();
 }
 
@@ -272,6 +273,7 @@ st_status ensure_engine(st_scene* s, int Q, int B, int NS, bool records, bool se
   if (nsec) {
     chk(dalloc(&e.sj, 4 * q * nB, &acc)); chk(dalloc(&e.sje, q * nB, &acc)); chk(dalloc(&e.pinj, q * nB, &acc));
   }
+  chk(dalloc(&e.sig, q, &acc));
   chk(dalloc(&e.cnt, CNT_SIZE, &acc));
   chk(dalloc(&e.stat, STAT_SIZE, &acc));
   if (r != cudaSuccess) {
@@ -350,6 +352,7 @@ KCtx make_ctx(st_scene* s, const Plan& p) {
   c.views = s->d_views; c.segs = s->d_segs; c.n_segs = (int)p.segs.size();
   c.args = s->d_args; c.B = p.B; c.e = s->eng; c.e.records = p.kind == 1; c.err = s->d_err;
   c.sec = p.sec ? 1 : 0;
+  c.sig = p.sig ? 1 : 0; c.sacc = s->sacc;
   return c;
 }
 
@@ -528,7 +531,7 @@ st_status enqueue_call(st_scene* s, const Plan& p, int Q, cudaStream_t st, bool 
 std::vector<long long> graph_key(const Plan& p, int Q, const st_scene* s) {
   std::vector<long long> k = {p.kind, p.B, (long long)p.views.size(), Q, p.o.edge_term, p.o.edge_mode, p.o.edge_spp,
                               p.interior, p.edges, p.o.count_visits, p.bins,
-                              p.o.persist_blocks, s->bin_cap, p.max_vl};
+                              p.o.persist_blocks, s->bin_cap, p.max_vl, p.sig};
   for (auto& v : p.views) { k.push_back(v.W); k.push_back(v.H); k.push_back(v.spp); k.push_back(v.pix_off); }
   return k;
 }
@@ -546,6 +549,7 @@ st_status plan_call(st_scene* s, const st_view* views, int n_views, int default_
     return fail(ST_ERR_INVALID_ARG, "negative option");
   if (p.o.edge_term < 0 || p.o.edge_term > (ST_EDGE_TERM_PRIMARY | ST_EDGE_TERM_SECONDARY))
     return fail(ST_ERR_INVALID_ARG, "bad edge_term");
+  p.sig = kind == 0 && p.o.path_signatures != nullptr;
   p.interior = kind == 1 && want_interior;
   p.edges = kind == 1 && (p.o.edge_term & ST_EDGE_TERM_PRIMARY);
   p.sec = p.interior && (p.o.edge_term & ST_EDGE_TERM_SECONDARY) && s->n_edges > 0;
@@ -614,7 +618,8 @@ st_status run_call(st_scene* s, Plan& p, const CallArgs& args, cudaStream_t st) 
     cudaDeviceSynchronize();
     drop_graphs(s);
     dfree(s->acc);
-    if (dalloc(&s->acc, 6 * (size_t)p.pixels) != cudaSuccess) {
+    dfree(s->sacc);
+    if (dalloc(&s->acc, 6 * (size_t)p.pixels) != cudaSuccess || dalloc(&s->sacc, (size_t)p.pixels) != cudaSuccess) {
       cudaGetLastError();
       s->acc_cap = 0;
       return fail(ST_ERR_OOM, "forward accumulation buffer");
@@ -691,7 +696,7 @@ void destroy(st_scene* s) {
   dfree(s->lights); dfree(s->env_tex); dfree(s->env_alias); dfree(s->edge_v); dfree(s->edge_f);
   dfree(s->edge_flag); dfree(s->edge_cand); dfree(s->edge_ncand); dfree(s->d_views); dfree(s->d_segs);
   dfree(s->bin_start); dfree(s->bin_cur); dfree(s->bin_list); dfree(s->bin_ok); dfree(s->bin_part);
-  dfree(s->acc); dfree(s->mstat);
+  dfree(s->acc); dfree(s->sacc); dfree(s->mstat);
   if (s->bin_total_host) cudaFreeHost(s->bin_total_host);
   dfree(s->d_args); dfree(s->d_err);
   for (auto& e : s->ev) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
@@ -861,7 +866,8 @@ st_status st_render(st_scene* s, const st_view* views, int n_views, int default_
   Plan p;
   st_status r = plan_call(s, views, n_views, default_spp, max_bounces, opts, 0, false, p);
   if (r != ST_OK) return r;
-  CallArgs a{(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32), out_image, nullptr, nullptr, nullptr};
+  CallArgs a{(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32), out_image, nullptr, nullptr, nullptr,
+             p.o.path_signatures};
   return run_call(s, p, a, (cudaStream_t)stream);
 }
 
@@ -875,7 +881,7 @@ st_status st_render_backward(st_scene* s, const st_view* views, int n_views, int
   Plan p;
   st_status r = plan_call(s, views, n_views, default_spp, max_bounces, &o, 1, true, p);
   if (r != ST_OK) return r;
-  CallArgs a{(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32), nullptr, dLdI, dV, dF};
+  CallArgs a{(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32), nullptr, dLdI, dV, dF, nullptr};
   return run_call(s, p, a, (cudaStream_t)stream);
 }
 

@@ -29,6 +29,7 @@ struct CallArgs {
   const float* dLdI;        // backward input
   float* dV;                // backward outputs (accumulated)
   float* dF;
+  unsigned long long* sig;  // forward, optional: per-pixel path signatures (image rows)
 };
 
 // A contiguous range of the call's job space: camera samples of one view, or
@@ -53,6 +54,7 @@ struct Engine {
   float4 *r0 = nullptr, *r1 = nullptr, *r2 = nullptr, *r3 = nullptr;  // [B+1][Q] records
   float4* esc = nullptr;      // escape radiance (rgb, flag)
   int* nb = nullptr;          // hits per path
+  unsigned long long* sig = nullptr;  // per-slot path signature (forward calls that ask for them)
   // secondary-visibility edge samples (backward calls that ask for them)
   long long sec_cap = 0;      // job capacity = B * Q (one sample per path vertex)
   float4* sj = nullptr;       // [4][sec_cap]: (p, face), (w, weight), (m, tau), (dL/dI * T, edge)
@@ -128,6 +130,7 @@ struct st_scene {
   int bin_views_cap = 0;
   int* bin_total_host = nullptr; // pinned: list length the last call needed
   float* acc = nullptr;          // [6 * pixels] forward accumulation, compensated FP32 (sum, error) per channel
+  unsigned long long* sacc = nullptr;  // [pixels] path-signature sums (bin-space pixel index)
   long long acc_cap = 0;
   // per-call tables
   st::DevView* d_views = nullptr;

@@ -54,6 +54,8 @@ struct KCtx {
   const CallArgs* args;
   int B;
   int sec;                // backward: secondary-visibility edge samples on
+  int sig;                // forward: path signatures on
+  unsigned long long* sacc;   // per-pixel signature sums (bin-space pixel index)
   Engine e;
   int* err;
 };
@@ -78,6 +80,12 @@ __device__ __forceinline__ int warp_append(int* counter, bool pred) {
     base = __shfl_sync(FULL, base, leader);
   }
   return pred ? base + __popc(m & ((1u << lane) - 1u)) : -1;
+}
+
+// path signatures: FNV-1a step over one 32-bit decision
+constexpr unsigned long long SIG_BASIS = 0xcbf29ce484222325ull;
+__device__ __forceinline__ void sig_mix(unsigned long long& h, uint32_t x) {
+  h = (h ^ (unsigned long long)x) * 0x100000001b3ull;
 }
 
 __device__ __forceinline__ float3 fetch_vertex(const float* V, int v) { return mk3(V[3 * v], V[3 * v + 1], V[3 * v + 2]); }
@@ -367,6 +375,7 @@ __global__ void k_zero_acc(KCtx c) {
   if (p >= c.bin_pixels) return;
   float2* a = reinterpret_cast<float2*>(c.acc) + 3 * p;
   a[0] = make_float2(0.0f, 0.0f); a[1] = make_float2(0.0f, 0.0f); a[2] = make_float2(0.0f, 0.0f);
+  if (c.sig) c.sacc[p] = 0ull;
 }
 
 // image rows of every view = mean of the samples (the output pointer comes from
@@ -381,6 +390,7 @@ __global__ void k_finish_views(KCtx c, int n_views) {
   img[0] = (a[0].x - a[0].y) * inv;   // compensated sum: running sum minus the carried error
   img[1] = (a[1].x - a[1].y) * inv;
   img[2] = (a[2].x - a[2].y) * inv;
+  if (c.sig && c.args->sig) c.args->sig[v.pix_off + (p - v.bin_base)] = c.sacc[p];
 }
 
 __global__ void k_fill_int(int* a, int n, int value) {
@@ -507,6 +517,7 @@ __global__ void k_raygen(KCtx c, long long j0, int n) {
       E.r1[i] = make_float4(d.x, d.y, d.z, 0.0f);
     }
     if (ok) {
+      if (c.sig) E.sig[i] = SIG_BASIS;
       E.o[i] = make_float4(o.x, o.y, o.z, 0.0f);
       E.d[i] = make_float4(d.x, d.y, d.z, 0.0f);
       E.thr[i] = make_float4(1, 1, 1, 0);
@@ -597,7 +608,9 @@ __global__ void k_shade(KCtx c, int b) {
     float4 o4 = E.o[slot], d4 = E.d[slot];
     float3 dir = xyz(d4);
     float3 T = xyz(E.thr[slot]);
+    unsigned long long hs = c.sig ? E.sig[slot] : 0ull;
     if (h.x < 0) {
+      if (c.sig) { sig_mix(hs, 0xffffffffu); E.sig[slot] = hs; }
       if (c.env.w > 0) {
         float st_;
         int tx = env_texel(c.env, dir, st_);
@@ -624,6 +637,7 @@ __global__ void k_shade(KCtx c, int b) {
       float3 n = dot3(ng, wo) < 0.0f ? -ng : ng;
       int tex = texel_of(c, f, p, v0, v1, v2);
       Mat m = fetch_mat(c.P, tex);
+      if (c.sig) sig_mix(hs, (uint32_t)f);
       if (E.records) {
         E.r0[b * Q + slot] = make_float4(p.x, p.y, p.z, __int_as_float(f));
         E.nb[slot] = b + 1;
@@ -648,6 +662,7 @@ __global__ void k_shade(KCtx c, int b) {
       if (c.env.w > 0) {
         U4 u = philox((uint32_t)ct.x, (uint32_t)ct.y, (uint32_t)(vb << 4) | 1u, (uint32_t)ct.z, key.k0, key.k1);
         int tx = env_pick(c.env, u.x, u.y);
+        if (c.sig) sig_mix(hs, (uint32_t)tx);
         int row = tx / c.env.w, col = tx - row * c.env.w;
         float uu = ((float)col + unif(u.z)) / (float)c.env.w, vq = ((float)row + unif(u.w)) / (float)c.env.h;
         float sth, cth, sph, cph;
@@ -682,6 +697,7 @@ __global__ void k_shade(KCtx c, int b) {
         U4 u = philox((uint32_t)ct.x, (uint32_t)ct.y, (uint32_t)(vb << 4) | 2u, (uint32_t)ct.z, key.k0, key.k1);
         float3 wi;
         float pdf = brdf_sample(c.brdf, m, n, wo, unif(u.x), unif(u.y), unif(u.z), wi);
+        if (c.sig) sig_mix(hs, (unif(u.x) < lobe_prob(m) ? 1u : 0u) | (pdf > 0.0f ? 2u : 0u));
         if (pdf > 0.0f) {
           float3 Qv = brdf_cos(c.brdf, m, n, wi, wo);
           T = mul(T, Qv) * (1.0f / pdf);
@@ -691,6 +707,7 @@ __global__ void k_shade(KCtx c, int b) {
           cont = true;
         }
       }
+      if (c.sig) E.sig[slot] = hs;
     }
   }
   int qs = warp_append(&E.cnt[CNT_SH + b], sh_any);
@@ -727,6 +744,11 @@ __global__ void __launch_bounds__(EXT_BLOCK) k_shadow(KCtx c, int b) {
     }
     float4 r = E.rad[slot];
     E.rad[slot] = make_float4(r.x + L.x, r.y + L.y, r.z + L.z, 0.0f);
+    if (c.sig) {
+      unsigned long long hs = E.sig[slot];
+      sig_mix(hs, (uint32_t)vis);
+      E.sig[slot] = hs;
+    }
     if (E.records && vis) {
       float4 r2 = E.r2[b * Q + slot];
       E.r2[b * Q + slot] = make_float4(r2.x, r2.y, r2.z, __int_as_float(__float_as_int(r2.w) | vis));
@@ -771,11 +793,14 @@ __global__ void __launch_bounds__(RESOLVE_BLOCK) k_resolve(KCtx c, long long j0,
   if (v.bin_base + pixel >= c.bin_pixels) { atomicOr(c.err, ERR_INDEX); return; }
   float2* a = reinterpret_cast<float2*>(c.acc) + 3 * (v.bin_base + pixel);
   float2 ax = a[0], ay = a[1], az = a[2];
+  unsigned long long hsum = 0ull;
   for (int k = i; s < v.spp && k < n; ++k, ++s) {
     float4 r = k < i0 + RESOLVE_BLOCK ? srad[k - i0] : c.e.rad[k];
     kahan_add(ax, r.x); kahan_add(ay, r.y); kahan_add(az, r.z);
+    if (c.sig) hsum += c.e.sig[k];
   }
   a[0] = ax; a[1] = ay; a[2] = az;
+  if (c.sig) c.sacc[v.bin_base + pixel] += hsum;
 }
 
 // ------------------------------------------------------------------ gradient scatter

@@ -63,7 +63,7 @@ class SceneDesc(C.Structure):
 class RenderOpts(C.Structure):
     _fields_ = [("edge_term", C.c_int), ("edge_mode", C.c_int), ("edge_spp", C.c_int), ("mode", C.c_int),
                 ("use_graph", C.c_int), ("chunk_paths", C.c_int), ("time_kernels", C.c_int),
-                ("count_visits", C.c_int), ("persist_blocks", C.c_int)]
+                ("count_visits", C.c_int), ("persist_blocks", C.c_int), ("path_signatures", C.c_void_p)]
 
 
 class Stats(C.Structure):
@@ -139,7 +139,7 @@ def n_pixels(views) -> int:
 
 
 def make_opts(**kw) -> RenderOpts:
-    o = RenderOpts(0, EDGE_SILHOUETTE, 0, MODE_BATCHED, 1, 0, 0, 0, 0)
+    o = RenderOpts(0, EDGE_SILHOUETTE, 0, MODE_BATCHED, 1, 0, 0, 0, 0, None)
     for k, v in kw.items():
         if k == "mode" and isinstance(v, str):
             v = {"batched": MODE_BATCHED, "per_view": MODE_PER_VIEW}[v]
@@ -212,10 +212,18 @@ class Scene:
         self.face_params.copy_(p)
 
     def render(self, views, max_bounces: int, seed: int, opts: Optional[RenderOpts] = None, out=None,
-               default_spp: int = 0, stream=None) -> torch.Tensor:
+               default_spp: int = 0, stream=None, signatures: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Forward render into ``out`` [N, 3]; with ``signatures`` (int64 [N] on the device), also each pixel's
+        path-signature sum (the uint64 bit pattern)."""
         vs = make_views(views)
         if out is None:
             out = torch.zeros((n_pixels(views), 3), dtype=torch.float32, device=self.vertices.device)
+        if signatures is not None:
+            if signatures.dtype != torch.int64 or signatures.numel() < n_pixels(views) or not signatures.is_cuda:
+                raise ValueError("signatures must be a CUDA int64 tensor with a row per pixel")
+            o = make_opts() if opts is None else RenderOpts.from_buffer_copy(opts)
+            o.path_signatures = signatures.data_ptr()
+            opts = o
         _check(lib().st_render(self.handle, vs, len(vs), default_spp, max_bounces, seed,
                                None if opts is None else C.byref(opts), out.data_ptr(), _stream(stream)))
         return out
