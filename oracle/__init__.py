@@ -33,7 +33,7 @@ class _Scene(C.Structure):
                 ("faces", C.c_void_p), ("face_params", C.c_void_p), ("brdf", C.c_int),
                 ("n_lights", C.c_int), ("light_pos", C.c_void_p), ("light_intensity", C.c_void_p),
                 ("env_width", C.c_int), ("env_height", C.c_int), ("env_rgb", C.c_void_p),
-                ("color_res", C.c_int)]
+                ("color_res", C.c_int), ("param_width", C.c_int)]
 
 
 class _View(C.Structure):
@@ -113,7 +113,8 @@ class OracleScene:
         self.s = _Scene(len(self.V), len(self.F), _ptr(self.V).value, _ptr(self.F).value, _ptr(self.P).value,
                         0 if sc.brdf == "ggx" else 1, len(self.LP), _ptr(self.LP).value, _ptr(self.LI).value,
                         0 if self.E is None else self.E.shape[1], 0 if self.E is None else self.E.shape[0],
-                        None if self.E is None else _ptr(self.E).value, int(getattr(sc, "color_res", 0)))
+                        None if self.E is None else _ptr(self.E).value, int(getattr(sc, "color_res", 0)),
+                        self.P.shape[1])
         self.views = (_View * len(sc.views))()
         for i, v in enumerate(sc.views):
             lights = list(getattr(v, "lights", ()) or ())
@@ -124,6 +125,7 @@ class OracleScene:
         self.n_views = len(sc.views)
         self.nv, self.nf = len(self.V), len(self.F)
         self.ntex = len(self.P)          # texels (= faces at mesh-colors resolution 0)
+        self.np = self.P.shape[1]        # parameters per texel: 5 (scalar specular) or 7 (RGB specular)
 
 
 def params(max_bounces, seed, edge_mode=0, edge_spp=0, n_threads=0, secondary=0):
@@ -170,7 +172,7 @@ def grad_pixels(osc: OracleScene, prm, pix, dLdI):
     pix = np.ascontiguousarray(pix, np.int32).reshape(-1, 3)
     w = np.ascontiguousarray(dLdI, np.float64).reshape(-1, 3)
     dv = np.zeros((osc.nv, 3), np.float64)
-    df = np.zeros((osc.ntex, 5), np.float64)
+    df = np.zeros((osc.ntex, osc.np), np.float64)
     seg = lib().orc_grad_pixels(C.byref(osc.s), osc.views, osc.n_views, C.byref(prm), _ptr(pix), len(pix),
                                 _ptr(w), _ptr(dv), _ptr(df))
     if seg < 0:
@@ -201,7 +203,7 @@ def trace_screen(osc: OracleScene, prm, view_index, px, py, c0=0, c1=0, stream=0
     if grad_w is not None:
         gw = np.ascontiguousarray(grad_w, np.float64)
         dv = np.zeros((osc.nv, 3), np.float64)
-        df = np.zeros((osc.ntex, 5), np.float64)
+        df = np.zeros((osc.ntex, osc.np), np.float64)
     seg = lib().orc_trace_screen(C.byref(osc.s), C.byref(osc.views[view_index]), C.byref(prm), px, py, c0, c1,
                                  stream, _ptr(rgb), _ptr(gw), _ptr(dv), _ptr(df))
     if seg < 0:

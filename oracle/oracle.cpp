@@ -22,10 +22,11 @@
 //    t in (T_EPS, tmax), origin triangle excluded, equal t -> lower face id.
 //  * Shading: flat face normal flipped toward the incoming ray (two-sided).
 //  * BRDF: f = kd/pi + ks D G1(i) G1(o) / (4 cos_i cos_o): the Fresnel factor
-//    is held at its normal-incidence value ks (the "specular color"), so
+//    is held at its normal-incidence value ks (the "specular color", one value
+//    for all channels with 5 parameters per texel, one per channel with 7), so
 //    ks = 0 is exactly Lambertian; D = GGX or Beckmann with alpha = roughness
 //    (clamped to [0.01, 1]); separable Smith G1.
-//  * Lobe choice p_s = clamp(ks / (ks + mean kd), 0.05, 0.95); diffuse by the
+//  * Lobe choice p_s = clamp(mean ks / (mean ks + mean kd), 0.05, 0.95); diffuse by the
 //    concentric-disk (Shirley-Chiu) cosine map, specular by h ~ D cos(theta_h)
 //    and reflection; frame after Duff et al. (JCGT 2017); pdf = one-sample
 //    mixture; invalid (below the surface) ends the path.
@@ -76,7 +77,7 @@ constexpr double SEC_BAND = 1e-5;    // secondary edge: plane-distance band, tim
 constexpr double SEC_RMIN = 1e-6;    // secondary edge: nearest edge point accepted
 constexpr double SEC_SMIN = 1e-6;    // secondary edge: sine of the edge/view angle accepted
 constexpr int MAX_B = 8;
-constexpr int MAXD = 20 * MAX_B;
+constexpr int MAXD = 24 * MAX_B;
 
 // ---------------------------------------------------------------- Philox
 struct U4 { uint32_t w[4]; };
@@ -194,7 +195,8 @@ struct Scene {
   int res = 0, ntex = 1;        // mesh-colors resolution r and texels per face (r+1)(r+2)/2
   std::vector<V3d> vert;
   std::vector<int> face;        // 3 per face
-  std::vector<double> param;    // 5 per face
+  int np = 5;                   // parameters per texel: kd rgb, ks, alpha (5) or kd rgb, ks rgb, alpha (7)
+  std::vector<double> param;    // np per texel
   int brdf = 0;
   std::vector<V3d> lpos, lint;
   int ew = 0, eh = 0;
@@ -365,14 +367,16 @@ double env_pdf(const Scene& s, int texel, double sin_t) {
 }
 
 // ---------------------------------------------------------------- BRDF
-struct Mat { double kd[3], ks, alpha; };
+struct Mat { double kd[3], ks[3], alpha; };
 
-template <class T> struct MatT { T kd[3], ks, alpha; };
+template <class T> struct MatT { T kd[3], ks[3], alpha; };
 
+// probability of the specular lobe: mean specular over mean specular + mean diffuse
 double lobe_prob(const Mat& m) {
-  double den = m.ks + (m.kd[0] + m.kd[1] + m.kd[2]) / 3.0;
+  double ks = (m.ks[0] + m.ks[1] + m.ks[2]) / 3.0;
+  double den = ks + (m.kd[0] + m.kd[1] + m.kd[2]) / 3.0;
   if (!(den > 0)) return 0.5;
-  return std::min(std::max(m.ks / den, 0.05), 0.95);
+  return std::min(std::max(ks / den, 0.05), 0.95);
 }
 
 template <class T> T clamp_alpha(const T& a) {
@@ -413,8 +417,8 @@ void brdf_eval(int brdf, const MatT<T>& m, const V3<T>& n, const V3<T>& wi, cons
   T ch = dot(n, h), cih = dot(wi, h);
   (void)cih;
   T a = clamp_alpha(m.alpha);
-  T spec = m.ks * D_fn(brdf, ch, a) * G1_fn(brdf, ci, a) * G1_fn(brdf, co, a) / (4.0 * ci * co);
-  for (int c = 0; c < 3; ++c) f[c] = m.kd[c] / PI + spec;
+  T spec = D_fn(brdf, ch, a) * G1_fn(brdf, ci, a) * G1_fn(brdf, co, a) / (4.0 * ci * co);
+  for (int c = 0; c < 3; ++c) f[c] = m.kd[c] / PI + m.ks[c] * spec;
 }
 
 double brdf_pdf(int brdf, const Mat& m, const V3d& n, const V3d& wi, const V3d& wo) {
@@ -490,8 +494,10 @@ template <> struct Access<double> {
   static V3<double> vertex(const Scene& s, Vars*, int v) { return s.vert[v]; }
   static MatT<double> params(const Scene& s, Vars*, int f) {
     MatT<double> m;
-    for (int c = 0; c < 3; ++c) m.kd[c] = s.param[5 * f + c];
-    m.ks = s.param[5 * f + 3]; m.alpha = s.param[5 * f + 4];
+    const double* q = &s.param[(size_t)s.np * f];
+    for (int c = 0; c < 3; ++c) m.kd[c] = q[c];
+    for (int c = 0; c < 3; ++c) m.ks[c] = q[s.np == 7 ? 3 + c : 3];
+    m.alpha = q[s.np - 1];
     return m;
   }
 };
@@ -521,13 +527,15 @@ template <> struct Access<Dual> {
     for (size_t i = 0; i < vars->fid.size(); ++i)
       if (vars->fid[i] == f) base = vars->fdim[i];
     if (base < 0) {
-      base = vars->nd; vars->nd += 5;
+      base = vars->nd; vars->nd += s.np;
       vars->fid.push_back(f); vars->fdim.push_back(base);
     }
+    const double* q = &s.param[(size_t)s.np * f];
     MatT<Dual> m;
-    for (int c = 0; c < 3; ++c) m.kd[c] = unit_dual(s.param[5 * f + c], base + c);
-    m.ks = unit_dual(s.param[5 * f + 3], base + 3);
-    m.alpha = unit_dual(s.param[5 * f + 4], base + 4);
+    for (int c = 0; c < 3; ++c) m.kd[c] = unit_dual(q[c], base + c);
+    // one specular value for all channels (5 parameters) or one per channel (7)
+    for (int c = 0; c < 3; ++c) m.ks[c] = s.np == 7 ? unit_dual(q[3 + c], base + 3 + c) : unit_dual(q[3], base + 3);
+    m.alpha = unit_dual(q[s.np - 1], base + s.np - 1);
     return m;
   }
 };
@@ -545,8 +553,10 @@ long long texel(const Scene& s, int t, double alpha, double beta) {
 
 Mat mat_val(const Scene& s, int f) {
   Mat m;
-  for (int c = 0; c < 3; ++c) m.kd[c] = s.param[5 * f + c];
-  m.ks = s.param[5 * f + 3]; m.alpha = s.param[5 * f + 4];
+  const double* q = &s.param[(size_t)s.np * f];
+  for (int c = 0; c < 3; ++c) m.kd[c] = q[c];
+  for (int c = 0; c < 3; ++c) m.ks[c] = q[s.np == 7 ? 3 + c : 3];
+  m.alpha = q[s.np - 1];
   return m;
 }
 
@@ -846,7 +856,9 @@ bool load_scene(const orc_scene* in, Scene& s) {
   if (in->color_res < 0 || in->color_res > 64) return false;
   s.res = in->color_res;
   s.ntex = (s.res + 1) * (s.res + 2) / 2;
-  s.param.resize(5 * (size_t)s.nf * s.ntex);
+  if (in->param_width != 5 && in->param_width != 7) return false;
+  s.np = in->param_width;
+  s.param.resize((size_t)s.np * s.nf * s.ntex);
   for (size_t i = 0; i < s.param.size(); ++i) s.param[i] = in->face_params[i];
   for (int j = 0; j < in->n_lights; ++j) {
     s.lpos.push_back({in->light_pos[3 * j], in->light_pos[3 * j + 1], in->light_pos[3 * j + 2]});
@@ -874,16 +886,16 @@ template <class F> void parallel_for(int n, int nt, F fn) {
   for (auto& x : th) x.join();
 }
 
-void scatter_grad(const Vars& vars, const Dual& loss, double* dv, double* df) {
+void scatter_grad(const Vars& vars, const Dual& loss, double* dv, double* df, int np) {
   for (size_t i = 0; i < vars.vid.size(); ++i)
     for (int k = 0; k < 3; ++k) {
       int dim = vars.vdim[i] + k;
       if (dim < loss.n) dv[3 * vars.vid[i] + k] += loss.g[dim];
     }
   for (size_t i = 0; i < vars.fid.size(); ++i)
-    for (int k = 0; k < 5; ++k) {
+    for (int k = 0; k < np; ++k) {
       int dim = vars.fdim[i] + k;
-      if (dim < loss.n && df) df[5 * vars.fid[i] + k] += loss.g[dim];
+      if (dim < loss.n && df) df[(size_t)np * vars.fid[i] + k] += loss.g[dim];
     }
 }
 
@@ -978,15 +990,16 @@ long long orc_mesh_color_index(int r, long long t, double alpha, double beta) {
 static Mat mat_from(const double* p5) {
   Mat m;
   for (int c = 0; c < 3; ++c) m.kd[c] = p5[c];
-  m.ks = p5[3]; m.alpha = p5[4];
+  for (int c = 0; c < 3; ++c) m.ks[c] = p5[3];
+  m.alpha = p5[4];
   return m;
 }
 
 void orc_brdf_eval(int brdf, const double* p5, const double* n, const double* wi, const double* wo, double* out) {
   Mat m = mat_from(p5);
   MatT<double> mt;
-  for (int c = 0; c < 3; ++c) mt.kd[c] = m.kd[c];
-  mt.ks = m.ks; mt.alpha = m.alpha;
+  for (int c = 0; c < 3; ++c) { mt.kd[c] = m.kd[c]; mt.ks[c] = m.ks[c]; }
+  mt.alpha = m.alpha;
   V3d N{n[0], n[1], n[2]}, I{wi[0], wi[1], wi[2]}, O{wo[0], wo[1], wo[2]};
   brdf_eval(brdf, mt, N, I, O, out);
 }
@@ -1096,7 +1109,7 @@ long long orc_grad_pixels(const orc_scene* in, const orc_view* views, int n_view
   int nt = nthreads(p);
   std::vector<long long> seg(nt, 0);
   std::vector<std::vector<double>> gv(nt, std::vector<double>(3 * (size_t)s.nv, 0.0));
-  std::vector<std::vector<double>> gf(nt, std::vector<double>(5 * (size_t)s.nf * s.ntex, 0.0));
+  std::vector<std::vector<double>> gf(nt, std::vector<double>((size_t)s.np * s.nf * s.ntex, 0.0));
   std::vector<Edge> E;
   if (p->secondary) E = edge_list(s);
   SecCtx sc{&E, p->edge_mode};
@@ -1115,7 +1128,7 @@ long long orc_grad_pixels(const orc_scene* in, const orc_view* views, int n_view
       Dual L[3];
       trace_path<Dual>(s, rng, p->max_bounces, c.lt, c.eye, d, c0, (uint32_t)sidx, 0u, &vars, L, seg[tid], nullptr, sec);
       Dual loss = L[0] * (w[0] / c.spp) + L[1] * (w[1] / c.spp) + L[2] * (w[2] / c.spp);
-      scatter_grad(vars, loss, gv[tid].data(), gf[tid].data());
+      scatter_grad(vars, loss, gv[tid].data(), gf[tid].data(), s.np);
     }
   });
   for (int t = 0; t < nt; ++t) {
@@ -1218,7 +1231,7 @@ long long orc_trace_screen(const orc_scene* in, const orc_view* view, const orc_
                    p->secondary ? &sc : nullptr);
   for (int k = 0; k < 3; ++k) rgb[k] = L[k].v;
   Dual loss = L[0] * grad_w[0] + L[1] * grad_w[1] + L[2] * grad_w[2];
-  scatter_grad(vars, loss, d_verts, d_face);
+  scatter_grad(vars, loss, d_verts, d_face, s.np);
   return seg;
 }
 

@@ -32,7 +32,7 @@ typedef struct {
   int n_vertices, n_faces;
   const double* vertices;    /* [V][3] */
   const int* faces;          /* [F][3] */
-  const double* face_params; /* [F][5] kd_r kd_g kd_b ks roughness */
+  const double* face_params; /* [texels][param_width]: kd_r kd_g kd_b ks (or ks_r ks_g ks_b) roughness */
   int brdf;                  /* 0 = GGX, 1 = Beckmann */
   int n_lights;
   const double* light_pos;   /* [L][3] */
@@ -41,6 +41,8 @@ typedef struct {
   const float* env_rgb;      /* [H][W][3] */
   int color_res;             /* mesh-colors resolution r >= 0; face_params then holds
                                 F*(r+1)(r+2)/2 texels of 5 params, texel k(r, t, alpha, beta) */
+  int param_width;           /* parameters per texel: 5 (kd rgb, ks, roughness) or 7 (kd rgb, ks rgb,
+                                roughness); gradients use the same layout */
 } orc_scene;
 
 typedef struct {

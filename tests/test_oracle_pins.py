@@ -721,3 +721,65 @@ def test_path_signature_depends_on_decisions_only():
     V2 = sc.vertices.astype(np.float64) * 1.05
     c = O.render_signatures(O.OracleScene(sc, vertices=V2, face_params=P), prm, pix)
     assert (c != a).mean() > 0.2
+
+
+# ---------------------------------------------------------------------------- RGB specular (7 parameters)
+def _rgb_params(P5, ks_rgb):
+    return np.c_[P5[:, :3], ks_rgb, P5[:, 4]].astype(np.float64)
+
+
+@pytest.mark.parametrize("brdf", ["ggx", "beckmann"])
+def test_rgb_specular_normal_incidence_closed_form(brdf):
+    # light at the eye, ray along the view axis onto a triangle facing the camera:
+    # wi = wo = n, so D = 1 / (pi alpha^2), G1 = 1 and L_c = (kd_c / pi + ks_c / (4 pi alpha^2)) I / d^2
+    sc = S.single_triangle(16, 16)
+    sc.brdf = brdf
+    sc.light_pos = np.array([sc.views[0].eye], np.float32)
+    sc.light_intensity = np.array([[2.0, 3.0, 4.0]], np.float32)
+    kd, ks, alpha = np.array([0.3, 0.5, 0.2]), np.array([0.6, 0.1, 0.35]), 0.4
+    P = np.array([np.r_[kd, ks, alpha]])
+    got = O.trace_screen(O.OracleScene(sc, face_params=P), O.params(1, 0), 0, 8.0, 8.0)
+    d = float(np.linalg.norm(np.array(sc.views[0].eye, np.float64)))
+    exp = (kd / math.pi + ks / (4 * math.pi * alpha ** 2)) * np.array([2.0, 3.0, 4.0]) / d ** 2
+    np.testing.assert_allclose(got, exp, rtol=1e-12)
+
+
+def test_rgb_specular_with_equal_channels_equals_scalar_specular():
+    sc = S.tiny(res=16, spp=2)
+    P5 = sc.face_params.astype(np.float64)
+    P7 = _rgb_params(P5, np.repeat(P5[:, 3:4], 3, axis=1))
+    pix = O.all_pixels(sc)
+    a, _ = O.render_pixels(O.OracleScene(sc, face_params=P5), O.params(3, 4), pix)
+    b, _ = O.render_pixels(O.OracleScene(sc, face_params=P7), O.params(3, 4), pix)
+    np.testing.assert_array_equal(a, b)
+    w = np.random.default_rng(1).normal(size=a.shape)
+    _, f5, _ = O.grad_pixels(O.OracleScene(sc, face_params=P5), O.params(3, 4), pix, w)
+    _, f7, _ = O.grad_pixels(O.OracleScene(sc, face_params=P7), O.params(3, 4), pix, w)
+    # the scalar specular's derivative is the sum of the three channels'
+    np.testing.assert_allclose(f7[:, 3:6].sum(1), f5[:, 3], rtol=1e-9, atol=1e-14)
+    np.testing.assert_allclose(f7[:, [0, 1, 2, 6]], f5[:, [0, 1, 2, 4]], rtol=1e-9, atol=1e-14)
+
+
+def test_rgb_specular_gradient_matches_tape_replay_fd():
+    sc = _book_scene()
+    rng = np.random.default_rng(23)
+    P0 = _rgb_params(sc.face_params.astype(np.float64), rng.uniform(0.05, 0.6, (len(sc.faces), 3)))
+    V0 = sc.vertices.astype(np.float64)
+    prm = O.params(3, 77)
+    w = np.array([0.4, -0.3, 0.8])
+    checked = 0
+    for (px, py, c1) in [(5.3, 9.1, 0), (8.7, 11.2, 1), (10.1, 6.4, 2)]:
+        osc = O.OracleScene(sc, vertices=V0, face_params=P0)
+        _, dv, df = O.trace_screen(osc, prm, 0, px, py, c0=5, c1=c1, grad_w=w)
+        _, tape = O.trace_screen_taped(osc, prm, 0, px, py, c0=5, c1=c1)
+        h = 1e-6
+        for (ti, k) in [(i, k) for i in range(len(P0)) for k in range(7) if df[i, k] != 0]:
+            Pp, Pm = P0.copy(), P0.copy()
+            Pp[ti, k] += h
+            Pm[ti, k] -= h
+            fp = O.trace_screen_taped(O.OracleScene(sc, vertices=V0, face_params=Pp), prm, 0, px, py, 5, c1, tape=tape)
+            fm = O.trace_screen_taped(O.OracleScene(sc, vertices=V0, face_params=Pm), prm, 0, px, py, 5, c1, tape=tape)
+            fd = (w @ fp - w @ fm) / (2 * h)
+            assert abs(fd - df[ti, k]) < 1e-5 * max(1.0, abs(fd)), (ti, k, fd, df[ti, k])
+            checked += 1
+    assert checked > 12
