@@ -102,18 +102,22 @@ typedef struct {
  * weights (alpha, beta) for the face's second and third vertices uses texel
  * k = (t (r+1)(r+2) + i (2r - i + 3)) / 2 + j, (i, j) = floor(r (alpha, beta)).
  * r = 0 is one parameter set per face. Each texel holds kd_r, kd_g, kd_b, ks,
- * roughness. */
+ * roughness (or, with rgb_specular, kd_r, kd_g, kd_b, ks_r, ks_g, ks_b,
+ * roughness: the paper's "specular color", Sec. 3.3). */
 typedef struct {
   int n_vertices, n_faces;
   const float* vertices;     /* device, float [V][3] */
   const int* faces;          /* device, int [F][3] vertex indices */
-  const float* face_params;  /* device, float [F*n][5] texel parameters (n = 1 when color_res = 0) */
+  const float* face_params;  /* device, float [F*n][5 or 7] texel parameters (n = 1 when color_res = 0) */
   int brdf;                  /* ST_BRDF_GGX or ST_BRDF_BECKMANN */
   int n_point_lights;        /* 0..ST_MAX_LIGHTS (a call needs some light: these, the environment or its views') */
   const st_point_light* point_lights; /* host array */
   const st_envmap* env;      /* NULL if no environment */
   int color_res;             /* mesh-colors resolution r, 0..64 */
   int bvh_builder;           /* ST_BVH_PLOC (0, default) or ST_BVH_LBVH; st_scene_create and st_rebuild use it */
+  int rgb_specular;          /* 0: 5 parameters per texel (kd rgb, ks, roughness); 1: 7 (kd rgb, ks rgb,
+                                roughness), a specular colour per channel. face_params, st_set_face_params and
+                                the d_face_params of st_render_backward all use this layout. */
 } st_scene_desc;
 
 typedef struct {
@@ -169,7 +173,7 @@ st_status st_refit(st_scene* scene, const float* new_vertices, void* stream);
 /* New vertex positions with a full rebuild (Morton order recomputed). */
 st_status st_rebuild(st_scene* scene, const float* new_vertices, void* stream);
 
-/* New texel parameters (device float [F*n][5], see st_scene_desc); the material update (Sec. 3.3). */
+/* New texel parameters (device float [F*n][5 or 7], see st_scene_desc); the material update (Sec. 3.3). */
 st_status st_set_face_params(st_scene* scene, const float* face_params, void* stream);
 
 /* Forward render of n_views views (host array) with max_bounces surface
@@ -182,7 +186,7 @@ st_status st_render(st_scene* scene, const st_view* views, int n_views, int defa
 
 /* Adjoint: given dL/dI (device float [N][3], same layout as out_image),
  * ACCUMULATE (+=) dL/dvertices into d_vertices (device float [V][3]) and
- * dL/dtexel-parameters into d_face_params (device float [F*n][5]). The interior term
+ * dL/dtexel-parameters into d_face_params (device float [F*n][5 or 7], as the scene's layout). The interior term
  * replays the forward paths of the same seed and sweeps each in reverse; the
  * edge term (opts->edge_term) samples visibility edges: in screen space
  * (primary) and, at every vertex of every camera path, on the vertex's sphere

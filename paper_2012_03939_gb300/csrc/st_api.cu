@@ -341,7 +341,7 @@ KCtx make_ctx(st_scene* s, const Plan& p) {
   KCtx c;
   c.V = s->verts; c.F = s->faces; c.P = s->params; c.nodes = s->nodes4; c.tri = s->tri; c.nf = s->nf;
   c.lights = s->lights; c.nl = s->nl; c.nlt = s->nl + p.max_vl; c.NS = c.nlt + (s->env.w > 0 ? 1 : 0);
-  c.env = s->env; c.brdf = s->brdf; c.res = s->res; c.ntex = s->ntex;
+  c.env = s->env; c.brdf = s->brdf; c.res = s->res; c.ntex = s->ntex; c.np = s->np;
   c.edge_v = s->edge_v; c.edge_f = s->edge_f; c.n_edges = s->n_edges; c.edge_mode = p.o.edge_mode;
   c.edge_flag = s->edge_flag; c.edge_cand = s->edge_cand; c.edge_ncand = s->edge_ncand;
   c.bin_start = p.bins ? s->bin_start : nullptr;   // nullptr: every primary ray traverses the BVH
@@ -704,12 +704,15 @@ void destroy(st_scene* s) {
   delete s;
 }
 
-__global__ void k_params_in(const float* in, float4* out, int nf) {
+// caller texels (np = 5: kd rgb, ks, roughness; np = 7: kd rgb, ks rgb, roughness) to the
+// device layout (kd rgb, ks_r), (roughness, ks_g, ks_b, 0)
+__global__ void k_params_in(const float* in, float4* out, int nt, int np) {
   int f = blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= nf) return;
-  const float* p = in + 5 * f;
+  if (f >= nt) return;
+  const float* p = in + (size_t)np * f;
+  float kg = np == 7 ? p[4] : p[3], kb = np == 7 ? p[5] : p[3];
   out[2 * f] = make_float4(p[0], p[1], p[2], p[3]);
-  out[2 * f + 1] = make_float4(p[4], 0.0f, 0.0f, 0.0f);
+  out[2 * f + 1] = make_float4(p[np - 1], kg, kb, 0.0f);
 }
 
 }  // namespace
@@ -752,6 +755,7 @@ st_status st_scene_create(const st_scene_desc* d, void* stream, st_scene** out) 
   s->nl = d->n_point_lights;
   s->res = d->color_res;
   s->builder = d->bvh_builder;
+  s->np = d->rgb_specular ? 7 : 5;
   s->ntex = (s->res + 1) * (s->res + 2) / 2;
   // host copy of the faces: validation and edge list
   std::vector<int> hf(3 * (size_t)s->nf);
@@ -808,7 +812,7 @@ st_status st_scene_create(const st_scene_desc* d, void* stream, st_scene** out) 
   chk(cudaMemcpyAsync(s->faces, d->faces, 3 * sizeof(int) * n, cudaMemcpyDeviceToDevice, st));
   {
     int nt = n * s->ntex;
-    k_params_in<<<(nt + 255) / 256, 256, 0, st>>>(d->face_params, s->params, nt);
+    k_params_in<<<(nt + 255) / 256, 256, 0, st>>>(d->face_params, s->params, nt, s->np);
   }
   chk(cudaMemcpyAsync(s->lights, hl.data(), hl.size() * sizeof(float4), cudaMemcpyHostToDevice, st));
   chk(cudaMemcpyAsync(s->edge_v, ev.data(), ev.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
@@ -855,7 +859,7 @@ st_status st_rebuild(st_scene* s, const float* v, void* stream) { return update_
 st_status st_set_face_params(st_scene* s, const float* p, void* stream) {
   if (!s || !p) return fail(ST_ERR_INVALID_ARG, "NULL argument");
   int nt = s->nf * s->ntex;
-  k_params_in<<<(nt + 255) / 256, 256, 0, (cudaStream_t)stream>>>(p, s->params, nt);
+  k_params_in<<<(nt + 255) / 256, 256, 0, (cudaStream_t)stream>>>(p, s->params, nt, s->np);
   ST_CUDA(cudaGetLastError());
   return ST_OK;
 }

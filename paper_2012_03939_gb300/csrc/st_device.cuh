@@ -182,12 +182,15 @@ __device__ __forceinline__ int env_pick(const DevEnv& e, uint32_t u0, uint32_t u
 }
 
 // ------------------------------------------------------------------ BRDF
-struct Mat { float kd[3]; float ks, alpha; };
+// kd and ks per channel (a scalar specular is stored in all three), roughness
+struct Mat { float kd[3]; float ks[3]; float alpha; };
 
+// specular lobe probability: mean ks over mean ks + mean kd, clamped
 __device__ __forceinline__ float lobe_prob(const Mat& m) {
-  float den = m.ks + (m.kd[0] + m.kd[1] + m.kd[2]) * (1.0f / 3.0f);
+  float ks = (m.ks[0] + m.ks[1] + m.ks[2]) * (1.0f / 3.0f);
+  float den = ks + (m.kd[0] + m.kd[1] + m.kd[2]) * (1.0f / 3.0f);
   if (!(den > 0.0f)) return 0.5f;
-  return fminf(fmaxf(m.ks / den, 0.05f), 0.95f);
+  return fminf(fmaxf(ks / den, 0.05f), 0.95f);
 }
 
 __device__ __forceinline__ float clamp_alpha(float a, bool& clamped) {
@@ -247,9 +250,9 @@ __device__ __forceinline__ float3 brdf_cos(int brdf, const Mat& m, float3 n, flo
   float ch = dot3(n, h);
   bool cl;
   float a = clamp_alpha(m.alpha, cl);
-  float spec = m.ks * D_eval(brdf, ch, a) * G1_eval(brdf, ci, a) * G1_eval(brdf, co, a) / (4.0f * co);
+  float spec = D_eval(brdf, ch, a) * G1_eval(brdf, ci, a) * G1_eval(brdf, co, a) / (4.0f * co);
   float kdc = ci * (1.0f / PI_F);
-  return mk3(m.kd[0] * kdc + spec, m.kd[1] * kdc + spec, m.kd[2] * kdc + spec);
+  return mk3(m.kd[0] * kdc + m.ks[0] * spec, m.kd[1] * kdc + m.ks[1] * spec, m.kd[2] * kdc + m.ks[2] * spec);
 }
 
 // One-sample lobe-mixture pdf (solid angle) of direction wi.
@@ -310,9 +313,9 @@ __device__ __forceinline__ float brdf_sample(int brdf, const Mat& m, float3 n, f
 }
 
 // Adjoint of Q = f(wi, wo) cos(n, wi) for an RGB output weight gw:
-// accumulates dn, dwi (if non-null) and d params (kd_r, kd_g, kd_b, ks, alpha).
+// accumulates dn, dwi (if non-null) and d params (kd_r, kd_g, kd_b, ks_r, ks_g, ks_b, alpha).
 __device__ __forceinline__ void brdf_cos_adj(int brdf, const Mat& m, float3 n, float3 wi, float3 wo, float3 gw,
-                                             float3& dn, float3* dwi, float dm[5]) {
+                                             float3& dn, float3* dwi, float dm[7]) {
   float ci = dot3(n, wi), co = dot3(n, wo);
   if (!(ci > 0.0f) || !(co > 0.0f)) return;
   float3 hu = wi + wo;
@@ -325,16 +328,19 @@ __device__ __forceinline__ void brdf_cos_adj(int brdf, const Mat& m, float3 n, f
   float D = D_eval(brdf, ch, a, &Dc, &Da);
   float Gi = G1_eval(brdf, ci, a, &Gic, &Gia);
   float Go = G1_eval(brdf, co, a, &Goc, &Goa);
-  float gs = gw.x + gw.y + gw.z;
+  float gs = gw.x * m.ks[0] + gw.y * m.ks[1] + gw.z * m.ks[2];   // output weight times specular colour
   float inv4co = 1.0f / (4.0f * co);
+  float S = D * Gi * Go * inv4co;
   dm[0] += gw.x * ci * (1.0f / PI_F);
   dm[1] += gw.y * ci * (1.0f / PI_F);
   dm[2] += gw.z * ci * (1.0f / PI_F);
-  dm[3] += gs * D * Gi * Go * inv4co;
-  if (!cl) dm[4] += gs * m.ks * (Da * Gi * Go + D * Gia * Go + D * Gi * Goa) * inv4co;
-  float dci = (gw.x * m.kd[0] + gw.y * m.kd[1] + gw.z * m.kd[2]) * (1.0f / PI_F) + gs * m.ks * D * Gic * Go * inv4co;
-  float dco = gs * m.ks * D * Gi * (Goc * co - Go) * inv4co / co;
-  float dch = gs * m.ks * Dc * Gi * Go * inv4co;
+  dm[3] += gw.x * S;
+  dm[4] += gw.y * S;
+  dm[5] += gw.z * S;
+  if (!cl) dm[6] += gs * (Da * Gi * Go + D * Gia * Go + D * Gi * Goa) * inv4co;
+  float dci = (gw.x * m.kd[0] + gw.y * m.kd[1] + gw.z * m.kd[2]) * (1.0f / PI_F) + gs * D * Gic * Go * inv4co;
+  float dco = gs * D * Gi * (Goc * co - Go) * inv4co / co;
+  float dch = gs * Dc * Gi * Go * inv4co;
   dn += wi * dci + wo * dco + h * dch;
   if (dwi) {
     float3 dh = n * dch;

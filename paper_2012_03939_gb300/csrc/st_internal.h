@@ -83,11 +83,12 @@ struct st_scene {
   int nv = 0, nf = 0, brdf = 0, nl = 0;
   int res = 0, ntex = 1;         // mesh-colors resolution and texels per face
   int builder = 0;               // ST_BVH_PLOC or ST_BVH_LBVH
+  int np = 5;                    // caller parameters per texel: 5 (scalar specular) or 7 (RGB specular)
   bool closed = false;           // one surface; every edge has two faces that traverse it in opposite directions
   st::MeshStat* mstat = nullptr; // signed volume and vertex bounds, recomputed on the device after each update
   float* verts = nullptr;        // [V*3]
   int* faces = nullptr;          // [F*3]
-  float4* params = nullptr;      // [F*ntex*2] per texel: (kd_r, kd_g, kd_b, ks), (roughness, 0, 0, 0)
+  float4* params = nullptr;      // [F*ntex*2] per texel: (kd_r, kd_g, kd_b, ks_r), (roughness, ks_g, ks_b, 0)
   // LBVH
   float4* tri = nullptr;         // [F*3] triangles in leaf order; tri[3i].w = face id bits
   float4* nodes = nullptr;       // [(F-1)*4]

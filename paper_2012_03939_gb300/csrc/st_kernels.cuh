@@ -32,6 +32,7 @@ struct KCtx {
   DevEnv env;
   int brdf;
   int res, ntex;          // mesh-colors resolution r and texels per face
+  int np;                 // parameters per texel in the caller's layout: 5 (scalar ks) or 7 (RGB ks)
   const int2* edge_v;
   const int2* edge_f;
   int n_edges;
@@ -91,9 +92,11 @@ __device__ __forceinline__ void sig_mix(unsigned long long& h, uint32_t x) {
 __device__ __forceinline__ float3 fetch_vertex(const float* V, int v) { return mk3(V[3 * v], V[3 * v + 1], V[3 * v + 2]); }
 
 __device__ __forceinline__ Mat fetch_mat(const float4* P, int f) {
-  float4 a = __ldg(&P[2 * f]), b = __ldg(&P[2 * f + 1]);
+  float4 a = __ldg(&P[2 * f]), b = __ldg(&P[2 * f + 1]);   // (kd rgb, ks_r), (roughness, ks_g, ks_b, -)
   Mat m;
-  m.kd[0] = a.x; m.kd[1] = a.y; m.kd[2] = a.z; m.ks = a.w; m.alpha = b.x;
+  m.kd[0] = a.x; m.kd[1] = a.y; m.kd[2] = a.z;
+  m.ks[0] = a.w; m.ks[1] = b.y; m.ks[2] = b.z;
+  m.alpha = b.x;
   return m;
 }
 
@@ -829,7 +832,7 @@ __device__ __forceinline__ void warp_reduce_peers(int key, float (&vals)[NV], fl
 constexpr int ADJ_BLOCK = 128;
 
 __global__ void __launch_bounds__(ADJ_BLOCK) k_adjoint(KCtx c, long long j0, int n) {
-  __shared__ float scratch[ADJ_BLOCK / 32][32 * 15];
+  __shared__ float scratch[ADJ_BLOCK / 32][32 * 17];
   float* scr = scratch[threadIdx.x >> 5];
   const Engine& E = c.e;
   const size_t Q = (size_t)E.Q;
@@ -875,9 +878,9 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_adjoint(KCtx c, long long j0, int
   if (esc) A = mul(g, xyz(E.esc[i]));
   float3 Pnext = mk3(0, 0, 0);
   for (int b = c.B - 1; b >= 0; --b) {
-    float vals[14];
+    float vals[16];
 #pragma unroll
-    for (int k = 0; k < 14; ++k) vals[k] = 0.0f;
+    for (int k = 0; k < 16; ++k) vals[k] = 0.0f;
     int face = -1, key = -1;      // key = texel: equal keys share face and parameters
     if (b < nbv) {
       float4 r0 = E.r0[b * Q + i], r1 = E.r1[b * Q + i], r2 = E.r2[b * Q + i], r3 = E.r3[b * Q + i];
@@ -896,7 +899,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_adjoint(KCtx c, long long j0, int
       Mat m = fetch_mat(c.P, key);
       float3 Nb = mk3(0, 0, 0), Pb = Pnext;
       if (c.sec) Pb += xyz(E.pinj[b * Q + i]);   // the vertex's secondary edge sample moves with p
-      float dm[5] = {0, 0, 0, 0, 0};
+      float dm[7] = {0, 0, 0, 0, 0, 0, 0};
       float3 gC = mul(g, T[b]);
       float3 C = mk3(0, 0, 0);
       int flags = __float_as_int(r2.w);
@@ -946,10 +949,10 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_adjoint(KCtx c, long long j0, int
       vals[3] = e1bar.x; vals[4] = e1bar.y; vals[5] = e1bar.z;
       vals[6] = e2bar.x; vals[7] = e2bar.y; vals[8] = e2bar.z;
 #pragma unroll
-      for (int k = 0; k < 5; ++k) vals[9 + k] = dm[k];
+      for (int k = 0; k < 7; ++k) vals[9 + k] = dm[k];
     }
     bool leader;
-    warp_reduce_peers<14>(key, vals, scr, leader);
+    warp_reduce_peers<16>(key, vals, scr, leader);
     if (leader) {
       if (dV) {
 #pragma unroll
@@ -962,7 +965,13 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_adjoint(KCtx c, long long j0, int
       }
       if (dF) {
 #pragma unroll
-        for (int k = 0; k < 5; ++k) atomicAdd(&dF[5 * key + k], vals[9 + k]);
+        if (c.np == 7) {
+          for (int k = 0; k < 7; ++k) atomicAdd(&dF[7 * key + k], vals[9 + k]);
+        } else {   // one specular value for all channels: its derivative is the channels' sum
+          atomicAdd(&dF[5 * key], vals[9]); atomicAdd(&dF[5 * key + 1], vals[10]); atomicAdd(&dF[5 * key + 2], vals[11]);
+          atomicAdd(&dF[5 * key + 3], vals[12] + vals[13] + vals[14]);
+          atomicAdd(&dF[5 * key + 4], vals[15]);
+        }
       }
     }
   }

@@ -57,7 +57,8 @@ class View(C.Structure):
 class SceneDesc(C.Structure):
     _fields_ = [("n_vertices", C.c_int), ("n_faces", C.c_int), ("vertices", C.c_void_p), ("faces", C.c_void_p),
                 ("face_params", C.c_void_p), ("brdf", C.c_int), ("n_point_lights", C.c_int),
-                ("point_lights", C.c_void_p), ("env", C.c_void_p), ("color_res", C.c_int), ("bvh_builder", C.c_int)]
+                ("point_lights", C.c_void_p), ("env", C.c_void_p), ("color_res", C.c_int), ("bvh_builder", C.c_int),
+                ("rgb_specular", C.c_int)]
 
 
 class RenderOpts(C.Structure):
@@ -159,6 +160,8 @@ class Scene:
         self.vertices = vertices.detach().to(dev, torch.float32).contiguous()
         self.faces = faces.detach().to(dev, torch.int32).contiguous()
         self.face_params = face_params.detach().to(dev, torch.float32).contiguous()
+        if self.face_params.dim() != 2 or self.face_params.shape[1] not in (5, 7):
+            raise ValueError("face_params must be [texels, 5] (scalar specular) or [texels, 7] (RGB specular)")
         self.nv, self.nf = self.vertices.shape[0], self.faces.shape[0]
         self.ntex = self.face_params.shape[0]      # texels: faces * (r+1)(r+2)/2
         lp = np.zeros((0, 3), np.float32) if light_pos is None else np.asarray(light_pos, np.float32).reshape(-1, 3)
@@ -174,7 +177,8 @@ class Scene:
         desc = SceneDesc(self.nv, self.nf, self.vertices.data_ptr(), self.faces.data_ptr(),
                          self.face_params.data_ptr(), {"ggx": 0, "beckmann": 1}[brdf], len(lp),
                          C.addressof(self._lights), None if self._env is None else C.addressof(self._env),
-                         int(color_res), {"ploc": BVH_PLOC, "lbvh": BVH_LBVH}[bvh_builder])
+                         int(color_res), {"ploc": BVH_PLOC, "lbvh": BVH_LBVH}[bvh_builder],
+                         1 if self.face_params.shape[1] == 7 else 0)
         h = C.c_void_p()
         _check(lib().st_scene_create(C.byref(desc), _stream(stream), C.byref(h)))
         self.handle = h
@@ -236,7 +240,8 @@ class Scene:
         if want_vertices and d_vertices is None:
             d_vertices = torch.zeros((self.nv, 3), dtype=torch.float32, device=dLdI.device)
         if want_params and d_face_params is None:
-            d_face_params = torch.zeros((self.ntex, 5), dtype=torch.float32, device=dLdI.device)
+            d_face_params = torch.zeros((self.ntex, self.face_params.shape[1]), dtype=torch.float32,
+                                        device=dLdI.device)
         _check(lib().st_render_backward(self.handle, vs, len(vs), default_spp, max_bounces, seed,
                                         None if opts is None else C.byref(opts), dLdI.data_ptr(),
                                         None if d_vertices is None else d_vertices.data_ptr(),
