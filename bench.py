@@ -20,6 +20,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import threading
 import time
 
@@ -317,7 +318,7 @@ def run_ours(args):
     if not args.chunk and not args.profile:
         from paper_2012_03939_gb300 import autotune
         tuned = autotune.tune(scene, step_views, B, seed, edge_term=edge_on, edge_mode=0,
-                              cache_path=os.path.join(ROOT, "_work", "autotune_cache.rank%d.json" % rank))
+                              cache_path=os.path.join(tempfile.gettempdir(), "st_autotune_cache.rank%d.json" % rank))
         chunk, persist = tuned["chunk_paths"], tuned["persist_blocks"]
     fb = st.make_opts(mode="batched", use_graph=1, chunk_paths=chunk, persist_blocks=persist)
     bb = st.make_opts(mode="batched", use_graph=1, edge_term=edge_on, edge_mode=0, chunk_paths=chunk,
