@@ -250,7 +250,7 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     img = torch.zeros((N, 3), dtype=torch.float32, device="cuda")
     dV = torch.zeros((scene.nv, 3), dtype=torch.float32, device="cuda")
-    dF = torch.zeros((scene.nf, 5), dtype=torch.float32, device="cuda")
+    dF = torch.zeros(tuple(scene.face_params.shape), dtype=torch.float32, device="cuda")
     inv_n = 1.0 / (3 * N)
 
     adam = args.workload == "scale"
@@ -410,7 +410,7 @@ def run_ours(args):
     hP = torch.from_numpy(sc.face_params.copy()).pin_memory()
     oI = torch.empty((N, 3), dtype=torch.float32).pin_memory()
     oV = torch.empty((scene.nv, 3), dtype=torch.float32).pin_memory()
-    oF = torch.empty((scene.nf, 5), dtype=torch.float32).pin_memory()
+    oF = torch.empty(tuple(scene.face_params.shape), dtype=torch.float32).pin_memory()
     dVert = torch.empty_like(scene.vertices)
     dPar = torch.empty_like(scene.face_params)
 

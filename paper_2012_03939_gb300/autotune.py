@@ -56,7 +56,7 @@ def tune(scene: "_st.Scene", views, max_bounces: int, seed: int = 1, edge_term: 
     img = torch.zeros((n, 3), dtype=torch.float32, device=dev)
     g = torch.full((n, 3), 1e-3, dtype=torch.float32, device=dev)
     dV = torch.zeros((scene.nv, 3), dtype=torch.float32, device=dev)
-    dF = torch.zeros((scene.nf, 5), dtype=torch.float32, device=dev)
+    dF = torch.zeros(tuple(scene.face_params.shape), dtype=torch.float32, device=dev)
     best = None
     results = []
     for ch in chunks:
