@@ -65,6 +65,8 @@ def lib():
         L.orc_grad_pixels.argtypes = [P, P, C.c_int, P, P, C.c_int, P, P, P]
         L.orc_edge_grad.restype = C.c_longlong
         L.orc_edge_grad.argtypes = [P, P, C.c_int, P, P, P]
+        L.orc_shadow_edge_grad.restype = C.c_longlong
+        L.orc_shadow_edge_grad.argtypes = [P, P, C.c_int, P, P, P]
         L.orc_edge_candidates.restype = C.c_int
         L.orc_edge_candidates.argtypes = [P, P, P, P]
         L.orc_trace_screen.restype = C.c_longlong
@@ -184,6 +186,15 @@ def edge_grad(osc: OracleScene, prm, dLdI_full):
     w = np.ascontiguousarray(dLdI_full, np.float64).reshape(-1, 3)
     dv = np.zeros((osc.nv, 3), np.float64)
     seg = lib().orc_edge_grad(C.byref(osc.s), osc.views, osc.n_views, C.byref(prm), _ptr(w), _ptr(dv))
+    if seg < 0:
+        raise ValueError("oracle rejected the input")
+    return dv, seg
+
+
+def shadow_edge_grad(osc: OracleScene, prm, dLdI_full):
+    w = np.ascontiguousarray(dLdI_full, np.float64).reshape(-1, 3)
+    dv = np.zeros((osc.nv, 3), np.float64)
+    seg = lib().orc_shadow_edge_grad(C.byref(osc.s), osc.views, osc.n_views, C.byref(prm), _ptr(w), _ptr(dv))
     if seg < 0:
         raise ValueError("oracle rejected the input")
     return dv, seg

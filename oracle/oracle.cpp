@@ -72,6 +72,7 @@ constexpr double PI = 3.14159265358979323846;
 constexpr double T_EPS = 1e-5;
 constexpr double Z_NEAR = 1e-4;
 constexpr double EDGE_EPS = 1e-3;
+constexpr double SH_EDGE_DELTA = 1e-4;   // shadow edge: receiver search starts this far (relative) past the edge
 constexpr double SEC_EPS = 1e-4;     // secondary edge: angular offset of the two side rays (radians)
 constexpr double SEC_BAND = 1e-5;    // secondary edge: plane-distance band, times (1 + |p|_inf)
 constexpr double SEC_RMIN = 1e-6;    // secondary edge: nearest edge point accepted
@@ -1201,6 +1202,118 @@ long long orc_edge_grad(const orc_scene* in, const orc_view* views, int n_views,
         G[3 * e.b] += wt * tau * jb.x; G[3 * e.b + 1] += wt * tau * jb.y; G[3 * e.b + 2] += wt * tau * jb.z;
       }
     });
+  }
+  for (int t = 0; t < nt; ++t)
+    for (size_t k = 0; k < gv[t].size(); ++k) d_verts[k] += gv[t][k];
+  long long tot = 0;
+  for (auto x : seg) tot += x;
+  return tot;
+}
+
+// Shadow-edge term (point lights, shadows on surfaces the camera sees). A
+// point light's shadow on a visible surface ends where light rays graze the
+// edges that are silhouettes seen from the light; in the image that boundary is
+// the projection, through the receiving surface, of those edges, and moving the
+// occluder or the receiver moves it. Per view and per light l: candidates =
+// edges whose two faces face the light on opposite sides (or boundary edges),
+// in edge order; N = W*H*spp samples (edge_spp overrides spp); sample k picks
+// candidate t/N for t uniform in [k n, (k+1) n) and tau uniform on the edge
+// (counter (k, pixel_offset, l<<4, 3)); y = A + tau (B - A); the light ray from
+// L through y, continued from y + SH_EDGE_DELTA |y - L| along it, finds the
+// receiver point q = L + s (y - L); S = q projected to the view. Camera paths
+// at S -+ EDGE_EPS n_S (counters (k, pixel_offset, b<<4|call, 4 + l)), n_S the
+// screen normal of the boundary curve S(tau), give L- - L+. The boundary moves
+// with the occluder (dq = s P dy, P = I - u n_r^T / n_r.u, u = y - L) and with
+// the receiver plane; its screen-normal speed is n_S . J_proj(q) dq. The
+// sample adds <dL/dI_S, L- - L+> n_cand |dS/dtau| / N times that speed.
+long long orc_shadow_edge_grad(const orc_scene* in, const orc_view* views, int n_views, const orc_params* p,
+                               const double* dLdI, double* d_verts) {
+  Scene s;
+  if (!load_scene(in, s) || !check_common(views, n_views, p)) return -1;
+  Rng rng = rng_of(p);
+  int nt = nthreads(p);
+  std::vector<Edge> E = edge_list(s);
+  std::vector<long long> seg(nt, 0);
+  std::vector<std::vector<double>> gv(nt, std::vector<double>(3 * (size_t)s.nv, 0.0));
+  for (int vi = 0; vi < n_views; ++vi) {
+    Cam c = make_cam(views[vi], s);
+    long long spp_e = p->edge_spp > 0 ? p->edge_spp : c.spp;
+    long long N = (long long)c.W * c.H * spp_e;
+    for (size_t l = 0; l < c.lt.pos.size(); ++l) {
+      V3d L = c.lt.pos[l];
+      std::vector<int> cand;
+      for (size_t i = 0; i < E.size(); ++i) {
+        const Edge& e = E[i];
+        if (e.nf == 2 && facing(s, e.f[0], L) == facing(s, e.f[1], L)) continue;
+        cand.push_back((int)i);
+      }
+      if (cand.empty()) continue;
+      uint64_t ncand = cand.size();
+      int nblk = nt * 8;
+      parallel_for(nblk, nt, [&](int tid, int blk) {
+        long long k0 = N * blk / nblk, k1 = N * (blk + 1) / nblk;
+        for (long long k = k0; k < k1; ++k) {
+          U4 u = rng.draw((uint32_t)k, c.off, (uint32_t)l << 4, 3u);
+          uint64_t t = (uint64_t)k * ncand + (((uint64_t)(u.w[0] >> 8) * ncand) >> 24);
+          const Edge& e = E[cand[(size_t)(t / (uint64_t)N)]];
+          double tau = unif(u.w[1]);
+          V3d A = s.vert[e.a], Bv = s.vert[e.b];
+          V3d y = A + scl(Bv - A, tau);
+          V3d uvec = y - L;
+          double dy = len(uvec);
+          if (!(dy > 0)) continue;
+          V3d dir = scl(uvec, 1.0 / dy);
+          V3d org = y + scl(dir, SH_EDGE_DELTA * dy);
+          ++seg[tid];
+          Hit h = closest(s, org, dir, -1, INFINITY);
+          if (h.tri < 0) continue;
+          V3d q = org + scl(dir, h.t);
+          double sx, sy;
+          if (!project(c, q, sx, sy)) continue;
+          int x = (int)std::floor(sx), yy = (int)std::floor(sy);
+          if (x < 0 || yy < 0 || x >= c.W || yy >= c.H) continue;
+          const double* w = dLdI + 3 * ((size_t)c.off + (size_t)yy * c.W + x);
+          if (w[0] == 0 && w[1] == 0 && w[2] == 0) continue;
+          // screen tangent of the boundary curve: dS/dtau = J_proj(q) s P (B - A)
+          const int* rf = &s.face[3 * h.tri];
+          V3d nr = cross(s.vert[rf[1]] - s.vert[rf[0]], s.vert[rf[2]] - s.vert[rf[0]]);
+          double nu = dot(nr, uvec);
+          if (!(std::fabs(nu) > 0)) continue;
+          double sc = len(q - L) / dy;
+          V3d ab = Bv - A;
+          V3d dq = scl(ab - scl(uvec, dot(nr, ab) / nu), sc);
+          V3d jx = proj_jt(c, q, 1.0, 0.0), jy = proj_jt(c, q, 0.0, 1.0);
+          double tx = dot(jx, dq), ty = dot(jy, dq);
+          double lt = std::sqrt(tx * tx + ty * ty);
+          if (!(lt > 0)) continue;
+          double nx = -ty / lt, ny = tx / lt;
+          double Lm[3], Lp[3];
+          trace_path<double>(s, rng, p->max_bounces, c.lt, c.eye, cam_dir(c, sx - EDGE_EPS * nx, sy - EDGE_EPS * ny),
+                             (uint32_t)k, c.off, 4u + (uint32_t)l, nullptr, Lm, seg[tid]);
+          trace_path<double>(s, rng, p->max_bounces, c.lt, c.eye, cam_dir(c, sx + EDGE_EPS * nx, sy + EDGE_EPS * ny),
+                             (uint32_t)k, c.off, 4u + (uint32_t)l, nullptr, Lp, seg[tid]);
+          double g = 0;
+          for (int ch = 0; ch < 3; ++ch) g += w[ch] * (Lm[ch] - Lp[ch]);
+          if (g == 0) continue;
+          double wt = g * (double)ncand * lt / (double)N;
+          // the boundary's screen-normal speed, through dual numbers of the occluder's
+          // edge and the receiver's vertices: q = L + s (y - L) on the receiver plane
+          Vars vars;
+          using DA = Access<Dual>;
+          V3<Dual> Ad = DA::vertex(s, &vars, e.a), Bd = DA::vertex(s, &vars, e.b);
+          V3<Dual> r0 = DA::vertex(s, &vars, rf[0]), r1 = DA::vertex(s, &vars, rf[1]), r2 = DA::vertex(s, &vars, rf[2]);
+          V3<Dual> yd = scl(Ad, 1.0 - tau) + scl(Bd, tau);
+          V3<Dual> Ld = lift<Dual>(L);
+          V3<Dual> ud = yd - Ld;
+          V3<Dual> nd = cross(r1 - r0, r2 - r0);
+          Dual sd = dot(nd, r0 - Ld) / dot(nd, ud);
+          V3<Dual> qd = Ld + scl(ud, sd);
+          V3d js = scl(jx, nx) + scl(jy, ny);
+          Dual vn = dot(lift<Dual>(js), qd - lift<Dual>(q));
+          scatter_grad(vars, vn * wt, gv[tid].data(), nullptr, s.np);
+        }
+      });
+    }
   }
   for (int t = 0; t < nt; ++t)
     for (size_t k = 0; k < gv[t].size(); ++k) d_verts[k] += gv[t][k];

@@ -91,6 +91,13 @@ long long orc_grad_pixels(const orc_scene* s, const orc_view* views, int n_views
 long long orc_edge_grad(const orc_scene* s, const orc_view* views, int n_views,
                         const orc_params* p, const double* dLdI, double* d_verts);
 
+/* Shadow-edge term of point lights on surfaces the camera sees (the boundary
+ * term of the image integral across shadow edges; oracle.cpp states the
+ * estimator); dLdI is the full packed image. d_verts accumulated (+=).
+ * Returns segments traced or -1. */
+long long orc_shadow_edge_grad(const orc_scene* s, const orc_view* views, int n_views,
+                               const orc_params* p, const double* dLdI, double* d_verts);
+
 /* Number of edge candidates of view v and the per-view sample count. */
 int orc_edge_candidates(const orc_scene* s, const orc_view* view, const orc_params* p,
                         int* out_edges /* may be NULL; [2*E] vertex pairs */);
