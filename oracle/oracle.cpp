@@ -28,8 +28,10 @@
 //    (clamped to [0.01, 1]); separable Smith G1.
 //  * Lobe choice p_s = clamp(mean ks / (mean ks + mean kd), 0.05, 0.95); diffuse by the
 //    concentric-disk (Shirley-Chiu) cosine map, specular by h ~ D cos(theta_h)
-//    and reflection; frame after Duff et al. (JCGT 2017); pdf = one-sample
-//    mixture; invalid (below the surface) ends the path.
+//    and reflection, in a tangent frame t = (h x n)/|h x n|, b = n x t about a
+//    fixed helper axis h (the lobes are isotropic, so the frame's rotation
+//    about n changes no density); pdf = one-sample mixture; invalid (below the
+//    surface) ends the path.
 //  * NEE: every point light (no MIS); one environment sample per vertex from an
 //    alias table (Vose) over texel weight lum * sin(theta_row), MIS power
 //    heuristic against the BSDF pdf (weight 1 at the last vertex, which draws no
@@ -274,10 +276,10 @@ bool tri_hit(const V3d& o, const V3d& d, const V3d& p0, const V3d& p1, const V3d
 
 struct Hit { int tri; double t, b1, b2; };
 
-Hit closest(const Scene& s, const V3d& o, const V3d& d, int exclude, double tmax) {
+Hit closest(const Scene& s, const V3d& o, const V3d& d, int exclude, double tmax, int exclude2 = -1) {
   Hit h{-1, tmax, 0, 0};
   for (int f = 0; f < s.nf; ++f) {
-    if (f == exclude) continue;
+    if (f == exclude || f == exclude2) continue;
     double t, b1, b2;
     const int* fi = &s.face[3 * f];
     if (!tri_hit(o, d, s.vert[fi[0]], s.vert[fi[1]], s.vert[fi[2]], t, &b1, &b2)) continue;
@@ -435,12 +437,19 @@ double brdf_pdf(int brdf, const Mat& m, const V3d& n, const V3d& wi, const V3d& 
 }
 
 void onb(const V3d& n, V3d& t, V3d& b) {
-  // Duff et al., "Building an Orthonormal Basis, Revisited", JCGT 2017.
-  double sign = std::copysign(1.0, n.z);
-  double a = -1.0 / (sign + n.z);
-  double bb = n.x * n.y * a;
-  t = {1.0 + sign * n.x * n.x * a, sign * bb, -sign * n.x};
-  b = {bb, sign + n.y * n.y * a, -n.y};
+  // Helper axis h = (7, 9, 11)/16: exact in binary and on no coordinate axis or
+  // plane. The frame is continuous in n except near n = +-h (then a second
+  // helper). A frame that switches on the sign of a coordinate of n jumps
+  // across a whole great circle, where a symmetric mesh's normals lie exactly
+  // and rounding alone would pick the side.
+  V3d c = cross(V3d{0.4375, 0.5625, 0.6875}, n);
+  double l = len(c);
+  if (!(l > 1e-6)) {
+    c = cross(V3d{0.6875, -0.4375, 0.5625}, n);
+    l = len(c);
+  }
+  t = scl(c, 1.0 / l);
+  b = cross(n, t);
 }
 
 void concentric(double u1, double u2, double& x, double& y) {
@@ -1220,7 +1229,9 @@ long long orc_edge_grad(const orc_scene* in, const orc_view* views, int n_views,
 // candidate t/N for t uniform in [k n, (k+1) n) and tau uniform on the edge
 // (counter (k, pixel_offset, l<<4, 3)); y = A + tau (B - A); the light ray from
 // L through y, continued from y + SH_EDGE_DELTA |y - L| along it, finds the
-// receiver point q = L + s (y - L); S = q projected to the view. Camera paths
+// receiver point q = L + s (y - L) on a face other than the edge's own (that
+// ray meets their planes only at y, so they receive no shadow from the edge);
+// S = q projected to the view. Camera paths
 // at S -+ EDGE_EPS n_S (counters (k, pixel_offset, b<<4|call, 4 + l)), n_S the
 // screen normal of the boundary curve S(tau), give L- - L+. The boundary moves
 // with the occluder (dq = s P dy, P = I - u n_r^T / n_r.u, u = y - L) and with
@@ -1265,7 +1276,7 @@ long long orc_shadow_edge_grad(const orc_scene* in, const orc_view* views, int n
           V3d dir = scl(uvec, 1.0 / dy);
           V3d org = y + scl(dir, SH_EDGE_DELTA * dy);
           ++seg[tid];
-          Hit h = closest(s, org, dir, -1, INFINITY);
+          Hit h = closest(s, org, dir, e.f[0], INFINITY, e.nf == 2 ? e.f[1] : -1);
           if (h.tri < 0) continue;
           V3d q = org + scl(dir, h.t);
           double sx, sy;

@@ -267,13 +267,20 @@ __device__ __forceinline__ float brdf_pdf(int brdf, const Mat& m, float3 n, floa
   return (1.0f - ps) * ci * (1.0f / PI_F) + ps * D_eval(brdf, ch, a) * ch / (4.0f * woh);
 }
 
-// Orthonormal frame around n (Duff et al., JCGT 2017).
+// Orthonormal frame around n: t = (h x n)/|h x n|, b = n x t, helper axis h =
+// (7, 9, 11)/16 (exact in binary, on no coordinate axis or plane), a second
+// helper near n = +-h. Continuous in n elsewhere, so normals that lie exactly
+// on a coordinate plane (symmetric meshes) get the same frame at any
+// precision; the lobes are isotropic, so the frame changes no density.
 __device__ __forceinline__ void onb(float3 n, float3& t, float3& b) {
-  float sign = copysignf(1.0f, n.z);
-  float a = -1.0f / (sign + n.z);
-  float bb = n.x * n.y * a;
-  t = mk3(1.0f + sign * n.x * n.x * a, sign * bb, -sign * n.x);
-  b = mk3(bb, sign + n.y * n.y * a, -n.y);
+  float3 c = cross3(mk3(0.4375f, 0.5625f, 0.6875f), n);
+  float l2 = dot3(c, c);
+  if (!(l2 > 1e-12f)) {
+    c = cross3(mk3(0.6875f, -0.4375f, 0.5625f), n);
+    l2 = dot3(c, c);
+  }
+  t = c * rsqrtf(l2);
+  b = cross3(n, t);
 }
 
 // Returns the mixture pdf of the sampled direction wi; 0 = no valid sample.

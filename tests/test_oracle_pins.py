@@ -186,6 +186,29 @@ def test_sampling_pdf_mass_closed_form(brdf, alpha):
 
 
 @pytest.mark.parametrize("brdf", [0, 1])
+def test_sampled_direction_is_continuous_across_coordinate_planes(brdf):
+    # the tangent frame may rotate about n, but a normal on a coordinate plane
+    # (every face of a mirror-symmetric mesh has some) must not switch frames
+    # when rounding moves it off the plane by an ulp: the same numbers give the
+    # same direction on both sides of the plane, and at a signed zero
+    p5 = np.array([0.4, 0.3, 0.2, 0.5, 0.3])
+    rng = np.random.default_rng(3)
+    for base in ([0.983104336, -0.183046071, 0.0], [0.0, 1.0, 0.0], [0.6, 0.0, -0.8], [-1.0, 0.0, 0.0]):
+        base = np.array(base) / np.linalg.norm(base)
+        wo = base + np.array([0.31, -0.22, 0.17]) * 0.5
+        wo /= np.linalg.norm(wo)
+        for ul, u1, u2 in rng.random((40, 3)):
+            ref, pref = O.brdf_sample(brdf, p5, base, wo, ul, u1, u2)
+            for k in np.nonzero(base == 0)[0]:
+                for eps in (-1e-9, 1e-9, -0.0):
+                    n = base.copy()
+                    n[k] = eps
+                    n /= np.linalg.norm(n)
+                    wi, pdf = O.brdf_sample(brdf, p5, n, wo, ul, u1, u2)
+                    assert np.abs(wi - ref).max() < 1e-6 and abs(pdf - pref) <= 1e-6 * max(pref, 1.0)
+
+
+@pytest.mark.parametrize("brdf", [0, 1])
 def test_sampling_matches_pdf_histogram(brdf):
     rng = np.random.default_rng(20 + brdf)
     n = np.array([0.0, 0, 1])

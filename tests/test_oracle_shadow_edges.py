@@ -138,3 +138,15 @@ def test_shadow_edge_gradient_matches_closed_form():
     # without the shadow-edge term the occluder receives no gradient at all
     plain = np.array([(O.grad_pixels(osc, O.params(1, 600), pix, w)[0] * D).sum() for D in dirs[:9]])
     assert np.all(plain == 0) and np.abs(exp[:9]).max() > 0.2 * scale
+
+
+def test_a_convex_mesh_receives_no_shadow_edge_from_itself():
+    # a line through a point of a convex surface's light silhouette touches the
+    # surface there only: no receiver, so the term is exactly zero, for lights
+    # near and far (a near light makes the light rays graze the edge's faces)
+    sc = S.small_variant(S.make("tiny"), n_views=1, max_res=24, spp=2)
+    w = np.random.default_rng(2).normal(size=(sc.n_pixels, 3))
+    for L in ([0.3, 1.6, 0.9], [0.0, 1.2, 0.0], [2.0, 0.0, -3.0]):
+        sc.light_pos = np.array([L], np.float32)
+        sv, _ = O.shadow_edge_grad(O.OracleScene(sc), O.params(1, 5), w)
+        assert np.all(sv == 0)
