@@ -61,6 +61,7 @@ typedef enum {
 #define ST_BVH_LBVH 1   /* Karras radix tree over the Morton order: faster build */
 #define ST_EDGE_TERM_PRIMARY 1    /* edge_term bit: primary visibility (image-space edges) */
 #define ST_EDGE_TERM_SECONDARY 2  /* edge_term bit: secondary visibility (edges seen from path vertices) */
+#define ST_EDGE_TERM_SHADOW 4     /* edge_term bit: point-light shadow boundaries on surfaces the camera sees */
 #define ST_MODE_BATCHED 0     /* all views in one job space, persistent kernels, optional CUDA graph */
 #define ST_MODE_PER_VIEW 1    /* one view at a time, grids sized from host-read queue counts */
 
@@ -121,7 +122,7 @@ typedef struct {
 } st_scene_desc;
 
 typedef struct {
-  int edge_term;    /* backward: OR of ST_EDGE_TERM_PRIMARY and ST_EDGE_TERM_SECONDARY (0 = interior only) */
+  int edge_term;    /* backward: OR of ST_EDGE_TERM_PRIMARY, _SECONDARY and _SHADOW (0 = interior only) */
   int edge_mode;    /* ST_EDGE_SILHOUETTE or ST_EDGE_ALL (silhouettes as seen from the camera, or from each
                        path vertex for the secondary term) */
   int edge_spp;     /* edge samples per pixel; 0 = the view's spp */
@@ -191,7 +192,11 @@ st_status st_render(st_scene* scene, const st_view* views, int n_views, int defa
  * edge term (opts->edge_term) samples visibility edges: in screen space
  * (primary) and, at every vertex of every camera path, on the vertex's sphere
  * of directions (secondary: one uniformly picked mesh edge per vertex, two
- * side paths continuing from the next vertex). Either gradient pointer may be
+ * side paths continuing from the next vertex), and, for every point light of
+ * every view, along the image of the light's shadow boundary on the surfaces
+ * the camera sees (shadow: an edge that is a silhouette seen from the light, a
+ * point on it, the light ray through it continued to the receiving surface,
+ * camera paths on both sides of that point's image). Either gradient pointer may be
  * NULL to skip it (d_vertices may not be NULL with edge_term). */
 st_status st_render_backward(st_scene* scene, const st_view* views, int n_views, int default_spp,
                              int max_bounces, unsigned long long seed, const st_render_opts* opts,

@@ -217,6 +217,8 @@ struct Plan {
   long long pixels = 0;       // sum of W*H: the primary-visibility bin space
   bool interior = false, edges = false;
   bool sec = false;           // secondary-visibility edge samples at every camera-path vertex
+  bool shadow = false;        // point-light shadow-edge samples
+  std::vector<int2> pairs;    // shadow edges: (view, light) of each candidate list
   bool sig = false;           // forward: path signatures
   int max_vl = 0;             // most point lights a view of the call adds to the scene's
   bool bins = false;          // build primary-visibility bins (worth it only for many primary rays)
@@ -235,7 +237,7 @@ void free_engine(Engine& e) {
   dfree(e.o); dfree(e.d); dfree(e.thr); dfree(e.rad); dfree(e.ctr); dfree(e.hit); dfree(e.origin); dfree(e.brange);
   dfree(e.q0); dfree(e.q1); dfree(e.qs); dfree(e.sh_dir); dfree(e.sh_c);
   dfree(e.r0); dfree(e.r1); dfree(e.r2); dfree(e.r3); dfree(e.esc); dfree(e.nb); dfree(e.cnt); dfree(e.stat);
-  dfree(e.sj); dfree(e.sje); dfree(e.pinj); dfree(e.sig);
+  dfree(e.sj); dfree(e.sje); dfree(e.pinj); dfree(e.sig); dfree(e.shr);
   e = Engine();
 }
 
@@ -245,15 +247,16 @@ void drop_graphs(st_scene* s) {
   s->graphs.clear();
 }
 
-st_status ensure_engine(st_scene* s, int Q, int B, int NS, bool records, bool sec) {
+st_status ensure_engine(st_scene* s, int Q, int B, int NS, bool records, bool sec, bool shadow) {
   Engine& e = s->eng;
   if (e.Q >= Q && e.NS >= NS && (!records || (e.records && e.B >= B)) &&
-      (!sec || e.sec_cap >= (long long)e.B * e.Q))
+      (!sec || e.sec_cap >= (long long)e.B * e.Q) && (!shadow || e.shadow))
     return ST_OK;
   // grow: keep the larger of old and new sizes so alternating calls do not thrash
   int nQ = std::max(Q, e.Q), nNS = std::max(NS, e.NS), nB = std::max(B, e.B);
   bool nrec = records || e.records;
   bool nsec = sec || e.sec_cap > 0;
+  bool nshadow = shadow || e.shadow;
   cudaDeviceSynchronize();
   drop_graphs(s);
   free_engine(e);
@@ -273,6 +276,7 @@ st_status ensure_engine(st_scene* s, int Q, int B, int NS, bool records, bool se
   if (nsec) {
     chk(dalloc(&e.sj, 4 * q * nB, &acc)); chk(dalloc(&e.sje, q * nB, &acc)); chk(dalloc(&e.pinj, q * nB, &acc));
   }
+  if (nshadow) chk(dalloc(&e.shr, 3 * q, &acc));
   chk(dalloc(&e.sig, q, &acc));
   chk(dalloc(&e.cnt, CNT_SIZE, &acc));
   chk(dalloc(&e.stat, STAT_SIZE, &acc));
@@ -283,6 +287,7 @@ st_status ensure_engine(st_scene* s, int Q, int B, int NS, bool records, bool se
   }
   e.Q = nQ; e.B = nB; e.NS = nNS; e.records = nrec; e.bytes = acc;
   e.sec_cap = nsec ? (long long)nB * nQ : 0;
+  e.shadow = nshadow;
   return ST_OK;
 }
 
@@ -344,6 +349,7 @@ KCtx make_ctx(st_scene* s, const Plan& p) {
   c.env = s->env; c.brdf = s->brdf; c.res = s->res; c.ntex = s->ntex; c.np = s->np;
   c.edge_v = s->edge_v; c.edge_f = s->edge_f; c.n_edges = s->n_edges; c.edge_mode = p.o.edge_mode;
   c.edge_flag = s->edge_flag; c.edge_cand = s->edge_cand; c.edge_ncand = s->edge_ncand;
+  c.sh_cand = s->sh_cand; c.sh_ncand = s->sh_ncand;
   c.bin_start = p.bins ? s->bin_start : nullptr;   // nullptr: every primary ray traverses the BVH
   c.bin_list = s->bin_list; c.bin_cur = s->bin_cur; c.bin_ok = s->bin_ok;
   c.bin_cap = s->bin_cap; c.bin_pixels = p.pixels;
@@ -372,6 +378,13 @@ cudaEvent_t next_event(st_scene* s, bool start) {
   auto& pr = s->ev[s->ev_used];
   if (!start) s->ev_used++;
   return start ? pr.first : pr.second;
+}
+
+// Does any segment of kind k overlap [a, b)?
+bool overlaps(const Plan& p, int kind, long long a, long long b) {
+  for (auto& sg : p.segs)
+    if (sg.kind == kind && sg.base < b && sg.base + sg.count > a) return true;
+  return false;
 }
 
 // Enqueue one chunk [j0, j0 + n) of the job space. host_sized: read the queue
@@ -422,6 +435,8 @@ st_status run_chunk(st_scene* s, const Plan& p, const KCtx& c, long long j0, int
     return ST_OK;
   };
   k_reset<<<1, 128, 0, st>>>(cnt);
+  bool has_shadow = p.shadow && overlaps(p, 2, j0, j0 + n);
+  if (has_shadow) { k_sh_prep<<<(n + EXT_BLOCK - 1) / EXT_BLOCK, EXT_BLOCK, 0, st>>>(c, j0, n); s->launches++; }
   k_raygen<<<(n + 255) / 256, 256, 0, st>>>(c, j0, n);
   s->launches += 2;
   st_status r = bounces(c, p.B);
@@ -432,6 +447,7 @@ st_status run_chunk(st_scene* s, const Plan& p, const KCtx& c, long long j0, int
   } else {
     int ga = (n + ADJ_BLOCK - 1) / ADJ_BLOCK;
     if (has_edge) { k_edge_resolve<<<ga, ADJ_BLOCK, 0, st>>>(c, j0, n); s->launches++; }
+    if (has_shadow) { k_sh_resolve<<<(n + 255) / 256, 256, 0, st>>>(c, j0, n); s->launches++; }
     if (has_cam && p.sec) {
       // secondary edge samples: jobs from the recorded vertices, then their side
       // paths in passes of Q slots (records off: they stay the camera paths'),
@@ -465,12 +481,6 @@ st_status run_chunk(st_scene* s, const Plan& p, const KCtx& c, long long j0, int
   return ST_OK;
 }
 
-// Does any segment of kind k overlap [a, b)?
-bool overlaps(const Plan& p, int kind, long long a, long long b) {
-  for (auto& sg : p.segs)
-    if (sg.kind == kind && sg.base < b && sg.base + sg.count > a) return true;
-  return false;
-}
 
 st_status enqueue_call(st_scene* s, const Plan& p, int Q, cudaStream_t st, bool host_sized, bool timing) {
   KCtx c = make_ctx(s, p);
@@ -495,6 +505,15 @@ st_status enqueue_call(st_scene* s, const Plan& p, int Q, cudaStream_t st, bool 
     k_bin<1><<<g, 128, 0, st>>>(c, nv, s->bin_ok);
     ST_CUDA(cudaMemcpyAsync(s->bin_total_host, s->bin_start + P, sizeof(int), cudaMemcpyDeviceToHost, st));
     s->launches += 6;
+  }
+  if (p.shadow && !p.pairs.empty()) {
+    int np = (int)p.pairs.size();
+    dim3 g((s->n_edges + 255) / 256, (unsigned)np);
+    k_sh_flags<<<g, 256, 0, st>>>(c, s->d_pairs, np, s->sh_flag);
+    KCtx cc = c;   // the ordered compaction of the primary candidates, on the shadow tables
+    cc.edge_flag = s->sh_flag; cc.edge_cand = s->sh_cand; cc.edge_ncand = s->sh_ncand;
+    k_edge_compact<<<(unsigned)np, 1024, 0, st>>>(cc);
+    s->launches += 2;
   }
   if (p.edges) {
     dim3 g((s->n_edges + 255) / 256, (unsigned)p.views.size());
@@ -532,7 +551,9 @@ std::vector<long long> graph_key(const Plan& p, int Q, const st_scene* s) {
   std::vector<long long> k = {p.kind, p.B, (long long)p.views.size(), Q, p.o.edge_term, p.o.edge_mode, p.o.edge_spp,
                               p.interior, p.edges, p.o.count_visits, p.bins,
                               p.o.persist_blocks, s->bin_cap, p.max_vl, p.sig};
-  for (auto& v : p.views) { k.push_back(v.W); k.push_back(v.H); k.push_back(v.spp); k.push_back(v.pix_off); }
+  for (auto& v : p.views) {
+    k.push_back(v.W); k.push_back(v.H); k.push_back(v.spp); k.push_back(v.pix_off); k.push_back(v.nvl);
+  }
   return k;
 }
 
@@ -547,12 +568,13 @@ st_status plan_call(st_scene* s, const st_view* views, int n_views, int default_
   if (p.o.edge_mode != ST_EDGE_SILHOUETTE && p.o.edge_mode != ST_EDGE_ALL) return fail(ST_ERR_INVALID_ARG, "bad edge_mode");
   if (p.o.edge_spp < 0 || p.o.chunk_paths < 0 || p.o.persist_blocks < 0)
     return fail(ST_ERR_INVALID_ARG, "negative option");
-  if (p.o.edge_term < 0 || p.o.edge_term > (ST_EDGE_TERM_PRIMARY | ST_EDGE_TERM_SECONDARY))
+  if (p.o.edge_term < 0 || p.o.edge_term > (ST_EDGE_TERM_PRIMARY | ST_EDGE_TERM_SECONDARY | ST_EDGE_TERM_SHADOW))
     return fail(ST_ERR_INVALID_ARG, "bad edge_term");
   p.sig = kind == 0 && p.o.path_signatures != nullptr;
   p.interior = kind == 1 && want_interior;
   p.edges = kind == 1 && (p.o.edge_term & ST_EDGE_TERM_PRIMARY);
   p.sec = p.interior && (p.o.edge_term & ST_EDGE_TERM_SECONDARY) && s->n_edges > 0;
+  p.shadow = kind == 1 && (p.o.edge_term & ST_EDGE_TERM_SHADOW) && s->n_edges > 0;
   long long base = 0;
   for (int i = 0; i < n_views; ++i) {
     const st_view& v = views[i];
@@ -585,6 +607,15 @@ st_status plan_call(st_scene* s, const st_view* views, int n_views, int default_
       p.segs.push_back(sg);
       base += sg.count;
     }
+    if (p.shadow) {
+      long long ne = (long long)v.width * v.height * (p.o.edge_spp > 0 ? p.o.edge_spp : spp);
+      for (int l = 0; l < s->nl + v.n_lights; ++l) {
+        Seg sg{base, (ne + 31) / 32 * 64, i, 2, ne, l, (int)p.pairs.size()};
+        p.pairs.push_back(make_int2(i, l));
+        p.segs.push_back(sg);
+        base += sg.count;
+      }
+    }
     p.view_range.push_back({start, base});
   }
   p.total = base;
@@ -610,6 +641,19 @@ st_status plan_call(st_scene* s, const st_view* views, int n_views, int default_
 st_status run_call(st_scene* s, Plan& p, const CallArgs& args, cudaStream_t st) {
   st_status r = ensure_tables(s, (int)p.views.size(), (int)p.segs.size(), p.edges);
   if (r != ST_OK) return r;
+  if (p.shadow && (int)p.pairs.size() > s->sh_cap_pairs) {
+    cudaDeviceSynchronize();
+    drop_graphs(s);
+    dfree(s->sh_flag); dfree(s->sh_cand); dfree(s->sh_ncand); dfree(s->d_pairs);
+    size_t n = p.pairs.size() * (size_t)std::max(s->n_edges, 1);
+    if (dalloc(&s->sh_flag, n) != cudaSuccess || dalloc(&s->sh_cand, n) != cudaSuccess ||
+        dalloc(&s->sh_ncand, p.pairs.size()) != cudaSuccess || dalloc(&s->d_pairs, p.pairs.size()) != cudaSuccess) {
+      cudaGetLastError();
+      s->sh_cap_pairs = 0;
+      return fail(ST_ERR_OOM, "shadow-edge tables");
+    }
+    s->sh_cap_pairs = (int)p.pairs.size();
+  }
   if (p.bins) {
     r = ensure_bins(s, p);
     if (r != ST_OK) return r;
@@ -636,10 +680,12 @@ st_status run_call(st_scene* s, Plan& p, const CallArgs& args, cudaStream_t st) 
     Q = (int)std::min<long long>(Q, (mx + SEG_ALIGN - 1) / SEG_ALIGN * SEG_ALIGN);
   }
   int NS = s->nl + p.max_vl + (s->env.w > 0 ? 1 : 0);
-  r = ensure_engine(s, Q, p.B, NS, p.kind == 1, p.sec);
+  r = ensure_engine(s, Q, p.B, NS, p.kind == 1, p.sec, p.shadow);
   if (r != ST_OK) return r;
   ST_CUDA(cudaMemcpyAsync(s->d_views, p.views.data(), sizeof(DevView) * p.views.size(), cudaMemcpyHostToDevice, st));
   ST_CUDA(cudaMemcpyAsync(s->d_segs, p.segs.data(), sizeof(Seg) * p.segs.size(), cudaMemcpyHostToDevice, st));
+  if (p.shadow && !p.pairs.empty())
+    ST_CUDA(cudaMemcpyAsync(s->d_pairs, p.pairs.data(), sizeof(int2) * p.pairs.size(), cudaMemcpyHostToDevice, st));
   ST_CUDA(cudaMemcpyAsync(s->d_args, &args, sizeof(CallArgs), cudaMemcpyHostToDevice, st));
   bool timing = p.o.time_kernels != 0;
   s->ev_used = 0;
@@ -694,7 +740,8 @@ void destroy(st_scene* s) {
   dfree(s->flags); dfree(s->keys); dfree(s->keys2); dfree(s->ids); dfree(s->ids2); dfree(s->hist); dfree(s->bounds);
   dfree(s->nodes4); dfree(s->src4); dfree(s->q4); dfree(s->c4);
   dfree(s->lights); dfree(s->env_tex); dfree(s->env_alias); dfree(s->edge_v); dfree(s->edge_f);
-  dfree(s->edge_flag); dfree(s->edge_cand); dfree(s->edge_ncand); dfree(s->d_views); dfree(s->d_segs);
+  dfree(s->edge_flag); dfree(s->edge_cand); dfree(s->edge_ncand);
+  dfree(s->sh_flag); dfree(s->sh_cand); dfree(s->sh_ncand); dfree(s->d_pairs); dfree(s->d_views); dfree(s->d_segs);
   dfree(s->bin_start); dfree(s->bin_cur); dfree(s->bin_list); dfree(s->bin_ok); dfree(s->bin_part);
   dfree(s->acc); dfree(s->sacc); dfree(s->mstat);
   if (s->bin_total_host) cudaFreeHost(s->bin_total_host);

@@ -36,8 +36,9 @@ struct CallArgs {
 // edge-sample sides of one view.
 struct Seg {
   long long base, count;
-  int view, kind;           // kind 0 = camera paths, 1 = edge sides (two jobs per sample)
-  long long n_samples;      // kind 1: N_e; kind 0: W*H*spp
+  int view, kind;           // kind 0 = camera paths, 1 = edge sides, 2 = shadow-edge sides (two jobs per sample)
+  long long n_samples;      // kinds 1, 2: samples; kind 0: W*H*spp
+  int light, pair;          // kind 2: the view's light and its (view, light) candidate list
 };
 
 // Device pointers of the wavefront engine (one chunk of Q path slots).
@@ -60,6 +61,9 @@ struct Engine {
   float4* sj = nullptr;       // [4][sec_cap]: (p, face), (w, weight), (m, tau), (dL/dI * T, edge)
   int4* sje = nullptr;        // [sec_cap]: (camera counter c0, sample, camera slot, vertex)
   float4* pinj = nullptr;     // [B][Q]: adjoint of each vertex position from its edge sample
+  float4* shr = nullptr;      // [3][Q] shadow-edge samples, at the slot of their minus side:
+                              // (S, n_S), (q, receiver face), (tau, edge, weight factor, s); S.x NaN = none
+  bool shadow = false;
   int* cnt = nullptr;         // counters, see CNT_*
   unsigned long long* stat = nullptr;  // per-call 64-bit statistics, see STAT_*
   long long bytes = 0;
@@ -120,6 +124,11 @@ struct st_scene {
   int* edge_cand = nullptr;      // [views * E]
   int* edge_ncand = nullptr;     // [views]
   int edge_cap_views = 0;
+  int* sh_flag = nullptr;        // [pairs * E] light-silhouette flags per (view, light)
+  int* sh_cand = nullptr;        // [pairs * E] their ordered compaction
+  int* sh_ncand = nullptr;       // [pairs]
+  int2* d_pairs = nullptr;       // [pairs] (view, light)
+  int sh_cap_pairs = 0;
   // primary-visibility bins: per view pixel, the leaves whose screen box covers it
   int* bin_start = nullptr;      // [P + 1] exclusive prefix of the counts
   int* bin_cur = nullptr;        // [P] counts, then fill cursors

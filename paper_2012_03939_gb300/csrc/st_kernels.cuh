@@ -40,6 +40,8 @@ struct KCtx {
   int* edge_flag;
   int* edge_cand;
   int* edge_ncand;
+  const int* sh_cand;     // shadow edges: candidate lists per (view, light) pair
+  const int* sh_ncand;
   const int* bin_start;   // primary-visibility bins (see k_bin)
   const int* bin_list;    // leaf indices per pixel
   int* bin_cur;
@@ -236,6 +238,97 @@ __global__ void k_edge_compact(KCtx c) {
   for (int i = b; i < en; ++i)
     if (fl[i]) out[run++] = i;
   if (threadIdx.x == 1023) c.edge_ncand[vi] = part[1023];
+}
+
+// ------------------------------------------------------------------ shadow edges (point lights)
+// A point light's shadow on a visible surface ends where light rays graze the
+// edges that are silhouettes seen from the light. Per (view, light) pair the
+// candidates are those edges (or boundary edges) in edge order; sample k picks
+// candidate t / N for t uniform in [k n, (k+1) n) and tau uniform on the edge
+// (counter (k, pixel_offset, light<<4, 3)); the light ray through y = A +
+// tau (B - A), continued from y + SH_EDGE_DELTA |y - L| along it, finds the
+// receiver point q = L + s (y - L) on a face other than the edge's own; its
+// image S, the screen normal n_S of the
+// boundary curve S(tau) (dS/dtau = J_proj(q) s P (B - A), P = I - u n_r^T /
+// n_r.u, u = y - L) and |dS/dtau| define the two camera paths at S -+ EDGE_EPS
+// n_S. The boundary's screen-normal speed n_S . J_proj(q) dq moves it with the
+// edge (dq = s P dy) and with the receiver plane (dq = u ds).
+constexpr float SH_EDGE_DELTA = 1e-4f;
+
+__global__ void k_sh_flags(KCtx c, const int2* pairs, int n_pairs, int* flag) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  int pi = blockIdx.y;
+  if (e >= c.n_edges || pi >= n_pairs) return;
+  int2 pr = pairs[pi];
+  float4 lp, li;
+  point_light(c, pr.x, pr.y, lp, li);
+  int2 ef = c.edge_f[e];
+  bool cand = ef.y < 0 || facing(c, ef.x, xyz(lp)) != facing(c, ef.y, xyz(lp));
+  flag[(size_t)pi * c.n_edges + e] = cand ? 1 : 0;
+}
+
+// Shadow-edge sample of each minus-side slot of the chunk (kind 2), stored at
+// that slot for raygen and resolve; S.x = NaN marks no sample.
+__global__ void __launch_bounds__(EXT_BLOCK) k_sh_prep(KCtx c, long long j0, int n) {
+  __shared__ int sstack[TRACE_SH * EXT_BLOCK];
+  const Engine& E = c.e;
+  const size_t Q = (size_t)E.Q;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  long long job = j0 + i;
+  int si = find_seg(c.segs, c.n_segs, job);
+  if (si < 0) return;
+  Seg sg = c.segs[si];
+  long long local = job - sg.base;
+  if (sg.kind != 2 || local >= sg.count || (local & 32)) return;
+  const float NaN = __int_as_float(0x7fc00000);
+  E.shr[i] = make_float4(NaN, 0, 0, 0);
+  long long k = (local >> 6) * 32 + (local & 31);
+  if (k >= sg.n_samples) return;
+  int nc = c.sh_ncand[sg.pair];
+  if (nc <= 0) return;
+  DevView v = c.views[sg.view];
+  Key key{c.args->k0, c.args->k1};
+  U4 u = philox((uint32_t)k, v.off, (uint32_t)sg.light << 4, 3u, key.k0, key.k1);
+  uint64_t t = (uint64_t)k * (uint64_t)nc + (((uint64_t)(u.x >> 8) * (uint64_t)nc) >> 24);
+  int e = c.sh_cand[(size_t)sg.pair * c.n_edges + (int)(t / (uint64_t)sg.n_samples)];
+  float tau = unif(u.y);
+  float4 lp, li;
+  point_light(c, sg.view, sg.light, lp, li);
+  float3 L = xyz(lp);
+  int2 ev = c.edge_v[e];
+  float3 A = fetch_vertex(c.V, ev.x), Bv = fetch_vertex(c.V, ev.y);
+  float3 y = A + (Bv - A) * tau;
+  float3 uv = y - L;
+  float dy = len3(uv);
+  if (!(dy > 0.0f)) return;
+  float3 dir = uv * (1.0f / dy);
+  float3 org = y + dir * (SH_EDGE_DELTA * dy);
+  // the edge's own faces meet that ray only at y: they receive no shadow from it
+  int2 ef = c.edge_f[e];
+  float th;
+  int leaf = -1;
+  int rf = trace_bvh<false, false, true>(c.nodes, c.tri, c.nf, org, dir, __int_as_float(0x7f800000), ef.x, th,
+                                         sstack + threadIdx.x, c.err, nullptr, &leaf, ef.y);
+  if (rf < 0) return;
+  float3 q = org + dir * th;
+  float sx, sy;
+  if (!cam_project(v, q, sx, sy)) return;
+  if (!(sx >= 0.0f && sy >= 0.0f && sx < (float)v.W && sy < (float)v.H)) return;
+  float3 r0 = fetch_vertex(c.V, c.F[3 * rf]), r1 = fetch_vertex(c.V, c.F[3 * rf + 1]),
+         r2 = fetch_vertex(c.V, c.F[3 * rf + 2]);
+  float3 nr = cross3(r1 - r0, r2 - r0);
+  float nu = dot3(nr, uv);
+  if (!(fabsf(nu) > 0.0f)) return;
+  float sc = len3(q - L) / dy;
+  float3 ab = Bv - A;
+  float3 dq = (ab - uv * (dot3(nr, ab) / nu)) * sc;
+  float tx = dot3(cam_project_jt(v, q, 1.0f, 0.0f), dq), ty = dot3(cam_project_jt(v, q, 0.0f, 1.0f), dq);
+  float lt = sqrtf(tx * tx + ty * ty);
+  if (!(lt > 0.0f)) return;
+  E.shr[i] = make_float4(sx, sy, -ty / lt, tx / lt);
+  E.shr[Q + i] = make_float4(q.x, q.y, q.z, __int_as_float(rf));
+  E.shr[2 * Q + i] = make_float4(tau, __int_as_float(e), (float)nc * lt / (float)sg.n_samples, sc);
 }
 
 // ------------------------------------------------------------------ primary-visibility bins
@@ -495,6 +588,19 @@ __global__ void k_raygen(KCtx c, long long j0, int n) {
           ct = make_int4((int)c0, s, 0, sg.view << 4);
           br = bin_range(c, sg.view, v, x, y);
           ok = true;
+        } else if (sg.kind == 2) {
+          // shadow-edge sides: the sample is stored at the block's minus slot
+          float4 r = E.shr[i - ((local & 32) ? 32 : 0)];
+          if (r.x == r.x) {
+            float sg2 = (local & 32) ? EDGE_EPS : -EDGE_EPS;
+            float sx = r.x + sg2 * r.z, sy = r.y + sg2 * r.w;
+            long long k = (local >> 6) * 32 + (local & 31);
+            d = cam_dir(v, sx, sy);
+            o = v.eye;
+            br = bin_range(c, sg.view, v, (int)floorf(sx), (int)floorf(sy));
+            ct = make_int4((int)(uint32_t)k, (int)v.off, 4 + sg.light, sg.view << 4);
+            ok = true;
+          }
         } else {
           // block of 64 jobs: minus sides of samples 32b..32b+31, then their plus sides
           long long k = (local >> 6) * 32 + (local & 31);
@@ -1263,6 +1369,58 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_sec_resolve(KCtx c, int pass) {
 
 __global__ void k_reset_pass(int* cnt) {
   for (int i = threadIdx.x; i < CNT_MISC; i += blockDim.x) cnt[i] = 0;
+}
+
+// (L- - L+) of each shadow-edge sample: the edge's endpoints move the boundary
+// through the light ray (s P^T js), the receiver's vertices through its plane
+// (u ds), js = J_proj(q)^T n_S.
+__global__ void k_sh_resolve(KCtx c, long long j0, int n) {
+  const Engine& E = c.e;
+  const size_t Q = (size_t)E.Q;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  long long job = j0 + i;
+  int si = find_seg(c.segs, c.n_segs, job);
+  if (si < 0) return;
+  Seg sg = c.segs[si];
+  long long local = job - sg.base;
+  if (sg.kind != 2 || local >= sg.count || (local & 32)) return;
+  float4 r0 = E.shr[i];
+  if (!(r0.x == r0.x)) return;
+  DevView v = c.views[sg.view];
+  int px = (int)floorf(r0.x), py = (int)floorf(r0.y);
+  const float* gp = c.args->dLdI + 3 * (v.pix_off + (long long)py * v.W + px);
+  float3 Lm = xyz(E.rad[i]), Lp = xyz(E.rad[i + 32]);
+  float g = gp[0] * (Lm.x - Lp.x) + gp[1] * (Lm.y - Lp.y) + gp[2] * (Lm.z - Lp.z);
+  if (g == 0.0f) return;
+  float4 r1 = E.shr[Q + i], r2 = E.shr[2 * Q + i];
+  float wt = g * r2.z;
+  float tau = r2.x, sc = r2.w;
+  int e = __float_as_int(r2.y), rf = __float_as_int(r1.w);
+  float3 q = xyz(r1);
+  float4 lp, li;
+  point_light(c, sg.view, sg.light, lp, li);
+  float3 L = xyz(lp);
+  int2 ev = c.edge_v[e];
+  float3 A = fetch_vertex(c.V, ev.x), Bv = fetch_vertex(c.V, ev.y);
+  float3 uv = A + (Bv - A) * tau - L;
+  int f0 = c.F[3 * rf], f1 = c.F[3 * rf + 1], f2 = c.F[3 * rf + 2];
+  float3 v0 = fetch_vertex(c.V, f0), v1 = fetch_vertex(c.V, f1), v2 = fetch_vertex(c.V, f2);
+  float3 e1 = v1 - v0, e2 = v2 - v0, nr = cross3(e1, e2);
+  float nu = dot3(nr, uv);
+  float3 js = cam_project_jt(v, q, r0.z, r0.w);
+  float3 pj = (js - nr * (dot3(uv, js) / nu)) * (wt * sc);
+  float* dV = c.args->dV;
+  float3 ga = pj * (1.0f - tau), gb = pj * tau;
+  atomicAdd(&dV[3 * ev.x], ga.x); atomicAdd(&dV[3 * ev.x + 1], ga.y); atomicAdd(&dV[3 * ev.x + 2], ga.z);
+  atomicAdd(&dV[3 * ev.y], gb.x); atomicAdd(&dV[3 * ev.y + 1], gb.y); atomicAdd(&dV[3 * ev.y + 2], gb.z);
+  float kap = wt * dot3(js, uv) / nu;
+  float3 w = q - v0;
+  float3 c1 = cross3(e2, w), c2 = cross3(w, e1);
+  float3 g0 = (nr + c1 + c2) * kap, g1 = c1 * (-kap), g2 = c2 * (-kap);
+  atomicAdd(&dV[3 * f0], g0.x); atomicAdd(&dV[3 * f0 + 1], g0.y); atomicAdd(&dV[3 * f0 + 2], g0.z);
+  atomicAdd(&dV[3 * f1], g1.x); atomicAdd(&dV[3 * f1 + 1], g1.y); atomicAdd(&dV[3 * f1 + 2], g1.z);
+  atomicAdd(&dV[3 * f2], g2.x); atomicAdd(&dV[3 * f2 + 1], g2.y); atomicAdd(&dV[3 * f2 + 2], g2.z);
 }
 
 // closest-hit queries for st_trace_closest

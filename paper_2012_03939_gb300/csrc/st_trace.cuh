@@ -39,15 +39,16 @@ __device__ __forceinline__ float box_hit(float lx, float hx, float ly, float hy,
 }
 
 // ANY = stop at the first hit (shadow rays). Returns the face id or -1; t in
-// tbest; the hit's leaf index in *leaf_out if given.
+// tbest; the hit's leaf index in *leaf_out if given. EX2 = a second face
+// (exclude2) is skipped too.
 // nodes = the 4-wide tree: per node lo.x, hi.x, lo.y, hi.y, lo.z, hi.z (one
 // float4 of four children each) and the four child links (>= 0 node, < 0 leaf
 // ~i, INT_MIN empty). Hit leaves are tested at once; hit internal children are
 // sorted by entry distance, the nearest is visited next, the others pushed.
-template <bool ANY, bool STATS>
+template <bool ANY, bool STATS, bool EX2 = false>
 __device__ __forceinline__ int trace_bvh(const float4* __restrict__ nodes, const float4* __restrict__ tri, int nf,
                                          float3 o, float3 d, float tmax, int exclude, float& tbest, int* sstack,
-                                         int* err, TraceStats* ts, int* leaf_out = nullptr) {
+                                         int* err, TraceStats* ts, int* leaf_out = nullptr, int exclude2 = -1) {
   RayPre rp = ray_pre(o, d);
   float3 inv = safe_inv(d);
   int best = -1, best_leaf = -1;
@@ -57,7 +58,7 @@ __device__ __forceinline__ int trace_bvh(const float4* __restrict__ nodes, const
     float4 a = __ldg(&tri[3 * li]);
     int fid = __float_as_int(a.w);
     if (STATS) ts->tests++;
-    if (fid == exclude) return false;
+    if (fid == exclude || (EX2 && fid == exclude2)) return false;
     float4 b = __ldg(&tri[3 * li + 1]);
     float4 c = __ldg(&tri[3 * li + 2]);
     float t = tri_test(rp, xyz(a), xyz(b), xyz(c), ANY ? tmax : tbest * 1.0000001f + 1e-30f);

@@ -23,7 +23,7 @@ STATUS = {0: "ST_OK", 1: "ST_ERR_INVALID_ARG", 2: "ST_ERR_OOM", 3: "ST_ERR_CUDA"
           5: "ST_ERR_STATE", 6: "ST_ERR_UNSUPPORTED", 7: "ST_ERR_DEVICE"}
 MODE_BATCHED, MODE_PER_VIEW = 0, 1
 EDGE_SILHOUETTE, EDGE_ALL = 0, 1
-EDGE_TERM_PRIMARY, EDGE_TERM_SECONDARY = 1, 2
+EDGE_TERM_PRIMARY, EDGE_TERM_SECONDARY, EDGE_TERM_SHADOW = 1, 2, 4
 BVH_PLOC, BVH_LBVH = 0, 1
 
 EXPORTED = ["st_scene_create", "st_scene_destroy", "st_refit", "st_rebuild", "st_set_face_params", "st_render",
