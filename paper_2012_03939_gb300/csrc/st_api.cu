@@ -437,7 +437,8 @@ st_status run_chunk(st_scene* s, const Plan& p, const KCtx& c, long long j0, int
   k_reset<<<1, 128, 0, st>>>(cnt);
   bool has_shadow = p.shadow && overlaps(p, 2, j0, j0 + n);
   if (has_shadow) { k_sh_prep<<<(n + EXT_BLOCK - 1) / EXT_BLOCK, EXT_BLOCK, 0, st>>>(c, j0, n); s->launches++; }
-  k_raygen<<<(n + 255) / 256, 256, 0, st>>>(c, j0, n);
+  if (has_shadow) k_raygen<true><<<(n + 255) / 256, 256, 0, st>>>(c, j0, n);
+  else k_raygen<false><<<(n + 255) / 256, 256, 0, st>>>(c, j0, n);
   s->launches += 2;
   st_status r = bounces(c, p.B);
   if (r != ST_OK) return r;
@@ -597,20 +598,21 @@ st_status plan_call(st_scene* s, const st_view* views, int n_views, int default_
     long long start = base;
     long long cam = (long long)v.width * v.height * spp;
     if (kind == 0 || p.interior) {
-      Seg sg{base, cam, i, 0, cam};
+      Seg sg{base, cam, i, 0, 0, 0, cam};
       p.segs.push_back(sg);
       base += (cam + SEG_ALIGN - 1) / SEG_ALIGN * SEG_ALIGN;
     }
     if (p.edges) {
       long long ne = (long long)v.width * v.height * (p.o.edge_spp > 0 ? p.o.edge_spp : spp);
-      Seg sg{base, (ne + 31) / 32 * 64, i, 1, ne};
+      Seg sg{base, (ne + 31) / 32 * 64, i, 1, 0, 0, ne};
       p.segs.push_back(sg);
       base += sg.count;
     }
     if (p.shadow) {
       long long ne = (long long)v.width * v.height * (p.o.edge_spp > 0 ? p.o.edge_spp : spp);
       for (int l = 0; l < s->nl + v.n_lights; ++l) {
-        Seg sg{base, (ne + 31) / 32 * 64, i, 2, ne, l, (int)p.pairs.size()};
+        if (p.pairs.size() >= (1u << 24)) return fail(ST_ERR_UNSUPPORTED, "too many (view, light) pairs");
+        Seg sg{base, (ne + 31) / 32 * 64, i, 2, (unsigned)l, (unsigned)p.pairs.size(), ne};
         p.pairs.push_back(make_int2(i, l));
         p.segs.push_back(sg);
         base += sg.count;

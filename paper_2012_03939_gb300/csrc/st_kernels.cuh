@@ -560,6 +560,9 @@ __global__ void k_reset(int* cnt) {
   for (int i = threadIdx.x; i < CNT_SIZE; i += blockDim.x) cnt[i] = 0;
 }
 
+// SH: the chunk holds shadow-edge side jobs (kind 2); chunks without them run
+// the variant without that branch, whose code is the hot path's.
+template <bool SH>
 __global__ void k_raygen(KCtx c, long long j0, int n) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   const Engine& E = c.e;
@@ -588,7 +591,7 @@ __global__ void k_raygen(KCtx c, long long j0, int n) {
           ct = make_int4((int)c0, s, 0, sg.view << 4);
           br = bin_range(c, sg.view, v, x, y);
           ok = true;
-        } else if (sg.kind == 2) {
+        } else if (SH && sg.kind == 2) {
           // shadow-edge sides: the sample is stored at the block's minus slot
           float4 r = E.shr[i - ((local & 32) ? 32 : 0)];
           if (r.x == r.x) {
