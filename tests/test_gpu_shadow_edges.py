@@ -114,3 +114,33 @@ def test_shadow_edges_do_not_depend_on_the_launch_path(st):
     ref = _gpu(st, sc, 2, 8, w, st.EDGE_TERM_SHADOW)
     for kw in [dict(use_graph=0), dict(chunk_paths=1024), dict(mode="per_view")]:
         assert rel_l2(_gpu(st, sc, 2, 8, w, st.EDGE_TERM_SHADOW, **kw), ref) <= 1e-5, kw
+
+
+def test_shadow_edges_in_a_binned_call_equal_the_views_traced_alone(st):
+    # six views of a closed torus knot under a point light: together they pass
+    # the 2^20 primary jobs that turn on the screen-space bins (back faces
+    # culled), alone each stays below and traverses the BVH; the knot's loops
+    # shadow one another, and every sample is the same in both
+    sc = S.make("env")
+    sc.light_pos = np.array([[0.4, 2.6, 1.2]], np.float32)
+    sc.light_intensity = np.full((1, 3), 8.0, np.float32)
+    sc.views = S.fibonacci_views(6, [160] * 6, [152] * 6, [4] * 6)
+    w = np.random.default_rng(9).normal(size=(sc.n_pixels, 3)).astype(np.float32)
+    scene = st.Scene.from_scene(sc)
+    et = st.EDGE_TERM_PRIMARY | st.EDGE_TERM_SHADOW
+    full = scene.backward(sc.views, 2, 17, torch.from_numpy(w).cuda(), st.make_opts(edge_term=et))
+    sh_full = full[0] - scene.backward(sc.views, 2, 17, torch.from_numpy(w).cuda(),
+                                       st.make_opts(edge_term=st.EDGE_TERM_PRIMARY))[0]
+    dv = torch.zeros_like(full[0])
+    df = torch.zeros_like(full[1])
+    for v in sc.views:
+        m = np.zeros_like(w)
+        rows = slice(v.pixel_offset, v.pixel_offset + v.width * v.height)
+        m[rows] = w[rows]
+        a, b = scene.backward([v], 2, 17, torch.from_numpy(m).cuda(), st.make_opts(edge_term=et))
+        dv += a
+        df += b
+    assert scene.stats()["device_error"] == 0
+    scene.close()
+    assert rel_l2([full[0].cpu().numpy(), full[1].cpu().numpy()], [dv.cpu().numpy(), df.cpu().numpy()]) <= 1e-5
+    assert sh_full.abs().max() > 0.05 * full[0].abs().max()
