@@ -33,7 +33,7 @@ class _Scene(C.Structure):
                 ("faces", C.c_void_p), ("face_params", C.c_void_p), ("brdf", C.c_int),
                 ("n_lights", C.c_int), ("light_pos", C.c_void_p), ("light_intensity", C.c_void_p),
                 ("env_width", C.c_int), ("env_height", C.c_int), ("env_rgb", C.c_void_p),
-                ("color_res", C.c_int), ("param_width", C.c_int)]
+                ("color_res", C.c_int), ("param_width", C.c_int), ("smooth_normals", C.c_int)]
 
 
 class _View(C.Structure):
@@ -116,7 +116,7 @@ class OracleScene:
                         0 if sc.brdf == "ggx" else 1, len(self.LP), _ptr(self.LP).value, _ptr(self.LI).value,
                         0 if self.E is None else self.E.shape[1], 0 if self.E is None else self.E.shape[0],
                         None if self.E is None else _ptr(self.E).value, int(getattr(sc, "color_res", 0)),
-                        self.P.shape[1])
+                        self.P.shape[1], int(bool(getattr(sc, "smooth_normals", False))))
         self.views = (_View * len(sc.views))()
         for i, v in enumerate(sc.views):
             lights = list(getattr(v, "lights", ()) or ())

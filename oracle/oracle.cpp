@@ -60,6 +60,7 @@
 #include "oracle.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -80,7 +81,7 @@ constexpr double SEC_BAND = 1e-5;    // secondary edge: plane-distance band, tim
 constexpr double SEC_RMIN = 1e-6;    // secondary edge: nearest edge point accepted
 constexpr double SEC_SMIN = 1e-6;    // secondary edge: sine of the edge/view angle accepted
 constexpr int MAX_B = 8;
-constexpr int MAXD = 24 * MAX_B;
+constexpr int MAXD = 64 * MAX_B;   // dual dimensions of one path (checked: see Vars)
 
 // ---------------------------------------------------------------- Philox
 struct U4 { uint32_t w[4]; };
@@ -206,6 +207,8 @@ struct Scene {
   std::vector<double> env;      // 3 per texel
   std::vector<double> prob, pmf;
   std::vector<int> alias;
+  bool smooth = false;          // interpolated shading normals
+  std::vector<int> vf_start, vf_list;   // faces around each vertex (CSR, face order)
 };
 
 // Point lights a path of one view sees: the scene's, then the view's own
@@ -496,7 +499,12 @@ struct Vars {
   std::vector<int> fid;   // face ids, 5 dims each
   std::vector<int> fdim;
   int nd = 0;
+  bool overflow = false;  // a variable found no room in MAXD: the path's gradient is incomplete
 };
+
+// set when any path of the current call overflowed its dual dimensions (the
+// call then reports an error instead of a partial gradient)
+std::atomic<bool> g_dual_overflow{false};
 
 template <class T> struct Access;
 
@@ -525,23 +533,31 @@ template <> struct Access<Dual> {
     int base = -1;
     for (size_t i = 0; i < vars->vid.size(); ++i)
       if (vars->vid[i] == v) base = vars->vdim[i];
+    const V3d& p = s.vert[v];
     if (base < 0) {
+      if (vars->nd + 3 > MAXD) { vars->overflow = true; return lift<Dual>(p); }
       base = vars->nd; vars->nd += 3;
       vars->vid.push_back(v); vars->vdim.push_back(base);
     }
-    const V3d& p = s.vert[v];
     return {unit_dual(p.x, base), unit_dual(p.y, base + 1), unit_dual(p.z, base + 2)};
   }
   static MatT<Dual> params(const Scene& s, Vars* vars, int f) {
     int base = -1;
     for (size_t i = 0; i < vars->fid.size(); ++i)
       if (vars->fid[i] == f) base = vars->fdim[i];
+    const double* q = &s.param[(size_t)s.np * f];
+    MatT<Dual> m;
+    if (base < 0 && vars->nd + s.np > MAXD) {
+      vars->overflow = true;
+      for (int c = 0; c < 3; ++c) m.kd[c] = Dual(q[c]);
+      for (int c = 0; c < 3; ++c) m.ks[c] = Dual(q[s.np == 7 ? 3 + c : 3]);
+      m.alpha = Dual(q[s.np - 1]);
+      return m;
+    }
     if (base < 0) {
       base = vars->nd; vars->nd += s.np;
       vars->fid.push_back(f); vars->fdim.push_back(base);
     }
-    const double* q = &s.param[(size_t)s.np * f];
-    MatT<Dual> m;
     for (int c = 0; c < 3; ++c) m.kd[c] = unit_dual(q[c], base + c);
     // one specular value for all channels (5 parameters) or one per channel (7)
     for (int c = 0; c < 3; ++c) m.ks[c] = s.np == 7 ? unit_dual(q[3 + c], base + 3 + c) : unit_dual(q[3], base + 3);
@@ -644,7 +660,7 @@ void trace_path(const Scene& s, const Rng& rng, int B, const Lights& lt, const V
 // T_b (g- - g+). It is added to L as a dual with zero value whose derivative is
 // that weight times m.(dx - dp), dx = (1 - tau) dA + tau dB.
 void secondary_edge(const Scene& s, const Rng& rng, int B, const Lights& lt, int b, const V3<Dual>& p, const V3d& nv,
-                    const V3d& wo,
+                    const V3d& ns, const V3d& wo,
                     int f0, long long tex, const Dual thr[3], uint32_t c0, uint32_t c1, uint32_t stream,
                     const SecCtx& sc, Vars* vars, Dual L[3], long long& segments) {
   const std::vector<Edge>& E = *sc.E;
@@ -667,12 +683,16 @@ void secondary_edge(const Scene& s, const Rng& rng, int B, const Lights& lt, int
     }
     if (!sil) return;
   }
-  // the part of the edge above the tangent plane (below it the BRDF is zero)
-  double hA = dot(nv, A - pv), hB = dot(nv, Bv - pv);
-  if (!(hA > bnd) && !(hB > bnd)) return;
+  // the part of the edge above the tangent plane (below it the BRDF is zero);
+  // with shading normals, above the shading plane as well
   double t0 = 0.0, t1 = 1.0;
-  if (!(hA > bnd)) t0 = (bnd - hA) / (hB - hA);
-  if (!(hB > bnd)) t1 = (hA - bnd) / (hA - hB);
+  for (int pl = 0; pl < (s.smooth ? 2 : 1); ++pl) {
+    const V3d& nc = pl == 0 ? nv : ns;
+    double hA = dot(nc, A - pv), hB = dot(nc, Bv - pv);
+    if (!(hA > bnd) && !(hB > bnd)) return;
+    if (!(hA > bnd)) t0 = std::max(t0, (bnd - hA) / (hB - hA));
+    if (!(hB > bnd)) t1 = std::min(t1, (hA - bnd) / (hA - hB));
+  }
   if (!(t1 > t0)) return;
   double tau = t0 + unif(u.w[1]) * (t1 - t0);
   V3d tv = Bv - A;
@@ -692,8 +712,9 @@ void secondary_edge(const Scene& s, const Rng& rng, int B, const Lights& lt, int
   for (int side = 0; side < 2; ++side) {
     V3d ws = nrm(w + scl(mh, side == 0 ? -SEC_EPS : SEC_EPS));
     double f[3], Li[3];
-    brdf_eval(s.brdf, m, nv, ws, wo, f);
-    double ci = dot(nv, ws);
+    brdf_eval(s.brdf, m, ns, ws, wo, f);
+    double ci = dot(ns, ws);
+    if (s.smooth && !(dot(nv, ws) > 0)) ci = 0;
     trace_path<double>(s, rng, B, lt, pv, ws, c0, c1, 16u + (uint32_t)b, nullptr, Li, segments, nullptr, nullptr, b + 1,
                        f0);
     for (int c = 0; c < 3; ++c) g[side][c] = ci > 0 ? f[c] * ci * Li[c] : 0.0;
@@ -710,6 +731,42 @@ void secondary_edge(const Scene& s, const Rng& rng, int B, const Lights& lt, int
   Dual ed = dot(lift<Dual>(mh), xd - p);
   Dual z = ed - ed.v;
   for (int c = 0; c < 3; ++c) L[c] = L[c] + z * k[c];
+}
+
+// ---------------------------------------------------------------- shading normals
+// Interpolated shading normals (scene option; the paper's facets are flat, the
+// variant is a standard one). Vertex normal N_v = M_v / |M_v|, M_v = the sum of
+// e1 x e2 = (v1 - v0) x (v2 - v0) over the faces around v (area weighting), in
+// face order. At a hit p on face (v0, v1, v2) with m = e1 x e2 the barycentric
+// weights are b1 = ((p - v0) x e2).m / m.m and b2 = (e1 x (p - v0)).m / m.m (p
+// on the face's plane), and n_s = s / |s|, s = (1 - b1 - b2) N0 + b1 N1 + b2 N2,
+// turned with the geometric normal toward the incoming direction. Everything is
+// differentiated: the vertex normals through every face around the vertex.
+template <class T>
+V3<T> vertex_normal_of(const Scene& s, Vars* vars, int v) {
+  using A = Access<T>;
+  V3<T> M = lift<T>(V3d{0, 0, 0});
+  for (int k = s.vf_start[v]; k < s.vf_start[(size_t)v + 1]; ++k) {
+    const int* fi = &s.face[3 * (size_t)s.vf_list[k]];
+    V3<T> a = A::vertex(s, vars, fi[0]), b = A::vertex(s, vars, fi[1]), c = A::vertex(s, vars, fi[2]);
+    M = M + cross(b - a, c - a);
+  }
+  return nrm(M);
+}
+
+// shading normal at p of face fi (vertices v0, v1, v2, m = e1 x e2), sign = +1 or
+// -1 as the geometric normal was turned
+template <class T>
+V3<T> shading_normal(const Scene& s, Vars* vars, const int* fi, const V3<T>& v0, const V3<T>& v1, const V3<T>& v2,
+                     const V3<T>& m, const V3<T>& p, double sign) {
+  V3<T> e1 = v1 - v0, e2 = v2 - v0, q = p - v0;
+  T mm = dot(m, m);
+  T b1 = dot(cross(q, e2), m) / mm;
+  T b2 = dot(cross(e1, q), m) / mm;
+  V3<T> N0 = vertex_normal_of<T>(s, vars, fi[0]), N1 = vertex_normal_of<T>(s, vars, fi[1]),
+        N2 = vertex_normal_of<T>(s, vars, fi[2]);
+  V3<T> sv = scl(N0, 1.0 - b1 - b2) + scl(N1, b1) + scl(N2, b2);
+  return scl(nrm(sv), sign);
 }
 
 // ---------------------------------------------------------------- one path
@@ -773,6 +830,11 @@ void trace_path(const Scene& s, const Rng& rng, int B, const Lights& lt, const V
     V3<T> wo = lift<T>(wo_d);
     V3<T> n = (dot(val(ng), wo_d) < 0) ? -ng : ng;
     V3d nv = val(n), pv = val(p);
+    // shading normal: the geometric one, or interpolated from the vertex normals;
+    // a direction counts only above both
+    V3<T> ns = s.smooth ? shading_normal<T>(s, vars, fi, v0, v1, v2, mvec, p, dot(val(ng), wo_d) < 0 ? -1.0 : 1.0)
+                        : n;
+    V3d nsv = val(ns);
 
     // next-event estimation: point lights
     bool traced = false;      // any shadow ray at this vertex
@@ -781,14 +843,14 @@ void trace_path(const Scene& s, const Rng& rng, int B, const Lights& lt, const V
       V3<T> dv = lift<T>(lt.pos[j]) - p;
       T dist = len(dv);
       V3<T> wi = scl(dv, 1.0 / dist);
-      T ci = dot(n, wi);
-      if (!(vv(ci) > 0) || !(vv(dist) > 2 * T_EPS)) continue;
+      T ci = dot(ns, wi);
+      if (!(vv(dot(n, wi)) > 0) || !(vv(ci) > 0) || !(vv(dist) > 2 * T_EPS)) continue;
       ++segments;
       traced = true;
       if (occluded(s, pv, val(wi), h.tri, vv(dist) - T_EPS)) continue;
       vis |= 1u << j;
       T f[3];
-      brdf_eval(s.brdf, m, n, wi, wo, f);
+      brdf_eval(s.brdf, m, ns, wi, wo, f);
       T g = ci / (dist * dist);
       for (int c = 0; c < 3; ++c) L[c] = L[c] + thr[c] * f[c] * g * comp(lt.I[j], c);
     }
@@ -807,8 +869,8 @@ void trace_path(const Scene& s, const Rng& rng, int B, const Lights& lt, const V
       st = tp.take(st);
       wi = tp.take(wi);
       if (st > 0) {
-        T ci = dot(n, lift<T>(wi));
-        if (vv(ci) > 0) {
+        T ci = dot(ns, lift<T>(wi));
+        if (vv(dot(n, lift<T>(wi))) > 0 && vv(ci) > 0) {
           ++segments;
           traced = true;
           if (!occluded(s, pv, wi, h.tri, INFINITY)) {
@@ -816,20 +878,21 @@ void trace_path(const Scene& s, const Rng& rng, int B, const Lights& lt, const V
             double pe = env_pdf(s, tx, st);
             double w = 1.0;
             if (b < B - 1) {
-              double pb = brdf_pdf(s.brdf, mv, nv, wi, wo_d);
+              double pb = brdf_pdf(s.brdf, mv, nsv, wi, wo_d);
               w = pe * pe / (pe * pe + pb * pb);
             }
             pe = tp.take(pe);
             w = tp.take(w);
             T f[3];
-            brdf_eval(s.brdf, m, n, lift<T>(wi), wo, f);
+            brdf_eval(s.brdf, m, ns, lift<T>(wi), wo, f);
             for (int c = 0; c < 3; ++c) L[c] = L[c] + thr[c] * f[c] * ci * (s.env[3 * tx + c] * w / pe);
           }
         }
       }
     }
     if constexpr (std::is_same<T, Dual>::value) {
-      if (sec) secondary_edge(s, rng, B, lt, b, p, nv, wo_d, h.tri, tex, thr, c0, c1, stream, *sec, vars, L, segments);
+      if (sec)
+        secondary_edge(s, rng, B, lt, b, p, nv, nsv, wo_d, h.tri, tex, thr, c0, c1, stream, *sec, vars, L, segments);
     }
     if (b == B - 1) {
       if (traced) mix(vis);
@@ -839,7 +902,8 @@ void trace_path(const Scene& s, const Rng& rng, int B, const Lights& lt, const V
     U4 u = rng.draw(c0, c1, (uint32_t)(b << 4) | 2u, stream);
     V3d wi;
     int lobe = 0;
-    double pdf = brdf_sample(s.brdf, mv, nv, wo_d, unif(u.w[0]), unif(u.w[1]), unif(u.w[2]), wi, &lobe);
+    double pdf = brdf_sample(s.brdf, mv, nsv, wo_d, unif(u.w[0]), unif(u.w[1]), unif(u.w[2]), wi, &lobe);
+    if (s.smooth && pdf > 0 && !(dot(nv, wi) > 0)) pdf = 0;   // below the geometric surface
     mix((uint32_t)lobe | (pdf > 0 ? 2u : 0u));
     if (traced) mix(vis);
     pdf = tp.take(pdf);
@@ -847,8 +911,8 @@ void trace_path(const Scene& s, const Rng& rng, int B, const Lights& lt, const V
     if (!(pdf > 0)) return;
     T f[3];
     V3<T> wiT = lift<T>(wi);
-    brdf_eval(s.brdf, m, n, wiT, wo, f);
-    T ci = dot(n, wiT);
+    brdf_eval(s.brdf, m, ns, wiT, wo, f);
+    T ci = dot(ns, wiT);
     for (int c = 0; c < 3; ++c) thr[c] = thr[c] * f[c] * ci / pdf;
     o = p; d = wi; origin = h.tri; last_pdf = pdf;
   }
@@ -868,6 +932,17 @@ bool load_scene(const orc_scene* in, Scene& s) {
   s.ntex = (s.res + 1) * (s.res + 2) / 2;
   if (in->param_width != 5 && in->param_width != 7) return false;
   s.np = in->param_width;
+  if (in->smooth_normals != 0 && in->smooth_normals != 1) return false;
+  s.smooth = in->smooth_normals == 1;
+  s.vf_start.assign((size_t)s.nv + 1, 0);
+  for (int v : s.face) ++s.vf_start[(size_t)v + 1];
+  for (int v = 0; v < s.nv; ++v) s.vf_start[(size_t)v + 1] += s.vf_start[v];
+  s.vf_list.resize(s.face.size());
+  {
+    std::vector<int> cur(s.vf_start.begin(), s.vf_start.end() - 1);
+    for (int f = 0; f < s.nf; ++f)
+      for (int k = 0; k < 3; ++k) s.vf_list[(size_t)cur[s.face[3 * f + k]]++] = f;
+  }
   s.param.resize((size_t)s.np * s.nf * s.ntex);
   for (size_t i = 0; i < s.param.size(); ++i) s.param[i] = in->face_params[i];
   for (int j = 0; j < in->n_lights; ++j) {
@@ -897,6 +972,7 @@ template <class F> void parallel_for(int n, int nt, F fn) {
 }
 
 void scatter_grad(const Vars& vars, const Dual& loss, double* dv, double* df, int np) {
+  if (vars.overflow) g_dual_overflow = true;
   for (size_t i = 0; i < vars.vid.size(); ++i)
     for (int k = 0; k < 3; ++k) {
       int dim = vars.vdim[i] + k;
@@ -1113,6 +1189,7 @@ long long orc_render_signatures(const orc_scene* in, const orc_view* views, int 
 
 long long orc_grad_pixels(const orc_scene* in, const orc_view* views, int n_views, const orc_params* p,
                           const int* pix, int n, const double* dLdI, double* d_verts, double* d_face) {
+  g_dual_overflow = false;
   Scene s;
   if (!load_scene(in, s) || !check_common(views, n_views, p)) return -1;
   Rng rng = rng_of(p);
@@ -1145,6 +1222,7 @@ long long orc_grad_pixels(const orc_scene* in, const orc_view* views, int n_view
     for (size_t k = 0; k < gv[t].size(); ++k) d_verts[k] += gv[t][k];
     if (d_face) for (size_t k = 0; k < gf[t].size(); ++k) d_face[k] += gf[t][k];
   }
+  if (g_dual_overflow) return -1;
   long long tot = 0;
   for (auto x : seg) tot += x;
   return tot;
@@ -1239,6 +1317,7 @@ long long orc_edge_grad(const orc_scene* in, const orc_view* views, int n_views,
 // sample adds <dL/dI_S, L- - L+> n_cand |dS/dtau| / N times that speed.
 long long orc_shadow_edge_grad(const orc_scene* in, const orc_view* views, int n_views, const orc_params* p,
                                const double* dLdI, double* d_verts) {
+  g_dual_overflow = false;
   Scene s;
   if (!load_scene(in, s) || !check_common(views, n_views, p)) return -1;
   Rng rng = rng_of(p);
@@ -1328,6 +1407,7 @@ long long orc_shadow_edge_grad(const orc_scene* in, const orc_view* views, int n
   }
   for (int t = 0; t < nt; ++t)
     for (size_t k = 0; k < gv[t].size(); ++k) d_verts[k] += gv[t][k];
+  if (g_dual_overflow) return -1;
   long long tot = 0;
   for (auto x : seg) tot += x;
   return tot;
@@ -1336,6 +1416,7 @@ long long orc_shadow_edge_grad(const orc_scene* in, const orc_view* views, int n
 long long orc_trace_screen(const orc_scene* in, const orc_view* view, const orc_params* p, double px, double py,
                            uint32_t c0, uint32_t c1, uint32_t stream, double* rgb, const double* grad_w,
                            double* d_verts, double* d_face) {
+  g_dual_overflow = false;
   Scene s;
   if (!load_scene(in, s) || !check_common(view, 1, p)) return -1;
   Rng rng = rng_of(p);
@@ -1356,6 +1437,7 @@ long long orc_trace_screen(const orc_scene* in, const orc_view* view, const orc_
   for (int k = 0; k < 3; ++k) rgb[k] = L[k].v;
   Dual loss = L[0] * grad_w[0] + L[1] * grad_w[1] + L[2] * grad_w[2];
   scatter_grad(vars, loss, d_verts, d_face, s.np);
+  if (g_dual_overflow) return -1;
   return seg;
 }
 

@@ -43,6 +43,8 @@ typedef struct {
                                 F*(r+1)(r+2)/2 texels of 5 params, texel k(r, t, alpha, beta) */
   int param_width;           /* parameters per texel: 5 (kd rgb, ks, roughness) or 7 (kd rgb, ks rgb,
                                 roughness); gradients use the same layout */
+  int smooth_normals;        /* 0: flat face normals; 1: shading normals interpolated from vertex normals
+                                (each the normalised sum of its faces' e1 x e2), oracle.cpp states the rules */
 } orc_scene;
 
 typedef struct {

@@ -1,0 +1,202 @@
+"""Pins of the oracle's interpolated shading normals (scene option ``smooth_normals``).
+
+The shading normal at a hit is the barycentric blend of vertex normals, each
+the normalised sum of e1 x e2 over the faces around the vertex, turned with
+the geometric normal toward the incoming ray; a direction counts only above
+both the geometric and the shading plane. Pinned by: a planar mesh renders as
+with flat normals; direct light at exact screen points equals a numpy
+evaluation written from that definition (own ray casting, vertex normals,
+blend, shadow test); the dual-number gradient (which now reaches every vertex
+around the hit face) equals central differences of the taped estimator; the
+secondary edge term is unchanged where vertex normals equal face normals; and
+a vertex with more neighbours than the dual numbers hold is reported.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2012_03939_gb300 import scenes as S
+from tests import _geom as G
+from tests.test_oracle_secondary_edges import _occluder_scene
+
+
+def _sphere_scene(brdf="ggx", smooth=True, env=True, ks=None, seed=5):
+    V, F = S.icosphere(1)
+    V = V * 0.8
+    rng = np.random.default_rng(seed)
+    P = S.random_face_params(rng, len(F))
+    if ks is not None:
+        P[:, 3] = ks
+    vs = [S.View((0.375, 0.875, 2.625), (0.0, 0.0, 0.0), (0.0, 1.0, 0.0), 45.0, 16, 16, 1)]   # exact in float32
+    return S.Scene("sphere", V.astype(np.float32), F, P, brdf, light_pos=np.array([[1.2, 1.6, 1.4]], np.float32),
+                   light_intensity=np.array([[3.0, 2.5, 2.0]], np.float32),
+                   env=S.lognormal_env(rng, 16, 8, sigma=0.5) if env else None, views=vs, max_bounces=2,
+                   smooth_normals=smooth)
+
+
+def test_planar_mesh_renders_as_with_flat_normals():
+    P, F = S._grid_quad((-1, 0, -1), (0, 0, 2), (2, 0, 0), 4)
+    rng = np.random.default_rng(2)
+    vs = S.fibonacci_views(2, [12, 10], [10, 12], [2, 2])
+    vs = [S.View(tuple(np.array(v.eye) * [1, 0, 1] * 0.6 + [0, 2.2, 0]), (0, 0, 0), (0, 0, 1), 50.0, v.width,
+                 v.height, v.spp, v.pixel_offset) for v in vs]
+    base = S.Scene("grid", P.astype(np.float32), F.astype(np.int32), S.random_face_params(rng, len(F)), "ggx",
+                   light_pos=np.array([[0.3, 1.5, 0.2]], np.float32), light_intensity=np.full((1, 3), 3.0, np.float32),
+                   env=S.lognormal_env(rng, 16, 8, sigma=0.5), views=vs, max_bounces=3)
+    pix = O.all_pixels(base)
+    prm = O.params(3, 44)
+    flat = O.render_pixels(O.OracleScene(base), prm, pix)[0]
+    smooth_sc = S.Scene(**{**base.__dict__, "smooth_normals": True})
+    smooth = O.render_pixels(O.OracleScene(smooth_sc), prm, pix)[0]
+    assert flat.max() > 0
+    np.testing.assert_allclose(smooth, flat, rtol=1e-12, atol=1e-14)
+    np.testing.assert_array_equal(O.render_signatures(O.OracleScene(smooth_sc), prm, pix),
+                                  O.render_signatures(O.OracleScene(base), prm, pix))
+
+
+def _vertex_normals(V, F):
+    M = np.zeros_like(V)
+    c = np.cross(V[F[:, 1]] - V[F[:, 0]], V[F[:, 2]] - V[F[:, 0]])
+    for k in range(3):
+        np.add.at(M, F[:, k], c)
+    return M / np.linalg.norm(M, axis=1, keepdims=True)
+
+
+def _cast(V, F, o, d, exclude=-1, tmax=np.inf):
+    """Moller-Trumbore over all faces: (face, t, b1, b2) of the nearest hit with t in (1e-5, tmax)."""
+    a, b, c = V[F[:, 0]], V[F[:, 1]], V[F[:, 2]]
+    e1, e2 = b - a, c - a
+    pv = np.cross(d, e2)
+    det = np.einsum("ij,ij->i", e1, pv)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        inv = 1.0 / det
+        tv = o - a
+        u = np.einsum("ij,ij->i", tv, pv) * inv
+        qv = np.cross(tv, e1)
+        v = (qv @ d) * inv
+        t = np.einsum("ij,ij->i", e2, qv) * inv
+    ok = (np.abs(det) > 0) & (u >= 0) & (v >= 0) & (u + v <= 1) & (t > 1e-5) & (t < tmax)
+    ok[exclude] = ok[exclude] and exclude < 0
+    if not ok.any():
+        return -1, np.inf, 0.0, 0.0
+    f = int(np.argmin(np.where(ok, t, np.inf)))
+    return f, t[f], u[f], v[f]
+
+
+@pytest.mark.parametrize("inward", [False, True])
+def test_direct_light_equals_the_definition_at_screen_points(inward):
+    # inward: faces wound the other way, so every hit turns both normals around
+    sc = _sphere_scene(env=False, ks=0.0)
+    sc.max_bounces = 1
+    if inward:
+        sc.faces = np.ascontiguousarray(sc.faces[:, [0, 2, 1]])
+    V = sc.vertices.astype(np.float64)
+    F = sc.faces
+    N = _vertex_normals(V, F)
+    L = sc.light_pos[0].astype(np.float64)
+    I = sc.light_intensity[0].astype(np.float64)
+    osc = O.OracleScene(sc)
+    prm = O.params(1, 3)
+    v = sc.views[0]
+    rng = np.random.default_rng(8)
+    n_hit = n_tilted = n_split = 0
+    for px, py in rng.uniform([3, 3], [13, 13], size=(300, 2)):
+        got = O.trace_screen(osc, prm, 0, px, py)
+        o, d = G.pixel_ray(v, px, py)
+        f, t, b1, b2 = _cast(V, F, o, d)
+        exp = np.zeros(3)
+        if f >= 0:
+            n_hit += 1
+            a, b, c = V[F[f]]
+            ng = np.cross(b - a, c - a)
+            ng /= np.linalg.norm(ng)
+            s = (1 - b1 - b2) * N[F[f, 0]] + b1 * N[F[f, 1]] + b2 * N[F[f, 2]]
+            ns = s / np.linalg.norm(s)
+            if ng @ -d < 0:
+                ng, ns = -ng, -ns
+            n_tilted += math.acos(min(1.0, ns @ ng)) > 1e-2
+            p = o + t * d
+            wi = L - p
+            dist = np.linalg.norm(wi)
+            wi /= dist
+            n_split += (ng @ wi > 0) != (ns @ wi > 0)
+            if ng @ wi > 0 and ns @ wi > 0 and _cast(V, F, p, wi, exclude=f, tmax=dist - 1e-5)[0] < 0:
+                exp = sc.face_params[f, :3].astype(np.float64) / math.pi * I * (ns @ wi) / dist ** 2
+        np.testing.assert_allclose(got, exp, rtol=1e-9, atol=1e-12)
+    assert n_hit > 150 and n_tilted > 100 and n_split > 0
+
+
+@pytest.mark.parametrize("brdf,B", [("ggx", 1), ("ggx", 3), ("beckmann", 2)])
+def test_smooth_gradient_matches_tape_replay_fd(brdf, B):
+    sc = _sphere_scene(brdf)
+    V0 = sc.vertices.astype(np.float64)
+    P0 = sc.face_params.astype(np.float64)
+    prm = O.params(B, 77)
+    w = np.array([0.4, -0.6, 0.5])
+    checked = ring = 0
+    for (px, py, c1) in [(6.3, 7.1, 0), (9.7, 8.2, 1), (8.1, 10.4, 2), (7.6, 5.8, 3)]:
+        osc = O.OracleScene(sc, vertices=V0, face_params=P0)
+        rgb, dv, df = O.trace_screen(osc, prm, 0, px, py, c0=5, c1=c1, grad_w=w)
+        _, tape = O.trace_screen_taped(osc, prm, 0, px, py, c0=5, c1=c1)
+        np.testing.assert_array_equal(rgb, O.trace_screen_taped(osc, prm, 0, px, py, c0=5, c1=c1, tape=tape))
+        o, d = G.pixel_ray(sc.views[0], px, py)
+        f = _cast(V0, sc.faces, o, d)[0]
+        ring += np.count_nonzero(np.delete(np.abs(dv).sum(1), sc.faces[f])) if f >= 0 else 0
+        h = 1e-6
+        for (vi, k) in [(i, k) for i in range(len(V0)) for k in range(3) if dv[i, k] != 0]:
+            Vp, Vm = V0.copy(), V0.copy()
+            Vp[vi, k] += h
+            Vm[vi, k] -= h
+            fp = O.trace_screen_taped(O.OracleScene(sc, vertices=Vp, face_params=P0), prm, 0, px, py, 5, c1, tape=tape)
+            fm = O.trace_screen_taped(O.OracleScene(sc, vertices=Vm, face_params=P0), prm, 0, px, py, 5, c1, tape=tape)
+            fd = (w @ fp - w @ fm) / (2 * h)
+            assert abs(fd - dv[vi, k]) < 1e-5 * max(1.0, abs(fd)), (vi, k, fd, dv[vi, k])
+            checked += 1
+        for (fi, k) in [(i, k) for i in range(len(P0)) for k in range(5) if df[i, k] != 0]:
+            Pp, Pm = P0.copy(), P0.copy()
+            Pp[fi, k] += h
+            Pm[fi, k] -= h
+            fp = O.trace_screen_taped(O.OracleScene(sc, vertices=V0, face_params=Pp), prm, 0, px, py, 5, c1, tape=tape)
+            fm = O.trace_screen_taped(O.OracleScene(sc, vertices=V0, face_params=Pm), prm, 0, px, py, 5, c1, tape=tape)
+            fd = (w @ fp - w @ fm) / (2 * h)
+            assert abs(fd - df[fi, k]) < 1e-5 * max(1.0, abs(fd)), (fi, k, fd, df[fi, k])
+            checked += 1
+    # the shading normals reach the vertices around the hit face, not just its own
+    assert checked > 40 and ring > 0
+
+
+def test_secondary_term_unchanged_where_vertex_normals_are_face_normals():
+    # floor and floating triangle share no vertex: every vertex normal is its
+    # face's normal, so the shading normal equals the geometric one and the
+    # secondary edge samples (their planes, sides and weights) are the flat ones
+    sc = _occluder_scene(spp=2)
+    pix = O.all_pixels(sc)[::7]
+    w = np.random.default_rng(3).normal(size=(len(pix), 3))
+    out = []
+    for smooth in (False, True):
+        s = S.Scene(**{**sc.__dict__, "smooth_normals": smooth})
+        osc = O.OracleScene(s)
+        g1 = O.grad_pixels(osc, O.params(1, 9, secondary=1), pix, w)[0]
+        g0 = O.grad_pixels(osc, O.params(1, 9), pix, w)[0]
+        out.append(g1 - g0)
+    assert np.abs(out[0]).max() > 0
+    np.testing.assert_allclose(out[1], out[0], rtol=1e-9, atol=1e-9 * np.abs(out[0]).max())
+
+
+def test_a_vertex_beyond_the_dual_capacity_is_reported():
+    # a fan of 200 triangles around one vertex: its normal depends on 201
+    # vertices, more than one path's dual numbers hold
+    n = 200
+    ang = np.linspace(0, 2 * np.pi, n, endpoint=False)
+    V = np.r_[[[0.0, 0.2, 0.0]], np.c_[np.cos(ang), np.zeros(n), np.sin(ang)]].astype(np.float32)
+    F = np.array([[0, 1 + (i + 1) % n, 1 + i] for i in range(n)], np.int32)
+    vs = [S.View((0.0, 2.5, 0.5), (0.0, 0.0, 0.0), (0.0, 1.0, 0.0), 40.0, 4, 4, 1)]
+    sc = S.Scene("fan", V, F, S.random_face_params(np.random.default_rng(1), n), "ggx",
+                 light_pos=np.array([[0.0, 2.0, 0.0]], np.float32), light_intensity=np.ones((1, 3), np.float32),
+                 views=vs, max_bounces=1, smooth_normals=True)
+    pix = O.all_pixels(sc)
+    O.render_pixels(O.OracleScene(sc), O.params(1, 1), pix)   # values need no duals
+    with pytest.raises(ValueError):
+        O.grad_pixels(O.OracleScene(sc), O.params(1, 1), pix, np.ones((len(pix), 3)))
