@@ -119,6 +119,13 @@ typedef struct {
   int rgb_specular;          /* 0: 5 parameters per texel (kd rgb, ks, roughness); 1: 7 (kd rgb, ks rgb,
                                 roughness), a specular colour per channel. face_params, st_set_face_params and
                                 the d_face_params of st_render_backward all use this layout. */
+  int smooth_normals;        /* 0: flat face normals (the paper's facets). 1: shading normals interpolated from
+                                vertex normals: N_v = normalised sum of (v1 - v0) x (v2 - v0) over the faces
+                                around v (recomputed after every vertex update); at a hit of barycentric weights
+                                (b1, b2), n_s = normalise((1 - b1 - b2) N0 + b1 N1 + b2 N2), turned with the face
+                                normal toward the incoming ray. Lights, environment samples and sampled
+                                directions count only above both the face's and the shading plane. Gradients
+                                reach every vertex around a hit face. */
 } st_scene_desc;
 
 typedef struct {

@@ -354,6 +354,7 @@ KCtx make_ctx(st_scene* s, const Plan& p) {
   c.bin_list = s->bin_list; c.bin_cur = s->bin_cur; c.bin_ok = s->bin_ok;
   c.bin_cap = s->bin_cap; c.bin_pixels = p.pixels;
   c.cull = s->closed ? 1 : 0; c.mstat = s->mstat;
+  c.smooth = s->smooth ? 1 : 0; c.vn = s->vnrm; c.dN = s->dN; c.nv = s->nv;
   c.acc = s->acc;
   c.views = s->d_views; c.segs = s->d_segs; c.n_segs = (int)p.segs.size();
   c.args = s->d_args; c.B = p.B; c.e = s->eng; c.e.records = p.kind == 1; c.err = s->d_err;
@@ -476,7 +477,11 @@ st_status run_chunk(st_scene* s, const Plan& p, const KCtx& c, long long j0, int
         s->launches++;
       }
     }
-    if (has_cam && p.interior) { k_adjoint<<<ga, ADJ_BLOCK, 0, st>>>(c, j0, n); s->launches++; }
+    if (has_cam && p.interior) {
+      if (s->smooth) k_adjoint<true><<<ga, ADJ_BLOCK, 0, st>>>(c, j0, n);
+      else k_adjoint<false><<<ga, ADJ_BLOCK, 0, st>>>(c, j0, n);
+      s->launches++;
+    }
   }
   ST_CUDA(cudaGetLastError());
   return ST_OK;
@@ -490,6 +495,7 @@ st_status enqueue_call(st_scene* s, const Plan& p, int Q, cudaStream_t st, bool 
     k_zero_acc<<<(unsigned)((p.pixels + 255) / 256), 256, 0, st>>>(c);
     s->launches++;
   }
+  if (p.kind == 1 && s->smooth) ST_CUDA(cudaMemsetAsync(s->dN, 0, 3 * sizeof(float) * s->nv, st));
   if (p.bins) {
     // primary-visibility bins of every view: count, scan, fill
     long long P = p.pixels;
@@ -543,6 +549,13 @@ st_status enqueue_call(st_scene* s, const Plan& p, int Q, cudaStream_t st, bool 
   if (p.kind == 0) {
     k_finish_views<<<(unsigned)((p.pixels + 255) / 256), 256, 0, st>>>(c, (int)p.views.size());
     s->launches++;
+    ST_CUDA(cudaGetLastError());
+  }
+  if (p.kind == 1 && s->smooth) {
+    int g = std::min((std::max(s->nv, s->nf) + 255) / 256, 4 * std::max(s->sm_count, 1));
+    k_vn_adj_vertex<<<g, 256, 0, st>>>(c);
+    k_vn_adj_face<<<g, 256, 0, st>>>(c);
+    s->launches += 2;
     ST_CUDA(cudaGetLastError());
   }
   return ST_OK;
@@ -745,7 +758,7 @@ void destroy(st_scene* s) {
   dfree(s->edge_flag); dfree(s->edge_cand); dfree(s->edge_ncand);
   dfree(s->sh_flag); dfree(s->sh_cand); dfree(s->sh_ncand); dfree(s->d_pairs); dfree(s->d_views); dfree(s->d_segs);
   dfree(s->bin_start); dfree(s->bin_cur); dfree(s->bin_list); dfree(s->bin_ok); dfree(s->bin_part);
-  dfree(s->acc); dfree(s->sacc); dfree(s->mstat);
+  dfree(s->acc); dfree(s->sacc); dfree(s->mstat); dfree(s->vnrm); dfree(s->vf_start); dfree(s->vf_list); dfree(s->dN);
   if (s->bin_total_host) cudaFreeHost(s->bin_total_host);
   dfree(s->d_args); dfree(s->d_err);
   for (auto& e : s->ev) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
@@ -782,6 +795,7 @@ st_status st_scene_create(const st_scene_desc* d, void* stream, st_scene** out) 
   if (d->brdf != ST_BRDF_GGX && d->brdf != ST_BRDF_BECKMANN) return fail(ST_ERR_INVALID_ARG, "unknown brdf");
   if (d->bvh_builder != ST_BVH_PLOC && d->bvh_builder != ST_BVH_LBVH) return fail(ST_ERR_INVALID_ARG, "unknown bvh_builder");
   if (d->color_res < 0 || d->color_res > 64) return fail(ST_ERR_UNSUPPORTED, "mesh-colors resolution must be in [0, 64]");
+  if (d->smooth_normals != 0 && d->smooth_normals != 1) return fail(ST_ERR_INVALID_ARG, "smooth_normals must be 0 or 1");
   if ((long long)d->n_faces * (d->color_res + 1) * (d->color_res + 2) / 2 > (1LL << 30))
     return fail(ST_ERR_UNSUPPORTED, "too many mesh-colors texels");
   if (d->n_point_lights < 0 || d->n_point_lights > ST_MAX_LIGHTS || (d->n_point_lights > 0 && !d->point_lights))
@@ -805,6 +819,7 @@ st_status st_scene_create(const st_scene_desc* d, void* stream, st_scene** out) 
   s->res = d->color_res;
   s->builder = d->bvh_builder;
   s->np = d->rgb_specular ? 7 : 5;
+  s->smooth = d->smooth_normals == 1;
   s->ntex = (s->res + 1) * (s->res + 2) / 2;
   // host copy of the faces: validation and edge list
   std::vector<int> hf(3 * (size_t)s->nf);
@@ -848,6 +863,19 @@ st_status st_scene_create(const st_scene_desc* d, void* stream, st_scene** out) 
   chk(dalloc(&s->lights, 2 * (size_t)std::max(s->nl, 1))); chk(dalloc(&s->edge_v, ev.size()));
   chk(dalloc(&s->edge_f, ef.size())); chk(dalloc(&s->d_args, 1)); chk(dalloc(&s->d_err, 1));
   chk(dalloc(&s->mstat, 1));
+  std::vector<int> vfs, vfl;
+  if (s->smooth) {
+    // faces around each vertex, in face order (CSR)
+    vfs.assign((size_t)s->nv + 1, 0);
+    for (int v : hf) ++vfs[(size_t)v + 1];
+    for (int v = 0; v < s->nv; ++v) vfs[(size_t)v + 1] += vfs[v];
+    vfl.resize(hf.size());
+    std::vector<int> cur(vfs.begin(), vfs.end() - 1);
+    for (int f = 0; f < n; ++f)
+      for (int k = 0; k < 3; ++k) vfl[(size_t)cur[hf[3 * (size_t)f + k]]++] = f;
+    chk(dalloc(&s->vnrm, (size_t)s->nv)); chk(dalloc(&s->vf_start, vfs.size())); chk(dalloc(&s->vf_list, vfl.size()));
+    chk(dalloc(&s->dN, 3 * (size_t)s->nv));
+  }
   if (d->env) { chk(dalloc(&s->env_tex, etex.size())); chk(dalloc(&s->env_alias, etab.size())); }
   if (e != cudaSuccess) { destroy(s); cudaGetLastError(); return fail(ST_ERR_OOM, "scene buffers"); }
   std::vector<float4> hl(2 * (size_t)std::max(s->nl, 1), make_float4(0, 0, 0, 0));
@@ -867,6 +895,10 @@ st_status st_scene_create(const st_scene_desc* d, void* stream, st_scene** out) 
   chk(cudaMemcpyAsync(s->edge_v, ev.data(), ev.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
   chk(cudaMemcpyAsync(s->edge_f, ef.data(), ef.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
   chk(cudaMemsetAsync(s->d_err, 0, sizeof(int), st));
+  if (s->smooth) {
+    chk(cudaMemcpyAsync(s->vf_start, vfs.data(), vfs.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    chk(cudaMemcpyAsync(s->vf_list, vfl.data(), vfl.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  }
   if (d->env) {
     chk(cudaMemcpyAsync(s->env_tex, etex.data(), etex.size() * sizeof(float4), cudaMemcpyHostToDevice, st));
     chk(cudaMemcpyAsync(s->env_alias, etab.data(), etab.size() * sizeof(float2), cudaMemcpyHostToDevice, st));

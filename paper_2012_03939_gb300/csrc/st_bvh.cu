@@ -639,7 +639,29 @@ __global__ void k_mesh_stat_final(MeshStat* m) {
   m->winding = fabs(m->vol6) > 1e-3 * box6 ? (m->vol6 > 0.0 ? 1 : -1) : 0;
 }
 
+// Vertex normals for interpolated shading: M_v = the sum of (v1 - v0) x (v2 - v0)
+// over the faces around v in face order (one thread per vertex, so the sum's
+// order is fixed), stored as (M_v / |M_v|, |M_v|).
+__global__ void k_vertex_normals(const float* V, const int* F, const int* vf_start, const int* vf_list, int nv,
+                                 float4* out) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += gridDim.x * blockDim.x) {
+    float3 M = mk3(0, 0, 0);
+    for (int k = vf_start[v]; k < vf_start[v + 1]; ++k) {
+      int f = vf_list[k];
+      auto vx = [&](int i) { return mk3(V[3 * i], V[3 * i + 1], V[3 * i + 2]); };
+      float3 a = vx(F[3 * f]), b = vx(F[3 * f + 1]), c = vx(F[3 * f + 2]);
+      M += cross3(b - a, c - a);
+    }
+    float l = len3(M);
+    out[v] = make_float4(M.x / l, M.y / l, M.z / l, l);
+  }
+}
+
 cudaError_t mesh_stat(st_scene* s, cudaStream_t stream) {
+  if (s->smooth && s->vnrm) {
+    int gv = std::min((s->nv + 255) / 256, 4 * std::max(s->sm_count, 1));
+    k_vertex_normals<<<gv, 256, 0, stream>>>(s->verts, s->faces, s->vf_start, s->vf_list, s->nv, s->vnrm);
+  }
   if (!s->mstat) return cudaSuccess;
   k_mesh_stat_init<<<1, 1, 0, stream>>>(s->mstat);
   int g = std::min((std::max(s->nf, s->nv) + 255) / 256, 4 * std::max(s->sm_count, 1));

@@ -94,6 +94,11 @@ struct st_scene {
   int np = 5;                    // caller parameters per texel: 5 (scalar specular) or 7 (RGB specular)
   bool closed = false;           // one surface; every edge has two faces that traverse it in opposite directions
   st::MeshStat* mstat = nullptr; // signed volume and vertex bounds, recomputed on the device after each update
+  bool smooth = false;           // interpolated shading normals
+  float4* vnrm = nullptr;        // [V] vertex normal N_v and |M_v| (smooth), recomputed with mstat
+  int* vf_start = nullptr;       // [V + 1] faces around each vertex (CSR, face order)
+  int* vf_list = nullptr;        // [3F]
+  float* dN = nullptr;           // [V][3] backward scratch: adjoint of the vertex normals (smooth)
   float* verts = nullptr;        // [V*3]
   int* faces = nullptr;          // [F*3]
   float4* params = nullptr;      // [F*ntex*2] per texel: (kd_r, kd_g, kd_b, ks_r), (roughness, ks_g, ks_b, 0)
@@ -167,7 +172,7 @@ struct st_scene {
 
 namespace st {
 cudaError_t bvh_build(st_scene* s, cudaStream_t stream);    // Morton order + radix-tree hierarchy + boxes
-cudaError_t mesh_stat(st_scene* s, cudaStream_t stream);   // MeshStat of the current vertices (no sync)
+cudaError_t mesh_stat(st_scene* s, cudaStream_t stream);   // MeshStat (and vertex normals) of the current vertices (no sync)
 cudaError_t bvh_build_ploc(st_scene* s, cudaStream_t stream);  // Morton order + PLOC clustering + boxes (synchronises)
 cudaError_t bvh_refit(st_scene* s, cudaStream_t stream);    // leaf records + boxes, same order (+ 4-wide boxes)
 cudaError_t bvh_collapse(st_scene* s, cudaStream_t stream); // 4-wide tree from the binary one (synchronises)

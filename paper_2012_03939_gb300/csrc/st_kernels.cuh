@@ -26,7 +26,7 @@ struct KCtx {
   const float4* P;
   const float4* nodes;
   const float4* tri;
-  int nf;
+  int nf, nv;
   const float4* lights;
   int nl, nlt, NS;        // scene lights, + the most any view of the call adds, + environment
   DevEnv env;
@@ -51,6 +51,9 @@ struct KCtx {
   float* acc;             // per-pixel compensated sample sums, (sum, error) x 3 (bin-space pixel index)
   int cull;               // the mesh is one closed, consistently wound surface (see MeshStat)
   const MeshStat* mstat;
+  int smooth;             // interpolated shading normals from vn
+  const float4* vn;       // [V] vertex normal N_v and |M_v|
+  float* dN;              // backward with smooth normals: [V][3] adjoint of the vertex normals
   const DevView* views;
   const Seg* segs;
   int n_segs;
@@ -130,6 +133,20 @@ __device__ __forceinline__ int texel_of(const KCtx& c, int f, float3 p, float3 v
   int i = min(max((int)floorf((float)r * alpha), 0), r);
   int j = min(max((int)floorf((float)r * beta), 0), r - i);
   return f * c.ntex + (i * (2 * r - i + 3)) / 2 + j;
+}
+
+// Interpolated shading normal at p on face f (vertices v0, v1, v2): barycentric
+// weights b1 = ((p - v0) x e2).m / m.m, b2 = (e1 x (p - v0)).m / m.m, n_s =
+// normalise((1 - b1 - b2) N0 + b1 N1 + b2 N2), times sgn (the face normal's turn
+// toward the incoming ray).
+__device__ __forceinline__ float3 shading_normal(const KCtx& c, int f, float3 p, float3 v0, float3 v1, float3 v2,
+                                                 float sgn) {
+  float3 e1 = v1 - v0, e2 = v2 - v0, q = p - v0;
+  float3 m = cross3(e1, e2);
+  float mm = dot3(m, m);
+  float b1 = dot3(cross3(q, e2), m) / mm, b2 = dot3(cross3(e1, q), m) / mm;
+  float3 n0 = xyz(c.vn[c.F[3 * f]]), n1 = xyz(c.vn[c.F[3 * f + 1]]), n2 = xyz(c.vn[c.F[3 * f + 2]]);
+  return norm3(n0 * (1.0f - b1 - b2) + n1 * b1 + n2 * b2) * sgn;
 }
 
 // ------------------------------------------------------------------ edges
@@ -747,6 +764,8 @@ __global__ void k_shade(KCtx c, int b) {
       float3 ng = norm3(cross3(v1 - v0, v2 - v0));
       float3 wo = -dir;
       float3 n = dot3(ng, wo) < 0.0f ? -ng : ng;
+      // shading normal: n, or interpolated; a direction counts only above both
+      float3 ns = c.smooth ? shading_normal(c, f, p, v0, v1, v2, dot3(ng, wo) < 0.0f ? -1.0f : 1.0f) : n;
       int tex = texel_of(c, f, p, v0, v1, v2);
       Mat m = fetch_mat(c.P, tex);
       if (c.sig) sig_mix(hs, (uint32_t)f);
@@ -762,9 +781,9 @@ __global__ void k_shade(KCtx c, int b) {
         float dist = len3(dv);
         float3 wi = dv * (1.0f / dist);
         float ci = dot3(n, wi);
-        bool valid = j < nlp && ci > 0.0f && dist > 2.0f * T_EPS;
+        bool valid = j < nlp && ci > 0.0f && dist > 2.0f * T_EPS && (!c.smooth || dot3(ns, wi) > 0.0f);
         float3 cc = mk3(0, 0, 0);
-        if (valid) cc = mul(mul(T, brdf_cos(c.brdf, m, n, wi, wo)), xyz(li)) * (1.0f / (dist * dist));
+        if (valid) cc = mul(mul(T, brdf_cos(c.brdf, m, ns, wi, wo)), xyz(li)) * (1.0f / (dist * dist));
         E.sh_dir[j * Q + slot] = make_float4(wi.x, wi.y, wi.z, dist - T_EPS);
         E.sh_c[j * Q + slot] = make_float4(cc.x, cc.y, cc.z, valid ? 1.0f : 0.0f);
         sh_any |= valid;
@@ -781,18 +800,18 @@ __global__ void k_shade(KCtx c, int b) {
         sincosf(PI_F * vq, &sth, &cth);
         sincosf(2.0f * PI_F * uu, &sph, &cph);
         ewi = mk3(-sth * sph, cth, sth * cph);
-        bool valid = sth > 0.0f && dot3(n, ewi) > 0.0f;
+        bool valid = sth > 0.0f && dot3(n, ewi) > 0.0f && (!c.smooth || dot3(ns, ewi) > 0.0f);
         float3 cc = mk3(0, 0, 0);
         if (valid) {
           float4 te = __ldg(&c.env.tex[tx]);
           float pe = env_pdf(c.env, te.w, sth);
           float w = 1.0f;
           if (vb < c.B - 1) {
-            float pb = brdf_pdf(c.brdf, m, n, ewi, wo);
+            float pb = brdf_pdf(c.brdf, m, ns, ewi, wo);
             w = pe * pe / (pe * pe + pb * pb);
           }
           escale = mk3(te.x, te.y, te.z) * (w / pe);
-          cc = mul(mul(T, brdf_cos(c.brdf, m, n, ewi, wo)), escale);
+          cc = mul(mul(T, brdf_cos(c.brdf, m, ns, ewi, wo)), escale);
           flags |= ENV_VALID;
         }
         E.sh_dir[c.nlt * Q + slot] = make_float4(ewi.x, ewi.y, ewi.z, __int_as_float(0x7f800000));
@@ -808,10 +827,11 @@ __global__ void k_shade(KCtx c, int b) {
       if (vb < c.B - 1) {
         U4 u = philox((uint32_t)ct.x, (uint32_t)ct.y, (uint32_t)(vb << 4) | 2u, (uint32_t)ct.z, key.k0, key.k1);
         float3 wi;
-        float pdf = brdf_sample(c.brdf, m, n, wo, unif(u.x), unif(u.y), unif(u.z), wi);
+        float pdf = brdf_sample(c.brdf, m, ns, wo, unif(u.x), unif(u.y), unif(u.z), wi);
+        if (c.smooth && pdf > 0.0f && !(dot3(n, wi) > 0.0f)) pdf = 0.0f;   // below the face
         if (c.sig) sig_mix(hs, (unif(u.x) < lobe_prob(m) ? 1u : 0u) | (pdf > 0.0f ? 2u : 0u));
         if (pdf > 0.0f) {
-          float3 Qv = brdf_cos(c.brdf, m, n, wi, wo);
+          float3 Qv = brdf_cos(c.brdf, m, ns, wi, wo);
           T = mul(T, Qv) * (1.0f / pdf);
           E.thr[slot] = make_float4(T.x, T.y, T.z, 0.0f);
           E.d[slot] = make_float4(wi.x, wi.y, wi.z, pdf);
@@ -940,6 +960,8 @@ __device__ __forceinline__ void warp_reduce_peers(int key, float (&vals)[NV], fl
 
 constexpr int ADJ_BLOCK = 128;
 
+// SMOOTH: interpolated shading normals (SMOOTH); the flat variant keeps its registers
+template <bool SMOOTH>
 __global__ void __launch_bounds__(ADJ_BLOCK) k_adjoint(KCtx c, long long j0, int n) {
   __shared__ float scratch[ADJ_BLOCK / 32][32 * 17];
   float* scr = scratch[threadIdx.x >> 5];
@@ -977,7 +999,8 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_adjoint(KCtx c, long long j0, int
            v2 = fetch_vertex(c.V, c.F[3 * f + 2]);
     float3 wo = -xyz(r1);
     float3 ng = norm3(cross3(v1 - v0, v2 - v0));
-    float3 nn = dot3(ng, wo) < 0.0f ? -ng : ng;
+    float sg = dot3(ng, wo) < 0.0f ? -1.0f : 1.0f;
+    float3 nn = SMOOTH ? shading_normal(c, f, xyz(r0), v0, v1, v2, sg) : ng * sg;
     int tex = __float_as_int(E.r3[b * Q + i].w);
     float3 Qv = brdf_cos(c.brdf, fetch_mat(c.P, tex), nn, xyz(r1n), wo);
     T[b + 1] = mul(T[b], Qv) * (1.0f / r1n.w);
@@ -1005,6 +1028,18 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_adjoint(KCtx c, long long j0, int
       float3 mh = mv * (1.0f / ml);
       float sgn = dot3(mh, wo) < 0.0f ? -1.0f : 1.0f;
       float3 nn = mh * sgn;
+      // with smooth normals: n_s = sgn s / |s|, s = (1 - b1 - b2) N0 + b1 N1 + b2 N2
+      float3 N0 = mk3(0, 0, 0), N1 = N0, N2 = N0, sv = N0;
+      float b1 = 0.0f, b2 = 0.0f;
+      if (SMOOTH) {
+        float3 q = p - v0;
+        float mm = dot3(mv, mv);
+        b1 = dot3(cross3(q, e2), mv) / mm;
+        b2 = dot3(cross3(e1, q), mv) / mm;
+        N0 = xyz(c.vn[c.F[3 * f]]); N1 = xyz(c.vn[c.F[3 * f + 1]]); N2 = xyz(c.vn[c.F[3 * f + 2]]);
+        sv = N0 * (1.0f - b1 - b2) + N1 * b1 + N2 * b2;
+        nn = norm3(sv) * sgn;
+      }
       Mat m = fetch_mat(c.P, key);
       float3 Nb = mk3(0, 0, 0), Pb = Pnext;
       if (c.sec) Pb += xyz(E.pinj[b * Q + i]);   // the vertex's secondary edge sample moves with p
@@ -1045,13 +1080,38 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_adjoint(KCtx c, long long j0, int
       }
       A = mul(g, C) + mul(A, w);
       // n = sgn * m / |m|, p = o + t d with t = ((v0 - o) . m) / (d . m)
-      float3 mbar = (Nb - mh * dot3(Nb, mh)) * (sgn / ml);
+      float3 mbar, e1d = mk3(0, 0, 0), e2d = mk3(0, 0, 0), qbar = mk3(0, 0, 0);
+      if (SMOOTH) {
+        // n_s: to the vertex normals (dN, mapped to the vertices around them after
+        // the sweep) and to the barycentric weights b1 = q.(e2 x m)/M, b2 =
+        // q.(m x e1)/M, q = p - v0, M = m.m
+        float sl = len3(sv);
+        float3 sh = sv * (1.0f / sl);
+        float3 sbar = (Nb - sh * dot3(Nb, sh)) * (sgn / sl);
+        float3 g0 = sbar * (1.0f - b1 - b2), g1 = sbar * b1, g2 = sbar * b2;
+        float* dN = c.dN + 3 * (size_t)c.F[3 * f];
+        atomicAdd(dN, g0.x); atomicAdd(dN + 1, g0.y); atomicAdd(dN + 2, g0.z);
+        dN = c.dN + 3 * (size_t)c.F[3 * f + 1];
+        atomicAdd(dN, g1.x); atomicAdd(dN + 1, g1.y); atomicAdd(dN + 2, g1.z);
+        dN = c.dN + 3 * (size_t)c.F[3 * f + 2];
+        atomicAdd(dN, g2.x); atomicAdd(dN + 1, g2.y); atomicAdd(dN + 2, g2.z);
+        float b1b = dot3(sbar, N1 - N0), b2b = dot3(sbar, N2 - N0);
+        float3 q = p - v0;
+        float iM = 1.0f / dot3(mv, mv);
+        qbar = (cross3(e2, mv) * b1b + cross3(mv, e1) * b2b) * iM;
+        e2d = cross3(mv, q) * (b1b * iM);
+        e1d = cross3(q, mv) * (b2b * iM);
+        mbar = ((cross3(q, e2) - mv * (2.0f * b1)) * b1b + (cross3(e1, q) - mv * (2.0f * b2)) * b2b) * iM;
+        Pb += qbar;
+      } else {
+        mbar = (Nb - mh * dot3(Nb, mh)) * (sgn / ml);
+      }
       float dmv = dot3(d, mv);
       float tb = dot3(Pb, d) / dmv;
       float3 obar = Pb - mv * tb;
-      float3 v0bar = mv * tb;
+      float3 v0bar = mv * tb - qbar;
       mbar += (v0 - p) * tb;
-      float3 e1bar = cross3(e2, mbar), e2bar = cross3(mbar, e1);
+      float3 e1bar = cross3(e2, mbar) + e1d, e2bar = cross3(mbar, e1) + e2d;
       v0bar -= e1bar + e2bar;
       Pnext = obar;
       vals[0] = v0bar.x; vals[1] = v0bar.y; vals[2] = v0bar.z;
@@ -1083,6 +1143,38 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_adjoint(KCtx c, long long j0, int
         }
       }
     }
+  }
+}
+
+// Adjoint of the vertex normals after the sweeps (smooth normals): N_v = M_v /
+// |M_v| gives Mbar_v = (Nbar_v - N_v (N_v . Nbar_v)) / |M_v| (in place in dN);
+// then each face's e1 x e2, a term of the M_v of its three vertices, takes the
+// sum of their Mbar and passes it to its vertices.
+__global__ void k_vn_adj_vertex(KCtx c) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < c.nv; v += gridDim.x * blockDim.x) {
+    float* g = c.dN + 3 * (size_t)v;
+    float3 Nb = mk3(g[0], g[1], g[2]);
+    float4 n4 = c.vn[v];
+    float3 N = xyz(n4);
+    float3 Mb = n4.w > 0.0f ? (Nb - N * dot3(N, Nb)) * (1.0f / n4.w) : mk3(0, 0, 0);
+    g[0] = Mb.x; g[1] = Mb.y; g[2] = Mb.z;
+  }
+}
+
+__global__ void k_vn_adj_face(KCtx c) {
+  float* dV = c.args->dV;
+  if (!dV) return;
+  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < c.nf; f += gridDim.x * blockDim.x) {
+    int a = c.F[3 * f], b = c.F[3 * f + 1], d = c.F[3 * f + 2];
+    float3 cb = mk3(c.dN[3 * a], c.dN[3 * a + 1], c.dN[3 * a + 2]) +
+                mk3(c.dN[3 * b], c.dN[3 * b + 1], c.dN[3 * b + 2]) +
+                mk3(c.dN[3 * d], c.dN[3 * d + 1], c.dN[3 * d + 2]);
+    float3 v0 = fetch_vertex(c.V, a);
+    float3 e1 = fetch_vertex(c.V, b) - v0, e2 = fetch_vertex(c.V, d) - v0;
+    float3 e1b = cross3(e2, cb), e2b = cross3(cb, e1), e0b = -(e1b + e2b);
+    atomicAdd(&dV[3 * b], e1b.x); atomicAdd(&dV[3 * b + 1], e1b.y); atomicAdd(&dV[3 * b + 2], e1b.z);
+    atomicAdd(&dV[3 * d], e2b.x); atomicAdd(&dV[3 * d + 1], e2b.y); atomicAdd(&dV[3 * d + 2], e2b.z);
+    atomicAdd(&dV[3 * a], e0b.x); atomicAdd(&dV[3 * a + 1], e0b.y); atomicAdd(&dV[3 * a + 2], e0b.z);
   }
 }
 
@@ -1163,8 +1255,8 @@ struct SecSample {
 // Edge sample at vertex p (shading normal n, face f0): false if the picked edge
 // is not a candidate (an edge of f0, not a silhouette seen from p in
 // silhouette mode, or wholly at or below the tangent plane).
-__device__ __forceinline__ bool sec_sample(const KCtx& c, float3 p, float3 n, int f0, uint32_t u0, uint32_t u1,
-                                           SecSample& s) {
+__device__ __forceinline__ bool sec_sample(const KCtx& c, float3 p, float3 n, float3 ns, int f0, uint32_t u0,
+                                           uint32_t u1, SecSample& s) {
   int nE = c.n_edges;
   if (nE <= 0) return false;
   s.e = (int)(((unsigned long long)(u0 >> 8) * (unsigned long long)nE) >> 24);
@@ -1184,11 +1276,16 @@ __device__ __forceinline__ bool sec_sample(const KCtx& c, float3 p, float3 n, in
   }
   int2 ev = c.edge_v[s.e];
   float3 A = fetch_vertex(c.V, ev.x), Bv = fetch_vertex(c.V, ev.y);
-  float hA = dot3(n, A - p), hB = dot3(n, Bv - p);
-  if (!(hA > bnd) && !(hB > bnd)) return false;
+  // the part above the tangent plane (and, with shading normals, above the
+  // shading plane too)
   float t0 = 0.0f, t1 = 1.0f;
-  if (!(hA > bnd)) t0 = (bnd - hA) / (hB - hA);
-  if (!(hB > bnd)) t1 = (hA - bnd) / (hA - hB);
+  for (int pl = 0; pl < (c.smooth ? 2 : 1); ++pl) {
+    float3 nc = pl == 0 ? n : ns;
+    float hA = dot3(nc, A - p), hB = dot3(nc, Bv - p);
+    if (!(hA > bnd) && !(hB > bnd)) return false;
+    if (!(hA > bnd)) t0 = fmaxf(t0, (bnd - hA) / (hB - hA));
+    if (!(hB > bnd)) t1 = fminf(t1, (hA - bnd) / (hA - hB));
+  }
   if (!(t1 > t0)) return false;
   s.tau = t0 + unif(u1) * (t1 - t0);
   float3 tv = Bv - A;
@@ -1205,12 +1302,15 @@ __device__ __forceinline__ bool sec_sample(const KCtx& c, float3 p, float3 n, in
   return true;
 }
 
-// shading normal of a recorded vertex (face normal turned toward wo)
-__device__ __forceinline__ float3 vertex_normal(const KCtx& c, int f, float3 wo) {
+// normals of a recorded vertex at p on face f: the face normal turned toward
+// wo (n) and the shading normal (ns: n, or interpolated)
+__device__ __forceinline__ void vertex_normals(const KCtx& c, int f, float3 p, float3 wo, float3& n, float3& ns) {
   float3 v0 = fetch_vertex(c.V, c.F[3 * f]), v1 = fetch_vertex(c.V, c.F[3 * f + 1]),
          v2 = fetch_vertex(c.V, c.F[3 * f + 2]);
   float3 ng = norm3(cross3(v1 - v0, v2 - v0));
-  return dot3(ng, wo) < 0.0f ? -ng : ng;
+  float sgn = dot3(ng, wo) < 0.0f ? -1.0f : 1.0f;
+  n = ng * sgn;
+  ns = c.smooth ? shading_normal(c, f, p, v0, v1, v2, sgn) : n;
 }
 
 // One edge sample per recorded vertex of every camera path of the chunk whose
@@ -1252,14 +1352,15 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_sec_gen(KCtx c, long long j0, int
       float4 r1 = E.r1[b * Q + i];
       int f = __float_as_int(r0.w);
       float3 wo = -xyz(r1);
-      float3 nn = vertex_normal(c, f, wo);
+      float3 nn, ns;
+      vertex_normals(c, f, xyz(r0), wo, nn, ns);
       E.pinj[b * Q + i] = make_float4(0, 0, 0, 0);
       U4 u = philox((uint32_t)ct.x, (uint32_t)ct.y, (uint32_t)(b << 4) | 3u, (uint32_t)ct.z, key.k0, key.k1);
-      ok = sec_sample(c, xyz(r0), nn, f, u.x, u.y, ss);
+      ok = sec_sample(c, xyz(r0), nn, ns, f, u.x, u.y, ss);
       if (b + 1 < nbv) {
         float4 r1n = E.r1[(b + 1) * Q + i];
         int tex = __float_as_int(E.r3[b * Q + i].w);
-        Tn = mul(T, brdf_cos(c.brdf, fetch_mat(c.P, tex), nn, xyz(r1n), wo)) * (1.0f / r1n.w);
+        Tn = mul(T, brdf_cos(c.brdf, fetch_mat(c.P, tex), ns, xyz(r1n), wo)) * (1.0f / r1n.w);
       }
     }
     int q = warp_append(&E.cnt[CNT_SEC], ok);
@@ -1305,9 +1406,11 @@ __global__ void k_sec_raygen(KCtx c, int pass) {
       int4 je = E.sje[job];
       int slot = je.z, b = je.w & 15, f = __float_as_int(a.w);
       float3 wo = -xyz(E.r1[b * Q + slot]);
-      float3 nn = vertex_normal(c, f, wo);
+      float3 nn, ns;
+      vertex_normals(c, f, xyz(a), wo, nn, ns);
       float3 ws = norm3(xyz(w) + xyz(m) * ((sidx & 32) ? SEC_EPS : -SEC_EPS));
-      float3 thr = brdf_cos(c.brdf, fetch_mat(c.P, __float_as_int(E.r3[b * Q + slot].w)), nn, ws, wo);
+      float3 thr = brdf_cos(c.brdf, fetch_mat(c.P, __float_as_int(E.r3[b * Q + slot].w)), ns, ws, wo);
+      if (c.smooth && !(dot3(nn, ws) > 0.0f)) thr = mk3(0, 0, 0);   // below the face
       E.rad[i] = make_float4(0, 0, 0, 0);
       if (thr.x > 0.0f || thr.y > 0.0f || thr.z > 0.0f) {
         E.o[i] = make_float4(a.x, a.y, a.z, 0.0f);

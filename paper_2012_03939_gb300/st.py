@@ -58,7 +58,7 @@ class SceneDesc(C.Structure):
     _fields_ = [("n_vertices", C.c_int), ("n_faces", C.c_int), ("vertices", C.c_void_p), ("faces", C.c_void_p),
                 ("face_params", C.c_void_p), ("brdf", C.c_int), ("n_point_lights", C.c_int),
                 ("point_lights", C.c_void_p), ("env", C.c_void_p), ("color_res", C.c_int), ("bvh_builder", C.c_int),
-                ("rgb_specular", C.c_int)]
+                ("rgb_specular", C.c_int), ("smooth_normals", C.c_int)]
 
 
 class RenderOpts(C.Structure):
@@ -155,7 +155,7 @@ class Scene:
 
     def __init__(self, vertices: torch.Tensor, faces: torch.Tensor, face_params: torch.Tensor, brdf: str = "ggx",
                  light_pos=None, light_intensity=None, env: Optional[np.ndarray] = None, stream=None,
-                 color_res: int = 0, bvh_builder: str = "ploc"):
+                 color_res: int = 0, bvh_builder: str = "ploc", smooth_normals: bool = False):
         dev = torch.device("cuda", torch.cuda.current_device())
         self.vertices = vertices.detach().to(dev, torch.float32).contiguous()
         self.faces = faces.detach().to(dev, torch.int32).contiguous()
@@ -178,7 +178,7 @@ class Scene:
                          self.face_params.data_ptr(), {"ggx": 0, "beckmann": 1}[brdf], len(lp),
                          C.addressof(self._lights), None if self._env is None else C.addressof(self._env),
                          int(color_res), {"ploc": BVH_PLOC, "lbvh": BVH_LBVH}[bvh_builder],
-                         1 if self.face_params.shape[1] == 7 else 0)
+                         1 if self.face_params.shape[1] == 7 else 0, int(bool(smooth_normals)))
         h = C.c_void_p()
         _check(lib().st_scene_create(C.byref(desc), _stream(stream), C.byref(h)))
         self.handle = h
@@ -187,7 +187,8 @@ class Scene:
     def from_scene(cls, sc, vertices=None, device="cuda", **kw):
         V = torch.as_tensor(sc.vertices if vertices is None else vertices, dtype=torch.float32, device=device)
         return cls(V, torch.as_tensor(sc.faces, device=device), torch.as_tensor(sc.face_params, device=device),
-                   sc.brdf, sc.light_pos, sc.light_intensity, sc.env, color_res=getattr(sc, "color_res", 0), **kw)
+                   sc.brdf, sc.light_pos, sc.light_intensity, sc.env, color_res=getattr(sc, "color_res", 0),
+                   smooth_normals=bool(getattr(sc, "smooth_normals", False)), **kw)
 
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:
