@@ -630,7 +630,90 @@ std::vector<Edge> edge_list(const Scene& s) {
 
 // Secondary-visibility edge sampling context: the mesh's edge list and the
 // candidate rule (0 = silhouettes as seen from the vertex, 1 = every edge).
-struct SecCtx { const std::vector<Edge>* E; int mode; };
+// Hierarchy over the edges for the importance-sampled secondary edge pick:
+// leaves are blocks of G consecutive edges in edge order (at most 2^14 blocks),
+// a complete binary tree above them in heap order (root 1, leaf i at 2^L + i);
+// each node keeps the box of its edges' endpoints and their summed length.
+struct EdgeTree {
+  int G = 4, L = 0, nleaf = 0, nE = 0;
+  std::vector<V3d> lo, hi;
+  std::vector<double> S;
+};
+
+EdgeTree edge_tree(const Scene& s, const std::vector<Edge>& E) {
+  EdgeTree t;
+  t.nE = (int)E.size();
+  t.G = std::max(4, (t.nE + (1 << 14) - 1) >> 14);
+  t.nleaf = (t.nE + t.G - 1) / t.G;
+  while ((1 << t.L) < t.nleaf) ++t.L;
+  size_t nn = (size_t)2 << t.L;
+  t.lo.assign(nn, V3d{INFINITY, INFINITY, INFINITY});
+  t.hi.assign(nn, V3d{-INFINITY, -INFINITY, -INFINITY});
+  t.S.assign(nn, 0.0);
+  auto grow = [&](size_t k, const V3d& a) {
+    t.lo[k] = {std::min(t.lo[k].x, a.x), std::min(t.lo[k].y, a.y), std::min(t.lo[k].z, a.z)};
+    t.hi[k] = {std::max(t.hi[k].x, a.x), std::max(t.hi[k].y, a.y), std::max(t.hi[k].z, a.z)};
+  };
+  for (int i = 0; i < t.nleaf; ++i) {
+    size_t k = ((size_t)1 << t.L) + i;
+    for (int e = i * t.G; e < std::min(t.nE, (i + 1) * t.G); ++e) {
+      const V3d &A = s.vert[E[e].a], &B = s.vert[E[e].b];
+      grow(k, A);
+      grow(k, B);
+      t.S[k] += len(B - A);
+    }
+  }
+  for (size_t k = ((size_t)1 << t.L) - 1; k >= 1; --k) {
+    const V3d &la = t.lo[2 * k], &lb = t.lo[2 * k + 1], &ha = t.hi[2 * k], &hb = t.hi[2 * k + 1];
+    t.lo[k] = {std::min(la.x, lb.x), std::min(la.y, lb.y), std::min(la.z, lb.z)};
+    t.hi[k] = {std::max(ha.x, hb.x), std::max(ha.y, hb.y), std::max(ha.z, hb.z)};
+    t.S[k] = t.S[2 * k] + t.S[2 * k + 1];
+  }
+  return t;
+}
+
+// Importance of node k at a path vertex (p, tangent plane normal n, band bnd):
+// 0 when the whole box lies at or below the plane (no edge in it can be
+// sampled), else the summed length over max(d^2, diag^2 / 4), d the distance
+// from p to the box.
+double tree_weight(const EdgeTree& t, size_t k, const V3d& p, const V3d& n, double bnd) {
+  if (!(t.S[k] > 0)) return 0.0;
+  const V3d &lo = t.lo[k], &hi = t.hi[k];
+  double top = (n.x > 0 ? hi.x - p.x : lo.x - p.x) * n.x + (n.y > 0 ? hi.y - p.y : lo.y - p.y) * n.y +
+               (n.z > 0 ? hi.z - p.z : lo.z - p.z) * n.z;
+  if (!(top > bnd)) return 0.0;
+  double dx = std::max(lo.x - p.x, std::max(0.0, p.x - hi.x));
+  double dy = std::max(lo.y - p.y, std::max(0.0, p.y - hi.y));
+  double dz = std::max(lo.z - p.z, std::max(0.0, p.z - hi.z));
+  double ex = hi.x - lo.x, ey = hi.y - lo.y, ez = hi.z - lo.z;
+  double den = std::max(dx * dx + dy * dy + dz * dz, 0.25 * (ex * ex + ey * ey + ez * ez));
+  return t.S[k] / std::max(den, 1e-30);
+}
+
+// Descends the tree with one uniform per level (level j: word j % 4 of the
+// draw (c0, c1, b<<4 | (4 + j/4), stream)), then picks uniformly in the leaf
+// block with the word uleaf. Returns the edge or -1; prob = its probability.
+int tree_pick(const EdgeTree& t, const Rng& rng, uint32_t c0, uint32_t c1, int b, uint32_t stream, const V3d& p,
+              const V3d& n, double bnd, uint32_t uleaf, double& prob) {
+  size_t k = 1;
+  prob = 1.0;
+  U4 u{};
+  for (int j = 0; j < t.L; ++j) {
+    if (j % 4 == 0) u = rng.draw(c0, c1, (uint32_t)(b << 4) | (4u + (uint32_t)(j / 4)), stream);
+    double wa = tree_weight(t, 2 * k, p, n, bnd), wb = tree_weight(t, 2 * k + 1, p, n, bnd);
+    if (!(wa + wb > 0)) return -1;
+    if (unif(u.w[j % 4]) < wa / (wa + wb)) { k = 2 * k; prob *= wa / (wa + wb); }
+    else { k = 2 * k + 1; prob *= wb / (wa + wb); }
+  }
+  int first = (int)(k - ((size_t)1 << t.L)) * t.G;
+  int cnt = std::min(t.G, t.nE - first);
+  if (cnt <= 0) return -1;
+  prob /= cnt;
+  return first + (int)(((uint64_t)(uleaf >> 8) * (uint64_t)cnt) >> 24);
+}
+
+// mode: silhouettes or every edge; sampling 1: uniform over all edges, 2: by the tree
+struct SecCtx { const std::vector<Edge>* E; int mode; int sampling = 1; const EdgeTree* T = nullptr; };
 
 // Signed distance of p from the plane of face f (unit normal of the face's winding).
 double face_side(const Scene& s, int f, const V3d& p) {
@@ -667,11 +750,23 @@ void secondary_edge(const Scene& s, const Rng& rng, int B, const Lights& lt, int
   if (E.empty()) return;
   U4 u = rng.draw(c0, c1, (uint32_t)(b << 4) | 3u, stream);
   uint64_t nE = E.size();
-  const Edge& e = E[(size_t)(((uint64_t)(u.w[0] >> 8) * nE) >> 24)];
-  if (e.f[0] == f0 || (e.nf == 2 && e.f[1] == f0)) return;   // its arc lies on the vertex's horizon
   V3d pv = val(p);
-  V3d A = s.vert[e.a], Bv = s.vert[e.b];
   double bnd = SEC_BAND * (1.0 + std::max(std::fabs(pv.x), std::max(std::fabs(pv.y), std::fabs(pv.z))));
+  size_t ei;
+  double inv_p;   // 1 / pick probability
+  if (sc.sampling == 2) {
+    double pr;
+    int k = tree_pick(*sc.T, rng, c0, c1, b, stream, pv, nv, bnd, u.w[0], pr);
+    if (k < 0) return;
+    ei = (size_t)k;
+    inv_p = 1.0 / pr;
+  } else {
+    ei = (size_t)(((uint64_t)(u.w[0] >> 8) * nE) >> 24);
+    inv_p = (double)nE;
+  }
+  const Edge& e = E[ei];
+  if (e.f[0] == f0 || (e.nf == 2 && e.f[1] == f0)) return;   // its arc lies on the vertex's horizon
+  V3d A = s.vert[e.a], Bv = s.vert[e.b];
   if (sc.mode == 0) {
     double s1 = face_side(s, e.f[0], pv);
     bool sil;
@@ -706,7 +801,7 @@ void secondary_edge(const Scene& s, const Rng& rng, int B, const Lights& lt, int
   double sn = len(cr);
   if (!(sn > SEC_SMIN)) return;
   V3d mh = scl(cr, 1.0 / sn);
-  double coef = sn * (double)nE * l * (t1 - t0) / (r * r);
+  double coef = sn * inv_p * l * (t1 - t0) / (r * r);
   MatT<double> m = Access<double>::params(s, nullptr, (int)tex);
   double g[2][3];
   for (int side = 0; side < 2; ++side) {
@@ -1116,6 +1211,7 @@ void orc_closest_hit(const orc_scene* in, const double* rays, int n, int exclude
 
 static bool check_common(const orc_view* views, int n_views, const orc_params* p) {
   if (!views || n_views <= 0 || !p || p->max_bounces < 1 || p->max_bounces > MAX_B) return false;
+  if (p->secondary < 0 || p->secondary > 2) return false;
   for (int v = 0; v < n_views; ++v)
     if (views[v].width <= 0 || views[v].height <= 0 || views[v].spp <= 0 || views[v].n_lights < 0 ||
         views[v].n_lights > 2)
@@ -1198,8 +1294,10 @@ long long orc_grad_pixels(const orc_scene* in, const orc_view* views, int n_view
   std::vector<std::vector<double>> gv(nt, std::vector<double>(3 * (size_t)s.nv, 0.0));
   std::vector<std::vector<double>> gf(nt, std::vector<double>((size_t)s.np * s.nf * s.ntex, 0.0));
   std::vector<Edge> E;
+  EdgeTree T;
   if (p->secondary) E = edge_list(s);
-  SecCtx sc{&E, p->edge_mode};
+  if (p->secondary == 2) T = edge_tree(s, E);
+  SecCtx sc{&E, p->edge_mode, p->secondary, &T};
   const SecCtx* sec = p->secondary ? &sc : nullptr;
   parallel_for(n, nt, [&](int tid, int i) {
     const double* w = dLdI + 3 * (size_t)i;
@@ -1430,8 +1528,10 @@ long long orc_trace_screen(const orc_scene* in, const orc_view* view, const orc_
   Vars vars;
   Dual L[3];
   std::vector<Edge> E;
+  EdgeTree T;
   if (p->secondary) E = edge_list(s);
-  SecCtx sc{&E, p->edge_mode};
+  if (p->secondary == 2) T = edge_tree(s, E);
+  SecCtx sc{&E, p->edge_mode, p->secondary, &T};
   trace_path<Dual>(s, rng, p->max_bounces, c.lt, c.eye, d, c0, c1, stream, &vars, L, seg, nullptr,
                    p->secondary ? &sc : nullptr);
   for (int k = 0; k < 3; ++k) rgb[k] = L[k].v;
@@ -1439,6 +1539,39 @@ long long orc_trace_screen(const orc_scene* in, const orc_view* view, const orc_
   scatter_grad(vars, loss, d_verts, d_face, s.np);
   if (g_dual_overflow) return -1;
   return seg;
+}
+
+int orc_sec_edge_pmf(const orc_scene* in, const double* p, const double* n, double bnd, double* pmf) {
+  Scene s;
+  if (!load_scene(in, s)) return -1;
+  std::vector<Edge> E = edge_list(s);
+  EdgeTree t = edge_tree(s, E);
+  V3d pv{p[0], p[1], p[2]}, nv{n[0], n[1], n[2]};
+  for (int leaf = 0; leaf < t.nleaf; ++leaf) {
+    size_t k = ((size_t)1 << t.L) + leaf;
+    double pr = 1.0;
+    for (size_t c = k; c > 1; c /= 2) {
+      size_t par = c / 2;
+      double wa = tree_weight(t, 2 * par, pv, nv, bnd), wb = tree_weight(t, 2 * par + 1, pv, nv, bnd);
+      pr *= wa + wb > 0 ? (c % 2 == 0 ? wa : wb) / (wa + wb) : 0.0;
+    }
+    int first = leaf * t.G, cnt = std::min(t.G, t.nE - first);
+    for (int e = first; e < first + cnt; ++e) pmf[e] = pr / cnt;
+  }
+  return (int)E.size();
+}
+
+int orc_sec_edge_picks(const orc_scene* in, unsigned long long seed, uint32_t c1, int b, uint32_t stream,
+                       const double* p, const double* n, double bnd, const uint32_t* uleaf, int count, int* edge,
+                       double* prob) {
+  Scene s;
+  if (!load_scene(in, s) || count < 0) return -1;
+  std::vector<Edge> E = edge_list(s);
+  EdgeTree t = edge_tree(s, E);
+  Rng rng{(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+  V3d pv{p[0], p[1], p[2]}, nv{n[0], n[1], n[2]};
+  for (int i = 0; i < count; ++i) edge[i] = tree_pick(t, rng, (uint32_t)i, c1, b, stream, pv, nv, bnd, uleaf[i], prob[i]);
+  return count;
 }
 
 long long orc_trace_screen_taped(const orc_scene* in, const orc_view* view, const orc_params* p, double px,

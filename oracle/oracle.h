@@ -63,7 +63,8 @@ typedef struct {
   int edge_mode;    /* 0 = silhouette edges, 1 = every mesh edge */
   int edge_spp;     /* edge samples per pixel; 0 = the view's spp */
   int n_threads;    /* 0 = all hardware threads */
-  int secondary;    /* gradients: add the secondary-visibility edge term at every path vertex */
+  int secondary;    /* gradients: add the secondary-visibility edge term at every path vertex: 0 = off,
+                       1 = one edge picked uniformly, 2 = picked through the edge hierarchy (importance) */
 } orc_params;
 
 /* Pixel values for a list of pixels (view index, x, y): out [n][3]. Returns the
@@ -147,6 +148,16 @@ int orc_alias_pick(const double* prob, const int* alias, int n, uint32_t u0, uin
 
 /* Mesh-colors texel index k(r, t, alpha, beta) (Sec. 3.3). */
 long long orc_mesh_color_index(int r, long long t, double alpha, double beta);
+
+/* Secondary edge pick through the edge hierarchy, for tests: the probability of
+ * every edge (pmf [E], edge order) at a vertex p with tangent-plane normal n and
+ * band bnd; returns E or -1. */
+int orc_sec_edge_pmf(const orc_scene* s, const double* p, const double* n, double bnd, double* pmf);
+/* count picks at the same vertex, pick i with the counters (i, c1) of vertex b
+ * and stream: edge [count] (-1 if every node is below the plane) and prob. */
+int orc_sec_edge_picks(const orc_scene* s, unsigned long long seed, uint32_t c1, int b, uint32_t stream,
+                       const double* p, const double* n, double bnd, const uint32_t* uleaf, int count, int* edge,
+                       double* prob);
 
 #ifdef __cplusplus
 }

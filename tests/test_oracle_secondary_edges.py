@@ -129,7 +129,9 @@ def test_closed_form_occluded_floor_value():
     assert exp.min() < 0.8 * exp.max()     # the pixels include the penumbra
 
 
-def test_secondary_edge_gradient_matches_closed_form():
+@pytest.mark.parametrize("sampling", [1, 2])
+def test_secondary_edge_gradient_matches_closed_form(sampling):
+    # sampling 1: one edge picked uniformly; 2: picked through the edge hierarchy
     sc = _occluder_scene(spp=512)
     pix = _free_pixels(sc)
     V0 = sc.vertices.astype(np.float64)
@@ -146,7 +148,7 @@ def test_secondary_edge_gradient_matches_closed_form():
     ests, plain = [], []
     osc = O.OracleScene(sc)
     for seed in range(8):
-        dv, _, _ = O.grad_pixels(osc, O.params(1, 700 + seed, secondary=1), pix, w)
+        dv, _, _ = O.grad_pixels(osc, O.params(1, 700 + seed, secondary=sampling), pix, w)
         ests.append(dv)
         if seed < 2:
             plain.append(O.grad_pixels(osc, O.params(1, 700 + seed), pix, w)[0])
@@ -238,7 +240,8 @@ def test_two_bounce_quadrature_value():
     assert exp.min() > 0.02
 
 
-def test_secondary_edge_gradient_two_bounces_matches_quadrature():
+@pytest.mark.parametrize("sampling", [1, 2])
+def test_secondary_edge_gradient_two_bounces_matches_quadrature(sampling):
     # every bit of the floor's light takes two bounces, so the gradient exercises
     # side paths that continue to a shaded vertex (edges seen from the floor) and
     # edges seen from the triangle's underside (the floor's boundary), with the
@@ -257,10 +260,72 @@ def test_secondary_edge_gradient_two_bounces_matches_quadrature():
             Vm[vi, k] -= h
             exp[vi, k] = ((_two_bounce_pixels(sc, Vp, pix) - _two_bounce_pixels(sc, Vm, pix)) * w).sum() / (2 * h)
     osc = O.OracleScene(sc)
-    ests = np.array([O.grad_pixels(osc, O.params(2, 800 + s, secondary=1), pix, w)[0] for s in range(8)])
+    ests = np.array([O.grad_pixels(osc, O.params(2, 800 + s, secondary=sampling), pix, w)[0] for s in range(8)])
     mean, se = ests.mean(0), ests.std(0, ddof=1) / math.sqrt(len(ests))
     scale = np.abs(exp).max()
     assert np.all(np.abs(mean - exp) < 4 * se + 2e-3 * scale), (mean, exp, se)
     # the pin tells the full estimator from one without the boundary term
     plain = np.array([O.grad_pixels(osc, O.params(2, 800 + s), pix, w)[0] for s in range(4)]).mean(0)
     assert (np.abs(plain - exp) / (se + 1e-3 * scale)).max() > 10, (plain, exp, se)
+
+
+# ---------------------------------------------------------------------------- edge hierarchy (importance pick)
+def _tangent_frames(sc, n, seed):
+    """Points just off random faces of the mesh with the face normal: (p, n) pairs."""
+    rng = np.random.default_rng(seed)
+    V = sc.vertices.astype(np.float64)
+    out = []
+    for f in rng.integers(0, len(sc.faces), size=n):
+        a, b, c = V[sc.faces[f]]
+        u, v = rng.random(2)
+        if u + v > 1:
+            u, v = 1 - u, 1 - v
+        m = np.cross(b - a, c - a)
+        m /= np.linalg.norm(m)
+        out.append((a + u * (b - a) + v * (c - a) + 1e-4 * m, m * rng.choice([-1.0, 1.0])))
+    return out
+
+
+def test_hierarchy_pick_probabilities():
+    # every edge with a part above the tangent plane can be picked (so the
+    # estimator stays unbiased); the mass never exceeds one; a pick returns the
+    # probability the enumeration gives; picks follow the probabilities
+    sc = S.small_variant(S.make("env"), n_views=1, max_res=8, spp=1)
+    osc = O.OracleScene(sc)
+    V = sc.vertices.astype(np.float64)
+    ev = np.unique(np.sort(np.concatenate([sc.faces[:, [0, 1]], sc.faces[:, [1, 2]], sc.faces[:, [2, 0]]]), 1), axis=0)
+    for k, (p, n) in enumerate(_tangent_frames(sc, 6, 4)):
+        bnd = 1e-5 * (1 + np.abs(p).max())
+        pmf = O.sec_edge_pmf(osc, p, n, bnd)
+        assert len(pmf) == len(ev) and pmf.sum() <= 1 + 1e-12
+        above = np.maximum((V[ev[:, 0]] - p) @ n, (V[ev[:, 1]] - p) @ n) > bnd
+        assert np.all(pmf[above] > 0) and np.all(pmf[~above & (pmf > 0)] >= 0)
+        if k < 2:
+            N = 40000
+            e, pr = O.sec_edge_picks(osc, 11, k, 1, 0, p, n, bnd, np.random.default_rng(k).integers(0, 1 << 32, N))
+            ok = e >= 0
+            np.testing.assert_allclose(pr[ok], pmf[e[ok]], rtol=1e-12)
+            cnt = np.bincount(e[ok], minlength=len(pmf)).astype(np.float64)
+            # chi^2 over 40 groups of edges of equal probability mass (most edges are rare)
+            order = np.argsort(pmf)
+            grp = np.minimum((np.cumsum(pmf[order]) / pmf.sum() * 40).astype(int), 39)
+            exp_g = np.bincount(grp, weights=N * pmf[order], minlength=40)
+            got_g = np.bincount(grp, weights=cnt[order], minlength=40)
+            chi2 = ((got_g - exp_g) ** 2 / exp_g).sum()
+            assert chi2 < 39 + 6 * math.sqrt(2 * 39), chi2
+            assert abs(cnt.sum() - N * pmf.sum()) < 6 * math.sqrt(N)
+
+
+def test_hierarchy_pick_lowers_the_variance_of_the_secondary_term():
+    # torus knot (self-occluding): the same gradient, estimated with the
+    # uniform pick and with the hierarchy, seed by seed
+    sc = S.small_variant(S.make("env"), n_views=1, max_res=24, spp=2)
+    osc = O.OracleScene(sc)
+    pix = O.all_pixels(sc)
+    w = np.random.default_rng(1).normal(size=(len(pix), 3))
+    std = {}
+    for sampling in (1, 2):
+        terms = [O.grad_pixels(osc, O.params(2, 100 + s, secondary=sampling), pix, w)[0] -
+                 O.grad_pixels(osc, O.params(2, 100 + s), pix, w)[0] for s in range(6)]
+        std[sampling] = np.linalg.norm(np.std(terms, axis=0))
+    assert 0 < std[2] < std[1] / 4, std
