@@ -89,6 +89,8 @@ typedef struct {
  * from the camera and from a point offset from it, Sec. 4); the scene's and
  * the view's lights together are at most ST_MAX_LIGHTS. */
 #define ST_MAX_VIEW_LIGHTS 2
+#define ST_SEC_PICK_TREE 0        /* st_render_opts.sec_pick: importance through the edge hierarchy */
+#define ST_SEC_PICK_UNIFORM 1     /* st_render_opts.sec_pick: uniform over all edges */
 typedef struct {
   float eye[3], target[3], up[3];
   float fov_y_deg;
@@ -146,6 +148,12 @@ typedef struct {
                        the shadow rays' visibility bits (bit j = point light j seen, bit 8 = the environment sample
                        seen) when any was traced; basis 0xcbf29ce484222325, prime 0x100000001b3. Equal signatures
                        with another implementation of the estimator mean the same decisions were taken. */
+  int sec_pick;     /* backward, secondary edge term: how each path vertex picks its edge. ST_SEC_PICK_TREE (0,
+                       default): through a hierarchy over the edges (Li et al. sample secondary edges by
+                       importance, Sec. 3.2): blocks of consecutive edges (at most 2^14) under a binary tree of
+                       boxes and summed lengths; a node weighs 0 below the vertex's tangent plane, else its length
+                       over max(d^2, diag^2/4); one uniform per level, uniform within the block; the sample is
+                       divided by its probability. ST_SEC_PICK_UNIFORM: one edge uniformly from all. */
 } st_render_opts;
 
 typedef struct {

@@ -217,6 +217,7 @@ struct Plan {
   long long pixels = 0;       // sum of W*H: the primary-visibility bin space
   bool interior = false, edges = false;
   bool sec = false;           // secondary-visibility edge samples at every camera-path vertex
+  bool sec_tree = false;      // ... picked through the edge hierarchy
   bool shadow = false;        // point-light shadow-edge samples
   std::vector<int2> pairs;    // shadow edges: (view, light) of each candidate list
   bool sig = false;           // forward: path signatures
@@ -355,6 +356,7 @@ KCtx make_ctx(st_scene* s, const Plan& p) {
   c.bin_cap = s->bin_cap; c.bin_pixels = p.pixels;
   c.cull = s->closed ? 1 : 0; c.mstat = s->mstat;
   c.smooth = s->smooth ? 1 : 0; c.vn = s->vnrm; c.dN = s->dN; c.nv = s->nv;
+  c.sec_tree = p.sec_tree ? 1 : 0; c.et_G = s->et_G; c.et_L = s->et_L; c.et_lo = s->et_lo; c.et_hi = s->et_hi;
   c.acc = s->acc;
   c.views = s->d_views; c.segs = s->d_segs; c.n_segs = (int)p.segs.size();
   c.args = s->d_args; c.B = p.B; c.e = s->eng; c.e.records = p.kind == 1; c.err = s->d_err;
@@ -496,6 +498,14 @@ st_status enqueue_call(st_scene* s, const Plan& p, int Q, cudaStream_t st, bool 
     s->launches++;
   }
   if (p.kind == 1 && s->smooth) ST_CUDA(cudaMemsetAsync(s->dN, 0, 3 * sizeof(float) * s->nv, st));
+  if (p.sec_tree) {
+    // the edge hierarchy on the current vertices: leaves, then level by level up to the root
+    int nl = 1 << s->et_L;
+    k_etree_leaves<<<std::min((nl + 255) / 256, 4 * std::max(s->sm_count, 1)), 256, 0, st>>>(c, s->et_lo, s->et_hi);
+    for (int l = s->et_L - 1; l >= 0; --l)
+      k_etree_level<<<std::min(((1 << l) + 255) / 256, 4 * std::max(s->sm_count, 1)), 256, 0, st>>>(s->et_lo, s->et_hi, l);
+    s->launches += 1 + s->et_L;
+  }
   if (p.bins) {
     // primary-visibility bins of every view: count, scan, fill
     long long P = p.pixels;
@@ -564,7 +574,7 @@ st_status enqueue_call(st_scene* s, const Plan& p, int Q, cudaStream_t st, bool 
 std::vector<long long> graph_key(const Plan& p, int Q, const st_scene* s) {
   std::vector<long long> k = {p.kind, p.B, (long long)p.views.size(), Q, p.o.edge_term, p.o.edge_mode, p.o.edge_spp,
                               p.interior, p.edges, p.o.count_visits, p.bins,
-                              p.o.persist_blocks, s->bin_cap, p.max_vl, p.sig};
+                              p.o.persist_blocks, s->bin_cap, p.max_vl, p.sig, p.sec_tree};
   for (auto& v : p.views) {
     k.push_back(v.W); k.push_back(v.H); k.push_back(v.spp); k.push_back(v.pix_off); k.push_back(v.nvl);
   }
@@ -588,6 +598,8 @@ st_status plan_call(st_scene* s, const st_view* views, int n_views, int default_
   p.interior = kind == 1 && want_interior;
   p.edges = kind == 1 && (p.o.edge_term & ST_EDGE_TERM_PRIMARY);
   p.sec = p.interior && (p.o.edge_term & ST_EDGE_TERM_SECONDARY) && s->n_edges > 0;
+  if (p.o.sec_pick != ST_SEC_PICK_TREE && p.o.sec_pick != ST_SEC_PICK_UNIFORM) return fail(ST_ERR_INVALID_ARG, "bad sec_pick");
+  p.sec_tree = p.sec && p.o.sec_pick == ST_SEC_PICK_TREE;
   p.shadow = kind == 1 && (p.o.edge_term & ST_EDGE_TERM_SHADOW) && s->n_edges > 0;
   long long base = 0;
   for (int i = 0; i < n_views; ++i) {
@@ -759,6 +771,7 @@ void destroy(st_scene* s) {
   dfree(s->sh_flag); dfree(s->sh_cand); dfree(s->sh_ncand); dfree(s->d_pairs); dfree(s->d_views); dfree(s->d_segs);
   dfree(s->bin_start); dfree(s->bin_cur); dfree(s->bin_list); dfree(s->bin_ok); dfree(s->bin_part);
   dfree(s->acc); dfree(s->sacc); dfree(s->mstat); dfree(s->vnrm); dfree(s->vf_start); dfree(s->vf_list); dfree(s->dN);
+  dfree(s->et_lo); dfree(s->et_hi);
   if (s->bin_total_host) cudaFreeHost(s->bin_total_host);
   dfree(s->d_args); dfree(s->d_err);
   for (auto& e : s->ev) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
@@ -863,6 +876,15 @@ st_status st_scene_create(const st_scene_desc* d, void* stream, st_scene** out) 
   chk(dalloc(&s->lights, 2 * (size_t)std::max(s->nl, 1))); chk(dalloc(&s->edge_v, ev.size()));
   chk(dalloc(&s->edge_f, ef.size())); chk(dalloc(&s->d_args, 1)); chk(dalloc(&s->d_err, 1));
   chk(dalloc(&s->mstat, 1));
+  {
+    // edge hierarchy: at most 2^14 leaf blocks of at least 4 edges
+    int nE = s->n_edges;
+    s->et_G = std::max(4, (nE + (1 << 14) - 1) >> 14);
+    s->et_nleaf = (nE + s->et_G - 1) / s->et_G;
+    s->et_L = 0;
+    while ((1 << s->et_L) < s->et_nleaf) ++s->et_L;
+    chk(dalloc(&s->et_lo, (size_t)2 << s->et_L)); chk(dalloc(&s->et_hi, (size_t)2 << s->et_L));
+  }
   std::vector<int> vfs, vfl;
   if (s->smooth) {
     // faces around each vertex, in face order (CSR)

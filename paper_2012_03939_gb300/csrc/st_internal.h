@@ -99,6 +99,10 @@ struct st_scene {
   int* vf_start = nullptr;       // [V + 1] faces around each vertex (CSR, face order)
   int* vf_list = nullptr;        // [3F]
   float* dN = nullptr;           // [V][3] backward scratch: adjoint of the vertex normals (smooth)
+  // hierarchy over the edges for the secondary pick: blocks of et_G edges, 2^et_L leaves
+  int et_G = 4, et_L = 0, et_nleaf = 0;
+  float4* et_lo = nullptr;       // [2^(L+1)] box low corner, summed edge length (heap order, root 1)
+  float4* et_hi = nullptr;       // [2^(L+1)] box high corner
   float* verts = nullptr;        // [V*3]
   int* faces = nullptr;          // [F*3]
   float4* params = nullptr;      // [F*ntex*2] per texel: (kd_r, kd_g, kd_b, ks_r), (roughness, ks_g, ks_b, 0)

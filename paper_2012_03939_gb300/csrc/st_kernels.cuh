@@ -54,6 +54,10 @@ struct KCtx {
   int smooth;             // interpolated shading normals from vn
   const float4* vn;       // [V] vertex normal N_v and |M_v|
   float* dN;              // backward with smooth normals: [V][3] adjoint of the vertex normals
+  int sec_tree;           // secondary pick through the edge hierarchy (else uniform)
+  int et_G, et_L;         // edges per leaf block, tree levels
+  const float4* et_lo;    // tree nodes (heap order): box low corner + summed length, high corner
+  const float4* et_hi;
   const DevView* views;
   const Seg* segs;
   int n_segs;
@@ -1246,6 +1250,55 @@ __device__ __forceinline__ float face_side(const KCtx& c, int f, float3 p) {
   return dot3(m, p - a);
 }
 
+// Hierarchy over the edges (importance pick of the secondary edge, Li et al.,
+// Sec. 3.2): leaf i holds edges [i G, (i + 1) G) in edge order, with the box of
+// their endpoints and their summed length; internal node k unites 2k and 2k + 1.
+// Rebuilt by every call that samples with it (the vertices may have moved).
+__global__ void k_etree_leaves(KCtx c, float4* lo, float4* hi) {
+  const int nleaf = 1 << c.et_L;
+  const float INF = __int_as_float(0x7f800000);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nleaf; i += gridDim.x * blockDim.x) {
+    float3 l = mk3(INF, INF, INF), h = mk3(-INF, -INF, -INF);
+    float S = 0.0f;
+    int e1 = min(c.n_edges, (i + 1) * c.et_G);
+    for (int e = i * c.et_G; e < e1; ++e) {
+      int2 ev = c.edge_v[e];
+      float3 a = fetch_vertex(c.V, ev.x), b = fetch_vertex(c.V, ev.y);
+      l = mk3(fminf(l.x, fminf(a.x, b.x)), fminf(l.y, fminf(a.y, b.y)), fminf(l.z, fminf(a.z, b.z)));
+      h = mk3(fmaxf(h.x, fmaxf(a.x, b.x)), fmaxf(h.y, fmaxf(a.y, b.y)), fmaxf(h.z, fmaxf(a.z, b.z)));
+      S += len3(b - a);
+    }
+    lo[nleaf + i] = make_float4(l.x, l.y, l.z, S);
+    hi[nleaf + i] = make_float4(h.x, h.y, h.z, 0.0f);
+  }
+}
+
+// nodes [2^level, 2^(level+1)) from their children
+__global__ void k_etree_level(float4* lo, float4* hi, int level) {
+  const int n = 1 << level;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int k = n + i;
+    float4 la = lo[2 * k], lb = lo[2 * k + 1], ha = hi[2 * k], hb = hi[2 * k + 1];
+    lo[k] = make_float4(fminf(la.x, lb.x), fminf(la.y, lb.y), fminf(la.z, lb.z), la.w + lb.w);
+    hi[k] = make_float4(fmaxf(ha.x, hb.x), fmaxf(ha.y, hb.y), fmaxf(ha.z, hb.z), 0.0f);
+  }
+}
+
+// Importance of node k at a vertex (p, tangent-plane normal n, band bnd): 0 when
+// its box lies at or below the plane, else summed length / max(d^2, diag^2 / 4).
+__device__ __forceinline__ float etree_weight(const KCtx& c, int k, float3 p, float3 n, float bnd) {
+  float4 lo = c.et_lo[k], hi = c.et_hi[k];
+  if (!(lo.w > 0.0f)) return 0.0f;
+  float top = (n.x > 0.0f ? hi.x - p.x : lo.x - p.x) * n.x + (n.y > 0.0f ? hi.y - p.y : lo.y - p.y) * n.y +
+              (n.z > 0.0f ? hi.z - p.z : lo.z - p.z) * n.z;
+  if (!(top > bnd)) return 0.0f;
+  float dx = fmaxf(lo.x - p.x, fmaxf(0.0f, p.x - hi.x)), dy = fmaxf(lo.y - p.y, fmaxf(0.0f, p.y - hi.y)),
+        dz = fmaxf(lo.z - p.z, fmaxf(0.0f, p.z - hi.z));
+  float ex = hi.x - lo.x, ey = hi.y - lo.y, ez = hi.z - lo.z;
+  float den = fmaxf(dx * dx + dy * dy + dz * dz, 0.25f * (ex * ex + ey * ey + ez * ez));
+  return lo.w / fmaxf(den, 1e-30f);
+}
+
 struct SecSample {
   int e;
   float tau, weight;
@@ -1255,14 +1308,40 @@ struct SecSample {
 // Edge sample at vertex p (shading normal n, face f0): false if the picked edge
 // is not a candidate (an edge of f0, not a silhouette seen from p in
 // silhouette mode, or wholly at or below the tangent plane).
+// ct, b, key: the vertex's counters, for the hierarchy's per-level uniforms
+// (draw (c0, c1, b<<4 | (4 + j/4), stream), word j % 4 at level j)
 __device__ __forceinline__ bool sec_sample(const KCtx& c, float3 p, float3 n, float3 ns, int f0, uint32_t u0,
-                                           uint32_t u1, SecSample& s) {
+                                           uint32_t u1, int4 ct, int b, Key key, SecSample& s) {
   int nE = c.n_edges;
   if (nE <= 0) return false;
-  s.e = (int)(((unsigned long long)(u0 >> 8) * (unsigned long long)nE) >> 24);
+  float bnd = SEC_BAND * (1.0f + fmaxf(fabsf(p.x), fmaxf(fabsf(p.y), fabsf(p.z))));
+  float inv_p;   // 1 / pick probability
+  if (c.sec_tree) {
+    int k = 1;
+    float pr = 1.0f;
+    U4 u = {0, 0, 0, 0};
+    for (int j = 0; j < c.et_L; ++j) {
+      if ((j & 3) == 0)
+        u = philox((uint32_t)ct.x, (uint32_t)ct.y, (uint32_t)(b << 4) | (4u + (uint32_t)(j >> 2)), (uint32_t)ct.z,
+                   key.k0, key.k1);
+      uint32_t w = (j & 3) == 0 ? u.x : (j & 3) == 1 ? u.y : (j & 3) == 2 ? u.z : u.w;
+      float wa = etree_weight(c, 2 * k, p, n, bnd), wb = etree_weight(c, 2 * k + 1, p, n, bnd);
+      if (!(wa + wb > 0.0f)) return false;
+      if (unif(w) < wa / (wa + wb)) { k = 2 * k; pr *= wa / (wa + wb); }
+      else { k = 2 * k + 1; pr *= wb / (wa + wb); }
+    }
+    int first = (k - (1 << c.et_L)) * c.et_G;
+    int cnt = min(c.et_G, nE - first);
+    if (cnt <= 0) return false;
+    pr /= (float)cnt;
+    s.e = first + (int)(((unsigned long long)(u0 >> 8) * (unsigned long long)cnt) >> 24);
+    inv_p = 1.0f / pr;
+  } else {
+    s.e = (int)(((unsigned long long)(u0 >> 8) * (unsigned long long)nE) >> 24);
+    inv_p = (float)nE;
+  }
   int2 ef = c.edge_f[s.e];
   if (ef.x == f0 || ef.y == f0) return false;
-  float bnd = SEC_BAND * (1.0f + fmaxf(fabsf(p.x), fmaxf(fabsf(p.y), fabsf(p.z))));
   if (c.edge_mode == 0) {
     float s1 = face_side(c, ef.x, p);
     bool sil;
@@ -1298,7 +1377,7 @@ __device__ __forceinline__ bool sec_sample(const KCtx& c, float3 p, float3 n, fl
   float sn = len3(cr);
   if (!(sn > SEC_SMIN)) return false;
   s.mh = cr * (1.0f / sn);
-  s.weight = sn * (float)nE * l * (t1 - t0) / (r * r);
+  s.weight = sn * inv_p * l * (t1 - t0) / (r * r);
   return true;
 }
 
@@ -1356,7 +1435,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_sec_gen(KCtx c, long long j0, int
       vertex_normals(c, f, xyz(r0), wo, nn, ns);
       E.pinj[b * Q + i] = make_float4(0, 0, 0, 0);
       U4 u = philox((uint32_t)ct.x, (uint32_t)ct.y, (uint32_t)(b << 4) | 3u, (uint32_t)ct.z, key.k0, key.k1);
-      ok = sec_sample(c, xyz(r0), nn, ns, f, u.x, u.y, ss);
+      ok = sec_sample(c, xyz(r0), nn, ns, f, u.x, u.y, ct, b, key, ss);
       if (b + 1 < nbv) {
         float4 r1n = E.r1[(b + 1) * Q + i];
         int tex = __float_as_int(E.r3[b * Q + i].w);

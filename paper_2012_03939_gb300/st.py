@@ -46,6 +46,7 @@ class EnvMap(C.Structure):
 
 
 MAX_VIEW_LIGHTS = 2
+SEC_PICK_TREE, SEC_PICK_UNIFORM = 0, 1
 
 
 class View(C.Structure):
@@ -64,7 +65,8 @@ class SceneDesc(C.Structure):
 class RenderOpts(C.Structure):
     _fields_ = [("edge_term", C.c_int), ("edge_mode", C.c_int), ("edge_spp", C.c_int), ("mode", C.c_int),
                 ("use_graph", C.c_int), ("chunk_paths", C.c_int), ("time_kernels", C.c_int),
-                ("count_visits", C.c_int), ("persist_blocks", C.c_int), ("path_signatures", C.c_void_p)]
+                ("count_visits", C.c_int), ("persist_blocks", C.c_int), ("path_signatures", C.c_void_p),
+                ("sec_pick", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -140,10 +142,12 @@ def n_pixels(views) -> int:
 
 
 def make_opts(**kw) -> RenderOpts:
-    o = RenderOpts(0, EDGE_SILHOUETTE, 0, MODE_BATCHED, 1, 0, 0, 0, 0, None)
+    o = RenderOpts(0, EDGE_SILHOUETTE, 0, MODE_BATCHED, 1, 0, 0, 0, 0, None, SEC_PICK_TREE)
     for k, v in kw.items():
         if k == "mode" and isinstance(v, str):
             v = {"batched": MODE_BATCHED, "per_view": MODE_PER_VIEW}[v]
+        if k == "sec_pick" and isinstance(v, str):
+            v = {"tree": SEC_PICK_TREE, "uniform": SEC_PICK_UNIFORM}[v]
         if k == "edge_mode" and isinstance(v, str):
             v = {"silhouette": EDGE_SILHOUETTE, "all": EDGE_ALL}[v]
         setattr(o, k, int(v))

@@ -46,35 +46,42 @@ def _gpu_grad(st, sc, B, seed, w, edge_term, edge_mode=0, **kw):
     return dV.cpu().numpy(), dF.cpu().numpy(), stats
 
 
-def _oracle_grad(sc, B, seed, w, edge_mode=0, secondary=1):
+def _oracle_grad(sc, B, seed, w, edge_mode=0, secondary=2):
     osc = O.OracleScene(sc)
     dv, df, _ = O.grad_pixels(osc, O.params(B, seed, edge_mode=edge_mode, secondary=secondary), O.all_pixels(sc), w)
     return dv, df
 
 
+# the edge pick: through the edge hierarchy (the default) or uniform, with the
+# oracle's matching estimator
+PICKS = [("tree", 2), ("uniform", 1)]
+
+
+@pytest.mark.parametrize("pick,osec", PICKS)
 @pytest.mark.parametrize("name,B", [("occluder", 1), ("underside", 2)])
-def test_secondary_matches_oracle_on_the_pinned_scenes(st, name, B):
+def test_secondary_matches_oracle_on_the_pinned_scenes(st, name, B, pick, osec):
     sc = _occluder_scene(spp=64) if name == "occluder" else _underside_scene(spp=64)
     w = np.random.default_rng(5).normal(size=(sc.n_pixels, 3))
-    dV, dF, stats = _gpu_grad(st, sc, B, 77, w, st.EDGE_TERM_SECONDARY)
+    dV, dF, stats = _gpu_grad(st, sc, B, 77, w, st.EDGE_TERM_SECONDARY, sec_pick=pick)
     assert stats["secondary_samples"] > 0
-    rv, rf = _oracle_grad(sc, B, 77, w)
+    rv, rf = _oracle_grad(sc, B, 77, w, secondary=osec)
     assert rel_l2([dV, dF], [rv, rf]) <= SEC_REL
     # the term is not negligible here: without it the gradient differs
     dV0, dF0, _ = _gpu_grad(st, sc, B, 77, w, 0)
     assert rel_l2([dV0, dF0], [rv, rf]) > 0.05
 
 
+@pytest.mark.parametrize("pick,osec", PICKS)
 @pytest.mark.parametrize("workload,edge_mode,B", [("color_bleed", 0, 3), ("color_bleed", 1, 3), ("env", 0, 2),
                                                    ("env", 1, 3)])
-def test_secondary_matches_oracle_on_workloads(st, workload, edge_mode, B):
+def test_secondary_matches_oracle_on_workloads(st, workload, edge_mode, B, pick, osec):
     # the three planes (a concave corner of coplanar grids) and the torus knot
     # (self-occluding): samples are accepted at many vertices
     sc = S.small_variant(S.make(workload), n_views=2, max_res=24, spp=2)
     w = np.random.default_rng(6).normal(size=(sc.n_pixels, 3))
-    dV, dF, stats = _gpu_grad(st, sc, B, 91, w, st.EDGE_TERM_SECONDARY, edge_mode)
+    dV, dF, stats = _gpu_grad(st, sc, B, 91, w, st.EDGE_TERM_SECONDARY, edge_mode, sec_pick=pick)
     assert stats["secondary_samples"] > 0
-    rv, rf = _oracle_grad(sc, B, 91, w, edge_mode)
+    rv, rf = _oracle_grad(sc, B, 91, w, edge_mode, secondary=osec)
     assert rel_l2([dV, dF], [rv, rf]) <= SEC_REL, stats
 
 
@@ -105,3 +112,14 @@ def test_secondary_graph_small_chunks_and_per_view_agree(st):
         got = _gpu_grad(st, sc, 3, 21, w, st.EDGE_TERM_SECONDARY, **kw)
         assert got[2]["secondary_samples"] == ref[2]["secondary_samples"] > 0
         assert rel_l2(got[:2], ref[:2]) <= 1e-5, kw
+
+
+def test_tree_pick_accepts_more_samples_than_the_uniform_pick(st):
+    # on the self-occluding torus knot the hierarchy steers picks to edges
+    # above the tangent plane and near the vertex, so more picks become
+    # samples (a silhouette seen from the vertex, with a part above the plane)
+    sc = S.small_variant(S.make("env"), n_views=2, max_res=64, spp=2)
+    w = np.random.default_rng(10).normal(size=(sc.n_pixels, 3))
+    n = {pick: _gpu_grad(st, sc, 2, 5, w, st.EDGE_TERM_SECONDARY, sec_pick=pick)[2]["secondary_samples"]
+         for pick in ("tree", "uniform")}
+    assert n["tree"] > 1.5 * n["uniform"] > 0, n

@@ -84,7 +84,7 @@ def test_smooth_gradient_with_every_edge_term(st):
     et = st.EDGE_TERM_PRIMARY | st.EDGE_TERM_SECONDARY | st.EDGE_TERM_SHADOW
     dV, dF = _backward(st, sc, 2, 12, w, et)
     osc = O.OracleScene(sc)
-    prm = O.params(2, 12, secondary=1)
+    prm = O.params(2, 12, secondary=2)
     rv, rf, _ = O.grad_pixels(osc, prm, O.all_pixels(sc), w)
     rv = rv + O.edge_grad(osc, prm, w)[0] + O.shadow_edge_grad(osc, prm, w)[0]
     assert rel_l2([dV, dF], [rv, rf]) <= EDGE_REL

@@ -67,7 +67,7 @@ def test_view_lights_with_both_edge_terms(st):
                            st.make_opts(edge_term=st.EDGE_TERM_PRIMARY | st.EDGE_TERM_SECONDARY, edge_spp=4))
     scene.close()
     osc = O.OracleScene(sc)
-    rv, _, _ = O.grad_pixels(osc, O.params(3, 5, secondary=1), O.all_pixels(sc), w)
+    rv, _, _ = O.grad_pixels(osc, O.params(3, 5, secondary=2), O.all_pixels(sc), w)
     ev, _ = O.edge_grad(osc, O.params(3, 5, edge_spp=4), w)
     assert rel_l2([dV.cpu().numpy()], [rv + ev]) <= 2e-3
 
