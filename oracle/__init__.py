@@ -94,10 +94,10 @@ def lib():
         L.orc_mesh_color_index.restype = C.c_longlong
         L.orc_mesh_color_index.argtypes = [C.c_int, C.c_longlong, C.c_double, C.c_double]
         L.orc_sec_edge_pmf.restype = C.c_int
-        L.orc_sec_edge_pmf.argtypes = [P, P, P, C.c_double, P]
+        L.orc_sec_edge_pmf.argtypes = [P, P, P, C.c_double, C.c_int, P]
         L.orc_sec_edge_picks.restype = C.c_int
-        L.orc_sec_edge_picks.argtypes = [P, C.c_ulonglong, C.c_uint32, C.c_int, C.c_uint32, P, P, C.c_double, P,
-                                         C.c_int, P, P]
+        L.orc_sec_edge_picks.argtypes = [P, C.c_ulonglong, C.c_uint32, C.c_int, C.c_uint32, P, P, C.c_double,
+                                         C.c_int, P, C.c_int, P, P]
         _lib = L
     return _lib
 
@@ -140,26 +140,26 @@ def params(max_bounces, seed, edge_mode=0, edge_spp=0, n_threads=0, secondary=0)
     return _Params(max_bounces, seed, edge_mode, edge_spp, n_threads, secondary)
 
 
-def sec_edge_pmf(osc: OracleScene, p, n, bnd):
+def sec_edge_pmf(osc: OracleScene, p, n, bnd, edge_mode=0):
     """Pick probability of every edge (edge order) at vertex p, tangent-plane normal n, band bnd."""
     p = np.ascontiguousarray(p, np.float64)
     n = np.ascontiguousarray(n, np.float64)
     out = np.zeros(3 * osc.nf, np.float64)
-    ne = lib().orc_sec_edge_pmf(C.byref(osc.s), _ptr(p), _ptr(n), bnd, _ptr(out))
+    ne = lib().orc_sec_edge_pmf(C.byref(osc.s), _ptr(p), _ptr(n), bnd, edge_mode, _ptr(out))
     if ne < 0:
         raise ValueError("oracle rejected the input")
     return out[:ne]
 
 
-def sec_edge_picks(osc: OracleScene, seed, c1, b, stream, p, n, bnd, uleaf):
+def sec_edge_picks(osc: OracleScene, seed, c1, b, stream, p, n, bnd, uleaf, edge_mode=0):
     """Hierarchy picks at one vertex, pick i with counters (i, c1): (edge or -1, probability) arrays."""
     p = np.ascontiguousarray(p, np.float64)
     n = np.ascontiguousarray(n, np.float64)
     u = np.ascontiguousarray(uleaf, np.uint32)
     e = np.zeros(len(u), np.int32)
     pr = np.zeros(len(u), np.float64)
-    if lib().orc_sec_edge_picks(C.byref(osc.s), seed, c1, b, stream, _ptr(p), _ptr(n), bnd, _ptr(u), len(u),
-                                _ptr(e), _ptr(pr)) < 0:
+    if lib().orc_sec_edge_picks(C.byref(osc.s), seed, c1, b, stream, _ptr(p), _ptr(n), bnd, edge_mode, _ptr(u),
+                                len(u), _ptr(e), _ptr(pr)) < 0:
         raise ValueError("oracle rejected the input")
     return e, pr
 

@@ -638,7 +638,15 @@ struct EdgeTree {
   int G = 4, L = 0, nleaf = 0, nE = 0;
   std::vector<V3d> lo, hi;
   std::vector<double> S;
+  // cone of the unit normals of the faces on the node's edges: axis, cos of the
+  // half-angle; cos < -1.5 marks a node whose silhouettes cannot be bounded (an
+  // edge with one face or more than two, or normals spread too wide)
+  std::vector<V3d> ax;
+  std::vector<double> ct;
+  std::vector<char> any;   // the node holds an edge of nonzero length
 };
+
+double angle_of(double c) { return std::acos(std::max(-1.0, std::min(1.0, c))); }
 
 EdgeTree edge_tree(const Scene& s, const std::vector<Edge>& E) {
   EdgeTree t;
@@ -650,38 +658,90 @@ EdgeTree edge_tree(const Scene& s, const std::vector<Edge>& E) {
   t.lo.assign(nn, V3d{INFINITY, INFINITY, INFINITY});
   t.hi.assign(nn, V3d{-INFINITY, -INFINITY, -INFINITY});
   t.S.assign(nn, 0.0);
+  t.ax.assign(nn, V3d{0, 0, 0});
+  t.ct.assign(nn, -2.0);
+  t.any.assign(nn, 0);
+  auto unit_normal = [&](int f) {
+    const int* fi = &s.face[3 * f];
+    return nrm(cross(s.vert[fi[1]] - s.vert[fi[0]], s.vert[fi[2]] - s.vert[fi[0]]));
+  };
   auto grow = [&](size_t k, const V3d& a) {
     t.lo[k] = {std::min(t.lo[k].x, a.x), std::min(t.lo[k].y, a.y), std::min(t.lo[k].z, a.z)};
     t.hi[k] = {std::max(t.hi[k].x, a.x), std::max(t.hi[k].y, a.y), std::max(t.hi[k].z, a.z)};
   };
   for (int i = 0; i < t.nleaf; ++i) {
     size_t k = ((size_t)1 << t.L) + i;
+    bool bounded = true;
+    V3d sum{0, 0, 0};
     for (int e = i * t.G; e < std::min(t.nE, (i + 1) * t.G); ++e) {
       const V3d &A = s.vert[E[e].a], &B = s.vert[E[e].b];
       grow(k, A);
       grow(k, B);
-      t.S[k] += len(B - A);
+      double l = len(B - A);
+      t.S[k] += l;
+      if (l > 0) t.any[k] = 1;
+      if (E[e].nf != 2) { bounded = false; continue; }
+      sum = sum + unit_normal(E[e].f[0]) + unit_normal(E[e].f[1]);
     }
+    double sl = len(sum);
+    if (!t.any[k] || !bounded || !(sl > 1e-6)) continue;
+    t.ax[k] = scl(sum, 1.0 / sl);
+    double c = 1.0;
+    for (int e = i * t.G; e < std::min(t.nE, (i + 1) * t.G); ++e)
+      c = std::min(c, std::min(dot(t.ax[k], unit_normal(E[e].f[0])), dot(t.ax[k], unit_normal(E[e].f[1]))));
+    t.ct[k] = c > 0.0 ? c : -2.0;    // cones wider than a hemisphere bound nothing
   }
   for (size_t k = ((size_t)1 << t.L) - 1; k >= 1; --k) {
     const V3d &la = t.lo[2 * k], &lb = t.lo[2 * k + 1], &ha = t.hi[2 * k], &hb = t.hi[2 * k + 1];
     t.lo[k] = {std::min(la.x, lb.x), std::min(la.y, lb.y), std::min(la.z, lb.z)};
     t.hi[k] = {std::max(ha.x, hb.x), std::max(ha.y, hb.y), std::max(ha.z, hb.z)};
     t.S[k] = t.S[2 * k] + t.S[2 * k + 1];
+    // the cone around the normalised sum of the children's axes that holds both
+    size_t a = 2 * k, b = 2 * k + 1;
+    t.any[k] = t.any[a] | t.any[b];
+    if (!t.any[a] || !t.any[b]) {
+      size_t o = t.any[a] ? a : b;
+      t.ax[k] = t.ax[o];
+      t.ct[k] = t.ct[o];
+      continue;
+    }
+    if (t.ct[a] < -1.5 || t.ct[b] < -1.5) continue;
+    V3d sum = t.ax[a] + t.ax[b];
+    double sl = len(sum);
+    if (!(sl > 1e-6)) continue;
+    t.ax[k] = scl(sum, 1.0 / sl);
+    double th = std::max(angle_of(dot(t.ax[k], t.ax[a])) + angle_of(t.ct[a]),
+                         angle_of(dot(t.ax[k], t.ax[b])) + angle_of(t.ct[b]));
+    t.ct[k] = th < 0.5 * PI ? std::cos(th) : -2.0;
   }
   return t;
 }
 
 // Importance of node k at a path vertex (p, tangent plane normal n, band bnd):
 // 0 when the whole box lies at or below the plane (no edge in it can be
-// sampled), else the summed length over max(d^2, diag^2 / 4), d the distance
-// from p to the box.
-double tree_weight(const EdgeTree& t, size_t k, const V3d& p, const V3d& n, double bnd) {
+// sampled) or, for silhouette sampling (sil), when every face on the node's
+// edges sees p on the same side (no edge in it is a silhouette from p); else
+// the summed length over max(d^2, diag^2 / 4), d the distance from p to the box.
+// Side bound: n_f.(p - x) for x in the box and n_f in the cone (axis a, half-
+// angle th) lies within |v| cos(phi -+ th) -+ r, v = p - c, c the box centre, r
+// its half-diagonal, phi the angle between a and v.
+double tree_weight(const EdgeTree& t, size_t k, const V3d& p, const V3d& n, double bnd, bool sil) {
   if (!(t.S[k] > 0)) return 0.0;
   const V3d &lo = t.lo[k], &hi = t.hi[k];
   double top = (n.x > 0 ? hi.x - p.x : lo.x - p.x) * n.x + (n.y > 0 ? hi.y - p.y : lo.y - p.y) * n.y +
                (n.z > 0 ? hi.z - p.z : lo.z - p.z) * n.z;
   if (!(top > bnd)) return 0.0;
+  if (sil && t.ct[k] > -1.5) {
+    V3d c = scl(lo + hi, 0.5), v = p - c;
+    double r = 0.5 * len(hi - lo), D = len(v);
+    if (D > r) {
+      double cp = dot(t.ax[k], v) / D, sp = std::sqrt(std::max(0.0, 1.0 - cp * cp));
+      double cq = t.ct[k], sq = std::sqrt(std::max(0.0, 1.0 - cq * cq));
+      double cmin = cp <= -cq ? -1.0 : cp * cq - sp * sq;
+      double cmax = cp >= cq ? 1.0 : cp * cq + sp * sq;
+      if (D * cmin - r > -bnd || D * cmax + r < bnd) return 0.0;
+    }
+  }
   double dx = std::max(lo.x - p.x, std::max(0.0, p.x - hi.x));
   double dy = std::max(lo.y - p.y, std::max(0.0, p.y - hi.y));
   double dz = std::max(lo.z - p.z, std::max(0.0, p.z - hi.z));
@@ -694,13 +754,13 @@ double tree_weight(const EdgeTree& t, size_t k, const V3d& p, const V3d& n, doub
 // draw (c0, c1, b<<4 | (4 + j/4), stream)), then picks uniformly in the leaf
 // block with the word uleaf. Returns the edge or -1; prob = its probability.
 int tree_pick(const EdgeTree& t, const Rng& rng, uint32_t c0, uint32_t c1, int b, uint32_t stream, const V3d& p,
-              const V3d& n, double bnd, uint32_t uleaf, double& prob) {
+              const V3d& n, double bnd, bool sil, uint32_t uleaf, double& prob) {
   size_t k = 1;
   prob = 1.0;
   U4 u{};
   for (int j = 0; j < t.L; ++j) {
     if (j % 4 == 0) u = rng.draw(c0, c1, (uint32_t)(b << 4) | (4u + (uint32_t)(j / 4)), stream);
-    double wa = tree_weight(t, 2 * k, p, n, bnd), wb = tree_weight(t, 2 * k + 1, p, n, bnd);
+    double wa = tree_weight(t, 2 * k, p, n, bnd, sil), wb = tree_weight(t, 2 * k + 1, p, n, bnd, sil);
     if (!(wa + wb > 0)) return -1;
     if (unif(u.w[j % 4]) < wa / (wa + wb)) { k = 2 * k; prob *= wa / (wa + wb); }
     else { k = 2 * k + 1; prob *= wb / (wa + wb); }
@@ -756,7 +816,7 @@ void secondary_edge(const Scene& s, const Rng& rng, int B, const Lights& lt, int
   double inv_p;   // 1 / pick probability
   if (sc.sampling == 2) {
     double pr;
-    int k = tree_pick(*sc.T, rng, c0, c1, b, stream, pv, nv, bnd, u.w[0], pr);
+    int k = tree_pick(*sc.T, rng, c0, c1, b, stream, pv, nv, bnd, sc.mode == 0, u.w[0], pr);
     if (k < 0) return;
     ei = (size_t)k;
     inv_p = 1.0 / pr;
@@ -1541,7 +1601,7 @@ long long orc_trace_screen(const orc_scene* in, const orc_view* view, const orc_
   return seg;
 }
 
-int orc_sec_edge_pmf(const orc_scene* in, const double* p, const double* n, double bnd, double* pmf) {
+int orc_sec_edge_pmf(const orc_scene* in, const double* p, const double* n, double bnd, int edge_mode, double* pmf) {
   Scene s;
   if (!load_scene(in, s)) return -1;
   std::vector<Edge> E = edge_list(s);
@@ -1552,7 +1612,8 @@ int orc_sec_edge_pmf(const orc_scene* in, const double* p, const double* n, doub
     double pr = 1.0;
     for (size_t c = k; c > 1; c /= 2) {
       size_t par = c / 2;
-      double wa = tree_weight(t, 2 * par, pv, nv, bnd), wb = tree_weight(t, 2 * par + 1, pv, nv, bnd);
+      double wa = tree_weight(t, 2 * par, pv, nv, bnd, edge_mode == 0),
+             wb = tree_weight(t, 2 * par + 1, pv, nv, bnd, edge_mode == 0);
       pr *= wa + wb > 0 ? (c % 2 == 0 ? wa : wb) / (wa + wb) : 0.0;
     }
     int first = leaf * t.G, cnt = std::min(t.G, t.nE - first);
@@ -1562,15 +1623,16 @@ int orc_sec_edge_pmf(const orc_scene* in, const double* p, const double* n, doub
 }
 
 int orc_sec_edge_picks(const orc_scene* in, unsigned long long seed, uint32_t c1, int b, uint32_t stream,
-                       const double* p, const double* n, double bnd, const uint32_t* uleaf, int count, int* edge,
-                       double* prob) {
+                       const double* p, const double* n, double bnd, int edge_mode, const uint32_t* uleaf, int count,
+                       int* edge, double* prob) {
   Scene s;
   if (!load_scene(in, s) || count < 0) return -1;
   std::vector<Edge> E = edge_list(s);
   EdgeTree t = edge_tree(s, E);
   Rng rng{(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
   V3d pv{p[0], p[1], p[2]}, nv{n[0], n[1], n[2]};
-  for (int i = 0; i < count; ++i) edge[i] = tree_pick(t, rng, (uint32_t)i, c1, b, stream, pv, nv, bnd, uleaf[i], prob[i]);
+  for (int i = 0; i < count; ++i)
+    edge[i] = tree_pick(t, rng, (uint32_t)i, c1, b, stream, pv, nv, bnd, edge_mode == 0, uleaf[i], prob[i]);
   return count;
 }
 

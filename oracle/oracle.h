@@ -151,13 +151,13 @@ long long orc_mesh_color_index(int r, long long t, double alpha, double beta);
 
 /* Secondary edge pick through the edge hierarchy, for tests: the probability of
  * every edge (pmf [E], edge order) at a vertex p with tangent-plane normal n and
- * band bnd; returns E or -1. */
-int orc_sec_edge_pmf(const orc_scene* s, const double* p, const double* n, double bnd, double* pmf);
+ * band bnd, for silhouette (edge_mode 0) or all-edge sampling; returns E or -1. */
+int orc_sec_edge_pmf(const orc_scene* s, const double* p, const double* n, double bnd, int edge_mode, double* pmf);
 /* count picks at the same vertex, pick i with the counters (i, c1) of vertex b
  * and stream: edge [count] (-1 if every node is below the plane) and prob. */
 int orc_sec_edge_picks(const orc_scene* s, unsigned long long seed, uint32_t c1, int b, uint32_t stream,
-                       const double* p, const double* n, double bnd, const uint32_t* uleaf, int count, int* edge,
-                       double* prob);
+                       const double* p, const double* n, double bnd, int edge_mode, const uint32_t* uleaf, int count,
+                       int* edge, double* prob);
 
 #ifdef __cplusplus
 }

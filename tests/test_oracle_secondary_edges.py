@@ -286,23 +286,46 @@ def _tangent_frames(sc, n, seed):
     return out
 
 
-def test_hierarchy_pick_probabilities():
-    # every edge with a part above the tangent plane can be picked (so the
-    # estimator stays unbiased); the mass never exceeds one; a pick returns the
-    # probability the enumeration gives; picks follow the probabilities
+def _edges_and_faces(sc):
+    """Edges in edge order (sorted vertex pairs) with their two faces (-1 if fewer)."""
+    F = sc.faces
+    pairs = {}
+    for f in range(len(F)):
+        for a, b in ((F[f, 0], F[f, 1]), (F[f, 1], F[f, 2]), (F[f, 2], F[f, 0])):
+            pairs.setdefault((min(a, b), max(a, b)), []).append(f)
+    keys = sorted(pairs)
+    return np.array(keys), [pairs[k] for k in keys]
+
+
+@pytest.mark.parametrize("edge_mode", [0, 1])
+def test_hierarchy_pick_probabilities(edge_mode):
+    # every edge the sample can use -- a part above the tangent plane and, when
+    # sampling silhouettes, one face seeing the vertex and the other not -- can
+    # be picked (so the estimator stays unbiased); the mass never exceeds one; a
+    # pick returns the probability the enumeration gives; picks follow it
     sc = S.small_variant(S.make("env"), n_views=1, max_res=8, spp=1)
     osc = O.OracleScene(sc)
     V = sc.vertices.astype(np.float64)
-    ev = np.unique(np.sort(np.concatenate([sc.faces[:, [0, 1]], sc.faces[:, [1, 2]], sc.faces[:, [2, 0]]]), 1), axis=0)
+    ev, ef = _edges_and_faces(sc)
+    tri = V[sc.faces]
+    un = np.cross(tri[:, 1] - tri[:, 0], tri[:, 2] - tri[:, 0])
+    un /= np.linalg.norm(un, axis=1, keepdims=True)
     for k, (p, n) in enumerate(_tangent_frames(sc, 6, 4)):
         bnd = 1e-5 * (1 + np.abs(p).max())
-        pmf = O.sec_edge_pmf(osc, p, n, bnd)
+        pmf = O.sec_edge_pmf(osc, p, n, bnd, edge_mode)
         assert len(pmf) == len(ev) and pmf.sum() <= 1 + 1e-12
-        above = np.maximum((V[ev[:, 0]] - p) @ n, (V[ev[:, 1]] - p) @ n) > bnd
-        assert np.all(pmf[above] > 0) and np.all(pmf[~above & (pmf > 0)] >= 0)
+        usable = np.maximum((V[ev[:, 0]] - p) @ n, (V[ev[:, 1]] - p) @ n) > bnd
+        if edge_mode == 0:
+            side = np.einsum("ij,ij->i", un, p - tri[:, 0])
+            sil = np.array([len(fs) != 2 or (side[fs[0]] > bnd and side[fs[1]] < -bnd) or
+                            (side[fs[0]] < -bnd and side[fs[1]] > bnd) for fs in ef])
+            usable &= sil
+            assert (pmf[~sil] == 0).mean() > 0.5     # the cones rule most of the rest out
+        assert np.all(pmf[usable] > 0)
         if k < 2:
             N = 40000
-            e, pr = O.sec_edge_picks(osc, 11, k, 1, 0, p, n, bnd, np.random.default_rng(k).integers(0, 1 << 32, N))
+            e, pr = O.sec_edge_picks(osc, 11, k, 1, 0, p, n, bnd, np.random.default_rng(k).integers(0, 1 << 32, N),
+                                     edge_mode)
             ok = e >= 0
             np.testing.assert_allclose(pr[ok], pmf[e[ok]], rtol=1e-12)
             cnt = np.bincount(e[ok], minlength=len(pmf)).astype(np.float64)
@@ -316,16 +339,27 @@ def test_hierarchy_pick_probabilities():
             assert abs(cnt.sum() - N * pmf.sum()) < 6 * math.sqrt(N)
 
 
-def test_hierarchy_pick_lowers_the_variance_of_the_secondary_term():
-    # torus knot (self-occluding): the same gradient, estimated with the
-    # uniform pick and with the hierarchy, seed by seed
-    sc = S.small_variant(S.make("env"), n_views=1, max_res=24, spp=2)
+def test_hierarchy_pick_lands_on_usable_edges_more_often():
+    # the chance that a pick can become a sample -- a silhouette seen from the
+    # vertex with a part above its tangent plane -- averaged over vertices of
+    # the self-occluding torus knot: the hierarchy (boxes below the plane and
+    # cones without silhouettes dropped, near edges favoured) against the
+    # uniform pick, computed exactly from the probabilities
+    sc = S.small_variant(S.make("env"), n_views=1, max_res=8, spp=1)
     osc = O.OracleScene(sc)
-    pix = O.all_pixels(sc)
-    w = np.random.default_rng(1).normal(size=(len(pix), 3))
-    std = {}
-    for sampling in (1, 2):
-        terms = [O.grad_pixels(osc, O.params(2, 100 + s, secondary=sampling), pix, w)[0] -
-                 O.grad_pixels(osc, O.params(2, 100 + s), pix, w)[0] for s in range(6)]
-        std[sampling] = np.linalg.norm(np.std(terms, axis=0))
-    assert 0 < std[2] < std[1] / 4, std
+    V = sc.vertices.astype(np.float64)
+    ev, ef = _edges_and_faces(sc)
+    tri = V[sc.faces]
+    un = np.cross(tri[:, 1] - tri[:, 0], tri[:, 2] - tri[:, 0])
+    un /= np.linalg.norm(un, axis=1, keepdims=True)
+    f0 = np.array([fs[0] for fs in ef])
+    f1 = np.array([fs[1] for fs in ef])
+    tree, unif = [], []
+    for p, n in _tangent_frames(sc, 30, 9):
+        bnd = 1e-5 * (1 + np.abs(p).max())
+        side = np.einsum("ij,ij->i", un, p - tri[:, 0])
+        sil = ((side[f0] > bnd) & (side[f1] < -bnd)) | ((side[f0] < -bnd) & (side[f1] > bnd))
+        usable = sil & (np.maximum((V[ev[:, 0]] - p) @ n, (V[ev[:, 1]] - p) @ n) > bnd)
+        tree.append(O.sec_edge_pmf(osc, p, n, bnd)[usable].sum())
+        unif.append(usable.mean())
+    assert np.mean(tree) > 3 * np.mean(unif) > 0, (np.mean(tree), np.mean(unif))
