@@ -357,6 +357,7 @@ KCtx make_ctx(st_scene* s, const Plan& p) {
   c.cull = s->closed ? 1 : 0; c.mstat = s->mstat;
   c.smooth = s->smooth ? 1 : 0; c.vn = s->vnrm; c.dN = s->dN; c.nv = s->nv;
   c.sec_tree = p.sec_tree ? 1 : 0; c.et_G = s->et_G; c.et_L = s->et_L; c.et_lo = s->et_lo; c.et_hi = s->et_hi;
+  c.et_cn = s->et_cn;
   c.acc = s->acc;
   c.views = s->d_views; c.segs = s->d_segs; c.n_segs = (int)p.segs.size();
   c.args = s->d_args; c.B = p.B; c.e = s->eng; c.e.records = p.kind == 1; c.err = s->d_err;
@@ -501,9 +502,11 @@ st_status enqueue_call(st_scene* s, const Plan& p, int Q, cudaStream_t st, bool 
   if (p.sec_tree) {
     // the edge hierarchy on the current vertices: leaves, then level by level up to the root
     int nl = 1 << s->et_L;
-    k_etree_leaves<<<std::min((nl + 255) / 256, 4 * std::max(s->sm_count, 1)), 256, 0, st>>>(c, s->et_lo, s->et_hi);
+    k_etree_leaves<<<std::min((nl + 255) / 256, 4 * std::max(s->sm_count, 1)), 256, 0, st>>>(c, s->et_lo, s->et_hi,
+                                                                                             s->et_cn);
     for (int l = s->et_L - 1; l >= 0; --l)
-      k_etree_level<<<std::min(((1 << l) + 255) / 256, 4 * std::max(s->sm_count, 1)), 256, 0, st>>>(s->et_lo, s->et_hi, l);
+      k_etree_level<<<std::min(((1 << l) + 255) / 256, 4 * std::max(s->sm_count, 1)), 256, 0, st>>>(
+          s->et_lo, s->et_hi, s->et_cn, l);
     s->launches += 1 + s->et_L;
   }
   if (p.bins) {
@@ -771,7 +774,7 @@ void destroy(st_scene* s) {
   dfree(s->sh_flag); dfree(s->sh_cand); dfree(s->sh_ncand); dfree(s->d_pairs); dfree(s->d_views); dfree(s->d_segs);
   dfree(s->bin_start); dfree(s->bin_cur); dfree(s->bin_list); dfree(s->bin_ok); dfree(s->bin_part);
   dfree(s->acc); dfree(s->sacc); dfree(s->mstat); dfree(s->vnrm); dfree(s->vf_start); dfree(s->vf_list); dfree(s->dN);
-  dfree(s->et_lo); dfree(s->et_hi);
+  dfree(s->et_lo); dfree(s->et_hi); dfree(s->et_cn);
   if (s->bin_total_host) cudaFreeHost(s->bin_total_host);
   dfree(s->d_args); dfree(s->d_err);
   for (auto& e : s->ev) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
@@ -884,6 +887,7 @@ st_status st_scene_create(const st_scene_desc* d, void* stream, st_scene** out) 
     s->et_L = 0;
     while ((1 << s->et_L) < s->et_nleaf) ++s->et_L;
     chk(dalloc(&s->et_lo, (size_t)2 << s->et_L)); chk(dalloc(&s->et_hi, (size_t)2 << s->et_L));
+    chk(dalloc(&s->et_cn, (size_t)2 << s->et_L));
   }
   std::vector<int> vfs, vfl;
   if (s->smooth) {

@@ -103,6 +103,7 @@ struct st_scene {
   int et_G = 4, et_L = 0, et_nleaf = 0;
   float4* et_lo = nullptr;       // [2^(L+1)] box low corner, summed edge length (heap order, root 1)
   float4* et_hi = nullptr;       // [2^(L+1)] box high corner
+  float4* et_cn = nullptr;       // [2^(L+1)] cone of the faces' unit normals: axis, cos half-angle (-2: none)
   float* verts = nullptr;        // [V*3]
   int* faces = nullptr;          // [F*3]
   float4* params = nullptr;      // [F*ntex*2] per texel: (kd_r, kd_g, kd_b, ks_r), (roughness, ks_g, ks_b, 0)

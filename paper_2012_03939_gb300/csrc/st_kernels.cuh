@@ -56,8 +56,9 @@ struct KCtx {
   float* dN;              // backward with smooth normals: [V][3] adjoint of the vertex normals
   int sec_tree;           // secondary pick through the edge hierarchy (else uniform)
   int et_G, et_L;         // edges per leaf block, tree levels
-  const float4* et_lo;    // tree nodes (heap order): box low corner + summed length, high corner
-  const float4* et_hi;
+  const float4* et_lo;    // tree nodes (heap order): box low corner + summed length, high corner,
+  const float4* et_hi;    // cone of the faces' unit normals (axis, cos half-angle; -2 = unbounded)
+  const float4* et_cn;
   const DevView* views;
   const Seg* segs;
   int n_segs;
@@ -1254,44 +1255,100 @@ __device__ __forceinline__ float face_side(const KCtx& c, int f, float3 p) {
 // Sec. 3.2): leaf i holds edges [i G, (i + 1) G) in edge order, with the box of
 // their endpoints and their summed length; internal node k unites 2k and 2k + 1.
 // Rebuilt by every call that samples with it (the vertices may have moved).
-__global__ void k_etree_leaves(KCtx c, float4* lo, float4* hi) {
+__device__ __forceinline__ float3 face_unit_normal(const KCtx& c, int f) {
+  float3 a = fetch_vertex(c.V, c.F[3 * f]);
+  return norm3(cross3(fetch_vertex(c.V, c.F[3 * f + 1]) - a, fetch_vertex(c.V, c.F[3 * f + 2]) - a));
+}
+
+__global__ void k_etree_leaves(KCtx c, float4* lo, float4* hi, float4* cn) {
   const int nleaf = 1 << c.et_L;
   const float INF = __int_as_float(0x7f800000);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nleaf; i += gridDim.x * blockDim.x) {
-    float3 l = mk3(INF, INF, INF), h = mk3(-INF, -INF, -INF);
+    float3 l = mk3(INF, INF, INF), h = mk3(-INF, -INF, -INF), sum = mk3(0, 0, 0);
     float S = 0.0f;
-    int e1 = min(c.n_edges, (i + 1) * c.et_G);
-    for (int e = i * c.et_G; e < e1; ++e) {
+    bool bounded = true;
+    int e0 = i * c.et_G, e1 = min(c.n_edges, (i + 1) * c.et_G);
+    for (int e = e0; e < e1; ++e) {
       int2 ev = c.edge_v[e];
       float3 a = fetch_vertex(c.V, ev.x), b = fetch_vertex(c.V, ev.y);
       l = mk3(fminf(l.x, fminf(a.x, b.x)), fminf(l.y, fminf(a.y, b.y)), fminf(l.z, fminf(a.z, b.z)));
       h = mk3(fmaxf(h.x, fmaxf(a.x, b.x)), fmaxf(h.y, fmaxf(a.y, b.y)), fmaxf(h.z, fmaxf(a.z, b.z)));
       S += len3(b - a);
+      int2 ef = c.edge_f[e];
+      if (ef.y < 0) { bounded = false; continue; }
+      sum += face_unit_normal(c, ef.x) + face_unit_normal(c, ef.y);
+    }
+    float4 cone = make_float4(0, 0, 0, -2.0f);
+    float sl = len3(sum);
+    if (S > 0.0f && bounded && sl > 1e-6f) {
+      float3 ax = sum * (1.0f / sl);
+      float ct = 1.0f;
+      for (int e = e0; e < e1; ++e) {
+        int2 ef = c.edge_f[e];
+        ct = fminf(ct, fminf(dot3(ax, face_unit_normal(c, ef.x)), dot3(ax, face_unit_normal(c, ef.y))));
+      }
+      cone = make_float4(ax.x, ax.y, ax.z, ct > 0.0f ? ct : -2.0f);
     }
     lo[nleaf + i] = make_float4(l.x, l.y, l.z, S);
     hi[nleaf + i] = make_float4(h.x, h.y, h.z, 0.0f);
+    cn[nleaf + i] = cone;
   }
 }
 
-// nodes [2^level, 2^(level+1)) from their children
-__global__ void k_etree_level(float4* lo, float4* hi, int level) {
+// nodes [2^level, 2^(level+1)) from their children: union of the boxes, sum of
+// the lengths, the cone around the normalised sum of the children's axes that
+// holds both
+__global__ void k_etree_level(float4* lo, float4* hi, float4* cn, int level) {
   const int n = 1 << level;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     int k = n + i;
     float4 la = lo[2 * k], lb = lo[2 * k + 1], ha = hi[2 * k], hb = hi[2 * k + 1];
     lo[k] = make_float4(fminf(la.x, lb.x), fminf(la.y, lb.y), fminf(la.z, lb.z), la.w + lb.w);
     hi[k] = make_float4(fmaxf(ha.x, hb.x), fmaxf(ha.y, hb.y), fmaxf(ha.z, hb.z), 0.0f);
+    float4 ca = cn[2 * k], cb = cn[2 * k + 1];
+    float4 cone = make_float4(0, 0, 0, -2.0f);
+    if (!(la.w > 0.0f) || !(lb.w > 0.0f)) {
+      cone = la.w > 0.0f ? ca : cb;
+    } else if (ca.w > -1.5f && cb.w > -1.5f) {
+      float3 sum = xyz(ca) + xyz(cb);
+      float sl = len3(sum);
+      if (sl > 1e-6f) {
+        float3 ax = sum * (1.0f / sl);
+        auto ang = [](float x) { return acosf(fmaxf(-1.0f, fminf(1.0f, x))); };
+        float th = fmaxf(ang(dot3(ax, xyz(ca))) + ang(ca.w), ang(dot3(ax, xyz(cb))) + ang(cb.w));
+        cone = make_float4(ax.x, ax.y, ax.z, th < 0.5f * PI_F ? cosf(th) : -2.0f);
+      }
+    }
+    cn[k] = cone;
   }
 }
 
 // Importance of node k at a vertex (p, tangent-plane normal n, band bnd): 0 when
-// its box lies at or below the plane, else summed length / max(d^2, diag^2 / 4).
+// its box lies at or below the plane or, sampling silhouettes, when every face on
+// its edges sees p on the same side (n_f.(p - x) within |v| cos(phi -+ th) -+ r
+// over the box and the cone: v = p - centre, r the half-diagonal, phi the angle
+// of v to the axis, th the cone's half-angle); else summed length / max(d^2,
+// diag^2 / 4), d the distance from p to the box.
 __device__ __forceinline__ float etree_weight(const KCtx& c, int k, float3 p, float3 n, float bnd) {
   float4 lo = c.et_lo[k], hi = c.et_hi[k];
   if (!(lo.w > 0.0f)) return 0.0f;
   float top = (n.x > 0.0f ? hi.x - p.x : lo.x - p.x) * n.x + (n.y > 0.0f ? hi.y - p.y : lo.y - p.y) * n.y +
               (n.z > 0.0f ? hi.z - p.z : lo.z - p.z) * n.z;
   if (!(top > bnd)) return 0.0f;
+  if (c.edge_mode == 0) {
+    float4 cn = c.et_cn[k];
+    if (cn.w > -1.5f) {
+      float3 v = p - (xyz(lo) + xyz(hi)) * 0.5f;
+      float r = 0.5f * len3(xyz(hi) - xyz(lo)), D = len3(v);
+      if (D > r) {
+        float cp = dot3(xyz(cn), v) / D, sp = sqrtf(fmaxf(0.0f, 1.0f - cp * cp));
+        float cq = cn.w, sq = sqrtf(fmaxf(0.0f, 1.0f - cq * cq));
+        float cmin = cp <= -cq ? -1.0f : cp * cq - sp * sq;
+        float cmax = cp >= cq ? 1.0f : cp * cq + sp * sq;
+        if (D * cmin - r > -bnd || D * cmax + r < bnd) return 0.0f;
+      }
+    }
+  }
   float dx = fmaxf(lo.x - p.x, fmaxf(0.0f, p.x - hi.x)), dy = fmaxf(lo.y - p.y, fmaxf(0.0f, p.y - hi.y)),
         dz = fmaxf(lo.z - p.z, fmaxf(0.0f, p.z - hi.z));
   float ex = hi.x - lo.x, ey = hi.y - lo.y, ez = hi.z - lo.z;
