@@ -123,3 +123,10 @@ def test_tree_pick_accepts_more_samples_than_the_uniform_pick(st):
     n = {pick: _gpu_grad(st, sc, 2, 5, w, st.EDGE_TERM_SECONDARY, sec_pick=pick)[2]["secondary_samples"]
          for pick in ("tree", "uniform")}
     assert n["tree"] > 1.5 * n["uniform"] > 0, n
+
+
+def test_unknown_pick_is_rejected(st):
+    sc = S.tiny(res=16, spp=1)
+    w = np.ones((sc.n_pixels, 3))
+    with pytest.raises(st.StError):
+        _gpu_grad(st, sc, 2, 1, w, st.EDGE_TERM_SECONDARY, sec_pick=5)

@@ -144,3 +144,13 @@ def test_shadow_edges_in_a_binned_call_equal_the_views_traced_alone(st):
     scene.close()
     assert rel_l2([full[0].cpu().numpy(), full[1].cpu().numpy()], [dv.cpu().numpy(), df.cpu().numpy()]) <= 1e-5
     assert sh_full.abs().max() > 0.05 * full[0].abs().max()
+
+
+def test_shadow_bit_adds_nothing_without_point_lights(st):
+    # an environment-only scene has no point light to cast a shadow edge
+    sc = S.small_variant(S.make("env"), n_views=1, max_res=24, spp=2)
+    assert len(sc.light_pos) == 0
+    w = np.random.default_rng(2).normal(size=(sc.n_pixels, 3))
+    a = _gpu(st, sc, 2, 4, w, st.EDGE_TERM_PRIMARY | st.EDGE_TERM_SHADOW)
+    b = _gpu(st, sc, 2, 4, w, st.EDGE_TERM_PRIMARY)
+    assert rel_l2(a, b) <= 1e-6

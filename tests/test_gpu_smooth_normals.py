@@ -111,3 +111,19 @@ def test_refit_recomputes_the_vertex_normals(st):
     fresh.close()
     np.testing.assert_array_equal(a, b)
     assert_image_parity(a, O.render_pixels(O.OracleScene(sc, vertices=V1), O.params(2, 5), O.all_pixels(sc))[0])
+
+
+def test_smooth_normals_with_rgb_specular_and_mesh_colors(st):
+    # the smooth adjoint with 7 parameters per texel at mesh-colors resolution 2
+    sc = S.tiny(res=32, spp=4)
+    sc.smooth_normals = True
+    rng = np.random.default_rng(12)
+    sc.face_params = np.repeat(sc.face_params, 6, axis=0)
+    sc.color_res = 2
+    P = sc.face_params
+    sc.face_params = np.c_[P[:, :3], rng.uniform(0.02, 0.5, (len(P), 3)), P[:, 4]].astype(np.float32)
+    w = rng.normal(size=(sc.n_pixels, 3))
+    dV, dF = _backward(st, sc, 2, 17, w)
+    assert dF.shape == (len(sc.face_params), 7)
+    rv, rf, _ = O.grad_pixels(O.OracleScene(sc), O.params(2, 17), O.all_pixels(sc), w)
+    assert rel_l2([dV], [rv]) <= GRAD_REL and rel_l2([dF], [rf]) <= GRAD_REL
