@@ -89,6 +89,7 @@ typedef struct {
  * from the camera and from a point offset from it, Sec. 4); the scene's and
  * the view's lights together are at most ST_MAX_LIGHTS. */
 #define ST_MAX_VIEW_LIGHTS 2
+#define ST_MAX_VIEWS 65535        /* views per call (and, for the shadow-edge term, (view, light) pairs) */
 #define ST_SEC_PICK_TREE 0        /* st_render_opts.sec_pick: importance through the edge hierarchy */
 #define ST_SEC_PICK_UNIFORM 1     /* st_render_opts.sec_pick: uniform over all edges */
 typedef struct {
@@ -192,8 +193,8 @@ st_status st_rebuild(st_scene* scene, const float* new_vertices, void* stream);
 /* New texel parameters (device float [F*n][5 or 7], see st_scene_desc); the material update (Sec. 3.3). */
 st_status st_set_face_params(st_scene* scene, const float* face_params, void* stream);
 
-/* Forward render of n_views views (host array) with max_bounces surface
- * vertices per path (1..ST_MAX_BOUNCES). out_image: device float [N][3], N =
+/* Forward render of n_views views (host array, 1..ST_MAX_VIEWS) with max_bounces
+ * surface vertices per path (1..ST_MAX_BOUNCES). out_image: device float [N][3], N =
  * max over views of pixel_offset + W*H; it is overwritten on every pixel of
  * the views (other rows untouched). opts may be NULL (batched, graph on). */
 st_status st_render(st_scene* scene, const st_view* views, int n_views, int default_spp,

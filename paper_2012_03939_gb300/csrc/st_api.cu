@@ -587,6 +587,7 @@ std::vector<long long> graph_key(const Plan& p, int Q, const st_scene* s) {
 st_status plan_call(st_scene* s, const st_view* views, int n_views, int default_spp, int B, const st_render_opts* opts,
                     int kind, bool want_interior, Plan& p) {
   if (!views || n_views <= 0) return fail(ST_ERR_INVALID_ARG, "no views");
+  if (n_views > ST_MAX_VIEWS) return fail(ST_ERR_UNSUPPORTED, "more than ST_MAX_VIEWS views in one call");
   if (B < 1 || B > ST_MAX_BOUNCES) return fail(ST_ERR_UNSUPPORTED, "max_bounces must be in [1, 8]");
   p.kind = kind;
   p.B = B;
@@ -639,7 +640,8 @@ st_status plan_call(st_scene* s, const st_view* views, int n_views, int default_
     if (p.shadow) {
       long long ne = (long long)v.width * v.height * (p.o.edge_spp > 0 ? p.o.edge_spp : spp);
       for (int l = 0; l < s->nl + v.n_lights; ++l) {
-        if (p.pairs.size() >= (1u << 24)) return fail(ST_ERR_UNSUPPORTED, "too many (view, light) pairs");
+        if (p.pairs.size() >= (size_t)ST_MAX_VIEWS)
+          return fail(ST_ERR_UNSUPPORTED, "shadow edges: more than ST_MAX_VIEWS (view, light) pairs in one call");
         Seg sg{base, (ne + 31) / 32 * 64, i, 2, (unsigned)l, (unsigned)p.pairs.size(), ne};
         p.pairs.push_back(make_int2(i, l));
         p.segs.push_back(sg);

@@ -154,3 +154,20 @@ def test_shadow_bit_adds_nothing_without_point_lights(st):
     a = _gpu(st, sc, 2, 4, w, st.EDGE_TERM_PRIMARY | st.EDGE_TERM_SHADOW)
     b = _gpu(st, sc, 2, 4, w, st.EDGE_TERM_PRIMARY)
     assert rel_l2(a, b) <= 1e-6
+
+
+def test_call_limits_on_views_and_shadow_pairs(st):
+    # grids index views (and shadow (view, light) pairs) in their y dimension:
+    # a call beyond the limit is refused before any launch
+    sc = S.tiny(res=8, spp=1)
+    scene = st.Scene.from_scene(sc)
+    v = sc.views[0]
+    many = [dataclasses.replace(v, width=1, height=1, pixel_offset=i) for i in range(65536)]
+    w = torch.zeros((65536, 3), device="cuda")
+    with pytest.raises(st.StError):
+        scene.render(many, 1, 1)
+    few = many[:40000]
+    two = [dataclasses.replace(u, lights=(((0.0, 2.0, 0.0), (1.0, 1.0, 1.0)),)) for u in few]
+    with pytest.raises(st.StError):     # 40000 views x (1 scene + 1 view light) pairs
+        scene.backward(two, 1, 1, w, st.make_opts(edge_term=st.EDGE_TERM_SHADOW))
+    scene.close()
