@@ -354,16 +354,17 @@ def run_ours(args):
     value_fwd = seg_fwd * args.steps * world / (ms_fwd / 1000.0) / 1e6
 
     # the same step with the secondary-visibility edge term added (one edge
-    # sample per camera-path vertex, two side paths per accepted sample)
+    # sample per camera-path vertex, picked through the edge hierarchy, two
+    # side paths per accepted sample)
     bs = st.make_opts(mode="batched", use_graph=1, edge_term=edge_on | st.EDGE_TERM_SECONDARY, edge_mode=0,
-                      chunk_paths=chunk, persist_blocks=persist)
+                      chunk_paths=chunk, persist_blocks=persist, sec_pick="tree")
     _, ss = counts(fb, bs)
     seg_sec = seg_fwd + ss["extension_rays"] + ss["shadow_rays"]
     sec_steps = max(2, args.steps // 2)
     ms_sec = timed(lambda: step(fb, bs), sec_steps, 1)
     with_sec = {"value": round(seg_sec * sec_steps * world / (ms_sec / 1000.0) / 1e6, 3),
                 "ms_per_step": round(ms_sec / sec_steps, 3), "segments_per_step": seg_sec,
-                "secondary_samples_per_step": ss["secondary_samples"]}
+                "secondary_samples_per_step": ss["secondary_samples"], "pick": "edge hierarchy"}
 
     # roofline of the dominant kernel (closest-hit traversal): algorithmic bytes
     # from the instrumented traversal, time from CUDA events around each launch
