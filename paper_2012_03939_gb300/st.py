@@ -47,6 +47,7 @@ class EnvMap(C.Structure):
 
 MAX_VIEW_LIGHTS = 2
 SEC_PICK_TREE, SEC_PICK_UNIFORM = 0, 1
+MAX_VIEWS = 65535
 
 
 class View(C.Structure):

@@ -70,3 +70,18 @@ def test_structure_sizes_match_c_layout(tmp_path):
         assert int(got[cname]) == ctypes.sizeof(py), cname
         for f, _ in py._fields_:
             assert int(got["%s.%s" % (cname, f)]) == getattr(py, f).offset, (cname, f)
+
+
+def test_binding_constants_match_header():
+    # every constant the binding restates has the header's value
+    from paper_2012_03939_gb300 import st
+    src = open(os.path.join(ROOT, "include", "st.h")).read()
+    defs = {k: int(v) for k, v in re.findall(r"#define ST_([A-Z0-9_]+)\s+(-?\d+)", src)}
+    pairs = {"MODE_BATCHED": st.MODE_BATCHED, "MODE_PER_VIEW": st.MODE_PER_VIEW,
+             "EDGE_SILHOUETTE": st.EDGE_SILHOUETTE, "EDGE_ALL": st.EDGE_ALL,
+             "EDGE_TERM_PRIMARY": st.EDGE_TERM_PRIMARY, "EDGE_TERM_SECONDARY": st.EDGE_TERM_SECONDARY,
+             "EDGE_TERM_SHADOW": st.EDGE_TERM_SHADOW, "BVH_PLOC": st.BVH_PLOC, "BVH_LBVH": st.BVH_LBVH,
+             "MAX_VIEW_LIGHTS": st.MAX_VIEW_LIGHTS, "MAX_VIEWS": st.MAX_VIEWS,
+             "SEC_PICK_TREE": st.SEC_PICK_TREE, "SEC_PICK_UNIFORM": st.SEC_PICK_UNIFORM}
+    for k, v in pairs.items():
+        assert defs[k] == v, k
