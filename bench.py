@@ -366,6 +366,42 @@ def run_ours(args):
                 "ms_per_step": round(ms_sec / sec_steps, 3), "segments_per_step": seg_sec,
                 "secondary_samples_per_step": ss["secondary_samples"], "pick": "edge hierarchy"}
 
+    # the same step with the optional terms and shading of the widened scope:
+    # point-light shadow edges (scenes with point lights) and interpolated
+    # vertex normals (a second scene created with the option)
+    def step_with(scn, fopts, bopts):
+        scn.render(views, B, seed, fopts, out=img)
+        g = (img - target) * (2 * inv_n)
+        dV.zero_()
+        dF.zero_()
+        scn.backward(views, B, seed, g, bopts, d_vertices=dV, d_face_params=dF)
+
+    def segments_with(scn, fopts, bopts):
+        step_with(scn, fopts, bopts)
+        s1 = scn.stats()
+        scn.render(views, B, seed, fopts, out=img)
+        s0 = scn.stats()
+        assert s0["device_error"] == 0 and s1["device_error"] == 0
+        return s0["extension_rays"] + s0["shadow_rays"] + s1["extension_rays"] + s1["shadow_rays"]
+
+    widened = {}
+    if not adam:
+        n_w = max(2, args.steps // 2)
+        if len(sc.light_pos) > 0:
+            bsh = st.make_opts(mode="batched", use_graph=1, edge_term=edge_on | st.EDGE_TERM_SHADOW, edge_mode=0,
+                               chunk_paths=chunk, persist_blocks=persist)
+            seg_w = segments_with(scene, fb, bsh)
+            ms_w = timed(lambda: step_with(scene, fb, bsh), n_w, 1)
+            widened["with_shadow_edges"] = {"value": round(seg_w * n_w * world / (ms_w / 1000.0) / 1e6, 3),
+                                            "ms_per_step": round(ms_w / n_w, 3), "segments_per_step": seg_w}
+        import dataclasses
+        sm_scene = st.Scene.from_scene(dataclasses.replace(sc, smooth_normals=True), bvh_builder=args.bvh)
+        seg_w = segments_with(sm_scene, fb, bb)
+        ms_w = timed(lambda: step_with(sm_scene, fb, bb), n_w, 1)
+        widened["with_smooth_normals"] = {"value": round(seg_w * n_w * world / (ms_w / 1000.0) / 1e6, 3),
+                                          "ms_per_step": round(ms_w / n_w, 3), "segments_per_step": seg_w}
+        sm_scene.close()
+
     # roofline of the dominant kernel (closest-hit traversal): algorithmic bytes
     # from the instrumented traversal, time from CUDA events around each launch
     ci = st.make_opts(mode="batched", use_graph=0, count_visits=1, chunk_paths=chunk)
@@ -467,7 +503,7 @@ def run_ours(args):
                "per_view": {"value": round(value_pv, 3), "ms_per_step": round(ms_pv / pv_steps, 3),
                             "launch": "per-view, host-read queue counts, no graph"},
                "forward_only": {"value": round(value_fwd, 3), "ms_per_step": round(ms_fwd / args.steps, 3)},
-               "with_secondary_edges": with_sec,
+               "with_secondary_edges": with_sec, **widened,
                "roofline": roofline, "cpu_baseline": cpu,
                "e2e": {"value": round(value_e2e, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": d2h, "ms_per_step": round(ms_e2e / args.steps, 3)},

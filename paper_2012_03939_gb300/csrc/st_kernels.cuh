@@ -328,6 +328,11 @@ __global__ void __launch_bounds__(EXT_BLOCK) k_sh_prep(KCtx c, long long j0, int
   float3 org = y + dir * (SH_EDGE_DELTA * dy);
   // the edge's own faces meet that ray only at y: they receive no shadow from it
   int2 ef = c.edge_f[e];
+  {
+    // the receiver search is a closest-hit query: counted with the extension rays
+    unsigned m = __activemask();
+    if ((int)(threadIdx.x & 31) == __ffs(m) - 1) atomicAdd(&E.stat[STAT_EXT], (unsigned long long)__popc(m));
+  }
   float th;
   int leaf = -1;
   int rf = trace_bvh<false, false, true>(c.nodes, c.tri, c.nf, org, dir, __int_as_float(0x7f800000), ef.x, th,
