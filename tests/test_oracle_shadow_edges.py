@@ -150,3 +150,107 @@ def test_a_convex_mesh_receives_no_shadow_edge_from_itself():
         sc.light_pos = np.array([L], np.float32)
         sv, _ = O.shadow_edge_grad(O.OracleScene(sc), O.params(1, 5), w)
         assert np.all(sv == 0)
+
+
+# ---------------------------------------------------------------------------- tilted receiver
+# The same construction on a floor tilted about two axes, so the receiver's
+# normal has no zero component: the shadow is the occluder projected from the
+# light onto the tilted plane, and the directions include a rigid rotation of
+# the floor (its normal turns) as well as its translation along the normal.
+def _rot(ax, ay, az):
+    cx, sx, cy, sy, cz, sz = math.cos(ax), math.sin(ax), math.cos(ay), math.sin(ay), math.cos(az), math.sin(az)
+    Rx = np.array([[1, 0, 0], [0, cx, -sx], [0, sx, cx]])
+    Ry = np.array([[cy, 0, sy], [0, 1, 0], [-sy, 0, cy]])
+    Rz = np.array([[cz, -sz, 0], [sz, cz, 0], [0, 0, 1]])
+    return Rz @ Ry @ Rx
+
+
+def _tilted_scene(spp=1):
+    sc = _scene(spp)
+    V = sc.vertices.astype(np.float64)
+    V[:4] = V[:4] @ _rot(0.25, 0.1, -0.18).T
+    sc.vertices = V.astype(np.float32)
+    return sc
+
+
+def _plane(V):
+    """Point and unit normal of the floor (faces (0, 2, 1) and (0, 3, 2) wind upward)."""
+    n = np.cross(V[1] - V[0], V[2] - V[0])
+    n = -n / np.linalg.norm(n)
+    return V[0], n
+
+
+def _h_tilted(v, V, pts):
+    eye, d = _rays(v, pts)
+    x0, n = _plane(V)
+    t = ((x0 - eye) @ n) / (d @ n)
+    p = eye + d * t[:, None]
+    wl = LIGHT - p
+    dist = np.linalg.norm(wl, axis=1)
+    cos = np.maximum((wl @ n) / dist, 0.0)
+    return np.outer(cos / dist ** 2 * INTENSITY / math.pi, KD)
+
+
+def _pixel_values_tilted(sc, V, pix):
+    v = sc.views[0]
+    x0, n = _plane(V)
+    occ = V[4:7]
+    s = ((x0 - LIGHT) @ n) / ((occ - LIGHT) @ n)
+    T = G.project(v, LIGHT + (occ - LIGHT) * s[:, None])
+    out = np.zeros((len(pix), 3))
+    for i, (_, x, y) in enumerate(pix):
+        sq = np.array([[x, y], [x + 1, y], [x + 1, y + 1], [x, y + 1]], np.float64)
+        p_all, w_all = G.polygon_quadrature(sq, subdiv=2)
+        full = w_all @ _h_tilted(v, V, p_all)
+        C = G.clip_polygon(T, x, y, x + 1, y + 1)
+        if len(C) >= 3:
+            p_s, w_s = G.polygon_quadrature(np.array(C), subdiv=2)
+            full = full - w_s @ _h_tilted(v, V, p_s)
+        out[i] = full
+    return out
+
+
+def test_shadow_edge_gradient_on_a_tilted_floor():
+    sc = _tilted_scene(spp=64)
+    pix = _pixels(sc)
+    rows = O.pixel_index(sc, pix)
+    V0 = sc.vertices.astype(np.float64)
+    # the closed form holds for the tilted floor (value check, many samples)
+    val = O.render_pixels(O.OracleScene(_tilted_scene(spp=2048)), O.params(1, 5), pix[::9])[0]
+    exp_val = _pixel_values_tilted(sc, V0, pix[::9])
+    assert np.all(np.abs(val - exp_val) < 4 * exp_val.max() / math.sqrt(2048) + 1e-6 * exp_val.max())
+    rng = np.random.default_rng(43)
+    w = rng.normal(size=(len(pix), 3))
+    wfull = np.zeros((sc.n_pixels, 3))
+    wfull[rows] = w
+    h = 1e-5
+    dirs = []
+    for vi in range(4, 7):
+        for k in range(3):
+            D = np.zeros_like(V0)
+            D[vi, k] = 1.0
+            dirs.append(D)
+    x0, n = _plane(V0)
+    c = V0[:4].mean(0)
+    D = np.zeros_like(V0)
+    D[:4] = n
+    dirs.append(D)                                  # the floor along its normal
+    axis = np.cross(n, [1.0, 0.0, 0.0])
+    axis /= np.linalg.norm(axis)
+    D = np.zeros_like(V0)
+    D[:4] = np.cross(axis, V0[:4] - c) * 0.1
+    dirs.append(D)                                  # the floor turned about an axis in it
+    exp = np.array([((_pixel_values_tilted(sc, V0 + h * D, pix) - _pixel_values_tilted(sc, V0 - h * D, pix)) * w).sum()
+                    / (2 * h) for D in dirs])
+    osc = O.OracleScene(sc)
+    ests = []
+    for seed in range(8):
+        prm = O.params(1, 640 + seed, edge_spp=64)
+        dv, _, _ = O.grad_pixels(osc, prm, pix, w)
+        sv, _ = O.shadow_edge_grad(osc, prm, wfull)
+        ests.append([((dv + sv) * D).sum() for D in dirs])
+    ests = np.array(ests)
+    mean, se = ests.mean(0), ests.std(0, ddof=1) / math.sqrt(len(ests))
+    scale = np.abs(exp).max()
+    assert np.all(np.abs(mean - exp) < 4 * se + 2e-3 * scale), (mean, exp, se)
+    assert np.abs(exp[:9]).max() > 0.2 * scale and abs(exp[10]) > 0.02 * scale
