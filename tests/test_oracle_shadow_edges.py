@@ -254,3 +254,17 @@ def test_shadow_edge_gradient_on_a_tilted_floor():
     scale = np.abs(exp).max()
     assert np.all(np.abs(mean - exp) < 4 * se + 2e-3 * scale), (mean, exp, se)
     assert np.abs(exp[:9]).max() > 0.2 * scale and abs(exp[10]) > 0.02 * scale
+
+
+def test_view_light_gives_the_scene_lights_shadow_edges():
+    # the same light as the view's own instead of the scene's: same index (the
+    # scene has no other), same counters, the same estimate bit for bit
+    import dataclasses
+    sc = _scene(spp=4)
+    w = np.random.default_rng(5).normal(size=(sc.n_pixels, 3))
+    a = O.shadow_edge_grad(O.OracleScene(sc), O.params(1, 9), w)[0]
+    sv = dataclasses.replace(sc, light_pos=np.zeros((0, 3), np.float32), light_intensity=np.zeros((0, 3), np.float32))
+    sv.views = [dataclasses.replace(v, lights=((tuple(LIGHT), (INTENSITY,) * 3),)) for v in sc.views]
+    b = O.shadow_edge_grad(O.OracleScene(sv), O.params(1, 9), w)[0]
+    assert np.abs(a).max() > 0
+    np.testing.assert_array_equal(a, b)
