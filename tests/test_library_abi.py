@@ -85,3 +85,15 @@ def test_binding_constants_match_header():
              "SEC_PICK_TREE": st.SEC_PICK_TREE, "SEC_PICK_UNIFORM": st.SEC_PICK_UNIFORM}
     for k, v in pairs.items():
         assert defs[k] == v, k
+
+
+def test_make_opts_maps_names_to_header_values():
+    from paper_2012_03939_gb300 import st
+    o = st.make_opts()
+    assert (o.sec_pick, o.edge_mode, o.mode, o.use_graph, o.edge_term) == (st.SEC_PICK_TREE, st.EDGE_SILHOUETTE,
+                                                                           st.MODE_BATCHED, 1, 0)
+    o = st.make_opts(sec_pick="uniform", edge_mode="all", mode="per_view",
+                     edge_term=st.EDGE_TERM_SECONDARY | st.EDGE_TERM_SHADOW)
+    assert (o.sec_pick, o.edge_mode, o.mode, o.edge_term) == (st.SEC_PICK_UNIFORM, st.EDGE_ALL, st.MODE_PER_VIEW, 6)
+    with pytest.raises(KeyError):
+        st.make_opts(sec_pick="random")
