@@ -20,7 +20,10 @@
 //  * Camera: pinhole, fov_y, +y up, row 0 at the top, box-filter jitter.
 //  * Intersection: watertight test (Woop, Benthin, Wald, JCGT 2013), closest
 //    t in (T_EPS, tmax), origin triangle excluded, equal t -> lower face id.
-//  * Shading: flat face normal flipped toward the incoming ray (two-sided).
+//  * Shading: flat face normal flipped toward the incoming ray (two-sided); with
+//    the scene option smooth_normals, a shading normal interpolated from vertex
+//    normals, used for NEE, BRDF, sampling and pdfs, a direction counting only
+//    above both planes (see shading_normal).
 //  * BRDF: f = kd/pi + ks D G1(i) G1(o) / (4 cos_i cos_o): the Fresnel factor
 //    is held at its normal-incidence value ks (the "specular color", one value
 //    for all channels with 5 parameters per texel, one per channel with 7), so
@@ -52,11 +55,13 @@
 //  * Edge term (secondary visibility, gradients only, orc_params.secondary):
 //    at every vertex b of a camera path, one edge of the mesh picked uniformly
 //    (u from counter (c0, c1, b<<4|3, stream): integer pick (u0>>8)*E>>24, u1
-//    along the edge), kept if it is a silhouette seen from the vertex (or every
+//    along the edge; secondary = 2 picks through the edge hierarchy instead, see
+//    EdgeTree), kept if it is a silhouette seen from the vertex (or every
 //    edge, edge_mode 1), is not an edge of the vertex's face, and has a part
 //    above the tangent plane; a point uniform on that part; two side paths at
 //    +-SEC_EPS radians across the edge's arc continue the path from vertex
 //    b + 1 (counters (c0, c1, vertex<<4|call, 16 + b)); see secondary_edge().
+//  * Shadow-edge term (point lights): see orc_shadow_edge_grad.
 #include "oracle.h"
 
 #include <algorithm>
