@@ -129,9 +129,11 @@ def test_closed_form_occluded_floor_value():
     assert exp.min() < 0.8 * exp.max()     # the pixels include the penumbra
 
 
-@pytest.mark.parametrize("sampling", [1, 2])
-def test_secondary_edge_gradient_matches_closed_form(sampling):
+@pytest.mark.parametrize("sampling,edge_mode", [(1, 0), (2, 0), (2, 1)])
+def test_secondary_edge_gradient_matches_closed_form(sampling, edge_mode):
     # sampling 1: one edge picked uniformly; 2: picked through the edge hierarchy
+    # (edge_mode 1: every edge is a candidate, so the normal cones drop nothing;
+    # the scene has no shading discontinuity, so the expectation is the same)
     sc = _occluder_scene(spp=512)
     pix = _free_pixels(sc)
     V0 = sc.vertices.astype(np.float64)
@@ -148,7 +150,7 @@ def test_secondary_edge_gradient_matches_closed_form(sampling):
     ests, plain = [], []
     osc = O.OracleScene(sc)
     for seed in range(8):
-        dv, _, _ = O.grad_pixels(osc, O.params(1, 700 + seed, secondary=sampling), pix, w)
+        dv, _, _ = O.grad_pixels(osc, O.params(1, 700 + seed, edge_mode=edge_mode, secondary=sampling), pix, w)
         ests.append(dv)
         if seed < 2:
             plain.append(O.grad_pixels(osc, O.params(1, 700 + seed), pix, w)[0])
