@@ -143,6 +143,9 @@ def n_pixels(views) -> int:
 
 
 def make_opts(**kw) -> RenderOpts:
+    """st_render_opts with the library's defaults, fields overridden by keyword. Names accepted for mode
+    ("batched", "per_view"), edge_mode ("silhouette", "all") and sec_pick ("tree": the edge hierarchy, "uniform");
+    edge_term is an OR of EDGE_TERM_PRIMARY, EDGE_TERM_SECONDARY and EDGE_TERM_SHADOW."""
     o = RenderOpts(0, EDGE_SILHOUETTE, 0, MODE_BATCHED, 1, 0, 0, 0, 0, None, SEC_PICK_TREE)
     for k, v in kw.items():
         if k == "mode" and isinstance(v, str):
@@ -156,7 +159,9 @@ def make_opts(**kw) -> RenderOpts:
 
 
 class Scene:
-    """A mesh scene on the current CUDA device (owns a library scene handle)."""
+    """A mesh scene on the current CUDA device (owns a library scene handle). color_res: mesh-colors resolution
+    (face_params then holds a row per texel); bvh_builder: "ploc" or "lbvh"; smooth_normals: shading normals
+    interpolated from vertex normals (recomputed by refit and rebuild) instead of flat face normals."""
 
     def __init__(self, vertices: torch.Tensor, faces: torch.Tensor, face_params: torch.Tensor, brdf: str = "ggx",
                  light_pos=None, light_intensity=None, env: Optional[np.ndarray] = None, stream=None,
