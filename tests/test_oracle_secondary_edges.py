@@ -365,3 +365,132 @@ def test_hierarchy_pick_lands_on_usable_edges_more_often():
         tree.append(O.sec_edge_pmf(osc, p, n, bnd)[usable].sum())
         unif.append(usable.mean())
     assert np.mean(tree) > 3 * np.mean(unif) > 0, (np.mean(tree), np.mean(unif))
+
+
+def _py_tree(sc):
+    """The edge hierarchy restated in numpy from its definition (blocks of G edges in edge order under a
+    complete binary tree; boxes, summed lengths and normal cones)."""
+    V = sc.vertices.astype(np.float64)
+    ev, ef = _edges_and_faces(sc)
+    tri = V[sc.faces]
+    un = np.cross(tri[:, 1] - tri[:, 0], tri[:, 2] - tri[:, 0])
+    un /= np.linalg.norm(un, axis=1, keepdims=True)
+    E = len(ev)
+    G = max(4, -(-E // (1 << 14)))
+    nleaf = -(-E // G)
+    L = 0
+    while (1 << L) < nleaf:
+        L += 1
+    nn = 2 << L
+    lo = np.full((nn, 3), np.inf)
+    hi = np.full((nn, 3), -np.inf)
+    S = np.zeros(nn)
+    ax = np.zeros((nn, 3))
+    ct = np.full(nn, -2.0)
+    for i in range(nleaf):
+        k = (1 << L) + i
+        es = range(i * G, min(E, (i + 1) * G))
+        P = V[ev[list(es)].ravel()]
+        lo[k], hi[k] = P.min(0), P.max(0)
+        S[k] = sum(np.linalg.norm(V[ev[e, 1]] - V[ev[e, 0]]) for e in es)
+        if any(len(ef[e]) != 2 for e in es):
+            continue
+        normals = np.array([un[f] for e in es for f in ef[e]])
+        a = normals.sum(0)
+        if np.linalg.norm(a) <= 1e-6:
+            continue
+        a /= np.linalg.norm(a)
+        c = (normals @ a).min()
+        ax[k], ct[k] = a, (c if c > 0 else -2.0)
+    for k in range((1 << L) - 1, 0, -1):
+        a, b = 2 * k, 2 * k + 1
+        lo[k], hi[k], S[k] = np.minimum(lo[a], lo[b]), np.maximum(hi[a], hi[b]), S[a] + S[b]
+        if not (S[a] > 0) or not (S[b] > 0):
+            o = a if S[a] > 0 else b
+            ax[k], ct[k] = ax[o], ct[o]
+            continue
+        if ct[a] < -1.5 or ct[b] < -1.5:
+            continue
+        s = ax[a] + ax[b]
+        if np.linalg.norm(s) <= 1e-6:
+            continue
+        s /= np.linalg.norm(s)
+        ang = lambda x: math.acos(max(-1.0, min(1.0, x)))
+        th = max(ang(s @ ax[a]) + ang(ct[a]), ang(s @ ax[b]) + ang(ct[b]))
+        ax[k], ct[k] = s, (math.cos(th) if th < math.pi / 2 else -2.0)
+    return dict(G=G, L=L, nleaf=nleaf, E=E, lo=lo, hi=hi, S=S, ax=ax, ct=ct)
+
+
+def _py_weight(t, k, p, n, bnd, sil):
+    if not (t["S"][k] > 0):
+        return 0.0
+    lo, hi = t["lo"][k], t["hi"][k]
+    top = np.where(n > 0, hi - p, lo - p) @ n
+    if not (top > bnd):
+        return 0.0
+    if sil and t["ct"][k] > -1.5:
+        v = p - 0.5 * (lo + hi)
+        r, D = 0.5 * np.linalg.norm(hi - lo), np.linalg.norm(v)
+        if D > r:
+            cp = t["ax"][k] @ v / D
+            sp = math.sqrt(max(0.0, 1 - cp * cp))
+            cq = t["ct"][k]
+            sq = math.sqrt(max(0.0, 1 - cq * cq))
+            cmin = -1.0 if cp <= -cq else cp * cq - sp * sq
+            cmax = 1.0 if cp >= cq else cp * cq + sp * sq
+            if D * cmin - r > -bnd or D * cmax + r < bnd:
+                return 0.0
+    d = np.maximum(lo - p, np.maximum(0.0, p - hi))
+    return t["S"][k] / max(max(d @ d, 0.25 * (hi - lo) @ (hi - lo)), 1e-30)
+
+
+@pytest.mark.parametrize("name", ["occluder", "edges"])
+def test_hierarchy_matches_a_restatement_of_its_definition(name):
+    # probabilities and picks from an independent numpy statement of the tree,
+    # its weights and its counters (Philox words of the vertex's draws)
+    sc = _occluder_scene() if name == "occluder" else S.small_variant(S.make("edges"), 1, 8, 1)
+    t = _py_tree(sc)
+    osc = O.OracleScene(sc)
+    key = np.array([11 & 0xffffffff, 0], np.uint32)
+    for k_frame, (p, n) in enumerate(_tangent_frames(sc, 4, 12)):
+        bnd = 1e-5 * (1 + np.abs(p).max())
+        for mode in (0, 1):
+            # probabilities: products of the branch ratios along each leaf's path
+            pmf = np.zeros(t["E"])
+            for leaf in range(t["nleaf"]):
+                k, pr = (1 << t["L"]) + leaf, 1.0
+                while k > 1:
+                    par = k // 2
+                    wa, wb = _py_weight(t, 2 * par, p, n, bnd, mode == 0), _py_weight(t, 2 * par + 1, p, n, bnd,
+                                                                                      mode == 0)
+                    pr *= (wa if k % 2 == 0 else wb) / (wa + wb) if wa + wb > 0 else 0.0
+                    k = par
+                first = leaf * t["G"]
+                cnt = min(t["G"], t["E"] - first)
+                pmf[first:first + cnt] = pr / cnt
+            got = O.sec_edge_pmf(osc, p, n, bnd, mode)
+            np.testing.assert_allclose(got, pmf, rtol=1e-9, atol=1e-15)
+        # picks: the descent with one Philox word per level, then the leaf word
+        N = 64
+        uleaf = np.random.default_rng(k_frame).integers(0, 1 << 32, N)
+        e_or, pr_or = O.sec_edge_picks(osc, 11, 3, 1, 0, p, n, bnd, uleaf)
+        for i in range(N):
+            k, pr, u = 1, 1.0, None
+            for j in range(t["L"]):
+                if j % 4 == 0:
+                    u = O.philox([i, 3, (1 << 4) | (4 + j // 4), 0], key)
+                wa, wb = _py_weight(t, 2 * k, p, n, bnd, True), _py_weight(t, 2 * k + 1, p, n, bnd, True)
+                if not (wa + wb > 0):
+                    k = -1
+                    break
+                if (int(u[j % 4]) >> 8) * 2.0 ** -24 < wa / (wa + wb):
+                    k, pr = 2 * k, pr * wa / (wa + wb)
+                else:
+                    k, pr = 2 * k + 1, pr * wb / (wa + wb)
+            if k < 0:
+                assert e_or[i] == -1
+                continue
+            first = (k - (1 << t["L"])) * t["G"]
+            cnt = min(t["G"], t["E"] - first)
+            assert e_or[i] == first + ((int(uleaf[i]) >> 8) * cnt >> 24)
+            assert abs(pr_or[i] - pr / cnt) <= 1e-9 * pr / cnt
