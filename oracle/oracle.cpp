@@ -503,6 +503,8 @@ struct Vars {
   std::vector<int> vdim;
   std::vector<int> fid;   // face ids, 5 dims each
   std::vector<int> fdim;
+  std::vector<int> nvid;  // vertex normals (interpolated shading), 3 dims each; scatter_grad
+  std::vector<int> nvdim; // carries their derivative on to the vertices around them
   int nd = 0;
   bool overflow = false;  // a variable found no room in MAXD: the path's gradient is incomplete
 };
@@ -515,6 +517,7 @@ template <class T> struct Access;
 
 template <> struct Access<double> {
   static V3<double> vertex(const Scene& s, Vars*, int v) { return s.vert[v]; }
+  static V3<double> vnormal(const Scene&, Vars*, int, const V3d& N) { return N; }
   static MatT<double> params(const Scene& s, Vars*, int f) {
     MatT<double> m;
     const double* q = &s.param[(size_t)s.np * f];
@@ -545,6 +548,18 @@ template <> struct Access<Dual> {
       vars->vid.push_back(v); vars->vdim.push_back(base);
     }
     return {unit_dual(p.x, base), unit_dual(p.y, base + 1), unit_dual(p.z, base + 2)};
+  }
+  // vertex normal N of vertex v as three variables of its own
+  static V3<Dual> vnormal(const Scene&, Vars* vars, int v, const V3d& N) {
+    int base = -1;
+    for (size_t i = 0; i < vars->nvid.size(); ++i)
+      if (vars->nvid[i] == v) base = vars->nvdim[i];
+    if (base < 0) {
+      if (vars->nd + 3 > MAXD) { vars->overflow = true; return lift<Dual>(N); }
+      base = vars->nd; vars->nd += 3;
+      vars->nvid.push_back(v); vars->nvdim.push_back(base);
+    }
+    return {unit_dual(N.x, base), unit_dual(N.y, base + 1), unit_dual(N.z, base + 2)};
   }
   static MatT<Dual> params(const Scene& s, Vars* vars, int f) {
     int base = -1;
@@ -901,17 +916,42 @@ void secondary_edge(const Scene& s, const Rng& rng, int B, const Lights& lt, int
 // weights are b1 = ((p - v0) x e2).m / m.m and b2 = (e1 x (p - v0)).m / m.m (p
 // on the face's plane), and n_s = s / |s|, s = (1 - b1 - b2) N0 + b1 N1 + b2 N2,
 // turned with the geometric normal toward the incoming direction. Everything is
-// differentiated: the vertex normals through every face around the vertex.
-template <class T>
-V3<T> vertex_normal_of(const Scene& s, Vars* vars, int v) {
-  using A = Access<T>;
-  V3<T> M = lift<T>(V3d{0, 0, 0});
+// differentiated: each vertex normal is a variable of the path, and its
+// derivative goes on to the vertices of the faces around the vertex
+// (vertex_normal_chain), so a path's variables do not grow with the valence.
+V3d vertex_normal_value(const Scene& s, int v, double* mlen = nullptr) {
+  V3d M{0, 0, 0};
   for (int k = s.vf_start[v]; k < s.vf_start[(size_t)v + 1]; ++k) {
     const int* fi = &s.face[3 * (size_t)s.vf_list[k]];
-    V3<T> a = A::vertex(s, vars, fi[0]), b = A::vertex(s, vars, fi[1]), c = A::vertex(s, vars, fi[2]);
-    M = M + cross(b - a, c - a);
+    M = M + cross(s.vert[fi[1]] - s.vert[fi[0]], s.vert[fi[2]] - s.vert[fi[0]]);
   }
+  if (mlen) *mlen = len(M);
   return nrm(M);
+}
+
+template <class T>
+V3<T> vertex_normal_of(const Scene& s, Vars* vars, int v) {
+  return Access<T>::vnormal(s, vars, v, vertex_normal_value(s, v));
+}
+
+// d/dN of vertex v's normal to the vertices: N = M / |M| gives dM = (dN - N
+// (N.dN)) / |M|; each face's (v1 - v0) x (v2 - v0), a term of M, passes dM on
+// as v1: e2 x dM, v2: dM x e1, v0: minus both.
+void vertex_normal_chain(const Scene& s, int v, const V3d& gN, double* dv) {
+  double ml;
+  V3d N = vertex_normal_value(s, v, &ml);
+  if (!(ml > 0)) return;
+  V3d gM = scl(gN - scl(N, dot(N, gN)), 1.0 / ml);
+  for (int k = s.vf_start[v]; k < s.vf_start[(size_t)v + 1]; ++k) {
+    const int* fi = &s.face[3 * (size_t)s.vf_list[k]];
+    V3d e1 = s.vert[fi[1]] - s.vert[fi[0]], e2 = s.vert[fi[2]] - s.vert[fi[0]];
+    V3d g1 = cross(e2, gM), g2 = cross(gM, e1);
+    V3d g0 = -(g1 + g2);
+    const V3d* g[3] = {&g0, &g1, &g2};
+    for (int j = 0; j < 3; ++j) {
+      dv[3 * fi[j]] += g[j]->x; dv[3 * fi[j] + 1] += g[j]->y; dv[3 * fi[j] + 2] += g[j]->z;
+    }
+  }
 }
 
 // shading normal at p of face fi (vertices v0, v1, v2, m = e1 x e2), sign = +1 or
@@ -1131,8 +1171,13 @@ template <class F> void parallel_for(int n, int nt, F fn) {
   for (auto& x : th) x.join();
 }
 
-void scatter_grad(const Vars& vars, const Dual& loss, double* dv, double* df, int np) {
+void scatter_grad(const Scene& s, const Vars& vars, const Dual& loss, double* dv, double* df, int np) {
   if (vars.overflow) g_dual_overflow = true;
+  for (size_t i = 0; i < vars.nvid.size(); ++i) {
+    int d = vars.nvdim[i];
+    V3d gN{d < loss.n ? loss.g[d] : 0.0, d + 1 < loss.n ? loss.g[d + 1] : 0.0, d + 2 < loss.n ? loss.g[d + 2] : 0.0};
+    vertex_normal_chain(s, vars.nvid[i], gN, dv);
+  }
   for (size_t i = 0; i < vars.vid.size(); ++i)
     for (int k = 0; k < 3; ++k) {
       int dim = vars.vdim[i] + k;
@@ -1378,7 +1423,7 @@ long long orc_grad_pixels(const orc_scene* in, const orc_view* views, int n_view
       Dual L[3];
       trace_path<Dual>(s, rng, p->max_bounces, c.lt, c.eye, d, c0, (uint32_t)sidx, 0u, &vars, L, seg[tid], nullptr, sec);
       Dual loss = L[0] * (w[0] / c.spp) + L[1] * (w[1] / c.spp) + L[2] * (w[2] / c.spp);
-      scatter_grad(vars, loss, gv[tid].data(), gf[tid].data(), s.np);
+      scatter_grad(s, vars, loss, gv[tid].data(), gf[tid].data(), s.np);
     }
   });
   for (int t = 0; t < nt; ++t) {
@@ -1563,7 +1608,7 @@ long long orc_shadow_edge_grad(const orc_scene* in, const orc_view* views, int n
           V3<Dual> qd = Ld + scl(ud, sd);
           V3d js = scl(jx, nx) + scl(jy, ny);
           Dual vn = dot(lift<Dual>(js), qd - lift<Dual>(q));
-          scatter_grad(vars, vn * wt, gv[tid].data(), nullptr, s.np);
+          scatter_grad(s, vars, vn * wt, gv[tid].data(), nullptr, s.np);
         }
       });
     }
@@ -1601,7 +1646,7 @@ long long orc_trace_screen(const orc_scene* in, const orc_view* view, const orc_
                    p->secondary ? &sc : nullptr);
   for (int k = 0; k < 3; ++k) rgb[k] = L[k].v;
   Dual loss = L[0] * grad_w[0] + L[1] * grad_w[1] + L[2] * grad_w[2];
-  scatter_grad(vars, loss, d_verts, d_face, s.np);
+  scatter_grad(s, vars, loss, d_verts, d_face, s.np);
   if (g_dual_overflow) return -1;
   return seg;
 }

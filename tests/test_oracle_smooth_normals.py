@@ -9,7 +9,7 @@ evaluation written from that definition (own ray casting, vertex normals,
 blend, shadow test); the dual-number gradient (which now reaches every vertex
 around the hit face) equals central differences of the taped estimator; the
 secondary edge term is unchanged where vertex normals equal face normals; and
-a vertex with more neighbours than the dual numbers hold is reported.
+the gradient around a vertex of valence 200 matches the taped central differences.
 """
 import math
 
@@ -185,18 +185,38 @@ def test_secondary_term_unchanged_where_vertex_normals_are_face_normals():
     np.testing.assert_allclose(out[1], out[0], rtol=1e-9, atol=1e-9 * np.abs(out[0]).max())
 
 
-def test_a_vertex_beyond_the_dual_capacity_is_reported():
-    # a fan of 200 triangles around one vertex: its normal depends on 201
-    # vertices, more than one path's dual numbers hold
+def test_high_valence_vertex_gradient_matches_tape_replay_fd():
+    # a fan of 200 triangles around a raised centre: the centre's normal depends
+    # on all 201 vertices; each vertex normal is one variable of the path and
+    # its derivative reaches every vertex around it
     n = 200
     ang = np.linspace(0, 2 * np.pi, n, endpoint=False)
-    V = np.r_[[[0.0, 0.2, 0.0]], np.c_[np.cos(ang), np.zeros(n), np.sin(ang)]].astype(np.float32)
+    rng = np.random.default_rng(1)
+    V = np.r_[[[0.0, 0.3, 0.0]], np.c_[np.cos(ang), rng.uniform(-0.05, 0.05, n), np.sin(ang)]].astype(np.float32)
     F = np.array([[0, 1 + (i + 1) % n, 1 + i] for i in range(n)], np.int32)
-    vs = [S.View((0.0, 2.5, 0.5), (0.0, 0.0, 0.0), (0.0, 1.0, 0.0), 40.0, 4, 4, 1)]
-    sc = S.Scene("fan", V, F, S.random_face_params(np.random.default_rng(1), n), "ggx",
-                 light_pos=np.array([[0.0, 2.0, 0.0]], np.float32), light_intensity=np.ones((1, 3), np.float32),
-                 views=vs, max_bounces=1, smooth_normals=True)
-    pix = O.all_pixels(sc)
-    O.render_pixels(O.OracleScene(sc), O.params(1, 1), pix)   # values need no duals
-    with pytest.raises(ValueError):
-        O.grad_pixels(O.OracleScene(sc), O.params(1, 1), pix, np.ones((len(pix), 3)))
+    vs = [S.View((0.125, 2.5, 0.5), (0.0, 0.0, 0.0), (0.0, 1.0, 0.0), 40.0, 8, 8, 1)]
+    P = S.random_face_params(rng, n)
+    P[:, 3] = 0.0
+    sc = S.Scene("fan", V, F, P, "ggx", light_pos=np.array([[0.5, 2.0, 0.25]], np.float32),
+                 light_intensity=np.full((1, 3), 3.0, np.float32), views=vs, max_bounces=1, smooth_normals=True)
+    V0 = V.astype(np.float64)
+    prm = O.params(1, 1)
+    w = np.array([0.3, 0.5, -0.2])
+    checked = far = 0
+    for px, py in [(3.6, 4.1), (4.4, 3.7), (4.05, 4.2)]:
+        osc = O.OracleScene(sc, vertices=V0)
+        _, dv, _ = O.trace_screen(osc, prm, 0, px, py, grad_w=w)
+        _, tape = O.trace_screen_taped(osc, prm, 0, px, py)
+        far += np.count_nonzero(np.abs(dv[1:]).sum(1)) > 10
+        h = 1e-6
+        for vi in [0] + list(rng.choice(np.arange(1, n + 1), 12, replace=False)):
+            for k in range(3):
+                Vp, Vm = V0.copy(), V0.copy()
+                Vp[vi, k] += h
+                Vm[vi, k] -= h
+                fp = O.trace_screen_taped(O.OracleScene(sc, vertices=Vp), prm, 0, px, py, tape=tape)
+                fm = O.trace_screen_taped(O.OracleScene(sc, vertices=Vm), prm, 0, px, py, tape=tape)
+                fd = (w @ fp - w @ fm) / (2 * h)
+                assert abs(fd - dv[vi, k]) < 1e-5 * max(1.0, abs(fd)), (vi, k, fd, dv[vi, k])
+                checked += 1
+    assert checked == 3 * 13 * 3 and far == 3
