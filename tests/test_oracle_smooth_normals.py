@@ -220,3 +220,98 @@ def test_high_valence_vertex_gradient_matches_tape_replay_fd():
                 assert abs(fd - dv[vi, k]) < 1e-5 * max(1.0, abs(fd)), (vi, k, fd, dv[vi, k])
                 checked += 1
     assert checked == 3 * 13 * 3 and far == 3
+
+
+def _valley(spp):
+    """Two faces meeting in a valley (concave, open below): the near face's vertex normals at the valley are the
+    mean of both faces', so its shading normal stands up out of the face toward the far face. The far face hides
+    part of the near face's sky; nothing lies below the near face."""
+    V = np.array([[-1.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 0.6, 1.2], [0.0, 0.6, -1.2]], np.float32)
+    F = np.array([[0, 2, 1], [0, 1, 3]], np.int32)
+    P = np.array([[0.6, 0.5, 0.4, 0.0, 0.5], [0.6, 0.5, 0.4, 0.0, 0.5]], np.float32)
+    vs = [S.View((0.25, 2.25, 2.5), (0.0, 0.25, 0.5), (0.0, 1.0, 0.0), 30.0, 16, 16, spp)]
+    return S.Scene("valley", V, F, P, "ggx", env=np.full((16, 32, 3), 0.7, np.float32), views=vs, max_bounces=1,
+                   smooth_normals=True)
+
+
+def _hits_triangle(o, W, a, b, c):
+    """Does the ray o + t w (t > 1e-5) meet triangle (a, b, c), for every direction w in W?"""
+    e1, e2 = b - a, c - a
+    pv = np.cross(W, e2)
+    det = pv @ e1
+    with np.errstate(divide="ignore", invalid="ignore"):
+        inv = 1.0 / det
+        tv = o - a
+        u = (pv @ tv) * inv
+        qv = np.cross(tv, e1)
+        v = (W @ qv) * inv
+        t = (qv @ e2) * inv
+    return (np.abs(det) > 0) & (u >= 0) & (v >= 0) & (u + v <= 1) & (t > 1e-5)
+
+
+def test_uniform_sky_counts_directions_above_both_planes():
+    # a Lambertian point under a uniform sky of radiance L0, one vertex (the
+    # environment sample's MIS weight is 1): E[L] = kd/pi L0 I, I the integral of
+    # (n_s.w)+ over the directions above the face's plane as well and not hidden
+    # by the far face. Expected pixel values: I by quadrature over the sphere
+    # with each direction cast against the far face, n_s from the definition
+    # (vertex normals, barycentric blend), averaged over the pixel by Gauss points
+    spp = 1 << 19
+    sc = _valley(spp)
+    V = sc.vertices.astype(np.float64)
+    N = _vertex_normals(V, sc.faces)
+    v = sc.views[0]
+    ng = np.cross(V[2] - V[0], V[1] - V[0])
+    ng /= np.linalg.norm(ng)
+    nz, nph = 240, 480
+    z = (np.arange(nz) + 0.5) / nz * 2 - 1
+    ph = (np.arange(nph) + 0.5) / nph * 2 * np.pi
+    zz, pp = np.meshgrid(z, ph, indexing="ij")
+    rr = np.sqrt(1 - zz ** 2)
+    W = np.stack([rr * np.cos(pp), rr * np.sin(pp), zz], -1).reshape(-1, 3)
+    dw = 4 * np.pi / len(W)
+
+    def expected(px, py):
+        o, d = G.pixel_ray(v, px, py)
+        f, t, b1, b2 = _cast(V, sc.faces, o, d)
+        assert f == 0
+        p = o + t * d
+        s = (1 - b1 - b2) * N[0] + b2 * N[1] + b1 * N[2]    # face (0, 2, 1): b1 weighs vertex 2, b2 vertex 1
+        ns = s / np.linalg.norm(s)
+        keep = (W @ ng > 0) & ~_hits_triangle(p, W, V[0], V[1], V[3])
+        return (np.maximum(W @ ns, 0) * keep).sum() * dw
+
+    img = G.project(v, V[[0, 2, 1]])
+    pix, exp = [], []
+    for y in range(v.height):
+        for x in range(v.width):
+            C = G.clip_polygon(img, x, y, x + 1, y + 1)
+            if len(C) >= 3 and G.polygon_area(np.array(C)) > 0.999:
+                pix.append((0, x, y))
+    pix = pix[::4]
+    for _, x, y in pix:
+        pts, wts = G.polygon_quadrature(np.array([[x, y], [x + 1, y], [x + 1, y + 1], [x, y + 1]], float), 1)
+        exp.append(0.6 / math.pi * 0.7 * sum(w * expected(px, py) for (px, py), w in zip(pts, wts)))
+    pix, exp = np.array(pix, np.int32), np.array(exp)
+    assert len(pix) >= 6
+    got = O.render_pixels(O.OracleScene(sc), O.params(1, 4), pix)[0][:, 0]
+    # the sky sample is uniform over the sphere (pdf 1/(4 pi)), so a sample is at
+    # most 4 kd L0 (n_s.w)+: E[X^2] <= 16 (kd L0)^2 / 6
+    se = 4 * 0.6 * 0.7 / math.sqrt(6 * spp)
+    assert np.all(np.abs(got - exp) < 4 * se), (got, exp, se)
+    # the rule matters here: counting the open sky below the face (above the
+    # shading plane) would raise some pixels by far more than the resolution
+    def without_face_plane(px, py):
+        o, d = G.pixel_ray(v, px, py)
+        f, t, b1, b2 = _cast(V, sc.faces, o, d)
+        p = o + t * d
+        s_ = (1 - b1 - b2) * N[0] + b2 * N[1] + b1 * N[2]
+        ns = s_ / np.linalg.norm(s_)
+        keep = ~_hits_triangle(p, W, V[0], V[1], V[3])
+        return (np.maximum(W @ ns, 0) * keep).sum() * dw
+
+    alt = []
+    for _, x, y in pix:
+        pts, wts = G.polygon_quadrature(np.array([[x, y], [x + 1, y], [x + 1, y + 1], [x, y + 1]], float), 1)
+        alt.append(0.6 / math.pi * 0.7 * sum(w * without_face_plane(px, py) for (px, py), w in zip(pts, wts)))
+    assert (np.array(alt) - exp).max() > 12 * se
