@@ -315,3 +315,50 @@ def test_uniform_sky_counts_directions_above_both_planes():
         pts, wts = G.polygon_quadrature(np.array([[x, y], [x + 1, y], [x + 1, y + 1], [x, y + 1]], float), 1)
         alt.append(0.6 / math.pi * 0.7 * sum(w * without_face_plane(px, py) for (px, py), w in zip(pts, wts)))
     assert (np.array(alt) - exp).max() > 12 * se
+
+
+def test_point_light_below_the_face_is_not_seen():
+    # the valley's near face under two lights: one above its plane, one low
+    # beyond its outer edge -- below the face's plane everywhere, but above the
+    # shading plane near the valley, with nothing in between (open below): by
+    # the definition that light adds nothing. Exact screen points; expected
+    # values restated in numpy (casts, vertex normals, blend, both plane tests,
+    # the far face as the only occluder)
+    import dataclasses
+    LP = np.array([[0.0, 1.0, 6.0], [0.3, 2.5, 0.5]])
+    I0 = np.array([[30.0, 20.0, 10.0], [3.0, 2.5, 2.0]])
+    sc = dataclasses.replace(_valley(1), env=None, light_pos=LP.astype(np.float32),
+                             light_intensity=I0.astype(np.float32))
+    LP = sc.light_pos.astype(np.float64)    # the values the scene holds (float32)
+    V = sc.vertices.astype(np.float64)
+    N = _vertex_normals(V, sc.faces)
+    ng = np.cross(V[2] - V[0], V[1] - V[0])
+    ng /= np.linalg.norm(ng)
+    v = sc.views[0]
+    osc = O.OracleScene(sc)
+    prm = O.params(1, 2)
+    img = G.project(v, V[[0, 2, 1]])
+    lo, hi = img.min(0), img.max(0)
+    rng = np.random.default_rng(3)
+    n_pts = n_below = n_lit = 0
+    for px, py in rng.uniform(lo, hi, size=(600, 2)):
+        o, d = G.pixel_ray(v, px, py)
+        f, t, b1, b2 = _cast(V, sc.faces, o, d)
+        if f != 0:
+            continue
+        n_pts += 1
+        p = o + t * d
+        s = (1 - b1 - b2) * N[0] + b2 * N[1] + b1 * N[2]
+        ns = s / np.linalg.norm(s)
+        exp = np.zeros(3)
+        for L, I in zip(LP, I0):
+            wl = L - p
+            dist = np.linalg.norm(wl)
+            wl /= dist
+            n_below += ns @ wl > 0 and not ng @ wl > 0
+            if ng @ wl > 0 and ns @ wl > 0 and not _hits_triangle(p, wl[None], V[0], V[1], V[3])[0]:
+                exp += sc.face_params[0, :3].astype(np.float64) / math.pi * I * (ns @ wl) / dist ** 2
+                n_lit += 1
+        got = O.trace_screen(osc, prm, 0, px, py)
+        np.testing.assert_allclose(got, exp, rtol=1e-9, atol=1e-12)
+    assert n_pts > 200 and n_below > 20 and n_lit > 100
