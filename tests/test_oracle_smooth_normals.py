@@ -362,3 +362,98 @@ def test_point_light_below_the_face_is_not_seen():
         got = O.trace_screen(osc, prm, 0, px, py)
         np.testing.assert_allclose(got, exp, rtol=1e-9, atol=1e-12)
     assert n_pts > 200 and n_below > 20 and n_lit > 100
+
+
+def _fnv(words):
+    h = 0xcbf29ce484222325
+    for x in words:
+        h = ((h ^ (int(x) & 0xffffffff)) * 0x100000001b3) & 0xffffffffffffffff
+    return h
+
+
+def test_path_decisions_over_the_valley_match_a_restatement():
+    # two-vertex paths over the valley under a point light, one sample per
+    # pixel: every decision the path signature hashes -- the faces hit, the
+    # shadow rays traced and their visibility, the BSDF lobe and whether its
+    # direction is valid (above the shading plane by the sampler, above the
+    # face's plane by the rule) -- restated in numpy from the counters
+    import dataclasses
+    seed = 77
+    LP = np.array([[0.3, 2.5, 0.5]])
+    sc = dataclasses.replace(_valley(1), env=None, light_pos=LP.astype(np.float32),
+                             light_intensity=np.full((1, 3), 3.0, np.float32))
+    sc.views = [dataclasses.replace(sc.views[0], width=32, height=32)]
+    sc.max_bounces = 2
+    L = sc.light_pos.astype(np.float64)[0]
+    V = sc.vertices.astype(np.float64)
+    F = sc.faces
+    N = _vertex_normals(V, F)
+    v = sc.views[0]
+    key = np.array([seed & 0xffffffff, seed >> 32], np.uint32)
+    unif = lambda w: (int(w) >> 8) * 2.0 ** -24
+    P5 = sc.face_params.astype(np.float64)
+
+    def normals(f, p, wo):
+        a, b, c = V[F[f]]
+        m = np.cross(b - a, c - a)
+        ng = m / np.linalg.norm(m)
+        q = p - a
+        b1 = np.cross(q, c - a) @ m / (m @ m)
+        b2 = np.cross(b - a, q) @ m / (m @ m)
+        s = (1 - b1 - b2) * N[F[f, 0]] + b1 * N[F[f, 1]] + b2 * N[F[f, 2]]
+        ns = s / np.linalg.norm(s)
+        sg = -1.0 if ng @ wo < 0 else 1.0
+        return ng * sg, ns * sg
+
+    def nee(f, p, ng, ns):
+        wl = L - p
+        dist = np.linalg.norm(wl)
+        wl /= dist
+        if not (ng @ wl > 0 and ns @ wl > 0 and dist > 2e-5):
+            return False, 0
+        seen = _cast(V, F, p, wl, exclude=f, tmax=dist - 1e-5)[0] < 0
+        return True, (1 if seen else 0)
+
+    pix = O.all_pixels(sc)
+    expect = []
+    n_invalid = n_bounce = 0
+    for _, x, y in pix:
+        c0 = v.pixel_offset + y * v.width + x
+        u = O.philox([c0, 0, 0, 0], key)
+        o, d = G.pixel_ray(v, x + unif(u[0]), y + unif(u[1]))
+        words = []
+        f, t, _, _ = _cast(V, F, o, d)
+        if f < 0:
+            expect.append(_fnv([0xffffffff]))
+            continue
+        words.append(f)
+        p = o + t * d
+        ng, ns = normals(f, p, -d)
+        traced, vis = nee(f, p, ng, ns)
+        ub = O.philox([c0, 0, (0 << 4) | 2, 0], key)
+        m = P5[f]
+        ps = min(max(m[3] / (m[3] + m[:3].mean()), 0.05), 0.95)
+        lobe = 1 if unif(ub[0]) < ps else 0
+        wi, pdf = O.brdf_sample(0, m, ns, -d, unif(ub[0]), unif(ub[1]), unif(ub[2]))
+        valid = pdf > 0 and ng @ wi > 0
+        n_invalid += pdf > 0 and not valid
+        words.append(lobe | (2 if valid else 0))
+        if traced:
+            words.append(vis)
+        if valid:
+            n_bounce += 1
+            f2, t2, _, _ = _cast(V, F, p, wi, exclude=f)
+            if f2 < 0:
+                words.append(0xffffffff)
+            else:
+                words.append(f2)
+                p2 = p + t2 * wi
+                ng2, ns2 = normals(f2, p2, -wi)
+                traced2, vis2 = nee(f2, p2, ng2, ns2)
+                if traced2:
+                    words.append(vis2)
+        expect.append(_fnv(words))
+    got = O.render_signatures(O.OracleScene(sc), O.params(2, seed), pix).astype(np.uint64)
+    same = got == np.array(expect, np.uint64)
+    assert same.mean() >= 0.998, (same.mean(), np.nonzero(~same)[0][:5])
+    assert n_invalid > 10 and n_bounce > 300
