@@ -111,7 +111,9 @@ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
 inline double unif(uint32_t x) { return (double)(x >> 8) * (1.0 / 16777216.0); }
 
 // Path signature: FNV-1a style 64-bit hash of a path's discrete decisions, in
-// this order at every vertex: the face hit (0xffffffff for a miss), the
+// this order at every vertex: the face hit (0xffffffff for a miss), then for a
+// miss under an environment the texel its direction reads (nearest lookup),
+// for a hit with mesh colors at r > 0 the texel the hit point picks, the
 // environment texel drawn for NEE, the BSDF lobe code (1 = specular, + 2 when
 // the sampled direction is valid) where a direction is drawn, and the
 // visibility bits of the vertex's shadow rays (bit j = point light j seen, bit
@@ -1003,6 +1005,7 @@ void trace_path(const Scene& s, const Rng& rng, int B, const Lights& lt, const V
       if (s.ew > 0) {
         double st;
         int tx = env_texel(s, d, st);
+        mix((uint32_t)tx);   // the nearest-texel lookup is a decision too
         double w = 1.0;
         if (b > b0) {
           double pe = env_pdf(s, tx, st);
@@ -1019,6 +1022,7 @@ void trace_path(const Scene& s, const Rng& rng, int B, const Lights& lt, const V
     V3<T> v1 = A::vertex(s, vars, fi[1]);
     V3<T> v2 = A::vertex(s, vars, fi[2]);
     long long tex = texel(s, h.tri, h.b1, h.b2);
+    if (s.res > 0) mix((uint32_t)tex);   // so is the mesh-colors texel of the hit
     MatT<T> m = A::params(s, vars, (int)tex);
     Mat mv = mat_val(s, (int)tex);
     V3<T> mvec = cross(v1 - v0, v2 - v0);

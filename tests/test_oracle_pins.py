@@ -724,6 +724,68 @@ def test_path_signature_closed_cases():
         assert int(sig[1]) == (spp * _fnv(basis, 0xffffffff)) & 0xffffffffffffffff
 
 
+def _camera_dirs(v, x, y, seed):
+    # per sample: the jittered pinhole direction through pixel (x, y), jitter from the
+    # camera counter (pixel_offset + y W + x, sample, 0, 0) of Philox keyed by the seed
+    e, t, up = (np.array(a, np.float64) for a in (v.eye, v.target, v.up))
+    fwd = (t - e) / np.linalg.norm(t - e)
+    right = np.cross(fwd, up)
+    right /= np.linalg.norm(right)
+    upv = np.cross(right, fwd)
+    th = np.tan(np.radians(v.fov_y_deg) / 2)
+    out = []
+    for smp in range(v.spp):
+        u = O.philox([v.pixel_offset + y * v.width + x, smp, 0, 0], [seed & 0xffffffff, seed >> 32])
+        px, py = x + (int(u[0]) >> 8) / 2.0 ** 24, y + (int(u[1]) >> 8) / 2.0 ** 24
+        sx, sy = 2 * px / v.width - 1, 1 - 2 * py / v.height
+        d = fwd + right * sx * th * v.width / v.height + upv * sy * th
+        out.append(d / np.linalg.norm(d))
+    return out
+
+
+def test_path_signature_holds_the_texel_a_miss_reads_and_the_texel_a_hit_picks():
+    # a miss under an environment hashes the equirectangular texel its direction
+    # reads (theta from +y, phi = atan2(x, -z) + pi); a hit with mesh colors at
+    # r = 2 hashes its texel k = (t (r+1)(r+2) + i (2r - i + 3)) / 2 + j,
+    # (i, j) = floor(r (alpha, beta)); both restated here from the camera model
+    basis, seed, spp, M = 0xcbf29ce484222325, 3, 6, 0xffffffffffffffff
+    sc = S.single_triangle(16, 16, light_dist=2.5)
+    sc.light_pos = np.array([[0.0, 0.0, 2.5]], np.float32)
+    sc.views[0].spp = spp
+    rng = np.random.default_rng(2)
+    W, H = 16, 8
+    sc.env = rng.lognormal(0, 1, (H, W, 3)).astype(np.float32)
+    v = sc.views[0]
+    want = 0
+    for d in _camera_dirs(v, 0, 0, seed):
+        phi = np.arctan2(d[0], -d[2]) + np.pi
+        col = min(int(phi / (2 * np.pi) * W), W - 1)
+        row = min(int(np.arccos(np.clip(d[1], -1, 1)) / np.pi * H), H - 1)
+        want += _fnv(_fnv(basis, 0xffffffff), row * W + col)
+    sig = O.render_signatures(O.OracleScene(sc), O.params(1, seed), np.array([[0, 0, 0]], np.int32))
+    assert int(sig[0]) == want & M
+
+    # mesh colors at r = 2 under the point light alone (no environment, so no NEE texel draw)
+    sc.env = None
+    r = 2
+    n_tex = (r + 1) * (r + 2) // 2
+    sc.color_res = r
+    sc.face_params = np.repeat(sc.face_params, n_tex, axis=0)
+    V = sc.vertices.astype(np.float64)
+    e1, e2 = V[1] - V[0], V[2] - V[0]
+    want, ks = 0, set()
+    for d in _camera_dirs(v, 8, 8, seed):
+        p = np.array(v.eye) + d * (-v.eye[2] / d[2])          # the triangle lies in z = 0
+        a, b = np.linalg.solve(np.c_[e1[:2], e2[:2]], (p - V[0])[:2])
+        i = min(max(int(np.floor(r * a)), 0), r)
+        j = min(max(int(np.floor(r * b)), 0), r - i)
+        k = (0 * (r + 1) * (r + 2) + i * (2 * r - i + 3)) // 2 + j
+        ks.add(k)
+        want += _fnv(_fnv(_fnv(basis, 0), k), 1)
+    sig = O.render_signatures(O.OracleScene(sc), O.params(1, seed), np.array([[0, 8, 8]], np.int32))
+    assert int(sig[0]) == want & M
+
+
 def test_path_signature_depends_on_decisions_only():
     # with ks = 0 the lobe probability is the same for any albedo, so changing kd
     # changes the pixel values but no decision: equal signatures; moving the
