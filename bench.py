@@ -133,6 +133,103 @@ def run_reference(args):
         "e2e": {"value": round(v, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
+def secondary_on_torus_knot(st, S, chunk, persist, n_views=8, steps=4):
+    """The step with and without the secondary-visibility edge term on the concave torus knot (8 of its
+    256x256 views, 4 spp, 4 bounces, silhouette primary term on), where path vertices see silhouettes."""
+    import torch
+    sc = S.env().subset_views(range(n_views))
+    B, seed = sc.max_bounces, 515
+    scn = st.Scene.from_scene(sc)
+    img = torch.zeros((sc.n_pixels, 3), dtype=torch.float32, device="cuda")
+    g = torch.full((sc.n_pixels, 3), 1e-3, dtype=torch.float32, device="cuda")
+    fo = st.make_opts(mode="batched", use_graph=1, chunk_paths=chunk, persist_blocks=persist)
+    out = {"workload": "torus knot 50000 faces, env 256x128, %d views 256x256, 4 spp, 4 bounces" % n_views}
+    for name, term in (("primary", st.EDGE_TERM_PRIMARY), ("primary+secondary",
+                                                            st.EDGE_TERM_PRIMARY | st.EDGE_TERM_SECONDARY)):
+        bo = st.make_opts(mode="batched", use_graph=1, edge_term=term, edge_mode=0, chunk_paths=chunk,
+                          persist_blocks=persist, sec_pick="tree")
+
+        def one():
+            scn.render(sc.views, B, seed, fo, out=img)
+            scn.backward(sc.views, B, seed, g, bo)
+
+        one()
+        s0 = scn.stats()
+        scn.render(sc.views, B, seed, fo, out=img)
+        s1 = scn.stats()
+        segs = s0["extension_rays"] + s0["shadow_rays"] + s1["extension_rays"] + s1["shadow_rays"]
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            one()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[name] = {"ms_per_step": round(ms, 3), "segments_per_step": segs,
+                     "value": round(segs / (ms / 1000.0) / 1e6, 3), "secondary_samples_per_step": s0["secondary_samples"]}
+    scn.close()
+    assert out["primary+secondary"]["secondary_samples_per_step"] > 0, "the secondary term drew no sample"
+    out["cost"] = round(out["primary+secondary"]["ms_per_step"] / out["primary"]["ms_per_step"] - 1.0, 4)
+    return out
+
+
+def oracle_parity(st, scene, sc, target, B, seed, fopts, bopts, edge_on, n_img=1024, n_grad=256):
+    """Checks the timed launch configuration against the FP64 oracle on seeded pixel samples: image values
+    and path signatures; the interior gradient of the step's L2 loss restricted to a pixel sample (relative
+    L2 over vertices and texel parameters: the metric's gradient error); the silhouette edge term on the same
+    sample against the oracle's estimator with identical samples."""
+    import torch
+    import oracle as O
+    t0 = time.perf_counter()
+    rng = np.random.default_rng(31)
+
+    def sample(n):
+        vi = rng.integers(len(sc.views), size=n)
+        pix = np.array([(v, rng.integers(sc.views[v].width), rng.integers(sc.views[v].height)) for v in vi], np.int32)
+        return np.unique(pix, axis=0)
+
+    N = sc.n_pixels
+    sig = torch.zeros(N, dtype=torch.int64, device="cuda")
+    img = scene.render(sc.views, B, seed, fopts, signatures=sig)
+    sig = sig.cpu().numpy().view(np.uint64)
+    osc = O.OracleScene(sc)
+    prm = O.params(B, seed, edge_mode=0)
+    pix = sample(n_img)
+    rows = O.pixel_index(sc, pix)
+    ref, _ = O.render_pixels(osc, prm, pix)
+    rsig = O.render_signatures(osc, prm, pix)
+    g = img.cpu().numpy()[rows].astype(np.float64)
+    err = np.abs(g - ref)
+    ok = err <= 1e-4 * np.abs(ref) + 1e-7
+    same = sig[rows] == rsig
+    out = {"pixels": int(len(pix)), "channels_within_1e-4": round(float(ok.mean()), 5),
+           "mean_rel_err": float(err.mean() / np.abs(ref).mean()), "signatures_equal": round(float(same.mean()), 5),
+           "out_of_tolerance_with_equal_signatures": int((~np.all(ok, 1) & same).sum())}
+    # the step's loss gradient dL/dI = 2 (I - target) / (3N), kept on a pixel sample
+    gp = sample(n_grad)
+    grows = O.pixel_index(sc, gp)
+    dLdI = ((img - target) * (2.0 / (3 * N))).cpu().numpy()
+    w = np.zeros_like(dLdI)
+    w[grows] = dLdI[grows]
+    wt = torch.from_numpy(w).cuda()
+    o_int = st.RenderOpts.from_buffer_copy(bopts)
+    o_int.edge_term = 0
+    dVi, dFi = scene.backward(sc.views, B, seed, wt, o_int)
+    rv, rf, _ = O.grad_pixels(osc, prm, gp, w[grows].astype(np.float64))
+    got = np.concatenate([dVi.cpu().numpy().ravel(), dFi.cpu().numpy().ravel()]).astype(np.float64)
+    exp = np.concatenate([rv.ravel(), rf.ravel()])
+    out["grad_pixels"] = int(len(gp))
+    out["grad_rel_err"] = float(np.linalg.norm(got - exp) / np.linalg.norm(exp))
+    if edge_on:
+        dVe, _ = scene.backward(sc.views, B, seed, wt, bopts)
+        ev, _ = O.edge_grad(osc, prm, w.astype(np.float64))
+        ge = (dVe - dVi).cpu().numpy().astype(np.float64)
+        out["edge_rel_err"] = float(np.linalg.norm(ge - ev) / max(np.linalg.norm(ev), 1e-300))
+    out["seconds"] = round(time.perf_counter() - t0, 1)
+    return out
+
+
 # ---------------------------------------------------------------------------- clocks
 class ClockSampler:
     def __init__(self, index):
@@ -365,6 +462,10 @@ def run_ours(args):
     with_sec = {"value": round(seg_sec * sec_steps * world / (ms_sec / 1000.0) / 1e6, 3),
                 "ms_per_step": round(ms_sec / sec_steps, 3), "segments_per_step": seg_sec,
                 "secondary_samples_per_step": ss["secondary_samples"], "pick": "edge hierarchy"}
+    if ss["secondary_samples"] == 0:
+        with_sec["note"] = ("no vertex of this mesh sees a silhouette edge: the row times the pick pass and "
+                            "the empty side-path passes only; with_secondary_edges_torus_knot is where it fires")
+    sec_knot = None if adam else secondary_on_torus_knot(st, S, chunk, persist)
 
     # the same step with the optional terms and shading of the widened scope:
     # point-light shadow edges (scenes with point lights) and interpolated
@@ -402,44 +503,87 @@ def run_ours(args):
                                           "ms_per_step": round(ms_w / n_w, 3), "segments_per_step": seg_w}
         sm_scene.close()
 
-    # roofline of the dominant kernel (closest-hit traversal): algorithmic bytes
-    # from the instrumented traversal, time from CUDA events around each launch
+    # rooflines of the two traversal kernels: algorithmic bytes from the instrumented
+    # traversal (same rays), time from CUDA events around each launch
     ci = st.make_opts(mode="batched", use_graph=0, count_visits=1, chunk_paths=chunk)
     cib = st.make_opts(mode="batched", use_graph=0, count_visits=1, edge_term=edge_on, edge_mode=0, chunk_paths=chunk)
     a, b = counts(ci, cib)
     visits = a["node_visits"] + b["node_visits"]
     tests = a["tri_tests"] + b["tri_tests"]
     rays = a["extension_rays"] + b["extension_rays"]
+    sh_visits = a["shadow_node_visits"] + b["shadow_node_visits"]
+    sh_tests = a["shadow_tri_tests"] + b["shadow_tri_tests"]
+    sh_rays = a["shadow_rays"] + b["shadow_rays"]
     ti = st.make_opts(mode="batched", use_graph=0, time_kernels=1, chunk_paths=chunk)
     tib = st.make_opts(mode="batched", use_graph=0, time_kernels=1, edge_term=edge_on, edge_mode=0, chunk_paths=chunk)
-    ext_ms, ext_n = 0.0, 0
-    for _ in range(3):
+    ext_ms, ext_n, sh_ms, sh_n, reps = 0.0, 0, 0.0, 0, 3
+    for _ in range(reps):
         flush.fill_(1.0)
         a, b = counts(ti, tib)
         ext_ms += a["extend_ms"] + b["extend_ms"]
         ext_n += a["extend_launches"] + b["extend_launches"]
-    # per query: 4-wide node fetch 112 B, triangle record 48 B, ray in (o, d, origin, queue) 40 B, hit out 8 B
-    alg_bytes = visits * 112 + tests * 48 + rays * 48
-    achieved = alg_bytes * 3 / (ext_ms / 1000.0) / 1e9
+        sh_ms += a["shadow_ms"] + b["shadow_ms"]
+        sh_n += a["shadow_launches"] + b["shadow_launches"]
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
-    peak = peaks.get("hbm_gbs", 6800.0)
-    tr = profiled_traffic()
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
     l2 = l2_peak_gbs(st)
-    roofline = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4),
-                "traffic": None if tr is None else round(tr * rays / max(1, ext_n // 3), 1),
-                "kernel": "k_extend (closest-hit BVH traversal)",
-                "launch_ms_avg": round(ext_ms / max(1, ext_n), 4),
-                "alg_bytes_per_ray": round(alg_bytes / max(rays, 1), 1),
-                "node_visits_per_ray": round(visits / max(rays, 1), 2),
-                "tri_tests_per_ray": round(tests / max(rays, 1), 2),
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback",
-                "l2": {"peak": round(l2, 1), "frac": round(achieved / l2, 4), "unit": "GB/s",
-                       "peak_source": "st_measure_l2_read: L2-resident read, best of 16/32/48 MiB, measured live"}}
+    tr = profiled_traffic()
+
+    def record(name, v, t, q, ms, n):
+        # per query: each 4-wide node fetch reads all four child boxes and links (112 B), each
+        # triangle test one leaf record (48 B), plus the ray in and the hit out (48 B)
+        alg = v * 112 + t * 48 + q * 48
+        achieved = alg * reps / (ms / 1000.0) / 1e9
+        per_launch_ms = ms / max(1, n)
+        rec = {"bound": "l2", "achieved": round(achieved, 2), "peak": round(l2, 1), "unit": "GB/s",
+               "frac": round(achieved / l2, 4), "traffic": None, "kernel": name,
+               "peak_source": "st_measure_l2_read: L2-resident read bandwidth, best of 16/32/48 MiB, measured live",
+               "launch_ms_avg": round(per_launch_ms, 4), "launches_per_step": n // reps,
+               "queries_per_step": q, "alg_bytes_per_query": round(alg / max(q, 1), 1),
+               "node_fetches_per_query": round(v / max(q, 1), 2), "tri_tests_per_query": round(t / max(q, 1), 2),
+               # the same queries counted with 64 B per node visit (a binary node), for comparison
+               "alg_bytes_per_query_64B_nodes": round((v * 64 + t * 48 + q * 48) / max(q, 1), 1),
+               "hbm": {"peak": hbm_peak, "unit": "GB/s",
+                       "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback"}}
+        return rec
+
+    roofline = record("k_extend (closest-hit BVH traversal)", visits, tests, rays, ext_ms, ext_n)
+    roofline_shadow = record("k_shadow (any-hit BVH traversal)", sh_visits, sh_tests, sh_rays, sh_ms, sh_n)
+    if tr is not None:
+        # DRAM bytes per query from the committed ncu capture (cold caches) times this step's queries
+        per_launch = tr * rays / max(1, ext_n // reps)
+        roofline["traffic"] = round(per_launch, 1)
+        roofline["hbm"]["dram_frac"] = round(per_launch / (roofline["launch_ms_avg"] / 1000.0) / 1e9 / hbm_peak, 4)
+
+    # where the per-view step's time goes: GPU time between its host synchronisations
+    # (queue counts read back after each stage) against the step's wall time
+    tp = st.make_opts(mode="per_view", use_graph=0, time_kernels=1)
+    tpb = st.make_opts(mode="per_view", use_graph=0, time_kernels=1, edge_term=edge_on, edge_mode=0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.fill_(1.0)
+    e0.record(stream)
+    a, b = counts(tp, tpb)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    pv_wall = e0.elapsed_time(e1)
+    pv_busy = a["busy_ms"] + b["busy_ms"]
+    per_view_split = {"wall_ms": round(pv_wall, 3), "gpu_busy_ms": round(pv_busy, 3),
+                      "host_sync_gap_ms": round(pv_wall - pv_busy, 3),
+                      "host_syncs": a["host_syncs"] + b["host_syncs"],
+                      "extend_ms": round(a["extend_ms"] + b["extend_ms"], 3),
+                      "shadow_ms": round(a["shadow_ms"] + b["shadow_ms"], 3)}
+    flush.fill_(1.0)
+    e0.record(stream)
+    a, b = counts(ti, tib)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    batched_split = {"wall_ms": round(e0.elapsed_time(e1), 3), "gpu_busy_ms": round(a["busy_ms"] + b["busy_ms"], 3),
+                     "extend_ms": round(a["extend_ms"] + b["extend_ms"], 3),
+                     "shadow_ms": round(a["shadow_ms"] + b["shadow_ms"], 3), "graph": False}
 
     # end to end through the C ABI with host buffers: H2D of the mesh state and
     # D2H of the image and both gradients every step
@@ -475,8 +619,13 @@ def run_ours(args):
     h2d = hV.numel() * 4 + hP.numel() * 4
     d2h = (0 if adam else oI.numel() * 4) + oV.numel() * 4 + oF.numel() * 4
 
-    # parity of this run's gradient against the oracle on a pixel subset
-    cpu = None
+    # CPU-baseline leg (rank 0): the oracle timed on a pixel sample, and the same oracle
+    # checking this run's launch configuration (image, signatures, gradients) on a sample
+    cpu, parity = None, None
+    if rank == 0 and not args.no_cpu:
+        import dataclasses
+        parity = oracle_parity(st, scene, dataclasses.replace(sc, views=step_views), step_target, B, seed, fb, bb,
+                               edge_on)
     if rank == 0 and world == 1 and not args.no_cpu:
         r, cores, pix, secs = oracle_sample_rate(sc, args.cpu_seconds)
         r1, _, pix1, secs1 = oracle_sample_rate(sc, max(2.0, args.cpu_seconds / 4), seed=2025, threads=1)
@@ -503,8 +652,11 @@ def run_ours(args):
                "per_view": {"value": round(value_pv, 3), "ms_per_step": round(ms_pv / pv_steps, 3),
                             "launch": "per-view, host-read queue counts, no graph"},
                "forward_only": {"value": round(value_fwd, 3), "ms_per_step": round(ms_fwd / args.steps, 3)},
-               "with_secondary_edges": with_sec, **widened,
-               "roofline": roofline, "cpu_baseline": cpu,
+               "with_secondary_edges": with_sec, "with_secondary_edges_torus_knot": sec_knot, **widened,
+               "roofline": roofline, "roofline_k_shadow": roofline_shadow,
+               "time_split": {"per_view": per_view_split, "batched_ungraphed": batched_split},
+               "grad_rel_err": None if parity is None else parity["grad_rel_err"], "parity": parity,
+               "cpu_baseline": cpu,
                "e2e": {"value": round(value_e2e, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": d2h, "ms_per_step": round(ms_e2e / args.steps, 3)},
                "gpu_launches": launches_step * args.steps, "clocks": clk.summary(),

@@ -73,10 +73,14 @@ typedef struct {
   float intensity[3];
 } st_point_light;
 
-/* Equirectangular HDR environment (Sec. 3.1): HOST pointer to float [H][W][3]
- * radiance. Row 0 is theta = 0 (the +y pole); direction for (theta, phi) is
- * (-sin theta sin phi, cos theta, sin theta cos phi), phi = 2 pi (col + 0.5)/W
- * at texel centres. Copied, and its FP64 alias table built, at scene create. */
+/* Equirectangular HDR environment (Sec. 3.1 "Input": an HDR environment map
+ * as the light): rgb = float [H][W][3] radiance in device memory of the
+ * current device or in host memory (st_scene_create tells them apart with
+ * cudaPointerGetAttributes; device memory is read back once, since the alias
+ * table is built on the host). Row 0 is theta = 0 (the +y pole); direction for
+ * (theta, phi) is (-sin theta sin phi, cos theta, sin theta cos phi),
+ * phi = 2 pi (col + 0.5)/W at texel centres. Copied, and its FP64 alias table
+ * built, at scene create; the caller keeps ownership. */
 typedef struct {
   int width, height;
   const float* rgb;
@@ -139,12 +143,15 @@ typedef struct {
   int mode;         /* ST_MODE_BATCHED or ST_MODE_PER_VIEW */
   int use_graph;    /* batched mode: capture and replay the call as a CUDA graph */
   int chunk_paths;  /* paths in flight per wavefront chunk; 0 = library default */
-  int time_kernels; /* per-view or ungraphed batched: time the closest-hit kernel (see st_stats) */
+  int time_kernels; /* per-view or ungraphed batched: time the closest-hit and any-hit kernels and the GPU-side
+                       intervals between host synchronisations (see st_stats) */
   int count_visits; /* run the instrumented traversal that counts node visits and triangle tests */
   int persist_blocks; /* batched mode: resident blocks per SM of the persistent stage kernels (0 = occupancy limit) */
   unsigned long long* path_signatures; /* forward, optional: device uint64 [N], same rows as out_image: per pixel,
                        the sum over its samples (mod 2^64) of a 64-bit FNV-1a hash of each path's discrete decisions:
-                       at every vertex the face hit (0xffffffff for a miss), the environment texel drawn for NEE,
+                       at every vertex the face hit (0xffffffff for a miss), then for a miss under an environment
+                       the texel its direction reads, for a hit with mesh colors at r > 0 the texel it picks,
+                       the environment texel drawn for NEE,
                        the BSDF lobe code (1 = specular, + 2 when the direction is valid) where one is drawn, then
                        the shadow rays' visibility bits (bit j = point light j seen, bit 8 = the environment sample
                        seen) when any was traced; basis 0xcbf29ce484222325, prime 0x100000001b3. Equal signatures
@@ -172,6 +179,13 @@ typedef struct {
   int kernel_launches;        /* kernels the last call launched (graph kernel nodes included) */
   int bvh4_nodes;             /* nodes of the 4-wide BVH the traversal walks */
   long long secondary_samples; /* accepted secondary edge samples of the last call (each traces two paths) */
+  long long shadow_node_visits; /* instrumented calls only: internal nodes fetched by any-hit (shadow) queries */
+  long long shadow_tri_tests;   /* instrumented calls only: triangle tests by any-hit queries */
+  int shadow_launches;        /* any-hit launches timed (time_kernels) */
+  double shadow_ms;           /* their summed CUDA-event time */
+  double busy_ms;             /* time_kernels: GPU time of the call between its host synchronisations (a per-view
+                                 call reads queue counts back; the rest of its wall time the GPU waits on the host) */
+  int host_syncs;             /* host synchronisations of the last call (per-view mode reads queue counts back) */
 } st_stats;
 
 /* Create a scene: copies the mesh into scene-owned device memory, builds the
@@ -262,6 +276,23 @@ st_status st_build_bvh_noalloc(const float* vertices, const int* faces, int n_ve
  * times by one kernel with cache-global 16-byte loads. Allocates and frees the
  * buffer; synchronises `stream`. Used as the L2 roofline denominator. */
 st_status st_measure_l2_read(long long bytes, int passes, void* stream, double* gbs);
+
+/* Host-side fault injection, for testing how callers handle failures; the
+ * paper has no counterpart. The nth next event (nth = 0: the next one) at
+ * `site` fails as the CUDA call would have, without making that call:
+ *  - ST_FAULT_ALLOC: a device allocation by the library (scene buffers,
+ *    wavefront buffers, per-call tables). The call returns ST_ERR_OOM.
+ *  - ST_FAULT_COPY: a copy between host and device of scene, call or
+ *    statistics data. The call returns ST_ERR_CUDA.
+ * nth < 0 disarms the site. Nothing is injected on the device. A call that
+ * fails this way leaves its scene valid: later calls succeed, and
+ * st_scene_destroy frees everything. The setting is process-wide (all
+ * threads, all scenes). The library's first fault query also reads the
+ * environment variable ST_FAULT ("alloc:N" or "copy:N"), for processes that
+ * cannot call this function. Unknown site: ST_ERR_INVALID_ARG. */
+#define ST_FAULT_ALLOC 1
+#define ST_FAULT_COPY 2
+st_status st_inject_fault(int site, int nth);
 
 /* Message for the last non-OK status on this thread. */
 const char* st_last_error(void);

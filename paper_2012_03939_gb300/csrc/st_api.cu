@@ -3,7 +3,9 @@
 // its two launch modes (batched persistent + CUDA graph, or plain per-view),
 // and statistics.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -15,6 +17,35 @@ namespace st {
 
 static thread_local std::string g_err;
 void set_error(const std::string& msg) { g_err = msg; }
+
+// Host-side fault injection (st_inject_fault): per site, the number of events
+// to let pass before one fails (-1 = disarmed). The first query reads the
+// ST_FAULT environment variable ("alloc:N" or "copy:N").
+static std::atomic<int> g_fault[3] = {{-1}, {-1}, {-1}};
+
+static void fault_from_env() {
+  const char* v = std::getenv("ST_FAULT");
+  if (!v) return;
+  std::string s(v);
+  size_t c = s.find(':');
+  std::string site = s.substr(0, c);
+  int n = c == std::string::npos ? 0 : std::atoi(s.c_str() + c + 1);
+  if (site == "alloc") g_fault[ST_FAULT_ALLOC].store(n);
+  else if (site == "copy") g_fault[ST_FAULT_COPY].store(n);
+}
+
+static void fault_init() {
+  static const bool env_read = (fault_from_env(), true);
+  (void)env_read;
+}
+
+bool fault_now(int site) {
+  fault_init();
+  int v = g_fault[site].load();
+  while (v >= 0)
+    if (g_fault[site].compare_exchange_weak(v, v - 1)) return v == 0;
+  return false;
+}
 
 namespace {
 
@@ -43,8 +74,21 @@ template <class T>
 cudaError_t dalloc(T** p, size_t n, long long* acc = nullptr) {
   *p = nullptr;
   if (n == 0) return cudaSuccess;
+  if (fault_now(ST_FAULT_ALLOC)) return cudaErrorMemoryAllocation;   // injected on the host, before CUDA
   if (acc) *acc += (long long)(n * sizeof(T));
   return cudaMalloc((void**)p, n * sizeof(T));
+}
+
+// Host<->device copies of scene, call and statistics data go through these, so
+// an injected copy fault reaches every caller's error path.
+cudaError_t copy_async(void* dst, const void* src, size_t bytes, cudaMemcpyKind kind, cudaStream_t st) {
+  if (fault_now(ST_FAULT_COPY)) return cudaErrorInvalidValue;
+  return cudaMemcpyAsync(dst, src, bytes, kind, st);
+}
+
+cudaError_t copy_sync(void* dst, const void* src, size_t bytes, cudaMemcpyKind kind) {
+  if (fault_now(ST_FAULT_COPY)) return cudaErrorInvalidValue;
+  return cudaMemcpy(dst, src, bytes, kind);
 }
 
 template <class T>
@@ -299,8 +343,14 @@ st_status ensure_tables(st_scene* s, int n_views, int n_segs, bool edges) {
     drop_graphs(s);
     dfree(s->d_views);
     dfree(s->d_segs);
-    if (dalloc(&s->d_views, need) != cudaSuccess || dalloc(&s->d_segs, need) != cudaSuccess)
+    if (dalloc(&s->d_views, need) != cudaSuccess || dalloc(&s->d_segs, need) != cudaSuccess) {
+      // leave no capacity behind a freed table: the next call allocates again
+      dfree(s->d_views);
+      dfree(s->d_segs);
+      s->view_cap = 0;
+      cudaGetLastError();
       return fail(ST_ERR_OOM, "view tables");
+    }
     s->view_cap = need;
   }
   if (edges && n_views > s->edge_cap_views) {
@@ -311,8 +361,14 @@ st_status ensure_tables(st_scene* s, int n_views, int n_segs, bool edges) {
     dfree(s->edge_ncand);
     size_t n = (size_t)n_views * std::max(s->n_edges, 1);
     if (dalloc(&s->edge_flag, n) != cudaSuccess || dalloc(&s->edge_cand, n) != cudaSuccess ||
-        dalloc(&s->edge_ncand, (size_t)n_views) != cudaSuccess)
+        dalloc(&s->edge_ncand, (size_t)n_views) != cudaSuccess) {
+      dfree(s->edge_flag);
+      dfree(s->edge_cand);
+      dfree(s->edge_ncand);
+      s->edge_cap_views = 0;
+      cudaGetLastError();
       return fail(ST_ERR_OOM, "edge tables");
+    }
     s->edge_cap_views = n_views;
   }
   return ST_OK;
@@ -334,6 +390,8 @@ st_status ensure_bins(st_scene* s, const Plan& p) {
   if (dalloc(&s->bin_start, (size_t)nP + 1) != cudaSuccess || dalloc(&s->bin_cur, (size_t)nP) != cudaSuccess ||
       dalloc(&s->bin_list, (size_t)nC) != cudaSuccess || dalloc(&s->bin_ok, (size_t)nV) != cudaSuccess ||
       dalloc(&s->bin_part, (size_t)nb) != cudaSuccess) {
+    dfree(s->bin_start); dfree(s->bin_cur); dfree(s->bin_list); dfree(s->bin_ok); dfree(s->bin_part);
+    s->bin_pix_cap = 0; s->bin_cap = 0; s->bin_views_cap = 0;
     cudaGetLastError();
     return fail(ST_ERR_OOM, "primary-visibility bins");
   }
@@ -345,7 +403,7 @@ st_status ensure_bins(st_scene* s, const Plan& p) {
 
 KCtx make_ctx(st_scene* s, const Plan& p) {
   KCtx c;
-  c.V = s->verts; c.F = s->faces; c.P = s->params; c.nodes = s->nodes4; c.tri = s->tri; c.nf = s->nf;
+  c.V = s->verts; c.F = s->faces; c.P = s->params; c.nodes = s->nodes4; c.tri = s->tri; c.nf = s->nf; c.n4 = s->n4;
   c.lights = s->lights; c.nl = s->nl; c.nlt = s->nl + p.max_vl; c.NS = c.nlt + (s->env.w > 0 ? 1 : 0);
   c.env = s->env; c.brdf = s->brdf; c.res = s->res; c.ntex = s->ntex; c.np = s->np;
   c.edge_v = s->edge_v; c.edge_f = s->edge_f; c.n_edges = s->n_edges; c.edge_mode = p.o.edge_mode;
@@ -372,15 +430,18 @@ int grid_of(const void* fn, int block, int sm) {
   return std::max(1, per) * std::max(1, sm);
 }
 
-cudaEvent_t next_event(st_scene* s, bool start) {
-  if (s->ev_used >= (int)s->ev.size()) {
+// event of timed set k (see st_scene::ev): the start of a new pair, or the end of the open one
+cudaEvent_t next_event(st_scene* s, int k, bool start) {
+  auto& ev = s->ev[k];
+  int& used = s->ev_used[k];
+  if (used >= (int)ev.size()) {
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
-    s->ev.push_back({a, b});
+    ev.push_back({a, b});
   }
-  auto& pr = s->ev[s->ev_used];
-  if (!start) s->ev_used++;
+  auto& pr = ev[used];
+  if (!start) used++;
   return start ? pr.first : pr.second;
 }
 
@@ -396,44 +457,69 @@ bool overlaps(const Plan& p, int kind, long long a, long long b) {
 st_status run_chunk(st_scene* s, const Plan& p, const KCtx& c, long long j0, int n, cudaStream_t st, bool host_sized,
                     bool timing, bool has_cam, bool has_edge) {
   int sm = s->sm_count;
-  static int g_ext = 0, g_ext_s = 0, g_shade = 0, g_shadow = 0;
-  if (!g_ext) {
-    g_ext = grid_of((const void*)k_extend<false>, EXT_BLOCK, sm);
-    g_ext_s = grid_of((const void*)k_extend<true>, EXT_BLOCK, sm);
-    g_shade = grid_of((const void*)k_shade, 256, sm);
-    g_shadow = grid_of((const void*)k_shadow, EXT_BLOCK, sm);
+  // occupancy-limited grids of the persistent stage kernels, for the scene's own device (a scene is used by one
+  // thread at a time, so these per-scene fields need no lock)
+  if (!s->g_ext) {
+    s->g_ext = grid_of((const void*)k_extend<false>, EXT_BLOCK, sm);
+    s->g_ext_s = grid_of((const void*)k_extend<true>, EXT_BLOCK, sm);
+    s->g_shade = grid_of((const void*)k_shade, 256, sm);
+    s->g_shadow = grid_of((const void*)k_shadow<false>, EXT_BLOCK, sm);
+    s->g_shadow_s = grid_of((const void*)k_shadow<true>, EXT_BLOCK, sm);
   }
+  const int g_ext = s->g_ext, g_ext_s = s->g_ext_s, g_shade = s->g_shade;
+  const int g_shadow = p.o.count_visits ? s->g_shadow_s : s->g_shadow;
   // persistent grids: occupancy limit, or fewer resident blocks per SM if asked
   auto cap = [&](int g) { return p.o.persist_blocks > 0 ? std::min(g, p.o.persist_blocks * sm) : g; };
   int* cnt = s->eng.cnt;
   int hc[CNT_SIZE];
+  // per-view calls read the queue counts back: the GPU idles from each read until the next launch. With timing on,
+  // event pairs bracket the GPU-side intervals between those reads (set 2).
+  auto read_counts = [&]() -> st_status {
+    if (timing) ST_CUDA(cudaEventRecord(next_event(s, 2, false), st));
+    ST_CUDA(copy_async(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, st));
+    ST_CUDA(cudaStreamSynchronize(st));
+    s->host_syncs++;
+    if (timing) ST_CUDA(cudaEventRecord(next_event(s, 2, true), st));
+    return ST_OK;
+  };
+  auto shadow = [&](const KCtx& k, int b, int g) -> st_status {
+    if (timing) ST_CUDA(cudaEventRecord(next_event(s, 1, true), st));
+    if (p.o.count_visits) k_shadow<true><<<g, EXT_BLOCK, 0, st>>>(k, b);
+    else k_shadow<false><<<g, EXT_BLOCK, 0, st>>>(k, b);
+    if (timing) ST_CUDA(cudaEventRecord(next_event(s, 1, false), st));
+    s->launches++;
+    return ST_OK;
+  };
   // extension / shading / shadow stages for `nb` bounces of the paths queued in q0
   auto bounces = [&](const KCtx& k, int nb) -> st_status {
     for (int b = 0; b < nb; ++b) {
       int ge = cap(p.o.count_visits ? g_ext_s : g_ext), gs = cap(g_shade), gw = cap(g_shadow);
       if (host_sized) {
-        ST_CUDA(cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, st));
-        ST_CUDA(cudaStreamSynchronize(st));
+        st_status r = read_counts();
+        if (r != ST_OK) return r;
         int q = hc[CNT_EXT + b];
         if (q == 0) break;
         ge = (q + EXT_BLOCK - 1) / EXT_BLOCK;
         gs = (q + 255) / 256;
       }
-      if (timing) ST_CUDA(cudaEventRecord(next_event(s, true), st));
+      if (timing) ST_CUDA(cudaEventRecord(next_event(s, 0, true), st));
       if (p.o.count_visits) k_extend<true><<<ge, EXT_BLOCK, 0, st>>>(k, b);
       else k_extend<false><<<ge, EXT_BLOCK, 0, st>>>(k, b);
-      if (timing) ST_CUDA(cudaEventRecord(next_event(s, false), st));
+      if (timing) ST_CUDA(cudaEventRecord(next_event(s, 0, false), st));
       k_shade<<<gs, 256, 0, st>>>(k, b);
       s->launches += 2;
       if (host_sized) {
-        ST_CUDA(cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, st));
-        ST_CUDA(cudaStreamSynchronize(st));
+        st_status r = read_counts();
+        if (r != ST_OK) return r;
         int q = hc[CNT_SH + b];
         gw = (q + EXT_BLOCK - 1) / EXT_BLOCK;
-        if (q > 0) { k_shadow<<<gw, EXT_BLOCK, 0, st>>>(k, b); s->launches++; }
+        if (q > 0) {
+          r = shadow(k, b, gw);
+          if (r != ST_OK) return r;
+        }
       } else if (k.NS > 0) {
-        k_shadow<<<gw, EXT_BLOCK, 0, st>>>(k, b);
-        s->launches++;
+        st_status r = shadow(k, b, gw);
+        if (r != ST_OK) return r;
       }
     }
     return ST_OK;
@@ -461,8 +547,8 @@ st_status run_chunk(st_scene* s, const Plan& p, const KCtx& c, long long j0, int
       s->launches++;
       long long jobs = (long long)p.B * n;
       if (host_sized) {
-        ST_CUDA(cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, st));
-        ST_CUDA(cudaStreamSynchronize(st));
+        r = read_counts();
+        if (r != ST_OK) return r;
         jobs = hc[CNT_SEC];
       }
       int Q = s->eng.Q;
@@ -491,8 +577,19 @@ st_status run_chunk(st_scene* s, const Plan& p, const KCtx& c, long long j0, int
 }
 
 
+st_status enqueue_body(st_scene* s, const Plan& p, const KCtx& c, int Q, cudaStream_t st, bool host_sized,
+                       bool timing);
+
 st_status enqueue_call(st_scene* s, const Plan& p, int Q, cudaStream_t st, bool host_sized, bool timing) {
   KCtx c = make_ctx(s, p);
+  if (timing) ST_CUDA(cudaEventRecord(next_event(s, 2, true), st));
+  st_status body = enqueue_body(s, p, c, Q, st, host_sized, timing);
+  if (timing) ST_CUDA(cudaEventRecord(next_event(s, 2, false), st));
+  return body;
+}
+
+st_status enqueue_body(st_scene* s, const Plan& p, const KCtx& c, int Q, cudaStream_t st, bool host_sized,
+                       bool timing) {
   ST_CUDA(cudaMemsetAsync(s->eng.stat, 0, sizeof(unsigned long long) * STAT_SIZE, st));
   if (p.kind == 0) {
     k_zero_acc<<<(unsigned)((p.pixels + 255) / 256), 256, 0, st>>>(c);
@@ -680,6 +777,7 @@ st_status run_call(st_scene* s, Plan& p, const CallArgs& args, cudaStream_t st) 
     size_t n = p.pairs.size() * (size_t)std::max(s->n_edges, 1);
     if (dalloc(&s->sh_flag, n) != cudaSuccess || dalloc(&s->sh_cand, n) != cudaSuccess ||
         dalloc(&s->sh_ncand, p.pairs.size()) != cudaSuccess || dalloc(&s->d_pairs, p.pairs.size()) != cudaSuccess) {
+      dfree(s->sh_flag); dfree(s->sh_cand); dfree(s->sh_ncand); dfree(s->d_pairs);
       cudaGetLastError();
       s->sh_cap_pairs = 0;
       return fail(ST_ERR_OOM, "shadow-edge tables");
@@ -696,6 +794,8 @@ st_status run_call(st_scene* s, Plan& p, const CallArgs& args, cudaStream_t st) 
     dfree(s->acc);
     dfree(s->sacc);
     if (dalloc(&s->acc, 6 * (size_t)p.pixels) != cudaSuccess || dalloc(&s->sacc, (size_t)p.pixels) != cudaSuccess) {
+      dfree(s->acc);
+      dfree(s->sacc);
       cudaGetLastError();
       s->acc_cap = 0;
       return fail(ST_ERR_OOM, "forward accumulation buffer");
@@ -714,13 +814,14 @@ st_status run_call(st_scene* s, Plan& p, const CallArgs& args, cudaStream_t st) 
   int NS = s->nl + p.max_vl + (s->env.w > 0 ? 1 : 0);
   r = ensure_engine(s, Q, p.B, NS, p.kind == 1, p.sec, p.shadow);
   if (r != ST_OK) return r;
-  ST_CUDA(cudaMemcpyAsync(s->d_views, p.views.data(), sizeof(DevView) * p.views.size(), cudaMemcpyHostToDevice, st));
-  ST_CUDA(cudaMemcpyAsync(s->d_segs, p.segs.data(), sizeof(Seg) * p.segs.size(), cudaMemcpyHostToDevice, st));
+  ST_CUDA(copy_async(s->d_views, p.views.data(), sizeof(DevView) * p.views.size(), cudaMemcpyHostToDevice, st));
+  ST_CUDA(copy_async(s->d_segs, p.segs.data(), sizeof(Seg) * p.segs.size(), cudaMemcpyHostToDevice, st));
   if (p.shadow && !p.pairs.empty())
-    ST_CUDA(cudaMemcpyAsync(s->d_pairs, p.pairs.data(), sizeof(int2) * p.pairs.size(), cudaMemcpyHostToDevice, st));
-  ST_CUDA(cudaMemcpyAsync(s->d_args, &args, sizeof(CallArgs), cudaMemcpyHostToDevice, st));
+    ST_CUDA(copy_async(s->d_pairs, p.pairs.data(), sizeof(int2) * p.pairs.size(), cudaMemcpyHostToDevice, st));
+  ST_CUDA(copy_async(s->d_args, &args, sizeof(CallArgs), cudaMemcpyHostToDevice, st));
   bool timing = p.o.time_kernels != 0;
-  s->ev_used = 0;
+  for (int k = 0; k < 3; ++k) s->ev_used[k] = 0;
+  s->host_syncs = 0;
   s->launches = 0;
   bool graph = p.o.mode == ST_MODE_BATCHED && p.o.use_graph && !timing;
   if (!graph) return enqueue_call(s, p, Q, st, p.o.mode == ST_MODE_PER_VIEW, timing);
@@ -779,7 +880,8 @@ void destroy(st_scene* s) {
   dfree(s->et_lo); dfree(s->et_hi); dfree(s->et_cn);
   if (s->bin_total_host) cudaFreeHost(s->bin_total_host);
   dfree(s->d_args); dfree(s->d_err);
-  for (auto& e : s->ev) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+  for (auto& set : s->ev)
+    for (auto& e : set) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
   if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
   delete s;
 }
@@ -803,6 +905,13 @@ using namespace st;
 extern "C" {
 
 const char* st_last_error(void) { return g_err.c_str(); }
+
+st_status st_inject_fault(int site, int nth) {
+  if (site != ST_FAULT_ALLOC && site != ST_FAULT_COPY) return fail(ST_ERR_INVALID_ARG, "unknown fault site");
+  fault_init();
+  g_fault[site].store(nth < 0 ? -1 : nth);
+  return ST_OK;
+}
 
 st_status st_scene_create(const st_scene_desc* d, void* stream, st_scene** out) {
   if (!out) return fail(ST_ERR_INVALID_ARG, "out is NULL");
@@ -842,8 +951,8 @@ st_status st_scene_create(const st_scene_desc* d, void* stream, st_scene** out) 
   // host copy of the faces: validation and edge list
   std::vector<int> hf(3 * (size_t)s->nf);
   std::vector<float> hv(3 * (size_t)s->nv);
-  cudaError_t e = cudaMemcpyAsync(hf.data(), d->faces, hf.size() * sizeof(int), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(hv.data(), d->vertices, hv.size() * sizeof(float), cudaMemcpyDeviceToHost, st);
+  cudaError_t e = copy_async(hf.data(), d->faces, hf.size() * sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = copy_async(hv.data(), d->vertices, hv.size() * sizeof(float), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) { destroy(s); return cuda_fail(e, "reading the mesh"); }
   for (int v : hf)
@@ -861,7 +970,20 @@ st_status st_scene_create(const st_scene_desc* d, void* stream, st_scene** out) 
   std::vector<float4> etex;
   std::vector<float2> etab;
   if (d->env) {
-    if (!build_alias(d->env->rgb, d->env->width, d->env->height, etex, etab)) {
+    // the map may be host or device memory; device memory is read back once (the alias table is built on the host)
+    const float* rgb = d->env->rgb;
+    std::vector<float> hrgb;
+    cudaPointerAttributes pa{};
+    cudaError_t pe = cudaPointerGetAttributes(&pa, rgb);
+    if (pe != cudaSuccess) cudaGetLastError();
+    if (pe == cudaSuccess && pa.type == cudaMemoryTypeDevice) {
+      hrgb.resize(3 * (size_t)d->env->width * d->env->height);
+      e = copy_async(hrgb.data(), rgb, hrgb.size() * sizeof(float), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) { destroy(s); return cuda_fail(e, "reading the environment map"); }
+      rgb = hrgb.data();
+    }
+    if (!build_alias(rgb, d->env->width, d->env->height, etex, etab)) {
       destroy(s);
       return fail(ST_ERR_INVALID_ARG, "environment map has no positive finite weight");
     }
@@ -913,23 +1035,23 @@ st_status st_scene_create(const st_scene_desc* d, void* stream, st_scene** out) 
     hl[2 * j] = make_float4(L.pos[0], L.pos[1], L.pos[2], 0.0f);
     hl[2 * j + 1] = make_float4(L.intensity[0], L.intensity[1], L.intensity[2], 0.0f);
   }
-  chk(cudaMemcpyAsync(s->verts, d->vertices, 3 * sizeof(float) * s->nv, cudaMemcpyDeviceToDevice, st));
-  chk(cudaMemcpyAsync(s->faces, d->faces, 3 * sizeof(int) * n, cudaMemcpyDeviceToDevice, st));
+  chk(copy_async(s->verts, d->vertices, 3 * sizeof(float) * s->nv, cudaMemcpyDeviceToDevice, st));
+  chk(copy_async(s->faces, d->faces, 3 * sizeof(int) * n, cudaMemcpyDeviceToDevice, st));
   {
     int nt = n * s->ntex;
     k_params_in<<<(nt + 255) / 256, 256, 0, st>>>(d->face_params, s->params, nt, s->np);
   }
-  chk(cudaMemcpyAsync(s->lights, hl.data(), hl.size() * sizeof(float4), cudaMemcpyHostToDevice, st));
-  chk(cudaMemcpyAsync(s->edge_v, ev.data(), ev.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
-  chk(cudaMemcpyAsync(s->edge_f, ef.data(), ef.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
+  chk(copy_async(s->lights, hl.data(), hl.size() * sizeof(float4), cudaMemcpyHostToDevice, st));
+  chk(copy_async(s->edge_v, ev.data(), ev.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
+  chk(copy_async(s->edge_f, ef.data(), ef.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
   chk(cudaMemsetAsync(s->d_err, 0, sizeof(int), st));
   if (s->smooth) {
-    chk(cudaMemcpyAsync(s->vf_start, vfs.data(), vfs.size() * sizeof(int), cudaMemcpyHostToDevice, st));
-    chk(cudaMemcpyAsync(s->vf_list, vfl.data(), vfl.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    chk(copy_async(s->vf_start, vfs.data(), vfs.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    chk(copy_async(s->vf_list, vfl.data(), vfl.size() * sizeof(int), cudaMemcpyHostToDevice, st));
   }
   if (d->env) {
-    chk(cudaMemcpyAsync(s->env_tex, etex.data(), etex.size() * sizeof(float4), cudaMemcpyHostToDevice, st));
-    chk(cudaMemcpyAsync(s->env_alias, etab.data(), etab.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
+    chk(copy_async(s->env_tex, etex.data(), etex.size() * sizeof(float4), cudaMemcpyHostToDevice, st));
+    chk(copy_async(s->env_alias, etab.data(), etab.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
     s->env.w = d->env->width;
     s->env.h = d->env->height;
     s->env.tex = s->env_tex;
@@ -954,7 +1076,7 @@ st_status st_scene_destroy(st_scene* s) {
 static st_status update_vertices(st_scene* s, const float* v, void* stream, bool rebuild) {
   if (!s || !v) return fail(ST_ERR_INVALID_ARG, "NULL argument");
   cudaStream_t st = (cudaStream_t)stream;
-  ST_CUDA(cudaMemcpyAsync(s->verts, v, 3 * sizeof(float) * s->nv, cudaMemcpyDeviceToDevice, st));
+  ST_CUDA(copy_async(s->verts, v, 3 * sizeof(float) * s->nv, cudaMemcpyDeviceToDevice, st));
   cudaError_t e = !rebuild ? bvh_refit(s, st) : s->builder == ST_BVH_LBVH ? bvh_build(s, st) : bvh_build_ploc(s, st);
   if (e == cudaSuccess && rebuild) e = bvh_collapse(s, st);
   if (e == cudaSuccess) e = mesh_stat(s, st);
@@ -1003,7 +1125,7 @@ st_status st_trace_closest(st_scene* s, const float* rays, int n, int exclude, i
   if (!s || (n > 0 && (!rays || !out_tri || !out_t)) || n < 0) return fail(ST_ERR_INVALID_ARG, "bad arguments");
   if (n == 0) return ST_OK;
   k_trace_rays<<<(n + EXT_BLOCK - 1) / EXT_BLOCK, EXT_BLOCK, 0, (cudaStream_t)stream>>>(
-      s->nodes4, s->tri, s->nf, (const float4*)rays, n, exclude, out_tri, out_t, s->d_err);
+      s->nodes4, s->tri, s->nf, s->n4, (const float4*)rays, n, exclude, out_tri, out_t, s->d_err);
   ST_CUDA(cudaGetLastError());
   return ST_OK;
 }
@@ -1014,24 +1136,33 @@ st_status st_get_stats(st_scene* s, st_stats* out) {
   st_stats r;
   std::memset(&r, 0, sizeof(r));
   unsigned long long h[STAT_SIZE] = {0};
-  if (s->eng.stat) ST_CUDA(cudaMemcpy(h, s->eng.stat, sizeof(h), cudaMemcpyDeviceToHost));
+  if (s->eng.stat) ST_CUDA(copy_sync(h, s->eng.stat, sizeof(h), cudaMemcpyDeviceToHost));
   int err = 0;
-  ST_CUDA(cudaMemcpy(&err, s->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  ST_CUDA(copy_sync(&err, s->d_err, sizeof(int), cudaMemcpyDeviceToHost));
   r.paths = (long long)h[STAT_PATHS];
   r.extension_rays = (long long)h[STAT_EXT];
   r.shadow_rays = (long long)h[STAT_SHADOW];
   r.node_visits = (long long)h[STAT_VISITS];
   r.tri_tests = (long long)h[STAT_TESTS];
   r.secondary_samples = (long long)h[STAT_SEC];
+  r.shadow_node_visits = (long long)h[STAT_SH_VISITS];
+  r.shadow_tri_tests = (long long)h[STAT_SH_TESTS];
   r.edge_samples = s->last_edge_samples;
-  double ms = 0;
-  for (int i = 0; i < s->ev_used; ++i) {
-    float x = 0;
-    cudaEventElapsedTime(&x, s->ev[i].first, s->ev[i].second);
-    ms += x;
-  }
-  r.extend_launches = s->ev_used;
-  r.extend_ms = ms;
+  auto timed = [&](int k) {
+    double ms = 0;
+    for (int i = 0; i < s->ev_used[k]; ++i) {
+      float x = 0;
+      cudaEventElapsedTime(&x, s->ev[k][i].first, s->ev[k][i].second);
+      ms += x;
+    }
+    return ms;
+  };
+  r.extend_launches = s->ev_used[0];
+  r.extend_ms = timed(0);
+  r.shadow_launches = s->ev_used[1];
+  r.shadow_ms = timed(1);
+  r.busy_ms = timed(2);
+  r.host_syncs = s->host_syncs;
   r.device_error = err;
   r.bvh_nodes = std::max(s->nf - 1, 0);
   r.bvh4_nodes = s->n4;

@@ -76,7 +76,7 @@ struct Engine {
 enum { CNT_EXT = 0, CNT_EXT_FETCH = 16, CNT_SHADE_FETCH = 32, CNT_SH = 48, CNT_SH_FETCH = 64, CNT_MISC = 80,
        CNT_SEC = CNT_MISC, CNT_SIZE = 96 };
 enum { STAT_PATHS = 0, STAT_EXT = 1, STAT_SHADOW = 2, STAT_EDGE = 3, STAT_VISITS = 4, STAT_TESTS = 5,
-       STAT_SEC = 6, STAT_SIZE = 8 };
+       STAT_SEC = 6, STAT_SH_VISITS = 7, STAT_SH_TESTS = 8, STAT_SIZE = 10 };
 
 struct GraphEntry {
   std::vector<long long> key;
@@ -166,10 +166,13 @@ struct st_scene {
   // graph cache
   cudaStream_t cap_stream = nullptr;
   std::vector<st::GraphEntry> graphs;
-  // timing
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
-  int ev_used = 0;
+  // timing (time_kernels): event pairs around k_extend launches (0), k_shadow launches (1), and the GPU-side
+  // intervals between the host synchronisations of a per-view call (2)
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[3];
+  int ev_used[3] = {0, 0, 0};
+  int host_syncs = 0;
   int sm_count = 0;
+  int g_ext = 0, g_ext_s = 0, g_shade = 0, g_shadow = 0, g_shadow_s = 0;  // persistent stage grids, this device
   long long last_edge_samples = 0;
   int launches = 0;              // kernels enqueued by the last call
   st_stats last{};
@@ -184,5 +187,6 @@ cudaError_t bvh_collapse(st_scene* s, cudaStream_t stream); // 4-wide tree from 
 cudaError_t trace_closest(st_scene* s, const float* rays, int n, int exclude, int* out_tri, float* out_t,
                           cudaStream_t stream);
 void set_error(const std::string& msg);
+bool fault_now(int site);   // host-side fault injection: true when this event at `site` is to fail
 int sort_blocks_for(int n);
 }  // namespace st

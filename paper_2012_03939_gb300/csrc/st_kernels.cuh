@@ -27,6 +27,7 @@ struct KCtx {
   const float4* nodes;
   const float4* tri;
   int nf, nv;
+  int n4;                 // nodes of the 4-wide tree
   const float4* lights;
   int nl, nlt, NS;        // scene lights, + the most any view of the call adds, + environment
   DevEnv env;
@@ -335,7 +336,7 @@ __global__ void __launch_bounds__(EXT_BLOCK) k_sh_prep(KCtx c, long long j0, int
   }
   float th;
   int leaf = -1;
-  int rf = trace_bvh<false, false, true>(c.nodes, c.tri, c.nf, org, dir, __int_as_float(0x7f800000), ef.x, th,
+  int rf = trace_bvh<false, false, true>(c.nodes, c.tri, c.nf, c.n4, org, dir, __int_as_float(0x7f800000), ef.x, th,
                                          sstack + threadIdx.x, c.err, nullptr, &leaf, ef.y);
   if (rf < 0) return;
   float3 q = org + dir * th;
@@ -711,7 +712,7 @@ __global__ void __launch_bounds__(EXT_BLOCK) k_extend(KCtx c, int b) {
         if (STATS) ts.tests++;
       }
     } else {
-      f = trace_bvh<false, STATS>(c.nodes, c.tri, c.nf, xyz(o), xyz(d), __int_as_float(0x7f800000), E.origin[slot], t,
+      f = trace_bvh<false, STATS>(c.nodes, c.tri, c.nf, c.n4, xyz(o), xyz(d), __int_as_float(0x7f800000), E.origin[slot], t,
                                   sstack + threadIdx.x, c.err, &ts, &fl);
     }
     E.hit[slot] = make_int2(fl, __float_as_int(t));   // leaf index: shading reads the contiguous leaf record
@@ -753,6 +754,7 @@ __global__ void k_shade(KCtx c, int b) {
       if (c.env.w > 0) {
         float st_;
         int tx = env_texel(c.env, dir, st_);
+        if (c.sig) { sig_mix(hs, (uint32_t)tx); E.sig[slot] = hs; }   // the nearest-texel lookup is a decision
         float4 te = __ldg(&c.env.tex[tx]);
         float w = 1.0f;
         if (b > 0) {
@@ -779,6 +781,7 @@ __global__ void k_shade(KCtx c, int b) {
       int tex = texel_of(c, f, p, v0, v1, v2);
       Mat m = fetch_mat(c.P, tex);
       if (c.sig) sig_mix(hs, (uint32_t)f);
+      if (c.sig && c.res > 0) sig_mix(hs, (uint32_t)tex);   // so is the mesh-colors texel
       if (E.records) {
         E.r0[b * Q + slot] = make_float4(p.x, p.y, p.z, __int_as_float(f));
         E.nb[slot] = b + 1;
@@ -859,11 +862,13 @@ __global__ void k_shade(KCtx c, int b) {
   ST_WARP_LOOP_END
 }
 
+template <bool STATS>
 __global__ void __launch_bounds__(EXT_BLOCK) k_shadow(KCtx c, int b) {
   __shared__ int sstack[TRACE_SH * EXT_BLOCK];
   const Engine& E = c.e;
   const size_t Q = (size_t)E.Q;
   int traced = 0;
+  TraceStats ts{0, 0};
   ST_WARP_LOOP(E.cnt[CNT_SH + b], &E.cnt[CNT_SH_FETCH + b])
   if (live_) {
     int slot = E.qs[qi_];
@@ -877,8 +882,8 @@ __global__ void __launch_bounds__(EXT_BLOCK) k_shadow(KCtx c, int b) {
       float4 sd = E.sh_dir[k * Q + slot];
       float t;
       ++traced;
-      int hf = trace_bvh<true, false>(c.nodes, c.tri, c.nf, p, xyz(sd), sd.w, exclude, t, sstack + threadIdx.x, c.err,
-                                      nullptr);
+      int hf = trace_bvh<true, STATS>(c.nodes, c.tri, c.nf, c.n4, p, xyz(sd), sd.w, exclude, t, sstack + threadIdx.x,
+                                      c.err, &ts);
       if (hf < 0) {
         L += xyz(sc);
         vis |= (k < c.nlt) ? (1 << k) : ENV_VIS;
@@ -899,6 +904,16 @@ __global__ void __launch_bounds__(EXT_BLOCK) k_shadow(KCtx c, int b) {
   ST_WARP_LOOP_END
   for (int off = 16; off > 0; off >>= 1) traced += __shfl_xor_sync(FULL, traced, off);
   if ((threadIdx.x & 31) == 0 && traced) atomicAdd(&E.stat[STAT_SHADOW], (unsigned long long)traced);
+  if (STATS) {
+    for (int off = 16; off > 0; off >>= 1) {
+      ts.visits += __shfl_xor_sync(FULL, ts.visits, off);
+      ts.tests += __shfl_xor_sync(FULL, ts.tests, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(&E.stat[STAT_SH_VISITS], (unsigned long long)ts.visits);
+      atomicAdd(&E.stat[STAT_SH_TESTS], (unsigned long long)ts.tests);
+    }
+  }
 }
 
 // Compensated (Kahan) summation in FP32: (sum, carried error); FP64 adds would
@@ -1671,7 +1686,7 @@ __global__ void k_sh_resolve(KCtx c, long long j0, int n) {
 }
 
 // closest-hit queries for st_trace_closest
-__global__ void __launch_bounds__(EXT_BLOCK) k_trace_rays(const float4* nodes, const float4* tri, int nf,
+__global__ void __launch_bounds__(EXT_BLOCK) k_trace_rays(const float4* nodes, const float4* tri, int nf, int nn,
                                                           const float4* rays, int n, int exclude, int* out_tri,
                                                           float* out_t, int* err) {
   __shared__ int sstack[TRACE_SH * EXT_BLOCK];
@@ -1679,7 +1694,7 @@ __global__ void __launch_bounds__(EXT_BLOCK) k_trace_rays(const float4* nodes, c
   if (i >= n) return;
   float4 a = rays[2 * i], b = rays[2 * i + 1];
   float t;
-  int f = trace_bvh<false, false>(nodes, tri, nf, xyz(a), xyz(b), b.w, exclude, t, sstack + threadIdx.x, err, nullptr);
+  int f = trace_bvh<false, false>(nodes, tri, nf, nn, xyz(a), xyz(b), b.w, exclude, t, sstack + threadIdx.x, err, nullptr);
   out_tri[i] = f;
   out_t[i] = f >= 0 ? t : __int_as_float(0x7f800000);
 }

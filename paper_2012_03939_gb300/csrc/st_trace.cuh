@@ -38,7 +38,8 @@ __device__ __forceinline__ float box_hit(float lx, float hx, float ly, float hy,
   return tn <= tf * 1.00000036f ? tn : __int_as_float(0x7f800000);
 }
 
-// ANY = stop at the first hit (shadow rays). Returns the face id or -1; t in
+// ANY = stop at the first hit (shadow rays). nf = leaves (faces), nn = 4-wide
+// nodes: indices outside them latch an error bit. Returns the face id or -1; t in
 // tbest; the hit's leaf index in *leaf_out if given. EX2 = a second face
 // (exclude2) is skipped too.
 // nodes = the 4-wide tree: per node lo.x, hi.x, lo.y, hi.y, lo.z, hi.z (one
@@ -47,7 +48,7 @@ __device__ __forceinline__ float box_hit(float lx, float hx, float ly, float hy,
 // sorted by entry distance, the nearest is visited next, the others pushed.
 template <bool ANY, bool STATS, bool EX2 = false>
 __device__ __forceinline__ int trace_bvh(const float4* __restrict__ nodes, const float4* __restrict__ tri, int nf,
-                                         float3 o, float3 d, float tmax, int exclude, float& tbest, int* sstack,
+                                         int nn, float3 o, float3 d, float tmax, int exclude, float& tbest, int* sstack,
                                          int* err, TraceStats* ts, int* leaf_out = nullptr, int exclude2 = -1) {
   RayPre rp = ray_pre(o, d);
   float3 inv = safe_inv(d);
@@ -79,9 +80,9 @@ __device__ __forceinline__ int trace_bvh(const float4* __restrict__ nodes, const
   const int bd = blockDim.x;
   int sp = 0;
   int node = 0;
-  int budget = nf;  // a well-formed tree fetches each of its < nf nodes at most once
+  int budget = nn;  // a well-formed tree fetches each of its nn nodes at most once
   for (;;) {
-    if (--budget < 0 || (unsigned)node >= (unsigned)nf) { atomicOr(err, ERR_LOOP); return best; }
+    if (--budget < 0 || (unsigned)node >= (unsigned)nn) { atomicOr(err, ERR_LOOP); return best; }
     const float4* np = nodes + 7 * node;
     float4 lx = __ldg(np), hx = __ldg(np + 1), ly = __ldg(np + 2), hy = __ldg(np + 3), lz = __ldg(np + 4),
            hz = __ldg(np + 5), ch = __ldg(np + 6);

@@ -32,6 +32,18 @@ class AdamConfig:
     seed: int = 12345
 
 
+def clamp_params_(P: torch.Tensor) -> torch.Tensor:
+    """Clamp texel parameters in place to their valid range, by layout: 5 per texel (kd rgb, ks, roughness) or
+    7 (kd rgb, ks rgb, roughness). Albedos and specular values to [0, 1], roughness (the last column) to
+    [0.01, 1]."""
+    if P.dim() != 2 or P.shape[1] not in (5, 7):
+        raise ValueError("texel parameters must be [texels, 5] or [texels, 7]")
+    r = P.shape[1] - 1
+    P[:, :r].clamp_(0.0, 1.0)
+    P[:, r].clamp_(0.01, 1.0)
+    return P
+
+
 class Reconstruction:
     """Holds the scene, the optimised tensors and the Adam state."""
 
@@ -73,8 +85,7 @@ class Reconstruction:
         loss.backward()
         self.opt.step()
         with torch.no_grad():
-            self.P[:, :4].clamp_(0.0, 1.0)
-            self.P[:, 4].clamp_(0.01, 1.0)
+            clamp_params_(self.P)
         self.it += 1
         return loss.detach()
 

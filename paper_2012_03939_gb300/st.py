@@ -28,7 +28,7 @@ BVH_PLOC, BVH_LBVH = 0, 1
 
 EXPORTED = ["st_scene_create", "st_scene_destroy", "st_refit", "st_rebuild", "st_set_face_params", "st_render",
             "st_render_backward", "st_trace_closest", "st_get_stats", "st_debug_bvh", "st_build_bvh_noalloc",
-            "st_measure_l2_read", "st_last_error"]
+            "st_measure_l2_read", "st_inject_fault", "st_last_error"]
 
 
 class StError(RuntimeError):
@@ -75,7 +75,10 @@ class Stats(C.Structure):
                 ("edge_samples", C.c_longlong), ("node_visits", C.c_longlong), ("tri_tests", C.c_longlong),
                 ("extend_launches", C.c_int), ("extend_ms", C.c_double), ("device_error", C.c_int),
                 ("bvh_nodes", C.c_int), ("scratch_bytes", C.c_longlong), ("kernel_launches", C.c_int),
-                ("bvh4_nodes", C.c_int), ("secondary_samples", C.c_longlong)]
+                ("bvh4_nodes", C.c_int), ("secondary_samples", C.c_longlong),
+                ("shadow_node_visits", C.c_longlong), ("shadow_tri_tests", C.c_longlong),
+                ("shadow_launches", C.c_int), ("shadow_ms", C.c_double), ("busy_ms", C.c_double),
+                ("host_syncs", C.c_int)]
 
 
 _lib = None
@@ -102,6 +105,7 @@ def lib():
         L.st_debug_bvh.argtypes = [P, P, P]
         L.st_build_bvh_noalloc.argtypes = [P, P, I, I, P, P, P, P]
         L.st_measure_l2_read.argtypes = [C.c_longlong, I, P, P]
+        L.st_inject_fault.argtypes = [I, I]
         L.st_last_error.restype = C.c_char_p
         L.st_last_error.argtypes = []
         for name in EXPORTED[:-1]:
@@ -180,10 +184,17 @@ class Scene:
         self._lights = (PointLight * max(len(lp), 1))()
         for j in range(len(lp)):
             self._lights[j] = PointLight((C.c_float * 3)(*lp[j]), (C.c_float * 3)(*li[j]))
-        self._env_arr = None if env is None else np.ascontiguousarray(env, np.float32)
+        # the environment may be a host array or a CUDA tensor [H, W, 3]; either is passed by pointer
+        if env is None:
+            self._env_arr = None
+        elif isinstance(env, torch.Tensor) and env.is_cuda:
+            self._env_arr = env.detach().to(dev, torch.float32).contiguous()
+        else:
+            self._env_arr = np.ascontiguousarray(env, np.float32)
         self._env = None
         if self._env_arr is not None:
-            self._env = EnvMap(self._env_arr.shape[1], self._env_arr.shape[0], self._env_arr.ctypes.data)
+            ptr = self._env_arr.data_ptr() if isinstance(self._env_arr, torch.Tensor) else self._env_arr.ctypes.data
+            self._env = EnvMap(self._env_arr.shape[1], self._env_arr.shape[0], ptr)
         desc = SceneDesc(self.nv, self.nf, self.vertices.data_ptr(), self.faces.data_ptr(),
                          self.face_params.data_ptr(), {"ggx": 0, "beckmann": 1}[brdf], len(lp),
                          C.addressof(self._lights), None if self._env is None else C.addressof(self._env),
@@ -279,6 +290,16 @@ class Scene:
         leaf = np.zeros(self.nf, np.int32)
         _check(lib().st_debug_bvh(self.handle, nodes.ctypes.data, leaf.ctypes.data))
         return nodes[: self.nf - 1], leaf
+
+
+FAULT_ALLOC, FAULT_COPY = 1, 2
+
+
+def inject_fault(site, nth: int = 0):
+    """Arm the library's host-side fault injection: the nth next device allocation ("alloc") or host<->device
+    copy ("copy") fails as the CUDA call would have; nth < 0 disarms the site."""
+    site = {"alloc": FAULT_ALLOC, "copy": FAULT_COPY}.get(site, site)
+    _check(lib().st_inject_fault(int(site), int(nth)))
 
 
 def measure_l2_read(bytes_=32 << 20, passes=64, stream=None) -> float:

@@ -75,6 +75,43 @@ def test_adam_recovers_material_and_resumes_from_checkpoint(st, tmp_path):
     scene.close()
 
 
+def test_adam_with_rgb_specular_recovers_colour_and_keeps_roughness_in_range(st):
+    # 7 parameters per texel (kd rgb, ks rgb, roughness): the step clamps by that layout
+    from paper_2012_03939_gb300.optimize import clamp_params_
+    from paper_2012_03939_gb300 import optimize as Opt
+    sc = S.tiny(res=40, spp=8)
+    sc.views = S.ring_views(4, 32, 8)
+    P5 = sc.face_params
+    rng = np.random.default_rng(21)
+    true_P = np.c_[P5[:, :3], rng.uniform(0.02, 0.3, (len(P5), 3)), P5[:, 4]].astype(np.float32)
+    sc.face_params = true_P
+    targets = Opt.render_targets(sc, max_bounces=2)
+    start = true_P.copy()
+    start[:, :3] = np.clip(start[:, :3] + 0.25, 0, 1)
+    start[:, 6] = 0.02                 # roughness near its lower bound: a 5-column clamp would leave it unclamped
+    scene = st.Scene.from_scene(sc)
+    assert scene.face_params.shape[1] == 7
+    cfg = Opt.AdamConfig(max_bounces=2, minibatch=2, lr_vertices=0.0, lr_params=0.03, edge_term=1, seed=5)
+    rec = Opt.Reconstruction(scene, sc.views, targets, torch.from_numpy(sc.vertices).cuda(),
+                             torch.from_numpy(start).cuda(), cfg)
+
+    def full_loss(P):
+        scene.set_face_params(P)
+        return float(torch.mean((scene.render(sc.views, 2, 99) - targets) ** 2))
+
+    l0 = full_loss(rec.P.detach())
+    for _ in range(25):
+        rec.step()
+        P = rec.P.detach()
+        assert float(P[:, 6].min()) >= float(np.float32(0.01)) and float(P[:, 6].max()) <= 1.0
+        assert float(P[:, :6].min()) >= 0.0 and float(P[:, :6].max()) <= 1.0
+    l1 = full_loss(rec.P.detach())
+    assert l1 < 0.5 * l0, (l0, l1)
+    P = rec.P.detach().clone()
+    assert torch.equal(clamp_params_(P.clone()), P)
+    scene.close()
+
+
 def test_refit_every_step_keeps_parity_with_a_fresh_scene(st):
     # vertex updates through the autograd wrapper refit the BVH; a scene built
     # from scratch on the same vertices renders the identical image

@@ -8,7 +8,7 @@ torch = pytest.importorskip("torch")
 
 import oracle as O
 from paper_2012_03939_gb300 import scenes as S
-from tests.gpu_util import (GRAD_REL, assert_image_parity, image_report, oracle_pixels, rel_l2, sample_pixels)
+from tests.gpu_util import GRAD_REL, assert_image_parity, oracle_pixels, rel_l2, sample_pixels
 
 pytestmark = pytest.mark.gpu
 
@@ -135,18 +135,6 @@ def test_forward_small_variants_full_image(st, name, B):
     ref, seg = O.render_pixels(O.OracleScene(sc), O.params(B, 77), O.all_pixels(sc))
     assert_image_parity(img, ref, what=name)
     assert abs(stats["extension_rays"] + stats["shadow_rays"] - seg) <= 2e-4 * seg
-
-
-@pytest.mark.parametrize("name,npix,views", [("edges", 48, None), ("batched", 24, None), ("scale", 12, 2)])
-def test_forward_full_size_sampled_pixels(st, name, npix, views):
-    sc = S.make(name)
-    if views:
-        sc = sc.subset_views(range(views))
-    img, _ = gpu_image(st, sc, sc.max_bounces, 2024)
-    pix = sample_pixels(sc, npix, seed=5)
-    ref = oracle_pixels(sc, sc.max_bounces, 2024, pix)
-    f, m, _ = image_report(img[rows_of(sc, pix)], ref)
-    assert f >= 0.99 and m <= 1e-4, (f, m)
 
 
 def test_batched_per_view_and_graph_agree_bitwise(st):
@@ -352,7 +340,7 @@ def test_primary_bins_and_bvh_fallback_views(st):
     assert stats["extension_rays"] + stats["shadow_rays"] == seg
 
 
-@pytest.mark.parametrize("name,npix,views", [("batched", 24, None), ("scale", 6, 2)])
+@pytest.mark.parametrize("name,npix,views", [("batched", 256, None), ("scale", 64, 8)])
 def test_full_size_gradient_in_bench_configuration(st, name, npix, views):
     # the benchmark's launch configuration (batched, CUDA graph, 8M-path chunks, silhouette
     # edge term) at full size; dL/dI nonzero on a pixel sample so the oracle can follow

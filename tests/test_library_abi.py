@@ -97,3 +97,17 @@ def test_make_opts_maps_names_to_header_values():
     assert (o.sec_pick, o.edge_mode, o.mode, o.edge_term) == (st.SEC_PICK_UNIFORM, st.EDGE_ALL, st.MODE_PER_VIEW, 6)
     with pytest.raises(KeyError):
         st.make_opts(sec_pick="random")
+
+
+def test_fault_injection_hook_validates_its_site_without_gpu():
+    # arming and disarming the host-side fault hook makes no CUDA call
+    from paper_2012_03939_gb300 import st
+    L = st.lib()
+    assert L.st_inject_fault(0, 0) == 1 and b"fault site" in L.st_last_error()
+    assert L.st_inject_fault(3, 0) == 1
+    for site in (st.FAULT_ALLOC, st.FAULT_COPY):
+        assert L.st_inject_fault(site, 5) == 0
+        assert L.st_inject_fault(site, -1) == 0
+    src = open(os.path.join(ROOT, "include", "st.h")).read()
+    defs = {k: int(v) for k, v in re.findall(r"#define ST_([A-Z0-9_]+)\s+(-?\d+)", src)}
+    assert (defs["FAULT_ALLOC"], defs["FAULT_COPY"]) == (st.FAULT_ALLOC, st.FAULT_COPY)
