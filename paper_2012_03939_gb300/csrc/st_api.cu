@@ -465,7 +465,10 @@ st_status run_chunk(st_scene* s, const Plan& p, const KCtx& c, long long j0, int
     s->g_shade = grid_of((const void*)k_shade, 256, sm);
     s->g_shadow = grid_of((const void*)k_shadow<false>, EXT_BLOCK, sm);
     s->g_shadow_s = grid_of((const void*)k_shadow<true>, EXT_BLOCK, sm);
+    s->g_bins = grid_of((const void*)k_extend_bins<false>, EXT_BLOCK, sm);
+    s->g_bins_s = grid_of((const void*)k_extend_bins<true>, EXT_BLOCK, sm);
   }
+  const int g_bins = p.o.count_visits ? s->g_bins_s : s->g_bins;
   const int g_ext = s->g_ext, g_ext_s = s->g_ext_s, g_shade = s->g_shade;
   const int g_shadow = p.o.count_visits ? s->g_shadow_s : s->g_shadow;
   // persistent grids: occupancy limit, or fewer resident blocks per SM if asked
@@ -490,21 +493,37 @@ st_status run_chunk(st_scene* s, const Plan& p, const KCtx& c, long long j0, int
     s->launches++;
     return ST_OK;
   };
-  // extension / shading / shadow stages for `nb` bounces of the paths queued in q0
-  auto bounces = [&](const KCtx& k, int nb) -> st_status {
+  // extension / shading / shadow stages for `nb` bounces of the paths queued in q0; with `bins`, the first
+  // rays test the leaves of their pixel's screen-space bin (k_extend_bins), the others go through the BVH
+  auto bounces = [&](const KCtx& k, int nb, bool bins) -> st_status {
     for (int b = 0; b < nb; ++b) {
-      int ge = cap(p.o.count_visits ? g_ext_s : g_ext), gs = cap(g_shade), gw = cap(g_shadow);
+      int ge = cap(p.o.count_visits ? g_ext_s : g_ext), gs = cap(g_shade), gw = cap(g_shadow), gb = cap(g_bins);
+      int gf = ge;
       if (host_sized) {
         st_status r = read_counts();
         if (r != ST_OK) return r;
         int q = hc[CNT_EXT + b];
         if (q == 0) break;
         ge = (q + EXT_BLOCK - 1) / EXT_BLOCK;
+        gb = std::min(gb, ge);
         gs = (q + 255) / 256;
       }
       if (timing) ST_CUDA(cudaEventRecord(next_event(s, 0, true), st));
-      if (p.o.count_visits) k_extend<true><<<ge, EXT_BLOCK, 0, st>>>(k, b);
-      else k_extend<false><<<ge, EXT_BLOCK, 0, st>>>(k, b);
+      if (b == 0 && bins) {
+        // the BVH launch takes the rays the bins kernel queued (a persistent grid: the count stays on the device)
+        if (p.o.count_visits) {
+          k_extend_bins<true><<<gb, EXT_BLOCK, 0, st>>>(k);
+          k_extend<true><<<gf, EXT_BLOCK, 0, st>>>(k, 0, 1);
+        } else {
+          k_extend_bins<false><<<gb, EXT_BLOCK, 0, st>>>(k);
+          k_extend<false><<<gf, EXT_BLOCK, 0, st>>>(k, 0, 1);
+        }
+        s->launches++;
+      } else if (p.o.count_visits) {
+        k_extend<true><<<ge, EXT_BLOCK, 0, st>>>(k, b, 0);
+      } else {
+        k_extend<false><<<ge, EXT_BLOCK, 0, st>>>(k, b, 0);
+      }
       if (timing) ST_CUDA(cudaEventRecord(next_event(s, 0, false), st));
       k_shade<<<gs, 256, 0, st>>>(k, b);
       s->launches += 2;
@@ -530,7 +549,7 @@ st_status run_chunk(st_scene* s, const Plan& p, const KCtx& c, long long j0, int
   if (has_shadow) k_raygen<true><<<(n + 255) / 256, 256, 0, st>>>(c, j0, n);
   else k_raygen<false><<<(n + 255) / 256, 256, 0, st>>>(c, j0, n);
   s->launches += 2;
-  st_status r = bounces(c, p.B);
+  st_status r = bounces(c, p.B, p.bins);
   if (r != ST_OK) return r;
   if (p.kind == 0) {
     k_resolve<<<(n + RESOLVE_BLOCK - 1) / RESOLVE_BLOCK, RESOLVE_BLOCK, 0, st>>>(c, j0, n);
@@ -560,7 +579,7 @@ st_status run_chunk(st_scene* s, const Plan& p, const KCtx& c, long long j0, int
         k_reset_pass<<<1, 128, 0, st>>>(cnt);
         k_sec_raygen<<<std::min((Q + 255) / 256, 4 * sm), 256, 0, st>>>(cs, ps);
         s->launches += 2;
-        r = bounces(cs, std::max(1, p.B - 1));
+        r = bounces(cs, std::max(1, p.B - 1), false);
         if (r != ST_OK) return r;
         k_sec_resolve<<<std::min((Q + ADJ_BLOCK - 1) / ADJ_BLOCK, 8 * sm), ADJ_BLOCK, 0, st>>>(cs, ps);
         s->launches++;

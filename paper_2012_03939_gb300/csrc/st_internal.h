@@ -74,7 +74,7 @@ struct Engine {
 };
 
 enum { CNT_EXT = 0, CNT_EXT_FETCH = 16, CNT_SHADE_FETCH = 32, CNT_SH = 48, CNT_SH_FETCH = 64, CNT_MISC = 80,
-       CNT_SEC = CNT_MISC, CNT_SIZE = 96 };
+       CNT_SEC = CNT_MISC, CNT_FB = 88, CNT_FB_FETCH = 89, CNT_SIZE = 96 };
 enum { STAT_PATHS = 0, STAT_EXT = 1, STAT_SHADOW = 2, STAT_EDGE = 3, STAT_VISITS = 4, STAT_TESTS = 5,
        STAT_SEC = 6, STAT_SH_VISITS = 7, STAT_SH_TESTS = 8, STAT_SIZE = 10 };
 
@@ -172,7 +172,7 @@ struct st_scene {
   int ev_used[3] = {0, 0, 0};
   int host_syncs = 0;
   int sm_count = 0;
-  int g_ext = 0, g_ext_s = 0, g_shade = 0, g_shadow = 0, g_shadow_s = 0;  // persistent stage grids, this device
+  int g_ext = 0, g_ext_s = 0, g_shade = 0, g_shadow = 0, g_shadow_s = 0, g_bins = 0, g_bins_s = 0;  // stage grids
   long long last_edge_samples = 0;
   int launches = 0;              // kernels enqueued by the last call
   st_stats last{};

@@ -686,13 +686,71 @@ __global__ void k_raygen(KCtx c, long long j0, int n) {
 
 #define ST_WARP_LOOP_END }
 
+// Closest hits of the first rays of a chunk whose pixel has a screen-space bin:
+// the leaves listed for that pixel, tested two at a time (two independent
+// list-entry and leaf-record loads in flight per lane), with no traversal
+// stack, so the kernel needs few registers and keeps many warps resident. The
+// hit is the smallest t, ties to the lower face id, as a sequential scan of
+// the list gives. Rays without a bin (views the bins do not serve) are queued
+// (q1, CNT_FB) for k_extend's BVH traversal.
 template <bool STATS>
-__global__ void __launch_bounds__(EXT_BLOCK) k_extend(KCtx c, int b) {
+__global__ void __launch_bounds__(EXT_BLOCK, 10) k_extend_bins(KCtx c) {
+  const Engine& E = c.e;
+  int tests = 0;
+  ST_WARP_LOOP(E.cnt[CNT_EXT + 0], &E.cnt[CNT_EXT_FETCH + 0])
+  bool fallback = false;
+  int slot = live_ ? E.q0[qi_] : 0;
+  if (live_) {
+    int2 br = E.brange[slot];
+    if (br.x < 0) {
+      fallback = true;
+    } else {
+      float4 o = E.o[slot], d = E.d[slot];
+      RayPre rp = ray_pre(xyz(o), xyz(d));
+      float t = __int_as_float(0x7f800000);
+      int f = -1, fl = -1;
+      if (br.y > c.bin_cap || br.x > br.y) { atomicOr(c.err, ERR_INDEX); br.y = br.x; }
+      for (int k = br.x; k < br.y; k += 2) {
+        bool two = k + 1 < br.y;
+        int l0 = __ldg(&c.bin_list[k]);
+        int l1 = two ? __ldg(&c.bin_list[k + 1]) : l0;
+        if ((unsigned)l0 >= (unsigned)c.nf || (unsigned)l1 >= (unsigned)c.nf) {
+          atomicOr(c.err, ERR_INDEX);
+          continue;
+        }
+        float4 a0 = __ldg(&c.tri[3 * l0]), b0 = __ldg(&c.tri[3 * l0 + 1]), c0 = __ldg(&c.tri[3 * l0 + 2]);
+        float4 a1 = __ldg(&c.tri[3 * l1]), b1 = __ldg(&c.tri[3 * l1 + 1]), c1 = __ldg(&c.tri[3 * l1 + 2]);
+        float tmax = t * 1.0000001f + 1e-30f;
+        float h0 = tri_test(rp, xyz(a0), xyz(b0), xyz(c0), tmax);
+        float h1 = two ? tri_test(rp, xyz(a1), xyz(b1), xyz(c1), tmax) : -1.0f;
+        int f0 = __float_as_int(a0.w), f1 = __float_as_int(a1.w);
+        if (h0 > 0.0f && (h0 < t || (h0 == t && f0 < f))) { t = h0; f = f0; fl = l0; }
+        if (h1 > 0.0f && (h1 < t || (h1 == t && f1 < f))) { t = h1; f = f1; fl = l1; }
+        if (STATS) tests += two ? 2 : 1;
+      }
+      E.hit[slot] = make_int2(fl, __float_as_int(t));
+    }
+  }
+  int qf = warp_append(&E.cnt[CNT_FB], fallback);
+  if (fallback) E.q1[qf] = slot;
+  ST_WARP_LOOP_END
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&E.stat[STAT_EXT], (unsigned long long)E.cnt[CNT_EXT + 0]);
+  if (STATS) {
+    for (int off = 16; off > 0; off >>= 1) tests += __shfl_xor_sync(FULL, tests, off);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&E.stat[STAT_TESTS], (unsigned long long)tests);
+  }
+}
+
+// Closest hits through the BVH (the rays of bounce b, or with fb = 1 the first
+// rays k_extend_bins queued). Rays of bounce 0 that carry a bin range test
+// their pixel's leaves here too when the call runs without k_extend_bins.
+template <bool STATS>
+__global__ void __launch_bounds__(EXT_BLOCK) k_extend(KCtx c, int b, int fb) {
   __shared__ int sstack[TRACE_SH * EXT_BLOCK];
   const Engine& E = c.e;
-  const int* q = (b & 1) ? E.q1 : E.q0;
+  const int* q = fb ? E.q1 : (b & 1) ? E.q1 : E.q0;
   TraceStats ts{0, 0};
-  ST_WARP_LOOP(E.cnt[CNT_EXT + b], &E.cnt[CNT_EXT_FETCH + b])
+  ST_WARP_LOOP(fb ? E.cnt[CNT_FB] : E.cnt[CNT_EXT + b], fb ? &E.cnt[CNT_FB_FETCH] : &E.cnt[CNT_EXT_FETCH + b])
   if (live_) {
     int slot = q[qi_];
     float4 o = E.o[slot], d = E.d[slot];
@@ -718,7 +776,7 @@ __global__ void __launch_bounds__(EXT_BLOCK) k_extend(KCtx c, int b) {
     E.hit[slot] = make_int2(fl, __float_as_int(t));   // leaf index: shading reads the contiguous leaf record
   }
   ST_WARP_LOOP_END
-  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&E.stat[STAT_EXT], (unsigned long long)E.cnt[CNT_EXT + b]);
+  if (!fb && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&E.stat[STAT_EXT], (unsigned long long)E.cnt[CNT_EXT + b]);
   if (STATS) {
     for (int off = 16; off > 0; off >>= 1) {
       ts.visits += __shfl_xor_sync(FULL, ts.visits, off);
