@@ -756,7 +756,7 @@ __global__ void __launch_bounds__(EXT_BLOCK) k_extend(KCtx c, int b, int fb) {
     float4 o = E.o[slot], d = E.d[slot];
     float t = __int_as_float(0x7f800000);
     int f = -1, fl = -1;
-    int2 br = b == 0 ? E.brange[slot] : make_int2(-1, -1);
+    int2 br = b == 0 && !fb ? E.brange[slot] : make_int2(-1, -1);
     if (br.x >= 0) {
       RayPre rp = ray_pre(xyz(o), xyz(d));
       if (br.y > c.bin_cap || br.x > br.y) { atomicOr(c.err, ERR_INDEX); br.y = br.x; }
