@@ -33,7 +33,8 @@ class _Scene(C.Structure):
                 ("faces", C.c_void_p), ("face_params", C.c_void_p), ("brdf", C.c_int),
                 ("n_lights", C.c_int), ("light_pos", C.c_void_p), ("light_intensity", C.c_void_p),
                 ("env_width", C.c_int), ("env_height", C.c_int), ("env_rgb", C.c_void_p),
-                ("color_res", C.c_int), ("param_width", C.c_int), ("smooth_normals", C.c_int)]
+                ("color_res", C.c_int), ("param_width", C.c_int), ("smooth_normals", C.c_int),
+                ("fresnel", C.c_int)]
 
 
 class _View(C.Structure):
@@ -80,7 +81,7 @@ def lib():
         L.orc_closest_hit.restype = None
         L.orc_closest_hit.argtypes = [P, P, C.c_int, C.c_int, P, P]
         L.orc_brdf_eval.restype = None
-        L.orc_brdf_eval.argtypes = [C.c_int, P, P, P, P, P]
+        L.orc_brdf_eval.argtypes = [C.c_int, C.c_int, P, P, P, P, P]
         L.orc_brdf_pdf.restype = C.c_double
         L.orc_brdf_pdf.argtypes = [C.c_int, P, P, P, P]
         L.orc_brdf_sample.restype = C.c_double
@@ -121,7 +122,8 @@ class OracleScene:
                         0 if sc.brdf == "ggx" else 1, len(self.LP), _ptr(self.LP).value, _ptr(self.LI).value,
                         0 if self.E is None else self.E.shape[1], 0 if self.E is None else self.E.shape[0],
                         None if self.E is None else _ptr(self.E).value, int(getattr(sc, "color_res", 0)),
-                        self.P.shape[1], int(bool(getattr(sc, "smooth_normals", False))))
+                        self.P.shape[1], int(bool(getattr(sc, "smooth_normals", False))),
+                        int(getattr(sc, "fresnel", 0)))
         self.views = (_View * len(sc.views))()
         for i, v in enumerate(sc.views):
             lights = list(getattr(v, "lights", ()) or ())
@@ -287,10 +289,11 @@ def closest_hit(osc: OracleScene, rays, exclude=-1):
     return tri, t
 
 
-def brdf_eval(brdf, p5, n, wi, wo):
+def brdf_eval(brdf, p5, n, wi, wo, fresnel=0):
+    """f(wi, wo) (RGB); fresnel: 0 = Fresnel factor held at ks, 1 = Schlick with F0 = ks."""
     out = np.zeros(3)
     a = [np.ascontiguousarray(x, np.float64) for x in (p5, n, wi, wo)]
-    lib().orc_brdf_eval(brdf, *[_ptr(x) for x in a], _ptr(out))
+    lib().orc_brdf_eval(brdf, int(fresnel), *[_ptr(x) for x in a], _ptr(out))
     return out
 
 

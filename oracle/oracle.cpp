@@ -24,11 +24,12 @@
 //    the scene option smooth_normals, a shading normal interpolated from vertex
 //    normals, used for NEE, BRDF, sampling and pdfs, a direction counting only
 //    above both planes (see shading_normal).
-//  * BRDF: f = kd/pi + ks D G1(i) G1(o) / (4 cos_i cos_o): the Fresnel factor
-//    is held at its normal-incidence value ks (the "specular color", one value
-//    for all channels with 5 parameters per texel, one per channel with 7), so
-//    ks = 0 is exactly Lambertian; D = GGX or Beckmann with alpha = roughness
-//    (clamped to [0.01, 1]); separable Smith G1.
+//  * BRDF: f = kd/pi + F D G1(i) G1(o) / (4 cos_i cos_o) with the "specular
+//    color" ks (one value for all channels with 5 parameters per texel, one
+//    per channel with 7): the Fresnel factor F is held at its normal-incidence
+//    value ks (scene option fresnel = 0, so ks = 0 is exactly Lambertian) or is
+//    Schlick's ks + (1 - ks)(1 - wi.h)^5 (fresnel = 1); D = GGX or Beckmann
+//    with alpha = roughness (clamped to [0.01, 1]); separable Smith G1.
 //  * Lobe choice p_s = clamp(mean ks / (mean ks + mean kd), 0.05, 0.95); diffuse by the
 //    concentric-disk (Shirley-Chiu) cosine map, specular by h ~ D cos(theta_h)
 //    and reflection, in a tangent frame t = (h x n)/|h x n|, b = n x t about a
@@ -209,6 +210,7 @@ struct Scene {
   int np = 5;                   // parameters per texel: kd rgb, ks, alpha (5) or kd rgb, ks rgb, alpha (7)
   std::vector<double> param;    // np per texel
   int brdf = 0;
+  int fresnel = 0;              // 0: Fresnel factor held at ks; 1: Schlick with F0 = ks
   std::vector<V3d> lpos, lint;
   int ew = 0, eh = 0;
   std::vector<double> env;      // 3 per texel
@@ -421,17 +423,27 @@ template <class T> T G1_fn(int brdf, const T& c, const T& a) {
   return 2.0 / (1.0 + erf(x) + exp(-x * x) / (x * std::sqrt(PI)));
 }
 
+// Fresnel factor of the specular lobe at cos(theta_d) = wi . h: held at its
+// normal-incidence value ks (fresnel = 0), or Schlick's approximation with
+// F0 = ks (fresnel = 1): ks + (1 - ks) (1 - cos theta_d)^5, which reaches 1 at
+// grazing and equals ks where wi = wo = h.
+template <class T> T fresnel_fn(int fresnel, const T& ks, const T& cih) {
+  if (fresnel == 0) return ks;
+  T x = 1.0 - cih;
+  T x2 = x * x;
+  return ks + (1.0 - ks) * (x2 * x2 * x);
+}
+
 // f(wi, wo) for unit n, wi, wo; zero unless both cosines are positive.
 template <class T>
-void brdf_eval(int brdf, const MatT<T>& m, const V3<T>& n, const V3<T>& wi, const V3<T>& wo, T f[3]) {
+void brdf_eval(int brdf, int fresnel, const MatT<T>& m, const V3<T>& n, const V3<T>& wi, const V3<T>& wo, T f[3]) {
   T ci = dot(n, wi), co = dot(n, wo);
   if (!(vv(ci) > 0) || !(vv(co) > 0)) { f[0] = f[1] = f[2] = T(0.0); return; }
   V3<T> h = nrm(wi + wo);
   T ch = dot(n, h), cih = dot(wi, h);
-  (void)cih;
   T a = clamp_alpha(m.alpha);
   T spec = D_fn(brdf, ch, a) * G1_fn(brdf, ci, a) * G1_fn(brdf, co, a) / (4.0 * ci * co);
-  for (int c = 0; c < 3; ++c) f[c] = m.kd[c] / PI + m.ks[c] * spec;
+  for (int c = 0; c < 3; ++c) f[c] = m.kd[c] / PI + fresnel_fn(fresnel, m.ks[c], cih) * spec;
 }
 
 double brdf_pdf(int brdf, const Mat& m, const V3d& n, const V3d& wi, const V3d& wo) {
@@ -889,7 +901,7 @@ void secondary_edge(const Scene& s, const Rng& rng, int B, const Lights& lt, int
   for (int side = 0; side < 2; ++side) {
     V3d ws = nrm(w + scl(mh, side == 0 ? -SEC_EPS : SEC_EPS));
     double f[3], Li[3];
-    brdf_eval(s.brdf, m, ns, ws, wo, f);
+    brdf_eval(s.brdf, s.fresnel, m, ns, ws, wo, f);
     double ci = dot(ns, ws);
     if (s.smooth && !(dot(nv, ws) > 0)) ci = 0;
     trace_path<double>(s, rng, B, lt, pv, ws, c0, c1, 16u + (uint32_t)b, nullptr, Li, segments, nullptr, nullptr, b + 1,
@@ -1054,7 +1066,7 @@ void trace_path(const Scene& s, const Rng& rng, int B, const Lights& lt, const V
       if (occluded(s, pv, val(wi), h.tri, vv(dist) - T_EPS)) continue;
       vis |= 1u << j;
       T f[3];
-      brdf_eval(s.brdf, m, ns, wi, wo, f);
+      brdf_eval(s.brdf, s.fresnel, m, ns, wi, wo, f);
       T g = ci / (dist * dist);
       for (int c = 0; c < 3; ++c) L[c] = L[c] + thr[c] * f[c] * g * comp(lt.I[j], c);
     }
@@ -1088,7 +1100,7 @@ void trace_path(const Scene& s, const Rng& rng, int B, const Lights& lt, const V
             pe = tp.take(pe);
             w = tp.take(w);
             T f[3];
-            brdf_eval(s.brdf, m, ns, lift<T>(wi), wo, f);
+            brdf_eval(s.brdf, s.fresnel, m, ns, lift<T>(wi), wo, f);
             for (int c = 0; c < 3; ++c) L[c] = L[c] + thr[c] * f[c] * ci * (s.env[3 * tx + c] * w / pe);
           }
         }
@@ -1115,7 +1127,7 @@ void trace_path(const Scene& s, const Rng& rng, int B, const Lights& lt, const V
     if (!(pdf > 0)) return;
     T f[3];
     V3<T> wiT = lift<T>(wi);
-    brdf_eval(s.brdf, m, ns, wiT, wo, f);
+    brdf_eval(s.brdf, s.fresnel, m, ns, wiT, wo, f);
     T ci = dot(ns, wiT);
     for (int c = 0; c < 3; ++c) thr[c] = thr[c] * f[c] * ci / pdf;
     o = p; d = wi; origin = h.tri; last_pdf = pdf;
@@ -1138,6 +1150,8 @@ bool load_scene(const orc_scene* in, Scene& s) {
   s.np = in->param_width;
   if (in->smooth_normals != 0 && in->smooth_normals != 1) return false;
   s.smooth = in->smooth_normals == 1;
+  if (in->fresnel != 0 && in->fresnel != 1) return false;
+  s.fresnel = in->fresnel;
   s.vf_start.assign((size_t)s.nv + 1, 0);
   for (int v : s.face) ++s.vf_start[(size_t)v + 1];
   for (int v = 0; v < s.nv; ++v) s.vf_start[(size_t)v + 1] += s.vf_start[v];
@@ -1290,13 +1304,14 @@ static Mat mat_from(const double* p5) {
   return m;
 }
 
-void orc_brdf_eval(int brdf, const double* p5, const double* n, const double* wi, const double* wo, double* out) {
+void orc_brdf_eval(int brdf, int fresnel, const double* p5, const double* n, const double* wi, const double* wo,
+                   double* out) {
   Mat m = mat_from(p5);
   MatT<double> mt;
   for (int c = 0; c < 3; ++c) { mt.kd[c] = m.kd[c]; mt.ks[c] = m.ks[c]; }
   mt.alpha = m.alpha;
   V3d N{n[0], n[1], n[2]}, I{wi[0], wi[1], wi[2]}, O{wo[0], wo[1], wo[2]};
-  brdf_eval(brdf, mt, N, I, O, out);
+  brdf_eval(brdf, fresnel, mt, N, I, O, out);
 }
 
 double orc_brdf_pdf(int brdf, const double* p5, const double* n, const double* wi, const double* wo) {

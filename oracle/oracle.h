@@ -45,6 +45,7 @@ typedef struct {
                                 roughness); gradients use the same layout */
   int smooth_normals;        /* 0: flat face normals; 1: shading normals interpolated from vertex normals
                                 (each the normalised sum of its faces' e1 x e2), oracle.cpp states the rules */
+  int fresnel;               /* 0: Fresnel factor held at ks; 1: Schlick's approximation with F0 = ks */
 } orc_scene;
 
 typedef struct {
@@ -128,8 +129,8 @@ void orc_microfacet(int brdf, double alpha, double c, double* D, double* G1);
 void orc_closest_hit(const orc_scene* s, const double* rays, int n, int exclude_tri,
                      int* out_tri, double* out_t);
 
-/* BRDF value (RGB) times nothing: f(wi, wo) for normal n; out [3]. */
-void orc_brdf_eval(int brdf, const double* params5, const double* n, const double* wi,
+/* BRDF value (RGB) times nothing: f(wi, wo) for normal n; out [3]. fresnel as in orc_scene. */
+void orc_brdf_eval(int brdf, int fresnel, const double* params5, const double* n, const double* wi,
                    const double* wo, double* out);
 /* Mixture sampling pdf (solid angle) of direction wi. */
 double orc_brdf_pdf(int brdf, const double* params5, const double* n, const double* wi,

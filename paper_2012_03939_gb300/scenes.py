@@ -55,6 +55,7 @@ class Scene:
     target_vertices: Optional[np.ndarray] = None  # perturbed copy used to render a target
     color_res: int = 0              # mesh-colors resolution r: face_params has F*(r+1)(r+2)/2 texel rows
     smooth_normals: bool = False    # shading normals interpolated from vertex normals (flat face normals if False)
+    fresnel: int = 0                # 0: Fresnel factor held at ks; 1: Schlick's approximation with F0 = ks
 
     @property
     def n_pixels(self) -> int:
