@@ -57,6 +57,8 @@ typedef enum {
 #define ST_BRDF_BECKMANN 1
 #define ST_EDGE_SILHOUETTE 0  /* edges whose two faces face opposite ways, and boundary edges */
 #define ST_EDGE_ALL 1         /* every mesh edge (also the shading discontinuities of flat faces) */
+#define ST_FRESNEL_HELD 0      /* st_scene_desc.fresnel: specular lobe scaled by ks at every angle */
+#define ST_FRESNEL_SCHLICK 1   /* st_scene_desc.fresnel: Schlick's Fresnel factor with F0 = ks */
 #define ST_BVH_PLOC 0   /* tree by locally-ordered clustering (Meister and Bittner 2018): lower traversal cost */
 #define ST_BVH_LBVH 1   /* Karras radix tree over the Morton order: faster build */
 #define ST_EDGE_TERM_PRIMARY 1    /* edge_term bit: primary visibility (image-space edges) */
@@ -133,6 +135,11 @@ typedef struct {
                                 normal toward the incoming ray. Lights, environment samples and sampled
                                 directions count only above both the face's and the shading plane. Gradients
                                 reach every vertex around a hit face. */
+  int fresnel;               /* Fresnel factor of the Torrance-Sparrow specular lobe (Sec. 3.3
+                                "Representation"): ST_FRESNEL_HELD (0, default) keeps it at ks at every angle,
+                                so ks = 0 is exactly Lambertian; ST_FRESNEL_SCHLICK (1) takes Schlick's
+                                approximation with F0 = ks per channel, F = ks + (1 - ks)(1 - wi.h)^5, h the
+                                half vector. Sampling (lobe probability, pdfs) is the same in both. */
 } st_scene_desc;
 
 typedef struct {
@@ -188,9 +195,19 @@ typedef struct {
   int host_syncs;             /* host synchronisations of the last call (per-view mode reads queue counts back) */
 } st_stats;
 
-/* Create a scene: copies the mesh into scene-owned device memory, builds the
- * LBVH (Morton codes, radix sort, Karras hierarchy, bottom-up boxes), the edge
- * list and the environment alias table. Synchronises `stream` once. */
+/* Create a scene from the reconstruction's state (Sec. 3.1 "Input": a
+ * triangle mesh of vertex positions x, lit by point lights or an HDR
+ * environment map; Sec. 3.3 "Representation": a Torrance-Sparrow material per
+ * facet, or mesh colors at resolution r). Copies the mesh and the texel
+ * parameters into scene-owned device memory, checks them on the host (face
+ * indices in range, no repeated index in a face, finite vertices, lights and
+ * environment valid), builds the BVH (Morton codes, radix sort, then PLOC
+ * clustering or Karras' radix tree, bottom-up boxes, 4-wide collapse), the edge
+ * list and the environment's FP64 alias table. *out receives the handle, owned
+ * by the library until st_scene_destroy. Errors: ST_ERR_INVALID_ARG (bad
+ * description), ST_ERR_UNSUPPORTED (beyond the limits), ST_ERR_OOM (device
+ * memory), ST_ERR_CUDA; on any error *out is NULL and nothing is held.
+ * Synchronises `stream`. */
 st_status st_scene_create(const st_scene_desc* desc, void* stream, st_scene** out);
 
 /* Free everything the scene owns. NULL is accepted. */
@@ -207,15 +224,27 @@ st_status st_rebuild(st_scene* scene, const float* new_vertices, void* stream);
 /* New texel parameters (device float [F*n][5 or 7], see st_scene_desc); the material update (Sec. 3.3). */
 st_status st_set_face_params(st_scene* scene, const float* face_params, void* stream);
 
-/* Forward render of n_views views (host array, 1..ST_MAX_VIEWS) with max_bounces
- * surface vertices per path (1..ST_MAX_BOUNCES). out_image: device float [N][3], N =
- * max over views of pixel_offset + W*H; it is overwritten on every pixel of
- * the views (other rows untouched). opts may be NULL (batched, graph on). */
+/* The renderer R(x, m, c_i) of the paper's loss (Sec. 3.2 "Vertex
+ * optimization": the images of the current reconstruction seen from the
+ * cameras c_i; Sec. 3.3 "Effects of Global Illumination": multi-bounce
+ * transport). Monte Carlo forward render of n_views views (host array,
+ * 1..ST_MAX_VIEWS) with max_bounces surface vertices per path
+ * (1..ST_MAX_BOUNCES). out_image: caller-owned device float [N][3], N = max
+ * over views of pixel_offset + W*H, row-major per view; it is overwritten on
+ * every pixel of the views (other rows untouched). opts may be NULL (batched,
+ * graph on). Asynchronous on `stream`. Errors: ST_ERR_INVALID_ARG (bad views,
+ * overlapping pixel ranges, no light), ST_ERR_UNSUPPORTED, ST_ERR_OOM, ST_ERR_CUDA;
+ * a kernel's latched error is reported by st_get_stats (device_error). */
 st_status st_render(st_scene* scene, const st_view* views, int n_views, int default_spp,
                     int max_bounces, unsigned long long seed, const st_render_opts* opts,
                     float* out_image, void* stream);
 
-/* Adjoint: given dL/dI (device float [N][3], same layout as out_image),
+/* The gradient the paper descends (Sec. 3.2 "Vertex optimization": the loss
+ * over the views c_i differentiated with respect to the vertex positions x,
+ * through Li et al.'s edge sampling for visibility; Sec. 3.3 "Material
+ * Optimization": the same loss with respect to the material). The loss itself
+ * stays with the caller, who passes dL/dI. Errors as st_render.
+ * Adjoint: given dL/dI (device float [N][3], same layout as out_image),
  * ACCUMULATE (+=) dL/dvertices into d_vertices (device float [V][3]) and
  * dL/dtexel-parameters into d_face_params (device float [F*n][5 or 7], as the scene's layout). The interior term
  * replays the forward paths of the same seed and sweeps each in reverse; the
@@ -263,7 +292,9 @@ st_status st_debug_bvh(st_scene* scene, float* nodes, int* leaf_faces);
  * leaf_faces device int [F] (face id of each leaf, Morton order).
  * Limits and behaviour:
  *  - F <= 65536, else ST_ERR_UNSUPPORTED; face indices are checked on the
- *    device first (ST_ERR_INVALID_ARG), which synchronises `stream` once.
+ *    device first (ST_ERR_INVALID_ARG), and the build's device error word is
+ *    read back at the end (ST_ERR_DEVICE when the bottom-up pass found a
+ *    malformed tree): each call synchronises `stream` twice.
  *  - The first call on a device looks up the scratch array's device address
  *    (cudaGetSymbolAddress); make that first call before any stream capture.
  *  - Every call shares the one scratch array: calls that overlap on the GPU

@@ -11,9 +11,20 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "st_kernels.cuh"
 
 namespace st {
+
+// NVTX range for the lifetime of a scope: names the host-side enqueue of each
+// call and wavefront stage for profilers (a captured graph replays as one range)
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
 
 static thread_local std::string g_err;
 void set_error(const std::string& msg) { g_err = msg; }
@@ -405,7 +416,7 @@ KCtx make_ctx(st_scene* s, const Plan& p) {
   KCtx c;
   c.V = s->verts; c.F = s->faces; c.P = s->params; c.nodes = s->nodes4; c.tri = s->tri; c.nf = s->nf; c.n4 = s->n4;
   c.lights = s->lights; c.nl = s->nl; c.nlt = s->nl + p.max_vl; c.NS = c.nlt + (s->env.w > 0 ? 1 : 0);
-  c.env = s->env; c.brdf = s->brdf; c.res = s->res; c.ntex = s->ntex; c.np = s->np;
+  c.env = s->env; c.brdf = s->brdf; c.fresnel = s->fresnel; c.res = s->res; c.ntex = s->ntex; c.np = s->np;
   c.edge_v = s->edge_v; c.edge_f = s->edge_f; c.n_edges = s->n_edges; c.edge_mode = p.o.edge_mode;
   c.edge_flag = s->edge_flag; c.edge_cand = s->edge_cand; c.edge_ncand = s->edge_ncand;
   c.sh_cand = s->sh_cand; c.sh_ncand = s->sh_ncand;
@@ -508,6 +519,7 @@ st_status run_chunk(st_scene* s, const Plan& p, const KCtx& c, long long j0, int
         gb = std::min(gb, ge);
         gs = (q + 255) / 256;
       }
+      Range rb(b == 0 ? "bounce 0" : b == 1 ? "bounce 1" : "bounce 2+");
       if (timing) ST_CUDA(cudaEventRecord(next_event(s, 0, true), st));
       if (b == 0 && bins) {
         // the BVH launch takes the rays the bins kernel queued (a persistent grid: the count stays on the device)
@@ -543,6 +555,7 @@ st_status run_chunk(st_scene* s, const Plan& p, const KCtx& c, long long j0, int
     }
     return ST_OK;
   };
+  Range rc("chunk");
   k_reset<<<1, 128, 0, st>>>(cnt);
   bool has_shadow = p.shadow && overlaps(p, 2, j0, j0 + n);
   if (has_shadow) { k_sh_prep<<<(n + EXT_BLOCK - 1) / EXT_BLOCK, EXT_BLOCK, 0, st>>>(c, j0, n); s->launches++; }
@@ -551,6 +564,7 @@ st_status run_chunk(st_scene* s, const Plan& p, const KCtx& c, long long j0, int
   s->launches += 2;
   st_status r = bounces(c, p.B, p.bins);
   if (r != ST_OK) return r;
+  Range rr(p.kind == 0 ? "resolve" : "adjoint");
   if (p.kind == 0) {
     k_resolve<<<(n + RESOLVE_BLOCK - 1) / RESOLVE_BLOCK, RESOLVE_BLOCK, 0, st>>>(c, j0, n);
     s->launches++;
@@ -577,6 +591,7 @@ st_status run_chunk(st_scene* s, const Plan& p, const KCtx& c, long long j0, int
       cs.e.records = false;
       for (int ps = 0; ps < passes; ++ps) {
         k_reset_pass<<<1, 128, 0, st>>>(cnt);
+        Range rs("secondary edge pass");
         k_sec_raygen<<<std::min((Q + 255) / 256, 4 * sm), 256, 0, st>>>(cs, ps);
         s->launches += 2;
         r = bounces(cs, std::max(1, p.B - 1), false);
@@ -626,6 +641,7 @@ st_status enqueue_body(st_scene* s, const Plan& p, const KCtx& c, int Q, cudaStr
     s->launches += 1 + s->et_L;
   }
   if (p.bins) {
+    Range r("primary bins");
     // primary-visibility bins of every view: count, scan, fill
     long long P = p.pixels;
     int nv = (int)p.views.size();
@@ -652,6 +668,7 @@ st_status enqueue_body(st_scene* s, const Plan& p, const KCtx& c, int Q, cudaStr
     s->launches += 2;
   }
   if (p.edges) {
+    Range r("edge candidates");
     dim3 g((s->n_edges + 255) / 256, (unsigned)p.views.size());
     k_edge_flags<<<g, 256, 0, st>>>(c, (int)p.views.size());
     k_edge_compact<<<(unsigned)p.views.size(), 1024, 0, st>>>(c);
@@ -942,6 +959,7 @@ st_status st_scene_create(const st_scene_desc* d, void* stream, st_scene** out) 
   if (d->bvh_builder != ST_BVH_PLOC && d->bvh_builder != ST_BVH_LBVH) return fail(ST_ERR_INVALID_ARG, "unknown bvh_builder");
   if (d->color_res < 0 || d->color_res > 64) return fail(ST_ERR_UNSUPPORTED, "mesh-colors resolution must be in [0, 64]");
   if (d->smooth_normals != 0 && d->smooth_normals != 1) return fail(ST_ERR_INVALID_ARG, "smooth_normals must be 0 or 1");
+  if (d->fresnel != ST_FRESNEL_HELD && d->fresnel != ST_FRESNEL_SCHLICK) return fail(ST_ERR_INVALID_ARG, "unknown fresnel");
   if ((long long)d->n_faces * (d->color_res + 1) * (d->color_res + 2) / 2 > (1LL << 30))
     return fail(ST_ERR_UNSUPPORTED, "too many mesh-colors texels");
   if (d->n_point_lights < 0 || d->n_point_lights > ST_MAX_LIGHTS || (d->n_point_lights > 0 && !d->point_lights))
@@ -966,6 +984,7 @@ st_status st_scene_create(const st_scene_desc* d, void* stream, st_scene** out) 
   s->builder = d->bvh_builder;
   s->np = d->rgb_specular ? 7 : 5;
   s->smooth = d->smooth_normals == 1;
+  s->fresnel = d->fresnel;
   s->ntex = (s->res + 1) * (s->res + 2) / 2;
   // host copy of the faces: validation and edge list
   std::vector<int> hf(3 * (size_t)s->nf);
@@ -1116,6 +1135,7 @@ st_status st_set_face_params(st_scene* s, const float* p, void* stream) {
 
 st_status st_render(st_scene* s, const st_view* views, int n_views, int default_spp, int max_bounces,
                     unsigned long long seed, const st_render_opts* opts, float* out_image, void* stream) {
+  Range range("st_render");
   if (!s || !out_image) return fail(ST_ERR_INVALID_ARG, "NULL argument");
   Plan p;
   st_status r = plan_call(s, views, n_views, default_spp, max_bounces, opts, 0, false, p);
@@ -1128,6 +1148,7 @@ st_status st_render(st_scene* s, const st_view* views, int n_views, int default_
 st_status st_render_backward(st_scene* s, const st_view* views, int n_views, int default_spp, int max_bounces,
                              unsigned long long seed, const st_render_opts* opts, const float* dLdI, float* dV,
                              float* dF, void* stream) {
+  Range range("st_render_backward");
   if (!s || !dLdI) return fail(ST_ERR_INVALID_ARG, "NULL argument");
   st_render_opts o = opts ? *opts : default_opts();
   if (o.edge_term && !dV) return fail(ST_ERR_INVALID_ARG, "edge term needs d_vertices");

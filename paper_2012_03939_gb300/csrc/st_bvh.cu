@@ -226,7 +226,10 @@ __global__ void k_boxes(const float* V, const int* F, const int* ids, int n, flo
 
 cudaError_t boxes(st_scene* s, cudaStream_t stream) {
   int n = s->nf;
-  if (n > 1) cudaMemsetAsync(s->flags, 0, sizeof(int) * (n - 1), stream);
+  if (n > 1) {
+    cudaError_t e = cudaMemsetAsync(s->flags, 0, sizeof(int) * (n - 1), stream);
+    if (e != cudaSuccess) return e;
+  }
   k_boxes<<<(n + 255) / 256, 256, 0, stream>>>(s->verts, s->faces, s->ids, n, s->tri, s->nodes, s->parent, s->flags,
                                                 s->d_err);
   return cudaGetLastError();

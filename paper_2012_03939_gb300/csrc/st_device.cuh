@@ -243,7 +243,17 @@ __device__ __forceinline__ float G1_eval(int brdf, float c, float a, float* dc =
 }
 
 // Q = f(wi, wo) * cos(n, wi), RGB; zero unless both cosines are positive.
-__device__ __forceinline__ float3 brdf_cos(int brdf, const Mat& m, float3 n, float3 wi, float3 wo) {
+// (1 - wi.h)^5 of Schlick's Fresnel approximation F = ks + (1 - ks) x^5 (fr = 1); with fr = 0 the factor is
+// held at ks, which x5 = 0 gives.
+__device__ __forceinline__ float fresnel_x5(int fr, float cih) {
+  if (!fr) return 0.0f;
+  float x = 1.0f - cih, x2 = x * x;
+  return x2 * x2 * x;
+}
+
+// f(wi, wo) cos(n, wi): kd/pi cos + F D G1(i) G1(o) / (4 cos_o), F per channel (held at ks, or Schlick with
+// F0 = ks when fr = 1).
+__device__ __forceinline__ float3 brdf_cos(int brdf, int fr, const Mat& m, float3 n, float3 wi, float3 wo) {
   float ci = dot3(n, wi), co = dot3(n, wo);
   if (!(ci > 0.0f) || !(co > 0.0f)) return mk3(0, 0, 0);
   float3 h = norm3(wi + wo);
@@ -251,8 +261,11 @@ __device__ __forceinline__ float3 brdf_cos(int brdf, const Mat& m, float3 n, flo
   bool cl;
   float a = clamp_alpha(m.alpha, cl);
   float spec = D_eval(brdf, ch, a) * G1_eval(brdf, ci, a) * G1_eval(brdf, co, a) / (4.0f * co);
+  float x5 = fresnel_x5(fr, dot3(wi, h));
   float kdc = ci * (1.0f / PI_F);
-  return mk3(m.kd[0] * kdc + m.ks[0] * spec, m.kd[1] * kdc + m.ks[1] * spec, m.kd[2] * kdc + m.ks[2] * spec);
+  return mk3(m.kd[0] * kdc + (m.ks[0] + (1.0f - m.ks[0]) * x5) * spec,
+             m.kd[1] * kdc + (m.ks[1] + (1.0f - m.ks[1]) * x5) * spec,
+             m.kd[2] * kdc + (m.ks[2] + (1.0f - m.ks[2]) * x5) * spec);
 }
 
 // One-sample lobe-mixture pdf (solid angle) of direction wi.
@@ -321,8 +334,10 @@ __device__ __forceinline__ float brdf_sample(int brdf, const Mat& m, float3 n, f
 
 // Adjoint of Q = f(wi, wo) cos(n, wi) for an RGB output weight gw:
 // accumulates dn, dwi (if non-null) and d params (kd_r, kd_g, kd_b, ks_r, ks_g, ks_b, alpha).
-__device__ __forceinline__ void brdf_cos_adj(int brdf, const Mat& m, float3 n, float3 wi, float3 wo, float3 gw,
-                                             float3& dn, float3* dwi, float dm[7]) {
+// With Schlick's factor (fr = 1), F_c = ks_c + (1 - ks_c) x^5, x = 1 - wi.h: dF_c/dks_c = 1 - x^5, and F
+// moves with wi through wi.h: d(wi.h)/dwi = h + (wi - h (wi.h)) / |wi + wo| (wo is a fixed direction).
+__device__ __forceinline__ void brdf_cos_adj(int brdf, int fr, const Mat& m, float3 n, float3 wi, float3 wo,
+                                             float3 gw, float3& dn, float3* dwi, float dm[7]) {
   float ci = dot3(n, wi), co = dot3(n, wo);
   if (!(ci > 0.0f) || !(co > 0.0f)) return;
   float3 hu = wi + wo;
@@ -335,15 +350,19 @@ __device__ __forceinline__ void brdf_cos_adj(int brdf, const Mat& m, float3 n, f
   float D = D_eval(brdf, ch, a, &Dc, &Da);
   float Gi = G1_eval(brdf, ci, a, &Gic, &Gia);
   float Go = G1_eval(brdf, co, a, &Goc, &Goa);
-  float gs = gw.x * m.ks[0] + gw.y * m.ks[1] + gw.z * m.ks[2];   // output weight times specular colour
+  float cih = dot3(wi, h);
+  float x5 = fresnel_x5(fr, cih);
+  float F0 = m.ks[0] + (1.0f - m.ks[0]) * x5, F1 = m.ks[1] + (1.0f - m.ks[1]) * x5,
+        F2 = m.ks[2] + (1.0f - m.ks[2]) * x5;
+  float gs = gw.x * F0 + gw.y * F1 + gw.z * F2;   // output weight times the lobe's colour
   float inv4co = 1.0f / (4.0f * co);
   float S = D * Gi * Go * inv4co;
   dm[0] += gw.x * ci * (1.0f / PI_F);
   dm[1] += gw.y * ci * (1.0f / PI_F);
   dm[2] += gw.z * ci * (1.0f / PI_F);
-  dm[3] += gw.x * S;
-  dm[4] += gw.y * S;
-  dm[5] += gw.z * S;
+  dm[3] += gw.x * S * (1.0f - x5);
+  dm[4] += gw.y * S * (1.0f - x5);
+  dm[5] += gw.z * S * (1.0f - x5);
   if (!cl) dm[6] += gs * (Da * Gi * Go + D * Gia * Go + D * Gi * Goa) * inv4co;
   float dci = (gw.x * m.kd[0] + gw.y * m.kd[1] + gw.z * m.kd[2]) * (1.0f / PI_F) + gs * D * Gic * Go * inv4co;
   float dco = gs * D * Gi * (Goc * co - Go) * inv4co / co;
@@ -351,6 +370,14 @@ __device__ __forceinline__ void brdf_cos_adj(int brdf, const Mat& m, float3 n, f
   dn += wi * dci + wo * dco + h * dch;
   if (dwi) {
     float3 dh = n * dch;
+    if (fr) {
+      // dQ/d(wi.h) = -5 x^4 S sum_c gw_c (1 - ks_c); wi.h = wi . h reaches wi directly and through h
+      float x = 1.0f - cih, x2 = x * x;
+      float dcih = -5.0f * x2 * x2 * S *
+                   (gw.x * (1.0f - m.ks[0]) + gw.y * (1.0f - m.ks[1]) + gw.z * (1.0f - m.ks[2]));
+      *dwi += h * dcih;
+      dh += wi * dcih;
+    }
     float3 dhu = (dh - h * dot3(dh, h)) * (1.0f / hl);
     *dwi += n * dci + dhu;
   }

@@ -95,6 +95,7 @@ struct st_scene {
   bool closed = false;           // one surface; every edge has two faces that traverse it in opposite directions
   st::MeshStat* mstat = nullptr; // signed volume and vertex bounds, recomputed on the device after each update
   bool smooth = false;           // interpolated shading normals
+  int fresnel = 0;               // ST_FRESNEL_HELD or ST_FRESNEL_SCHLICK
   float4* vnrm = nullptr;        // [V] vertex normal N_v and |M_v| (smooth), recomputed with mstat
   int* vf_start = nullptr;       // [V + 1] faces around each vertex (CSR, face order)
   int* vf_list = nullptr;        // [3F]

@@ -32,6 +32,7 @@ struct KCtx {
   int nl, nlt, NS;        // scene lights, + the most any view of the call adds, + environment
   DevEnv env;
   int brdf;
+  int fresnel;            // 1: Schlick's Fresnel factor (F0 = ks); 0: held at ks
   int res, ntex;          // mesh-colors resolution r and texels per face
   int np;                 // parameters per texel in the caller's layout: 5 (scalar ks) or 7 (RGB ks)
   const int2* edge_v;
@@ -854,7 +855,7 @@ __global__ void k_shade(KCtx c, int b) {
         float ci = dot3(n, wi);
         bool valid = j < nlp && ci > 0.0f && dist > 2.0f * T_EPS && (!c.smooth || dot3(ns, wi) > 0.0f);
         float3 cc = mk3(0, 0, 0);
-        if (valid) cc = mul(mul(T, brdf_cos(c.brdf, m, ns, wi, wo)), xyz(li)) * (1.0f / (dist * dist));
+        if (valid) cc = mul(mul(T, brdf_cos(c.brdf, c.fresnel, m, ns, wi, wo)), xyz(li)) * (1.0f / (dist * dist));
         E.sh_dir[j * Q + slot] = make_float4(wi.x, wi.y, wi.z, dist - T_EPS);
         E.sh_c[j * Q + slot] = make_float4(cc.x, cc.y, cc.z, valid ? 1.0f : 0.0f);
         sh_any |= valid;
@@ -882,7 +883,7 @@ __global__ void k_shade(KCtx c, int b) {
             w = pe * pe / (pe * pe + pb * pb);
           }
           escale = mk3(te.x, te.y, te.z) * (w / pe);
-          cc = mul(mul(T, brdf_cos(c.brdf, m, ns, ewi, wo)), escale);
+          cc = mul(mul(T, brdf_cos(c.brdf, c.fresnel, m, ns, ewi, wo)), escale);
           flags |= ENV_VALID;
         }
         E.sh_dir[c.nlt * Q + slot] = make_float4(ewi.x, ewi.y, ewi.z, __int_as_float(0x7f800000));
@@ -902,7 +903,7 @@ __global__ void k_shade(KCtx c, int b) {
         if (c.smooth && pdf > 0.0f && !(dot3(n, wi) > 0.0f)) pdf = 0.0f;   // below the face
         if (c.sig) sig_mix(hs, (unif(u.x) < lobe_prob(m) ? 1u : 0u) | (pdf > 0.0f ? 2u : 0u));
         if (pdf > 0.0f) {
-          float3 Qv = brdf_cos(c.brdf, m, ns, wi, wo);
+          float3 Qv = brdf_cos(c.brdf, c.fresnel, m, ns, wi, wo);
           T = mul(T, Qv) * (1.0f / pdf);
           E.thr[slot] = make_float4(T.x, T.y, T.z, 0.0f);
           E.d[slot] = make_float4(wi.x, wi.y, wi.z, pdf);
@@ -1085,7 +1086,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_adjoint(KCtx c, long long j0, int
     float sg = dot3(ng, wo) < 0.0f ? -1.0f : 1.0f;
     float3 nn = SMOOTH ? shading_normal(c, f, xyz(r0), v0, v1, v2, sg) : ng * sg;
     int tex = __float_as_int(E.r3[b * Q + i].w);
-    float3 Qv = brdf_cos(c.brdf, fetch_mat(c.P, tex), nn, xyz(r1n), wo);
+    float3 Qv = brdf_cos(c.brdf, c.fresnel, fetch_mat(c.P, tex), nn, xyz(r1n), wo);
     T[b + 1] = mul(T[b], Qv) * (1.0f / r1n.w);
   }
   bool esc = nbv > 0 && E.esc[i].w != 0.0f;
@@ -1138,11 +1139,11 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_adjoint(KCtx c, long long j0, int
         float r = len3(l);
         float3 wi = l * (1.0f / r);
         float ir2 = 1.0f / (r * r);
-        float3 Qv = brdf_cos(c.brdf, m, nn, wi, wo);
+        float3 Qv = brdf_cos(c.brdf, c.fresnel, m, nn, wi, wo);
         C += mul(Qv, xyz(li)) * ir2;
         float3 gw = mul(gC, xyz(li)) * ir2;
         float3 dwi = mk3(0, 0, 0);
-        brdf_cos_adj(c.brdf, m, nn, wi, wo, gw, Nb, &dwi, dm);
+        brdf_cos_adj(c.brdf, c.fresnel, m, nn, wi, wo, gw, Nb, &dwi, dm);
         float sr = gC.x * Qv.x * li.x + gC.y * Qv.y * li.y + gC.z * Qv.z * li.z;
         float rbar = sr * (-2.0f * ir2 / r);
         float3 lbar = (dwi - wi * dot3(dwi, wi)) * (1.0f / r) + wi * rbar;
@@ -1150,16 +1151,16 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_adjoint(KCtx c, long long j0, int
       }
       if (flags & ENV_VIS) {
         float3 wi = xyz(r2), sc = xyz(r3);
-        C += mul(brdf_cos(c.brdf, m, nn, wi, wo), sc);
-        brdf_cos_adj(c.brdf, m, nn, wi, wo, mul(gC, sc), Nb, nullptr, dm);
+        C += mul(brdf_cos(c.brdf, c.fresnel, m, nn, wi, wo), sc);
+        brdf_cos_adj(c.brdf, c.fresnel, m, nn, wi, wo, mul(gC, sc), Nb, nullptr, dm);
       }
       float3 w = mk3(0, 0, 0);
       if (b + 1 < nbv || esc) {
         float4 r1n = E.r1[(b + 1) * Q + i];
         float ip = 1.0f / r1n.w;
         float3 wi = xyz(r1n);
-        w = brdf_cos(c.brdf, m, nn, wi, wo) * ip;
-        brdf_cos_adj(c.brdf, m, nn, wi, wo, mul(A, T[b]) * ip, Nb, nullptr, dm);
+        w = brdf_cos(c.brdf, c.fresnel, m, nn, wi, wo) * ip;
+        brdf_cos_adj(c.brdf, c.fresnel, m, nn, wi, wo, mul(A, T[b]) * ip, Nb, nullptr, dm);
       }
       A = mul(g, C) + mul(A, w);
       // n = sgn * m / |m|, p = o + t d with t = ((v0 - o) . m) / (d . m)
@@ -1574,7 +1575,7 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_sec_gen(KCtx c, long long j0, int
       if (b + 1 < nbv) {
         float4 r1n = E.r1[(b + 1) * Q + i];
         int tex = __float_as_int(E.r3[b * Q + i].w);
-        Tn = mul(T, brdf_cos(c.brdf, fetch_mat(c.P, tex), ns, xyz(r1n), wo)) * (1.0f / r1n.w);
+        Tn = mul(T, brdf_cos(c.brdf, c.fresnel, fetch_mat(c.P, tex), ns, xyz(r1n), wo)) * (1.0f / r1n.w);
       }
     }
     int q = warp_append(&E.cnt[CNT_SEC], ok);
@@ -1623,7 +1624,7 @@ __global__ void k_sec_raygen(KCtx c, int pass) {
       float3 nn, ns;
       vertex_normals(c, f, xyz(a), wo, nn, ns);
       float3 ws = norm3(xyz(w) + xyz(m) * ((sidx & 32) ? SEC_EPS : -SEC_EPS));
-      float3 thr = brdf_cos(c.brdf, fetch_mat(c.P, __float_as_int(E.r3[b * Q + slot].w)), ns, ws, wo);
+      float3 thr = brdf_cos(c.brdf, c.fresnel, fetch_mat(c.P, __float_as_int(E.r3[b * Q + slot].w)), ns, ws, wo);
       if (c.smooth && !(dot3(nn, ws) > 0.0f)) thr = mk3(0, 0, 0);   // below the face
       E.rad[i] = make_float4(0, 0, 0, 0);
       if (thr.x > 0.0f || thr.y > 0.0f || thr.z > 0.0f) {

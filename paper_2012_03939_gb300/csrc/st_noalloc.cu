@@ -128,9 +128,16 @@ extern "C" st_status st_build_bvh_noalloc(const float* vertices, const int* face
   s.sort_blocks = sort_blocks_for(n_faces);
   e = bvh_build(&s, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(leaf_faces, s.ids, sizeof(int) * n_faces, cudaMemcpyDeviceToDevice, st);
+  // the bottom-up box pass latches an error bit in the same word when the tree it walks is malformed
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     set_error(std::string("st_build_bvh_noalloc: ") + cudaGetErrorString(e));
     return ST_ERR_CUDA;
+  }
+  if (herr) {
+    set_error("st_build_bvh_noalloc: the build latched device error bits " + std::to_string(herr));
+    return ST_ERR_DEVICE;
   }
   return ST_OK;
 }

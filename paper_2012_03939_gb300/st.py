@@ -25,6 +25,7 @@ MODE_BATCHED, MODE_PER_VIEW = 0, 1
 EDGE_SILHOUETTE, EDGE_ALL = 0, 1
 EDGE_TERM_PRIMARY, EDGE_TERM_SECONDARY, EDGE_TERM_SHADOW = 1, 2, 4
 BVH_PLOC, BVH_LBVH = 0, 1
+FRESNEL_HELD, FRESNEL_SCHLICK = 0, 1
 
 EXPORTED = ["st_scene_create", "st_scene_destroy", "st_refit", "st_rebuild", "st_set_face_params", "st_render",
             "st_render_backward", "st_trace_closest", "st_get_stats", "st_debug_bvh", "st_build_bvh_noalloc",
@@ -60,7 +61,7 @@ class SceneDesc(C.Structure):
     _fields_ = [("n_vertices", C.c_int), ("n_faces", C.c_int), ("vertices", C.c_void_p), ("faces", C.c_void_p),
                 ("face_params", C.c_void_p), ("brdf", C.c_int), ("n_point_lights", C.c_int),
                 ("point_lights", C.c_void_p), ("env", C.c_void_p), ("color_res", C.c_int), ("bvh_builder", C.c_int),
-                ("rgb_specular", C.c_int), ("smooth_normals", C.c_int)]
+                ("rgb_specular", C.c_int), ("smooth_normals", C.c_int), ("fresnel", C.c_int)]
 
 
 class RenderOpts(C.Structure):
@@ -165,11 +166,12 @@ def make_opts(**kw) -> RenderOpts:
 class Scene:
     """A mesh scene on the current CUDA device (owns a library scene handle). color_res: mesh-colors resolution
     (face_params then holds a row per texel); bvh_builder: "ploc" or "lbvh"; smooth_normals: shading normals
-    interpolated from vertex normals (recomputed by refit and rebuild) instead of flat face normals."""
+    interpolated from vertex normals (recomputed by refit and rebuild) instead of flat face normals; fresnel:
+    "held" (0: the specular lobe scaled by ks at every angle) or "schlick" (1: Schlick's factor, F0 = ks)."""
 
     def __init__(self, vertices: torch.Tensor, faces: torch.Tensor, face_params: torch.Tensor, brdf: str = "ggx",
                  light_pos=None, light_intensity=None, env: Optional[np.ndarray] = None, stream=None,
-                 color_res: int = 0, bvh_builder: str = "ploc", smooth_normals: bool = False):
+                 color_res: int = 0, bvh_builder: str = "ploc", smooth_normals: bool = False, fresnel=0):
         dev = torch.device("cuda", torch.cuda.current_device())
         self.vertices = vertices.detach().to(dev, torch.float32).contiguous()
         self.faces = faces.detach().to(dev, torch.int32).contiguous()
@@ -199,7 +201,8 @@ class Scene:
                          self.face_params.data_ptr(), {"ggx": 0, "beckmann": 1}[brdf], len(lp),
                          C.addressof(self._lights), None if self._env is None else C.addressof(self._env),
                          int(color_res), {"ploc": BVH_PLOC, "lbvh": BVH_LBVH}[bvh_builder],
-                         1 if self.face_params.shape[1] == 7 else 0, int(bool(smooth_normals)))
+                         1 if self.face_params.shape[1] == 7 else 0, int(bool(smooth_normals)),
+                         {"held": FRESNEL_HELD, "schlick": FRESNEL_SCHLICK}.get(fresnel, fresnel))
         h = C.c_void_p()
         _check(lib().st_scene_create(C.byref(desc), _stream(stream), C.byref(h)))
         self.handle = h
@@ -209,7 +212,8 @@ class Scene:
         V = torch.as_tensor(sc.vertices if vertices is None else vertices, dtype=torch.float32, device=device)
         return cls(V, torch.as_tensor(sc.faces, device=device), torch.as_tensor(sc.face_params, device=device),
                    sc.brdf, sc.light_pos, sc.light_intensity, sc.env, color_res=getattr(sc, "color_res", 0),
-                   smooth_normals=bool(getattr(sc, "smooth_normals", False)), **kw)
+                   smooth_normals=bool(getattr(sc, "smooth_normals", False)), fresnel=int(getattr(sc, "fresnel", 0)),
+                   **kw)
 
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:

@@ -82,7 +82,8 @@ def test_binding_constants_match_header():
              "EDGE_TERM_PRIMARY": st.EDGE_TERM_PRIMARY, "EDGE_TERM_SECONDARY": st.EDGE_TERM_SECONDARY,
              "EDGE_TERM_SHADOW": st.EDGE_TERM_SHADOW, "BVH_PLOC": st.BVH_PLOC, "BVH_LBVH": st.BVH_LBVH,
              "MAX_VIEW_LIGHTS": st.MAX_VIEW_LIGHTS, "MAX_VIEWS": st.MAX_VIEWS,
-             "SEC_PICK_TREE": st.SEC_PICK_TREE, "SEC_PICK_UNIFORM": st.SEC_PICK_UNIFORM}
+             "SEC_PICK_TREE": st.SEC_PICK_TREE, "SEC_PICK_UNIFORM": st.SEC_PICK_UNIFORM,
+             "FRESNEL_HELD": st.FRESNEL_HELD, "FRESNEL_SCHLICK": st.FRESNEL_SCHLICK}
     for k, v in pairs.items():
         assert defs[k] == v, k
 

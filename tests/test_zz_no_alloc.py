@@ -68,6 +68,26 @@ def test_noalloc_bvh_matches_allocating_build_twice_in_a_row(st):
         np.testing.assert_array_equal(tris, exp)
 
 
+def test_noalloc_leaves_free_device_memory_unchanged(st):
+    # buffers made first, then two builds: the device's free memory does not move
+    sc = S.edges()
+    _noalloc(st, sc.vertices, sc.faces)            # the first call on the device looks up the scratch address
+    n = len(sc.faces)
+    dV = torch.from_numpy(sc.vertices).cuda()
+    dF = torch.from_numpy(sc.faces).cuda()
+    nodes = torch.empty((n - 1, 16), dtype=torch.float32, device="cuda")
+    tris = torch.empty((n, 12), dtype=torch.float32, device="cuda")
+    leaf = torch.empty((n,), dtype=torch.int32, device="cuda")
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(2):
+        assert st.lib().st_build_bvh_noalloc(dV.data_ptr(), dF.data_ptr(), len(sc.vertices), n, nodes.data_ptr(),
+                                             tris.data_ptr(), leaf.data_ptr(), stream) == 0
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+
+
 def test_noalloc_refuses_oversized_and_invalid_meshes(st):
     V, F = S.uv_sphere(300, 120)                 # 71,400 faces > 65,536
     status, *_ = _noalloc(st, V, F)
