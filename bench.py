@@ -221,6 +221,20 @@ def oracle_parity(st, scene, sc, target, B, seed, fopts, bopts, edge_on, n_img=1
     exp = np.concatenate([rv.ravel(), rf.ravel()])
     out["grad_pixels"] = int(len(gp))
     out["grad_rel_err"] = float(np.linalg.norm(got - exp) / np.linalg.norm(exp))
+    # the same over the pixels whose paths took the oracle's decisions (equal path signatures): what is left
+    # when the few paths where FP32 and FP64 decided differently are set aside
+    gsame = sig[grows] == O.render_signatures(osc, prm, gp)
+    out["grad_pixels_diverged"] = int((~gsame).sum())
+    if (~gsame).any():
+        w2 = np.zeros_like(dLdI)
+        w2[grows[gsame]] = dLdI[grows[gsame]]
+        dV2, dF2 = scene.backward(sc.views, B, seed, torch.from_numpy(w2).cuda(), o_int)
+        rv2, rf2, _ = O.grad_pixels(osc, prm, gp[gsame], w2[grows[gsame]].astype(np.float64))
+        g2 = np.concatenate([dV2.cpu().numpy().ravel(), dF2.cpu().numpy().ravel()]).astype(np.float64)
+        e2 = np.concatenate([rv2.ravel(), rf2.ravel()])
+        out["grad_rel_err_equal_signatures"] = float(np.linalg.norm(g2 - e2) / np.linalg.norm(e2))
+    else:
+        out["grad_rel_err_equal_signatures"] = out["grad_rel_err"]
     if edge_on:
         dVe, _ = scene.backward(sc.views, B, seed, wt, bopts)
         ev, _ = O.edge_grad(osc, prm, w.astype(np.float64))
@@ -291,18 +305,19 @@ def source_hash():
 
 
 def profiled_traffic():
-    """DRAM bytes per closest-hit query from the committed ncu summary, if taken on the current kernel source."""
-    p = os.path.join(ROOT, "profiles", "extend_dram_traffic.txt")
+    """DRAM bytes per closest-hit and per any-hit query from the committed ncu summary, if taken on the current
+    traversal sources (else None, None)."""
+    p = os.path.join(ROOT, "profiles", "traversal_dram_traffic_batched_8views.txt")
     if not os.path.exists(p):
-        return None
+        return None, None
     kv = {}
     for ln in open(p):
         if "=" in ln and not ln.startswith("#"):
             k, v = ln.split("=", 1)
             kv[k.strip()] = v.strip()
     if kv.get("source_hash") != source_hash():
-        return None
-    return float(kv["dram_bytes_per_ray"])
+        return None, None
+    return float(kv["extend_dram_bytes_per_query"]), float(kv["shadow_dram_bytes_per_query"])
 
 
 def l2_peak_gbs(st):
@@ -424,11 +439,17 @@ def run_ours(args):
         for _ in range(args.warmup):
             step(fb, bb)
         torch.cuda.synchronize()
-        step(fb, bb)
+        scene.render(views, B, seed, fb, out=img)
+        torch.cuda.synchronize()
+        sf = scene.stats()
+        g = (img - target) * (2 * inv_n)
+        scene.backward(views, B, seed, g, bb, d_vertices=dV, d_face_params=dF)
         torch.cuda.synchronize()
         s = scene.stats()
-        print("profile step done: %d kernel launches in the last call, device_error %d" % (
-            s["kernel_launches"], s["device_error"]))
+        print("profile step done: %d + %d kernel launches, %d + %d closest-hit and %d + %d any-hit queries "
+              "(forward + adjoint), device_error %d" % (sf["kernel_launches"], s["kernel_launches"],
+                                                         sf["extension_rays"], s["extension_rays"],
+                                                         sf["shadow_rays"], s["shadow_rays"], s["device_error"]))
         scene.close()
         return
     fp = st.make_opts(mode="per_view", use_graph=0)
@@ -531,7 +552,7 @@ def run_ours(args):
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     l2 = l2_peak_gbs(st)
-    tr = profiled_traffic()
+    tr, tr_sh = profiled_traffic()
 
     def record(name, v, t, q, ms, n):
         # per query: each 4-wide node fetch reads all four child boxes and links (112 B), each
@@ -553,11 +574,13 @@ def run_ours(args):
 
     roofline = record("k_extend (closest-hit BVH traversal)", visits, tests, rays, ext_ms, ext_n)
     roofline_shadow = record("k_shadow (any-hit BVH traversal)", sh_visits, sh_tests, sh_rays, sh_ms, sh_n)
-    if tr is not None:
-        # DRAM bytes per query from the committed ncu capture (cold caches) times this step's queries
-        per_launch = tr * rays / max(1, ext_n // reps)
-        roofline["traffic"] = round(per_launch, 1)
-        roofline["hbm"]["dram_frac"] = round(per_launch / (roofline["launch_ms_avg"] / 1000.0) / 1e9 / hbm_peak, 4)
+    # DRAM bytes per query from the committed ncu capture (cold caches) times this step's queries per launch
+    for rec, per_query, q, n in ((roofline, tr, rays, ext_n), (roofline_shadow, tr_sh, sh_rays, sh_n)):
+        if per_query is None:
+            continue
+        per_launch = per_query * q / max(1, n // reps)
+        rec["traffic"] = round(per_launch, 1)
+        rec["hbm"]["dram_frac"] = round(per_launch / (rec["launch_ms_avg"] / 1000.0) / 1e9 / hbm_peak, 4)
 
     # where the per-view step's time goes: GPU time between its host synchronisations
     # (queue counts read back after each stage) against the step's wall time
