@@ -554,13 +554,13 @@ def run_ours(args):
     l2 = l2_peak_gbs(st)
     tr, tr_sh = profiled_traffic()
 
-    def record(name, v, t, q, ms, n):
+    def roof_record(name, v, t, q, ms, n):
         # per query: each 4-wide node fetch reads all four child boxes and links (112 B), each
         # triangle test one leaf record (48 B), plus the ray in and the hit out (48 B)
         alg = v * 112 + t * 48 + q * 48
         achieved = alg * reps / (ms / 1000.0) / 1e9
         per_launch_ms = ms / max(1, n)
-        rec = {"bound": "l2", "achieved": round(achieved, 2), "peak": round(l2, 1), "unit": "GB/s",
+        out = {"bound": "l2", "achieved": round(achieved, 2), "peak": round(l2, 1), "unit": "GB/s",
                "frac": round(achieved / l2, 4), "traffic": None, "kernel": name,
                "peak_source": "st_measure_l2_read: L2-resident read bandwidth, best of 16/32/48 MiB, measured live",
                "launch_ms_avg": round(per_launch_ms, 4), "launches_per_step": n // reps,
@@ -570,17 +570,17 @@ def run_ours(args):
                "alg_bytes_per_query_64B_nodes": round((v * 64 + t * 48 + q * 48) / max(q, 1), 1),
                "hbm": {"peak": hbm_peak, "unit": "GB/s",
                        "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback"}}
-        return rec
+        return out
 
-    roofline = record("k_extend (closest-hit BVH traversal)", visits, tests, rays, ext_ms, ext_n)
-    roofline_shadow = record("k_shadow (any-hit BVH traversal)", sh_visits, sh_tests, sh_rays, sh_ms, sh_n)
+    roofline = roof_record("k_extend (closest-hit BVH traversal)", visits, tests, rays, ext_ms, ext_n)
+    roofline_shadow = roof_record("k_shadow (any-hit BVH traversal)", sh_visits, sh_tests, sh_rays, sh_ms, sh_n)
     # DRAM bytes per query from the committed ncu capture (cold caches) times this step's queries per launch
-    for rec, per_query, q, n in ((roofline, tr, rays, ext_n), (roofline_shadow, tr_sh, sh_rays, sh_n)):
+    for rl, per_query, q, n in ((roofline, tr, rays, ext_n), (roofline_shadow, tr_sh, sh_rays, sh_n)):
         if per_query is None:
             continue
         per_launch = per_query * q / max(1, n // reps)
-        rec["traffic"] = round(per_launch, 1)
-        rec["hbm"]["dram_frac"] = round(per_launch / (rec["launch_ms_avg"] / 1000.0) / 1e9 / hbm_peak, 4)
+        rl["traffic"] = round(per_launch, 1)
+        rl["hbm"]["dram_frac"] = round(per_launch / (rl["launch_ms_avg"] / 1000.0) / 1e9 / hbm_peak, 4)
 
     # where the per-view step's time goes: GPU time between its host synchronisations
     # (queue counts read back after each stage) against the step's wall time

@@ -688,14 +688,15 @@ __global__ void k_raygen(KCtx c, long long j0, int n) {
 #define ST_WARP_LOOP_END }
 
 // Closest hits of the first rays of a chunk whose pixel has a screen-space bin:
-// the leaves listed for that pixel, tested two at a time (two independent
-// list-entry and leaf-record loads in flight per lane), with no traversal
-// stack, so the kernel needs few registers and keeps many warps resident. The
-// hit is the smallest t, ties to the lower face id, as a sequential scan of
-// the list gives. Rays without a bin (views the bins do not serve) are queued
-// (q1, CNT_FB) for k_extend's BVH traversal.
+// the leaves listed for that pixel, BIN_ILP at a time (independent list-entry
+// and leaf-record loads in flight per lane), with no traversal stack, so the
+// kernel needs few registers and keeps many warps resident. The hit is the
+// smallest t, ties to the lower face id, as a sequential scan of the list
+// gives. Rays without a bin (views the bins do not serve) are queued (q1,
+// CNT_FB) for k_extend's BVH traversal.
+constexpr int BIN_ILP = 2;   // list entries a lane tests per step
 template <bool STATS>
-__global__ void __launch_bounds__(EXT_BLOCK, 10) k_extend_bins(KCtx c) {
+__global__ void __launch_bounds__(EXT_BLOCK, 8) k_extend_bins(KCtx c) {
   const Engine& E = c.e;
   int tests = 0;
   ST_WARP_LOOP(E.cnt[CNT_EXT + 0], &E.cnt[CNT_EXT_FETCH + 0])
@@ -711,23 +712,35 @@ __global__ void __launch_bounds__(EXT_BLOCK, 10) k_extend_bins(KCtx c) {
       float t = __int_as_float(0x7f800000);
       int f = -1, fl = -1;
       if (br.y > c.bin_cap || br.x > br.y) { atomicOr(c.err, ERR_INDEX); br.y = br.x; }
-      for (int k = br.x; k < br.y; k += 2) {
-        bool two = k + 1 < br.y;
-        int l0 = __ldg(&c.bin_list[k]);
-        int l1 = two ? __ldg(&c.bin_list[k + 1]) : l0;
-        if ((unsigned)l0 >= (unsigned)c.nf || (unsigned)l1 >= (unsigned)c.nf) {
+      for (int k = br.x; k < br.y; k += BIN_ILP) {
+        // BIN_ILP list entries and leaf records in flight, tested against the same bound, merged in list order
+        int li[BIN_ILP];
+        bool bad = false;
+#pragma unroll
+        for (int u = 0; u < BIN_ILP; ++u) {
+          li[u] = k + u < br.y ? __ldg(&c.bin_list[k + u]) : -1;
+          bad |= k + u < br.y && (unsigned)li[u] >= (unsigned)c.nf;
+        }
+        if (bad) {
           atomicOr(c.err, ERR_INDEX);
           continue;
         }
-        float4 a0 = __ldg(&c.tri[3 * l0]), b0 = __ldg(&c.tri[3 * l0 + 1]), c0 = __ldg(&c.tri[3 * l0 + 2]);
-        float4 a1 = __ldg(&c.tri[3 * l1]), b1 = __ldg(&c.tri[3 * l1 + 1]), c1 = __ldg(&c.tri[3 * l1 + 2]);
+        float4 ta[BIN_ILP], tb[BIN_ILP], tc[BIN_ILP];
+#pragma unroll
+        for (int u = 0; u < BIN_ILP; ++u) {
+          int l = li[u] >= 0 ? li[u] : li[0];
+          ta[u] = __ldg(&c.tri[3 * l]);
+          tb[u] = __ldg(&c.tri[3 * l + 1]);
+          tc[u] = __ldg(&c.tri[3 * l + 2]);
+        }
         float tmax = t * 1.0000001f + 1e-30f;
-        float h0 = tri_test(rp, xyz(a0), xyz(b0), xyz(c0), tmax);
-        float h1 = two ? tri_test(rp, xyz(a1), xyz(b1), xyz(c1), tmax) : -1.0f;
-        int f0 = __float_as_int(a0.w), f1 = __float_as_int(a1.w);
-        if (h0 > 0.0f && (h0 < t || (h0 == t && f0 < f))) { t = h0; f = f0; fl = l0; }
-        if (h1 > 0.0f && (h1 < t || (h1 == t && f1 < f))) { t = h1; f = f1; fl = l1; }
-        if (STATS) tests += two ? 2 : 1;
+#pragma unroll
+        for (int u = 0; u < BIN_ILP; ++u) {
+          float h = li[u] >= 0 ? tri_test(rp, xyz(ta[u]), xyz(tb[u]), xyz(tc[u]), tmax) : -1.0f;
+          int fu = __float_as_int(ta[u].w);
+          if (h > 0.0f && (h < t || (h == t && fu < f))) { t = h; f = fu; fl = li[u]; }
+          if (STATS && li[u] >= 0) tests++;
+        }
       }
       E.hit[slot] = make_int2(fl, __float_as_int(t));
     }
