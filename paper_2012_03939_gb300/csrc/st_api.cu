@@ -303,8 +303,7 @@ void drop_graphs(st_scene* s) {
   s->graphs.clear();
 }
 
-st_status ensure_engine(st_scene* s, int Q, int B, int NS, bool records, bool sec, bool shadow) {
-  Engine& e = s->eng;
+st_status grow_engine(st_scene* s, Engine& e, int Q, int B, int NS, bool records, bool sec, bool shadow) {
   if (e.Q >= Q && e.NS >= NS && (!records || (e.records && e.B >= B)) &&
       (!sec || e.sec_cap >= (long long)e.B * e.Q) && (!shadow || e.shadow))
     return ST_OK;
@@ -345,6 +344,14 @@ st_status ensure_engine(st_scene* s, int Q, int B, int NS, bool records, bool se
   e.sec_cap = nsec ? (long long)nB * nQ : 0;
   e.shadow = nshadow;
   return ST_OK;
+}
+
+// The call's wavefront buffers: one engine, or two when consecutive chunks are to
+// overlap on two streams (see enqueue_body).
+st_status ensure_engine(st_scene* s, int Q, int B, int NS, bool records, bool sec, bool shadow, bool two) {
+  st_status r = grow_engine(s, s->eng, Q, B, NS, records, sec, shadow);
+  if (r == ST_OK && two) r = grow_engine(s, s->eng2, Q, B, NS, records, sec, shadow);
+  return r;
 }
 
 st_status ensure_tables(st_scene* s, int n_views, int n_segs, bool edges) {
@@ -466,7 +473,8 @@ bool overlaps(const Plan& p, int kind, long long a, long long b) {
 // Enqueue one chunk [j0, j0 + n) of the job space. host_sized: read the queue
 // counts after each stage and size each grid to them (plain per-view path).
 st_status run_chunk(st_scene* s, const Plan& p, const KCtx& c, long long j0, int n, cudaStream_t st, bool host_sized,
-                    bool timing, bool has_cam, bool has_edge) {
+                    bool timing, bool has_cam, bool has_edge, cudaEvent_t resolve_after = nullptr,
+                    cudaEvent_t resolved = nullptr) {
   int sm = s->sm_count;
   // occupancy-limited grids of the persistent stage kernels, for the scene's own device (a scene is used by one
   // thread at a time, so these per-scene fields need no lock)
@@ -484,7 +492,7 @@ st_status run_chunk(st_scene* s, const Plan& p, const KCtx& c, long long j0, int
   const int g_shadow = p.o.count_visits ? s->g_shadow_s : s->g_shadow;
   // persistent grids: occupancy limit, or fewer resident blocks per SM if asked
   auto cap = [&](int g) { return p.o.persist_blocks > 0 ? std::min(g, p.o.persist_blocks * sm) : g; };
-  int* cnt = s->eng.cnt;
+  int* cnt = c.e.cnt;
   int hc[CNT_SIZE];
   // per-view calls read the queue counts back: the GPU idles from each read until the next launch. With timing on,
   // event pairs bracket the GPU-side intervals between those reads (set 2).
@@ -566,7 +574,10 @@ st_status run_chunk(st_scene* s, const Plan& p, const KCtx& c, long long j0, int
   if (r != ST_OK) return r;
   Range rr(p.kind == 0 ? "resolve" : "adjoint");
   if (p.kind == 0) {
+    // pixels add their samples in sample order: this chunk's sums come after the previous chunk's
+    if (resolve_after) ST_CUDA(cudaStreamWaitEvent(st, resolve_after, 0));
     k_resolve<<<(n + RESOLVE_BLOCK - 1) / RESOLVE_BLOCK, RESOLVE_BLOCK, 0, st>>>(c, j0, n);
+    if (resolved) ST_CUDA(cudaEventRecord(resolved, st));
     s->launches++;
   } else {
     int ga = (n + ADJ_BLOCK - 1) / ADJ_BLOCK;
@@ -584,7 +595,7 @@ st_status run_chunk(st_scene* s, const Plan& p, const KCtx& c, long long j0, int
         if (r != ST_OK) return r;
         jobs = hc[CNT_SEC];
       }
-      int Q = s->eng.Q;
+      int Q = c.e.Q;
       long long sides = (jobs + 31) / 32 * 64;
       int passes = (int)((sides + Q - 1) / Q);
       KCtx cs = c;
@@ -614,6 +625,19 @@ st_status run_chunk(st_scene* s, const Plan& p, const KCtx& c, long long j0, int
 st_status enqueue_body(st_scene* s, const Plan& p, const KCtx& c, int Q, cudaStream_t st, bool host_sized,
                        bool timing);
 
+long long chunk_count(const Plan& p, int Q) {
+  if (p.o.mode == ST_MODE_PER_VIEW) return 0;
+  return (p.total + Q - 1) / Q;
+}
+
+// Overlap consecutive chunks on two engines: batched calls of two chunks or more whose grids are not sized on the
+// host and whose kernels are not timed one by one, once the second engine and the events are in place.
+bool overlap_chunks(const st_scene* s, const Plan& p, int Q, bool host_sized, bool timing) {
+  long long nc = chunk_count(p, Q);
+  return !host_sized && !timing && nc >= 2 && s->aux_stream && s->eng2.Q >= Q &&
+         (long long)s->xev.size() >= nc + 2 && s->eng2.records == s->eng.records;
+}
+
 st_status enqueue_call(st_scene* s, const Plan& p, int Q, cudaStream_t st, bool host_sized, bool timing) {
   KCtx c = make_ctx(s, p);
   if (timing) ST_CUDA(cudaEventRecord(next_event(s, 2, true), st));
@@ -625,6 +649,7 @@ st_status enqueue_call(st_scene* s, const Plan& p, int Q, cudaStream_t st, bool 
 st_status enqueue_body(st_scene* s, const Plan& p, const KCtx& c, int Q, cudaStream_t st, bool host_sized,
                        bool timing) {
   ST_CUDA(cudaMemsetAsync(s->eng.stat, 0, sizeof(unsigned long long) * STAT_SIZE, st));
+  if (s->eng2.stat) ST_CUDA(cudaMemsetAsync(s->eng2.stat, 0, sizeof(unsigned long long) * STAT_SIZE, st));
   if (p.kind == 0) {
     k_zero_acc<<<(unsigned)((p.pixels + 255) / 256), 256, 0, st>>>(c);
     s->launches++;
@@ -674,12 +699,37 @@ st_status enqueue_body(st_scene* s, const Plan& p, const KCtx& c, int Q, cudaStr
     k_edge_compact<<<(unsigned)p.views.size(), 1024, 0, st>>>(c);
     s->launches += 2;
   }
+  // Batched calls of several chunks alternate two engines on two streams, so one
+  // chunk's last, sparsely filled bounces and launch tails overlap the next
+  // chunk's full stages. The auxiliary stream forks after the set-up above and
+  // joins before the finishing kernels; forward chunks resolve in order.
+  const bool two = overlap_chunks(s, p, Q, host_sized, timing);
+  KCtx c2 = c;
+  if (two) {
+    c2.e = s->eng2;
+    c2.e.records = c.e.records;
+  }
   auto chunks = [&](long long a, long long b) -> st_status {
-    for (long long j0 = a; j0 < b; j0 += Q) {
+    cudaEvent_t prev = nullptr;
+    int k = 0;
+    if (two) {
+      cudaEvent_t fork = s->xev[s->xev_used++];
+      ST_CUDA(cudaEventRecord(fork, st));
+      ST_CUDA(cudaStreamWaitEvent(s->aux_stream, fork, 0));
+    }
+    for (long long j0 = a; j0 < b; j0 += Q, ++k) {
       int n = (int)std::min<long long>(Q, b - j0);
-      st_status r = run_chunk(s, p, c, j0, n, st, host_sized, timing, overlaps(p, 0, j0, j0 + n),
-                              overlaps(p, 1, j0, j0 + n));
+      bool second = two && (k & 1);
+      cudaEvent_t done = two && p.kind == 0 ? s->xev[s->xev_used++] : nullptr;
+      st_status r = run_chunk(s, p, second ? c2 : c, j0, n, second ? s->aux_stream : st, host_sized, timing,
+                              overlaps(p, 0, j0, j0 + n), overlaps(p, 1, j0, j0 + n), prev, done);
       if (r != ST_OK) return r;
+      prev = done;
+    }
+    if (two) {
+      cudaEvent_t join = s->xev[s->xev_used++];
+      ST_CUDA(cudaEventRecord(join, s->aux_stream));
+      ST_CUDA(cudaStreamWaitEvent(st, join, 0));
     }
     return ST_OK;
   };
@@ -848,8 +898,20 @@ st_status run_call(st_scene* s, Plan& p, const CallArgs& args, cudaStream_t st) 
     Q = (int)std::min<long long>(Q, (mx + SEG_ALIGN - 1) / SEG_ALIGN * SEG_ALIGN);
   }
   int NS = s->nl + p.max_vl + (s->env.w > 0 ? 1 : 0);
-  r = ensure_engine(s, Q, p.B, NS, p.kind == 1, p.sec, p.shadow);
+  bool timing_call = p.o.time_kernels != 0;
+  bool want_two = p.o.mode == ST_MODE_BATCHED && !timing_call && chunk_count(p, Q) >= 2;
+  r = ensure_engine(s, Q, p.B, NS, p.kind == 1, p.sec, p.shadow, want_two);
   if (r != ST_OK) return r;
+  if (want_two) {
+    // events for the fork, every chunk's resolve and the join, made before any capture
+    long long need = chunk_count(p, Q) + 2;
+    while ((long long)s->xev.size() < need) {
+      cudaEvent_t e;
+      ST_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      s->xev.push_back(e);
+    }
+  }
+  s->xev_used = 0;
   ST_CUDA(copy_async(s->d_views, p.views.data(), sizeof(DevView) * p.views.size(), cudaMemcpyHostToDevice, st));
   ST_CUDA(copy_async(s->d_segs, p.segs.data(), sizeof(Seg) * p.segs.size(), cudaMemcpyHostToDevice, st));
   if (p.shadow && !p.pairs.empty())
@@ -905,6 +967,7 @@ void destroy(st_scene* s) {
   cudaDeviceSynchronize();
   drop_graphs(s);
   free_engine(s->eng);
+  free_engine(s->eng2);
   dfree(s->verts); dfree(s->faces); dfree(s->params); dfree(s->tri); dfree(s->nodes); dfree(s->parent);
   dfree(s->flags); dfree(s->keys); dfree(s->keys2); dfree(s->ids); dfree(s->ids2); dfree(s->hist); dfree(s->bounds);
   dfree(s->nodes4); dfree(s->src4); dfree(s->q4); dfree(s->c4);
@@ -918,7 +981,9 @@ void destroy(st_scene* s) {
   dfree(s->d_args); dfree(s->d_err);
   for (auto& set : s->ev)
     for (auto& e : set) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+  for (auto e : s->xev) cudaEventDestroy(e);
   if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+  if (s->aux_stream) cudaStreamDestroy(s->aux_stream);
   delete s;
 }
 
@@ -1097,6 +1162,7 @@ st_status st_scene_create(const st_scene_desc* d, void* stream, st_scene** out) 
     s->env.pdf_scale = (float)((double)d->env->width * d->env->height / (2.0 * 3.14159265358979323846 * 3.14159265358979323846));
   }
   chk(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
+  chk(cudaStreamCreateWithFlags(&s->aux_stream, cudaStreamNonBlocking));
   if (e == cudaSuccess) e = s->builder == ST_BVH_LBVH ? bvh_build(s, st) : bvh_build_ploc(s, st);
   if (e == cudaSuccess) e = bvh_collapse(s, st);
   if (e == cudaSuccess) e = mesh_stat(s, st);
@@ -1177,6 +1243,12 @@ st_status st_get_stats(st_scene* s, st_stats* out) {
   std::memset(&r, 0, sizeof(r));
   unsigned long long h[STAT_SIZE] = {0};
   if (s->eng.stat) ST_CUDA(copy_sync(h, s->eng.stat, sizeof(h), cudaMemcpyDeviceToHost));
+  if (s->eng2.stat) {
+    // an overlapped call counts in both engines (both are zeroed at the start of every call)
+    unsigned long long h2[STAT_SIZE] = {0};
+    ST_CUDA(copy_sync(h2, s->eng2.stat, sizeof(h2), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < STAT_SIZE; ++i) h[i] += h2[i];
+  }
   int err = 0;
   ST_CUDA(copy_sync(&err, s->d_err, sizeof(int), cudaMemcpyDeviceToHost));
   r.paths = (long long)h[STAT_PATHS];
@@ -1206,7 +1278,7 @@ st_status st_get_stats(st_scene* s, st_stats* out) {
   r.device_error = err;
   r.bvh_nodes = std::max(s->nf - 1, 0);
   r.bvh4_nodes = s->n4;
-  r.scratch_bytes = s->eng.bytes;
+  r.scratch_bytes = s->eng.bytes + s->eng2.bytes;
   r.kernel_launches = s->launches;
   *out = r;
   return ST_OK;

@@ -163,6 +163,10 @@ struct st_scene {
   st::CallArgs* d_args = nullptr;
   int view_cap = 0;
   st::Engine eng;
+  st::Engine eng2;               // second engine: consecutive chunks of a batched call alternate between the two
+  cudaStream_t aux_stream = nullptr;   // the second engine's stream (joins a captured graph through events)
+  std::vector<cudaEvent_t> xev;  // fork, per-chunk resolve and join events of overlapped calls
+  int xev_used = 0;
   int* d_err = nullptr;
   // graph cache
   cudaStream_t cap_stream = nullptr;
