@@ -346,11 +346,12 @@ st_status grow_engine(st_scene* s, Engine& e, int Q, int B, int NS, bool records
   return ST_OK;
 }
 
-// The call's wavefront buffers: one engine, or two when consecutive chunks are to
-// overlap on two streams (see enqueue_body).
+// The call's wavefront buffers: one engine, or all OVERLAP_ENGINES when consecutive
+// chunks are to overlap on their streams (see enqueue_body).
 st_status ensure_engine(st_scene* s, int Q, int B, int NS, bool records, bool sec, bool shadow, bool two) {
   st_status r = grow_engine(s, s->eng, Q, B, NS, records, sec, shadow);
-  if (r == ST_OK && two) r = grow_engine(s, s->eng2, Q, B, NS, records, sec, shadow);
+  for (int k = 0; r == ST_OK && two && k < OVERLAP_ENGINES - 1; ++k)
+    r = grow_engine(s, s->eng2[k], Q, B, NS, records, sec, shadow);
   return r;
 }
 
@@ -630,12 +631,14 @@ long long chunk_count(const Plan& p, int Q) {
   return (p.total + Q - 1) / Q;
 }
 
-// Overlap consecutive chunks on two engines: batched calls of two chunks or more whose grids are not sized on the
-// host and whose kernels are not timed one by one, once the second engine and the events are in place.
+// Overlap consecutive chunks on the engines: batched calls of two chunks or more whose grids are not sized on the
+// host and whose kernels are not timed one by one, once the further engines and the events are in place.
 bool overlap_chunks(const st_scene* s, const Plan& p, int Q, bool host_sized, bool timing) {
   long long nc = chunk_count(p, Q);
-  return !host_sized && !timing && nc >= 2 && s->aux_stream && s->eng2.Q >= Q &&
-         (long long)s->xev.size() >= nc + 2 && s->eng2.records == s->eng.records;
+  if (host_sized || timing || nc < 2 || (long long)s->xev.size() < nc + 2 * OVERLAP_ENGINES) return false;
+  for (int k = 0; k < OVERLAP_ENGINES - 1; ++k)
+    if (!s->aux_stream[k] || s->eng2[k].Q < Q || s->eng2[k].records != s->eng.records) return false;
+  return true;
 }
 
 st_status enqueue_call(st_scene* s, const Plan& p, int Q, cudaStream_t st, bool host_sized, bool timing) {
@@ -649,7 +652,8 @@ st_status enqueue_call(st_scene* s, const Plan& p, int Q, cudaStream_t st, bool 
 st_status enqueue_body(st_scene* s, const Plan& p, const KCtx& c, int Q, cudaStream_t st, bool host_sized,
                        bool timing) {
   ST_CUDA(cudaMemsetAsync(s->eng.stat, 0, sizeof(unsigned long long) * STAT_SIZE, st));
-  if (s->eng2.stat) ST_CUDA(cudaMemsetAsync(s->eng2.stat, 0, sizeof(unsigned long long) * STAT_SIZE, st));
+  for (auto& e : s->eng2)
+    if (e.stat) ST_CUDA(cudaMemsetAsync(e.stat, 0, sizeof(unsigned long long) * STAT_SIZE, st));
   if (p.kind == 0) {
     k_zero_acc<<<(unsigned)((p.pixels + 255) / 256), 256, 0, st>>>(c);
     s->launches++;
@@ -699,37 +703,44 @@ st_status enqueue_body(st_scene* s, const Plan& p, const KCtx& c, int Q, cudaStr
     k_edge_compact<<<(unsigned)p.views.size(), 1024, 0, st>>>(c);
     s->launches += 2;
   }
-  // Batched calls of several chunks alternate two engines on two streams, so one
-  // chunk's last, sparsely filled bounces and launch tails overlap the next
-  // chunk's full stages. The auxiliary stream forks after the set-up above and
-  // joins before the finishing kernels; forward chunks resolve in order.
-  const bool two = overlap_chunks(s, p, Q, host_sized, timing);
-  KCtx c2 = c;
-  if (two) {
-    c2.e = s->eng2;
-    c2.e.records = c.e.records;
+  // Batched calls of several chunks rotate them over the engines, each on its own
+  // stream, so one chunk's last, sparsely filled bounces and launch tails overlap
+  // the next chunks' full stages. The auxiliary streams fork after the set-up
+  // above and join before the finishing kernels; forward chunks resolve in order.
+  const bool multi = overlap_chunks(s, p, Q, host_sized, timing);
+  KCtx cx[OVERLAP_ENGINES];
+  cudaStream_t sx[OVERLAP_ENGINES];
+  cx[0] = c;
+  sx[0] = st;
+  for (int k = 1; k < OVERLAP_ENGINES; ++k) {
+    cx[k] = c;
+    cx[k].e = s->eng2[k - 1];
+    cx[k].e.records = c.e.records;
+    sx[k] = s->aux_stream[k - 1];
   }
   auto chunks = [&](long long a, long long b) -> st_status {
     cudaEvent_t prev = nullptr;
     int k = 0;
-    if (two) {
+    if (multi) {
       cudaEvent_t fork = s->xev[s->xev_used++];
       ST_CUDA(cudaEventRecord(fork, st));
-      ST_CUDA(cudaStreamWaitEvent(s->aux_stream, fork, 0));
+      for (int i = 1; i < OVERLAP_ENGINES; ++i) ST_CUDA(cudaStreamWaitEvent(sx[i], fork, 0));
     }
     for (long long j0 = a; j0 < b; j0 += Q, ++k) {
       int n = (int)std::min<long long>(Q, b - j0);
-      bool second = two && (k & 1);
-      cudaEvent_t done = two && p.kind == 0 ? s->xev[s->xev_used++] : nullptr;
-      st_status r = run_chunk(s, p, second ? c2 : c, j0, n, second ? s->aux_stream : st, host_sized, timing,
-                              overlaps(p, 0, j0, j0 + n), overlaps(p, 1, j0, j0 + n), prev, done);
+      int e = multi ? k % OVERLAP_ENGINES : 0;
+      cudaEvent_t done = multi && p.kind == 0 ? s->xev[s->xev_used++] : nullptr;
+      st_status r = run_chunk(s, p, cx[e], j0, n, sx[e], host_sized, timing, overlaps(p, 0, j0, j0 + n),
+                              overlaps(p, 1, j0, j0 + n), prev, done);
       if (r != ST_OK) return r;
       prev = done;
     }
-    if (two) {
-      cudaEvent_t join = s->xev[s->xev_used++];
-      ST_CUDA(cudaEventRecord(join, s->aux_stream));
-      ST_CUDA(cudaStreamWaitEvent(st, join, 0));
+    if (multi) {
+      for (int i = 1; i < OVERLAP_ENGINES; ++i) {
+        cudaEvent_t join = s->xev[s->xev_used++];
+        ST_CUDA(cudaEventRecord(join, sx[i]));
+        ST_CUDA(cudaStreamWaitEvent(st, join, 0));
+      }
     }
     return ST_OK;
   };
@@ -904,7 +915,7 @@ st_status run_call(st_scene* s, Plan& p, const CallArgs& args, cudaStream_t st) 
   if (r != ST_OK) return r;
   if (want_two) {
     // events for the fork, every chunk's resolve and the join, made before any capture
-    long long need = chunk_count(p, Q) + 2;
+    long long need = chunk_count(p, Q) + 2 * OVERLAP_ENGINES;
     while ((long long)s->xev.size() < need) {
       cudaEvent_t e;
       ST_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -967,7 +978,7 @@ void destroy(st_scene* s) {
   cudaDeviceSynchronize();
   drop_graphs(s);
   free_engine(s->eng);
-  free_engine(s->eng2);
+  for (auto& e : s->eng2) free_engine(e);
   dfree(s->verts); dfree(s->faces); dfree(s->params); dfree(s->tri); dfree(s->nodes); dfree(s->parent);
   dfree(s->flags); dfree(s->keys); dfree(s->keys2); dfree(s->ids); dfree(s->ids2); dfree(s->hist); dfree(s->bounds);
   dfree(s->nodes4); dfree(s->src4); dfree(s->q4); dfree(s->c4);
@@ -983,7 +994,8 @@ void destroy(st_scene* s) {
     for (auto& e : set) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
   for (auto e : s->xev) cudaEventDestroy(e);
   if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
-  if (s->aux_stream) cudaStreamDestroy(s->aux_stream);
+  for (auto a : s->aux_stream)
+    if (a) cudaStreamDestroy(a);
   delete s;
 }
 
@@ -1162,7 +1174,7 @@ st_status st_scene_create(const st_scene_desc* d, void* stream, st_scene** out) 
     s->env.pdf_scale = (float)((double)d->env->width * d->env->height / (2.0 * 3.14159265358979323846 * 3.14159265358979323846));
   }
   chk(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
-  chk(cudaStreamCreateWithFlags(&s->aux_stream, cudaStreamNonBlocking));
+  for (auto& a : s->aux_stream) chk(cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking));
   if (e == cudaSuccess) e = s->builder == ST_BVH_LBVH ? bvh_build(s, st) : bvh_build_ploc(s, st);
   if (e == cudaSuccess) e = bvh_collapse(s, st);
   if (e == cudaSuccess) e = mesh_stat(s, st);
@@ -1243,10 +1255,11 @@ st_status st_get_stats(st_scene* s, st_stats* out) {
   std::memset(&r, 0, sizeof(r));
   unsigned long long h[STAT_SIZE] = {0};
   if (s->eng.stat) ST_CUDA(copy_sync(h, s->eng.stat, sizeof(h), cudaMemcpyDeviceToHost));
-  if (s->eng2.stat) {
-    // an overlapped call counts in both engines (both are zeroed at the start of every call)
+  for (auto& e : s->eng2) {
+    // an overlapped call counts in every engine (all are zeroed at the start of every call)
+    if (!e.stat) continue;
     unsigned long long h2[STAT_SIZE] = {0};
-    ST_CUDA(copy_sync(h2, s->eng2.stat, sizeof(h2), cudaMemcpyDeviceToHost));
+    ST_CUDA(copy_sync(h2, e.stat, sizeof(h2), cudaMemcpyDeviceToHost));
     for (int i = 0; i < STAT_SIZE; ++i) h[i] += h2[i];
   }
   int err = 0;
@@ -1278,7 +1291,8 @@ st_status st_get_stats(st_scene* s, st_stats* out) {
   r.device_error = err;
   r.bvh_nodes = std::max(s->nf - 1, 0);
   r.bvh4_nodes = s->n4;
-  r.scratch_bytes = s->eng.bytes + s->eng2.bytes;
+  r.scratch_bytes = s->eng.bytes;
+  for (auto& e : s->eng2) r.scratch_bytes += e.bytes;
   r.kernel_launches = s->launches;
   *out = r;
   return ST_OK;

@@ -73,6 +73,10 @@ struct Engine {
   long long bytes = 0;
 };
 
+// Wavefront engines (buffer sets) of a batched call: consecutive chunks rotate over them, each on its own stream,
+// so one chunk's sparse last bounces overlap the next chunks' stages.
+constexpr int OVERLAP_ENGINES = 2;
+
 enum { CNT_EXT = 0, CNT_EXT_FETCH = 16, CNT_SHADE_FETCH = 32, CNT_SH = 48, CNT_SH_FETCH = 64, CNT_MISC = 80,
        CNT_SEC = CNT_MISC, CNT_FB = 88, CNT_FB_FETCH = 89, CNT_SIZE = 96 };
 enum { STAT_PATHS = 0, STAT_EXT = 1, STAT_SHADOW = 2, STAT_EDGE = 3, STAT_VISITS = 4, STAT_TESTS = 5,
@@ -163,8 +167,8 @@ struct st_scene {
   st::CallArgs* d_args = nullptr;
   int view_cap = 0;
   st::Engine eng;
-  st::Engine eng2;               // second engine: consecutive chunks of a batched call alternate between the two
-  cudaStream_t aux_stream = nullptr;   // the second engine's stream (joins a captured graph through events)
+  st::Engine eng2[st::OVERLAP_ENGINES - 1];   // further engines: consecutive chunks of a batched call rotate over all
+  cudaStream_t aux_stream[st::OVERLAP_ENGINES - 1] = {};   // their streams (join a captured graph through events)
   std::vector<cudaEvent_t> xev;  // fork, per-chunk resolve and join events of overlapped calls
   int xev_used = 0;
   int* d_err = nullptr;
