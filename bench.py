@@ -606,7 +606,10 @@ def run_ours(args):
     torch.cuda.synchronize()
     batched_split = {"wall_ms": round(e0.elapsed_time(e1), 3), "gpu_busy_ms": round(a["busy_ms"] + b["busy_ms"], 3),
                      "extend_ms": round(a["extend_ms"] + b["extend_ms"], 3),
-                     "shadow_ms": round(a["shadow_ms"] + b["shadow_ms"], 3), "graph": False}
+                     "shadow_ms": round(a["shadow_ms"] + b["shadow_ms"], 3), "graph": False,
+                     "chunks_overlapped": False,
+                     "note": "kernels timed one by one on one stream; the timed step overlaps consecutive chunks on "
+                             "two engines and streams (ms_per_step)"}
 
     # end to end through the C ABI with host buffers: H2D of the mesh state and
     # D2H of the image and both gradients every step
