@@ -61,6 +61,8 @@ bool fault_now(int site) {
 namespace {
 
 constexpr int DEFAULT_CHUNK = 1 << 22;
+// Faces per bin cell a view may hold, over the whole screen, before its cells are split further
+constexpr double BIN_FACES_PER_CELL = 0.5;
 // Segment bases and chunk sizes are multiples of 64: an edge segment is laid out
 // in blocks of 64 jobs, the minus sides of 32 consecutive samples then their plus
 // sides, so every warp traces one side along one edge (same behaviour per lane).
@@ -269,7 +271,8 @@ struct Plan {
   std::vector<Seg> segs;
   std::vector<std::pair<long long, long long>> view_range;  // job range per view (per-view mode)
   long long total = 0;
-  long long pixels = 0;       // sum of W*H: the primary-visibility bin space
+  long long pixels = 0;       // sum of W*H: the call's pixel space (accumulation)
+  long long cells = 0;        // sum of W*H*kb^2: the primary-visibility bin space
   bool interior = false, edges = false;
   bool sec = false;           // secondary-visibility edge samples at every camera-path vertex
   bool sec_tree = false;      // ... picked through the edge hierarchy
@@ -394,8 +397,8 @@ st_status ensure_tables(st_scene* s, int n_views, int n_segs, bool edges) {
 }
 
 st_status ensure_bins(st_scene* s, const Plan& p) {
-  long long P = p.pixels;
-  long long want = std::max<long long>(8 * P, 1 << 20);
+  long long P = p.cells;
+  long long want = std::max<long long>(4 * P, 1 << 20);
   if (s->bin_total_host && *s->bin_total_host > s->bin_cap) want = std::max(want, 2LL * *s->bin_total_host);
   want = std::min<long long>(want, 0x7ffffff0LL);   // a clamped total (INT_MAX) always exceeds it
   bool grow = P > s->bin_pix_cap || (int)p.views.size() > s->bin_views_cap || want > s->bin_cap;
@@ -430,7 +433,7 @@ KCtx make_ctx(st_scene* s, const Plan& p) {
   c.sh_cand = s->sh_cand; c.sh_ncand = s->sh_ncand;
   c.bin_start = p.bins ? s->bin_start : nullptr;   // nullptr: every primary ray traverses the BVH
   c.bin_list = s->bin_list; c.bin_cur = s->bin_cur; c.bin_ok = s->bin_ok;
-  c.bin_cap = s->bin_cap; c.bin_pixels = p.pixels;
+  c.bin_cap = s->bin_cap; c.bin_pixels = p.pixels; c.bin_cells = p.cells;
   c.cull = s->closed ? 1 : 0; c.mstat = s->mstat;
   c.smooth = s->smooth ? 1 : 0; c.vn = s->vnrm; c.dN = s->dN; c.nv = s->nv;
   c.sec_tree = p.sec_tree ? 1 : 0; c.et_G = s->et_G; c.et_L = s->et_L; c.et_lo = s->et_lo; c.et_hi = s->et_hi;
@@ -672,7 +675,7 @@ st_status enqueue_body(st_scene* s, const Plan& p, const KCtx& c, int Q, cudaStr
   if (p.bins) {
     Range r("primary bins");
     // primary-visibility bins of every view: count, scan, fill
-    long long P = p.pixels;
+    long long P = p.cells;
     int nv = (int)p.views.size();
     long long nb = (P + 4095) / 4096;
     dim3 g((s->nf + 127) / 128, (unsigned)nv);
@@ -818,6 +821,15 @@ st_status plan_call(st_scene* s, const st_view* views, int n_views, int default_
     p.views.push_back(make_view(v, spp));
     p.views.back().bin_base = p.pixels;
     p.pixels += (long long)v.width * v.height;
+    {
+      // bin cells per pixel side: enough that a cell holds a few faces when the mesh is dense on screen (a
+      // 64 x 64 view of 200,000 faces gets 8 x 8 cells per pixel), at most 8
+      int kb = 1;
+      while (kb < 8 && (double)s->nf > BIN_FACES_PER_CELL * (double)v.width * v.height * kb * kb) kb *= 2;
+      p.views.back().kb = kb;
+      p.views.back().bin_cell = p.cells;
+      p.cells += (long long)v.width * v.height * kb * kb;
+    }
     long long start = base;
     long long cam = (long long)v.width * v.height * spp;
     if (kind == 0 || p.interior) {

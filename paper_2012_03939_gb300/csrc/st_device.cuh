@@ -69,7 +69,9 @@ struct DevView {
   int W, H, spp;
   uint32_t off;            // low 32 bits of pixel_offset (counter word)
   long long pix_off;       // packed-image row of pixel (0, 0)
-  long long bin_base;      // first pixel of the view in the primary-visibility bins
+  long long bin_base;      // first pixel of the view in the call's pixel space (accumulation)
+  long long bin_cell;      // first cell of the view in the primary-visibility bins
+  int kb;                  // bin cells per pixel side (1, 2, 4 or 8)
   int nvl;                 // the view's own point lights (after the scene's)
   float4 vl[4];            // (position, 0), (intensity, 0) per view light
 };

@@ -154,7 +154,7 @@ struct st_scene {
   int* bin_list = nullptr;       // [bin_cap] leaf indices
   int* bin_ok = nullptr;         // [views] 1 = the view's primary rays may use the bins
   int* bin_part = nullptr;       // scan block sums
-  long long bin_pix_cap = 0;     // P capacity
+  long long bin_pix_cap = 0;     // cell capacity (bin_start, bin_cur)
   long long bin_cap = 0;         // list capacity
   int bin_views_cap = 0;
   int* bin_total_host = nullptr; // pinned: list length the last call needed

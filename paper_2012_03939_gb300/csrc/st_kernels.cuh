@@ -49,7 +49,8 @@ struct KCtx {
   int* bin_cur;
   const int* bin_ok;
   long long bin_cap;
-  long long bin_pixels;
+  long long bin_pixels;   // pixels of the call (accumulation space)
+  long long bin_cells;    // cells of the primary-visibility bins (kb x kb per pixel of each view)
   float* acc;             // per-pixel compensated sample sums, (sum, error) x 3 (bin-space pixel index)
   int cull;               // the mesh is one closed, consistently wound surface (see MeshStat)
   const MeshStat* mstat;
@@ -382,11 +383,13 @@ struct ScreenTri {
 
 // 0: cannot be hit from the eye or off screen; 1: box in (x0..x1, y0..y1);
 // -1: view must use the BVH
+// Screen coordinates are in bin cells: pixels times v.kb.
 __device__ __forceinline__ int leaf_screen_box(const DevView& v, float4 a, float4 b, float4 c, int& x0, int& y0,
                                                int& x1, int& y1, ScreenTri& et) {
   float3 P[3] = {xyz(a), xyz(b), xyz(c)};
   int front = 0, behind = 0;
   float px[3], py[3];
+  const int Wc = v.W * v.kb, Hc = v.H * v.kb;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     float3 rel = P[k] - v.eye;
@@ -394,16 +397,16 @@ __device__ __forceinline__ int leaf_screen_box(const DevView& v, float4 a, float
     front += z > Z_NEAR;
     behind += z <= 0.0f;
     float zz = fmaxf(z, Z_NEAR);
-    px[k] = (dot3(rel, v.right) / (zz * v.kx) + 1.0f) * (float)v.W * 0.5f;
-    py[k] = (1.0f - dot3(rel, v.up) / (zz * v.ky)) * (float)v.H * 0.5f;
+    px[k] = (dot3(rel, v.right) / (zz * v.kx) + 1.0f) * (float)Wc * 0.5f;
+    py[k] = (1.0f - dot3(rel, v.up) / (zz * v.ky)) * (float)Hc * 0.5f;
   }
   if (behind == 3) return 0;
   if (front < 3) return -1;
   float lx = fminf(fminf(px[0], px[1]), px[2]) - BIN_PAD, hx = fmaxf(fmaxf(px[0], px[1]), px[2]) + BIN_PAD;
   float ly = fminf(fminf(py[0], py[1]), py[2]) - BIN_PAD, hy = fmaxf(fmaxf(py[0], py[1]), py[2]) + BIN_PAD;
-  if (hx < 0.0f || hy < 0.0f || lx >= (float)v.W || ly >= (float)v.H) return 0;
+  if (hx < 0.0f || hy < 0.0f || lx >= (float)Wc || ly >= (float)Hc) return 0;
   x0 = max(0, (int)floorf(lx)); y0 = max(0, (int)floorf(ly));
-  x1 = min(v.W - 1, (int)floorf(hx)); y1 = min(v.H - 1, (int)floorf(hy));
+  x1 = min(Wc - 1, (int)floorf(hx)); y1 = min(Hc - 1, (int)floorf(hy));
   if ((long long)(x1 - x0 + 1) * (y1 - y0 + 1) > BIN_MAX_BOX) return -1;
   float area = (px[1] - px[0]) * (py[2] - py[0]) - (py[1] - py[0]) * (px[2] - px[0]);
   et.degenerate = !(fabsf(area) > 1e-6f);
@@ -419,7 +422,7 @@ __device__ __forceinline__ int leaf_screen_box(const DevView& v, float4 a, float
   return 1;
 }
 
-// can any point of pixel (x, y), padded by BIN_PAD, lie inside the triangle?
+// can any point of cell (x, y), padded by BIN_PAD, lie inside the triangle?
 __device__ __forceinline__ bool pixel_may_overlap(const ScreenTri& et, int x, int y) {
   if (et.degenerate) return true;
 #pragma unroll
@@ -470,11 +473,12 @@ __global__ void k_bin(KCtx c, int n_views, int* ok) {
   int r = leaf_screen_box(v, ta, tb, tc, x0, y0, x1, y1, et);
   if (r < 0) { if (!FILL) atomicAnd(&ok[vi], 0); return; }
   if (r == 0) return;
-  if (FILL && c.bin_start[c.bin_pixels] > c.bin_cap) return;   // overflow: every view uses the BVH
+  if (FILL && c.bin_start[c.bin_cells] > c.bin_cap) return;   // overflow: every view uses the BVH
+  const long long Wc = (long long)v.W * v.kb;
   for (int y = y0; y <= y1; ++y)
     for (int x = x0; x <= x1; ++x) {
       if (!pixel_may_overlap(et, x, y)) continue;
-      long long p = v.bin_base + (long long)y * v.W + x;
+      long long p = v.bin_cell + (long long)y * Wc + x;
       int k = atomicAdd(&c.bin_cur[p], 1);
       if (FILL) {
         long long at = (long long)c.bin_start[p] + k;
@@ -577,11 +581,18 @@ __global__ void k_scan_add(int* out, long long n, const int* part) {
     if (i < n) out[i] += add;
 }
 
+// the list of bin cell (x, y) of view vi (cells: v.kb x v.kb per pixel)
 __device__ __forceinline__ int2 bin_range(const KCtx& c, int vi, const DevView& v, int x, int y) {
-  if (c.bin_start == nullptr || !c.bin_ok[vi] || c.bin_start[c.bin_pixels] > c.bin_cap) return make_int2(-1, -1);
-  if (x < 0 || y < 0 || x >= v.W || y >= v.H) return make_int2(-1, -1);
-  long long p = v.bin_base + (long long)y * v.W + x;
+  if (c.bin_start == nullptr || !c.bin_ok[vi] || c.bin_start[c.bin_cells] > c.bin_cap) return make_int2(-1, -1);
+  if (x < 0 || y < 0 || x >= v.W * v.kb || y >= v.H * v.kb) return make_int2(-1, -1);
+  long long p = v.bin_cell + (long long)y * ((long long)v.W * v.kb) + x;
   return make_int2(c.bin_start[p], c.bin_start[p + 1]);
+}
+
+// the cell of a camera sample at pixel (x, y) + the 24-bit jitter words ux, uy: exact in integers
+__device__ __forceinline__ int2 sample_cell(const DevView& v, int x, int y, uint32_t ux, uint32_t uy) {
+  return make_int2(x * v.kb + (int)(((ux >> 8) * (uint32_t)v.kb) >> 24),
+                   y * v.kb + (int)(((uy >> 8) * (uint32_t)v.kb) >> 24));
 }
 
 // ------------------------------------------------------------------ chunk stages
@@ -618,7 +629,8 @@ __global__ void k_raygen(KCtx c, long long j0, int n) {
           d = cam_dir(v, (float)x + unif(u.x), (float)y + unif(u.y));
           o = v.eye;
           ct = make_int4((int)c0, s, 0, sg.view << 4);
-          br = bin_range(c, sg.view, v, x, y);
+          int2 cell = sample_cell(v, x, y, u.x, u.y);
+          br = bin_range(c, sg.view, v, cell.x, cell.y);
           ok = true;
         } else if (SH && sg.kind == 2) {
           // shadow-edge sides: the sample is stored at the block's minus slot
@@ -629,7 +641,7 @@ __global__ void k_raygen(KCtx c, long long j0, int n) {
             long long k = (local >> 6) * 32 + (local & 31);
             d = cam_dir(v, sx, sy);
             o = v.eye;
-            br = bin_range(c, sg.view, v, (int)floorf(sx), (int)floorf(sy));
+            br = bin_range(c, sg.view, v, (int)floorf(sx * (float)v.kb), (int)floorf(sy * (float)v.kb));
             ct = make_int4((int)(uint32_t)k, (int)v.off, 4 + sg.light, sg.view << 4);
             ok = true;
           }
@@ -644,7 +656,7 @@ __global__ void k_raygen(KCtx c, long long j0, int n) {
             float sx = es.S.x + sg2 * es.ns.x, sy = es.S.y + sg2 * es.ns.y;
             d = cam_dir(v, sx, sy);
             o = v.eye;
-            br = bin_range(c, sg.view, v, (int)floorf(sx), (int)floorf(sy));
+            br = bin_range(c, sg.view, v, (int)floorf(sx * (float)v.kb), (int)floorf(sy * (float)v.kb));
             ct = make_int4((int)(uint32_t)k, (int)v.off, 2, sg.view << 4);
             ok = true;
           }
