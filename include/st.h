@@ -178,7 +178,8 @@ typedef struct {
   long long edge_samples;     /* edge samples of the last call (each traces two paths) */
   long long node_visits;      /* instrumented calls only: internal nodes fetched by closest-hit */
   long long tri_tests;        /* instrumented calls only: triangle tests by closest-hit */
-  int extend_launches;        /* closest-hit launches timed (time_kernels) */
+  int extend_launches;        /* closest-hit launches timed (time_kernels): ray generation, which finds the hits of
+                                 the first rays a screen-space bin serves, and the BVH traversals */
   double extend_ms;           /* their summed CUDA-event time */
   int device_error;           /* latched device error bits (0 = none) */
   int bvh_nodes;              /* internal nodes of the binary BVH (refit / st_debug_bvh layout) */

@@ -293,7 +293,7 @@ st_render_opts default_opts() {
 }
 
 void free_engine(Engine& e) {
-  dfree(e.o); dfree(e.d); dfree(e.thr); dfree(e.rad); dfree(e.ctr); dfree(e.hit); dfree(e.origin); dfree(e.brange);
+  dfree(e.o); dfree(e.d); dfree(e.thr); dfree(e.rad); dfree(e.ctr); dfree(e.hit); dfree(e.origin);
   dfree(e.q0); dfree(e.q1); dfree(e.qs); dfree(e.sh_dir); dfree(e.sh_c);
   dfree(e.r0); dfree(e.r1); dfree(e.r2); dfree(e.r3); dfree(e.esc); dfree(e.nb); dfree(e.cnt); dfree(e.stat);
   dfree(e.sj); dfree(e.sje); dfree(e.pinj); dfree(e.sig); dfree(e.shr);
@@ -324,7 +324,6 @@ st_status grow_engine(st_scene* s, Engine& e, int Q, int B, int NS, bool records
   auto chk = [&](cudaError_t x) { if (x != cudaSuccess && r == cudaSuccess) r = x; };
   chk(dalloc(&e.o, q, &acc)); chk(dalloc(&e.d, q, &acc)); chk(dalloc(&e.thr, q, &acc)); chk(dalloc(&e.rad, q, &acc));
   chk(dalloc(&e.ctr, q, &acc)); chk(dalloc(&e.hit, q, &acc)); chk(dalloc(&e.origin, q, &acc));
-  chk(dalloc(&e.brange, q, &acc));
   chk(dalloc(&e.q0, q, &acc)); chk(dalloc(&e.q1, q, &acc)); chk(dalloc(&e.qs, q, &acc));
   chk(dalloc(&e.sh_dir, q * std::max(nNS, 1), &acc)); chk(dalloc(&e.sh_c, q * std::max(nNS, 1), &acc));
   if (nrec) {
@@ -488,10 +487,7 @@ st_status run_chunk(st_scene* s, const Plan& p, const KCtx& c, long long j0, int
     s->g_shade = grid_of((const void*)k_shade, 256, sm);
     s->g_shadow = grid_of((const void*)k_shadow<false>, EXT_BLOCK, sm);
     s->g_shadow_s = grid_of((const void*)k_shadow<true>, EXT_BLOCK, sm);
-    s->g_bins = grid_of((const void*)k_extend_bins<false>, EXT_BLOCK, sm);
-    s->g_bins_s = grid_of((const void*)k_extend_bins<true>, EXT_BLOCK, sm);
   }
-  const int g_bins = p.o.count_visits ? s->g_bins_s : s->g_bins;
   const int g_ext = s->g_ext, g_ext_s = s->g_ext_s, g_shade = s->g_shade;
   const int g_shadow = p.o.count_visits ? s->g_shadow_s : s->g_shadow;
   // persistent grids: occupancy limit, or fewer resident blocks per SM if asked
@@ -516,41 +512,34 @@ st_status run_chunk(st_scene* s, const Plan& p, const KCtx& c, long long j0, int
     s->launches++;
     return ST_OK;
   };
-  // extension / shading / shadow stages for `nb` bounces of the paths queued in q0; with `bins`, the first
-  // rays test the leaves of their pixel's screen-space bin (k_extend_bins), the others go through the BVH
-  auto bounces = [&](const KCtx& k, int nb, bool bins) -> st_status {
+  // extension / shading / shadow stages for `nb` bounces of the paths queued in q0. With `from_raygen` the first
+  // rays already hold their closest hits where a bin cell served them (k_raygen), and bounce 0's BVH launch takes
+  // the rest from the fallback queue.
+  auto bounces = [&](const KCtx& k, int nb, bool from_raygen) -> st_status {
     for (int b = 0; b < nb; ++b) {
-      int ge = cap(p.o.count_visits ? g_ext_s : g_ext), gs = cap(g_shade), gw = cap(g_shadow), gb = cap(g_bins);
-      int gf = ge;
+      int ge = cap(p.o.count_visits ? g_ext_s : g_ext), gs = cap(g_shade), gw = cap(g_shadow);
+      const bool fb = b == 0 && from_raygen;
+      bool launch = true;
       if (host_sized) {
         st_status r = read_counts();
         if (r != ST_OK) return r;
         int q = hc[CNT_EXT + b];
         if (q == 0) break;
-        ge = (q + EXT_BLOCK - 1) / EXT_BLOCK;
-        gb = std::min(gb, ge);
+        int qe = fb ? hc[CNT_FB] : q;
+        launch = qe > 0;
+        ge = std::max(1, (qe + EXT_BLOCK - 1) / EXT_BLOCK);
         gs = (q + 255) / 256;
       }
       Range rb(b == 0 ? "bounce 0" : b == 1 ? "bounce 1" : "bounce 2+");
-      if (timing) ST_CUDA(cudaEventRecord(next_event(s, 0, true), st));
-      if (b == 0 && bins) {
-        // the BVH launch takes the rays the bins kernel queued (a persistent grid: the count stays on the device)
-        if (p.o.count_visits) {
-          k_extend_bins<true><<<gb, EXT_BLOCK, 0, st>>>(k);
-          k_extend<true><<<gf, EXT_BLOCK, 0, st>>>(k, 0, 1);
-        } else {
-          k_extend_bins<false><<<gb, EXT_BLOCK, 0, st>>>(k);
-          k_extend<false><<<gf, EXT_BLOCK, 0, st>>>(k, 0, 1);
-        }
+      if (launch) {
+        if (timing) ST_CUDA(cudaEventRecord(next_event(s, 0, true), st));
+        if (p.o.count_visits) k_extend<true><<<ge, EXT_BLOCK, 0, st>>>(k, b, fb ? 1 : 0);
+        else k_extend<false><<<ge, EXT_BLOCK, 0, st>>>(k, b, fb ? 1 : 0);
+        if (timing) ST_CUDA(cudaEventRecord(next_event(s, 0, false), st));
         s->launches++;
-      } else if (p.o.count_visits) {
-        k_extend<true><<<ge, EXT_BLOCK, 0, st>>>(k, b, 0);
-      } else {
-        k_extend<false><<<ge, EXT_BLOCK, 0, st>>>(k, b, 0);
       }
-      if (timing) ST_CUDA(cudaEventRecord(next_event(s, 0, false), st));
       k_shade<<<gs, 256, 0, st>>>(k, b);
-      s->launches += 2;
+      s->launches++;
       if (host_sized) {
         st_status r = read_counts();
         if (r != ST_OK) return r;
@@ -571,10 +560,21 @@ st_status run_chunk(st_scene* s, const Plan& p, const KCtx& c, long long j0, int
   k_reset<<<1, 128, 0, st>>>(cnt);
   bool has_shadow = p.shadow && overlaps(p, 2, j0, j0 + n);
   if (has_shadow) { k_sh_prep<<<(n + EXT_BLOCK - 1) / EXT_BLOCK, EXT_BLOCK, 0, st>>>(c, j0, n); s->launches++; }
-  if (has_shadow) k_raygen<true><<<(n + 255) / 256, 256, 0, st>>>(c, j0, n);
-  else k_raygen<false><<<(n + 255) / 256, 256, 0, st>>>(c, j0, n);
-  s->launches += 2;
-  st_status r = bounces(c, p.B, p.bins);
+  // k_raygen finds the closest hits of the first rays its bin cells serve: timed with the closest-hit launches
+  {
+    const int gr = (n + 255) / 256;
+    if (timing) ST_CUDA(cudaEventRecord(next_event(s, 0, true), st));
+    if (has_shadow) {
+      if (p.o.count_visits) k_raygen<true, true><<<gr, 256, 0, st>>>(c, j0, n);
+      else k_raygen<true, false><<<gr, 256, 0, st>>>(c, j0, n);
+    } else {
+      if (p.o.count_visits) k_raygen<false, true><<<gr, 256, 0, st>>>(c, j0, n);
+      else k_raygen<false, false><<<gr, 256, 0, st>>>(c, j0, n);
+    }
+    if (timing) ST_CUDA(cudaEventRecord(next_event(s, 0, false), st));
+    s->launches += 2;
+  }
+  st_status r = bounces(c, p.B, true);
   if (r != ST_OK) return r;
   Range rr(p.kind == 0 ? "resolve" : "adjoint");
   if (p.kind == 0) {

@@ -52,7 +52,6 @@ struct Engine {
   float4 *o = nullptr, *d = nullptr, *thr = nullptr, *rad = nullptr;
   int4* ctr = nullptr;        // Philox counter words (c0, c1, stream) and the vertex index of the first ray
   int2* hit = nullptr;        // (face, t bits)
-  int2* brange = nullptr;     // primary rays: range of the pixel's bin list, (-1, -1) = use the BVH
   int* origin = nullptr;
   int *q0 = nullptr, *q1 = nullptr, *qs = nullptr;
   float4 *sh_dir = nullptr, *sh_c = nullptr;  // [NS][Q]
@@ -181,7 +180,7 @@ struct st_scene {
   int ev_used[3] = {0, 0, 0};
   int host_syncs = 0;
   int sm_count = 0;
-  int g_ext = 0, g_ext_s = 0, g_shade = 0, g_shadow = 0, g_shadow_s = 0, g_bins = 0, g_bins_s = 0;  // stage grids
+  int g_ext = 0, g_ext_s = 0, g_shade = 0, g_shadow = 0, g_shadow_s = 0;  // stage grids
   long long last_edge_samples = 0;
   int launches = 0;              // kernels enqueued by the last call
   st_stats last{};

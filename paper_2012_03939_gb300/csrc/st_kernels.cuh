@@ -600,13 +600,61 @@ __global__ void k_reset(int* cnt) {
   for (int i = threadIdx.x; i < CNT_SIZE; i += blockDim.x) cnt[i] = 0;
 }
 
+constexpr int BIN_ILP = 2;   // list entries a lane tests per step
+
+// The closest hit of a first ray from the leaves listed for its bin cell:
+// BIN_ILP entries at a time, tested against the same bound and merged in list
+// order, which gives what a sequential scan gives (smallest t, ties to the lower
+// face id).
+template <bool STATS>
+__device__ __forceinline__ int2 bin_closest(const KCtx& c, float3 o, float3 d, int2 br, int& tests) {
+  RayPre rp = ray_pre(o, d);
+  float t = __int_as_float(0x7f800000);
+  int f = -1, fl = -1;
+  if (br.y > c.bin_cap || br.x > br.y) { atomicOr(c.err, ERR_INDEX); br.y = br.x; }
+  for (int k = br.x; k < br.y; k += BIN_ILP) {
+    int li[BIN_ILP];
+    bool bad = false;
+#pragma unroll
+    for (int u = 0; u < BIN_ILP; ++u) {
+      li[u] = k + u < br.y ? __ldg(&c.bin_list[k + u]) : -1;
+      bad |= k + u < br.y && (unsigned)li[u] >= (unsigned)c.nf;
+    }
+    if (bad) {
+      atomicOr(c.err, ERR_INDEX);
+      continue;
+    }
+    float4 ta[BIN_ILP], tb[BIN_ILP], tc[BIN_ILP];
+#pragma unroll
+    for (int u = 0; u < BIN_ILP; ++u) {
+      int l = li[u] >= 0 ? li[u] : li[0];
+      ta[u] = __ldg(&c.tri[3 * l]);
+      tb[u] = __ldg(&c.tri[3 * l + 1]);
+      tc[u] = __ldg(&c.tri[3 * l + 2]);
+    }
+    float tmax = t * 1.0000001f + 1e-30f;
+#pragma unroll
+    for (int u = 0; u < BIN_ILP; ++u) {
+      float h = li[u] >= 0 ? tri_test(rp, xyz(ta[u]), xyz(tb[u]), xyz(tc[u]), tmax) : -1.0f;
+      int fu = __float_as_int(ta[u].w);
+      if (h > 0.0f && (h < t || (h == t && fu < f))) { t = h; f = fu; fl = li[u]; }
+      if (STATS && li[u] >= 0) tests++;
+    }
+  }
+  return make_int2(fl, __float_as_int(t));
+}
+
 // SH: the chunk holds shadow-edge side jobs (kind 2); chunks without them run
-// the variant without that branch, whose code is the hot path's.
-template <bool SH>
+// the variant without that branch, whose code is the hot path's. A first ray
+// whose view has primary-visibility bins finds its closest hit here, from the
+// leaves of its cell (bin_closest); the others are queued (q1, CNT_FB) for
+// k_extend's BVH traversal.
+template <bool SH, bool STATS>
 __global__ void k_raygen(KCtx c, long long j0, int n) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   const Engine& E = c.e;
-  bool ok = false;
+  bool ok = false, fb = false;
+  int tests = 0;
   float3 o = mk3(0, 0, 0), d = mk3(0, 0, 1);
   int4 ct = make_int4(0, 0, 0, 0);
   int2 br = make_int2(-1, -1);
@@ -676,13 +724,23 @@ __global__ void k_raygen(KCtx c, long long j0, int n) {
       E.thr[i] = make_float4(1, 1, 1, 0);
       E.origin[i] = -1;
       E.ctr[i] = ct;
-      E.brange[i] = br;
+      if (br.x >= 0) E.hit[i] = bin_closest<STATS>(c, o, d, br, tests);
+      else fb = true;
     }
   }
   int q = warp_append(&E.cnt[CNT_EXT + 0], ok);
   if (ok) E.q0[q] = i;
+  int qf = warp_append(&E.cnt[CNT_FB], fb);
+  if (fb) E.q1[qf] = i;
   unsigned m = __ballot_sync(FULL, ok);
-  if ((threadIdx.x & 31) == 0 && m) atomicAdd(&E.stat[STAT_PATHS], (unsigned long long)__popc(m));
+  if ((threadIdx.x & 31) == 0 && m) {
+    atomicAdd(&E.stat[STAT_PATHS], (unsigned long long)__popc(m));
+    atomicAdd(&E.stat[STAT_EXT], (unsigned long long)__popc(m));   // every first ray is a closest-hit query
+  }
+  if (STATS) {
+    for (int off = 16; off > 0; off >>= 1) tests += __shfl_xor_sync(FULL, tests, off);
+    if ((threadIdx.x & 31) == 0 && tests) atomicAdd(&E.stat[STAT_TESTS], (unsigned long long)tests);
+  }
 }
 
 // persistent fetch: a warp takes 32 consecutive queue entries per step
@@ -699,77 +757,8 @@ __global__ void k_raygen(KCtx c, long long j0, int n) {
 
 #define ST_WARP_LOOP_END }
 
-// Closest hits of the first rays of a chunk whose pixel has a screen-space bin:
-// the leaves listed for that pixel, BIN_ILP at a time (independent list-entry
-// and leaf-record loads in flight per lane), with no traversal stack, so the
-// kernel needs few registers and keeps many warps resident. The hit is the
-// smallest t, ties to the lower face id, as a sequential scan of the list
-// gives. Rays without a bin (views the bins do not serve) are queued (q1,
-// CNT_FB) for k_extend's BVH traversal.
-constexpr int BIN_ILP = 2;   // list entries a lane tests per step
-template <bool STATS>
-__global__ void __launch_bounds__(EXT_BLOCK, 8) k_extend_bins(KCtx c) {
-  const Engine& E = c.e;
-  int tests = 0;
-  ST_WARP_LOOP(E.cnt[CNT_EXT + 0], &E.cnt[CNT_EXT_FETCH + 0])
-  bool fallback = false;
-  int slot = live_ ? E.q0[qi_] : 0;
-  if (live_) {
-    int2 br = E.brange[slot];
-    if (br.x < 0) {
-      fallback = true;
-    } else {
-      float4 o = E.o[slot], d = E.d[slot];
-      RayPre rp = ray_pre(xyz(o), xyz(d));
-      float t = __int_as_float(0x7f800000);
-      int f = -1, fl = -1;
-      if (br.y > c.bin_cap || br.x > br.y) { atomicOr(c.err, ERR_INDEX); br.y = br.x; }
-      for (int k = br.x; k < br.y; k += BIN_ILP) {
-        // BIN_ILP list entries and leaf records in flight, tested against the same bound, merged in list order
-        int li[BIN_ILP];
-        bool bad = false;
-#pragma unroll
-        for (int u = 0; u < BIN_ILP; ++u) {
-          li[u] = k + u < br.y ? __ldg(&c.bin_list[k + u]) : -1;
-          bad |= k + u < br.y && (unsigned)li[u] >= (unsigned)c.nf;
-        }
-        if (bad) {
-          atomicOr(c.err, ERR_INDEX);
-          continue;
-        }
-        float4 ta[BIN_ILP], tb[BIN_ILP], tc[BIN_ILP];
-#pragma unroll
-        for (int u = 0; u < BIN_ILP; ++u) {
-          int l = li[u] >= 0 ? li[u] : li[0];
-          ta[u] = __ldg(&c.tri[3 * l]);
-          tb[u] = __ldg(&c.tri[3 * l + 1]);
-          tc[u] = __ldg(&c.tri[3 * l + 2]);
-        }
-        float tmax = t * 1.0000001f + 1e-30f;
-#pragma unroll
-        for (int u = 0; u < BIN_ILP; ++u) {
-          float h = li[u] >= 0 ? tri_test(rp, xyz(ta[u]), xyz(tb[u]), xyz(tc[u]), tmax) : -1.0f;
-          int fu = __float_as_int(ta[u].w);
-          if (h > 0.0f && (h < t || (h == t && fu < f))) { t = h; f = fu; fl = li[u]; }
-          if (STATS && li[u] >= 0) tests++;
-        }
-      }
-      E.hit[slot] = make_int2(fl, __float_as_int(t));
-    }
-  }
-  int qf = warp_append(&E.cnt[CNT_FB], fallback);
-  if (fallback) E.q1[qf] = slot;
-  ST_WARP_LOOP_END
-  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&E.stat[STAT_EXT], (unsigned long long)E.cnt[CNT_EXT + 0]);
-  if (STATS) {
-    for (int off = 16; off > 0; off >>= 1) tests += __shfl_xor_sync(FULL, tests, off);
-    if ((threadIdx.x & 31) == 0) atomicAdd(&E.stat[STAT_TESTS], (unsigned long long)tests);
-  }
-}
-
-// Closest hits through the BVH (the rays of bounce b, or with fb = 1 the first
-// rays k_extend_bins queued). Rays of bounce 0 that carry a bin range test
-// their pixel's leaves here too when the call runs without k_extend_bins.
+// Closest hits through the BVH: the rays of bounce b, or with fb = 1 the first
+// rays k_raygen queued because no bin cell serves them.
 template <bool STATS>
 __global__ void __launch_bounds__(EXT_BLOCK) k_extend(KCtx c, int b, int fb) {
   __shared__ int sstack[TRACE_SH * EXT_BLOCK];
@@ -781,24 +770,9 @@ __global__ void __launch_bounds__(EXT_BLOCK) k_extend(KCtx c, int b, int fb) {
     int slot = q[qi_];
     float4 o = E.o[slot], d = E.d[slot];
     float t = __int_as_float(0x7f800000);
-    int f = -1, fl = -1;
-    int2 br = b == 0 && !fb ? E.brange[slot] : make_int2(-1, -1);
-    if (br.x >= 0) {
-      RayPre rp = ray_pre(xyz(o), xyz(d));
-      if (br.y > c.bin_cap || br.x > br.y) { atomicOr(c.err, ERR_INDEX); br.y = br.x; }
-      for (int k = br.x; k < br.y; ++k) {
-        int li = __ldg(&c.bin_list[k]);
-        if ((unsigned)li >= (unsigned)c.nf) { atomicOr(c.err, ERR_INDEX); continue; }
-        float4 ta = __ldg(&c.tri[3 * li]), tb = __ldg(&c.tri[3 * li + 1]), tc = __ldg(&c.tri[3 * li + 2]);
-        int fid = __float_as_int(ta.w);
-        float th = tri_test(rp, xyz(ta), xyz(tb), xyz(tc), t * 1.0000001f + 1e-30f);
-        if (th > 0.0f && (th < t || (th == t && fid < f))) { t = th; f = fid; fl = li; }
-        if (STATS) ts.tests++;
-      }
-    } else {
-      f = trace_bvh<false, STATS>(c.nodes, c.tri, c.nf, c.n4, xyz(o), xyz(d), __int_as_float(0x7f800000), E.origin[slot], t,
-                                  sstack + threadIdx.x, c.err, &ts, &fl);
-    }
+    int fl = -1;
+    trace_bvh<false, STATS>(c.nodes, c.tri, c.nf, c.n4, xyz(o), xyz(d), __int_as_float(0x7f800000), E.origin[slot], t,
+                            sstack + threadIdx.x, c.err, &ts, &fl);
     E.hit[slot] = make_int2(fl, __float_as_int(t));   // leaf index: shading reads the contiguous leaf record
   }
   ST_WARP_LOOP_END
@@ -1658,7 +1632,6 @@ __global__ void k_sec_raygen(KCtx c, int pass) {
         E.thr[i] = make_float4(thr.x, thr.y, thr.z, 0.0f);
         E.origin[i] = f;
         E.ctr[i] = make_int4(je.x, je.y, 16 + b, (b + 1) | (je.w & ~15));
-        E.brange[i] = make_int2(-1, -1);
         ok = true;
       }
     }
