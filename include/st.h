@@ -235,7 +235,11 @@ st_status st_set_face_params(st_scene* scene, const float* face_params, void* st
  * every pixel of the views (other rows untouched). opts may be NULL (batched,
  * graph on). Asynchronous on `stream`. Errors: ST_ERR_INVALID_ARG (bad views,
  * overlapping pixel ranges, no light), ST_ERR_UNSUPPORTED, ST_ERR_OOM, ST_ERR_CUDA;
- * a kernel's latched error is reported by st_get_stats (device_error). */
+ * a kernel's latched error is reported by st_get_stats (device_error).
+ * A call of at least 2^20 primary rays finds their hits in screen-space leaf
+ * lists of its views, kept on the device: a later call (forward or backward)
+ * with the same views (camera, size) and no vertex update since uses them
+ * without building them again. */
 st_status st_render(st_scene* scene, const st_view* views, int n_views, int default_spp,
                     int max_bounces, unsigned long long seed, const st_render_opts* opts,
                     float* out_image, void* stream);

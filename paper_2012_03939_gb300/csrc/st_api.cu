@@ -281,6 +281,7 @@ struct Plan {
   bool sig = false;           // forward: path signatures
   int max_vl = 0;             // most point lights a view of the call adds to the scene's
   bool bins = false;          // build primary-visibility bins (worth it only for many primary rays)
+  bool bins_reused = false;   // the previous build's lists serve this call (same views, same vertices)
   st_render_opts o{};
 };
 
@@ -404,6 +405,7 @@ st_status ensure_bins(st_scene* s, const Plan& p) {
   if (!grow) return ST_OK;
   cudaDeviceSynchronize();
   drop_graphs(s);
+  s->bins_valid = false;
   long long nP = std::max(P, s->bin_pix_cap), nC = std::max(want, s->bin_cap);
   int nV = std::max((int)p.views.size(), s->bin_views_cap);
   dfree(s->bin_start); dfree(s->bin_cur); dfree(s->bin_list); dfree(s->bin_ok); dfree(s->bin_part);
@@ -420,6 +422,19 @@ st_status ensure_bins(st_scene* s, const Plan& p) {
   if (s->bin_total_host) *s->bin_total_host = 0;
   s->bin_pix_cap = nP; s->bin_cap = nC; s->bin_views_cap = nV;
   return ST_OK;
+}
+
+// what the bins depend on besides the vertices: each view's camera frame, size and cell layout (bit patterns)
+std::vector<uint32_t> bins_key(const Plan& p) {
+  std::vector<uint32_t> k;
+  auto f = [&](float x) { uint32_t u; std::memcpy(&u, &x, 4); k.push_back(u); };
+  for (const DevView& v : p.views) {
+    for (const float3& a : {v.eye, v.fwd, v.right, v.up}) { f(a.x); f(a.y); f(a.z); }
+    f(v.kx); f(v.ky);
+    k.push_back((uint32_t)v.W); k.push_back((uint32_t)v.H); k.push_back((uint32_t)v.kb);
+    k.push_back((uint32_t)v.bin_cell); k.push_back((uint32_t)(v.bin_cell >> 32));
+  }
+  return k;
 }
 
 KCtx make_ctx(st_scene* s, const Plan& p) {
@@ -672,7 +687,7 @@ st_status enqueue_body(st_scene* s, const Plan& p, const KCtx& c, int Q, cudaStr
           s->et_lo, s->et_hi, s->et_cn, l);
     s->launches += 1 + s->et_L;
   }
-  if (p.bins) {
+  if (p.bins && !p.bins_reused) {
     Range r("primary bins");
     // primary-visibility bins of every view: count, scan, fill
     long long P = p.cells;
@@ -773,7 +788,7 @@ st_status enqueue_body(st_scene* s, const Plan& p, const KCtx& c, int Q, cudaStr
 
 std::vector<long long> graph_key(const Plan& p, int Q, const st_scene* s) {
   std::vector<long long> k = {p.kind, p.B, (long long)p.views.size(), Q, p.o.edge_term, p.o.edge_mode, p.o.edge_spp,
-                              p.interior, p.edges, p.o.count_visits, p.bins,
+                              p.interior, p.edges, p.o.count_visits, p.bins, p.bins_reused,
                               p.o.persist_blocks, s->bin_cap, p.max_vl, p.sig, p.sec_tree};
   for (auto& v : p.views) {
     k.push_back(v.W); k.push_back(v.H); k.push_back(v.spp); k.push_back(v.pix_off); k.push_back(v.nvl);
@@ -876,6 +891,8 @@ st_status plan_call(st_scene* s, const st_view* views, int n_views, int default_
   return ST_OK;
 }
 
+st_status launch_call(st_scene* s, Plan& p, const CallArgs& args, int Q, cudaStream_t st);
+
 st_status run_call(st_scene* s, Plan& p, const CallArgs& args, cudaStream_t st) {
   st_status r = ensure_tables(s, (int)p.views.size(), (int)p.segs.size(), p.edges);
   if (r != ST_OK) return r;
@@ -893,9 +910,15 @@ st_status run_call(st_scene* s, Plan& p, const CallArgs& args, cudaStream_t st) 
     }
     s->sh_cap_pairs = (int)p.pairs.size();
   }
+  std::vector<uint32_t> bkey;
   if (p.bins) {
     r = ensure_bins(s, p);
     if (r != ST_OK) return r;
+    bkey = bins_key(p);
+    // a build whose lists overflowed (as far as its readback shows yet) is redone with more room
+    p.bins_reused = s->bins_valid && s->bins_geom == s->geom_version && s->bins_key == bkey &&
+                    !(s->bin_total_host && *s->bin_total_host > s->bin_cap);
+    if (!p.bins_reused) s->bins_valid = false;
   }
   if (p.kind == 0 && p.pixels > s->acc_cap) {
     cudaDeviceSynchronize();
@@ -934,6 +957,17 @@ st_status run_call(st_scene* s, Plan& p, const CallArgs& args, cudaStream_t st) 
       s->xev.push_back(e);
     }
   }
+  st_status res = launch_call(s, p, args, Q, st);
+  if (res == ST_OK && p.bins && !p.bins_reused) {
+    s->bins_valid = true;
+    s->bins_geom = s->geom_version;
+    s->bins_key = std::move(bkey);
+  }
+  return res;
+}
+
+// upload the call's tables and enqueue it: directly, or as the replay of a graph captured once per call shape
+st_status launch_call(st_scene* s, Plan& p, const CallArgs& args, int Q, cudaStream_t st) {
   s->xev_used = 0;
   ST_CUDA(copy_async(s->d_views, p.views.data(), sizeof(DevView) * p.views.size(), cudaMemcpyHostToDevice, st));
   ST_CUDA(copy_async(s->d_segs, p.segs.data(), sizeof(Seg) * p.segs.size(), cudaMemcpyHostToDevice, st));
@@ -1203,6 +1237,7 @@ st_status st_scene_destroy(st_scene* s) {
 
 static st_status update_vertices(st_scene* s, const float* v, void* stream, bool rebuild) {
   if (!s || !v) return fail(ST_ERR_INVALID_ARG, "NULL argument");
+  s->geom_version++;   // the primary-visibility bins are rebuilt by the next call
   cudaStream_t st = (cudaStream_t)stream;
   ST_CUDA(copy_async(s->verts, v, 3 * sizeof(float) * s->nv, cudaMemcpyDeviceToDevice, st));
   cudaError_t e = !rebuild ? bvh_refit(s, st) : s->builder == ST_BVH_LBVH ? bvh_build(s, st) : bvh_build_ploc(s, st);

@@ -157,6 +157,12 @@ struct st_scene {
   long long bin_cap = 0;         // list capacity
   int bin_views_cap = 0;
   int* bin_total_host = nullptr; // pinned: list length the last call needed
+  // the lists are a function of the vertices and of each view's camera, size and cell layout: a call whose key
+  // equals the last build's, with no vertex update since, uses them as they are
+  bool bins_valid = false;
+  unsigned long long bins_geom = 0;     // geom_version of the last build
+  std::vector<uint32_t> bins_key;       // views of the last build (bins_key())
+  unsigned long long geom_version = 0;  // bumped by every vertex update (refit, rebuild)
   float* acc = nullptr;          // [6 * pixels] forward accumulation, compensated FP32 (sum, error) per channel
   unsigned long long* sacc = nullptr;  // [pixels] path-signature sums (bin-space pixel index)
   long long acc_cap = 0;

@@ -1216,8 +1216,8 @@ __global__ void __launch_bounds__(ADJ_BLOCK) k_adjoint(KCtx c, long long j0, int
         }
       }
       if (dF) {
-#pragma unroll
         if (c.np == 7) {
+#pragma unroll
           for (int k = 0; k < 7; ++k) atomicAdd(&dF[7 * key + k], vals[9 + k]);
         } else {   // one specular value for all channels: its derivative is the channels' sum
           atomicAdd(&dF[5 * key], vals[9]); atomicAdd(&dF[5 * key + 1], vals[10]); atomicAdd(&dF[5 * key + 2], vals[11]);
