@@ -388,11 +388,18 @@ def run_ours(args):
         step_views, Ns, step_target = views, N, target
     inv_s = 1.0 / (3 * Ns)
 
+    def new_vertices(scn):
+        # an optimisation iteration renders updated vertices: the refit (on the same vertices here, so that the
+        # ray counts stay exact) makes every step redo what depends on them, the BVH boxes and the
+        # primary-visibility lists, which calls on unchanged vertices and views would otherwise reuse
+        scn.refit(scn.vertices)
+
     def step(fopts, bopts):
         if adam:
             rec.fopts, rec.bopts = fopts, bopts
             rec.step()
             return
+        new_vertices(scene)
         scene.render(views, B, seed, fopts, out=img)
         g = (img - target) * (2 * inv_n)
         dV.zero_()
@@ -400,6 +407,7 @@ def run_ours(args):
         scene.backward(views, B, seed, g, bopts, d_vertices=dV, d_face_params=dF)
 
     def counts(fopts, bopts):
+        new_vertices(scene)
         scene.render(step_views, B, seed, fopts, out=img)
         a = scene.stats()
         g = (img - step_target) * (2 * inv_s)
@@ -439,6 +447,7 @@ def run_ours(args):
         for _ in range(args.warmup):
             step(fb, bb)
         torch.cuda.synchronize()
+        new_vertices(scene)
         scene.render(views, B, seed, fb, out=img)
         torch.cuda.synchronize()
         sf = scene.stats()
@@ -458,7 +467,9 @@ def run_ours(args):
     sf, sb = counts(fb, bb)
     seg_fwd = sf["extension_rays"] + sf["shadow_rays"]
     seg_step = seg_fwd + sb["extension_rays"] + sb["shadow_rays"]
-    launches_step = sf["kernel_launches"] + sb["kernel_launches"]
+    # + the refit of every step (bottom-up boxes, 4-wide boxes, three mesh-statistics kernels) and, in an Adam
+    # iteration, the upload of the face parameters
+    launches_step = sf["kernel_launches"] + sb["kernel_launches"] + (6 if adam else 5)
     assert sf["device_error"] == 0 and sb["device_error"] == 0
 
     with ClockSampler(local) as clk:
@@ -468,7 +479,11 @@ def run_ours(args):
     pv_steps = args.per_view_steps or max(2, args.steps // 3)
     ms_pv = timed(lambda: step(fp, bp), pv_steps, 1)
     value_pv = seg_step * pv_steps * world / (ms_pv / 1000.0) / 1e6
-    ms_fwd = timed(lambda: scene.render(step_views, B, seed, fb, out=img), args.steps, 2)
+    def fwd_step():
+        new_vertices(scene)
+        scene.render(step_views, B, seed, fb, out=img)
+
+    ms_fwd = timed(fwd_step, args.steps, 2)
     value_fwd = seg_fwd * args.steps * world / (ms_fwd / 1000.0) / 1e6
 
     # the same step with the secondary-visibility edge term added (one edge
@@ -492,6 +507,7 @@ def run_ours(args):
     # point-light shadow edges (scenes with point lights) and interpolated
     # vertex normals (a second scene created with the option)
     def step_with(scn, fopts, bopts):
+        new_vertices(scn)
         scn.render(views, B, seed, fopts, out=img)
         g = (img - target) * (2 * inv_n)
         dV.zero_()
@@ -572,7 +588,8 @@ def run_ours(args):
                        "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback"}}
         return out
 
-    roofline = roof_record("k_extend (closest-hit BVH traversal)", visits, tests, rays, ext_ms, ext_n)
+    roofline = roof_record("closest hit: k_raygen bin-cell tests + k_extend BVH traversal", visits, tests, rays, ext_ms,
+                           ext_n)
     roofline_shadow = roof_record("k_shadow (any-hit BVH traversal)", sh_visits, sh_tests, sh_rays, sh_ms, sh_n)
     # DRAM bytes per query from the committed ncu capture (cold caches) times this step's queries per launch
     for rl, per_query, q, n in ((roofline, tr, rays, ext_n), (roofline_shadow, tr_sh, sh_rays, sh_n)):
