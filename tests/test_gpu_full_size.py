@@ -1,7 +1,9 @@
 """Full-size parity of the images and interior gradients with the FP64 oracle.
 
 The large workloads are rendered whole, in the benchmark's launch configuration
-(batched, CUDA graph, 8M-path chunks); the oracle follows a seeded sample of
+(batched, CUDA graph, 16M-path chunks: the autotuner's pick for the headline
+and scale workloads; other chunk sizes give bitwise the same images, which the
+overlap and launch-path tests check); the oracle follows a seeded sample of
 about 4096 of their pixels with the same counters, so it computes exactly the
 paths the GPU traced there. Per pixel the bar is |gpu - oracle| <= 1e-4 |oracle|
 + 1e-7 on >= 99.9 % of channels and a mean error <= 1e-5.
@@ -47,7 +49,7 @@ def st():
 
 
 def _bench_opts(st, **kw):
-    return st.make_opts(mode="batched", use_graph=1, chunk_paths=1 << 23, **kw)
+    return st.make_opts(mode="batched", use_graph=1, chunk_paths=1 << 24, **kw)
 
 
 @pytest.mark.parametrize("name,views,npix,ngrad,div_max", CASES)

@@ -342,8 +342,9 @@ def test_primary_bins_and_bvh_fallback_views(st):
 
 @pytest.mark.parametrize("name,npix,views", [("batched", 256, None), ("scale", 64, 8)])
 def test_full_size_gradient_in_bench_configuration(st, name, npix, views):
-    # the benchmark's launch configuration (batched, CUDA graph, 8M-path chunks, silhouette
-    # edge term) at full size; dL/dI nonzero on a pixel sample so the oracle can follow
+    # the benchmark's launch configuration (batched, CUDA graph, 16M-path chunks as the autotuner
+    # picks for these workloads, silhouette edge term) at full size; dL/dI nonzero on a pixel
+    # sample so the oracle can follow
     sc = S.make(name)
     if views:
         sc = sc.subset_views(range(views))
@@ -351,7 +352,7 @@ def test_full_size_gradient_in_bench_configuration(st, name, npix, views):
     rows = rows_of(sc, pix)
     w = np.zeros((sc.n_pixels, 3))
     w[rows] = np.random.default_rng(14).normal(size=(len(pix), 3))
-    opts = st.make_opts(mode="batched", use_graph=1, chunk_paths=1 << 23, edge_term=1, edge_mode=0)
+    opts = st.make_opts(mode="batched", use_graph=1, chunk_paths=1 << 24, edge_term=1, edge_mode=0)
     dV, dF = _grad_gpu(st, sc, sc.max_bounces, 2025, w, opts)
     osc = O.OracleScene(sc)
     prm = O.params(sc.max_bounces, 2025, edge_mode=0)
