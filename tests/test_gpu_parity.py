@@ -362,3 +362,72 @@ def test_full_size_gradient_in_bench_configuration(st, name, npix, views):
     r_tot = rel_l2([dV, dF], [rv + ev, rf])         # vertices: interior + edge term
     assert r_int <= GRAD_REL, r_int
     assert r_tot <= 5e-3, r_tot
+
+
+@pytest.mark.parametrize("n_faces", [1, 2])
+def test_one_and_two_triangle_scenes(st, n_faces):
+    # the smallest meshes: a single face (no internal node: traversal tests the one
+    # leaf, the 4-wide tree is empty) and two faces sharing an edge (one internal
+    # node); every edge is a boundary edge except the shared one. Image, interior
+    # gradient and edge term against the oracle; a refit equals a fresh scene.
+    V = np.array([[-0.8, -0.6, 0.0], [0.7, -0.7, 0.1], [0.6, 0.8, 0.0], [-0.7, 0.7, -0.1]], np.float32)
+    F = np.array([[0, 1, 2], [0, 2, 3]], np.int32)[:n_faces]
+    P = np.array([[0.7, 0.5, 0.3, 0.04, 0.3], [0.2, 0.6, 0.8, 0.04, 0.5]], np.float32)[:n_faces]
+    views = [S.View((0.2, -0.3, 3.0), (0.0, 0.0, 0.0), (0, 1, 0), 45.0, 24, 20, 4, 0),
+             S.View((-1.5, 0.4, 2.2), (0.0, 0.1, 0.0), (0, 1, 0), 50.0, 16, 16, 3, 480)]
+    sc = S.Scene("tri%d" % n_faces, V, F, P, light_pos=np.array([[0.3, 0.5, 2.0]], np.float32),
+                 light_intensity=np.array([[6.0, 6.0, 6.0]], np.float32), views=views, max_bounces=2)
+    img, stats = gpu_image(st, sc, 2, 19)
+    ref, seg = O.render_pixels(O.OracleScene(sc), O.params(2, 19), O.all_pixels(sc))
+    assert_image_parity(img, ref, what="%d face(s)" % n_faces)
+    assert stats["extension_rays"] + stats["shadow_rays"] == seg
+    assert img.max() > 0.0
+
+    w = np.random.default_rng(20).normal(size=(sc.n_pixels, 3))
+    dVi, dFi = _grad_gpu(st, sc, 2, 19, w, st.make_opts(edge_term=0))
+    rv, rf, _ = O.grad_pixels(O.OracleScene(sc), O.params(2, 19), O.all_pixels(sc), w)
+    r = rel_l2([dVi, dFi], [rv, rf])
+    assert r <= GRAD_REL, r
+    dVe, _ = _grad_gpu(st, sc, 2, 19, w, st.make_opts(edge_term=1, edge_mode=0))
+    ev, _ = O.edge_grad(O.OracleScene(sc), O.params(2, 19, edge_mode=0), w)
+    assert np.abs(ev).max() > 0.0
+    r = rel_l2([dVe - dVi], [ev])
+    assert r <= 5e-3, r
+
+    V2 = V + np.float32(0.05) * np.random.default_rng(21).normal(size=V.shape).astype(np.float32)
+    scene = st.Scene.from_scene(sc)
+    scene.refit(torch.from_numpy(V2).cuda())
+    refit = scene.render(views, 2, 19).cpu().numpy()
+    scene.close()
+    fresh, _ = gpu_image(st, sc, 2, 19, vertices=V2)
+    np.testing.assert_array_equal(refit, fresh)
+
+
+def test_maximum_bounces_and_lights(st):
+    # ST_MAX_BOUNCES (8) vertices per path and ST_MAX_LIGHTS (8) point lights per path, six of the scene's
+    # and two of each view's own, on the concave three-plane scene where paths keep bouncing between the
+    # walls: image (with path signatures) and interior gradient against the oracle
+    sc = S.small_variant(S.make("color_bleed"), n_views=2, max_res=20, spp=2)
+    rng = np.random.default_rng(30)
+    sc.light_pos = rng.uniform(0.3, 1.8, size=(6, 3)).astype(np.float32)   # inside the open corner
+    sc.light_intensity = rng.uniform(0.5, 2.0, size=(6, 3)).astype(np.float32)
+    sc.views = S.with_view_lights(sc.views, intensity=(1.5, 1.5, 1.5))
+    B = 8
+    scene = st.Scene.from_scene(sc)
+    sig = torch.zeros(sc.n_pixels, dtype=torch.int64, device="cuda")
+    img = scene.render(sc.views, B, 23, signatures=sig).cpu().numpy()
+    stats = scene.stats()
+    assert stats["device_error"] == 0
+    scene.close()
+    osc = O.OracleScene(sc)
+    pix = O.all_pixels(sc)
+    ref, seg = O.render_pixels(osc, O.params(B, 23), pix)
+    assert_image_parity(img, ref, what="B = 8, 8 lights")
+    assert stats["extension_rays"] + stats["shadow_rays"] == seg
+    same = sig.cpu().numpy().view(np.uint64) == O.render_signatures(osc, O.params(B, 23), pix)
+    assert same.mean() >= 0.999, same.mean()
+    w = rng.normal(size=(sc.n_pixels, 3))
+    dV, dF = _grad_gpu(st, sc, B, 23, w, st.make_opts(edge_term=0))
+    rv, rf, _ = O.grad_pixels(osc, O.params(B, 23), pix, w)
+    r = rel_l2([dV, dF], [rv, rf])
+    assert r <= GRAD_REL, r
