@@ -54,6 +54,11 @@ def test_reused_bins_equal_fresh_builds(st):
     assert lc == la
     np.testing.assert_array_equal(a, b)
     np.testing.assert_array_equal(a, c)
+    # per-view calls (host-sized grids) and ungraphed calls reuse the same lists
+    for opts in (st.make_opts(mode="per_view", use_graph=0), st.make_opts(use_graph=0)):
+        pv = scene.render(vs, B, seed, opts).cpu().numpy()
+        assert scene.stats()["device_error"] == 0
+        np.testing.assert_array_equal(pv, a)
 
     # the adjoint of the same views reuses the forward's lists: same gradient as a scene that builds them
     g = torch.from_numpy(np.random.default_rng(5).normal(size=a.shape).astype(np.float32)).cuda()

@@ -431,3 +431,28 @@ def test_maximum_bounces_and_lights(st):
     rv, rf, _ = O.grad_pixels(osc, O.params(B, 23), pix, w)
     r = rel_l2([dV, dF], [rv, rf])
     assert r <= GRAD_REL, r
+
+
+def test_many_small_views_in_one_call(st):
+    # 5000 views of 2 x 3 pixels (uneven spp, some with their own lights, the widest view 1 x 1) in one
+    # batched, graph-captured call: 5000+ job segments, each a few jobs, found by every job's segment
+    # search; every pixel against the oracle, and the gradient on a pixel sample
+    sc = S.tiny()
+    n = 5000
+    rng = np.random.default_rng(40)
+    vs = S.fibonacci_views(n, np.full(n, 2), np.full(n, 3), rng.choice([1, 2, 3], size=n), fov=20.0)
+    vs[7] = S.View(vs[7].eye, vs[7].target, vs[7].up, 20.0, 1, 1, 4)
+    S._pack_offsets(vs)
+    vs[::97] = S.with_view_lights(vs[::97], intensity=(2.0, 2.0, 2.0))
+    sc.views = vs
+    img, stats = gpu_image(st, sc, 2, 29)
+    ref, seg = O.render_pixels(O.OracleScene(sc), O.params(2, 29), O.all_pixels(sc))
+    assert_image_parity(img, ref, what="5000 views")
+    assert stats["extension_rays"] + stats["shadow_rays"] == seg
+    pix = sample_pixels(sc, 400, seed=41)
+    w = np.zeros((sc.n_pixels, 3))
+    w[rows_of(sc, pix)] = rng.normal(size=(len(pix), 3))
+    dV, dF = _grad_gpu(st, sc, 2, 29, w, st.make_opts(edge_term=0))
+    rv, rf, _ = O.grad_pixels(O.OracleScene(sc), O.params(2, 29), pix, w[rows_of(sc, pix)])
+    r = rel_l2([dV, dF], [rv, rf])
+    assert r <= GRAD_REL, r
