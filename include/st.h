@@ -239,7 +239,11 @@ st_status st_set_face_params(st_scene* scene, const float* face_params, void* st
  * A call of at least 2^20 primary rays finds their hits in screen-space leaf
  * lists of its views, kept on the device: a later call (forward or backward)
  * with the same views (camera, size) and no vertex update since uses them
- * without building them again. */
+ * without building them again. Such a call also bins the leaves, seen from each
+ * scene light outside the mesh's bounding sphere, into a frustum of cells, and
+ * the shadow rays to that light test their cell's leaves instead of traversing
+ * the BVH (the same test: the same visibility); these lists are rebuilt after a
+ * vertex update. */
 st_status st_render(st_scene* scene, const st_view* views, int n_views, int default_spp,
                     int max_bounces, unsigned long long seed, const st_render_opts* opts,
                     float* out_image, void* stream);

@@ -282,6 +282,8 @@ struct Plan {
   int max_vl = 0;             // most point lights a view of the call adds to the scene's
   bool bins = false;          // build primary-visibility bins (worth it only for many primary rays)
   bool bins_reused = false;   // the previous build's lists serve this call (same views, same vertices)
+  bool lbins = false;         // point-light shadow lists (scene lights, calls with many rays)
+  bool lbins_reused = false;  // ... as the last build left them (no vertex update since)
   st_render_opts o{};
 };
 
@@ -424,6 +426,44 @@ st_status ensure_bins(st_scene* s, const Plan& p) {
   return ST_OK;
 }
 
+void free_light_bins(st_scene* s) {
+  dfree(s->d_lviews); dfree(s->lbin_start); dfree(s->lbin_cur); dfree(s->lbin_list); dfree(s->lbin_ok);
+  dfree(s->lbin_part);
+  s->lbin_cells = 0;
+  s->lbin_cap = 0;
+}
+
+// The point-light shadow lists, allocated by the first call that uses them: lbin_res^2 cells per scene light
+// (lbin_res = 2 sqrt(F), in [16, 2048]: a closed mesh seen from a light outside it turns about F/2 faces toward
+// the light, a few per ten cells of its disk); the list store grows when the last build's total (read back as
+// for the primary-visibility bins) overflowed it.
+st_status ensure_light_bins(st_scene* s) {
+  if (s->lbin_res == 0) s->lbin_res = (int)std::min(2048.0, std::max(16.0, std::ceil(2.0 * std::sqrt((double)s->nf))));
+  const long long R = s->lbin_res, P = (long long)s->nl * R * R;
+  long long want = std::max<long long>(4 * P, 1 << 20);
+  if (s->lbin_total_host && *s->lbin_total_host > s->lbin_cap) want = std::max(want, 2LL * *s->lbin_total_host);
+  want = std::min<long long>(want, 0x7ffffff0LL);
+  if (s->lbin_start && want <= s->lbin_cap) return ST_OK;
+  cudaDeviceSynchronize();
+  drop_graphs(s);
+  s->lbins_valid = false;
+  long long nC = std::max(want, s->lbin_cap);
+  free_light_bins(s);
+  long long nb = (P + 4095) / 4096;
+  if (dalloc(&s->d_lviews, (size_t)s->nl) != cudaSuccess || dalloc(&s->lbin_start, (size_t)P + 1) != cudaSuccess ||
+      dalloc(&s->lbin_cur, (size_t)P) != cudaSuccess || dalloc(&s->lbin_list, (size_t)nC) != cudaSuccess ||
+      dalloc(&s->lbin_ok, (size_t)s->nl) != cudaSuccess || dalloc(&s->lbin_part, (size_t)nb) != cudaSuccess) {
+    free_light_bins(s);
+    cudaGetLastError();
+    return fail(ST_ERR_OOM, "point-light shadow lists");
+  }
+  if (!s->lbin_total_host) cudaMallocHost((void**)&s->lbin_total_host, sizeof(int));
+  if (s->lbin_total_host) *s->lbin_total_host = 0;
+  s->lbin_cells = P;
+  s->lbin_cap = nC;
+  return ST_OK;
+}
+
 // what the bins depend on besides the vertices: each view's camera frame, size and cell layout (bit patterns)
 std::vector<uint32_t> bins_key(const Plan& p) {
   std::vector<uint32_t> k;
@@ -446,6 +486,9 @@ KCtx make_ctx(st_scene* s, const Plan& p) {
   c.edge_flag = s->edge_flag; c.edge_cand = s->edge_cand; c.edge_ncand = s->edge_ncand;
   c.sh_cand = s->sh_cand; c.sh_ncand = s->sh_ncand;
   c.bin_start = p.bins ? s->bin_start : nullptr;   // nullptr: every primary ray traverses the BVH
+  c.lviews = s->d_lviews;
+  c.lbin_start = p.lbins ? s->lbin_start : nullptr;   // nullptr: every shadow ray traverses the BVH
+  c.lbin_list = s->lbin_list; c.lbin_ok = s->lbin_ok; c.lbin_cap = s->lbin_cap; c.lbin_cells = s->lbin_cells;
   c.bin_list = s->bin_list; c.bin_cur = s->bin_cur; c.bin_ok = s->bin_ok;
   c.bin_cap = s->bin_cap; c.bin_pixels = p.pixels; c.bin_cells = p.cells;
   c.cull = s->closed ? 1 : 0; c.mstat = s->mstat;
@@ -705,6 +748,30 @@ st_status enqueue_body(st_scene* s, const Plan& p, const KCtx& c, int Q, cudaStr
     ST_CUDA(cudaMemcpyAsync(s->bin_total_host, s->bin_start + P, sizeof(int), cudaMemcpyDeviceToHost, st));
     s->launches += 6;
   }
+  if (p.lbins && !p.lbins_reused) {
+    Range r("light bins");
+    // a frustum per scene light from the current vertex bounds, then count, scan and fill as for the views
+    const int nl = s->nl;
+    const long long P = s->lbin_cells;
+    const long long nb = (P + 4095) / 4096;
+    KCtx cl = c;
+    cl.views = s->d_lviews;
+    cl.bin_start = s->lbin_start; cl.bin_list = s->lbin_list; cl.bin_cur = s->lbin_cur; cl.bin_ok = s->lbin_ok;
+    cl.bin_cap = s->lbin_cap; cl.bin_cells = P;
+    dim3 g((s->nf + 127) / 128, (unsigned)nl);
+    k_fill_int<<<(nl + 127) / 128, 128, 0, st>>>(s->lbin_ok, nl, 1);
+    k_light_views<<<nl, LVIEW_BLOCK, 0, st>>>(s->lights, s->verts, s->nv, s->mstat, s->lbin_res, s->d_lviews,
+                                             s->lbin_ok);
+    ST_CUDA(cudaMemsetAsync(s->lbin_cur, 0, sizeof(int) * P, st));
+    k_bin<0><<<g, 128, 0, st>>>(cl, nl, s->lbin_ok);
+    k_scan_blocks<<<(unsigned)nb, SCAN_BLOCK, 0, st>>>(s->lbin_cur, s->lbin_start, P, s->lbin_part);
+    k_scan_parts<<<1, SCAN_BLOCK, 0, st>>>(s->lbin_part, (int)nb, s->lbin_start, P);
+    k_scan_add<<<(unsigned)nb, SCAN_BLOCK, 0, st>>>(s->lbin_start, P, s->lbin_part);
+    ST_CUDA(cudaMemsetAsync(s->lbin_cur, 0, sizeof(int) * P, st));
+    k_bin<1><<<g, 128, 0, st>>>(cl, nl, s->lbin_ok);
+    ST_CUDA(cudaMemcpyAsync(s->lbin_total_host, s->lbin_start + P, sizeof(int), cudaMemcpyDeviceToHost, st));
+    s->launches += 7;
+  }
   if (p.shadow && !p.pairs.empty()) {
     int np = (int)p.pairs.size();
     dim3 g((s->n_edges + 255) / 256, (unsigned)np);
@@ -788,7 +855,8 @@ st_status enqueue_body(st_scene* s, const Plan& p, const KCtx& c, int Q, cudaStr
 
 std::vector<long long> graph_key(const Plan& p, int Q, const st_scene* s) {
   std::vector<long long> k = {p.kind, p.B, (long long)p.views.size(), Q, p.o.edge_term, p.o.edge_mode, p.o.edge_spp,
-                              p.interior, p.edges, p.o.count_visits, p.bins, p.bins_reused,
+                              p.interior, p.edges, p.o.count_visits, p.bins, p.bins_reused, p.lbins,
+                              p.lbins_reused, s->lbin_cap,
                               p.o.persist_blocks, s->bin_cap, p.max_vl, p.sig, p.sec_tree};
   for (auto& v : p.views) {
     k.push_back(v.W); k.push_back(v.H); k.push_back(v.spp); k.push_back(v.pix_off); k.push_back(v.nvl);
@@ -877,6 +945,7 @@ st_status plan_call(st_scene* s, const st_view* views, int n_views, int default_
   // below about a million primary rays the fixed cost of building the bins
   // (seven launches) exceeds what they save; those calls traverse the BVH
   p.bins = p.total >= (1LL << 20);
+  p.lbins = p.bins && s->nl > 0;   // the same threshold: the build is a few launches over the faces
   {
     std::vector<std::pair<long long, long long>> rg;
     for (int i = 0; i < n_views; ++i)
@@ -920,6 +989,13 @@ st_status run_call(st_scene* s, Plan& p, const CallArgs& args, cudaStream_t st) 
                     !(s->bin_total_host && *s->bin_total_host > s->bin_cap);
     if (!p.bins_reused) s->bins_valid = false;
   }
+  if (p.lbins) {
+    r = ensure_light_bins(s);
+    if (r != ST_OK) return r;
+    p.lbins_reused = s->lbins_valid && s->lbins_geom == s->geom_version &&
+                     !(s->lbin_total_host && *s->lbin_total_host > s->lbin_cap);
+    if (!p.lbins_reused) s->lbins_valid = false;
+  }
   if (p.kind == 0 && p.pixels > s->acc_cap) {
     cudaDeviceSynchronize();
     drop_graphs(s);
@@ -962,6 +1038,10 @@ st_status run_call(st_scene* s, Plan& p, const CallArgs& args, cudaStream_t st) 
     s->bins_valid = true;
     s->bins_geom = s->geom_version;
     s->bins_key = std::move(bkey);
+  }
+  if (res == ST_OK && p.lbins && !p.lbins_reused) {
+    s->lbins_valid = true;
+    s->lbins_geom = s->geom_version;
   }
   return res;
 }
@@ -1031,6 +1111,8 @@ void destroy(st_scene* s) {
   dfree(s->lights); dfree(s->env_tex); dfree(s->env_alias); dfree(s->edge_v); dfree(s->edge_f);
   dfree(s->edge_flag); dfree(s->edge_cand); dfree(s->edge_ncand);
   dfree(s->sh_flag); dfree(s->sh_cand); dfree(s->sh_ncand); dfree(s->d_pairs); dfree(s->d_views); dfree(s->d_segs);
+  free_light_bins(s);
+  if (s->lbin_total_host) cudaFreeHost(s->lbin_total_host);
   dfree(s->bin_start); dfree(s->bin_cur); dfree(s->bin_list); dfree(s->bin_ok); dfree(s->bin_part);
   dfree(s->acc); dfree(s->sacc); dfree(s->mstat); dfree(s->vnrm); dfree(s->vf_start); dfree(s->vf_list); dfree(s->dN);
   dfree(s->et_lo); dfree(s->et_hi); dfree(s->et_cn);
@@ -1237,7 +1319,7 @@ st_status st_scene_destroy(st_scene* s) {
 
 static st_status update_vertices(st_scene* s, const float* v, void* stream, bool rebuild) {
   if (!s || !v) return fail(ST_ERR_INVALID_ARG, "NULL argument");
-  s->geom_version++;   // the primary-visibility bins are rebuilt by the next call
+  s->geom_version++;   // the primary-visibility bins and point-light lists are rebuilt by the next call
   cudaStream_t st = (cudaStream_t)stream;
   ST_CUDA(copy_async(s->verts, v, 3 * sizeof(float) * s->nv, cudaMemcpyDeviceToDevice, st));
   cudaError_t e = !rebuild ? bvh_refit(s, st) : s->builder == ST_BVH_LBVH ? bvh_build(s, st) : bvh_build_ploc(s, st);

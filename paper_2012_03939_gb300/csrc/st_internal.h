@@ -163,6 +163,19 @@ struct st_scene {
   unsigned long long bins_geom = 0;     // geom_version of the last build
   std::vector<uint32_t> bins_key;       // views of the last build (bins_key())
   unsigned long long geom_version = 0;  // bumped by every vertex update (refit, rebuild)
+  // point-light shadow lists: per scene light an lbin_res x lbin_res frustum of cells (k_light_views), built
+  // like the primary-visibility bins; they depend on the vertices only (the scene's lights are fixed)
+  st::DevView* d_lviews = nullptr;  // [nl]
+  int* lbin_start = nullptr;        // [cells + 1]
+  int* lbin_cur = nullptr;          // [cells]
+  int* lbin_list = nullptr;         // [lbin_cap]
+  int* lbin_ok = nullptr;           // [nl]
+  int* lbin_part = nullptr;         // scan block sums
+  int* lbin_total_host = nullptr;   // pinned: list length the last build needed
+  long long lbin_cells = 0, lbin_cap = 0;
+  int lbin_res = 0;
+  bool lbins_valid = false;
+  unsigned long long lbins_geom = 0;
   float* acc = nullptr;          // [6 * pixels] forward accumulation, compensated FP32 (sum, error) per channel
   unsigned long long* sacc = nullptr;  // [pixels] path-signature sums (bin-space pixel index)
   long long acc_cap = 0;

@@ -51,6 +51,14 @@ struct KCtx {
   long long bin_cap;
   long long bin_pixels;   // pixels of the call (accumulation space)
   long long bin_cells;    // cells of the primary-visibility bins (kb x kb per pixel of each view)
+  // point-light shadow lists: per scene light, a frustum from the light around the mesh (k_light_views) whose
+  // cells list the leaves a shadow ray to that light may cross (see light_bin_range)
+  const DevView* lviews;
+  const int* lbin_start;  // nullptr: shadow rays to scene lights traverse the BVH
+  const int* lbin_list;
+  const int* lbin_ok;     // per scene light: 1 = its shadow rays may use the lists
+  long long lbin_cap;
+  long long lbin_cells;
   float* acc;             // per-pixel compensated sample sums, (sum, error) x 3 (bin-space pixel index)
   int cull;               // the mesh is one closed, consistently wound surface (see MeshStat)
   const MeshStat* mstat;
@@ -372,6 +380,7 @@ __global__ void __launch_bounds__(EXT_BLOCK) k_sh_prep(KCtx c, long long j0, int
 // the BVH for its primary rays.
 constexpr float BIN_PAD = 0.02f;
 constexpr int BIN_MAX_BOX = 1 << 16;   // a larger screen box sends its view back to the BVH
+constexpr int BIN_ILP = 2;              // list entries a lane tests per step
 
 
 // Screen-space edge functions of a projected triangle, oriented so the inside
@@ -380,6 +389,13 @@ struct ScreenTri {
   float a[3], b[3], c[3];
   bool degenerate;
 };
+
+// bin-cell coordinates of a point at rel = X - eye and depth z along fwd (cells: pixels times v.kb)
+__device__ __forceinline__ float2 cell_xy(const DevView& v, float3 rel, float z) {
+  const float zz = fmaxf(z, Z_NEAR);
+  return make_float2((dot3(rel, v.right) / (zz * v.kx) + 1.0f) * (float)(v.W * v.kb) * 0.5f,
+                     (1.0f - dot3(rel, v.up) / (zz * v.ky)) * (float)(v.H * v.kb) * 0.5f);
+}
 
 // 0: cannot be hit from the eye or off screen; 1: box in (x0..x1, y0..y1);
 // -1: view must use the BVH
@@ -396,9 +412,9 @@ __device__ __forceinline__ int leaf_screen_box(const DevView& v, float4 a, float
     float z = dot3(rel, v.fwd);
     front += z > Z_NEAR;
     behind += z <= 0.0f;
-    float zz = fmaxf(z, Z_NEAR);
-    px[k] = (dot3(rel, v.right) / (zz * v.kx) + 1.0f) * (float)Wc * 0.5f;
-    py[k] = (1.0f - dot3(rel, v.up) / (zz * v.ky)) * (float)Hc * 0.5f;
+    float2 q = cell_xy(v, rel, z);
+    px[k] = q.x;
+    py[k] = q.y;
   }
   if (behind == 3) return 0;
   if (front < 3) return -1;
@@ -466,6 +482,7 @@ __global__ void k_bin(KCtx c, int n_views, int* ok) {
   int vi = blockIdx.y;
   if (li >= c.nf || vi >= n_views) return;
   DevView v = c.views[vi];
+  if (v.W <= 0) return;   // a light frustum that does not exist (k_light_views)
   int x0, y0, x1, y1;
   ScreenTri et;
   float4 ta = __ldg(&c.tri[3 * li]), tb = __ldg(&c.tri[3 * li + 1]), tc = __ldg(&c.tri[3 * li + 2]);
@@ -486,6 +503,125 @@ __global__ void k_bin(KCtx c, int n_views, int* ok) {
         else atomicOr(c.err, ERR_INDEX);
       }
     }
+}
+
+// ------------------------------------------------------------------ point-light shadow lists
+// A shadow ray from x to a point light L lies on the line through L and x, so
+// every triangle it can cross projects, seen from L, onto x's own projection.
+// Each scene light gets a square frustum of R x R cells from L around the
+// mesh's bounding sphere (centred on MeshStat's box, radius the farthest
+// vertex), binned by k_bin like a camera view: the shadow ray tests the leaves
+// of x's cell with the traversal's watertight test and bound, so it finds a
+// crossing exactly when the traversal does. A closed, consistently wound
+// surface lets k_bin drop the faces wound away from L: a segment that enters
+// the solid must leave it through a face wound toward L before reaching L,
+// which lies outside. A light inside the sphere (or too close to it) has no
+// frustum: W = H = 0, ok = 0, and its shadow rays traverse the BVH.
+// One block per light: the block finds the radius, thread 0 writes the view.
+constexpr int LVIEW_BLOCK = 256;
+__global__ void __launch_bounds__(LVIEW_BLOCK) k_light_views(const float4* lights, const float* V, int nv,
+                                                             const MeshStat* m, int R, DevView* lv, int* ok) {
+  __shared__ float red[LVIEW_BLOCK];
+  const int j = blockIdx.x;
+  float3 lo = mk3(from_ordered(m->lo[0]), from_ordered(m->lo[1]), from_ordered(m->lo[2]));
+  float3 hi = mk3(from_ordered(m->hi[0]), from_ordered(m->hi[1]), from_ordered(m->hi[2]));
+  float3 ctr = (lo + hi) * 0.5f;
+  float r2 = 0.0f;
+  for (int i = threadIdx.x; i < nv; i += LVIEW_BLOCK) {
+    float3 d = mk3(V[3 * i], V[3 * i + 1], V[3 * i + 2]) - ctr;
+    r2 = fmaxf(r2, dot3(d, d));
+  }
+  red[threadIdx.x] = r2;
+  __syncthreads();
+  for (int h = LVIEW_BLOCK / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + h]);
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  float rad = sqrtf(red[0]) * 1.001f + 1e-6f;
+  float3 L = xyz(lights[2 * j]);
+  float3 dv = ctr - L;
+  float d = len3(dv);
+  DevView v;
+  v.eye = L;
+  v.kb = 1;
+  v.spp = 1;
+  v.off = 0;
+  v.pix_off = 0;
+  v.bin_base = 0;
+  v.nvl = 0;
+  v.bin_cell = (long long)j * R * R;
+  for (int k = 0; k < 4; ++k) v.vl[k] = make_float4(0, 0, 0, 0);
+  if (!(d > 1.02f * rad + 1e-3f)) {
+    v.fwd = v.right = v.up = mk3(0, 0, 0);
+    v.kx = v.ky = 1.0f;
+    v.W = v.H = 0;
+    lv[j] = v;
+    ok[j] = 0;
+    return;
+  }
+  float3 f = dv * (1.0f / d);
+  float3 a = fabsf(f.y) < 0.9f ? mk3(0, 1, 0) : mk3(1, 0, 0);
+  float3 r = norm3(cross3(f, a));
+  v.fwd = f;
+  v.right = r;
+  v.up = cross3(r, f);
+  float sn = rad / d;
+  v.kx = v.ky = 1.01f * sn / sqrtf(1.0f - sn * sn);   // tangent of the sphere's half-angle, with a margin
+  v.W = v.H = R;
+  lv[j] = v;
+}
+
+// the list of shadow rays from p to scene light j, or (-1, -1): traverse the BVH
+__device__ __forceinline__ int2 light_bin_range(const KCtx& c, int j, float3 p) {
+  if (c.lbin_start == nullptr || !c.lbin_ok[j] || c.lbin_start[c.lbin_cells] > c.lbin_cap) return make_int2(-1, -1);
+  const DevView& v = c.lviews[j];
+  float3 rel = p - v.eye;
+  float z = dot3(rel, v.fwd);
+  if (!(z > Z_NEAR) || v.W <= 0) return make_int2(-1, -1);
+  float2 q = cell_xy(v, rel, z);
+  int x = (int)floorf(q.x), y = (int)floorf(q.y);
+  if (!(q.x >= 0.0f) || !(q.y >= 0.0f) || x >= v.W || y >= v.H) return make_int2(-1, -1);
+  long long k = v.bin_cell + (long long)y * v.W + x;
+  return make_int2(c.lbin_start[k], c.lbin_start[k + 1]);
+}
+
+// any hit of the ray (o, d) before tmax among the listed leaves, skipping face `exclude`: the traversal's leaf
+// test, BIN_ILP entries at a time
+template <bool STATS>
+__device__ __forceinline__ bool bin_any_hit(const KCtx& c, float3 o, float3 d, float tmax, int exclude, int2 br,
+                                            TraceStats* ts) {
+  RayPre rp = ray_pre(o, d);
+  if (br.y > c.lbin_cap || br.x > br.y) { atomicOr(c.err, ERR_INDEX); return false; }
+  for (int k = br.x; k < br.y; k += BIN_ILP) {
+    int li[BIN_ILP];
+    bool bad = false;
+#pragma unroll
+    for (int u = 0; u < BIN_ILP; ++u) {
+      li[u] = k + u < br.y ? __ldg(&c.lbin_list[k + u]) : -1;
+      bad |= k + u < br.y && (unsigned)li[u] >= (unsigned)c.nf;
+    }
+    if (bad) {
+      atomicOr(c.err, ERR_INDEX);
+      continue;
+    }
+    float4 ta[BIN_ILP], tb[BIN_ILP], tc[BIN_ILP];
+#pragma unroll
+    for (int u = 0; u < BIN_ILP; ++u) {
+      int l = li[u] >= 0 ? li[u] : li[0];
+      ta[u] = __ldg(&c.tri[3 * l]);
+      tb[u] = __ldg(&c.tri[3 * l + 1]);
+      tc[u] = __ldg(&c.tri[3 * l + 2]);
+    }
+#pragma unroll
+    for (int u = 0; u < BIN_ILP; ++u) {
+      if (li[u] < 0) continue;
+      if (STATS) ts->tests++;
+      if (__float_as_int(ta[u].w) == exclude) continue;
+      if (tri_test(rp, xyz(ta[u]), xyz(tb[u]), xyz(tc[u]), tmax) > 0.0f) return true;
+    }
+  }
+  return false;
 }
 
 __device__ __forceinline__ int view_of_pixel(const KCtx& c, int n_views, long long p) {
@@ -599,8 +735,6 @@ __device__ __forceinline__ int2 sample_cell(const DevView& v, int x, int y, uint
 __global__ void k_reset(int* cnt) {
   for (int i = threadIdx.x; i < CNT_SIZE; i += blockDim.x) cnt[i] = 0;
 }
-
-constexpr int BIN_ILP = 2;   // list entries a lane tests per step
 
 // The closest hit of a first ray from the leaves listed for its bin cell:
 // BIN_ILP entries at a time, tested against the same bound and merged in list
@@ -940,8 +1074,10 @@ __global__ void __launch_bounds__(EXT_BLOCK) k_shadow(KCtx c, int b) {
       float4 sd = E.sh_dir[k * Q + slot];
       float t;
       ++traced;
-      int hf = trace_bvh<true, STATS>(c.nodes, c.tri, c.nf, c.n4, p, xyz(sd), sd.w, exclude, t, sstack + threadIdx.x,
-                                      c.err, &ts);
+      int2 lr = k < c.nl ? light_bin_range(c, k, p) : make_int2(-1, -1);
+      int hf = lr.x >= 0 ? (bin_any_hit<STATS>(c, p, xyz(sd), sd.w, exclude, lr, &ts) ? 0 : -1)
+                         : trace_bvh<true, STATS>(c.nodes, c.tri, c.nf, c.n4, p, xyz(sd), sd.w, exclude, t,
+                                                  sstack + threadIdx.x, c.err, &ts);
       if (hf < 0) {
         L += xyz(sc);
         vis |= (k < c.nlt) ? (1 << k) : ENV_VIS;
