@@ -745,7 +745,7 @@ st_status enqueue_body(st_scene* s, const Plan& p, const KCtx& c, int Q, cudaStr
     k_scan_add<<<(unsigned)nb, SCAN_BLOCK, 0, st>>>(s->bin_start, P, s->bin_part);
     ST_CUDA(cudaMemsetAsync(s->bin_cur, 0, sizeof(int) * P, st));
     k_bin<1><<<g, 128, 0, st>>>(c, nv, s->bin_ok);
-    ST_CUDA(cudaMemcpyAsync(s->bin_total_host, s->bin_start + P, sizeof(int), cudaMemcpyDeviceToHost, st));
+    ST_CUDA(copy_async(s->bin_total_host, s->bin_start + P, sizeof(int), cudaMemcpyDeviceToHost, st));
     s->launches += 6;
   }
   if (p.lbins && !p.lbins_reused) {
@@ -769,7 +769,7 @@ st_status enqueue_body(st_scene* s, const Plan& p, const KCtx& c, int Q, cudaStr
     k_scan_add<<<(unsigned)nb, SCAN_BLOCK, 0, st>>>(s->lbin_start, P, s->lbin_part);
     ST_CUDA(cudaMemsetAsync(s->lbin_cur, 0, sizeof(int) * P, st));
     k_bin<1><<<g, 128, 0, st>>>(cl, nl, s->lbin_ok);
-    ST_CUDA(cudaMemcpyAsync(s->lbin_total_host, s->lbin_start + P, sizeof(int), cudaMemcpyDeviceToHost, st));
+    ST_CUDA(copy_async(s->lbin_total_host, s->lbin_start + P, sizeof(int), cudaMemcpyDeviceToHost, st));
     s->launches += 7;
   }
   if (p.shadow && !p.pairs.empty()) {

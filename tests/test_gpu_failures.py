@@ -138,6 +138,38 @@ def test_calls_fail_cleanly_and_leave_the_scene_usable(st, site, status, backwar
     assert abs(_free_bytes() - free0) <= 8 << 20
 
 
+@pytest.mark.parametrize("site,status", [("alloc", ST_ERR_OOM), ("copy", ST_ERR_CUDA)])
+def test_list_builds_fail_cleanly(st, site, status):
+    # a call of 2^20 primary rays under a point light builds the primary-visibility and the point-light lists:
+    # each allocation or copy of its first call fails in turn; the same call then succeeds with the image of a
+    # scene that never failed (the lists are built again, not reused half-made) and nothing leaks
+    sc = S.tiny()
+    sc.views = S.fibonacci_views(4, [256] * 4, [256] * 4, [4] * 4)
+    opts = st.make_opts()
+    ref = _reference(st, sc, opts)
+    free0 = _free_bytes()
+    fails = 0
+    for n in range(120):
+        scene = st.Scene.from_scene(sc)
+        st.inject_fault(site, n)
+        try:
+            _call(st, scene, sc, opts, False)
+            ok = True
+        except st.StError as e:
+            assert e.status == status, (n, str(e))
+            ok = False
+        finally:
+            st.inject_fault(site, -1)
+        np.testing.assert_array_equal(_call(st, scene, sc, opts, False), ref)
+        assert scene.stats()["device_error"] == 0
+        scene.close()
+        if ok:
+            break
+        fails += 1
+    assert fails >= 1 and ok
+    assert abs(_free_bytes() - free0) <= 8 << 20
+
+
 def test_growth_failure_keeps_no_stale_capacity(st):
     # a scene sized by a small call, then a larger call whose buffer growth fails at each allocation in turn:
     # the larger call succeeds on retry and matches a fresh scene
