@@ -22,7 +22,7 @@ import torch
 from . import st as _st
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "st_autotune.json")
-CHUNKS = (1 << 20, 1 << 21, 1 << 22, 1 << 23, 1 << 24)
+CHUNKS = (1 << 20, 1 << 21, 1 << 22, 1 << 23, 1 << 24, 1 << 25)
 PERSIST = (0, 2)
 
 
