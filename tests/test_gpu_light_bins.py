@@ -56,10 +56,14 @@ def _scene(name):
     return S.make(name)
 
 
-@pytest.mark.parametrize("name,B", [("edges", 3), ("two_spheres", 2), ("color_bleed_far_light", 3), ("scale", 2)])
+@pytest.mark.parametrize("name,B", [("edges", 3), ("two_spheres", 2), ("color_bleed_far_light", 3), ("scale", 2),
+                                    ("edges_view_lights", 2)])
 def test_listed_shadow_rays_equal_traversal(st, name, B):
-    sc = _scene(name)
+    sc = _scene(name.replace("_view_lights", ""))
     vs = S.fibonacci_views(4, [448, 384, 512, 320], [448, 384, 256, 320], [2, 2, 3, 2])
+    if name.endswith("_view_lights"):
+        # each view's own two lights (camera and offset) trace the BVH beside the scene's listed lights
+        vs = S.with_view_lights(vs, intensity=(2.0, 2.0, 2.0))
     if name == "color_bleed_far_light":
         vs = [dataclasses.replace(v, eye=tuple(np.array(v.eye) * 1.2 + [1.5, 1.0, 1.5]), target=(0.6, 0.5, 0.6))
               for v in vs]
